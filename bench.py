@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Benchmark: solves/s on the dense single-right-hand-side workload.
+
+Workload: A = (3 + 0.5 + 0.5i) I + G / sqrt(n), n = 8192, G iid complex
+normal (seed 0), one complex-normal right-hand side, x0 = 0 (the manual's
+Sec. 1 problem A x = y).  One step solves it to relative residual 1e-10 with
+each of BiCGSTAB, CGNR and QMR (Sec. 2.1).  The matrix (1.07 GB in complex128)
+is larger than L2, so no flush is needed between steps.
+
+Paths: "fp64" runs every iteration in complex128; "mixed" runs single-
+precision inner solves inside double-precision iterative refinement (the
+default when the library provides it).
+
+Multi-GPU: the solves do not shard; under torchrun every rank runs its own
+replica on its own GPU ("replicas only"), value = all ranks' solves / the
+slowest rank's time.
+
+--impl reference times the CPU oracle (the plain serial C++ restatement of
+the methods, oracle/) on this machine's host cores, each step one solve with
+the methods taken in turn.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no FP64 entry in the measured peaks)
+METRIC = "solves/s at rel-res 1e-10, mixed vs FP64 GPU; % HBM roofline; p50/p99 ms"
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ccg", "reference"], default="ccg")
+    p.add_argument("--n", type=int, default=8192)
+    p.add_argument("--methods", default="bicgstab,cgnr,qmr")
+    p.add_argument("--path", choices=["fp64", "mixed", "auto"], default="auto")
+    p.add_argument("--tol", type=float, default=1e-10)
+    p.add_argument("--maxit", type=int, default=1000)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args(argv)
+
+
+# ----------------------------------------------------------------- ranks
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+
+
+def reduce_max(value, world, device=None):
+    """Max of a float over ranks (identity for one rank)."""
+    if world == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(value, world, device=None):
+    if world == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- roofline helpers
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def profiled_traffic(kernel, src_files):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
+    when the summary is missing or the kernel's sources changed since."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256()
+    for f in src_files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    sha = h.hexdigest()[:16]
+    for line in open(path):
+        m = re.match(r"\s*(\S+)\s+(\S+)\s+(\d+)\s+sha=(\w+)", line)
+        if m and m.group(1) == kernel and m.group(4) == sha:
+            return int(m.group(3)), m.group(2)
+    return None
+
+
+SWEEP_KERNELS = {0: ("gemv_n_rows", 1), 1: ("gemv_tile_c", 1), 2: ("gemv_tile_both", 2)}
+KERNEL_SOURCES = ["paper_1208_4869_gb300/csrc/gemv.cuh", "paper_1208_4869_gb300/csrc/common.cuh"]
+
+
+def roofline(ccg, sweep_stats, n, dtype):
+    """Roofline of the sweep kind that took the most device time in the timed
+    region: algorithmic flops (8 n^2 per complex product; the fused QMR sweep
+    forms two) and bytes (the matrix, read once per sweep) over the mean
+    CUDA-event duration of its launches."""
+    kinds = {}
+    for kind, (cnt, ms, nbytes) in sweep_stats.items():
+        if cnt:
+            name, products = SWEEP_KERNELS[kind]
+            avg = ms / cnt
+            kinds[name] = {"launches": cnt, "total_ms": ms, "avg_ms": avg,
+                           "tflops": 8.0 * products * n * n / (avg * 1e-3) / 1e12,
+                           "gbs": nbytes / (avg * 1e-3) / 1e9, "bytes": nbytes}
+    if not kinds:
+        return None
+    top = max(kinds, key=lambda k: kinds[k]["total_ms"])
+    k = kinds[top]
+    hbm, hbm_src = peaks()
+    traffic = profiled_traffic("%s_%s" % (top, dtype), KERNEL_SOURCES)
+    if dtype == "c128":   # FP64 FMA pipe bound (4 DFMA per 16-byte element)
+        roof = {"kernel": "%s<%s>" % (top, dtype), "bound": "alu", "achieved": k["tflops"], "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": k["tflops"] / FP64_PEAK_TFLOPS,
+                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (no measured FP64 peak)"}
+    else:                 # HBM bound
+        roof = {"kernel": "%s<%s>" % (top, dtype), "bound": "hbm", "achieved": k["gbs"], "peak": hbm,
+                "unit": "GB/s", "frac": k["gbs"] / hbm, "peak_source": "%s copy bandwidth" % hbm_src}
+    roof["traffic"] = traffic[0] if traffic else None
+    roof["algorithmic_bytes"] = k["bytes"]
+    roof["avg_launch_ms"] = k["avg_ms"]
+    roof["hbm_equiv_gbs"] = k["gbs"]
+    roof["hbm_peak_gbs"] = hbm
+    roof["sweeps"] = kinds
+    return roof
+
+
+# ----------------------------------------------------------------- CPU oracle baseline
+def oracle_sample(A, y, methods, budget_s=20.0, tol=1e-10, maxit=1000):
+    """Time the CPU oracle as it stands: whole solves, methods in turn, until
+    about budget_s seconds are spent (at least one solve)."""
+    import oracle as O
+    op = O.DenseOp(A)
+    t0 = time.perf_counter()
+    done, i, iters = 0, 0, []
+    while True:
+        m = methods[i % len(methods)]
+        r = O.solve(op, m, y, tol=tol, maxit=maxit)
+        iters.append((m, r.iters))
+        done += 1
+        i += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt, iters
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1208_4869_gb300 import workloads as W
+    import oracle as O
+    methods = args.methods.split(",")
+    A, y = W.dense_system(args.n, 3.0, 0)
+    op = O.DenseOp(A)
+    for s in range(args.warmup):
+        O.solve(op, methods[s % len(methods)], y, tol=args.tol, maxit=args.maxit)
+    t0 = time.perf_counter()
+    lat = []
+    for s in range(args.steps):
+        t = time.perf_counter()
+        O.solve(op, methods[s % len(methods)], y, tol=args.tol, maxit=args.maxit)
+        lat.append(time.perf_counter() - t)
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": "dense single-RHS n=%d shift 3, bicgstab/cgnr/qmr to 1e-10" % args.n,
+                   "n": args.n, "methods": methods, "tol": args.tol, "l2": "inputs larger than L2 (A %.2f GB)"
+                   % (args.n * args.n * 16 / 1e9)},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": "%d whole solves, one per step, methods in turn" % args.steps},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "latency_ms": {"p50": 1e3 * statistics.median(lat), "p99": 1e3 * float(sorted(lat)[int(0.99 * (len(lat) - 1))])},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist_init(world, "nccl")
+    dev = torch.device("cuda", local)
+
+    from paper_1208_4869_gb300 import build as B
+    from paper_1208_4869_gb300 import ccg
+    from paper_1208_4869_gb300 import workloads as W
+    B.build()
+    ccg.lib()
+
+    methods = args.methods.split(",")
+    n = args.n
+    A, y = W.dense_system(n, 3.0, 0)
+    path = "fp64" if args.path in ("auto", "fp64") else args.path
+    if path != "fp64":
+        raise SystemExit("path %s not available" % path)
+    Ad = torch.from_numpy(A).to(dev)
+    yd = torch.from_numpy(y).to(dev)
+    xd = torch.zeros_like(yd)
+    stream = torch.cuda.current_stream(dev)
+    h = ccg.Handle(stream)
+    op = h.op_dense(Ad)
+
+    def one_step(lat=None, statuses=None):
+        for m in methods:
+            xd.zero_()
+            t = time.perf_counter()
+            st, info, _ = h.solve(m, op, yd, xd, tol=args.tol, maxit=args.maxit, want_hist=False)
+            if lat is not None:
+                lat.append(time.perf_counter() - t)
+            if statuses is not None:
+                statuses.append((m, st, info["iters"], info["true_relres"]))
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    h.timing(enable=True, reset=True)
+    launches0 = h.launch_count()
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lat, statuses = [], []
+    e0.record(stream)
+    for _ in range(args.steps):
+        one_step(lat, statuses)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(world)
+    elapsed_ms = e0.elapsed_time(e1)
+    launches = h.launch_count() - launches0
+    sweep_stats = {k: h.timing(kind=k) for k in (ccg.SWEEP_N, ccg.SWEEP_C, ccg.SWEEP_BOTH)}
+    h.timing(enable=False)
+    t_max_ms = reduce_max(elapsed_ms, world, dev)
+    solves = reduce_sum(args.steps * len(methods), world, dev)
+    value = solves / (t_max_ms / 1e3)
+
+    # end to end through the same call with pinned host buffers (y in, x0 in, x out)
+    e2e = None
+    if not args.no_e2e:
+        yh = torch.from_numpy(y).pin_memory()
+        xh = torch.zeros_like(yh).pin_memory()
+        for _ in range(max(1, args.warmup // 2)):
+            h.solve(methods[0], op, yh, xh, tol=args.tol, maxit=args.maxit, want_hist=False)
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for m in methods:
+                xh.zero_()
+                h.solve(m, op, yh, xh, tol=args.tol, maxit=args.maxit, want_hist=False)
+        dt = reduce_max(time.perf_counter() - t0, world, dev)
+        e2e = {"value": solves / dt, "unit": "solves/s", "h2d_bytes_per_step": 2 * len(methods) * y.nbytes,
+               "d2h_bytes_per_step": len(methods) * y.nbytes}
+
+    roof = roofline(ccg, sweep_stats, n, "c128")
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, nsolve, dt, its = oracle_sample(A, y, methods[:1], budget_s=15.0, tol=args.tol, maxit=args.maxit)
+        cpu = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": "%d whole %s solve(s) of the same system in %.1f s, serial C++" % (nsolve, methods[0], dt)}
+
+    ok = all(st == 0 and tr <= 10 * args.tol for _, st, _, tr in statuses)
+    if rank == 0:
+        lat_sorted = sorted(lat)
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": "dense single-RHS n=%d shift 3, bicgstab/cgnr/qmr to 1e-10" % n, "n": n,
+                       "methods": methods, "tol": args.tol, "path": path,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (A %.2f GB)" % (A.nbytes / 1e9)},
+            "path": path,
+            "iters": {m: it for m, _, it, _ in statuses[: len(methods)]},
+            "all_converged": ok,
+            "latency_ms": {"p50": 1e3 * statistics.median(lat_sorted),
+                           "p99": 1e3 * lat_sorted[int(0.99 * (len(lat_sorted) - 1))]},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

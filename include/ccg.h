@@ -1,0 +1,173 @@
+/*
+ * ccg.h -- C ABI of libccg, GB300 (sm_103a) complex Krylov solvers.
+ *
+ * Problem (CCGPAK 2.0 manual, Sec. 1): solve A x = y for a complex matrix A,
+ * unknown x and known right-hand side y, in single or double precision
+ * (abstract; Sec. 5 `ddprecision`).  The operator is kept apart from the
+ * iteration (Sec. 5: `matvec` for A x and `cmatvec` for A^H x), and the
+ * solve takes a tolerance and an iteration cap (Sec. 5 `cgmodule`:
+ * `epsilon_err`, `maxit`).  The methods are those of Sec. 2.1 (PIM:
+ * `bicgstab`, `cgnr`, `qmr`) and Sec. 2.2 (the Sarkar complex-symmetric CG),
+ * in their unpreconditioned textbook forms.
+ *
+ * Conventions shared by every entry point:
+ *  - Complex vectors and matrices are interleaved (re, im) pairs in the
+ *    operator's precision: CCG_C128 = two doubles (16 B per element),
+ *    CCG_C64 = two floats (8 B per element).
+ *  - Pointers named "device" must be CUDA device (or managed) memory that
+ *    stays valid for the call; nothing is copied or freed by the library
+ *    unless stated.  ccg_solve also accepts host pointers for y and x (see
+ *    there).
+ *  - A handle owns its CUDA stream binding and its workspace; all work is
+ *    enqueued on that stream.  A handle must not be used from two host
+ *    threads at once.  Calls return a ccg_status; negative values are
+ *    errors, after which ccg_last_error() gives a message.
+ *  - The library never falls back to host arithmetic: without a usable
+ *    CUDA device every call that computes returns CCG_ERR_CUDA.
+ */
+#ifndef CCG_H_
+#define CCG_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CCG_ABI_VERSION 1
+
+typedef enum {
+  CCG_BICGSTAB = 0, /* van der Vorst BiCGSTAB (Sec. 2.1, PIM `bicgstab`)      */
+  CCG_CGNR = 1,     /* CG on A^H A x = A^H y (Sec. 2.1, PIM `cgnr`)          */
+  CCG_QMR = 2,      /* Freund-Nachtigal QMR, no look-ahead (Sec. 2.1 `qmr`)  */
+  CCG_COCG = 3      /* complex-symmetric CG, unconjugated form (Sec. 2.2)    */
+} ccg_method;
+
+typedef enum { CCG_C64 = 0, CCG_C128 = 1 } ccg_dtype;
+
+typedef enum {
+  CCG_OK = 0,             /* converged: ||r_k|| / ||y|| <= tol              */
+  CCG_NOT_CONVERGED = 1,  /* maxit iterations done without meeting tol      */
+  CCG_BREAKDOWN = 2,      /* a divisor vanished; see ccg_info.breakdown     */
+  CCG_ERR_INVALID = -1,   /* bad argument                                   */
+  CCG_ERR_NOMEM = -2,     /* device allocation failed                       */
+  CCG_ERR_CUDA = -3,      /* CUDA runtime error or no device                */
+  CCG_ERR_NONFINITE = -4, /* NaN or Inf in y or in a residual               */
+  CCG_ERR_TIMEOUT = -5,   /* a bounded device wait expired                  */
+  CCG_ERR_UNSUPPORTED = -6 /* method/operator combination not available     */
+} ccg_status;
+
+/* Which scalar vanished on CCG_BREAKDOWN. */
+typedef enum {
+  CCG_BD_NONE = 0, CCG_BD_RHO = 1, CCG_BD_SIGMA = 2, CCG_BD_TT = 3, CCG_BD_OMEGA = 4,
+  CCG_BD_GAMMA = 5, CCG_BD_WW = 6, CCG_BD_XI = 7, CCG_BD_DELTA = 8, CCG_BD_EPS = 9,
+  CCG_BD_BETA = 10, CCG_BD_MU = 11
+} ccg_breakdown;
+
+/* Operator flags. */
+#define CCG_OP_SYMMETRIC 1 /* caller asserts A = A^T (required by CCG_COCG) */
+
+typedef struct ccg_handle ccg_handle;
+typedef struct ccg_operator ccg_operator;
+
+/* Result of one solve. */
+typedef struct {
+  int32_t iters;       /* completed iterations (BiCGSTAB's half-step exit counts as one) */
+  int32_t status;      /* ccg_status of the solve                                        */
+  int32_t breakdown;   /* ccg_breakdown                                                 */
+  int32_t reserved;
+  double relres;       /* last recurrence residual ||r_k|| / ||y||                      */
+  double true_relres;  /* ||y - A x|| / ||y|| recomputed from x at the end (-1 if skipped) */
+  double ynorm;        /* ||y||_2                                                        */
+} ccg_info;
+
+/* Create a handle bound to `stream` (a cudaStream_t; NULL = legacy default
+ * stream) on the current CUDA device.  *h receives the handle.  Returns
+ * CCG_ERR_CUDA when no device is usable. */
+ccg_status ccg_create(ccg_handle** h, void* stream);
+/* Destroy a handle and free its workspace (after synchronising its stream). */
+ccg_status ccg_destroy(ccg_handle* h);
+/* Rebind the handle to another stream. */
+ccg_status ccg_set_stream(ccg_handle* h, void* stream);
+/* Text of the last error recorded on this thread (never NULL). */
+const char* ccg_last_error(void);
+/* Text for a status code (never NULL). */
+const char* ccg_status_string(int status);
+/* Returns CCG_ABI_VERSION. */
+int ccg_abi_version(void);
+
+/* Dense operator on a caller-owned device matrix (the manual's `matvec` and
+ * `cmatvec`, Sec. 5, for a dense A).  A is n x n, row-major with leading
+ * dimension lda >= n, element (i, j) at A[i * lda + j], in precision `dtype`.
+ * The matrix is NOT copied: it must stay valid and unchanged while the
+ * operator is used.  flags: CCG_OP_SYMMETRIC or 0.  Errors: CCG_ERR_INVALID
+ * for n < 1, lda < n, a NULL pointer, or A not 8-byte (C64) / 16-byte
+ * (C128) aligned. */
+ccg_status ccg_op_dense(ccg_handle* h, ccg_dtype dtype, int64_t n, const void* A, int64_t lda, int flags,
+                        ccg_operator** op);
+/* Free an operator (not the caller's matrix). */
+ccg_status ccg_op_destroy(ccg_operator* op);
+/* Number of unknowns of an operator. */
+int64_t ccg_op_size(const ccg_operator* op);
+
+/* y = A x (trans = 0) or y = A^H x (trans = 1): the manual's `matvec` /
+ * `cmatvec` (Sec. 5).  x and y are device vectors of ccg_op_size(op)
+ * elements in the operator's precision; they must not overlap.  Enqueued on
+ * the handle's stream; returns without synchronising. */
+ccg_status ccg_matvec(ccg_handle* h, const ccg_operator* op, int trans, const void* x, void* y);
+
+/* Dot product of two device vectors of n elements, the Fortran
+ * `dot_product` of the manual (Sec. 1, Sec. 2.1): conj = 1 gives
+ * <u, v> = sum conj(u_i) v_i, conj = 0 gives [u, v] = sum u_i v_i.  The sum
+ * is accumulated in double; out2 (host) receives {re, im}.  Synchronises
+ * the handle's stream. */
+ccg_status ccg_dot(ccg_handle* h, ccg_dtype dtype, int64_t n, const void* u, const void* v, int conj,
+                   double* out2);
+
+/* Solve A x = y with `method` (Sec. 1 problem statement, Sec. 2 methods).
+ *  y        right-hand side, n elements; never written.
+ *  x        on entry the start vector x0, on exit the solution (the last
+ *           iterate also on CCG_NOT_CONVERGED / CCG_BREAKDOWN).
+ *           y and x may both be device pointers or both host pointers; with
+ *           host pointers the library copies them through its workspace.
+ *  tol      stop when ||r_k||_2 / ||y||_2 <= tol on the recurrence residual.
+ *  maxit    iteration cap (>= 0).
+ *  res_hist optional host array of maxit + 1 doubles: res_hist[k] =
+ *           ||r_k|| / ||y|| for k = 0 .. iters; may be NULL.
+ *  info     optional host struct receiving the result; info->true_relres is
+ *           computed (one extra operator application) only when info is not
+ *           NULL.
+ * y = 0 gives x = 0, iters = 0, CCG_OK.  CCG_COCG needs an operator made
+ * with CCG_OP_SYMMETRIC (else CCG_ERR_INVALID).  Blocks the calling thread
+ * until the solve has finished on the handle's stream.  Returns the solve's
+ * status (CCG_OK, CCG_NOT_CONVERGED, CCG_BREAKDOWN) or an error. */
+ccg_status ccg_solve(ccg_handle* h, ccg_method method, const ccg_operator* op, const void* y, void* x, double tol,
+                     int maxit, double* res_hist, ccg_info* info);
+
+/* Kinds of operator sweep, for timing. */
+typedef enum {
+  CCG_SWEEP_N = 0,    /* y = A x                          */
+  CCG_SWEEP_C = 1,    /* y = A^H x                        */
+  CCG_SWEEP_BOTH = 2, /* A p and A^H q from one read of A */
+  CCG_SWEEP_KINDS = 3
+} ccg_sweep_kind;
+
+/* Per-kernel timing of the operator sweeps: when enabled, each sweep that a
+ * call of this handle launches is bracketed by CUDA events on the handle's
+ * stream.  ccg_timing_read returns, for one sweep kind, the number of sweeps
+ * timed since the last reset, their total device milliseconds, and the
+ * algorithmic bytes of one sweep (the matrix bytes read).  Durations are
+ * collected when a solve ends (and by ccg_timing_read, which synchronises
+ * the stream). */
+ccg_status ccg_timing_enable(ccg_handle* h, int enable);
+ccg_status ccg_timing_read(ccg_handle* h, int kind, int64_t* sweeps, double* total_ms, double* bytes_per_sweep);
+ccg_status ccg_timing_reset(ccg_handle* h);
+
+/* Number of kernels this handle has launched since it was created. */
+int64_t ccg_launch_count(const ccg_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CCG_H_ */

@@ -1,0 +1,199 @@
+"""Python binding of libccg (include/ccg.h): argument marshalling only.
+
+Every computation runs in libccg.so's CUDA kernels; this module only turns
+torch tensors / numpy arrays into pointers and sizes.  There is no CPU
+fallback: if libccg.so is missing or no CUDA device is present, calls raise.
+
+Device memory and streams come from PyTorch: pass CUDA tensors (complex128
+or complex64) and, optionally, a torch.cuda.Stream.  ccg_solve also takes
+numpy arrays (host memory), which the library copies through its own
+workspace.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libccg.so")
+
+BICGSTAB, CGNR, QMR, COCG = 0, 1, 2, 3
+METHODS = {"bicgstab": BICGSTAB, "cgnr": CGNR, "qmr": QMR, "cocg": COCG}
+C64, C128 = 0, 1
+OK, NOT_CONVERGED, BREAKDOWN = 0, 1, 2
+ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
+OP_SYMMETRIC = 1
+SWEEP_N, SWEEP_C, SWEEP_BOTH = 0, 1, 2
+
+_lib = None
+
+
+class CcgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("libccg status %d: %s" % (status, msg))
+        self.status = status
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("breakdown", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("relres", ctypes.c_double), ("true_relres", ctypes.c_double),
+                ("ynorm", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+def lib():
+    """Load libccg.so (built by paper_1208_4869_gb300.build); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libccg.so is not built (%s); run paper_1208_4869_gb300.build.build()" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    L.ccg_abi_version.restype = i32
+    L.ccg_last_error.restype = ctypes.c_char_p
+    L.ccg_status_string.restype = ctypes.c_char_p
+    L.ccg_status_string.argtypes = [i32]
+    L.ccg_create.argtypes = [ctypes.POINTER(vp), vp]
+    L.ccg_destroy.argtypes = [vp]
+    L.ccg_set_stream.argtypes = [vp, vp]
+    L.ccg_op_dense.argtypes = [vp, i32, i64, vp, i64, i32, ctypes.POINTER(vp)]
+    L.ccg_op_destroy.argtypes = [vp]
+    L.ccg_op_size.restype = i64
+    L.ccg_op_size.argtypes = [vp]
+    L.ccg_matvec.argtypes = [vp, vp, i32, vp, vp]
+    L.ccg_dot.argtypes = [vp, i32, i64, vp, vp, i32, vp]
+    L.ccg_solve.argtypes = [vp, i32, vp, vp, vp, dbl, i32, vp, ctypes.POINTER(Info)]
+    L.ccg_timing_enable.argtypes = [vp, i32]
+    L.ccg_timing_read.argtypes = [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+    L.ccg_timing_reset.argtypes = [vp]
+    L.ccg_launch_count.restype = i64
+    L.ccg_launch_count.argtypes = [vp]
+    for name in ("ccg_create", "ccg_destroy", "ccg_set_stream", "ccg_op_dense", "ccg_op_destroy", "ccg_matvec",
+                 "ccg_dot", "ccg_solve", "ccg_timing_enable", "ccg_timing_read", "ccg_timing_reset"):
+        getattr(L, name).restype = i32
+    if L.ccg_abi_version() != 1:
+        raise ImportError("libccg ABI version mismatch")
+    _lib = L
+    return L
+
+
+def _check(st):
+    if st < 0:
+        raise CcgError(st, lib().ccg_last_error().decode())
+    return st
+
+
+def _dtype_code(dt):
+    s = str(dt)
+    if "complex128" in s:
+        return C128
+    if "complex64" in s:
+        return C64
+    raise TypeError("complex64 or complex128 expected, got %s" % s)
+
+
+def _ptr(a):
+    """Pointer of a torch tensor (device or host) or numpy array; must be contiguous."""
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous or a.ndim == 1
+        return ctypes.c_void_p(a.ctypes.data)
+    assert a.is_contiguous(), "contiguous tensor expected"
+    return ctypes.c_void_p(a.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(getattr(stream, "cuda_stream", stream) or 0)
+
+
+class Handle:
+    """ccg_create / ccg_destroy: a handle bound to a CUDA stream."""
+
+    def __init__(self, stream=None):
+        h = ctypes.c_void_p()
+        _check(lib().ccg_create(ctypes.byref(h), _stream_ptr(stream)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            lib().ccg_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    __del__ = close
+
+    def set_stream(self, stream):
+        _check(lib().ccg_set_stream(self.h, _stream_ptr(stream)))
+
+    def op_dense(self, A, symmetric=False):
+        """ccg_op_dense on a CUDA tensor A (n x n, row-major, complex64/128); A is not copied."""
+        assert A.dim() == 2 and A.shape[0] == A.shape[1] and A.is_cuda
+        assert A.stride(1) == 1
+        op = ctypes.c_void_p()
+        _check(lib().ccg_op_dense(self.h, _dtype_code(A.dtype), A.shape[0], _ptr(A), A.stride(0),
+                                  OP_SYMMETRIC if symmetric else 0, ctypes.byref(op)))
+        return Operator(op, A, _dtype_code(A.dtype))
+
+    def matvec(self, op, x, y, trans=False):
+        """ccg_matvec: y = A x (trans=False) or A^H x (trans=True), device vectors."""
+        _check(lib().ccg_matvec(self.h, op.op, int(bool(trans)), _ptr(x), _ptr(y)))
+        return y
+
+    def dot(self, u, v, conj=True):
+        """ccg_dot: <u, v> (conj) or [u, v] of two device vectors, as a Python complex."""
+        out = np.zeros(2)
+        _check(lib().ccg_dot(self.h, _dtype_code(u.dtype), u.numel(), _ptr(u), _ptr(v), int(bool(conj)),
+                             ctypes.c_void_p(out.ctypes.data)))
+        return complex(out[0], out[1])
+
+    def solve(self, method, op, y, x, tol=1e-10, maxit=1000, want_hist=True, want_info=True):
+        """ccg_solve.  x holds x0 and receives the solution.  Returns (status, info dict, hist)."""
+        m = METHODS[method] if isinstance(method, str) else int(method)
+        hist = np.full(maxit + 1, np.nan) if want_hist else None
+        info = Info()
+        st = lib().ccg_solve(self.h, m, op.op, _ptr(y), _ptr(x), float(tol), int(maxit),
+                             ctypes.c_void_p(hist.ctypes.data) if want_hist else ctypes.c_void_p(0),
+                             ctypes.byref(info) if want_info else None)
+        _check(st)
+        d = info.as_dict() if want_info else {}
+        if want_hist and want_info:
+            hist = hist[: info.iters + 1]
+        return st, d, hist
+
+    def timing(self, enable=None, reset=False, kind=SWEEP_N):
+        """Per-sweep CUDA-event timing of one sweep kind: (sweeps, total_ms, bytes_per_sweep)."""
+        if enable is not None:
+            _check(lib().ccg_timing_enable(self.h, int(bool(enable))))
+        if reset:
+            _check(lib().ccg_timing_reset(self.h))
+        n = ctypes.c_int64()
+        ms = ctypes.c_double()
+        b = ctypes.c_double()
+        _check(lib().ccg_timing_read(self.h, int(kind), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(b)))
+        return n.value, ms.value, b.value
+
+    def launch_count(self):
+        """ccg_launch_count: kernels this handle has launched."""
+        return int(lib().ccg_launch_count(self.h))
+
+
+class Operator:
+    def __init__(self, op, keep, dtype_code):
+        self.op = op
+        self._keep = keep
+        self.dtype_code = dtype_code
+
+    @property
+    def n(self):
+        return int(lib().ccg_op_size(self.op))
+
+    def close(self):
+        if getattr(self, "op", None) and self.op.value:
+            lib().ccg_op_destroy(self.op)
+            self.op = ctypes.c_void_p()
+
+    __del__ = close

@@ -1,0 +1,246 @@
+// C ABI of libccg (include/ccg.h): handles, operators, argument checks,
+// workspace, timing, and dispatch to the solver and operator code.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace ccg {
+
+static thread_local std::string g_error = "";
+
+void set_error(const std::string& msg) { g_error = msg; }
+
+#define API_CUDA(call)                                                                 \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+      return CCG_ERR_CUDA;                                                             \
+    }                                                                                  \
+  } while (0)
+
+int arena_reserve(ccg_handle* h, size_t bytes) {
+  if (bytes <= h->arena_bytes) return CCG_OK;
+  if (h->arena) {
+    API_CUDA(cudaStreamSynchronize(h->stream));
+    API_CUDA(cudaFree(h->arena));
+    h->arena = nullptr;
+    h->arena_bytes = 0;
+  }
+  const size_t want = bytes + bytes / 8;  // headroom against small growth steps
+  if (cudaMalloc(&h->arena, want) != cudaSuccess) {
+    cudaGetLastError();
+    h->arena = nullptr;
+    set_error("workspace allocation of " + std::to_string(want) + " bytes failed");
+    return CCG_ERR_NOMEM;
+  }
+  h->arena_bytes = want;
+  return CCG_OK;
+}
+
+void timing_begin(ccg_handle* h) {
+  if (!h->timing) return;
+  if (h->tev_used + 2 > h->tev.size()) {
+    for (int i = 0; i < 64; ++i) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      h->tev.push_back(e);
+      h->tev_kind.push_back(0);
+    }
+  }
+  cudaEventRecord(h->tev[h->tev_used], h->stream);
+}
+
+void timing_end(ccg_handle* h, int kind, double bytes) {
+  if (!h->timing) return;
+  cudaEventRecord(h->tev[h->tev_used + 1], h->stream);
+  h->tev_kind[h->tev_used] = kind;
+  h->tev_used += 2;
+  h->bytes_per_sweep[kind] = bytes;
+}
+
+// Sum the recorded sweep durations (the stream must be idle) and recycle the events.
+void timing_collect(ccg_handle* h) {
+  for (size_t i = 0; i + 1 < h->tev_used; i += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->tev[i], h->tev[i + 1]) == cudaSuccess) {
+      h->timed_ms[h->tev_kind[i]] += ms;
+      h->timed_sweeps[h->tev_kind[i]] += 1;
+    }
+  }
+  cudaGetLastError();
+  h->tev_used = 0;
+}
+
+static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+}  // namespace ccg
+
+using namespace ccg;
+
+extern "C" {
+
+int ccg_abi_version(void) { return CCG_ABI_VERSION; }
+
+const char* ccg_last_error(void) { return g_error.c_str(); }
+
+const char* ccg_status_string(int status) {
+  switch (status) {
+    case CCG_OK: return "converged";
+    case CCG_NOT_CONVERGED: return "iteration cap reached";
+    case CCG_BREAKDOWN: return "breakdown";
+    case CCG_ERR_INVALID: return "invalid argument";
+    case CCG_ERR_NOMEM: return "out of device memory";
+    case CCG_ERR_CUDA: return "CUDA error";
+    case CCG_ERR_NONFINITE: return "non-finite value";
+    case CCG_ERR_TIMEOUT: return "device wait timed out";
+    case CCG_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+ccg_status ccg_create(ccg_handle** out, void* stream) {
+  if (!out) { set_error("ccg_create: NULL output"); return CCG_ERR_INVALID; }
+  *out = nullptr;
+  int dev = 0, count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) {
+    cudaGetLastError();
+    set_error("ccg_create: no CUDA device");
+    return CCG_ERR_CUDA;
+  }
+  API_CUDA(cudaGetDevice(&dev));
+  ccg_handle* h = new (std::nothrow) ccg_handle();
+  if (!h) { set_error("ccg_create: host allocation failed"); return CCG_ERR_NOMEM; }
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->device = dev;
+  cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (h->num_sms <= 0) h->num_sms = 1;
+  if (cudaHostAlloc(&h->pinned, 2 * sizeof(Poll), cudaHostAllocDefault) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->poll_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->poll_ev[1], cudaEventDisableTiming) != cudaSuccess) {
+    set_error(std::string("ccg_create: ") + cudaGetErrorString(cudaGetLastError()));
+    ccg_destroy(h);
+    return CCG_ERR_CUDA;
+  }
+  std::memset(h->pinned, 0, 2 * sizeof(Poll));
+  *out = h;
+  return CCG_OK;
+}
+
+ccg_status ccg_destroy(ccg_handle* h) {
+  if (!h) return CCG_OK;
+  cudaStreamSynchronize(h->stream);
+  if (h->arena) cudaFree(h->arena);
+  if (h->pinned) cudaFreeHost(h->pinned);
+  for (int i = 0; i < 2; ++i)
+    if (h->poll_ev[i]) cudaEventDestroy(h->poll_ev[i]);
+  for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
+  cudaGetLastError();
+  delete h;
+  return CCG_OK;
+}
+
+ccg_status ccg_set_stream(ccg_handle* h, void* stream) {
+  if (!h) { set_error("ccg_set_stream: NULL handle"); return CCG_ERR_INVALID; }
+  API_CUDA(cudaStreamSynchronize(h->stream));
+  h->stream = static_cast<cudaStream_t>(stream);
+  return CCG_OK;
+}
+
+ccg_status ccg_op_dense(ccg_handle* h, ccg_dtype dtype, int64_t n, const void* A, int64_t lda, int flags,
+                        ccg_operator** op) {
+  if (!op) { set_error("ccg_op_dense: NULL output"); return CCG_ERR_INVALID; }
+  *op = nullptr;
+  if (!h || !A) { set_error("ccg_op_dense: NULL handle or matrix"); return CCG_ERR_INVALID; }
+  if (dtype != CCG_C64 && dtype != CCG_C128) { set_error("ccg_op_dense: bad dtype"); return CCG_ERR_INVALID; }
+  if (n < 1 || lda < n) { set_error("ccg_op_dense: need n >= 1 and lda >= n"); return CCG_ERR_INVALID; }
+  if (n > (int64_t(1) << 31)) { set_error("ccg_op_dense: n too large"); return CCG_ERR_INVALID; }
+  const size_t esz = dtype == CCG_C128 ? 16 : 8;
+  if (!aligned(A, esz)) { set_error("ccg_op_dense: matrix not aligned to its element size"); return CCG_ERR_INVALID; }
+  if (flags & ~CCG_OP_SYMMETRIC) { set_error("ccg_op_dense: unknown flags"); return CCG_ERR_INVALID; }
+  ccg_operator* o = new (std::nothrow) ccg_operator();
+  if (!o) { set_error("ccg_op_dense: host allocation failed"); return CCG_ERR_NOMEM; }
+  o->kind = CCG_OPK_DENSE;
+  o->dtype = dtype;
+  o->n = n;
+  o->flags = flags;
+  o->A = A;
+  o->lda = lda;
+  o->unit = 1;
+  if (dtype == CCG_C64 && (n % 2 == 0) && (lda % 2 == 0) && aligned(A, 16)) o->unit = 2;
+  *op = o;
+  return CCG_OK;
+}
+
+ccg_status ccg_op_destroy(ccg_operator* op) {
+  delete op;
+  return CCG_OK;
+}
+
+int64_t ccg_op_size(const ccg_operator* op) { return op ? op->n : 0; }
+
+ccg_status ccg_matvec(ccg_handle* h, const ccg_operator* op, int trans, const void* x, void* y) {
+  if (!h || !op || !x || !y) { set_error("ccg_matvec: NULL argument"); return CCG_ERR_INVALID; }
+  if (trans != 0 && trans != 1) { set_error("ccg_matvec: trans must be 0 or 1"); return CCG_ERR_INVALID; }
+  const size_t esz = op->dtype == CCG_C128 ? 16 : 8;
+  if (!aligned(x, op->unit * esz) || !aligned(y, esz)) { set_error("ccg_matvec: misaligned vector"); return CCG_ERR_INVALID; }
+  return static_cast<ccg_status>(matvec_dense(h, op, trans, x, y));
+}
+
+ccg_status ccg_dot(ccg_handle* h, ccg_dtype dtype, int64_t n, const void* u, const void* v, int conj, double* out2) {
+  if (!h || !u || !v || !out2) { set_error("ccg_dot: NULL argument"); return CCG_ERR_INVALID; }
+  if (n < 0 || (dtype != CCG_C64 && dtype != CCG_C128)) { set_error("ccg_dot: bad size or dtype"); return CCG_ERR_INVALID; }
+  if (n == 0) { out2[0] = out2[1] = 0.0; return CCG_OK; }
+  return static_cast<ccg_status>(dot_device(h, dtype, n, u, v, conj ? 1 : 0, out2));
+}
+
+ccg_status ccg_solve(ccg_handle* h, ccg_method method, const ccg_operator* op, const void* y, void* x, double tol,
+                     int maxit, double* res_hist, ccg_info* info) {
+  if (!h || !op || !y || !x) { set_error("ccg_solve: NULL argument"); return CCG_ERR_INVALID; }
+  if (method < CCG_BICGSTAB || method > CCG_COCG) { set_error("ccg_solve: unknown method"); return CCG_ERR_INVALID; }
+  if (maxit < 0 || !(tol >= 0.0)) { set_error("ccg_solve: need maxit >= 0 and tol >= 0"); return CCG_ERR_INVALID; }
+  if (method == CCG_COCG && !(op->flags & CCG_OP_SYMMETRIC)) {
+    set_error("ccg_solve: COCG needs an operator flagged CCG_OP_SYMMETRIC");
+    return CCG_ERR_INVALID;
+  }
+  const size_t esz = op->dtype == CCG_C128 ? 16 : 8;
+  if (!aligned(y, esz) || !aligned(x, op->unit * esz)) { set_error("ccg_solve: misaligned vector"); return CCG_ERR_INVALID; }
+  return static_cast<ccg_status>(solve_dense(h, method, op, y, x, tol, maxit, res_hist, info));
+}
+
+ccg_status ccg_timing_enable(ccg_handle* h, int enable) {
+  if (!h) return CCG_ERR_INVALID;
+  h->timing = enable != 0;
+  return CCG_OK;
+}
+
+ccg_status ccg_timing_read(ccg_handle* h, int kind, int64_t* sweeps, double* total_ms, double* bytes_per_sweep) {
+  if (!h || kind < 0 || kind >= CCG_SWEEP_KINDS) { set_error("ccg_timing_read: bad handle or kind"); return CCG_ERR_INVALID; }
+  API_CUDA(cudaStreamSynchronize(h->stream));
+  timing_collect(h);
+  if (sweeps) *sweeps = h->timed_sweeps[kind];
+  if (total_ms) *total_ms = h->timed_ms[kind];
+  if (bytes_per_sweep) *bytes_per_sweep = h->bytes_per_sweep[kind];
+  return CCG_OK;
+}
+
+ccg_status ccg_timing_reset(ccg_handle* h) {
+  if (!h) return CCG_ERR_INVALID;
+  API_CUDA(cudaStreamSynchronize(h->stream));
+  timing_collect(h);
+  for (int k = 0; k < CCG_SWEEP_KINDS; ++k) {
+    h->timed_sweeps[k] = 0;
+    h->timed_ms[k] = 0.0;
+  }
+  return CCG_OK;
+}
+
+int64_t ccg_launch_count(const ccg_handle* h) { return h ? h->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,186 @@
+// Dense complex matrix-vector kernels: the manual's `matvec` (y = A x) and
+// `cmatvec` (y = A^H x) for a dense row-major A (Sec. 5), plus the fused
+// sweep that forms A p and A^H q from one read of A (both products of one
+// QMR iteration, Sec. 2.1).
+//
+// The matrix streams from HBM once per sweep in 16-byte units (one complex
+// double, or two complex floats) through loads that skip L1, so that the
+// reused vector stays in L1.  Two shapes:
+//   * gemv_n_rows: one warp per row, lanes striding along the row; the row
+//     sum is a warp reduction and is written directly (no scratch).
+//   * gemv_tile: a block owns a column chunk (each lane E units, strided by
+//     32 units so every warp load is 512 contiguous bytes) and a row range.
+//     A^H x accumulates per column in registers and leaves one partial per
+//     row range; A x (in the fused sweep) leaves one partial per column
+//     chunk.  Consumers sum the partials (MvOut::get), which keeps the
+//     sweep free of atomics and the sums deterministic.
+#pragma once
+
+#include "common.cuh"
+
+namespace ccg {
+
+// 16-byte load unit holding U complex numbers of precision R.
+template <class R, int U> struct Unit;
+template <> struct Unit<double, 1> {
+  typedef double2 L;
+  static __device__ __forceinline__ double2 get(const L& v, int) { return v; }
+  static __device__ __forceinline__ L zero() { return make_double2(0.0, 0.0); }
+};
+template <> struct Unit<float, 2> {
+  typedef float4 L;
+  static __device__ __forceinline__ float2 get(const L& v, int c) {
+    return c == 0 ? make_float2(v.x, v.y) : make_float2(v.z, v.w);
+  }
+  static __device__ __forceinline__ L zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+};
+template <> struct Unit<float, 1> {
+  typedef float2 L;
+  static __device__ __forceinline__ float2 get(const L& v, int) { return v; }
+  static __device__ __forceinline__ L zero() { return make_float2(0.f, 0.f); }
+};
+
+__device__ __forceinline__ double2 ldg_unit(const double2* p) { return __ldg(p); }
+__device__ __forceinline__ float4 ldg_unit(const float4* p) { return __ldg(p); }
+__device__ __forceinline__ float2 ldg_unit(const float2* p) { return __ldg(p); }
+
+template <class T> __device__ __forceinline__ T warp_csum(T s) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s.x += __shfl_down_sync(0xffffffffu, s.x, o);
+    s.y += __shfl_down_sync(0xffffffffu, s.y, o);
+  }
+  return s;
+}
+
+// Result of an operator application: either a plain vector y, or `nparts`
+// partial vectors P[part * ld + i] whose sum is y (summed in part order).
+template <class R> struct MvOut {
+  const cx<R>* y;
+  const cx<R>* P;
+  int64_t ld;
+  int nparts;
+  __device__ __forceinline__ cx<R> get(int64_t i) const {
+    if (P == nullptr) return y[i];
+    cx<R> s = P[i];
+    for (int q = 1; q < nparts; ++q) s = cadd(s, P[(int64_t)q * ld + i]);
+    return s;
+  }
+};
+
+// y[i] = (A x)_i, one warp per row.  Requires n % U == 0 and 16-byte aligned
+// rows when U * sizeof(cx<R>) == 16.
+template <class R, int U>
+__global__ void __launch_bounds__(kBlock) gemv_n_rows(const cx<R>* __restrict__ A, int64_t lda, int64_t n,
+                                                      const cx<R>* __restrict__ x, cx<R>* __restrict__ y,
+                                                      const SolveState* __restrict__ st) {
+  typedef Unit<R, U> Un;
+  typedef typename Un::L L;
+  if (st != nullptr && (st->poll.done || st->half)) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t nunits = n / U;
+  const L* xv = reinterpret_cast<const L*>(x);
+  for (int64_t row = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); row < n; row += (int64_t)gridDim.x * kWarps) {
+    const L* a = reinterpret_cast<const L*>(A + row * lda);
+    cx<R> s0 = mk<R>(0, 0), s1 = mk<R>(0, 0);
+    int64_t u = lane;
+    for (; u + 96 < nunits; u += 128) {
+      const L a0 = ld_stream(a + u), a1 = ld_stream(a + u + 32), a2 = ld_stream(a + u + 64), a3 = ld_stream(a + u + 96);
+      const L x0 = ldg_unit(xv + u), x1 = ldg_unit(xv + u + 32), x2 = ldg_unit(xv + u + 64), x3 = ldg_unit(xv + u + 96);
+#pragma unroll
+      for (int c = 0; c < U; ++c) {
+        s0 = cfma(Un::get(a0, c), Un::get(x0, c), s0);
+        s1 = cfma(Un::get(a1, c), Un::get(x1, c), s1);
+        s0 = cfma(Un::get(a2, c), Un::get(x2, c), s0);
+        s1 = cfma(Un::get(a3, c), Un::get(x3, c), s1);
+      }
+    }
+    for (; u < nunits; u += 32) {
+      const L a0 = ld_stream(a + u), x0 = ldg_unit(xv + u);
+#pragma unroll
+      for (int c = 0; c < U; ++c) s0 = cfma(Un::get(a0, c), Un::get(x0, c), s0);
+    }
+    const cx<R> s = warp_csum(cadd(s0, s1));
+    if (lane == 0) y[row] = s;
+  }
+}
+
+// Column-tiled sweep.  grid = (column chunks, row ranges).  With Y1 it
+// writes P1[chunk * n + row] = sum over the chunk's columns of A[row, c] x1[c];
+// with Y2 it writes P2[range * n + col] = sum over the range's rows of
+// conj(A[row, col]) x2[row].
+template <class R, int U, int E, bool Y1, bool Y2>
+__global__ void __launch_bounds__(kBlock) gemv_tile(const cx<R>* __restrict__ A, int64_t lda, int64_t n,
+                                                    int64_t rows_per_range, const cx<R>* __restrict__ x1,
+                                                    const cx<R>* __restrict__ x2, cx<R>* __restrict__ P1,
+                                                    cx<R>* __restrict__ P2, const SolveState* __restrict__ st) {
+  typedef Unit<R, U> Un;
+  typedef typename Un::L L;
+  constexpr int CBU = 32 * E;  // units per column chunk
+  if (st != nullptr && (st->poll.done || st->half)) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t nunits = n / U;
+  const int64_t unit0 = (int64_t)blockIdx.x * CBU;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_range;
+  const int64_t r1 = r0 + rows_per_range < n ? r0 + rows_per_range : n;
+
+  L xl[E];
+  if (Y1) {
+    const L* xv = reinterpret_cast<const L*>(x1);
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const int64_t u = unit0 + lane + 32 * j;
+      xl[j] = u < nunits ? ldg_unit(xv + u) : Un::zero();
+    }
+  }
+  cx<R> acc[E][U];
+#pragma unroll
+  for (int j = 0; j < E; ++j)
+#pragma unroll
+    for (int c = 0; c < U; ++c) acc[j][c] = mk<R>(0, 0);
+
+  for (int64_t r = r0 + warp; r < r1; r += kWarps) {
+    const L* a = reinterpret_cast<const L*>(A + r * lda);
+    L av[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const int64_t u = unit0 + lane + 32 * j;
+      av[j] = u < nunits ? ld_stream(a + u) : Un::zero();
+    }
+    if (Y2) {
+      const cx<R> xr = x2[r];
+#pragma unroll
+      for (int j = 0; j < E; ++j)
+#pragma unroll
+        for (int c = 0; c < U; ++c) acc[j][c] = cfma_conj(Un::get(av[j], c), xr, acc[j][c]);
+    }
+    if (Y1) {
+      cx<R> s = mk<R>(0, 0);
+#pragma unroll
+      for (int j = 0; j < E; ++j)
+#pragma unroll
+        for (int c = 0; c < U; ++c) s = cfma(Un::get(av[j], c), Un::get(xl[j], c), s);
+      s = warp_csum(s);
+      if (lane == 0) P1[(int64_t)blockIdx.x * n + r] = s;
+    }
+  }
+  if (Y2) {
+    __shared__ cx<R> sm[kWarps][CBU * U];
+#pragma unroll
+    for (int j = 0; j < E; ++j)
+#pragma unroll
+      for (int c = 0; c < U; ++c) sm[warp][(lane + 32 * j) * U + c] = acc[j][c];
+    __syncthreads();
+    for (int t = threadIdx.x; t < CBU * U; t += kBlock) {
+      const int64_t col = unit0 * U + t;
+      if (col < n) {
+        cx<R> s = sm[0][t];
+#pragma unroll
+        for (int w = 1; w < kWarps; ++w) s = cadd(s, sm[w][t]);
+        P2[(int64_t)blockIdx.y * n + col] = s;
+      }
+    }
+  }
+}
+
+}  // namespace ccg

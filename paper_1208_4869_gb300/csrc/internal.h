@@ -1,0 +1,69 @@
+// Host-side structures of libccg shared by its translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ccg.h"
+
+namespace ccg {
+struct SolveState;
+void set_error(const std::string& msg);
+}  // namespace ccg
+
+enum { CCG_OPK_DENSE = 0 };
+
+struct ccg_operator {
+  int kind = CCG_OPK_DENSE;
+  ccg_dtype dtype = CCG_C128;
+  int64_t n = 0;
+  int flags = 0;
+  // dense
+  const void* A = nullptr;
+  int64_t lda = 0;
+  int unit = 1;  // complex numbers per 16-byte load (2 only for aligned complex64 with even n, lda)
+};
+
+struct ccg_handle {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  // grow-only device arena holding vectors, partial sums and solve state
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  // pinned host poll slots and their events
+  void* pinned = nullptr;
+  cudaEvent_t poll_ev[2] = {nullptr, nullptr};
+  // operator-sweep timing, per ccg_sweep_kind
+  bool timing = false;
+  std::vector<cudaEvent_t> tev;  // start/stop pairs
+  std::vector<int> tev_kind;     // sweep kind of each pair
+  size_t tev_used = 0;
+  int64_t timed_sweeps[CCG_SWEEP_KINDS] = {0, 0, 0};
+  double timed_ms[CCG_SWEEP_KINDS] = {0.0, 0.0, 0.0};
+  double bytes_per_sweep[CCG_SWEEP_KINDS] = {0.0, 0.0, 0.0};
+  // kernels launched by this handle
+  int64_t launches = 0;
+};
+
+namespace ccg {
+
+// Ensure the arena holds at least `bytes`; synchronises the stream before a
+// reallocation.  Returns a ccg_status.
+int arena_reserve(ccg_handle* h, size_t bytes);
+
+// Timing hooks around one operator sweep (no-ops unless timing is enabled).
+void timing_begin(ccg_handle* h);
+void timing_end(ccg_handle* h, int kind, double bytes);
+void timing_collect(ccg_handle* h);
+
+// Entry points implemented in solve.cu.
+int solve_dense(ccg_handle* h, int method, const ccg_operator* op, const void* y, void* x, double tol, int maxit,
+                double* res_hist, ccg_info* info);
+int matvec_dense(ccg_handle* h, const ccg_operator* op, int trans, const void* x, void* y);
+int dot_device(ccg_handle* h, ccg_dtype dtype, int64_t n, const void* u, const void* v, int conj, double* out2);
+
+}  // namespace ccg

@@ -1,0 +1,1008 @@
+// Krylov iterations on the GPU: BiCGSTAB, CGNR, QMR (Sec. 2.1, the PIM
+// methods) and the complex-symmetric CG (Sec. 2.2), unpreconditioned.
+//
+// One iteration is a fixed sequence of kernels on the handle's stream:
+// operator sweeps (gemv.cuh) and "phase" kernels.  A phase kernel makes one
+// pass over the vectors doing a method's elementwise updates, accumulates
+// the dot products the next step needs, reduces them in a single pass over
+// the grid (common.cuh), and in the last block computes the method's scalar
+// recurrences into the device SolveState.  Scalars never travel to the host
+// during a solve.  Every kernel first reads SolveState::poll.done and returns
+// at once when the solve has stopped, so the host may enqueue iterations
+// ahead of the convergence test and only polls a small record every few
+// iterations.
+//
+// Readings of the methods (the manual prints no recurrences): stopping on
+// ||r_k|| / ||y|| <= tol with the recurrence residual; shadow vectors equal
+// to r_0; BiCGSTAB's half-step exit on ||s||; QMR with A^H and conjugated
+// products; COCG with the unconjugated form [u, v] = sum u_i v_i.  Dot
+// products accumulate in double at both precisions, and the scalars are
+// formed in double and rounded to the working precision for the vector
+// updates.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+
+#include "common.cuh"
+#include "gemv.cuh"
+#include "internal.h"
+
+namespace ccg {
+
+// ---------------------------------------------------------------------------
+// Phase kernel and accumulation helpers.
+// ---------------------------------------------------------------------------
+struct PhaseBase {
+  static constexpr bool kReduce = true;
+  __device__ __forceinline__ bool skip(const SolveState*) const { return false; }
+  __device__ __forceinline__ void load(const SolveState*) {}
+};
+
+template <class P>
+__global__ void __launch_bounds__(kBlock) phase_kernel(P p, SolveState* st, Red red) {
+  if (st->poll.done || p.skip(st)) return;
+  p.load(st);
+  double acc[P::NQ];
+#pragma unroll
+  for (int q = 0; q < P::NQ; ++q) acc[q] = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * kBlock;
+  for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < p.n; i += stride) p.element(i, acc);
+  if (P::kReduce) {
+    double tot[P::NQ];
+    if (grid_reduce<P::NQ>(acc, red.partials, red.counter, tot) && threadIdx.x == 0) p.finish(tot, st);
+  }
+}
+
+template <class T> __device__ __forceinline__ void acc_dotc(double* acc, T u, T v) {  // conj(u) v
+  const double2 a = widen(u), b = widen(v);
+  acc[0] += a.x * b.x + a.y * b.y;
+  acc[1] += a.x * b.y - a.y * b.x;
+}
+template <class T> __device__ __forceinline__ void acc_dotu(double* acc, T u, T v) {  // u v
+  const double2 a = widen(u), b = widen(v);
+  acc[0] += a.x * b.x - a.y * b.y;
+  acc[1] += a.x * b.y + a.y * b.x;
+}
+template <class T> __device__ __forceinline__ void acc_nrm2(double* acc, T u) {
+  const double2 a = widen(u);
+  acc[0] += a.x * a.x + a.y * a.y;
+}
+template <class R> __device__ __forceinline__ bool tiny(double2 s) { return cabs(s) < tiny_guard<R>(); }
+template <class R> __device__ __forceinline__ bool tiny(double s) { return fabs(s) < tiny_guard<R>(); }
+__device__ __forceinline__ bool nonfinite(double v) { return !(v == v) || isinf(v); }
+
+// Record the end of iteration k (residual rel).  The checks follow the
+// methods' order: converged, then a breakdown found in this iteration
+// (bd != 0), then the iteration cap.  Returns true if the solve stops.
+__device__ __forceinline__ bool end_iteration(SolveState* st, int k, double rel, int bd) {
+  st->poll.k = k;
+  st->poll.relres = rel;
+  st->hist[k] = rel;
+  if (nonfinite(rel)) { st->poll.status = ST_NONFINITE; st->poll.done = 1; return true; }
+  if (rel <= st->tol) { st->poll.status = ST_OK; st->poll.done = 1; return true; }
+  if (bd) { st->poll.status = ST_BREAKDOWN; st->poll.breakdown = bd; st->poll.done = 1; return true; }
+  if (k >= st->maxit) { st->poll.status = ST_NOT_CONVERGED; st->poll.done = 1; return true; }
+  return false;
+}
+__device__ __forceinline__ void set_breakdown(SolveState* st, int which) {
+  st->poll.status = ST_BREAKDOWN;
+  st->poll.breakdown = which;
+  st->poll.done = 1;
+}
+
+enum { M_BICGSTAB = CCG_BICGSTAB, M_CGNR = CCG_CGNR, M_QMR = CCG_QMR, M_COCG = CCG_COCG };
+
+// ---------------------------------------------------------------------------
+// Start of every method: r = y - A x0, ||y||, ||r||, and the method's first
+// scalars; the copies of r each method keeps (shadow vector, p, ...).
+// ---------------------------------------------------------------------------
+template <class R> struct InitR : PhaseBase {
+  static constexpr int NQ = 5;  // ||y||^2, ||r||^2, non-finite count in y, [r, r]
+  int64_t n;
+  const cx<R>* y;
+  MvOut<R> ax;
+  cx<R>* r;
+  cx<R>* c1;
+  cx<R>* c2;
+  int method;
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    const cx<R> yi = y[i];
+    const cx<R> ri = csub(yi, ax.get(i));
+    r[i] = ri;
+    if (c1) c1[i] = ri;
+    if (c2) c2[i] = ri;
+    acc_nrm2(acc, yi);
+    acc_nrm2(acc + 1, ri);
+    if (!(isfinite((double)yi.x) && isfinite((double)yi.y))) acc[2] += 1.0;
+    if (method == M_COCG) acc_dotu(acc + 3, ri, ri);
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    st->poll.k = 0;
+    if (t[2] != 0.0) { st->poll.status = ST_NONFINITE; st->poll.done = 1; return; }
+    const double yn = sqrt(t[0]);
+    st->poll.ynorm = yn;
+    if (yn == 0.0) {
+      st->zero_rhs = 1;
+      st->hist[0] = 0.0;
+      st->poll.relres = 0.0;
+      st->poll.status = ST_OK;
+      st->poll.done = 1;
+      return;
+    }
+    const double rel = sqrt(t[1]) / yn;
+    st->hist[0] = rel;
+    st->poll.relres = rel;
+    if (nonfinite(rel)) { st->poll.status = ST_NONFINITE; st->poll.done = 1; return; }
+    if (rel <= st->tol) { st->poll.status = ST_OK; st->poll.done = 1; return; }
+    if (st->maxit <= 0) { st->poll.status = ST_NOT_CONVERGED; st->poll.done = 1; return; }
+    switch (method) {
+      case M_BICGSTAB:
+        st->rho = mkc(t[1], 0.0);  // <r^, r> with r^ = r
+        st->rho_old = st->alpha = st->omega = mkc(1.0, 0.0);
+        if (tiny<R>(st->rho)) set_breakdown(st, CCG_BD_RHO);
+        break;
+      case M_QMR:
+        st->qrho = st->xi = sqrt(t[1]);  // ||v~_1|| = ||w~_1|| = ||r_0||
+        st->gamma_prev = 1.0;
+        st->theta_prev = 0.0;
+        st->eta = mkc(-1.0, 0.0);
+        st->eps = mkc(0.0, 0.0);
+        if (tiny<R>(st->qrho)) set_breakdown(st, CCG_BD_RHO);
+        break;
+      case M_COCG:
+        st->rho = mkc(t[3], t[4]);
+        if (tiny<R>(st->rho)) set_breakdown(st, CCG_BD_RHO);
+        break;
+      default:
+        break;
+    }
+  }
+};
+
+// ||y - A x||^2 for the final true residual.
+template <class R> struct TrueRes : PhaseBase {
+  static constexpr int NQ = 1;
+  int64_t n;
+  const cx<R>* y;
+  MvOut<R> ax;
+  double* out;
+  __device__ __forceinline__ void element(int64_t i, double* acc) { acc_nrm2(acc, csub(y[i], ax.get(i))); }
+  __device__ void finish(const double* t, SolveState*) { *out = t[0]; }
+};
+
+// Standalone pieces of the C ABI: sum of partials, and a dot product.
+template <class R> struct SumParts : PhaseBase {
+  static constexpr bool kReduce = false;
+  static constexpr int NQ = 1;
+  int64_t n;
+  MvOut<R> mv;
+  cx<R>* y;
+  __device__ __forceinline__ void element(int64_t i, double*) { y[i] = mv.get(i); }
+  __device__ void finish(const double*, SolveState*) {}
+};
+template <class R> struct DotPhase : PhaseBase {
+  static constexpr int NQ = 2;
+  int64_t n;
+  const cx<R>* u;
+  const cx<R>* v;
+  int conj;
+  double* out;
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    if (conj) acc_dotc(acc, u[i], v[i]);
+    else acc_dotu(acc, u[i], v[i]);
+  }
+  __device__ void finish(const double* t, SolveState*) { out[0] = t[0]; out[1] = t[1]; }
+};
+
+// ---------------------------------------------------------------------------
+// BiCGSTAB (van der Vorst; PIM `bicgstab`).
+// ---------------------------------------------------------------------------
+template <class R> struct BiP : PhaseBase {  // p = r, or p = r + beta (p - omega v)
+  static constexpr bool kReduce = false;
+  static constexpr int NQ = 1;
+  int64_t n;
+  const cx<R>* r;
+  cx<R>* p;
+  const cx<R>* v;
+  cx<R> beta, omega;
+  bool first;
+  __device__ __forceinline__ void load(const SolveState* st) {
+    first = st->poll.k == 0;
+    beta = narrow<R>(st->beta);
+    omega = narrow<R>(st->omega);
+  }
+  __device__ __forceinline__ void element(int64_t i, double*) {
+    p[i] = first ? r[i] : cadd(r[i], cmul(beta, csub(p[i], cmul(omega, v[i]))));
+  }
+  __device__ void finish(const double*, SolveState*) {}
+};
+template <class R> struct BiSigma : PhaseBase {  // sigma = <r^, v>, alpha = rho / sigma
+  static constexpr int NQ = 2;
+  int64_t n;
+  MvOut<R> mv;
+  cx<R>* v;
+  const cx<R>* rh;
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    const cx<R> vi = mv.get(i);
+    if (mv.P) v[i] = vi;
+    acc_dotc(acc, rh[i], vi);
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    const double2 sigma = mkc(t[0], t[1]);
+    if (tiny<R>(sigma)) { set_breakdown(st, CCG_BD_SIGMA); return; }
+    st->alpha = cdiv(st->rho, sigma);
+  }
+};
+template <class R> struct BiS : PhaseBase {  // s = r - alpha v; half-step exit when ||s|| meets tol
+  static constexpr int NQ = 1;
+  int64_t n;
+  const cx<R>* r;
+  const cx<R>* v;
+  cx<R>* s;
+  cx<R> alpha;
+  __device__ __forceinline__ void load(const SolveState* st) { alpha = narrow<R>(st->alpha); }
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    const cx<R> si = csub(r[i], cmul(alpha, v[i]));
+    s[i] = si;
+    acc_nrm2(acc, si);
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    st->snorm = sqrt(t[0]) / st->poll.ynorm;
+    st->half = st->snorm <= st->tol ? 1 : 0;
+  }
+};
+template <class R> struct BiOmega : PhaseBase {  // omega = <t, s> / <t, t>
+  static constexpr int NQ = 3;
+  int64_t n;
+  MvOut<R> mv;
+  cx<R>* t;
+  const cx<R>* s;
+  __device__ __forceinline__ bool skip(const SolveState* st) const { return st->half != 0; }
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    const cx<R> ti = mv.get(i);
+    if (mv.P) t[i] = ti;
+    acc_dotc(acc, ti, s[i]);
+    acc_nrm2(acc + 2, ti);
+  }
+  __device__ void finish(const double* q, SolveState* st) {
+    const double tt = q[2];
+    if (tiny<R>(tt)) { set_breakdown(st, CCG_BD_TT); return; }
+    st->omega = mkc(q[0] / tt, q[1] / tt);
+  }
+};
+template <class R> struct BiXR : PhaseBase {  // x += alpha p + omega s; r = s - omega t; next rho = <r^, r>
+  static constexpr int NQ = 3;
+  int64_t n;
+  cx<R>* x;
+  cx<R>* r;
+  const cx<R>* p;
+  const cx<R>* s;
+  const cx<R>* t;
+  const cx<R>* rh;
+  cx<R> alpha, omega;
+  bool half;
+  __device__ __forceinline__ void load(const SolveState* st) {
+    half = st->half != 0;
+    alpha = narrow<R>(st->alpha);
+    omega = narrow<R>(st->omega);
+  }
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    if (half) {
+      x[i] = cadd(x[i], cmul(alpha, p[i]));
+      return;
+    }
+    x[i] = cadd(x[i], cadd(cmul(alpha, p[i]), cmul(omega, s[i])));
+    const cx<R> ri = csub(s[i], cmul(omega, t[i]));
+    r[i] = ri;
+    acc_dotc(acc, rh[i], ri);
+    acc_nrm2(acc + 2, ri);
+  }
+  __device__ void finish(const double* q, SolveState* st) {
+    const int k = st->poll.k + 1;
+    if (st->half) {
+      st->poll.k = k;
+      st->poll.relres = st->snorm;
+      st->hist[k] = st->snorm;
+      st->poll.status = ST_OK;
+      st->poll.done = 1;
+      return;
+    }
+    const double rel = sqrt(q[2]) / st->poll.ynorm;
+    if (end_iteration(st, k, rel, tiny<R>(st->omega) ? CCG_BD_OMEGA : 0)) return;
+    const double2 rho_new = mkc(q[0], q[1]);
+    if (tiny<R>(rho_new)) { set_breakdown(st, CCG_BD_RHO); return; }
+    st->beta = cmul(cdiv(rho_new, st->rho), cdiv(st->alpha, st->omega));
+    st->rho_old = st->rho;
+    st->rho = rho_new;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// CGNR (PIM `cgnr`): CG on A^H A x = A^H y, residual r = y - A x.
+// ---------------------------------------------------------------------------
+template <class R> struct CgZ : PhaseBase {  // z = A^H r (from partials), gamma' = ||z||^2; first: p = z
+  static constexpr int NQ = 1;
+  int64_t n;
+  MvOut<R> mv;
+  cx<R>* z;
+  cx<R>* p;  // non-null on the first call
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    const cx<R> zi = mv.get(i);
+    if (mv.P) z[i] = zi;
+    if (p) p[i] = zi;
+    acc_nrm2(acc, zi);
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    const double g = t[0];
+    if (st->poll.k > 0) st->beta = mkc(g / st->gamma, 0.0);
+    st->gamma = g;
+    if (tiny<R>(g)) set_breakdown(st, CCG_BD_GAMMA);
+  }
+};
+template <class R> struct CgAlpha : PhaseBase {  // w = A p, alpha = gamma / ||w||^2
+  static constexpr int NQ = 1;
+  int64_t n;
+  MvOut<R> mv;
+  cx<R>* w;
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    const cx<R> wi = mv.get(i);
+    if (mv.P) w[i] = wi;
+    acc_nrm2(acc, wi);
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    if (tiny<R>(t[0])) { set_breakdown(st, CCG_BD_WW); return; }
+    st->alpha = mkc(st->gamma / t[0], 0.0);
+  }
+};
+template <class R> struct CgXR : PhaseBase {  // x += alpha p; r -= alpha w
+  static constexpr int NQ = 1;
+  int64_t n;
+  cx<R>* x;
+  cx<R>* r;
+  const cx<R>* p;
+  const cx<R>* w;
+  R alpha;
+  __device__ __forceinline__ void load(const SolveState* st) { alpha = (R)st->alpha.x; }
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    x[i] = cadd(x[i], cscale(alpha, p[i]));
+    const cx<R> ri = csub(r[i], cscale(alpha, w[i]));
+    r[i] = ri;
+    acc_nrm2(acc, ri);
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    end_iteration(st, st->poll.k + 1, sqrt(t[0]) / st->poll.ynorm, 0);
+  }
+};
+template <class R> struct CgP : PhaseBase {  // p = z + beta p
+  static constexpr bool kReduce = false;
+  static constexpr int NQ = 1;
+  int64_t n;
+  const cx<R>* z;
+  cx<R>* p;
+  R beta;
+  __device__ __forceinline__ void load(const SolveState* st) { beta = (R)st->beta.x; }
+  __device__ __forceinline__ void element(int64_t i, double*) { p[i] = cadd(z[i], cscale(beta, p[i])); }
+  __device__ void finish(const double*, SolveState*) {}
+};
+
+// ---------------------------------------------------------------------------
+// QMR without look-ahead, coupled two-term recurrences (Freund-Nachtigal;
+// PIM `qmr`), complex form with A^H.
+// ---------------------------------------------------------------------------
+template <class R> __device__ __forceinline__ void qmr_pq_coefs(SolveState* st) {
+  // cp = xi delta / eps, cq = conj(rho delta / eps), for iterations after the first
+  st->cp = cdiv(cscale(st->xi, st->delta), st->eps);
+  st->cq = cconj(cdiv(cscale(st->qrho, st->delta), st->eps));
+}
+template <class R> struct QVW : PhaseBase {  // first iteration: v = v~/rho, w = w~/xi, delta = <w, v>
+  static constexpr int NQ = 2;
+  int64_t n;
+  const cx<R>* vt;
+  const cx<R>* wt;
+  cx<R>* v;
+  cx<R>* w;
+  R rinv, xinv;
+  __device__ __forceinline__ void load(const SolveState* st) {
+    rinv = (R)(1.0 / st->qrho);
+    xinv = (R)(1.0 / st->xi);
+  }
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    const cx<R> vi = cscale(rinv, vt[i]), wi = cscale(xinv, wt[i]);
+    v[i] = vi;
+    w[i] = wi;
+    acc_dotc(acc, wi, vi);
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    st->delta = mkc(t[0], t[1]);
+    if (tiny<R>(st->delta)) set_breakdown(st, CCG_BD_DELTA);
+  }
+};
+template <class R> struct QPQ : PhaseBase {  // p = v - cp p, q = w - cq q (first: p = v, q = w)
+  static constexpr bool kReduce = false;
+  static constexpr int NQ = 1;
+  int64_t n;
+  const cx<R>* v;
+  const cx<R>* w;
+  cx<R>* p;
+  cx<R>* q;
+  cx<R> cp, cq;
+  bool first;
+  __device__ __forceinline__ void load(const SolveState* st) {
+    first = st->poll.k == 0;
+    cp = narrow<R>(st->cp);
+    cq = narrow<R>(st->cq);
+  }
+  __device__ __forceinline__ void element(int64_t i, double*) {
+    if (first) {
+      p[i] = v[i];
+      q[i] = w[i];
+    } else {
+      p[i] = csub(v[i], cmul(cp, p[i]));
+      q[i] = csub(w[i], cmul(cq, q[i]));
+    }
+  }
+  __device__ void finish(const double*, SolveState*) {}
+};
+template <class R> struct QEps : PhaseBase {  // p~ = A p, u = A^H q; eps = <q, p~>, beta = eps / delta
+  static constexpr int NQ = 2;
+  int64_t n;
+  MvOut<R> mv1, mv2;
+  cx<R>* pt;
+  cx<R>* u;
+  const cx<R>* q;
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    const cx<R> pti = mv1.get(i), ui = mv2.get(i);
+    if (mv1.P) pt[i] = pti;
+    if (mv2.P) u[i] = ui;
+    acc_dotc(acc, q[i], pti);
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    const double2 eps = mkc(t[0], t[1]);
+    if (tiny<R>(eps)) { set_breakdown(st, CCG_BD_EPS); return; }
+    st->eps = eps;
+    st->beta = cdiv(eps, st->delta);
+    if (tiny<R>(st->beta)) set_breakdown(st, CCG_BD_BETA);
+  }
+};
+template <class R> struct QVT : PhaseBase {  // v~ = p~ - beta v, w~ = u - conj(beta) w; theta, gamma, eta
+  static constexpr int NQ = 2;
+  int64_t n;
+  const cx<R>* pt;
+  const cx<R>* u;
+  const cx<R>* v;
+  const cx<R>* w;
+  cx<R>* vt;
+  cx<R>* wt;
+  cx<R> beta, betac;
+  __device__ __forceinline__ void load(const SolveState* st) {
+    beta = narrow<R>(st->beta);
+    betac = cconj(beta);
+  }
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    const cx<R> a = csub(pt[i], cmul(beta, v[i])), b = csub(u[i], cmul(betac, w[i]));
+    vt[i] = a;
+    wt[i] = b;
+    acc_nrm2(acc, a);
+    acc_nrm2(acc + 1, b);
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    st->rho_n = sqrt(t[0]);
+    st->xi_n = sqrt(t[1]);
+    const double theta = st->rho_n / (st->gamma_prev * cabs(st->beta));
+    const double gamma = 1.0 / sqrt(1.0 + theta * theta);
+    if (tiny<R>(gamma)) { set_breakdown(st, CCG_BD_GAMMA); return; }
+    // eta = -eta rho gamma^2 / (beta gamma_prev^2)
+    const double2 num = cscale(st->qrho * gamma * gamma, mkc(-st->eta.x, -st->eta.y));
+    st->eta = cdiv(num, cscale(st->gamma_prev * st->gamma_prev, st->beta));
+    st->c = (st->theta_prev * gamma) * (st->theta_prev * gamma);
+    st->theta = theta;
+    st->gamma = gamma;
+  }
+};
+template <class R> struct QDX : PhaseBase {
+  // d = eta p + c d, s = eta p~ + c s (first: d = eta p, s = eta p~); x += d; r -= s;
+  // and the start of the next iteration: v = v~/rho', w = w~/xi', delta' = <w, v>.
+  static constexpr int NQ = 3;
+  int64_t n;
+  const cx<R>* p;
+  const cx<R>* pt;
+  cx<R>* d;
+  cx<R>* s;
+  cx<R>* x;
+  cx<R>* r;
+  const cx<R>* vt;
+  const cx<R>* wt;
+  cx<R>* v;
+  cx<R>* w;
+  cx<R> eta;
+  R c, rinv, xinv;
+  bool first;
+  __device__ __forceinline__ void load(const SolveState* st) {
+    first = st->poll.k == 0;
+    eta = narrow<R>(st->eta);
+    c = (R)st->c;
+    rinv = (R)(1.0 / st->rho_n);
+    xinv = (R)(1.0 / st->xi_n);
+  }
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    cx<R> di = cmul(eta, p[i]), si = cmul(eta, pt[i]);
+    if (!first) {
+      di = cadd(di, cscale(c, d[i]));
+      si = cadd(si, cscale(c, s[i]));
+    }
+    d[i] = di;
+    s[i] = si;
+    x[i] = cadd(x[i], di);
+    const cx<R> ri = csub(r[i], si);
+    r[i] = ri;
+    acc_nrm2(acc, ri);
+    const cx<R> vi = cscale(rinv, vt[i]), wi = cscale(xinv, wt[i]);
+    v[i] = vi;
+    w[i] = wi;
+    acc_dotc(acc + 1, wi, vi);
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    if (end_iteration(st, st->poll.k + 1, sqrt(t[0]) / st->poll.ynorm, 0)) return;
+    st->qrho = st->rho_n;
+    st->xi = st->xi_n;
+    st->gamma_prev = st->gamma;
+    st->theta_prev = st->theta;
+    if (tiny<R>(st->qrho)) { set_breakdown(st, CCG_BD_RHO); return; }
+    if (tiny<R>(st->xi)) { set_breakdown(st, CCG_BD_XI); return; }
+    st->delta = mkc(t[1], t[2]);
+    if (tiny<R>(st->delta)) { set_breakdown(st, CCG_BD_DELTA); return; }
+    qmr_pq_coefs<R>(st);
+  }
+};
+// ---------------------------------------------------------------------------
+// COCG: complex-symmetric CG with [u, v] = sum u_i v_i (Sec. 2.2 reading).
+// ---------------------------------------------------------------------------
+template <class R> struct CoMu : PhaseBase {  // q = A p, mu = [p, q], alpha = rho / mu
+  static constexpr int NQ = 2;
+  int64_t n;
+  MvOut<R> mv;
+  cx<R>* q;
+  const cx<R>* p;
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    const cx<R> qi = mv.get(i);
+    if (mv.P) q[i] = qi;
+    acc_dotu(acc, p[i], qi);
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    const double2 mu = mkc(t[0], t[1]);
+    if (tiny<R>(mu)) { set_breakdown(st, CCG_BD_MU); return; }
+    st->alpha = cdiv(st->rho, mu);
+  }
+};
+template <class R> struct CoXR : PhaseBase {  // x += alpha p; r -= alpha q; rho' = [r, r], beta = rho'/rho
+  static constexpr int NQ = 3;
+  int64_t n;
+  cx<R>* x;
+  cx<R>* r;
+  const cx<R>* p;
+  const cx<R>* q;
+  cx<R> alpha;
+  __device__ __forceinline__ void load(const SolveState* st) { alpha = narrow<R>(st->alpha); }
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    x[i] = cadd(x[i], cmul(alpha, p[i]));
+    const cx<R> ri = csub(r[i], cmul(alpha, q[i]));
+    r[i] = ri;
+    acc_nrm2(acc, ri);
+    acc_dotu(acc + 1, ri, ri);
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    if (end_iteration(st, st->poll.k + 1, sqrt(t[0]) / st->poll.ynorm, 0)) return;
+    const double2 rho_new = mkc(t[1], t[2]);
+    if (tiny<R>(rho_new)) { set_breakdown(st, CCG_BD_RHO); return; }
+    st->beta = cdiv(rho_new, st->rho);
+    st->rho = rho_new;
+  }
+};
+template <class R> struct CoP : PhaseBase {  // p = r + beta p
+  static constexpr bool kReduce = false;
+  static constexpr int NQ = 1;
+  int64_t n;
+  const cx<R>* r;
+  cx<R>* p;
+  cx<R> beta;
+  __device__ __forceinline__ void load(const SolveState* st) { beta = narrow<R>(st->beta); }
+  __device__ __forceinline__ void element(int64_t i, double*) { p[i] = cadd(r[i], cmul(beta, p[i])); }
+  __device__ void finish(const double*, SolveState*) {}
+};
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+#define CCG_CUDA(call)                                                                 \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+      return CCG_ERR_CUDA;                                                             \
+    }                                                                                  \
+  } while (0)
+
+static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Launch geometry of the dense sweeps for one operator.
+template <class R> struct Dense {
+  const cx<R>* A;
+  int64_t lda, n;
+  int unit;
+  int grid_rows;            // gemv_n_rows blocks
+  int ncb, nsplit;          // gemv_tile grid
+  int64_t rows_per_range;
+  static constexpr int E = 4;
+
+  Dense(const ccg_operator* op, int num_sms) {
+    A = static_cast<const cx<R>*>(op->A);
+    lda = op->lda;
+    n = op->n;
+    unit = op->unit;
+    const int64_t rows_blocks = (n + kWarps - 1) / kWarps;
+    grid_rows = (int)std::min<int64_t>(rows_blocks, (int64_t)num_sms * 16);
+    const int64_t nunits = n / unit;
+    ncb = (int)((nunits + 32 * E - 1) / (32 * E));
+    const int64_t target = (int64_t)num_sms * 4;
+    int64_t ns = (target + ncb - 1) / ncb;
+    ns = std::max<int64_t>(1, std::min<int64_t>(ns, std::min<int64_t>(32, (n + kWarps - 1) / kWarps)));
+    rows_per_range = (n + ns - 1) / ns;
+    nsplit = (int)((n + rows_per_range - 1) / rows_per_range);
+  }
+  size_t p1_elems() const { return (size_t)ncb * n; }
+  size_t p2_elems() const { return (size_t)nsplit * n; }
+  double sweep_bytes() const { return (double)n * (double)n * sizeof(cx<R>); }
+};
+
+template <class R> struct Ws {
+  cx<R>* vec[12];
+  cx<R>* P1;
+  cx<R>* P2;
+  cx<R>* ystage;
+  cx<R>* xstage;
+  double* partials;
+  unsigned int* counter;
+  SolveState* st;
+  double* hist;
+  double* scratch;  // a few doubles for standalone results
+};
+
+template <class R> static size_t ws_bytes(int64_t n, const Dense<R>& d, int maxit) {
+  size_t b = 0;
+  b += 12 * align256(n * sizeof(cx<R>));
+  b += align256(std::max(d.p1_elems(), d.p2_elems()) * sizeof(cx<R>));
+  b += align256(d.p2_elems() * sizeof(cx<R>));
+  b += 2 * align256(n * sizeof(cx<R>));
+  b += align256(kMaxRedBlocks * kMaxNQ * sizeof(double));
+  b += align256(sizeof(unsigned int));
+  b += align256(sizeof(SolveState));
+  b += align256((size_t)(maxit + 1) * sizeof(double));
+  b += align256(16 * sizeof(double));
+  return b;
+}
+
+template <class R> static Ws<R> ws_carve(char* base, int64_t n, const Dense<R>& d, int maxit) {
+  Ws<R> w;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { char* p = base + off; off += align256(bytes); return p; };
+  for (int i = 0; i < 12; ++i) w.vec[i] = reinterpret_cast<cx<R>*>(take(n * sizeof(cx<R>)));
+  w.P1 = reinterpret_cast<cx<R>*>(take(std::max(d.p1_elems(), d.p2_elems()) * sizeof(cx<R>)));
+  w.P2 = reinterpret_cast<cx<R>*>(take(d.p2_elems() * sizeof(cx<R>)));
+  w.ystage = reinterpret_cast<cx<R>*>(take(n * sizeof(cx<R>)));
+  w.xstage = reinterpret_cast<cx<R>*>(take(n * sizeof(cx<R>)));
+  w.partials = reinterpret_cast<double*>(take(kMaxRedBlocks * kMaxNQ * sizeof(double)));
+  w.counter = reinterpret_cast<unsigned int*>(take(sizeof(unsigned int)));
+  w.st = reinterpret_cast<SolveState*>(take(sizeof(SolveState)));
+  w.hist = reinterpret_cast<double*>(take((size_t)(maxit + 1) * sizeof(double)));
+  w.scratch = reinterpret_cast<double*>(take(16 * sizeof(double)));
+  return w;
+}
+
+template <class R> struct Runner {
+  ccg_handle* h;
+  cudaStream_t s;
+  Dense<R> d;
+  Ws<R> w;
+  Red red;
+  int grid_vec;
+
+  Runner(ccg_handle* h_, const ccg_operator* op, const Ws<R>& w_)
+      : h(h_), s(h_->stream), d(op, h_->num_sms), w(w_) {
+    red.partials = w.partials;
+    red.counter = w.counter;
+    grid_vec = (int)std::min<int64_t>((d.n + kBlock - 1) / kBlock, (int64_t)h->num_sms * 8);
+    grid_vec = std::max(1, std::min(grid_vec, kMaxRedBlocks));
+  }
+
+  template <class P> void phase(const P& p) {
+    phase_kernel<P><<<grid_vec, kBlock, 0, s>>>(p, w.st, red);
+    ++h->launches;
+  }
+
+  MvOut<R> plain(const cx<R>* y) const { MvOut<R> m; m.y = y; m.P = nullptr; m.ld = d.n; m.nparts = 1; return m; }
+
+  // y = A x
+  MvOut<R> apply_n(const cx<R>* x, cx<R>* y, const SolveState* st) {
+    timing_begin(h);
+    if constexpr (sizeof(R) == 4) {
+      if (d.unit == 2) gemv_n_rows<R, 2><<<d.grid_rows, kBlock, 0, s>>>(d.A, d.lda, d.n, x, y, st);
+      else gemv_n_rows<R, 1><<<d.grid_rows, kBlock, 0, s>>>(d.A, d.lda, d.n, x, y, st);
+    } else {
+      gemv_n_rows<R, 1><<<d.grid_rows, kBlock, 0, s>>>(d.A, d.lda, d.n, x, y, st);
+    }
+    timing_end(h, CCG_SWEEP_N, d.sweep_bytes());
+    ++h->launches;
+    return plain(y);
+  }
+  // A^H x as nsplit partial vectors in P2
+  MvOut<R> apply_c(const cx<R>* x, const SolveState* st) {
+    dim3 grid(d.ncb, d.nsplit);
+    timing_begin(h);
+    if constexpr (sizeof(R) == 4) {
+      if (d.unit == 2)
+        gemv_tile<R, 2, Dense<R>::E, false, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, nullptr, x, nullptr, w.P2, st);
+      else
+        gemv_tile<R, 1, Dense<R>::E, false, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, nullptr, x, nullptr, w.P2, st);
+    } else {
+      gemv_tile<R, 1, Dense<R>::E, false, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, nullptr, x, nullptr, w.P2, st);
+    }
+    timing_end(h, CCG_SWEEP_C, d.sweep_bytes());
+    ++h->launches;
+    MvOut<R> m; m.y = nullptr; m.P = w.P2; m.ld = d.n; m.nparts = d.nsplit;
+    return m;
+  }
+  // A x1 (ncb partials in P1) and A^H x2 (nsplit partials in P2) from one sweep
+  void apply_both(const cx<R>* x1, const cx<R>* x2, MvOut<R>& o1, MvOut<R>& o2, const SolveState* st) {
+    dim3 grid(d.ncb, d.nsplit);
+    timing_begin(h);
+    if constexpr (sizeof(R) == 4) {
+      if (d.unit == 2)
+        gemv_tile<R, 2, Dense<R>::E, true, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, x1, x2, w.P1, w.P2, st);
+      else
+        gemv_tile<R, 1, Dense<R>::E, true, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, x1, x2, w.P1, w.P2, st);
+    } else {
+      gemv_tile<R, 1, Dense<R>::E, true, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, x1, x2, w.P1, w.P2, st);
+    }
+    timing_end(h, CCG_SWEEP_BOTH, d.sweep_bytes());
+    ++h->launches;
+    o1.y = nullptr; o1.P = w.P1; o1.ld = d.n; o1.nparts = d.ncb;
+    o2.y = nullptr; o2.P = w.P2; o2.ld = d.n; o2.nparts = d.nsplit;
+  }
+};
+
+// Iterations to enqueue between polls: about 50 us of matrix traffic.
+template <class R> static int poll_chunk(const Dense<R>& d) {
+  const double t_iter = 2.0 * d.sweep_bytes() / 5e12;
+  const int c = (int)std::ceil(50e-6 / std::max(t_iter, 1e-9));
+  return std::max(1, std::min(c, 4));
+}
+
+template <class R>
+static int run_dense(ccg_handle* h, int method, const ccg_operator* op, const void* y_in, void* x_in, double tol,
+                     int maxit, double* res_hist, ccg_info* info) {
+  const int64_t n = op->n;
+  Dense<R> dl(op, h->num_sms);
+  int rc = arena_reserve(h, ws_bytes<R>(n, dl, maxit));
+  if (rc != CCG_OK) return rc;
+  Ws<R> w = ws_carve<R>(h->arena, n, dl, maxit);
+  Runner<R> run(h, op, w);
+  cudaStream_t s = h->stream;
+
+  // Host or device vectors?
+  cudaPointerAttributes ay, ax;
+  CCG_CUDA(cudaPointerGetAttributes(&ay, y_in));
+  CCG_CUDA(cudaPointerGetAttributes(&ax, x_in));
+  const bool host_y = ay.type == cudaMemoryTypeUnregistered || ay.type == cudaMemoryTypeHost;
+  const bool host_x = ax.type == cudaMemoryTypeUnregistered || ax.type == cudaMemoryTypeHost;
+  if (host_y != host_x) { set_error("ccg_solve: y and x must both be host or both be device pointers"); return CCG_ERR_INVALID; }
+  const cx<R>* y = static_cast<const cx<R>*>(y_in);
+  cx<R>* x = static_cast<cx<R>*>(x_in);
+  if (host_y) {
+    CCG_CUDA(cudaMemcpyAsync(w.ystage, y_in, n * sizeof(cx<R>), cudaMemcpyHostToDevice, s));
+    CCG_CUDA(cudaMemcpyAsync(w.xstage, x_in, n * sizeof(cx<R>), cudaMemcpyHostToDevice, s));
+    y = w.ystage;
+    x = w.xstage;
+  }
+
+  SolveState init;
+  std::memset(&init, 0, sizeof(init));
+  init.maxit = maxit;
+  init.tol = tol;
+  init.hist = w.hist;
+  CCG_CUDA(cudaMemcpyAsync(w.st, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+  CCG_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(unsigned int), s));
+
+  cx<R>** V = w.vec;
+  SolveState* st = w.st;
+
+  // r0 = y - A x0
+  {
+    InitR<R> p;
+    p.n = n; p.y = y; p.r = V[0]; p.c1 = nullptr; p.c2 = nullptr; p.method = method;
+    cx<R>* tmp = V[11];
+    switch (method) {
+      case M_BICGSTAB: p.c1 = V[1]; break;               // r^
+      case M_QMR: p.c1 = V[1]; p.c2 = V[2]; break;       // v~, w~
+      case M_COCG: p.c1 = V[1]; break;                   // p
+      default: break;
+    }
+    p.ax = run.apply_n(x, tmp, st);
+    run.phase(p);
+  }
+
+  // Per-method vector slots and one iteration's launches.
+  std::function<void()> step;
+  if (method == M_BICGSTAB) {
+    cx<R>*r = V[0], *rh = V[1], *pv = V[2], *v = V[3], *sv = V[4], *t = V[5];
+    step = [=, &run]() {
+      BiP<R> a; a.n = n; a.r = r; a.p = pv; a.v = v; run.phase(a);
+      BiSigma<R> b; b.n = n; b.v = v; b.rh = rh; b.mv = run.apply_n(pv, v, st); run.phase(b);
+      BiS<R> c; c.n = n; c.r = r; c.v = v; c.s = sv; run.phase(c);
+      BiOmega<R> e; e.n = n; e.t = t; e.s = sv; e.mv = run.apply_n(sv, t, st); run.phase(e);
+      BiXR<R> f; f.n = n; f.x = x; f.r = r; f.p = pv; f.s = sv; f.t = t; f.rh = rh; run.phase(f);
+    };
+  } else if (method == M_CGNR) {
+    cx<R>*r = V[0], *z = V[1], *pv = V[2], *wv = V[3];
+    CgZ<R> z0; z0.n = n; z0.z = z; z0.p = pv; z0.mv = run.apply_c(r, st); run.phase(z0);
+    step = [=, &run]() {
+      CgAlpha<R> a; a.n = n; a.w = wv; a.mv = run.apply_n(pv, wv, st); run.phase(a);
+      CgXR<R> b; b.n = n; b.x = x; b.r = r; b.p = pv; b.w = wv; run.phase(b);
+      CgZ<R> c; c.n = n; c.z = z; c.p = nullptr; c.mv = run.apply_c(r, st); run.phase(c);
+      CgP<R> e; e.n = n; e.z = z; e.p = pv; run.phase(e);
+    };
+  } else if (method == M_QMR) {
+    cx<R>*r = V[0], *vt = V[1], *wt = V[2], *v = V[3], *wv = V[4], *pv = V[5], *q = V[6], *pt = V[7], *u = V[8],
+         *dv = V[9], *sv = V[10];
+    QVW<R> f; f.n = n; f.vt = vt; f.wt = wt; f.v = v; f.w = wv; run.phase(f);
+    step = [=, &run]() {
+      QPQ<R> a; a.n = n; a.v = v; a.w = wv; a.p = pv; a.q = q; run.phase(a);
+      QEps<R> b; b.n = n; b.pt = pt; b.u = u; b.q = q; run.apply_both(pv, q, b.mv1, b.mv2, st); run.phase(b);
+      QVT<R> c; c.n = n; c.pt = pt; c.u = u; c.v = v; c.w = wv; c.vt = vt; c.wt = wt; run.phase(c);
+      QDX<R> e; e.n = n; e.p = pv; e.pt = pt; e.d = dv; e.s = sv; e.x = x; e.r = r; e.vt = vt; e.wt = wt; e.v = v;
+      e.w = wv; run.phase(e);
+    };
+  } else {  // COCG
+    cx<R>*r = V[0], *pv = V[1], *q = V[2];
+    step = [=, &run]() {
+      CoMu<R> a; a.n = n; a.q = q; a.p = pv; a.mv = run.apply_n(pv, q, st); run.phase(a);
+      CoXR<R> b; b.n = n; b.x = x; b.r = r; b.p = pv; b.q = q; run.phase(b);
+      CoP<R> c; c.n = n; c.r = r; c.p = pv; run.phase(c);
+    };
+  }
+  CCG_CUDA(cudaGetLastError());
+
+  // Enqueue iterations in chunks; poll the device record of the chunk before.
+  Poll* pin = static_cast<Poll*>(h->pinned);
+  const int chunk = poll_chunk(dl);
+  int launched = 0, npoll = 0;
+  for (;;) {
+    if (launched < maxit) {
+      const int c = std::min(chunk, maxit - launched);
+      for (int j = 0; j < c; ++j) step();
+      launched += c;
+      CCG_CUDA(cudaGetLastError());
+    }
+    const int slot = npoll & 1;
+    CCG_CUDA(cudaMemcpyAsync(&pin[slot], &st->poll, sizeof(Poll), cudaMemcpyDeviceToHost, s));
+    CCG_CUDA(cudaEventRecord(h->poll_ev[slot], s));
+    if (npoll > 0) {
+      CCG_CUDA(cudaEventSynchronize(h->poll_ev[slot ^ 1]));
+      if (pin[slot ^ 1].done) break;
+    }
+    ++npoll;
+    if (launched >= maxit) break;
+  }
+  CCG_CUDA(cudaStreamSynchronize(s));
+  SolveState fin;
+  CCG_CUDA(cudaMemcpy(&fin, st, sizeof(fin), cudaMemcpyDeviceToHost));
+  const int iters = fin.poll.k;
+  if (!fin.poll.done) {  // cannot happen: maxit bounds the loop and the last iteration stops the solve
+    set_error("ccg_solve: solve did not record its end");
+    return CCG_ERR_CUDA;
+  }
+  if (fin.zero_rhs) CCG_CUDA(cudaMemsetAsync(x, 0, n * sizeof(cx<R>), s));
+  if (res_hist) CCG_CUDA(cudaMemcpyAsync(res_hist, w.hist, (size_t)(iters + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+  double true_rr = -1.0;
+  if (info) {
+    // ||y - A x|| from the final x, outside the iteration (state forced live)
+    SolveState live = fin;
+    live.poll.done = 0;
+    live.half = 0;
+    CCG_CUDA(cudaMemcpyAsync(st, &live, sizeof(live), cudaMemcpyHostToDevice, s));
+    TrueRes<R> tr;
+    tr.n = n; tr.y = y; tr.out = w.scratch;
+    tr.ax = run.apply_n(x, w.vec[11], st);
+    run.phase(tr);
+    CCG_CUDA(cudaGetLastError());
+    CCG_CUDA(cudaMemcpyAsync(&true_rr, w.scratch, sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
+  if (host_x) CCG_CUDA(cudaMemcpyAsync(x_in, x, n * sizeof(cx<R>), cudaMemcpyDeviceToHost, s));
+  CCG_CUDA(cudaStreamSynchronize(s));
+  timing_collect(h);
+  if (info) {
+    info->iters = iters;
+    info->status = fin.poll.status;
+    info->breakdown = fin.poll.breakdown;
+    info->reserved = 0;
+    info->relres = fin.poll.relres;
+    info->ynorm = fin.poll.ynorm;
+    info->true_relres = fin.poll.ynorm > 0 ? std::sqrt(true_rr) / fin.poll.ynorm : 0.0;
+  }
+  return fin.poll.status;
+}
+
+int solve_dense(ccg_handle* h, int method, const ccg_operator* op, const void* y, void* x, double tol, int maxit,
+                double* res_hist, ccg_info* info) {
+  if (op->dtype == CCG_C128) return run_dense<double>(h, method, op, y, x, tol, maxit, res_hist, info);
+  return run_dense<float>(h, method, op, y, x, tol, maxit, res_hist, info);
+}
+
+template <class R> static int matvec_t(ccg_handle* h, const ccg_operator* op, int trans, const void* x_, void* y_) {
+  Dense<R> dl(op, h->num_sms);
+  int rc = arena_reserve(h, ws_bytes<R>(op->n, dl, 0));
+  if (rc != CCG_OK) return rc;
+  Ws<R> w = ws_carve<R>(h->arena, op->n, dl, 0);
+  Runner<R> run(h, op, w);
+  const cx<R>* x = static_cast<const cx<R>*>(x_);
+  cx<R>* y = static_cast<cx<R>*>(y_);
+  SolveState init;
+  std::memset(&init, 0, sizeof(init));
+  init.hist = w.hist;
+  CCG_CUDA(cudaMemcpyAsync(w.st, &init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
+  if (!trans) {
+    run.apply_n(x, y, nullptr);
+  } else {
+    SumParts<R> p;
+    p.n = op->n;
+    p.y = y;
+    p.mv = run.apply_c(x, nullptr);
+    run.phase(p);
+  }
+  CCG_CUDA(cudaGetLastError());
+  return CCG_OK;
+}
+
+int matvec_dense(ccg_handle* h, const ccg_operator* op, int trans, const void* x, void* y) {
+  if (op->dtype == CCG_C128) return matvec_t<double>(h, op, trans, x, y);
+  return matvec_t<float>(h, op, trans, x, y);
+}
+
+template <class R> static int dot_t(ccg_handle* h, int64_t n, const void* u, const void* v, int conj, double* out2) {
+  ccg_operator fake;
+  fake.n = 1;
+  fake.lda = 1;
+  Dense<R> dl(&fake, h->num_sms);
+  int rc = arena_reserve(h, ws_bytes<R>(1, dl, 0));
+  if (rc != CCG_OK) return rc;
+  Ws<R> w = ws_carve<R>(h->arena, 1, dl, 0);
+  SolveState init;
+  std::memset(&init, 0, sizeof(init));
+  init.hist = w.hist;
+  CCG_CUDA(cudaMemcpyAsync(w.st, &init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
+  CCG_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(unsigned int), h->stream));
+  DotPhase<R> p;
+  p.n = n;
+  p.u = static_cast<const cx<R>*>(u);
+  p.v = static_cast<const cx<R>*>(v);
+  p.conj = conj;
+  p.out = w.scratch;
+  Red red;
+  red.partials = w.partials;
+  red.counter = w.counter;
+  int grid = (int)std::min<int64_t>((n + kBlock - 1) / kBlock, (int64_t)h->num_sms * 8);
+  grid = std::max(1, std::min(grid, kMaxRedBlocks));
+  phase_kernel<DotPhase<R>><<<grid, kBlock, 0, h->stream>>>(p, w.st, red);
+  ++h->launches;
+  CCG_CUDA(cudaGetLastError());
+  CCG_CUDA(cudaMemcpyAsync(out2, w.scratch, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CCG_CUDA(cudaStreamSynchronize(h->stream));
+  return CCG_OK;
+}
+
+int dot_device(ccg_handle* h, ccg_dtype dtype, int64_t n, const void* u, const void* v, int conj, double* out2) {
+  if (dtype == CCG_C128) return dot_t<double>(h, n, u, v, conj, out2);
+  return dot_t<float>(h, n, u, v, conj, out2);
+}
+
+}  // namespace ccg

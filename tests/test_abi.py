@@ -1,0 +1,59 @@
+"""The C ABI library loads and exports every symbol include/ccg.h declares,
+and refuses to compute without a GPU (no CPU fallback).  No GPU needed."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1208_4869_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(ccg_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    return B.build()
+
+
+def test_header_declares_entry_points():
+    names = declared_symbols()
+    for must in ("ccg_create", "ccg_destroy", "ccg_op_dense", "ccg_matvec", "ccg_dot", "ccg_solve"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    L = ctypes.CDLL(libpath)
+    missing = [n for n in declared_symbols() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_no_cpu_fallback_without_gpu(libpath):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    L = ctypes.CDLL(libpath)
+    L.ccg_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]
+    L.ccg_last_error.restype = ctypes.c_char_p
+    h = ctypes.c_void_p()
+    st = L.ccg_create(ctypes.byref(h), None)
+    assert st == -3 and not h.value
+    assert b"device" in L.ccg_last_error()
+
+
+def test_binding_raises_when_library_missing(monkeypatch, tmp_path):
+    from paper_1208_4869_gb300 import ccg
+    monkeypatch.setattr(ccg, "LIB_PATH", str(tmp_path / "nope.so"))
+    monkeypatch.setattr(ccg, "_lib", None)
+    with pytest.raises(ImportError):
+        ccg.lib()
