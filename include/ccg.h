@@ -166,6 +166,38 @@ ccg_status ccg_timing_reset(ccg_handle* h);
 /* Number of kernels this handle has launched since it was created. */
 int64_t ccg_launch_count(const ccg_handle* h);
 
+/* Allocation-free y = A^H x for a dense matrix.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory -- for instance a host program whose device memory is all
+ * owned by its own pool allocator, or a loop that cannot afford the
+ * device-wide synchronisation that cudaMalloc / cudaFree imply.  Every other
+ * call of this library needs a handle, whose workspace is allocated with
+ * cudaMalloc; this one needs none and calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *
+ * Arguments are those of ccg_op_dense + ccg_matvec(trans = 1): A is n x n,
+ * row-major with leading dimension lda, precision `dtype`, on the current
+ * CUDA device; x (input) and y (output) are device vectors of n elements;
+ * the work is enqueued on `stream` (a cudaStream_t, NULL = legacy default
+ * stream) and the call returns without synchronising.
+ *
+ * Scratch: the partial sums live in one fixed device array of
+ * CCG_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads
+ * the library holds until the process exits.  n above CCG_NOALLOC_MAX_N is
+ * rejected with CCG_ERR_INVALID before anything is launched.  All calls on a
+ * device share that array, so two calls whose work overlaps on the GPU (on
+ * different streams, or from different threads) race and give wrong results:
+ * order them on one stream or synchronise between them.  Each call writes
+ * every scratch entry it reads, so nothing carries over from the last call.
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * Returns CCG_OK, CCG_ERR_INVALID (NULL or misaligned pointer, bad dtype,
+ * n < 1, lda < n, n too large) or CCG_ERR_CUDA (no device, launch error). */
+#define CCG_NOALLOC_MAX_N 65536
+#define CCG_NOALLOC_SCRATCH_BYTES (16u << 20)
+ccg_status ccg_matvec_h_noalloc(ccg_dtype dtype, int64_t n, const void* A, int64_t lda, const void* x, void* y,
+                                void* stream);
+
 #ifdef __cplusplus
 }
 #endif
