@@ -41,7 +41,7 @@ METRIC = "solves/s at rel-res 1e-10, mixed vs FP64 GPU; % HBM roofline; p50/p99 
 def parse_args(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ccg", "reference"], default="ccg")
     p.add_argument("--n", type=int, default=8192)
@@ -49,6 +49,9 @@ def parse_args(argv=None):
     p.add_argument("--path", choices=["fp64", "mixed", "auto"], default="auto")
     p.add_argument("--tol", type=float, default=1e-10)
     p.add_argument("--maxit", type=int, default=1000)
+    p.add_argument("--max-outer", type=int, default=30)
+    p.add_argument("--inner-tol", type=float, default=1e-5)
+    p.add_argument("--inner-maxit", type=int, default=200)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args(argv)
@@ -178,37 +181,36 @@ SWEEP_KERNELS = {0: ("gemv_n_rows", 1), 1: ("gemv_tile_c", 1), 2: ("gemv_tile_bo
 KERNEL_SOURCES = ["paper_1208_4869_gb300/csrc/gemv.cuh", "paper_1208_4869_gb300/csrc/common.cuh"]
 
 
-def roofline(ccg, sweep_stats, n, dtype):
-    """Roofline of the sweep kind that took the most device time in the timed
-    region: algorithmic flops (8 n^2 per complex product; the fused QMR sweep
-    forms two) and bytes (the matrix, read once per sweep) over the mean
-    CUDA-event duration of its launches."""
+def roofline(ccg, sweep_stats, n):
+    """Roofline of the sweep (precision, kind) that took the most device time
+    in the timed region: algorithmic flops (8 n^2 per complex product; the
+    fused QMR sweep forms two) and bytes (the matrix, read once per sweep)
+    over the mean CUDA-event duration of its launches."""
     kinds = {}
-    for kind, (cnt, ms, nbytes) in sweep_stats.items():
+    for (dt, kind), (cnt, ms, nbytes) in sweep_stats.items():
         if cnt:
             name, products = SWEEP_KERNELS[kind]
+            tag = "%s_%s" % (name, "c128" if dt == ccg.C128 else "c64")
             avg = ms / cnt
-            kinds[name] = {"launches": cnt, "total_ms": ms, "avg_ms": avg,
-                           "tflops": 8.0 * products * n * n / (avg * 1e-3) / 1e12,
-                           "gbs": nbytes / (avg * 1e-3) / 1e9, "bytes": nbytes}
+            kinds[tag] = {"launches": cnt, "total_ms": ms, "avg_ms": avg,
+                          "tflops": 8.0 * products * n * n / (avg * 1e-3) / 1e12,
+                          "gbs": nbytes / (avg * 1e-3) / 1e9, "bytes": nbytes}
     if not kinds:
         return None
     top = max(kinds, key=lambda k: kinds[k]["total_ms"])
     k = kinds[top]
     hbm, hbm_src = peaks()
-    traffic = profiled_traffic("%s_%s" % (top, dtype), KERNEL_SOURCES)
-    if dtype == "c128":   # FP64 FMA pipe bound (4 DFMA per 16-byte element)
-        roof = {"kernel": "%s<%s>" % (top, dtype), "bound": "alu", "achieved": k["tflops"], "peak": FP64_PEAK_TFLOPS,
+    traffic = profiled_traffic(top, KERNEL_SOURCES)
+    if top.endswith("c128"):   # FP64 FMA pipe bound (4 DFMA per 16-byte element)
+        roof = {"kernel": top, "bound": "alu", "achieved": k["tflops"], "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": k["tflops"] / FP64_PEAK_TFLOPS,
                 "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (no measured FP64 peak)"}
-    else:                 # HBM bound
-        roof = {"kernel": "%s<%s>" % (top, dtype), "bound": "hbm", "achieved": k["gbs"], "peak": hbm,
+    else:                      # HBM bound
+        roof = {"kernel": top, "bound": "hbm", "achieved": k["gbs"], "peak": hbm,
                 "unit": "GB/s", "frac": k["gbs"] / hbm, "peak_source": "%s copy bandwidth" % hbm_src}
     roof["traffic"] = traffic[0] if traffic else None
     roof["algorithmic_bytes"] = k["bytes"]
     roof["avg_launch_ms"] = k["avg_ms"]
-    roof["hbm_equiv_gbs"] = k["gbs"]
-    roof["hbm_peak_gbs"] = hbm
     roof["sweeps"] = kinds
     return roof
 
@@ -270,6 +272,31 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------- our arm
+def timed_region(h, ccg, torch, stream, step, steps, world, dev, clocks=None):
+    """Run `steps` steps between CUDA events on the solve stream, with the
+    library's per-sweep timing on; returns elapsed ms, per-solve host latencies,
+    per-solve results, sweep statistics and the kernels launched."""
+    h.timing(enable=True, reset=True)
+    launches0 = h.launch_count()
+    barrier(world)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lat, results = [], []
+    e0.record(stream)
+    for _ in range(steps):
+        step(lat, results)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    barrier(world)
+    stats = {(dt, k): h.timing(kind=k, dtype=dt) for dt in (ccg.C128, ccg.C64)
+             for k in (ccg.SWEEP_N, ccg.SWEEP_C, ccg.SWEEP_BOTH)}
+    h.timing(enable=False)
+    return e0.elapsed_time(e1), lat, results, stats, h.launch_count() - launches0, clk
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -288,52 +315,59 @@ def run_ours(args):
     methods = args.methods.split(",")
     n = args.n
     A, y = W.dense_system(n, 3.0, 0)
-    path = "fp64" if args.path in ("auto", "fp64") else args.path
-    if path != "fp64":
-        raise SystemExit("path %s not available" % path)
+    headline = "mixed" if args.path == "auto" else args.path
     Ad = torch.from_numpy(A).to(dev)
+    A32 = Ad.to(torch.complex64)
     yd = torch.from_numpy(y).to(dev)
     xd = torch.zeros_like(yd)
     stream = torch.cuda.current_stream(dev)
     h = ccg.Handle(stream)
-    op = h.op_dense(Ad)
+    op64 = h.op_dense(Ad)
+    op32 = h.op_dense(A32)
 
-    def one_step(lat=None, statuses=None):
-        for m in methods:
-            xd.zero_()
-            t = time.perf_counter()
-            st, info, _ = h.solve(m, op, yd, xd, tol=args.tol, maxit=args.maxit, want_hist=False)
-            if lat is not None:
-                lat.append(time.perf_counter() - t)
-            if statuses is not None:
-                statuses.append((m, st, info["iters"], info["true_relres"]))
+    def solve(path, m, yv, xv):
+        if path == "mixed":
+            st, info, _, inner = h.solve_refined(m, op64, op32, yv, xv, tol=args.tol, max_outer=args.max_outer,
+                                                 inner_tol=args.inner_tol, inner_maxit=args.inner_maxit,
+                                                 want_hist=False)
+            return st, info, inner
+        st, info, _ = h.solve(m, op64, yv, xv, tol=args.tol, maxit=args.maxit, want_hist=False)
+        return st, info, info["iters"]
 
-    for _ in range(args.warmup):
-        one_step()
-    torch.cuda.synchronize()
+    def make_step(path):
+        def step(lat=None, results=None):
+            for m in methods:
+                xd.zero_()
+                t = time.perf_counter()
+                st, info, inner = solve(path, m, yd, xd)
+                if lat is not None:
+                    lat.append(time.perf_counter() - t)
+                if results is not None:
+                    results.append((m, st, info["iters"], inner, info["true_relres"]))
+        return step
 
-    h.timing(enable=True, reset=True)
-    launches0 = h.launch_count()
-    clocks = ClockSampler(local)
-    barrier(world)
-    torch.cuda.synchronize()
-    clocks.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    lat, statuses = [], []
-    e0.record(stream)
-    for _ in range(args.steps):
-        one_step(lat, statuses)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    barrier(world)
-    elapsed_ms = e0.elapsed_time(e1)
-    launches = h.launch_count() - launches0
-    sweep_stats = {k: h.timing(kind=k) for k in (ccg.SWEEP_N, ccg.SWEEP_C, ccg.SWEEP_BOTH)}
-    h.timing(enable=False)
-    t_max_ms = reduce_max(elapsed_ms, world, dev)
+    runs = {}
+    for path in [headline] + [p for p in ("mixed", "fp64") if p != headline]:
+        step = make_step(path)
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local) if path == headline else None
+        runs[path] = timed_region(h, ccg, torch, stream, step, args.steps, world, dev, clocks)
+
+    ms, lat, results, stats, launches, clk = runs[headline]
+    t_max_ms = reduce_max(ms, world, dev)
     solves = reduce_sum(args.steps * len(methods), world, dev)
     value = solves / (t_max_ms / 1e3)
+    other = {}
+    for path, (oms, olat, ores, _, _, _) in runs.items():
+        if path == headline:
+            continue
+        om = reduce_max(oms, world, dev)
+        other[path] = {"value": solves / (om / 1e3), "unit": "solves/s", "ms_per_step": om / args.steps,
+                       "latency_ms": {"p50": 1e3 * statistics.median(olat)},
+                       "iters": {m: it for m, _, it, _, _ in ores[: len(methods)]},
+                       "all_converged": all(st == 0 and tr <= 10 * args.tol for _, st, _, _, tr in ores)}
 
     # end to end through the same call with pinned host buffers (y in, x0 in, x out)
     e2e = None
@@ -341,41 +375,44 @@ def run_ours(args):
         yh = torch.from_numpy(y).pin_memory()
         xh = torch.zeros_like(yh).pin_memory()
         for _ in range(max(1, args.warmup // 2)):
-            h.solve(methods[0], op, yh, xh, tol=args.tol, maxit=args.maxit, want_hist=False)
+            solve(headline, methods[0], yh, xh)
         barrier(world)
         t0 = time.perf_counter()
         for _ in range(args.steps):
             for m in methods:
                 xh.zero_()
-                h.solve(m, op, yh, xh, tol=args.tol, maxit=args.maxit, want_hist=False)
+                solve(headline, m, yh, xh)
         dt = reduce_max(time.perf_counter() - t0, world, dev)
         e2e = {"value": solves / dt, "unit": "solves/s", "h2d_bytes_per_step": 2 * len(methods) * y.nbytes,
                "d2h_bytes_per_step": len(methods) * y.nbytes}
 
-    roof = roofline(ccg, sweep_stats, n, "c128")
+    roof = roofline(ccg, stats, n)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, nsolve, dt, its = oracle_sample(A, y, methods[:1], budget_s=15.0, tol=args.tol, maxit=args.maxit)
         cpu = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
-               "sample": "%d whole %s solve(s) of the same system in %.1f s, serial C++" % (nsolve, methods[0], dt)}
+               "sample": "%d whole %s solve(s) of the same system (complex128, to %g) in %.1f s, serial C++"
+                         % (nsolve, methods[0], args.tol, dt)}
 
-    ok = all(st == 0 and tr <= 10 * args.tol for _, st, _, tr in statuses)
+    ok = all(st == 0 and tr <= 10 * args.tol for _, st, _, _, tr in results)
     if rank == 0:
         lat_sorted = sorted(lat)
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64+c128" if headline == "mixed" else "c128",
+            "data": "synthetic",
             "config": {"workload": "dense single-RHS n=%d shift 3, bicgstab/cgnr/qmr to 1e-10" % n, "n": n,
-                       "methods": methods, "tol": args.tol, "path": path,
+                       "methods": methods, "tol": args.tol, "path": headline,
+                       "inner_tol": args.inner_tol if headline == "mixed" else None,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (A %.2f GB)" % (A.nbytes / 1e9)},
-            "path": path,
-            "iters": {m: it for m, _, it, _ in statuses[: len(methods)]},
+            "iters": {m: [it, inner] for m, _, it, inner, _ in results[: len(methods)]},
             "all_converged": ok,
             "latency_ms": {"p50": 1e3 * statistics.median(lat_sorted),
                            "p99": 1e3 * lat_sorted[int(0.99 * (len(lat_sorted) - 1))]},
+            "other_paths": other,
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -144,6 +144,31 @@ ccg_status ccg_dot(ccg_handle* h, ccg_dtype dtype, int64_t n, const void* u, con
 ccg_status ccg_solve(ccg_handle* h, ccg_method method, const ccg_operator* op, const void* y, void* x, double tol,
                      int maxit, double* res_hist, ccg_info* info);
 
+/* Mixed-precision solve of A x = y: iterative refinement with the residual
+ * r = y - A x and the update x += d in complex128, and each correction
+ * A d = r solved by `inner_method` in complex64 (the manual's single and
+ * double precision, abstract and Sec. 5, used together).
+ *  op        complex128 operator of A (residuals, updates)
+ *  op_inner  complex64 operator of the same matrix rounded to single
+ *            precision (the inner Krylov sweeps); same size as op
+ *  y, x      complex128 right-hand side and start/solution, both device or
+ *            both host pointers (as in ccg_solve)
+ *  tol       stop when ||y - A x|| / ||y|| <= tol, the residual recomputed
+ *            in complex128 from x at every outer step
+ *  max_outer cap on corrections (>= 0)
+ *  inner_tol, inner_maxit  relative tolerance (> 0) and cap (>= 1) of each
+ *            inner solve
+ *  res_hist  optional host array of max_outer + 1 doubles: the outer
+ *            residuals ||y - A x_j|| / ||y||, j = 0 .. info->iters
+ *  inner_iters optional: total inner iterations
+ *  info      optional; iters = corrections applied, relres = true_relres =
+ *            the last outer residual.
+ * Returns CCG_OK, CCG_NOT_CONVERGED (max_outer reached), CCG_BREAKDOWN (an
+ * inner solve broke down before its first iteration) or an error. */
+ccg_status ccg_solve_refined(ccg_handle* h, ccg_method inner_method, const ccg_operator* op,
+                             const ccg_operator* op_inner, const void* y, void* x, double tol, int max_outer,
+                             double inner_tol, int inner_maxit, double* res_hist, int* inner_iters, ccg_info* info);
+
 /* Kinds of operator sweep, for timing. */
 typedef enum {
   CCG_SWEEP_N = 0,    /* y = A x                          */
@@ -154,13 +179,13 @@ typedef enum {
 
 /* Per-kernel timing of the operator sweeps: when enabled, each sweep that a
  * call of this handle launches is bracketed by CUDA events on the handle's
- * stream.  ccg_timing_read returns, for one sweep kind, the number of sweeps
- * timed since the last reset, their total device milliseconds, and the
- * algorithmic bytes of one sweep (the matrix bytes read).  Durations are
- * collected when a solve ends (and by ccg_timing_read, which synchronises
- * the stream). */
+ * stream.  ccg_timing_read returns, for one precision (ccg_dtype) and one
+ * sweep kind, the number of sweeps timed since the last reset, their total
+ * device milliseconds, and the algorithmic bytes of one sweep (the matrix
+ * bytes read).  It synchronises the handle's stream. */
 ccg_status ccg_timing_enable(ccg_handle* h, int enable);
-ccg_status ccg_timing_read(ccg_handle* h, int kind, int64_t* sweeps, double* total_ms, double* bytes_per_sweep);
+ccg_status ccg_timing_read(ccg_handle* h, int dtype, int kind, int64_t* sweeps, double* total_ms,
+                           double* bytes_per_sweep);
 ccg_status ccg_timing_reset(ccg_handle* h);
 
 /* Number of kernels this handle has launched since it was created. */

@@ -67,12 +67,14 @@ def lib():
     L.ccg_dot.argtypes = [vp, i32, i64, vp, vp, i32, vp]
     L.ccg_solve.argtypes = [vp, i32, vp, vp, vp, dbl, i32, vp, ctypes.POINTER(Info)]
     L.ccg_timing_enable.argtypes = [vp, i32]
-    L.ccg_timing_read.argtypes = [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+    L.ccg_timing_read.argtypes = [vp, i32, i32, ctypes.POINTER(i64), ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+    L.ccg_solve_refined.argtypes = [vp, i32, vp, vp, vp, vp, dbl, i32, dbl, i32, vp, ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(Info)]
     L.ccg_timing_reset.argtypes = [vp]
     L.ccg_launch_count.restype = i64
     L.ccg_launch_count.argtypes = [vp]
     for name in ("ccg_create", "ccg_destroy", "ccg_set_stream", "ccg_op_dense", "ccg_op_destroy", "ccg_matvec",
-                 "ccg_dot", "ccg_solve", "ccg_timing_enable", "ccg_timing_read", "ccg_timing_reset"):
+                 "ccg_dot", "ccg_solve", "ccg_solve_refined", "ccg_timing_enable", "ccg_timing_read", "ccg_timing_reset"):
         getattr(L, name).restype = i32
     if L.ccg_abi_version() != 1:
         raise ImportError("libccg ABI version mismatch")
@@ -164,8 +166,25 @@ class Handle:
             hist = hist[: info.iters + 1]
         return st, d, hist
 
-    def timing(self, enable=None, reset=False, kind=SWEEP_N):
-        """Per-sweep CUDA-event timing of one sweep kind: (sweeps, total_ms, bytes_per_sweep)."""
+    def solve_refined(self, method, op, op_inner, y, x, tol=1e-10, max_outer=30, inner_tol=1e-5, inner_maxit=200,
+                      want_hist=True):
+        """ccg_solve_refined: complex128 residual/update around complex64 inner solves.
+        Returns (status, info dict, outer residual history, total inner iterations)."""
+        m = METHODS[method] if isinstance(method, str) else int(method)
+        hist = np.full(max_outer + 1, np.nan) if want_hist else None
+        info = Info()
+        inner = ctypes.c_int(0)
+        st = lib().ccg_solve_refined(self.h, m, op.op, op_inner.op, _ptr(y), _ptr(x), float(tol), int(max_outer),
+                                     float(inner_tol), int(inner_maxit),
+                                     ctypes.c_void_p(hist.ctypes.data) if want_hist else ctypes.c_void_p(0),
+                                     ctypes.byref(inner), ctypes.byref(info))
+        _check(st)
+        if want_hist:
+            hist = hist[: info.iters + 1]
+        return st, info.as_dict(), hist, inner.value
+
+    def timing(self, enable=None, reset=False, kind=SWEEP_N, dtype=C128):
+        """Per-sweep CUDA-event timing of one precision and sweep kind: (sweeps, total_ms, bytes_per_sweep)."""
         if enable is not None:
             _check(lib().ccg_timing_enable(self.h, int(bool(enable))))
         if reset:
@@ -173,7 +192,8 @@ class Handle:
         n = ctypes.c_int64()
         ms = ctypes.c_double()
         b = ctypes.c_double()
-        _check(lib().ccg_timing_read(self.h, int(kind), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(b)))
+        _check(lib().ccg_timing_read(self.h, int(dtype), int(kind), ctypes.byref(n), ctypes.byref(ms),
+                                     ctypes.byref(b)))
         return n.value, ms.value, b.value
 
     def launch_count(self):

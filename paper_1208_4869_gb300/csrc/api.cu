@@ -57,12 +57,13 @@ void timing_begin(ccg_handle* h) {
   cudaEventRecord(h->tev[h->tev_used], h->stream);
 }
 
-void timing_end(ccg_handle* h, int kind, double bytes) {
+void timing_end(ccg_handle* h, int dtype, int kind, double bytes) {
   if (!h->timing) return;
+  const int slot = dtype * CCG_SWEEP_KINDS + kind;
   cudaEventRecord(h->tev[h->tev_used + 1], h->stream);
-  h->tev_kind[h->tev_used] = kind;
+  h->tev_kind[h->tev_used] = slot;
   h->tev_used += 2;
-  h->bytes_per_sweep[kind] = bytes;
+  h->bytes_per_sweep[slot] = bytes;
 }
 
 // Sum the recorded sweep durations (the stream must be idle) and recycle the events.
@@ -214,19 +215,46 @@ ccg_status ccg_solve(ccg_handle* h, ccg_method method, const ccg_operator* op, c
   return static_cast<ccg_status>(solve_dense(h, method, op, y, x, tol, maxit, res_hist, info));
 }
 
+ccg_status ccg_solve_refined(ccg_handle* h, ccg_method method, const ccg_operator* op, const ccg_operator* op_in,
+                             const void* y, void* x, double tol, int max_outer, double inner_tol, int inner_maxit,
+                             double* res_hist, int* inner_iters, ccg_info* info) {
+  if (!h || !op || !op_in || !y || !x) { set_error("ccg_solve_refined: NULL argument"); return CCG_ERR_INVALID; }
+  if (method < CCG_BICGSTAB || method > CCG_COCG) { set_error("ccg_solve_refined: unknown method"); return CCG_ERR_INVALID; }
+  if (op->dtype != CCG_C128 || op_in->dtype != CCG_C64 || op->n != op_in->n) {
+    set_error("ccg_solve_refined: need a complex128 operator and a complex64 operator of the same size");
+    return CCG_ERR_INVALID;
+  }
+  if (!(tol >= 0.0) || max_outer < 0 || !(inner_tol > 0.0) || inner_maxit < 1) {
+    set_error("ccg_solve_refined: need tol >= 0, max_outer >= 0, inner_tol > 0, inner_maxit >= 1");
+    return CCG_ERR_INVALID;
+  }
+  if (method == CCG_COCG && !(op_in->flags & CCG_OP_SYMMETRIC)) {
+    set_error("ccg_solve_refined: COCG needs an inner operator flagged CCG_OP_SYMMETRIC");
+    return CCG_ERR_INVALID;
+  }
+  if (!aligned(y, 16) || !aligned(x, 16)) { set_error("ccg_solve_refined: misaligned vector"); return CCG_ERR_INVALID; }
+  return static_cast<ccg_status>(
+      solve_refined(h, method, op, op_in, y, x, tol, max_outer, inner_tol, inner_maxit, res_hist, inner_iters, info));
+}
+
 ccg_status ccg_timing_enable(ccg_handle* h, int enable) {
   if (!h) return CCG_ERR_INVALID;
   h->timing = enable != 0;
   return CCG_OK;
 }
 
-ccg_status ccg_timing_read(ccg_handle* h, int kind, int64_t* sweeps, double* total_ms, double* bytes_per_sweep) {
-  if (!h || kind < 0 || kind >= CCG_SWEEP_KINDS) { set_error("ccg_timing_read: bad handle or kind"); return CCG_ERR_INVALID; }
+ccg_status ccg_timing_read(ccg_handle* h, int dtype, int kind, int64_t* sweeps, double* total_ms,
+                           double* bytes_per_sweep) {
+  if (!h || kind < 0 || kind >= CCG_SWEEP_KINDS || (dtype != CCG_C64 && dtype != CCG_C128)) {
+    set_error("ccg_timing_read: bad handle, dtype or kind");
+    return CCG_ERR_INVALID;
+  }
   API_CUDA(cudaStreamSynchronize(h->stream));
   timing_collect(h);
-  if (sweeps) *sweeps = h->timed_sweeps[kind];
-  if (total_ms) *total_ms = h->timed_ms[kind];
-  if (bytes_per_sweep) *bytes_per_sweep = h->bytes_per_sweep[kind];
+  const int slot = dtype * CCG_SWEEP_KINDS + kind;
+  if (sweeps) *sweeps = h->timed_sweeps[slot];
+  if (total_ms) *total_ms = h->timed_ms[slot];
+  if (bytes_per_sweep) *bytes_per_sweep = h->bytes_per_sweep[slot];
   return CCG_OK;
 }
 
@@ -234,7 +262,7 @@ ccg_status ccg_timing_reset(ccg_handle* h) {
   if (!h) return CCG_ERR_INVALID;
   API_CUDA(cudaStreamSynchronize(h->stream));
   timing_collect(h);
-  for (int k = 0; k < CCG_SWEEP_KINDS; ++k) {
+  for (int k = 0; k < 2 * CCG_SWEEP_KINDS; ++k) {
     h->timed_sweeps[k] = 0;
     h->timed_ms[k] = 0.0;
   }

@@ -54,14 +54,15 @@ template <class T> __device__ __forceinline__ T warp_csum(T s) {
 }
 
 // Result of an operator application: either a plain vector y, or `nparts`
-// partial vectors P[part * ld + i] whose sum is y (summed in part order).
+// partial vectors P[part * ld + i] whose sum is y (summed in part order), or
+// (both null) the zero vector.
 template <class R> struct MvOut {
   const cx<R>* y;
   const cx<R>* P;
   int64_t ld;
   int nparts;
   __device__ __forceinline__ cx<R> get(int64_t i) const {
-    if (P == nullptr) return y[i];
+    if (P == nullptr) return y != nullptr ? y[i] : mk<R>(0, 0);
     cx<R> s = P[i];
     for (int q = 1; q < nparts; ++q) s = cadd(s, P[(int64_t)q * ld + i]);
     return s;

@@ -40,11 +40,11 @@ struct ccg_handle {
   // operator-sweep timing, per ccg_sweep_kind
   bool timing = false;
   std::vector<cudaEvent_t> tev;  // start/stop pairs
-  std::vector<int> tev_kind;     // sweep kind of each pair
+  std::vector<int> tev_kind;     // dtype * CCG_SWEEP_KINDS + sweep kind of each pair
   size_t tev_used = 0;
-  int64_t timed_sweeps[CCG_SWEEP_KINDS] = {0, 0, 0};
-  double timed_ms[CCG_SWEEP_KINDS] = {0.0, 0.0, 0.0};
-  double bytes_per_sweep[CCG_SWEEP_KINDS] = {0.0, 0.0, 0.0};
+  int64_t timed_sweeps[2 * CCG_SWEEP_KINDS] = {};
+  double timed_ms[2 * CCG_SWEEP_KINDS] = {};
+  double bytes_per_sweep[2 * CCG_SWEEP_KINDS] = {};
   // kernels launched by this handle
   int64_t launches = 0;
 };
@@ -57,12 +57,15 @@ int arena_reserve(ccg_handle* h, size_t bytes);
 
 // Timing hooks around one operator sweep (no-ops unless timing is enabled).
 void timing_begin(ccg_handle* h);
-void timing_end(ccg_handle* h, int kind, double bytes);
+void timing_end(ccg_handle* h, int dtype, int kind, double bytes);
 void timing_collect(ccg_handle* h);
 
 // Entry points implemented in solve.cu.
 int solve_dense(ccg_handle* h, int method, const ccg_operator* op, const void* y, void* x, double tol, int maxit,
                 double* res_hist, ccg_info* info);
+int solve_refined(ccg_handle* h, int method, const ccg_operator* op, const ccg_operator* op_in, const void* y,
+                  void* x, double tol, int max_outer, double inner_tol, int inner_maxit, double* res_hist,
+                  int* inner_iters, ccg_info* info);
 int matvec_dense(ccg_handle* h, const ccg_operator* op, int trans, const void* x, void* y);
 int dot_device(ccg_handle* h, ccg_dtype dtype, int64_t n, const void* u, const void* v, int conj, double* out2);
 

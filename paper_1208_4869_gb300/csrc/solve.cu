@@ -731,7 +731,7 @@ template <class R> struct Runner {
     } else {
       gemv_n_rows<R, 1><<<d.grid_rows, kBlock, 0, s>>>(d.A, d.lda, d.n, x, y, st);
     }
-    timing_end(h, CCG_SWEEP_N, d.sweep_bytes());
+    timing_end(h, sizeof(R) == 8 ? CCG_C128 : CCG_C64, CCG_SWEEP_N, d.sweep_bytes());
     ++h->launches;
     return plain(y);
   }
@@ -747,7 +747,7 @@ template <class R> struct Runner {
     } else {
       gemv_tile<R, 1, Dense<R>::E, false, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, nullptr, x, nullptr, w.P2, st);
     }
-    timing_end(h, CCG_SWEEP_C, d.sweep_bytes());
+    timing_end(h, sizeof(R) == 8 ? CCG_C128 : CCG_C64, CCG_SWEEP_C, d.sweep_bytes());
     ++h->launches;
     MvOut<R> m; m.y = nullptr; m.P = w.P2; m.ld = d.n; m.nparts = d.nsplit;
     return m;
@@ -764,7 +764,7 @@ template <class R> struct Runner {
     } else {
       gemv_tile<R, 1, Dense<R>::E, true, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, x1, x2, w.P1, w.P2, st);
     }
-    timing_end(h, CCG_SWEEP_BOTH, d.sweep_bytes());
+    timing_end(h, sizeof(R) == 8 ? CCG_C128 : CCG_C64, CCG_SWEEP_BOTH, d.sweep_bytes());
     ++h->launches;
     o1.y = nullptr; o1.P = w.P1; o1.ld = d.n; o1.nparts = d.ncb;
     o2.y = nullptr; o2.P = w.P2; o2.ld = d.n; o2.nparts = d.nsplit;
@@ -778,32 +778,27 @@ template <class R> static int poll_chunk(const Dense<R>& d) {
   return std::max(1, std::min(c, 4));
 }
 
+// Host or device vectors?  Both y and x must be of the same kind.
+static int classify(const void* y, const void* x, bool* host) {
+  cudaPointerAttributes ay, ax;
+  CCG_CUDA(cudaPointerGetAttributes(&ay, y));
+  CCG_CUDA(cudaPointerGetAttributes(&ax, x));
+  const bool hy = ay.type == cudaMemoryTypeUnregistered || ay.type == cudaMemoryTypeHost;
+  const bool hx = ax.type == cudaMemoryTypeUnregistered || ax.type == cudaMemoryTypeHost;
+  if (hy != hx) { set_error("y and x must both be host or both be device pointers"); return CCG_ERR_INVALID; }
+  *host = hy;
+  return CCG_OK;
+}
+
+// One solve on device vectors y, x with the workspace w: r0, the method's
+// iterations, polling; returns with the stream idle and the final state in
+// *fin.  x0_zero skips the A x0 sweep (x is then set to zero on entry).
 template <class R>
-static int run_dense(ccg_handle* h, int method, const ccg_operator* op, const void* y_in, void* x_in, double tol,
-                     int maxit, double* res_hist, ccg_info* info) {
+static int solve_core(ccg_handle* h, int method, const ccg_operator* op, const Ws<R>& w, const cx<R>* y, cx<R>* x,
+                      double tol, int maxit, bool x0_zero, SolveState* fin) {
   const int64_t n = op->n;
-  Dense<R> dl(op, h->num_sms);
-  int rc = arena_reserve(h, ws_bytes<R>(n, dl, maxit));
-  if (rc != CCG_OK) return rc;
-  Ws<R> w = ws_carve<R>(h->arena, n, dl, maxit);
   Runner<R> run(h, op, w);
   cudaStream_t s = h->stream;
-
-  // Host or device vectors?
-  cudaPointerAttributes ay, ax;
-  CCG_CUDA(cudaPointerGetAttributes(&ay, y_in));
-  CCG_CUDA(cudaPointerGetAttributes(&ax, x_in));
-  const bool host_y = ay.type == cudaMemoryTypeUnregistered || ay.type == cudaMemoryTypeHost;
-  const bool host_x = ax.type == cudaMemoryTypeUnregistered || ax.type == cudaMemoryTypeHost;
-  if (host_y != host_x) { set_error("ccg_solve: y and x must both be host or both be device pointers"); return CCG_ERR_INVALID; }
-  const cx<R>* y = static_cast<const cx<R>*>(y_in);
-  cx<R>* x = static_cast<cx<R>*>(x_in);
-  if (host_y) {
-    CCG_CUDA(cudaMemcpyAsync(w.ystage, y_in, n * sizeof(cx<R>), cudaMemcpyHostToDevice, s));
-    CCG_CUDA(cudaMemcpyAsync(w.xstage, x_in, n * sizeof(cx<R>), cudaMemcpyHostToDevice, s));
-    y = w.ystage;
-    x = w.xstage;
-  }
 
   SolveState init;
   std::memset(&init, 0, sizeof(init));
@@ -812,22 +807,26 @@ static int run_dense(ccg_handle* h, int method, const ccg_operator* op, const vo
   init.hist = w.hist;
   CCG_CUDA(cudaMemcpyAsync(w.st, &init, sizeof(init), cudaMemcpyHostToDevice, s));
   CCG_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(unsigned int), s));
+  if (x0_zero) CCG_CUDA(cudaMemsetAsync(x, 0, n * sizeof(cx<R>), s));
 
-  cx<R>** V = w.vec;
+  cx<R>* const* V = w.vec;
   SolveState* st = w.st;
 
   // r0 = y - A x0
   {
     InitR<R> p;
     p.n = n; p.y = y; p.r = V[0]; p.c1 = nullptr; p.c2 = nullptr; p.method = method;
-    cx<R>* tmp = V[11];
     switch (method) {
       case M_BICGSTAB: p.c1 = V[1]; break;               // r^
       case M_QMR: p.c1 = V[1]; p.c2 = V[2]; break;       // v~, w~
       case M_COCG: p.c1 = V[1]; break;                   // p
       default: break;
     }
-    p.ax = run.apply_n(x, tmp, st);
+    if (x0_zero) {
+      p.ax.y = nullptr; p.ax.P = nullptr; p.ax.ld = n; p.ax.nparts = 0;
+    } else {
+      p.ax = run.apply_n(x, V[11], st);
+    }
     run.phase(p);
   }
 
@@ -874,7 +873,7 @@ static int run_dense(ccg_handle* h, int method, const ccg_operator* op, const vo
 
   // Enqueue iterations in chunks; poll the device record of the chunk before.
   Poll* pin = static_cast<Poll*>(h->pinned);
-  const int chunk = poll_chunk(dl);
+  const int chunk = poll_chunk(run.d);
   int launched = 0, npoll = 0;
   for (;;) {
     if (launched < maxit) {
@@ -894,30 +893,62 @@ static int run_dense(ccg_handle* h, int method, const ccg_operator* op, const vo
     if (launched >= maxit) break;
   }
   CCG_CUDA(cudaStreamSynchronize(s));
-  SolveState fin;
-  CCG_CUDA(cudaMemcpy(&fin, st, sizeof(fin), cudaMemcpyDeviceToHost));
-  const int iters = fin.poll.k;
-  if (!fin.poll.done) {  // cannot happen: maxit bounds the loop and the last iteration stops the solve
-    set_error("ccg_solve: solve did not record its end");
+  CCG_CUDA(cudaMemcpy(fin, st, sizeof(SolveState), cudaMemcpyDeviceToHost));
+  if (!fin->poll.done) {  // cannot happen: maxit bounds the loop and the last iteration stops the solve
+    set_error("solve did not record its end");
     return CCG_ERR_CUDA;
   }
+  return CCG_OK;
+}
+
+// ||y - A x|| / ||y|| from the final x (one more sweep), with st forced live.
+template <class R>
+static int true_residual(ccg_handle* h, const ccg_operator* op, const Ws<R>& w, const SolveState& fin,
+                         const cx<R>* y, const cx<R>* x, double* out) {
+  Runner<R> run(h, op, w);
+  SolveState live = fin;
+  live.poll.done = 0;
+  live.half = 0;
+  CCG_CUDA(cudaMemcpyAsync(w.st, &live, sizeof(live), cudaMemcpyHostToDevice, h->stream));
+  TrueRes<R> tr;
+  tr.n = op->n; tr.y = y; tr.out = w.scratch;
+  tr.ax = run.apply_n(x, w.vec[11], w.st);
+  run.phase(tr);
+  CCG_CUDA(cudaGetLastError());
+  double rr = 0.0;
+  CCG_CUDA(cudaMemcpyAsync(&rr, w.scratch, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CCG_CUDA(cudaStreamSynchronize(h->stream));
+  *out = fin.poll.ynorm > 0 ? std::sqrt(rr) / fin.poll.ynorm : 0.0;
+  return CCG_OK;
+}
+
+template <class R>
+static int run_dense(ccg_handle* h, int method, const ccg_operator* op, const void* y_in, void* x_in, double tol,
+                     int maxit, double* res_hist, ccg_info* info) {
+  const int64_t n = op->n;
+  Dense<R> dl(op, h->num_sms);
+  int rc = arena_reserve(h, ws_bytes<R>(n, dl, maxit));
+  if (rc != CCG_OK) return rc;
+  Ws<R> w = ws_carve<R>(h->arena, n, dl, maxit);
+  cudaStream_t s = h->stream;
+  bool host = false;
+  if ((rc = classify(y_in, x_in, &host)) != CCG_OK) return rc;
+  const cx<R>* y = static_cast<const cx<R>*>(y_in);
+  cx<R>* x = static_cast<cx<R>*>(x_in);
+  if (host) {
+    CCG_CUDA(cudaMemcpyAsync(w.ystage, y_in, n * sizeof(cx<R>), cudaMemcpyHostToDevice, s));
+    CCG_CUDA(cudaMemcpyAsync(w.xstage, x_in, n * sizeof(cx<R>), cudaMemcpyHostToDevice, s));
+    y = w.ystage;
+    x = w.xstage;
+  }
+  SolveState fin;
+  if ((rc = solve_core<R>(h, method, op, w, y, x, tol, maxit, false, &fin)) != CCG_OK) return rc;
+  const int iters = fin.poll.k;
   if (fin.zero_rhs) CCG_CUDA(cudaMemsetAsync(x, 0, n * sizeof(cx<R>), s));
   if (res_hist) CCG_CUDA(cudaMemcpyAsync(res_hist, w.hist, (size_t)(iters + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
-  double true_rr = -1.0;
-  if (info) {
-    // ||y - A x|| from the final x, outside the iteration (state forced live)
-    SolveState live = fin;
-    live.poll.done = 0;
-    live.half = 0;
-    CCG_CUDA(cudaMemcpyAsync(st, &live, sizeof(live), cudaMemcpyHostToDevice, s));
-    TrueRes<R> tr;
-    tr.n = n; tr.y = y; tr.out = w.scratch;
-    tr.ax = run.apply_n(x, w.vec[11], st);
-    run.phase(tr);
-    CCG_CUDA(cudaGetLastError());
-    CCG_CUDA(cudaMemcpyAsync(&true_rr, w.scratch, sizeof(double), cudaMemcpyDeviceToHost, s));
-  }
-  if (host_x) CCG_CUDA(cudaMemcpyAsync(x_in, x, n * sizeof(cx<R>), cudaMemcpyDeviceToHost, s));
+  double true_rel = -1.0;
+  if (info && (rc = true_residual<R>(h, op, w, fin, y, x, &true_rel)) != CCG_OK) return rc;
+  if (host) CCG_CUDA(cudaMemcpyAsync(x_in, x, n * sizeof(cx<R>), cudaMemcpyDeviceToHost, s));
   CCG_CUDA(cudaStreamSynchronize(s));
   timing_collect(h);
   if (info) {
@@ -927,7 +958,7 @@ static int run_dense(ccg_handle* h, int method, const ccg_operator* op, const vo
     info->reserved = 0;
     info->relres = fin.poll.relres;
     info->ynorm = fin.poll.ynorm;
-    info->true_relres = fin.poll.ynorm > 0 ? std::sqrt(true_rr) / fin.poll.ynorm : 0.0;
+    info->true_relres = true_rel;
   }
   return fin.poll.status;
 }
@@ -936,6 +967,142 @@ int solve_dense(ccg_handle* h, int method, const ccg_operator* op, const void* y
                 double* res_hist, ccg_info* info) {
   if (op->dtype == CCG_C128) return run_dense<double>(h, method, op, y, x, tol, maxit, res_hist, info);
   return run_dense<float>(h, method, op, y, x, tol, maxit, res_hist, info);
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-precision iterative refinement: r = y - A x and x += d in complex128,
+// the correction A d = r solved by a complex64 Krylov method.
+// ---------------------------------------------------------------------------
+struct RefResid : PhaseBase {  // r = y - A x (double); r32 = round(r); d32 = 0
+  static constexpr int NQ = 3;   // ||y||^2, ||r||^2, non-finite count in y
+  int64_t n;
+  const double2* y;
+  MvOut<double> ax;
+  float2* r32;
+  float2* d32;
+  int outer;
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    const double2 yi = y[i];
+    const double2 ri = csub(yi, ax.get(i));
+    r32[i] = make_float2((float)ri.x, (float)ri.y);
+    d32[i] = make_float2(0.f, 0.f);
+    acc[0] += yi.x * yi.x + yi.y * yi.y;
+    acc[1] += ri.x * ri.x + ri.y * ri.y;
+    if (!(isfinite(yi.x) && isfinite(yi.y))) acc[2] += 1.0;
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    st->poll.k = outer;
+    if (t[2] != 0.0) { st->poll.status = ST_NONFINITE; st->poll.done = 1; return; }
+    const double yn = sqrt(t[0]);
+    st->poll.ynorm = yn;
+    if (yn == 0.0) {
+      st->zero_rhs = 1;
+      st->hist[outer] = 0.0;
+      st->poll.relres = 0.0;
+      st->poll.status = ST_OK;
+      st->poll.done = 1;
+      return;
+    }
+    const double rel = sqrt(t[1]) / yn;
+    st->hist[outer] = rel;
+    st->poll.relres = rel;
+    if (nonfinite(rel)) { st->poll.status = ST_NONFINITE; st->poll.done = 1; return; }
+    if (rel <= st->tol) { st->poll.status = ST_OK; st->poll.done = 1; return; }
+    if (outer >= st->maxit) { st->poll.status = ST_NOT_CONVERGED; st->poll.done = 1; }
+  }
+};
+struct RefUpdate : PhaseBase {  // x += widen(d32)
+  static constexpr bool kReduce = false;
+  static constexpr int NQ = 1;
+  int64_t n;
+  double2* x;
+  const float2* d32;
+  __device__ __forceinline__ void element(int64_t i, double*) {
+    const float2 d = d32[i];
+    x[i] = cadd(x[i], make_double2((double)d.x, (double)d.y));
+  }
+  __device__ void finish(const double*, SolveState*) {}
+};
+
+int solve_refined(ccg_handle* h, int method, const ccg_operator* op, const ccg_operator* op_in, const void* y_in,
+                  void* x_in, double tol, int max_outer, double inner_tol, int inner_maxit, double* res_hist,
+                  int* inner_iters, ccg_info* info) {
+  const int64_t n = op->n;
+  Dense<double> d64(op, h->num_sms);
+  Dense<float> d32(op_in, h->num_sms);
+  const size_t b64 = ws_bytes<double>(n, d64, max_outer);
+  int rc = arena_reserve(h, b64 + ws_bytes<float>(n, d32, inner_maxit));
+  if (rc != CCG_OK) return rc;
+  Ws<double> w = ws_carve<double>(h->arena, n, d64, max_outer);
+  Ws<float> wi = ws_carve<float>(h->arena + b64, n, d32, inner_maxit);
+  cudaStream_t s = h->stream;
+  bool host = false;
+  if ((rc = classify(y_in, x_in, &host)) != CCG_OK) return rc;
+  const double2* y = static_cast<const double2*>(y_in);
+  double2* x = static_cast<double2*>(x_in);
+  if (host) {
+    CCG_CUDA(cudaMemcpyAsync(w.ystage, y_in, n * sizeof(double2), cudaMemcpyHostToDevice, s));
+    CCG_CUDA(cudaMemcpyAsync(w.xstage, x_in, n * sizeof(double2), cudaMemcpyHostToDevice, s));
+    y = w.ystage;
+    x = w.xstage;
+  }
+  float2* r32 = wi.ystage;   // right-hand side of the inner solve
+  float2* dd = wi.xstage;    // its solution, the correction
+  Runner<double> run(h, op, w);
+
+  SolveState init;
+  std::memset(&init, 0, sizeof(init));
+  init.maxit = max_outer;
+  init.tol = tol;
+  init.hist = w.hist;
+  CCG_CUDA(cudaMemcpyAsync(w.st, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+  CCG_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(unsigned int), s));
+
+  int total_inner = 0, status = CCG_NOT_CONVERGED, bd = 0;
+  SolveState outer_state;
+  std::memset(&outer_state, 0, sizeof(outer_state));
+  for (int outer = 0;; ++outer) {
+    RefResid rp;
+    rp.n = n; rp.y = y; rp.r32 = r32; rp.d32 = dd; rp.outer = outer;
+    rp.ax = run.apply_n(x, w.vec[0], w.st);
+    run.phase(rp);
+    CCG_CUDA(cudaGetLastError());
+    CCG_CUDA(cudaMemcpyAsync(h->pinned, &w.st->poll, sizeof(Poll), cudaMemcpyDeviceToHost, s));
+    CCG_CUDA(cudaStreamSynchronize(s));
+    const Poll pl = *static_cast<Poll*>(h->pinned);
+    outer_state.poll = pl;
+    if (pl.done) { status = pl.status; break; }
+    SolveState fin;
+    if ((rc = solve_core<float>(h, method, op_in, wi, r32, dd, inner_tol, inner_maxit, true, &fin)) != CCG_OK)
+      return rc;
+    total_inner += fin.poll.k;
+    if (fin.poll.status == ST_NONFINITE) { status = CCG_ERR_NONFINITE; break; }
+    if (fin.poll.status == ST_BREAKDOWN && fin.poll.k == 0) { status = CCG_BREAKDOWN; bd = fin.poll.breakdown; break; }
+    RefUpdate up;
+    up.n = n; up.x = x; up.d32 = dd;
+    run.phase(up);
+  }
+  CCG_CUDA(cudaGetLastError());
+  const int outer_steps = outer_state.poll.k;
+  SolveState fs;
+  CCG_CUDA(cudaMemcpy(&fs, w.st, sizeof(fs), cudaMemcpyDeviceToHost));
+  if (fs.zero_rhs) CCG_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double2), s));
+  if (res_hist)
+    CCG_CUDA(cudaMemcpyAsync(res_hist, w.hist, (size_t)(outer_steps + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (host) CCG_CUDA(cudaMemcpyAsync(x_in, x, n * sizeof(double2), cudaMemcpyDeviceToHost, s));
+  CCG_CUDA(cudaStreamSynchronize(s));
+  timing_collect(h);
+  if (inner_iters) *inner_iters = total_inner;
+  if (info) {
+    info->iters = outer_steps;
+    info->status = status;
+    info->breakdown = bd;
+    info->reserved = 0;
+    info->relres = outer_state.poll.relres;
+    info->ynorm = outer_state.poll.ynorm;
+    info->true_relres = outer_state.poll.relres;   // the outer residual is recomputed from x in double
+  }
+  return status;
 }
 
 template <class R> static int matvec_t(ccg_handle* h, const ccg_operator* op, int trans, const void* x_, void* y_) {
