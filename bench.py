@@ -41,20 +41,34 @@ METRIC = "solves/s at rel-res 1e-10, mixed vs FP64 GPU; % HBM roofline; p50/p99 
 def parse_args(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--steps", type=int, default=None)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ccg", "reference"], default="ccg")
+    p.add_argument("--workload", choices=["dense", "dipole"], default="dense")
     p.add_argument("--n", type=int, default=8192)
-    p.add_argument("--methods", default="bicgstab,cgnr,qmr")
+    p.add_argument("--L", type=int, default=64)
+    p.add_argument("--methods", default=None)
     p.add_argument("--path", choices=["fp64", "mixed", "auto"], default="auto")
-    p.add_argument("--tol", type=float, default=1e-10)
+    p.add_argument("--tol", type=float, default=None)
     p.add_argument("--maxit", type=int, default=1000)
     p.add_argument("--max-outer", type=int, default=30)
-    p.add_argument("--inner-tol", type=float, default=1e-5)
-    p.add_argument("--inner-maxit", type=int, default=200)
+    p.add_argument("--inner-tol", type=float, default=None)
+    p.add_argument("--inner-maxit", type=int, default=None)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    return p.parse_args(argv)
+    a = p.parse_args(argv)
+    dense = a.workload == "dense"
+    if a.methods is None:
+        a.methods = "bicgstab,cgnr,qmr" if dense else "cocg,bicgstab"
+    if a.tol is None:
+        a.tol = 1e-10 if dense else 1e-8
+    if a.inner_tol is None:
+        a.inner_tol = 1e-5 if dense else 1e-4
+    if a.steps is None:
+        a.steps = 30 if dense else 3
+    if a.inner_maxit is None:
+        a.inner_maxit = 200 if dense else 2000
+    return a
 
 
 # ----------------------------------------------------------------- ranks
@@ -178,10 +192,11 @@ def profiled_traffic(kernel, src_files):
 
 
 SWEEP_KERNELS = {0: ("gemv_n_rows", 1), 1: ("gemv_tile_c", 1), 2: ("gemv_tile_both", 2)}
+DIPOLE_KERNELS = {0: ("dipole_fft_matvec", 1), 1: ("dipole_fft_matvec_h", 1), 2: ("dipole_fft_both", 2)}
 KERNEL_SOURCES = ["paper_1208_4869_gb300/csrc/gemv.cuh", "paper_1208_4869_gb300/csrc/common.cuh"]
 
 
-def roofline(ccg, sweep_stats, n):
+def roofline(ccg, sweep_stats, n, dipole=False):
     """Roofline of the sweep (precision, kind) that took the most device time
     in the timed region: algorithmic flops (8 n^2 per complex product; the
     fused QMR sweep forms two) and bytes (the matrix, read once per sweep)
@@ -189,11 +204,11 @@ def roofline(ccg, sweep_stats, n):
     kinds = {}
     for (dt, kind), (cnt, ms, nbytes) in sweep_stats.items():
         if cnt:
-            name, products = SWEEP_KERNELS[kind]
+            name, products = (DIPOLE_KERNELS if dipole else SWEEP_KERNELS)[kind]
             tag = "%s_%s" % (name, "c128" if dt == ccg.C128 else "c64")
             avg = ms / cnt
             kinds[tag] = {"launches": cnt, "total_ms": ms, "avg_ms": avg,
-                          "tflops": 8.0 * products * n * n / (avg * 1e-3) / 1e12,
+                          "tflops": None if dipole else 8.0 * products * n * n / (avg * 1e-3) / 1e12,
                           "gbs": nbytes / (avg * 1e-3) / 1e9, "bytes": nbytes}
     if not kinds:
         return None
@@ -201,11 +216,11 @@ def roofline(ccg, sweep_stats, n):
     k = kinds[top]
     hbm, hbm_src = peaks()
     traffic = profiled_traffic(top, KERNEL_SOURCES)
-    if top.endswith("c128"):   # FP64 FMA pipe bound (4 DFMA per 16-byte element)
+    if top.endswith("c128") and not dipole:   # FP64 FMA pipe bound (4 DFMA per 16-byte element)
         roof = {"kernel": top, "bound": "alu", "achieved": k["tflops"], "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": k["tflops"] / FP64_PEAK_TFLOPS,
                 "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (no measured FP64 peak)"}
-    else:                      # HBM bound
+    else:                      # HBM bound (complex64 sweeps; the FFT operator)
         roof = {"kernel": top, "bound": "hbm", "achieved": k["gbs"], "peak": hbm,
                 "unit": "GB/s", "frac": k["gbs"] / hbm, "peak_source": "%s copy bandwidth" % hbm_src}
     roof["traffic"] = traffic[0] if traffic else None
@@ -313,17 +328,32 @@ def run_ours(args):
     ccg.lib()
 
     methods = args.methods.split(",")
-    n = args.n
-    A, y = W.dense_system(n, 3.0, 0)
     headline = "mixed" if args.path == "auto" else args.path
-    Ad = torch.from_numpy(A).to(dev)
-    A32 = Ad.to(torch.complex64)
-    yd = torch.from_numpy(y).to(dev)
-    xd = torch.zeros_like(yd)
     stream = torch.cuda.current_stream(dev)
     h = ccg.Handle(stream)
-    op64 = h.op_dense(Ad)
-    op32 = h.op_dense(A32)
+    dipole = args.workload == "dipole"
+    if dipole:
+        occ = W.sphere_occupancy(args.L)
+        y = W.plane_wave_rhs(occ, W.DIPOLE_CFG["kd"])
+        op64 = h.op_dipole(occ, W.DIPOLE_CFG["kd"], W.DIPOLE_CFG["m"], dtype="complex128")
+        op32 = h.op_dipole(occ, W.DIPOLE_CFG["kd"], W.DIPOLE_CFG["m"], dtype="complex64")
+        n = op64.n
+        A = None
+        workload = ("dipole L=%d sphere (%d dipoles), kd=0.5, m=1.5+0.01i, x-polarised plane wave, %s to %g"
+                    % (args.L, op64.nsites, "/".join(methods), args.tol))
+        l2 = "inputs larger than L2 (field tensor %.0f MB complex64 + %.0f MB complex128)" % (
+            6 * (2 * args.L) ** 3 * 8 / 1e6, 6 * (2 * args.L) ** 3 * 16 / 1e6)
+    else:
+        n = args.n
+        A, y = W.dense_system(n, 3.0, 0)
+        Ad = torch.from_numpy(A).to(dev)
+        A32 = Ad.to(torch.complex64)
+        op64 = h.op_dense(Ad)
+        op32 = h.op_dense(A32)
+        workload = "dense single-RHS n=%d shift 3, %s to %g" % (n, "/".join(methods), args.tol)
+        l2 = "inputs larger than L2 (A %.2f GB)" % (A.nbytes / 1e9)
+    yd = torch.from_numpy(y).to(dev)
+    xd = torch.zeros_like(yd)
 
     def solve(path, m, yv, xv):
         if path == "mixed":
@@ -386,10 +416,10 @@ def run_ours(args):
         e2e = {"value": solves / dt, "unit": "solves/s", "h2d_bytes_per_step": 2 * len(methods) * y.nbytes,
                "d2h_bytes_per_step": len(methods) * y.nbytes}
 
-    roof = roofline(ccg, stats, n)
+    roof = roofline(ccg, stats, n, dipole)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not dipole:
         v, nsolve, dt, its = oracle_sample(A, y, methods[:1], budget_s=15.0, tol=args.tol, maxit=args.maxit)
         cpu = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
                "sample": "%d whole %s solve(s) of the same system (complex128, to %g) in %.1f s, serial C++"
@@ -403,11 +433,9 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": t_max_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64+c128" if headline == "mixed" else "c128",
             "data": "synthetic",
-            "config": {"workload": "dense single-RHS n=%d shift 3, bicgstab/cgnr/qmr to 1e-10" % n, "n": n,
-                       "methods": methods, "tol": args.tol, "path": headline,
+            "config": {"workload": workload, "n": n, "methods": methods, "tol": args.tol, "path": headline,
                        "inner_tol": args.inner_tol if headline == "mixed" else None,
-                       "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "inputs larger than L2 (A %.2f GB)" % (A.nbytes / 1e9)},
+                       "parallelism": "replicas" if world > 1 else "single", "l2": l2},
             "iters": {m: [it, inner] for m, _, it, inner, _ in results[: len(methods)]},
             "all_converged": ok,
             "latency_ms": {"p50": 1e3 * statistics.median(lat_sorted),

@@ -105,6 +105,29 @@ int ccg_abi_version(void);
  * (C128) aligned. */
 ccg_status ccg_op_dense(ccg_handle* h, ccg_dtype dtype, int64_t n, const void* A, int64_t lda, int flags,
                         ccg_operator** op);
+/* Discrete-dipole operator (the DDSCAT application named in Sec. 1; the
+ * manual does not define it -- this is the standard system):
+ *   (A p)_s = p_s / alpha - sum_{t != s} G(r_s - r_t) p_t
+ * over the occupied cells of an nx x ny x nz lattice with unit spacing,
+ * G(r) = exp(ikr)/r^3 [ (kr)^2 (I - u u^T) + (1 - ikr)(3 u u^T - I) ] the
+ * field tensor of a point dipole (u = r/|r|, k = kd), and the
+ * Clausius-Mossotti polarizability alpha = (3/4pi)(m^2 - 1)/(m^2 + 2) for
+ * refractive index m = m_re + i m_im.
+ *  occ   host array of nx*ny*nz bytes, occ[(i*ny + j)*nz + l] != 0 marks an
+ *        occupied cell; read during the call only.
+ * Unknowns: 3N for N occupied cells, ordered v[a*N + s] (a = x, y, z; sites
+ * in occ order).  The operator is complex symmetric (flagged
+ * CCG_OP_SYMMETRIC).  It is applied by zero-padded FFT convolution on a
+ * (2nx) x (2ny) x (2nz) grid in the operator's precision; each of 2nx, 2ny,
+ * 2nz must be of the form 2^a 3^b and at most 256 (else CCG_ERR_INVALID).
+ * The operator owns its device memory (field tensor, FFT grids): about
+ * 9 * 8 nx ny nz * (16 B complex128 | 8 B complex64); its applications use
+ * one set of grids, so they must not run concurrently on two streams.
+ * Synchronises the handle's stream. */
+ccg_status ccg_op_dipole(ccg_handle* h, ccg_dtype dtype, int nx, int ny, int nz, const uint8_t* occ, double kd,
+                         double m_re, double m_im, ccg_operator** op);
+/* Number of occupied sites N of a dipole operator (0 for other operators). */
+int64_t ccg_dipole_sites(const ccg_operator* op);
 /* Free an operator (not the caller's matrix). */
 ccg_status ccg_op_destroy(ccg_operator* op);
 /* Number of unknowns of an operator. */

@@ -61,6 +61,9 @@ def lib():
     L.ccg_set_stream.argtypes = [vp, vp]
     L.ccg_op_dense.argtypes = [vp, i32, i64, vp, i64, i32, ctypes.POINTER(vp)]
     L.ccg_op_destroy.argtypes = [vp]
+    L.ccg_op_dipole.argtypes = [vp, i32, i32, i32, i32, vp, dbl, dbl, dbl, ctypes.POINTER(vp)]
+    L.ccg_dipole_sites.restype = i64
+    L.ccg_dipole_sites.argtypes = [vp]
     L.ccg_op_size.restype = i64
     L.ccg_op_size.argtypes = [vp]
     L.ccg_matvec.argtypes = [vp, vp, i32, vp, vp]
@@ -73,7 +76,7 @@ def lib():
     L.ccg_timing_reset.argtypes = [vp]
     L.ccg_launch_count.restype = i64
     L.ccg_launch_count.argtypes = [vp]
-    for name in ("ccg_create", "ccg_destroy", "ccg_set_stream", "ccg_op_dense", "ccg_op_destroy", "ccg_matvec",
+    for name in ("ccg_create", "ccg_destroy", "ccg_set_stream", "ccg_op_dense", "ccg_op_dipole", "ccg_op_destroy", "ccg_matvec",
                  "ccg_dot", "ccg_solve", "ccg_solve_refined", "ccg_timing_enable", "ccg_timing_read", "ccg_timing_reset"):
         getattr(L, name).restype = i32
     if L.ccg_abi_version() != 1:
@@ -139,6 +142,19 @@ class Handle:
         _check(lib().ccg_op_dense(self.h, _dtype_code(A.dtype), A.shape[0], _ptr(A), A.stride(0),
                                   OP_SYMMETRIC if symmetric else 0, ctypes.byref(op)))
         return Operator(op, A, _dtype_code(A.dtype))
+
+    def op_dipole(self, occ, kd, m, dtype="complex128"):
+        """ccg_op_dipole on a host uint8 occupancy array of shape (nx, ny, nz)."""
+        occ = np.ascontiguousarray(occ, dtype=np.uint8)
+        assert occ.ndim == 3
+        code = C128 if "128" in str(dtype) else C64
+        op = ctypes.c_void_p()
+        m = complex(m)
+        _check(lib().ccg_op_dipole(self.h, code, occ.shape[0], occ.shape[1], occ.shape[2],
+                                   ctypes.c_void_p(occ.ctypes.data), float(kd), m.real, m.imag, ctypes.byref(op)))
+        o = Operator(op, None, code)
+        o.nsites = int(lib().ccg_dipole_sites(op))
+        return o
 
     def matvec(self, op, x, y, trans=False):
         """ccg_matvec: y = A x (trans=False) or A^H x (trans=True), device vectors."""

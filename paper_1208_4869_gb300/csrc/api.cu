@@ -2,6 +2,8 @@
 // workspace, timing, and dispatch to the solver and operator code.
 #include <cuda_runtime.h>
 
+#include <cmath>
+#include <complex>
 #include <cstdint>
 #include <cstring>
 #include <new>
@@ -179,7 +181,52 @@ ccg_status ccg_op_dense(ccg_handle* h, ccg_dtype dtype, int64_t n, const void* A
   return CCG_OK;
 }
 
+ccg_status ccg_op_dipole(ccg_handle* h, ccg_dtype dtype, int nx, int ny, int nz, const uint8_t* occ, double kd,
+                         double m_re, double m_im, ccg_operator** op) {
+  if (!op) { set_error("ccg_op_dipole: NULL output"); return CCG_ERR_INVALID; }
+  *op = nullptr;
+  if (!h || !occ) { set_error("ccg_op_dipole: NULL handle or occupancy"); return CCG_ERR_INVALID; }
+  if (dtype != CCG_C64 && dtype != CCG_C128) { set_error("ccg_op_dipole: bad dtype"); return CCG_ERR_INVALID; }
+  if (nx < 1 || ny < 1 || nz < 1 || !(kd >= 0.0) || !std::isfinite(m_re) || !std::isfinite(m_im)) {
+    set_error("ccg_op_dipole: need nx, ny, nz >= 1, kd >= 0 and a finite refractive index");
+    return CCG_ERR_INVALID;
+  }
+  // Clausius-Mossotti polarizability (unit lattice spacing)
+  const std::complex<double> m(m_re, m_im), m2 = m * m;
+  const std::complex<double> alpha = (3.0 / (4.0 * M_PI)) * (m2 - 1.0) / (m2 + 2.0);
+  if (std::abs(alpha) == 0.0) { set_error("ccg_op_dipole: m^2 = 1 gives zero polarizability"); return CCG_ERR_INVALID; }
+  int64_t count = 0;
+  for (int64_t c = 0; c < (int64_t)nx * ny * nz; ++c) count += occ[c] != 0;
+  if (count == 0) { set_error("ccg_op_dipole: no occupied site"); return CCG_ERR_INVALID; }
+  ccg_operator* o = new (std::nothrow) ccg_operator();
+  if (!o) { set_error("ccg_op_dipole: host allocation failed"); return CCG_ERR_NOMEM; }
+  o->kind = CCG_OPK_DIPOLE;
+  o->dtype = dtype;
+  o->flags = CCG_OP_SYMMETRIC;
+  o->dip.nx = nx;
+  o->dip.ny = ny;
+  o->dip.nz = nz;
+  o->dip.kd = kd;
+  const std::complex<double> ainv = 1.0 / alpha;
+  o->dip.alpha_inv[0] = ainv.real();
+  o->dip.alpha_inv[1] = ainv.imag();
+  const int rc = dipole_create(o, occ, h->stream);
+  if (rc != CCG_OK) {
+    dipole_free(o);
+    delete o;
+    return static_cast<ccg_status>(rc);
+  }
+  *op = o;
+  return CCG_OK;
+}
+
+int64_t ccg_dipole_sites(const ccg_operator* op) { return (op && op->kind == CCG_OPK_DIPOLE) ? op->dip.nsites : 0; }
+
 ccg_status ccg_op_destroy(ccg_operator* op) {
+  if (op && op->kind == CCG_OPK_DIPOLE) {
+    cudaDeviceSynchronize();
+    dipole_free(op);
+  }
   delete op;
   return CCG_OK;
 }

@@ -1,0 +1,517 @@
+// Discrete-dipole operator (the DDSCAT application of the manual, Sec. 1):
+//     (A p)_s = p_s / alpha - sum_{t != s} G(r_s - r_t) p_t
+// over the occupied sites of an nx x ny x nz lattice with unit spacing, G the
+// field tensor of an oscillating point dipole (Gaussian units),
+//     G(r) = exp(ikr)/r^3 [ (kr)^2 (I - u u^T) + (1 - ikr)(3 u u^T - I) ],
+// and the Clausius-Mossotti polarizability alpha = (3/4pi)(m^2-1)/(m^2+2).
+//
+// The sum is a convolution on the lattice, applied by FFT on a grid of
+// M = 2n points per axis (circulant embedding: grid index q < n is
+// displacement q, q > n is q - M, q = n and the origin carry zero).  One
+// application is five kernels, pruned to the nonzero input octant and the
+// needed output octant, with the scatter, the 3x3 tensor multiply and the
+// gather fused into FFT passes:
+//   K1 scatter p into z-lines (i < nx, j < ny) + forward FFT along z
+//   K2 forward FFT along y for i < nx (input j < ny)
+//   K3 forward FFT along x (input i < nx), Y_a = sum_b Ghat_ab X_b, inverse
+//      FFT along x (output i < nx), all three components in one block
+//   K4 inverse FFT along y for i < nx (output j < ny)
+//   K5 inverse FFT along z + gather + diagonal term into y
+// Ghat (six symmetric components, scaled by 1/(Mx My Mz)) is computed once
+// per operator in double precision with the same FFT passes.  Unknowns are
+// ordered v[a * N + s] (component a = x, y, z; sites lexicographic, z
+// fastest).  A is complex symmetric, so A^H p = conj(A conj(p)).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "fft.cuh"
+#include "internal.h"
+
+namespace ccg {
+
+struct DipGeom {
+  int nx, ny, nz;
+  int Mx, My, Mz;
+  int64_t G;  // Mx * My * Mz
+  int64_t N;  // occupied sites
+};
+
+static DipGeom geom(const ccg_operator* op) {
+  DipGeom g;
+  g.nx = op->dip.nx; g.ny = op->dip.ny; g.nz = op->dip.nz;
+  g.Mx = 2 * g.nx; g.My = 2 * g.ny; g.Mz = 2 * g.nz;
+  g.G = (int64_t)g.Mx * g.My * g.Mz;
+  g.N = op->dip.nsites;
+  return g;
+}
+
+__device__ __forceinline__ bool skip_state(const SolveState* st) {
+  return st != nullptr && (st->poll.done || st->half);
+}
+
+// K1: gather the lattice z-line (i, j) of component q from the site vector,
+// zero-pad to Mz, forward FFT, store grid[q][i][j][:].
+template <class R, int N, int BL>
+__global__ void __launch_bounds__(kBlock) dip_fwd_z(const cx<R>* __restrict__ x, cx<R>* __restrict__ grid,
+                                                    const int* __restrict__ idx, DipGeom g, int bl_rt,
+                                                    const cx<R>* __restrict__ W, int conj_in,
+                                                    const SolveState* __restrict__ st) {
+  if (skip_state(st)) return;
+  extern __shared__ unsigned char smem_raw[];
+  const int Mz = N > 0 ? N : g.Mz;
+  const int ls = N > 0 ? fft_ls<N>() : g.Mz;
+  const int bl = BL > 0 ? BL : bl_rt;
+  cx<R>* buf0 = reinterpret_cast<cx<R>*>(smem_raw);
+  cx<R>* buf1 = buf0 + bl * ls;
+  const int q = blockIdx.y;
+  const int64_t nlines = (int64_t)g.nx * g.ny;
+  const int64_t l0 = (int64_t)blockIdx.x * bl;
+  const cx<R>* xq = x + (int64_t)q * g.N;
+  for (int t = threadIdx.x; t < bl * Mz; t += blockDim.x) {
+    const int b = t / Mz, l = t - b * Mz;
+    const int64_t line = l0 + b;
+    cx<R> v = mk<R>(0, 0);
+    if (line < nlines && l < g.nz) {
+      const int s = __ldg(&idx[line * g.nz + l]);
+      if (s >= 0) {
+        v = xq[s];
+        if (conj_in) v = cconj(v);
+      }
+    }
+    buf0[b * ls + l] = v;
+  }
+  __syncthreads();
+  const cx<R>* res = fft_lines<R, N, BL>(buf0, buf1, Mz, bl, W, -1);
+  cx<R>* gq = grid + (int64_t)q * g.G;
+  for (int t = threadIdx.x; t < bl * Mz; t += blockDim.x) {
+    const int b = t / Mz, kz = t - b * Mz;
+    const int64_t line = l0 + b;
+    if (line < nlines) {
+      const int64_t i = line / g.ny, j = line - i * g.ny;
+      gq[(i * g.My + j) * Mz + kz] = res[b * ls + kz];
+    }
+  }
+}
+
+// K3: x-lines (ky, kz0 .. kz0+bl-1) of all three components: forward FFT
+// (input i < nx), tensor multiply, inverse FFT, store i < nx.
+template <class R, int N, int BL>
+__global__ void __launch_bounds__(kBlock) dip_x_mul(cx<R>* __restrict__ grid, const cx<R>* __restrict__ ghat,
+                                                    DipGeom g, int bl_rt, const cx<R>* __restrict__ W,
+                                                    const SolveState* __restrict__ st) {
+  if (skip_state(st)) return;
+  extern __shared__ unsigned char smem_raw[];
+  const int Mx = N > 0 ? N : g.Mx;
+  const int ls = N > 0 ? fft_ls<N>() : g.Mx;
+  const int bl = BL > 0 ? BL : bl_rt;
+  const int per = bl * ls;                      // one component's lines
+  cx<R>* buf0 = reinterpret_cast<cx<R>*>(smem_raw);
+  cx<R>* buf1 = buf0 + 3 * per;
+  const int cblocks = (g.Mz + bl - 1) / bl;
+  const int ky = blockIdx.x / cblocks;
+  const int kz0 = (blockIdx.x - ky * cblocks) * bl;
+  const int64_t sx = (int64_t)g.My * g.Mz;      // stride along x
+  const int64_t off = (int64_t)ky * g.Mz + kz0;
+  for (int t = threadIdx.x; t < 3 * bl * Mx; t += blockDim.x) {
+    const int q = t / (bl * Mx), r = t - q * (bl * Mx);
+    const int b = r % bl, i = r / bl;
+    cx<R> v = mk<R>(0, 0);
+    if (i < g.nx && kz0 + b < g.Mz) v = grid[(int64_t)q * g.G + i * sx + off + b];
+    buf0[q * per + b * ls + i] = v;
+  }
+  __syncthreads();
+  cx<R>* fw = fft_lines<R, N, 3 * BL>(buf0, buf1, Mx, 3 * bl, W, -1);
+  cx<R>* other = fw == buf0 ? buf1 : buf0;
+  for (int t = threadIdx.x; t < bl * Mx; t += blockDim.x) {
+    const int b = t % bl, kx = t / bl;
+    if (kz0 + b < g.Mz) {
+      const int64_t gi = kx * sx + off + b;
+      cx<R> c[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) c[k] = __ldg(&ghat[(int64_t)k * g.G + gi]);
+      const int e = b * ls + kx;
+      const cx<R> X0 = fw[e], X1 = fw[per + e], X2 = fw[2 * per + e];
+      // components xx, xy, xz, yy, yz, zz
+      fw[e] = cfma(c[2], X2, cfma(c[1], X1, cmul(c[0], X0)));
+      fw[per + e] = cfma(c[4], X2, cfma(c[3], X1, cmul(c[1], X0)));
+      fw[2 * per + e] = cfma(c[5], X2, cfma(c[4], X1, cmul(c[2], X0)));
+    }
+  }
+  __syncthreads();
+  const cx<R>* res = fft_lines<R, N, 3 * BL>(fw, other, Mx, 3 * bl, W, +1);
+  for (int t = threadIdx.x; t < 3 * bl * g.nx; t += blockDim.x) {
+    const int q = t / (bl * g.nx), r = t - q * (bl * g.nx);
+    const int b = r % bl, i = r / bl;
+    if (kz0 + b < g.Mz) grid[(int64_t)q * g.G + i * sx + off + b] = res[q * per + b * ls + i];
+  }
+}
+
+// K5: inverse FFT of z-line (i, j) of component q, then for occupied sites
+// y = x / alpha - (G * x) (conjugated in and out for A^H).
+template <class R, int N, int BL>
+__global__ void __launch_bounds__(kBlock) dip_inv_z(const cx<R>* __restrict__ x, cx<R>* __restrict__ y,
+                                                    cx<R>* __restrict__ grid, const int* __restrict__ idx, DipGeom g,
+                                                    int bl_rt, const cx<R>* __restrict__ W, cx<R> alpha_inv, int conj,
+                                                    const SolveState* __restrict__ st) {
+  if (skip_state(st)) return;
+  extern __shared__ unsigned char smem_raw[];
+  const int Mz = N > 0 ? N : g.Mz;
+  const int ls = N > 0 ? fft_ls<N>() : g.Mz;
+  const int bl = BL > 0 ? BL : bl_rt;
+  cx<R>* buf0 = reinterpret_cast<cx<R>*>(smem_raw);
+  cx<R>* buf1 = buf0 + bl * ls;
+  const int q = blockIdx.y;
+  const int64_t nlines = (int64_t)g.nx * g.ny;
+  const int64_t l0 = (int64_t)blockIdx.x * bl;
+  const cx<R>* gq = grid + (int64_t)q * g.G;
+  for (int t = threadIdx.x; t < bl * Mz; t += blockDim.x) {
+    const int b = t / Mz, kz = t - b * Mz;
+    const int64_t line = l0 + b;
+    cx<R> v = mk<R>(0, 0);
+    if (line < nlines) {
+      const int64_t i = line / g.ny, j = line - i * g.ny;
+      v = gq[(i * g.My + j) * Mz + kz];
+    }
+    buf0[b * ls + kz] = v;
+  }
+  __syncthreads();
+  const cx<R>* res = fft_lines<R, N, BL>(buf0, buf1, Mz, bl, W, +1);
+  const cx<R>* xq = x + (int64_t)q * g.N;
+  cx<R>* yq = y + (int64_t)q * g.N;
+  for (int t = threadIdx.x; t < bl * g.nz; t += blockDim.x) {
+    const int b = t / g.nz, l = t - b * g.nz;
+    const int64_t line = l0 + b;
+    if (line < nlines) {
+      const int s = __ldg(&idx[line * g.nz + l]);
+      if (s >= 0) {
+        cx<R> xi = xq[s];
+        if (conj) xi = cconj(xi);
+        cx<R> v = csub(cmul(alpha_inv, xi), res[b * ls + l]);
+        if (conj) v = cconj(v);
+        yq[s] = v;
+      }
+    }
+  }
+}
+
+// One-time setup: the circulant-embedded field tensor on the grid (double).
+__global__ void dip_green(double2* __restrict__ g6, DipGeom g, double k) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < g.G; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = p / ((int64_t)g.My * g.Mz);
+    const int64_t rem = p - a * (int64_t)g.My * g.Mz;
+    const int64_t b = rem / g.Mz, c = rem - b * g.Mz;
+    double2 out[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) out[q] = make_double2(0.0, 0.0);
+    const bool excluded = a == g.nx || b == g.ny || c == g.nz || (a == 0 && b == 0 && c == 0);
+    if (!excluded) {
+      const double dx = a < g.nx ? (double)a : (double)(a - g.Mx);
+      const double dy = b < g.ny ? (double)b : (double)(b - g.My);
+      const double dz = c < g.nz ? (double)c : (double)(c - g.Mz);
+      const double r = sqrt(dx * dx + dy * dy + dz * dz);
+      const double u[3] = {dx / r, dy / r, dz / r};
+      double sn, cs;
+      sincos(k * r, &sn, &cs);
+      const double r3 = r * r * r;
+      const double2 e = make_double2(cs / r3, sn / r3);   // exp(ikr)/r^3
+      const double kr2 = (k * r) * (k * r);               // multiplies (I - u u^T)
+      const double2 bb = make_double2(1.0, -k * r);       // 1 - ikr, multiplies (3 u u^T - I)
+      const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        const double uu = u[ia[q]] * u[ib[q]];
+        const double d = ia[q] == ib[q] ? 1.0 : 0.0;
+        const double2 inner = make_double2(kr2 * (d - uu) + bb.x * (3.0 * uu - d), bb.y * (3.0 * uu - d));
+        out[q] = cmul(e, inner);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q) g6[(int64_t)q * g.G + p] = out[q];
+  }
+}
+
+template <class R>
+__global__ void dip_convert(const double2* __restrict__ src, cx<R>* __restrict__ dst, int64_t count, double scale) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < count; p += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = src[p];
+    dst[p] = mk<R>((R)(v.x * scale), (R)(v.y * scale));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+#define DIP_CUDA(call)                                                                 \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+      return CCG_ERR_CUDA;                                                             \
+    }                                                                                  \
+  } while (0)
+
+static bool fft_size_ok(int n) {
+  if (n < 2 || n > kFftMaxN) return false;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  return n == 1;
+}
+
+// Lines per block of a pass: 16 for complex64, 8 for complex128 (8 for the
+// three-component x pass of complex128 too, keeping shared memory <= 96 KB
+// at M = 128).
+template <class R> static int lines_per_block(int M) {
+  int bl = sizeof(R) == 4 ? 16 : 8;
+  while (bl > 1 && (size_t)3 * 2 * bl * M * sizeof(cx<R>) > 200 * 1024) bl /= 2;
+  return bl;
+}
+
+template <class R> static int set_smem(const void* fn, size_t bytes) {
+  if (bytes > 48 * 1024) DIP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return CCG_OK;
+}
+
+template <class R> static std::vector<cx<R>> twiddles(int n) {
+  std::vector<cx<R>> w(n);
+  for (int t = 0; t < n; ++t) {
+    const std::complex<double> z = std::polar(1.0, -2.0 * M_PI * (double)t / (double)n);
+    w[t] = mk<R>((R)z.real(), (R)z.imag());
+  }
+  return w;
+}
+
+// Per-operator device data, owned through ccg_operator::dip.
+template <class R> static int upload_twiddles(ccg_operator* op, const DipGeom& g) {
+  const int dims[3] = {g.Mx, g.My, g.Mz};
+  for (int a = 0; a < 3; ++a) {
+    std::vector<cx<R>> w = twiddles<R>(dims[a]);
+    DIP_CUDA(cudaMalloc(&op->dip.tw[a], w.size() * sizeof(cx<R>)));
+    DIP_CUDA(cudaMemcpy(op->dip.tw[a], w.data(), w.size() * sizeof(cx<R>), cudaMemcpyHostToDevice));
+  }
+  return CCG_OK;
+}
+
+static int strided_launch_d(double2* data, const StridedPass& p, int ncomp, const double2* W, int sign,
+                            cudaStream_t s) {
+  const int cblocks = (p.nc + p.bl - 1) / p.bl;
+  const size_t smem = (size_t)2 * p.bl * p.n * sizeof(double2);
+  if (set_smem<double>((const void*)fft_strided<double, 0, 0>, smem) != CCG_OK) return CCG_ERR_CUDA;
+  fft_strided<double, 0, 0><<<dim3(p.na * cblocks, ncomp), kBlock, smem, s>>>(data, p, W, sign, nullptr);
+  return CCG_OK;
+}
+
+// Field tensor on the grid, forward-transformed, scaled and rounded to R.
+template <class R> static int build_ghat(ccg_operator* op, const DipGeom& g, cudaStream_t s) {
+  double2* g6 = nullptr;
+  void* twd[3] = {nullptr, nullptr, nullptr};
+  int rc = CCG_OK;
+  const int dims[3] = {g.Mx, g.My, g.Mz};
+  if (cudaMalloc(&g6, (size_t)6 * g.G * sizeof(double2)) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("ccg_op_dipole: field-tensor setup allocation failed");
+    return CCG_ERR_NOMEM;
+  }
+  for (int a = 0; a < 3 && rc == CCG_OK; ++a) {
+    std::vector<double2> w = twiddles<double>(dims[a]);
+    if (cudaMalloc(&twd[a], w.size() * sizeof(double2)) != cudaSuccess ||
+        cudaMemcpy(twd[a], w.data(), w.size() * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess) {
+      set_error(std::string("ccg_op_dipole: ") + cudaGetErrorString(cudaGetLastError()));
+      rc = CCG_ERR_CUDA;
+    }
+  }
+  if (rc == CCG_OK) {
+    const int grid = (int)std::min<int64_t>((g.G + kBlock - 1) / kBlock, 4096);
+    dip_green<<<grid, kBlock, 0, s>>>(g6, g, op->dip.kd);
+    // z (contiguous lines), then y and x (strided)
+    const int blz = 8;
+    const size_t smz = (size_t)2 * blz * g.Mz * sizeof(double2);
+    if (set_smem<double>((const void*)fft_contig<double>, smz) != CCG_OK) rc = CCG_ERR_CUDA;
+    const int nlz = g.Mx * g.My;
+    if (rc == CCG_OK)
+      fft_contig<double><<<dim3((nlz + blz - 1) / blz, 6), kBlock, smz, s>>>(g6, g.G, g.Mz, nlz, g.Mz, blz,
+                                                                             (const double2*)twd[2], -1);
+    StridedPass py = {g.G, (int64_t)g.My * g.Mz, g.Mz, g.Mx, g.Mz, g.My, g.My, g.My, 8};
+    if (rc == CCG_OK) rc = strided_launch_d(g6, py, 6, (const double2*)twd[1], -1, s);
+    StridedPass px = {g.G, g.Mz, (int64_t)g.My * g.Mz, g.My, g.Mz, g.Mx, g.Mx, g.Mx, 8};
+    if (rc == CCG_OK) rc = strided_launch_d(g6, px, 6, (const double2*)twd[0], -1, s);
+    if (rc == CCG_OK) {
+      if (cudaMalloc(&op->dip.ghat, (size_t)6 * g.G * sizeof(cx<R>)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("ccg_op_dipole: field-tensor allocation failed");
+        rc = CCG_ERR_NOMEM;
+      } else {
+        dip_convert<R><<<4096, kBlock, 0, s>>>(g6, static_cast<cx<R>*>(op->dip.ghat), 6 * g.G, 1.0 / (double)g.G);
+      }
+    }
+    if (rc == CCG_OK && cudaStreamSynchronize(s) != cudaSuccess) {
+      set_error(std::string("ccg_op_dipole: setup failed: ") + cudaGetErrorString(cudaGetLastError()));
+      rc = CCG_ERR_CUDA;
+    }
+  }
+  cudaFree(g6);
+  for (int a = 0; a < 3; ++a)
+    if (twd[a]) cudaFree(twd[a]);
+  return rc;
+}
+
+template <class R> static int create_t(ccg_operator* op, const uint8_t* occ, cudaStream_t s) {
+  const DipGeom g = geom(op);
+  // site index grid: idx[(i*ny + j)*nz + l] = site number or -1
+  const int64_t cells = (int64_t)g.nx * g.ny * g.nz;
+  std::vector<int> idx(cells);
+  int64_t count = 0;
+  for (int64_t c = 0; c < cells; ++c) idx[c] = occ[c] ? (int)(count++) : -1;
+  op->dip.nsites = count;
+  op->n = 3 * count;
+  DIP_CUDA(cudaMalloc(&op->dip.idx, cells * sizeof(int)));
+  DIP_CUDA(cudaMemcpy(op->dip.idx, idx.data(), cells * sizeof(int), cudaMemcpyHostToDevice));
+  DIP_CUDA(cudaMalloc(&op->dip.work, (size_t)3 * g.G * sizeof(cx<R>)));
+  int rc = upload_twiddles<R>(op, geom(op));
+  if (rc != CCG_OK) return rc;
+  rc = build_ghat<R>(op, geom(op), s);
+  if (rc != CCG_OK) return rc;
+  const int bl = lines_per_block<R>(std::max(g.Mx, std::max(g.My, g.Mz)));
+  op->dip.bl = bl;
+  // opt in to large dynamic shared memory for the runtime-size kernels
+  const int M = std::max(g.Mx, std::max(g.My, g.Mz));
+  const size_t sm1 = (size_t)2 * bl * M * sizeof(cx<R>), sm3 = 3 * sm1;
+  if (set_smem<R>((const void*)dip_fwd_z<R, 0, 0>, sm1) != CCG_OK) return CCG_ERR_CUDA;
+  if (set_smem<R>((const void*)dip_inv_z<R, 0, 0>, sm1) != CCG_OK) return CCG_ERR_CUDA;
+  if (set_smem<R>((const void*)fft_strided<R, 0, 0>, sm1) != CCG_OK) return CCG_ERR_CUDA;
+  if (set_smem<R>((const void*)dip_x_mul<R, 0, 0>, sm3) != CCG_OK) return CCG_ERR_CUDA;
+  // algorithmic bytes of one application (each pass reads and writes its
+  // pruned region once; the field tensor is read once)
+  const double e = sizeof(cx<R>);
+  const double zl = 3.0 * g.nx * g.ny * g.Mz * e;     // z-line region
+  const double yl = 3.0 * g.nx * g.My * g.Mz * e;     // after the y pass
+  const double vec = 3.0 * count * e;
+  op->dip.sweep_bytes = (vec + zl) + (zl + yl) + (yl + 6.0 * g.G * e + yl) + (yl + zl) + (zl + 2 * vec) +
+                        2.0 * cells * 4.0;
+  return CCG_OK;
+}
+
+int dipole_create(ccg_operator* op, const uint8_t* occ, cudaStream_t s) {
+  const DipGeom g = geom(op);
+  if (!fft_size_ok(g.Mx) || !fft_size_ok(g.My) || !fft_size_ok(g.Mz)) {
+    set_error("ccg_op_dipole: each of 2*nx, 2*ny, 2*nz must be 2^a 3^b and at most 256");
+    return CCG_ERR_INVALID;
+  }
+  return op->dtype == CCG_C128 ? create_t<double>(op, occ, s) : create_t<float>(op, occ, s);
+}
+
+void dipole_free(ccg_operator* op) {
+  if (op->dip.idx) cudaFree(op->dip.idx);
+  if (op->dip.work) cudaFree(op->dip.work);
+  if (op->dip.ghat) cudaFree(op->dip.ghat);
+  for (int a = 0; a < 3; ++a)
+    if (op->dip.tw[a]) cudaFree(op->dip.tw[a]);
+  op->dip.idx = nullptr;
+  op->dip.work = op->dip.ghat = nullptr;
+}
+
+// Lines per block of each pass for FFT length N: z-lines (K1, K5) about
+// 1024 points per block; strided y passes 16 (complex64) / 8 (complex128)
+// consecutive lines; the three-component x pass 8 / 4.  At N = 128 each
+// keeps shared memory at or below 48 KB.
+template <class R, int N> constexpr int bl_z() { return N >= 1024 ? 1 : 1024 / N; }
+template <class R> constexpr int bl_y() { return sizeof(R) == 4 ? 16 : 8; }
+template <class R> constexpr int bl_x() { return sizeof(R) == 4 ? 8 : 4; }
+
+template <class F> static void smem_opt_in(F* fn, size_t bytes, bool& done) {
+  if (!done && bytes > 48 * 1024) cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  done = true;
+}
+
+template <class R, int N>
+static void k1(const cx<R>* x, cx<R>* grid, const ccg_operator* op, const DipGeom& g, const cx<R>* W, int conj,
+               const SolveState* st, cudaStream_t s) {
+  constexpr int BL = N > 0 ? bl_z<R, N>() : 0;
+  const int bl = N > 0 ? BL : op->dip.bl;
+  const int64_t nlines = (int64_t)g.nx * g.ny;
+  const size_t sm = (size_t)2 * bl * (N > 0 ? fft_ls<N>() : g.Mz) * sizeof(cx<R>);
+  static bool opted = false;
+  smem_opt_in(dip_fwd_z<R, N, BL>, sm, opted);
+  dip_fwd_z<R, N, BL><<<dim3((unsigned)((nlines + bl - 1) / bl), 3), kBlock, sm, s>>>(x, grid, op->dip.idx, g, bl, W,
+                                                                                      conj, st);
+}
+template <class R, int N>
+static void k5(const cx<R>* x, cx<R>* y, cx<R>* grid, const ccg_operator* op, const DipGeom& g, const cx<R>* W,
+               cx<R> ainv, int conj, const SolveState* st, cudaStream_t s) {
+  constexpr int BL = N > 0 ? bl_z<R, N>() : 0;
+  const int bl = N > 0 ? BL : op->dip.bl;
+  const int64_t nlines = (int64_t)g.nx * g.ny;
+  const size_t sm = (size_t)2 * bl * (N > 0 ? fft_ls<N>() : g.Mz) * sizeof(cx<R>);
+  static bool opted = false;
+  smem_opt_in(dip_inv_z<R, N, BL>, sm, opted);
+  dip_inv_z<R, N, BL><<<dim3((unsigned)((nlines + bl - 1) / bl), 3), kBlock, sm, s>>>(x, y, grid, op->dip.idx, g, bl,
+                                                                                      W, ainv, conj, st);
+}
+template <class R, int N>
+static void ky(cx<R>* grid, const ccg_operator* op, const DipGeom& g, const cx<R>* W, int sign,
+               const SolveState* st, cudaStream_t s) {
+  constexpr int BL = N > 0 ? bl_y<R>() : 0;
+  const int bl = N > 0 ? BL : op->dip.bl;
+  StridedPass p = {g.G, (int64_t)g.My * g.Mz, g.Mz, g.nx, g.Mz, g.My, sign < 0 ? g.ny : g.My,
+                   sign < 0 ? g.My : g.ny, bl};
+  const int cb = (g.Mz + bl - 1) / bl;
+  const size_t sm = (size_t)2 * bl * (N > 0 ? fft_ls<N>() : g.My) * sizeof(cx<R>);
+  static bool opted = false;
+  smem_opt_in(fft_strided<R, N, BL>, sm, opted);
+  fft_strided<R, N, BL><<<dim3(g.nx * cb, 3), kBlock, sm, s>>>(grid, p, W, sign, st);
+}
+template <class R, int N>
+static void k3(cx<R>* grid, const ccg_operator* op, const DipGeom& g, const cx<R>* W, const SolveState* st,
+               cudaStream_t s) {
+  constexpr int BL = N > 0 ? bl_x<R>() : 0;
+  const int bl = N > 0 ? BL : op->dip.bl;
+  const int cb = (g.Mz + bl - 1) / bl;
+  const size_t sm = (size_t)3 * 2 * bl * (N > 0 ? fft_ls<N>() : g.Mx) * sizeof(cx<R>);
+  static bool opted = false;
+  smem_opt_in(dip_x_mul<R, N, BL>, sm, opted);
+  dip_x_mul<R, N, BL><<<g.My * cb, kBlock, sm, s>>>(grid, static_cast<const cx<R>*>(op->dip.ghat), g, bl, W, st);
+}
+
+// FFT lengths with compile-time kernels; other 2^a 3^b lengths use the
+// runtime kernels.
+#define CCG_FFT_SIZES(X) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256)
+
+template <class R>
+static int apply_t(const ccg_operator* op, const cx<R>* x, cx<R>* y, bool conj, const SolveState* st, cudaStream_t s) {
+  const DipGeom g = geom(op);
+  cx<R>* grid = static_cast<cx<R>*>(op->dip.work);
+  const cx<R>* Wx = static_cast<const cx<R>*>(op->dip.tw[0]);
+  const cx<R>* Wy = static_cast<const cx<R>*>(op->dip.tw[1]);
+  const cx<R>* Wz = static_cast<const cx<R>*>(op->dip.tw[2]);
+  const int cj = conj ? 1 : 0;
+  const cx<R> ainv = mk<R>((R)op->dip.alpha_inv[0], (R)op->dip.alpha_inv[1]);
+#define CCG_CASE_K1(n) case n: k1<R, n>(x, grid, op, g, Wz, cj, st, s); break;
+  switch (g.Mz) { CCG_FFT_SIZES(CCG_CASE_K1) default: k1<R, 0>(x, grid, op, g, Wz, cj, st, s); }
+#define CCG_CASE_KY(n) case n: ky<R, n>(grid, op, g, Wy, sign, st, s); break;
+  for (int sign = -1; sign <= 1; sign += 2) {
+    if (sign > 0) {
+#define CCG_CASE_K3(n) case n: k3<R, n>(grid, op, g, Wx, st, s); break;
+      switch (g.Mx) { CCG_FFT_SIZES(CCG_CASE_K3) default: k3<R, 0>(grid, op, g, Wx, st, s); }
+    }
+    switch (g.My) { CCG_FFT_SIZES(CCG_CASE_KY) default: ky<R, 0>(grid, op, g, Wy, sign, st, s); }
+  }
+#define CCG_CASE_K5(n) case n: k5<R, n>(x, y, grid, op, g, Wz, ainv, cj, st, s); break;
+  switch (g.Mz) { CCG_FFT_SIZES(CCG_CASE_K5) default: k5<R, 0>(x, y, grid, op, g, Wz, ainv, cj, st, s); }
+  return cudaGetLastError() == cudaSuccess ? CCG_OK : CCG_ERR_CUDA;
+}
+
+int dipole_apply(const ccg_operator* op, const double2* x, double2* y, bool conj, const SolveState* st,
+                 cudaStream_t s) {
+  return apply_t<double>(op, x, y, conj, st, s);
+}
+int dipole_apply(const ccg_operator* op, const float2* x, float2* y, bool conj, const SolveState* st,
+                 cudaStream_t s) {
+  return apply_t<float>(op, x, y, conj, st, s);
+}
+
+}  // namespace ccg

@@ -14,7 +14,21 @@ struct SolveState;
 void set_error(const std::string& msg);
 }  // namespace ccg
 
-enum { CCG_OPK_DENSE = 0 };
+enum { CCG_OPK_DENSE = 0, CCG_OPK_DIPOLE = 1 };
+
+// Device data of a discrete-dipole operator (owned by the operator).
+struct DipoleData {
+  int nx = 0, ny = 0, nz = 0;   // lattice box
+  int64_t nsites = 0;           // occupied sites N; unknowns 3N
+  double kd = 0.0;              // wavenumber times lattice spacing
+  double alpha_inv[2] = {0.0, 0.0};
+  int* idx = nullptr;           // site number of each lattice cell, or -1
+  void* work = nullptr;         // 3 FFT grids
+  void* ghat = nullptr;         // 6 transformed field-tensor components
+  void* tw[3] = {nullptr, nullptr, nullptr};  // twiddle tables along x, y, z
+  int bl = 8;                   // lines per block of the FFT passes
+  double sweep_bytes = 0.0;     // algorithmic bytes of one application
+};
 
 struct ccg_operator {
   int kind = CCG_OPK_DENSE;
@@ -25,6 +39,8 @@ struct ccg_operator {
   const void* A = nullptr;
   int64_t lda = 0;
   int unit = 1;  // complex numbers per 16-byte load (2 only for aligned complex64 with even n, lda)
+  // dipole
+  DipoleData dip;
 };
 
 struct ccg_handle {
@@ -66,6 +82,14 @@ int solve_dense(ccg_handle* h, int method, const ccg_operator* op, const void* y
 int solve_refined(ccg_handle* h, int method, const ccg_operator* op, const ccg_operator* op_in, const void* y,
                   void* x, double tol, int max_outer, double inner_tol, int inner_maxit, double* res_hist,
                   int* inner_iters, ccg_info* info);
+int dipole_create(ccg_operator* op, const uint8_t* occ, cudaStream_t s);
+void dipole_free(ccg_operator* op);
+// y = A x (conj = false) or A^H x (conj = true), enqueued on s; kernels skip
+// when st says the solve has stopped (st may be null).
+int dipole_apply(const ccg_operator* op, const double2* x, double2* y, bool conj, const SolveState* st,
+                 cudaStream_t s);
+int dipole_apply(const ccg_operator* op, const float2* x, float2* y, bool conj, const SolveState* st,
+                 cudaStream_t s);
 int matvec_dense(ccg_handle* h, const ccg_operator* op, int trans, const void* x, void* y);
 int dot_device(ccg_handle* h, ccg_dtype dtype, int64_t n, const void* u, const void* v, int conj, double* out2);
 

@@ -649,10 +649,14 @@ template <class R> struct Dense {
     ns = std::max<int64_t>(1, std::min<int64_t>(ns, std::min<int64_t>(32, (n + kWarps - 1) / kWarps)));
     rows_per_range = (n + ns - 1) / ns;
     nsplit = (int)((n + rows_per_range - 1) / rows_per_range);
+    dense = op->kind == CCG_OPK_DENSE;
+    dip_bytes = op->dip.sweep_bytes;
   }
-  size_t p1_elems() const { return (size_t)ncb * n; }
-  size_t p2_elems() const { return (size_t)nsplit * n; }
-  double sweep_bytes() const { return (double)n * (double)n * sizeof(cx<R>); }
+  bool dense = true;
+  double dip_bytes = 0.0;
+  size_t p1_elems() const { return dense ? (size_t)ncb * n : 0; }
+  size_t p2_elems() const { return dense ? (size_t)nsplit * n : 0; }
+  double sweep_bytes() const { return dense ? (double)n * (double)n * sizeof(cx<R>) : dip_bytes; }
 };
 
 template <class R> struct Ws {
@@ -701,14 +705,16 @@ template <class R> static Ws<R> ws_carve(char* base, int64_t n, const Dense<R>& 
 
 template <class R> struct Runner {
   ccg_handle* h;
+  const ccg_operator* op;
   cudaStream_t s;
   Dense<R> d;
   Ws<R> w;
   Red red;
   int grid_vec;
+  static constexpr int kDt = sizeof(R) == 8 ? CCG_C128 : CCG_C64;
 
-  Runner(ccg_handle* h_, const ccg_operator* op, const Ws<R>& w_)
-      : h(h_), s(h_->stream), d(op, h_->num_sms), w(w_) {
+  Runner(ccg_handle* h_, const ccg_operator* op_, const Ws<R>& w_)
+      : h(h_), op(op_), s(h_->stream), d(op_, h_->num_sms), w(w_) {
     red.partials = w.partials;
     red.counter = w.counter;
     grid_vec = (int)std::min<int64_t>((d.n + kBlock - 1) / kBlock, (int64_t)h->num_sms * 8);
@@ -725,20 +731,31 @@ template <class R> struct Runner {
   // y = A x
   MvOut<R> apply_n(const cx<R>* x, cx<R>* y, const SolveState* st) {
     timing_begin(h);
-    if constexpr (sizeof(R) == 4) {
-      if (d.unit == 2) gemv_n_rows<R, 2><<<d.grid_rows, kBlock, 0, s>>>(d.A, d.lda, d.n, x, y, st);
-      else gemv_n_rows<R, 1><<<d.grid_rows, kBlock, 0, s>>>(d.A, d.lda, d.n, x, y, st);
+    if (op->kind == CCG_OPK_DIPOLE) {
+      dipole_apply(op, x, y, false, st, s);
+      h->launches += 5;
     } else {
-      gemv_n_rows<R, 1><<<d.grid_rows, kBlock, 0, s>>>(d.A, d.lda, d.n, x, y, st);
+      if constexpr (sizeof(R) == 4) {
+        if (d.unit == 2) gemv_n_rows<R, 2><<<d.grid_rows, kBlock, 0, s>>>(d.A, d.lda, d.n, x, y, st);
+        else gemv_n_rows<R, 1><<<d.grid_rows, kBlock, 0, s>>>(d.A, d.lda, d.n, x, y, st);
+      } else {
+        gemv_n_rows<R, 1><<<d.grid_rows, kBlock, 0, s>>>(d.A, d.lda, d.n, x, y, st);
+      }
+      ++h->launches;
     }
-    timing_end(h, sizeof(R) == 8 ? CCG_C128 : CCG_C64, CCG_SWEEP_N, d.sweep_bytes());
-    ++h->launches;
+    timing_end(h, kDt, CCG_SWEEP_N, d.sweep_bytes());
     return plain(y);
   }
-  // A^H x as nsplit partial vectors in P2
-  MvOut<R> apply_c(const cx<R>* x, const SolveState* st) {
-    dim3 grid(d.ncb, d.nsplit);
+  // A^H x: dense operators leave nsplit partial vectors in P2; others write y.
+  MvOut<R> apply_c(const cx<R>* x, cx<R>* y, const SolveState* st) {
     timing_begin(h);
+    if (op->kind == CCG_OPK_DIPOLE) {
+      dipole_apply(op, x, y, true, st, s);
+      h->launches += 5;
+      timing_end(h, kDt, CCG_SWEEP_C, d.sweep_bytes());
+      return plain(y);
+    }
+    dim3 grid(d.ncb, d.nsplit);
     if constexpr (sizeof(R) == 4) {
       if (d.unit == 2)
         gemv_tile<R, 2, Dense<R>::E, false, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, nullptr, x, nullptr, w.P2, st);
@@ -747,13 +764,20 @@ template <class R> struct Runner {
     } else {
       gemv_tile<R, 1, Dense<R>::E, false, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, nullptr, x, nullptr, w.P2, st);
     }
-    timing_end(h, sizeof(R) == 8 ? CCG_C128 : CCG_C64, CCG_SWEEP_C, d.sweep_bytes());
     ++h->launches;
+    timing_end(h, kDt, CCG_SWEEP_C, d.sweep_bytes());
     MvOut<R> m; m.y = nullptr; m.P = w.P2; m.ld = d.n; m.nparts = d.nsplit;
     return m;
   }
-  // A x1 (ncb partials in P1) and A^H x2 (nsplit partials in P2) from one sweep
-  void apply_both(const cx<R>* x1, const cx<R>* x2, MvOut<R>& o1, MvOut<R>& o2, const SolveState* st) {
+  // A x1 and A^H x2: dense operators from one sweep (ncb partials in P1,
+  // nsplit in P2); others by two applications into y1, y2.
+  void apply_both(const cx<R>* x1, const cx<R>* x2, cx<R>* y1, cx<R>* y2, MvOut<R>& o1, MvOut<R>& o2,
+                  const SolveState* st) {
+    if (op->kind == CCG_OPK_DIPOLE) {
+      o1 = apply_n(x1, y1, st);
+      o2 = apply_c(x2, y2, st);
+      return;
+    }
     dim3 grid(d.ncb, d.nsplit);
     timing_begin(h);
     if constexpr (sizeof(R) == 4) {
@@ -764,8 +788,8 @@ template <class R> struct Runner {
     } else {
       gemv_tile<R, 1, Dense<R>::E, true, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, x1, x2, w.P1, w.P2, st);
     }
-    timing_end(h, sizeof(R) == 8 ? CCG_C128 : CCG_C64, CCG_SWEEP_BOTH, d.sweep_bytes());
     ++h->launches;
+    timing_end(h, kDt, CCG_SWEEP_BOTH, d.sweep_bytes());
     o1.y = nullptr; o1.P = w.P1; o1.ld = d.n; o1.nparts = d.ncb;
     o2.y = nullptr; o2.P = w.P2; o2.ld = d.n; o2.nparts = d.nsplit;
   }
@@ -843,11 +867,11 @@ static int solve_core(ccg_handle* h, int method, const ccg_operator* op, const W
     };
   } else if (method == M_CGNR) {
     cx<R>*r = V[0], *z = V[1], *pv = V[2], *wv = V[3];
-    CgZ<R> z0; z0.n = n; z0.z = z; z0.p = pv; z0.mv = run.apply_c(r, st); run.phase(z0);
+    CgZ<R> z0; z0.n = n; z0.z = z; z0.p = pv; z0.mv = run.apply_c(r, z, st); run.phase(z0);
     step = [=, &run]() {
       CgAlpha<R> a; a.n = n; a.w = wv; a.mv = run.apply_n(pv, wv, st); run.phase(a);
       CgXR<R> b; b.n = n; b.x = x; b.r = r; b.p = pv; b.w = wv; run.phase(b);
-      CgZ<R> c; c.n = n; c.z = z; c.p = nullptr; c.mv = run.apply_c(r, st); run.phase(c);
+      CgZ<R> c; c.n = n; c.z = z; c.p = nullptr; c.mv = run.apply_c(r, z, st); run.phase(c);
       CgP<R> e; e.n = n; e.z = z; e.p = pv; run.phase(e);
     };
   } else if (method == M_QMR) {
@@ -856,7 +880,7 @@ static int solve_core(ccg_handle* h, int method, const ccg_operator* op, const W
     QVW<R> f; f.n = n; f.vt = vt; f.wt = wt; f.v = v; f.w = wv; run.phase(f);
     step = [=, &run]() {
       QPQ<R> a; a.n = n; a.v = v; a.w = wv; a.p = pv; a.q = q; run.phase(a);
-      QEps<R> b; b.n = n; b.pt = pt; b.u = u; b.q = q; run.apply_both(pv, q, b.mv1, b.mv2, st); run.phase(b);
+      QEps<R> b; b.n = n; b.pt = pt; b.u = u; b.q = q; run.apply_both(pv, q, pt, u, b.mv1, b.mv2, st); run.phase(b);
       QVT<R> c; c.n = n; c.pt = pt; c.u = u; c.v = v; c.w = wv; c.vt = vt; c.wt = wt; run.phase(c);
       QDX<R> e; e.n = n; e.p = pv; e.pt = pt; e.d = dv; e.s = sv; e.x = x; e.r = r; e.vt = vt; e.wt = wt; e.v = v;
       e.w = wv; run.phase(e);
@@ -1120,11 +1144,14 @@ template <class R> static int matvec_t(ccg_handle* h, const ccg_operator* op, in
   if (!trans) {
     run.apply_n(x, y, nullptr);
   } else {
-    SumParts<R> p;
-    p.n = op->n;
-    p.y = y;
-    p.mv = run.apply_c(x, nullptr);
-    run.phase(p);
+    MvOut<R> mv = run.apply_c(x, y, nullptr);
+    if (mv.P != nullptr) {
+      SumParts<R> p;
+      p.n = op->n;
+      p.y = y;
+      p.mv = mv;
+      run.phase(p);
+    }
   }
   CCG_CUDA(cudaGetLastError());
   return CCG_OK;
