@@ -44,7 +44,8 @@ def parse_args(argv=None):
     p.add_argument("--steps", type=int, default=None)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ccg", "reference"], default="ccg")
-    p.add_argument("--workload", choices=["dense", "dipole"], default="dense")
+    p.add_argument("--workload", choices=["dense", "dipole", "batched"], default="dense")
+    p.add_argument("--nrhs", type=int, default=256)
     p.add_argument("--n", type=int, default=8192)
     p.add_argument("--L", type=int, default=64)
     p.add_argument("--methods", default=None)
@@ -57,7 +58,7 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     a = p.parse_args(argv)
-    dense = a.workload == "dense"
+    dense = a.workload != "dipole"
     if a.methods is None:
         a.methods = "bicgstab,cgnr,qmr" if dense else "cocg,bicgstab"
     if a.tol is None:
@@ -65,7 +66,9 @@ def parse_args(argv=None):
     if a.inner_tol is None:
         a.inner_tol = 1e-5 if dense else 1e-4
     if a.steps is None:
-        a.steps = 30 if dense else 3
+        a.steps = 30 if a.workload == "dense" else 3
+    if a.workload == "batched" and a.methods == "bicgstab,cgnr,qmr":
+        a.methods = "bicgstab"
     if a.inner_maxit is None:
         a.inner_maxit = 200 if dense else 2000
     return a
@@ -191,12 +194,13 @@ def profiled_traffic(kernel, src_files):
     return None
 
 
-SWEEP_KERNELS = {0: ("gemv_n_rows", 1), 1: ("gemv_tile_c", 1), 2: ("gemv_tile_both", 2)}
+SWEEP_KERNELS = {0: ("gemv_n_rows", 1), 1: ("gemv_tile_c", 1), 2: ("gemv_tile_both", 2), 3: ("cgemm_rows", 1)}
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flops x max SM clock
 DIPOLE_KERNELS = {0: ("dipole_fft_matvec", 1), 1: ("dipole_fft_matvec_h", 1), 2: ("dipole_fft_both", 2)}
 KERNEL_SOURCES = ["paper_1208_4869_gb300/csrc/gemv.cuh", "paper_1208_4869_gb300/csrc/common.cuh"]
 
 
-def roofline(ccg, sweep_stats, n, dipole=False):
+def roofline(ccg, sweep_stats, n, dipole=False, nrhs=1):
     """Roofline of the sweep (precision, kind) that took the most device time
     in the timed region: algorithmic flops (8 n^2 per complex product; the
     fused QMR sweep forms two) and bytes (the matrix, read once per sweep)
@@ -207,8 +211,9 @@ def roofline(ccg, sweep_stats, n, dipole=False):
             name, products = (DIPOLE_KERNELS if dipole else SWEEP_KERNELS)[kind]
             tag = "%s_%s" % (name, "c128" if dt == ccg.C128 else "c64")
             avg = ms / cnt
+            cols = nrhs if kind == 3 else 1
             kinds[tag] = {"launches": cnt, "total_ms": ms, "avg_ms": avg,
-                          "tflops": None if dipole else 8.0 * products * n * n / (avg * 1e-3) / 1e12,
+                          "tflops": None if dipole else 8.0 * products * n * n * cols / (avg * 1e-3) / 1e12,
                           "gbs": nbytes / (avg * 1e-3) / 1e9, "bytes": nbytes}
     if not kinds:
         return None
@@ -220,6 +225,10 @@ def roofline(ccg, sweep_stats, n, dipole=False):
         roof = {"kernel": top, "bound": "alu", "achieved": k["tflops"], "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": k["tflops"] / FP64_PEAK_TFLOPS,
                 "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (no measured FP64 peak)"}
+    elif top.startswith("cgemm_rows"):        # complex64 block product on the FP32 pipe
+        roof = {"kernel": top, "bound": "alu", "achieved": k["tflops"], "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": k["tflops"] / FP32_PEAK_TFLOPS,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
     else:                      # HBM bound (complex64 sweeps; the FFT operator)
         roof = {"kernel": top, "bound": "hbm", "achieved": k["gbs"], "peak": hbm,
                 "unit": "GB/s", "frac": k["gbs"] / hbm, "peak_source": "%s copy bandwidth" % hbm_src}
@@ -307,7 +316,7 @@ def timed_region(h, ccg, torch, stream, step, steps, world, dev, clocks=None):
     clk = clocks.stop() if clocks else None
     barrier(world)
     stats = {(dt, k): h.timing(kind=k, dtype=dt) for dt in (ccg.C128, ccg.C64)
-             for k in (ccg.SWEEP_N, ccg.SWEEP_C, ccg.SWEEP_BOTH)}
+             for k in (ccg.SWEEP_N, ccg.SWEEP_C, ccg.SWEEP_BOTH, ccg.SWEEP_BLOCK)}
     h.timing(enable=False)
     return e0.elapsed_time(e1), lat, results, stats, h.launch_count() - launches0, clk
 
@@ -343,6 +352,17 @@ def run_ours(args):
                     % (args.L, op64.nsites, "/".join(methods), args.tol))
         l2 = "inputs larger than L2 (field tensor %.0f MB complex64 + %.0f MB complex128)" % (
             6 * (2 * args.L) ** 3 * 8 / 1e6, 6 * (2 * args.L) ** 3 * 16 / 1e6)
+    elif args.workload == "batched":
+        n = args.n
+        A, _ = W.dense_system(n, 3.0, 0)
+        y = W.dense_rhs_block(n, args.nrhs, seed=1)          # (n, k) column-major
+        Ad = torch.from_numpy(A).to(dev)
+        A32 = Ad.to(torch.complex64)
+        op64 = h.op_dense(Ad)
+        op32 = h.op_dense(A32)
+        workload = ("multi-RHS n=%d shift 3, %d right-hand sides, bicgstab to %g (mixed: batched complex64 inner, "
+                    "complex128 block refinement; fp64: per-right-hand-side complex128 solves)" % (n, args.nrhs, args.tol))
+        l2 = "inputs larger than L2 (A %.2f GB)" % (A.nbytes / 1e9)
     else:
         n = args.n
         A, y = W.dense_system(n, 3.0, 0)
@@ -352,10 +372,33 @@ def run_ours(args):
         op32 = h.op_dense(A32)
         workload = "dense single-RHS n=%d shift 3, %s to %g" % (n, "/".join(methods), args.tol)
         l2 = "inputs larger than L2 (A %.2f GB)" % (A.nbytes / 1e9)
-    yd = torch.from_numpy(y).to(dev)
-    xd = torch.zeros_like(yd)
+    batched = args.workload == "batched"
+    if batched:
+        yd = torch.from_numpy(np.ascontiguousarray(y.T)).to(dev).t()     # column-major (n, k)
+        xd = torch.zeros((y.shape[1], n), dtype=torch.complex128, device=dev).t()
+        ycols = [yd[:, c].contiguous() for c in range(y.shape[1])]
+        xcol = torch.zeros(n, dtype=torch.complex128, device=dev)
+    else:
+        yd = torch.from_numpy(y).to(dev)
+        xd = torch.zeros_like(yd)
+    per_step = args.nrhs if batched else len(methods)
 
     def solve(path, m, yv, xv):
+        if batched and path == "mixed":
+            st, outer, inner, sts, rr = h.solve_batched_refined(m, op64, op32, yv, xv, tol=args.tol,
+                                                                max_outer=args.max_outer, inner_tol=args.inner_tol,
+                                                                inner_maxit=args.inner_maxit)
+            return st, {"iters": int(outer.max()), "true_relres": float(rr.max())}, int(inner.max())
+        if batched:   # complex128 solves one right-hand side at a time
+            worst, its = 0, 0
+            for c, yc in enumerate(ycols):
+                xcol.zero_()
+                st, info, _ = h.solve(m, op64, yc, xcol, tol=args.tol, maxit=args.maxit, want_hist=False)
+                worst = max(worst, info["true_relres"])
+                its = max(its, info["iters"])
+                if st != 0:
+                    return st, {"iters": its, "true_relres": worst}, its
+            return 0, {"iters": its, "true_relres": worst}, its
         if path == "mixed":
             st, info, _, inner = h.solve_refined(m, op64, op32, yv, xv, tol=args.tol, max_outer=args.max_outer,
                                                  inner_tol=args.inner_tol, inner_maxit=args.inner_maxit,
@@ -387,7 +430,7 @@ def run_ours(args):
 
     ms, lat, results, stats, launches, clk = runs[headline]
     t_max_ms = reduce_max(ms, world, dev)
-    solves = reduce_sum(args.steps * len(methods), world, dev)
+    solves = reduce_sum(args.steps * per_step, world, dev)
     value = solves / (t_max_ms / 1e3)
     other = {}
     for path, (oms, olat, ores, _, _, _) in runs.items():
@@ -401,7 +444,7 @@ def run_ours(args):
 
     # end to end through the same call with pinned host buffers (y in, x0 in, x out)
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not batched:
         yh = torch.from_numpy(y).pin_memory()
         xh = torch.zeros_like(yh).pin_memory()
         for _ in range(max(1, args.warmup // 2)):
@@ -416,10 +459,10 @@ def run_ours(args):
         e2e = {"value": solves / dt, "unit": "solves/s", "h2d_bytes_per_step": 2 * len(methods) * y.nbytes,
                "d2h_bytes_per_step": len(methods) * y.nbytes}
 
-    roof = roofline(ccg, stats, n, dipole)
+    roof = roofline(ccg, stats, n, dipole, args.nrhs if batched else 1)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and not dipole:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "dense":
         v, nsolve, dt, its = oracle_sample(A, y, methods[:1], budget_s=15.0, tol=args.tol, maxit=args.maxit)
         cpu = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
                "sample": "%d whole %s solve(s) of the same system (complex128, to %g) in %.1f s, serial C++"

@@ -192,12 +192,44 @@ ccg_status ccg_solve_refined(ccg_handle* h, ccg_method inner_method, const ccg_o
                              const ccg_operator* op_inner, const void* y, void* x, double tol, int max_outer,
                              double inner_tol, int inner_maxit, double* res_hist, int* inner_iters, ccg_info* info);
 
+/* Many right-hand sides at once (the Sec. 1 problem for a block Y of k
+ * columns): BiCGSTAB (Sec. 2.1) per column, all columns advancing together so
+ * that each iteration's two operator applications are block products A P,
+ * A S that read the matrix once for all columns.  Every column keeps its own
+ * scalars, iteration count and stopping test (||r_c|| / ||y_c|| <= tol); a
+ * stopped column is frozen while the others continue.
+ *  method    CCG_BICGSTAB (others return CCG_ERR_UNSUPPORTED)
+ *  op        dense operator (CCG_ERR_UNSUPPORTED otherwise)
+ *  nrhs      k, 1 <= k <= 256
+ *  Y, ldy    device block, column c at Y + c*ldy (ldy >= n), op's precision
+ *  X, ldx    device block, start vectors in, solutions out
+ *  iters, status, relres  optional host arrays of k entries
+ * Returns the worst column status (an error, else CCG_BREAKDOWN >
+ * CCG_NOT_CONVERGED > CCG_OK).  Synchronises the handle's stream. */
+ccg_status ccg_solve_batched(ccg_handle* h, ccg_method method, const ccg_operator* op, int64_t nrhs, const void* Y,
+                             int64_t ldy, void* X, int64_t ldx, double tol, int maxit, int32_t* iters,
+                             int32_t* status, double* relres);
+
+/* Batched mixed precision: complex128 block residuals R = Y - A X and
+ * updates X += D, each correction A D = R solved by the batched complex64
+ * BiCGSTAB above (op_inner: the complex64 copy of op's matrix).  Y, X are
+ * complex128.  X0 = 0 is detected on the device and its product skipped.
+ * Columns stop refining individually when ||y_c - A x_c|| / ||y_c|| <= tol
+ * (recomputed in complex128).  outer, inner: optional host arrays of k
+ * entries (corrections, inner iterations in total).  Other arguments as in
+ * ccg_solve_batched and ccg_solve_refined. */
+ccg_status ccg_solve_batched_refined(ccg_handle* h, ccg_method inner_method, const ccg_operator* op,
+                                     const ccg_operator* op_inner, int64_t nrhs, const void* Y, int64_t ldy, void* X,
+                                     int64_t ldx, double tol, int max_outer, double inner_tol, int inner_maxit,
+                                     int32_t* outer, int32_t* inner, int32_t* status, double* relres);
+
 /* Kinds of operator sweep, for timing. */
 typedef enum {
   CCG_SWEEP_N = 0,    /* y = A x                          */
   CCG_SWEEP_C = 1,    /* y = A^H x                        */
   CCG_SWEEP_BOTH = 2, /* A p and A^H q from one read of A */
-  CCG_SWEEP_KINDS = 3
+  CCG_SWEEP_BLOCK = 3, /* A X for a block of right-hand sides */
+  CCG_SWEEP_KINDS = 4
 } ccg_sweep_kind;
 
 /* Per-kernel timing of the operator sweeps: when enabled, each sweep that a

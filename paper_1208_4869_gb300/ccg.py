@@ -23,7 +23,7 @@ C64, C128 = 0, 1
 OK, NOT_CONVERGED, BREAKDOWN = 0, 1, 2
 ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
 OP_SYMMETRIC = 1
-SWEEP_N, SWEEP_C, SWEEP_BOTH = 0, 1, 2
+SWEEP_N, SWEEP_C, SWEEP_BOTH, SWEEP_BLOCK = 0, 1, 2, 3
 
 _lib = None
 
@@ -74,10 +74,13 @@ def lib():
     L.ccg_solve_refined.argtypes = [vp, i32, vp, vp, vp, vp, dbl, i32, dbl, i32, vp, ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(Info)]
     L.ccg_timing_reset.argtypes = [vp]
+    L.ccg_solve_batched.argtypes = [vp, i32, vp, i64, vp, i64, vp, i64, dbl, i32, vp, vp, vp]
+    L.ccg_solve_batched_refined.argtypes = [vp, i32, vp, vp, i64, vp, i64, vp, i64, dbl, i32, dbl, i32, vp, vp, vp, vp]
     L.ccg_launch_count.restype = i64
     L.ccg_launch_count.argtypes = [vp]
     for name in ("ccg_create", "ccg_destroy", "ccg_set_stream", "ccg_op_dense", "ccg_op_dipole", "ccg_op_destroy", "ccg_matvec",
-                 "ccg_dot", "ccg_solve", "ccg_solve_refined", "ccg_timing_enable", "ccg_timing_read", "ccg_timing_reset"):
+                 "ccg_dot", "ccg_solve", "ccg_solve_refined", "ccg_solve_batched", "ccg_solve_batched_refined",
+                 "ccg_timing_enable", "ccg_timing_read", "ccg_timing_reset"):
         getattr(L, name).restype = i32
     if L.ccg_abi_version() != 1:
         raise ImportError("libccg ABI version mismatch")
@@ -198,6 +201,44 @@ class Handle:
         if want_hist:
             hist = hist[: info.iters + 1]
         return st, info.as_dict(), hist, inner.value
+
+    def _block_args(self, op, Y, X):
+        n = op.n
+        assert Y.dim() == 2 and X.dim() == 2 and Y.shape == X.shape and Y.shape[0] == n
+        # column-major blocks: torch tensors of shape (n, k) with stride (1, ld)
+        assert Y.stride(0) == 1 and X.stride(0) == 1, "blocks must be column-major (stride (1, ld))"
+        return Y.shape[1], ctypes.c_void_p(Y.data_ptr()), max(Y.stride(1), n), ctypes.c_void_p(X.data_ptr()), \
+            max(X.stride(1), n)
+
+    def solve_batched(self, method, op, Y, X, tol=1e-10, maxit=1000):
+        """ccg_solve_batched on column-major device blocks Y, X of shape (n, k).
+        Returns (status, iters, per-column statuses, relres)."""
+        k, yp, ldy, xp, ldx = self._block_args(op, Y, X)
+        it = np.zeros(k, np.int32)
+        sts = np.zeros(k, np.int32)
+        rr = np.zeros(k)
+        m = METHODS[method] if isinstance(method, str) else int(method)
+        st = lib().ccg_solve_batched(self.h, m, op.op, k, yp, ldy, xp, ldx, float(tol), int(maxit),
+                                     ctypes.c_void_p(it.ctypes.data), ctypes.c_void_p(sts.ctypes.data),
+                                     ctypes.c_void_p(rr.ctypes.data))
+        _check(st)
+        return st, it, sts, rr
+
+    def solve_batched_refined(self, method, op, op_inner, Y, X, tol=1e-10, max_outer=30, inner_tol=1e-5,
+                              inner_maxit=200):
+        """ccg_solve_batched_refined.  Returns (status, outer, inner, per-column statuses, relres)."""
+        k, yp, ldy, xp, ldx = self._block_args(op, Y, X)
+        outer = np.zeros(k, np.int32)
+        inner = np.zeros(k, np.int32)
+        sts = np.zeros(k, np.int32)
+        rr = np.zeros(k)
+        m = METHODS[method] if isinstance(method, str) else int(method)
+        st = lib().ccg_solve_batched_refined(self.h, m, op.op, op_inner.op, k, yp, ldy, xp, ldx, float(tol),
+                                             int(max_outer), float(inner_tol), int(inner_maxit),
+                                             ctypes.c_void_p(outer.ctypes.data), ctypes.c_void_p(inner.ctypes.data),
+                                             ctypes.c_void_p(sts.ctypes.data), ctypes.c_void_p(rr.ctypes.data))
+        _check(st)
+        return st, outer, inner, sts, rr
 
     def timing(self, enable=None, reset=False, kind=SWEEP_N, dtype=C128):
         """Per-sweep CUDA-event timing of one precision and sweep kind: (sweeps, total_ms, bytes_per_sweep)."""

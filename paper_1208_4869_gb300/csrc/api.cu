@@ -284,6 +284,53 @@ ccg_status ccg_solve_refined(ccg_handle* h, ccg_method method, const ccg_operato
       solve_refined(h, method, op, op_in, y, x, tol, max_outer, inner_tol, inner_maxit, res_hist, inner_iters, info));
 }
 
+static int check_block(const ccg_operator* op, int64_t k, const void* Y, int64_t ldy, const void* X, int64_t ldx,
+                       const char* who) {
+  if (!op || !Y || !X) { set_error(std::string(who) + ": NULL argument"); return CCG_ERR_INVALID; }
+  if (op->kind != CCG_OPK_DENSE) { set_error(std::string(who) + ": needs a dense operator"); return CCG_ERR_UNSUPPORTED; }
+  if (k < 1 || k > 256 || ldy < op->n || ldx < op->n) {
+    set_error(std::string(who) + ": need 1 <= nrhs <= 256 and leading dimensions >= n");
+    return CCG_ERR_INVALID;
+  }
+  const size_t esz = op->dtype == CCG_C128 ? 16 : 8;
+  if (!aligned(Y, esz) || !aligned(X, esz)) { set_error(std::string(who) + ": misaligned block"); return CCG_ERR_INVALID; }
+  return CCG_OK;
+}
+
+ccg_status ccg_solve_batched(ccg_handle* h, ccg_method method, const ccg_operator* op, int64_t nrhs, const void* Y,
+                             int64_t ldy, void* X, int64_t ldx, double tol, int maxit, int32_t* iters,
+                             int32_t* status, double* relres) {
+  if (!h) { set_error("ccg_solve_batched: NULL handle"); return CCG_ERR_INVALID; }
+  if (method != CCG_BICGSTAB) { set_error("ccg_solve_batched: only CCG_BICGSTAB is batched"); return CCG_ERR_UNSUPPORTED; }
+  int rc = check_block(op, nrhs, Y, ldy, X, ldx, "ccg_solve_batched");
+  if (rc != CCG_OK) return static_cast<ccg_status>(rc);
+  if (maxit < 0 || !(tol >= 0.0)) { set_error("ccg_solve_batched: need maxit >= 0 and tol >= 0"); return CCG_ERR_INVALID; }
+  return static_cast<ccg_status>(solve_batched(h, op, nrhs, Y, ldy, X, ldx, tol, maxit, iters, status, relres));
+}
+
+ccg_status ccg_solve_batched_refined(ccg_handle* h, ccg_method method, const ccg_operator* op,
+                                     const ccg_operator* op_in, int64_t nrhs, const void* Y, int64_t ldy, void* X,
+                                     int64_t ldx, double tol, int max_outer, double inner_tol, int inner_maxit,
+                                     int32_t* outer, int32_t* inner, int32_t* status, double* relres) {
+  if (!h || !op_in) { set_error("ccg_solve_batched_refined: NULL argument"); return CCG_ERR_INVALID; }
+  if (method != CCG_BICGSTAB) {
+    set_error("ccg_solve_batched_refined: only CCG_BICGSTAB is batched");
+    return CCG_ERR_UNSUPPORTED;
+  }
+  int rc = check_block(op, nrhs, Y, ldy, X, ldx, "ccg_solve_batched_refined");
+  if (rc != CCG_OK) return static_cast<ccg_status>(rc);
+  if (op->dtype != CCG_C128 || op_in->dtype != CCG_C64 || op_in->n != op->n || op_in->kind != CCG_OPK_DENSE) {
+    set_error("ccg_solve_batched_refined: need complex128 and complex64 dense operators of the same size");
+    return CCG_ERR_INVALID;
+  }
+  if (!(tol >= 0.0) || max_outer < 0 || !(inner_tol > 0.0) || inner_maxit < 1) {
+    set_error("ccg_solve_batched_refined: need tol >= 0, max_outer >= 0, inner_tol > 0, inner_maxit >= 1");
+    return CCG_ERR_INVALID;
+  }
+  return static_cast<ccg_status>(solve_batched_refined(h, op, op_in, nrhs, Y, ldy, X, ldx, tol, max_outer, inner_tol,
+                                                       inner_maxit, outer, inner, status, relres));
+}
+
 ccg_status ccg_timing_enable(ccg_handle* h, int enable) {
   if (!h) return CCG_ERR_INVALID;
   h->timing = enable != 0;

@@ -1,0 +1,120 @@
+// Multi-right-hand-side dense products on CUDA cores: C = A B for complex A
+// (n x n, row-major, leading dimension lda) and blocks B, C of k right-hand
+// sides stored row-major (row i holds the k values of unknown i, leading
+// dimension k), in complex128 or complex64.
+//
+// A block computes a 64 x 64 tile of C; each of its 256 threads owns a 4 x 4
+// sub-tile (16 complex accumulators in registers).  K advances 8 complex
+// values at a time through shared memory (A transposed so that a thread's
+// four rows are one broadcast-friendly load).  complex128 is bound by the
+// FP64 pipe (4 DFMA per complex multiply-add); complex64 by the FP32 pipe.
+#pragma once
+
+#include "common.cuh"
+
+namespace ccg {
+
+constexpr int kGemmBM = 64, kGemmBN = 64, kGemmBK = 8;
+
+template <class R>
+__global__ void __launch_bounds__(kBlock) cgemm_rows(const cx<R>* __restrict__ A, int64_t lda,
+                                                     const cx<R>* __restrict__ B, cx<R>* __restrict__ C, int64_t n,
+                                                     int k, const int* __restrict__ skip) {
+  if (skip != nullptr && *skip) return;
+  __shared__ cx<R> As[kGemmBK][kGemmBM];
+  __shared__ cx<R> Bs[kGemmBK][kGemmBN];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int64_t row0 = (int64_t)blockIdx.y * kGemmBM;
+  const int col0 = blockIdx.x * kGemmBN;
+  cx<R> acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = mk<R>(0, 0);
+
+  // load mapping: A tile 64 rows x 8 k, B tile 8 k x 64 cols, two elements per thread each
+  for (int64_t k0 = 0; k0 < n; k0 += kGemmBK) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int idx = threadIdx.x + e * kBlock;        // 0..511
+      const int ar = idx / kGemmBK, ak = idx % kGemmBK; // A: row-major reads along k
+      const int64_t gr = row0 + ar, gk = k0 + ak;
+      As[ak][ar] = (gr < n && gk < n) ? A[gr * lda + gk] : mk<R>(0, 0);
+      const int bk = idx / kGemmBN, bc = idx % kGemmBN; // B: rows of k values
+      const int64_t gbk = k0 + bk;
+      const int gc = col0 + bc;
+      Bs[bk][bc] = (gbk < n && gc < k) ? B[gbk * k + gc] : mk<R>(0, 0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kGemmBK; ++kk) {
+      cx<R> a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = cfma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t gr = row0 + ty * 4 + i;
+    if (gr >= n) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gc = col0 + tx * 4 + j;
+      if (gc < k) C[gr * k + gc] = acc[i][j];
+    }
+  }
+}
+
+// Column-major user block (column c at U[c * ld .. c * ld + n)) <-> row-major
+// internal block (row i at V[i * k .. i * k + k)), with precision change.
+template <class Rin, class Rout>
+__global__ void block_to_rows(const cx<Rin>* __restrict__ U, int64_t ld, cx<Rout>* __restrict__ V, int64_t n, int k) {
+  __shared__ cx<Rin> tile[32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 8 rows of 32 threads
+  for (int r = ty; r < 32; r += 8) {
+    const int c = c0 + r;
+    const int64_t i = i0 + tx;
+    if (c < k && i < n) tile[r][tx] = U[(int64_t)c * ld + i];
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t i = i0 + r;
+    const int c = c0 + tx;
+    if (c < k && i < n) {
+      const cx<Rin> v = tile[tx][r];
+      V[i * k + c] = mk<Rout>((Rout)v.x, (Rout)v.y);
+    }
+  }
+}
+template <class Rin, class Rout>
+__global__ void rows_to_block(const cx<Rin>* __restrict__ V, cx<Rout>* __restrict__ U, int64_t ld, int64_t n, int k) {
+  __shared__ cx<Rin> tile[32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t i = i0 + r;
+    const int c = c0 + tx;
+    if (c < k && i < n) tile[r][tx] = V[i * k + c];
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int c = c0 + r;
+    const int64_t i = i0 + tx;
+    if (c < k && i < n) {
+      const cx<Rin> v = tile[tx][r];
+      U[(int64_t)c * ld + i] = mk<Rout>((Rout)v.x, (Rout)v.y);
+    }
+  }
+}
+
+}  // namespace ccg

@@ -90,6 +90,11 @@ int dipole_apply(const ccg_operator* op, const double2* x, double2* y, bool conj
                  cudaStream_t s);
 int dipole_apply(const ccg_operator* op, const float2* x, float2* y, bool conj, const SolveState* st,
                  cudaStream_t s);
+int solve_batched(ccg_handle* h, const ccg_operator* op, int64_t k, const void* Y, int64_t ldy, void* X, int64_t ldx,
+                  double tol, int maxit, int32_t* iters, int32_t* status, double* relres);
+int solve_batched_refined(ccg_handle* h, const ccg_operator* op, const ccg_operator* op_in, int64_t k, const void* Y,
+                          int64_t ldy, void* X, int64_t ldx, double tol, int max_outer, double inner_tol,
+                          int inner_maxit, int32_t* outer_out, int32_t* inner_out, int32_t* status, double* relres);
 int matvec_dense(ccg_handle* h, const ccg_operator* op, int trans, const void* x, void* y);
 int dot_device(ccg_handle* h, ccg_dtype dtype, int64_t n, const void* u, const void* v, int conj, double* out2);
 
