@@ -223,6 +223,32 @@ ccg_status ccg_solve_batched_refined(ccg_handle* h, ccg_method inner_method, con
                                      int64_t ldx, double tol, int max_outer, double inner_tol, int inner_maxit,
                                      int32_t* outer, int32_t* inner, int32_t* status, double* relres);
 
+/* Y = A X for a block of right-hand sides: the manual's `matvec` (Sec. 5)
+ * applied to nrhs columns at once.  X, Y: device column-major blocks of the
+ * operator's precision (column c at X + c*ldx; ldx, ldy >= n), 1 <= nrhs <=
+ * 256; dense operators only.  complex64 products run on the tensor cores
+ * (split-bf16 operands, fp32 accumulation; see CCG_OPT_TC_SPLIT) unless
+ * disabled with ccg_set_option(h, CCG_OPT_TENSOR_CORES, 0); complex128 and
+ * disabled complex64 products use CUDA cores.  Synchronises the stream;
+ * returns CCG_ERR_TIMEOUT if a bounded wait of the tensor-core pipeline gave
+ * up. */
+ccg_status ccg_block_matvec(ccg_handle* h, const ccg_operator* op, int64_t nrhs, const void* X, int64_t ldx, void* Y,
+                            int64_t ldy);
+
+/* Handle options.
+ * CCG_OPT_TENSOR_CORES selects where complex64 block products run on the
+ * tcgen05 tensor cores: 0 never; 1 (default) in ccg_block_matvec and in the
+ * inner solves of ccg_solve_batched_refined; 2 also in plain complex64
+ * ccg_solve_batched.
+ * CCG_OPT_TC_SPLIT: bf16 terms per operand entry, 2 (default: three
+ * products) or 3 (six products).  The tensor cores' fp32 accumulation bounds
+ * both to ~1e-5 relative at K ~ 10^3 and ~1e-4 at K ~ 10^4, so the third
+ * term rarely pays; refined batched solves correct the difference with one
+ * exact complex64 residual per correction. */
+#define CCG_OPT_TENSOR_CORES 1
+#define CCG_OPT_TC_SPLIT 2
+ccg_status ccg_set_option(ccg_handle* h, int option, int value);
+
 /* Kinds of operator sweep, for timing. */
 typedef enum {
   CCG_SWEEP_N = 0,    /* y = A x                          */

@@ -23,6 +23,8 @@ C64, C128 = 0, 1
 OK, NOT_CONVERGED, BREAKDOWN = 0, 1, 2
 ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
 OP_SYMMETRIC = 1
+OPT_TENSOR_CORES = 1
+OPT_TC_SPLIT = 2
 SWEEP_N, SWEEP_C, SWEEP_BOTH, SWEEP_BLOCK = 0, 1, 2, 3
 
 _lib = None
@@ -76,10 +78,13 @@ def lib():
     L.ccg_timing_reset.argtypes = [vp]
     L.ccg_solve_batched.argtypes = [vp, i32, vp, i64, vp, i64, vp, i64, dbl, i32, vp, vp, vp]
     L.ccg_solve_batched_refined.argtypes = [vp, i32, vp, vp, i64, vp, i64, vp, i64, dbl, i32, dbl, i32, vp, vp, vp, vp]
+    L.ccg_block_matvec.argtypes = [vp, vp, i64, vp, i64, vp, i64]
+    L.ccg_set_option.argtypes = [vp, i32, i32]
     L.ccg_launch_count.restype = i64
     L.ccg_launch_count.argtypes = [vp]
     for name in ("ccg_create", "ccg_destroy", "ccg_set_stream", "ccg_op_dense", "ccg_op_dipole", "ccg_op_destroy", "ccg_matvec",
                  "ccg_dot", "ccg_solve", "ccg_solve_refined", "ccg_solve_batched", "ccg_solve_batched_refined",
+                 "ccg_block_matvec", "ccg_set_option",
                  "ccg_timing_enable", "ccg_timing_read", "ccg_timing_reset"):
         getattr(L, name).restype = i32
     if L.ccg_abi_version() != 1:
@@ -209,6 +214,15 @@ class Handle:
         assert Y.stride(0) == 1 and X.stride(0) == 1, "blocks must be column-major (stride (1, ld))"
         return Y.shape[1], ctypes.c_void_p(Y.data_ptr()), max(Y.stride(1), n), ctypes.c_void_p(X.data_ptr()), \
             max(X.stride(1), n)
+
+    def block_matvec(self, op, X, Y):
+        """ccg_block_matvec: Y = A X for column-major device blocks of shape (n, k)."""
+        k, xp, ldx, yp, ldy = self._block_args(op, X, Y)
+        _check(lib().ccg_block_matvec(self.h, op.op, k, xp, ldx, yp, ldy))
+        return Y
+
+    def set_option(self, option, value):
+        _check(lib().ccg_set_option(self.h, int(option), int(value)))
 
     def solve_batched(self, method, op, Y, X, tol=1e-10, maxit=1000):
         """ccg_solve_batched on column-major device blocks Y, X of shape (n, k).

@@ -140,6 +140,7 @@ ccg_status ccg_destroy(ccg_handle* h) {
   if (!h) return CCG_OK;
   cudaStreamSynchronize(h->stream);
   if (h->arena) cudaFree(h->arena);
+  if (h->tc_buf) cudaFree(h->tc_buf);
   if (h->pinned) cudaFreeHost(h->pinned);
   for (int i = 0; i < 2; ++i)
     if (h->poll_ev[i]) cudaEventDestroy(h->poll_ev[i]);
@@ -226,6 +227,10 @@ ccg_status ccg_op_destroy(ccg_operator* op) {
   if (op && op->kind == CCG_OPK_DIPOLE) {
     cudaDeviceSynchronize();
     dipole_free(op);
+  }
+  if (op && op->tc_ready) {
+    cudaDeviceSynchronize();
+    tc_free(op);
   }
   delete op;
   return CCG_OK;
@@ -329,6 +334,28 @@ ccg_status ccg_solve_batched_refined(ccg_handle* h, ccg_method method, const ccg
   }
   return static_cast<ccg_status>(solve_batched_refined(h, op, op_in, nrhs, Y, ldy, X, ldx, tol, max_outer, inner_tol,
                                                        inner_maxit, outer, inner, status, relres));
+}
+
+ccg_status ccg_block_matvec(ccg_handle* h, const ccg_operator* op, int64_t nrhs, const void* X, int64_t ldx, void* Y,
+                            int64_t ldy) {
+  if (!h) { set_error("ccg_block_matvec: NULL handle"); return CCG_ERR_INVALID; }
+  int rc = check_block(op, nrhs, X, ldx, Y, ldy, "ccg_block_matvec");
+  if (rc != CCG_OK) return static_cast<ccg_status>(rc);
+  return static_cast<ccg_status>(block_matvec(h, op, nrhs, X, ldx, Y, ldy));
+}
+
+ccg_status ccg_set_option(ccg_handle* h, int option, int value) {
+  if (!h) { set_error("ccg_set_option: NULL handle"); return CCG_ERR_INVALID; }
+  if (option == CCG_OPT_TENSOR_CORES && value >= 0 && value <= 2) {
+    h->tc_mode = value;
+    return CCG_OK;
+  }
+  if (option == CCG_OPT_TC_SPLIT && (value == 2 || value == 3)) {
+    h->tc_terms = value;
+    return CCG_OK;
+  }
+  set_error("ccg_set_option: unknown option");
+  return CCG_ERR_INVALID;
 }
 
 ccg_status ccg_timing_enable(ccg_handle* h, int enable) {

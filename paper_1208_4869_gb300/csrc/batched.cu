@@ -386,6 +386,38 @@ struct BRefUpdate : BPhaseBase {  // x += widen(d32) for columns still refining
   __device__ void finish(int, const double*, const BCols&, const BCtl*) const {}
 };
 
+struct BMidResid : BPhaseBase {  // rm = r - A d (complex64, exact product)
+  static constexpr bool kReduce = false;
+  static constexpr int NQ = 1;
+  struct Col {};
+  int64_t n;
+  int k;
+  const float2* r;
+  const float2* ad;
+  float2* rm;
+  __device__ __forceinline__ Col col(int, const BCols&) const { return Col(); }
+  __device__ __forceinline__ void element(int64_t row, int c, const Col&, double*) const {
+    const int64_t e = row * k + c;
+    rm[e] = csub(r[e], ad[e]);
+  }
+  __device__ void finish(int, const double*, const BCols&, const BCtl*) const {}
+};
+struct BMidAdd : BPhaseBase {  // d += e
+  static constexpr bool kReduce = false;
+  static constexpr int NQ = 1;
+  struct Col {};
+  int64_t n;
+  int k;
+  float2* d;
+  const float2* e;
+  __device__ __forceinline__ Col col(int, const BCols&) const { return Col(); }
+  __device__ __forceinline__ void element(int64_t row, int c, const Col&, double*) const {
+    const int64_t x = row * k + c;
+    d[x] = cadd(d[x], e[x]);
+  }
+  __device__ void finish(int, const double*, const BCols&, const BCtl*) const {}
+};
+
 // ---------------------------------------------------------------------------
 // Host side.
 // ---------------------------------------------------------------------------
@@ -445,6 +477,7 @@ static int phase_grid(const ccg_handle* h, int64_t n, int k) {
 template <class R> struct BRun {
   ccg_handle* h;
   const ccg_operator* op;
+  bool allow_tc = false;  // complex64 products may use the tensor cores
   cudaStream_t s;
   int64_t n;
   int k;
@@ -456,13 +489,22 @@ template <class R> struct BRun {
     bphase_kernel<P><<<grid, kBlock, 0, s>>>(p, w.ctl, w.cols, red);
     ++h->launches;
   }
-  void gemm(const cx<R>* B, cx<R>* C, const int* skip) {
-    dim3 g((k + kGemmBN - 1) / kGemmBN, (unsigned)((n + kGemmBM - 1) / kGemmBM));
+  // C = A B; complex64 products go to the tensor cores when enabled.
+  int gemm(const cx<R>* B, cx<R>* C, const int* skip) {
     timing_begin(h);
+    if constexpr (sizeof(R) == 4) {
+      if (allow_tc && tc_available(op)) {
+        const int rc = tc_block_product(h, op, B, C, k, skip);
+        timing_end(h, CCG_C64, CCG_SWEEP_BLOCK, (double)n * n * 8.0 + 2.0 * n * k * sizeof(cx<R>));
+        return rc;
+      }
+    }
+    dim3 g((k + kGemmBN - 1) / kGemmBN, (unsigned)((n + kGemmBM - 1) / kGemmBM));
     cgemm_rows<R><<<g, kBlock, 0, s>>>(static_cast<const cx<R>*>(op->A), op->lda, B, C, n, k, skip);
     ++h->launches;
     timing_end(h, sizeof(R) == 8 ? CCG_C128 : CCG_C64, CCG_SWEEP_BLOCK,
                (double)n * n * sizeof(cx<R>) + 2.0 * n * k * sizeof(cx<R>));
+    return CCG_OK;
   }
 };
 
@@ -563,6 +605,7 @@ static int batched_t(ccg_handle* h, const ccg_operator* op, int64_t k, const voi
   const int kk = (int)k;
   BRun<R> run;
   run.h = h; run.op = op; run.s = h->stream; run.n = n; run.k = kk; run.grid = phase_grid(h, n, kk);
+  run.allow_tc = h->tc_mode >= 2;
   int rc = arena_reserve(h, BWs<R>::bytes(n, kk, maxit, run.grid));
   if (rc != CCG_OK) return rc;
   run.w.carve(h->arena, n, kk, maxit, run.grid);
@@ -583,6 +626,7 @@ static int batched_t(ccg_handle* h, const ccg_operator* op, int64_t k, const voi
   copy_cols_out(run.w.cols, kk, iters, status, relres, h->stream);
   B_CUDA(cudaStreamSynchronize(h->stream));
   timing_collect(h);
+  if ((rc = tc_check_error(h)) != CCG_OK) return rc;
   return worst_status(st);
 }
 
@@ -590,6 +634,34 @@ int solve_batched(ccg_handle* h, const ccg_operator* op, int64_t k, const void* 
                   double tol, int maxit, int32_t* iters, int32_t* status, double* relres) {
   if (op->dtype == CCG_C128) return batched_t<double>(h, op, k, Y, ldy, X, ldx, tol, maxit, iters, status, relres);
   return batched_t<float>(h, op, k, Y, ldy, X, ldx, tol, maxit, iters, status, relres);
+}
+
+// Y = A X for column-major device blocks (the multi-right-hand-side
+// operator application on its own).
+template <class R>
+static int block_matvec_t(ccg_handle* h, const ccg_operator* op, int64_t k, const void* X, int64_t ldx, void* Y,
+                          int64_t ldy) {
+  const int64_t n = op->n;
+  const int kk = (int)k;
+  BRun<R> run;
+  run.h = h; run.op = op; run.s = h->stream; run.n = n; run.k = kk; run.grid = phase_grid(h, n, kk);
+  run.allow_tc = h->tc_mode >= 1;
+  int rc = arena_reserve(h, BWs<R>::bytes(n, kk, 0, run.grid));
+  if (rc != CCG_OK) return rc;
+  run.w.carve(h->arena, n, kk, 0, run.grid);
+  dim3 tg((unsigned)((n + 31) / 32), (unsigned)((k + 31) / 32));
+  block_to_rows<R, R><<<tg, kBlock, 0, h->stream>>>(static_cast<const cx<R>*>(X), ldx, run.w.vec[6], n, kk);
+  if ((rc = run.gemm(run.w.vec[6], run.w.vec[7], nullptr)) != CCG_OK) return rc;
+  rows_to_block<R, R><<<tg, kBlock, 0, h->stream>>>(run.w.vec[7], static_cast<cx<R>*>(Y), ldy, n, kk);
+  h->launches += 2;
+  B_CUDA(cudaStreamSynchronize(h->stream));
+  timing_collect(h);
+  return tc_check_error(h);
+}
+
+int block_matvec(ccg_handle* h, const ccg_operator* op, int64_t k, const void* X, int64_t ldx, void* Y, int64_t ldy) {
+  if (op->dtype == CCG_C128) return block_matvec_t<double>(h, op, k, X, ldx, Y, ldy);
+  return block_matvec_t<float>(h, op, k, X, ldx, Y, ldy);
 }
 
 // X == 0 check: sets ctl->skip_mv when every entry of X is zero.
@@ -617,6 +689,7 @@ int solve_batched_refined(ccg_handle* h, const ccg_operator* op, const ccg_opera
   ro.h = h; ro.op = op; ro.s = s; ro.n = n; ro.k = kk; ro.grid = phase_grid(h, n, kk);
   BRun<float> ri;
   ri.h = h; ri.op = op_in; ri.s = s; ri.n = n; ri.k = kk; ri.grid = ro.grid;
+  ri.allow_tc = h->tc_mode >= 1;
   const size_t b64 = al256(BWs<double>::bytes(n, kk, max_outer, ro.grid));
   int rc = arena_reserve(h, b64 + BWs<float>::bytes(n, kk, inner_maxit, ri.grid));
   if (rc != CCG_OK) return rc;
@@ -629,6 +702,10 @@ int solve_batched_refined(ccg_handle* h, const ccg_operator* op, const ccg_opera
   double2* AX = ro.w.vec[2];
   float2* R32 = ri.w.vec[6];
   float2* D32 = ri.w.vec[7];
+  // complex64 blocks of the nested correction, in unused complex128 slots
+  float2* E32 = reinterpret_cast<float2*>(ro.w.vec[3]);
+  float2* AD32 = reinterpret_cast<float2*>(ro.w.vec[4]);
+  float2* Rm = reinterpret_cast<float2*>(ro.w.vec[5]);
   dim3 tg((unsigned)((n + 31) / 32), (unsigned)((k + 31) / 32));
   block_to_rows<double, double><<<tg, kBlock, 0, s>>>(static_cast<const double2*>(Y), ldy, Yr, n, kk);
   block_to_rows<double, double><<<tg, kBlock, 0, s>>>(static_cast<const double2*>(X), ldx, Xr, n, kk);
@@ -649,28 +726,49 @@ int solve_batched_refined(ccg_handle* h, const ccg_operator* op, const ccg_opera
   ++h->launches;
   std::vector<int> inner_it(kk, 0), inner_total(kk, 0);
   int outer = 0;
+  B_CUDA(cudaMemcpyAsync(&init, ro.w.ctl, sizeof(init), cudaMemcpyDeviceToHost, s));
+  B_CUDA(cudaStreamSynchronize(s));
+  const bool x0_zero = init.skip_mv != 0;
   for (;; ++outer) {
-    const int* skip = outer == 0 ? &ro.w.ctl->skip_mv : nullptr;
-    ro.gemm(Xr, AX, skip);
     BRefResid p;
     p.n = n; p.k = kk; p.y = Yr; p.ax = AX; p.r32 = R32; p.d32 = D32; p.outer = outer;
-    if (outer == 0) {
-      // ax is zero if the product was skipped: clear it on the device side
-      // by reusing the skip flag (the GEMM left AX untouched).
-      B_CUDA(cudaMemcpyAsync(&init, ro.w.ctl, sizeof(init), cudaMemcpyDeviceToHost, s));
-      B_CUDA(cudaStreamSynchronize(s));
-      if (init.skip_mv) p.ax = nullptr;
-    }
+    if (outer == 0 && x0_zero) p.ax = nullptr;   // R = Y: no product needed
+    else if ((rc = ro.gemm(Xr, AX, nullptr)) != CCG_OK) return rc;
     ro.phase(p);
     B_CUDA(cudaGetLastError());
     int all = 0;
     B_CUDA(cudaMemcpyAsync(&all, &ro.w.ctl->all_done, sizeof(int), cudaMemcpyDeviceToHost, s));
     B_CUDA(cudaStreamSynchronize(s));
     if (all) break;
-    if ((rc = bicgstab_core<float>(ri, R32, D32, inner_tol, inner_maxit, true, ro.w.cols.done)) != CCG_OK) return rc;
-    B_CUDA(cudaMemcpyAsync(inner_it.data(), ri.w.cols.iters, kk * sizeof(int), cudaMemcpyDeviceToHost, s));
-    B_CUDA(cudaStreamSynchronize(s));
-    for (int c = 0; c < kk; ++c) inner_total[c] += inner_it[c];
+    // Correction D32 for A D = R32.  Tensor-core products are ~1e-4
+    // accurate at this size (their fp32 accumulation), so a tensor-core solve
+    // is followed by one exact complex64 residual R32 - A D32 on CUDA cores
+    // and a second tensor-core solve of it: the correction is then as good as
+    // an all-CUDA-core inner solve, with one CUDA-core product instead of
+    // one per iteration.
+    const bool tc_inner = ri.allow_tc && tc_available(op_in);
+    const int mid_steps = tc_inner ? 2 : 1;
+    for (int mid = 0; mid < mid_steps; ++mid) {
+      float2* rhs = mid == 0 ? R32 : Rm;
+      float2* sol = mid == 0 ? D32 : E32;
+      if ((rc = bicgstab_core<float>(ri, rhs, sol, inner_tol, inner_maxit, true, ro.w.cols.done)) != CCG_OK) return rc;
+      B_CUDA(cudaMemcpyAsync(inner_it.data(), ri.w.cols.iters, kk * sizeof(int), cudaMemcpyDeviceToHost, s));
+      B_CUDA(cudaStreamSynchronize(s));
+      for (int c = 0; c < kk; ++c) inner_total[c] += inner_it[c];
+      if (mid > 0) {
+        BMidAdd a;
+        a.n = n; a.k = kk; a.d = D32; a.e = E32;
+        ro.phase(a);
+      }
+      if (mid + 1 < mid_steps) {
+        ri.allow_tc = false;           // the exact complex64 product
+        if ((rc = ri.gemm(D32, AD32, nullptr)) != CCG_OK) return rc;
+        ri.allow_tc = true;
+        BMidResid m;
+        m.n = n; m.k = kk; m.r = R32; m.ad = AD32; m.rm = Rm;
+        ro.phase(m);
+      }
+    }
     BRefUpdate u;
     u.n = n; u.k = kk; u.x = Xr; u.d32 = D32;
     ro.phase(u);
@@ -684,6 +782,7 @@ int solve_batched_refined(ccg_handle* h, const ccg_operator* op, const ccg_opera
   B_CUDA(cudaStreamSynchronize(s));
   if (inner_out) std::memcpy(inner_out, inner_total.data(), kk * sizeof(int));
   timing_collect(h);
+  if ((rc = tc_check_error(h)) != CCG_OK) return rc;
   return worst_status(st);
 }
 

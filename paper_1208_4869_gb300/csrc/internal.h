@@ -41,6 +41,11 @@ struct ccg_operator {
   int unit = 1;  // complex numbers per 16-byte load (2 only for aligned complex64 with even n, lda)
   // dipole
   DipoleData dip;
+  // tensor-core copies of a complex64 dense matrix (made on first use)
+  bool tc_ready = false;
+  int tc_terms = 0;                            // bf16 terms per entry (2 or 3)
+  void* tc_ahi = nullptr;                      // the terms, one n x 2n bf16 matrix each
+  alignas(64) unsigned char tc_map[3][128] = {};  // their TMA descriptors
 };
 
 struct ccg_handle {
@@ -63,6 +68,12 @@ struct ccg_handle {
   double bytes_per_sweep[2 * CCG_SWEEP_KINDS] = {};
   // kernels launched by this handle
   int64_t launches = 0;
+  // tensor-core block products: enabled flag, staging for split blocks and
+  // the pipeline's error flag (first 256 bytes)
+  int tc_mode = 1;   // 0 never, 1 refined inner solves and block products, 2 also plain batched solves
+  int tc_terms = 2;  // bf16 terms of the split operands (2 or 3; the fp32 accumulation limits both to ~1e-4 at K ~ 1e4)
+  void* tc_buf = nullptr;
+  size_t tc_bytes = 0;
 };
 
 namespace ccg {
@@ -95,6 +106,11 @@ int solve_batched(ccg_handle* h, const ccg_operator* op, int64_t k, const void* 
 int solve_batched_refined(ccg_handle* h, const ccg_operator* op, const ccg_operator* op_in, int64_t k, const void* Y,
                           int64_t ldy, void* X, int64_t ldx, double tol, int max_outer, double inner_tol,
                           int inner_maxit, int32_t* outer_out, int32_t* inner_out, int32_t* status, double* relres);
+bool tc_available(const ccg_operator* op);
+int tc_block_product(ccg_handle* h, const ccg_operator* op, const float2* X, float2* Y, int k, const int* skip);
+int tc_check_error(ccg_handle* h);
+void tc_free(ccg_operator* op);
+int block_matvec(ccg_handle* h, const ccg_operator* op, int64_t k, const void* X, int64_t ldx, void* Y, int64_t ldy);
 int matvec_dense(ccg_handle* h, const ccg_operator* op, int trans, const void* x, void* y);
 int dot_device(ccg_handle* h, ccg_dtype dtype, int64_t n, const void* u, const void* v, int conj, double* out2);
 

@@ -1,0 +1,464 @@
+// Tensor-core block product for complex64 operators: Y = A X for a block of
+// k right-hand sides, on the 5th-generation tensor cores (tcgen05) with
+// operands staged by TMA and the accumulator in tensor memory.
+//
+// The complex product is one real GEMM: with the interleaved complex matrix
+// read as a real n x 2n matrix Ah (row i = re a_i0, im a_i0, re a_i1, ...),
+// and the real 2n x 2k matrix Xh whose columns 2c and 2c+1 are
+// (re x_c, -im x_c) and (im x_c, re x_c) interleaved the same way,
+//     Yh = Ah Xh
+// is the interleaved complex block Y (row-major n x k).  Single precision
+// is carried by operands split into T bf16 terms (a = a_0 + a_1 [+ a_2],
+// a_0 = bf16(a), a_t = bf16(a - a_0 - ... - a_{t-1})) and the products of
+// order below T accumulated in fp32 in tensor memory:
+//   T = 2: A0 X0 + A0 X1 + A1 X0                    (~2^-17 relative)
+//   T = 3: A0 X0 + A0 X1 + A1 X0 + A0 X2 + A1 X1 + A2 X0   (~2^-24, fp32 level)
+//
+// Kernel: one CTA per 128 x BN output tile (BN = 256 for T = 2, 128 for
+// T = 3), 4 warps.  Lane 0 of warp 0 feeds a 2-stage ring of shared-memory
+// tiles (T tiles of A, 128 x 64 bf16, and T of X, BN x 64; 128-byte swizzle)
+// with cp.async.bulk.tensor and mbarrier transaction counts; lane 0 of warp 1
+// issues the tcgen05.mma of every product and K=16 step of a stage and
+// releases the stage with tcgen05.commit; after the last stage all four warps
+// read their 32 rows of the fp32 accumulator with tcgen05.ld and store them.  Every mbarrier wait
+// gives up after about two seconds, records an error flag and lets the CTA
+// finish (tensor memory is always freed), so a fault in the pipeline cannot
+// hang the GPU.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <string>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace ccg {
+namespace tc {
+
+constexpr int BM = 128, BK = 64, STAGES = 2, THREADS = 128;
+template <int T> struct Cfg {
+  static constexpr int BN = T == 2 ? 256 : 128;
+  static constexpr int A_TILE = BM * BK * 2;         // bytes of one bf16 A tile
+  static constexpr int B_TILE = BN * BK * 2;         // bytes of one bf16 X tile
+  static constexpr int STAGE_BYTES = T * (A_TILE + B_TILE);
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+  static constexpr uint32_t TMEM_COLS = BN;
+  static constexpr int NPROD = T == 2 ? 3 : 6;       // products of order below T
+};
+// (term of A, term of X) of each product
+__device__ constexpr int kProdA[6] = {0, 0, 1, 0, 1, 2};
+__device__ constexpr int kProdX[6] = {0, 1, 0, 2, 1, 0};
+
+struct TcMaps {
+  CUtensorMap a[3];
+  CUtensorMap x[3];
+};
+
+constexpr long long WAIT_CYCLES = 4000000000LL;       // ~2 s at the SM clock
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase of the given parity; false (and the error flag set)
+// after ~2 s or when another thread already gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* err) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(b, parity)) {
+    if (*err) return false;
+    if (clock64() - t0 > WAIT_CYCLES) {
+      *err = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+// Bounded wait that ignores the shared error flag: used at teardown so that
+// no copy or MMA of this CTA is still in flight when it frees its memory.
+__device__ __forceinline__ bool mbar_drain(uint64_t* b, uint32_t parity, volatile int* err) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(b, parity)) {
+    if (clock64() - t0 > WAIT_CYCLES) {
+      *err = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile of rows x 64 bf16 written by
+// TMA with the 128-byte swizzle (8-row atoms of 1024 bytes).
+__device__ __forceinline__ uint64_t sdesc_k128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);   // start address, 16-byte units
+  d |= (uint64_t)1 << 16;                      // leading byte offset (unused with swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset: next 8-row atom
+  d |= (uint64_t)1 << 46;                      // descriptor version
+  d |= (uint64_t)2 << 61;                      // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: bf16 x bf16 -> fp32, both operands K-major, M x N.
+constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4)                       // D format fp32
+         | (1u << 7)                     // A format bf16
+         | (1u << 10)                    // B format bf16
+         | ((uint32_t)(N >> 3) << 17)    // N / 8
+         | ((uint32_t)(M >> 4) << 24);   // M / 16
+}
+
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// C (M x N fp32, leading dimension ldc) = sum of the split products.
+template <int T>
+__global__ void __launch_bounds__(THREADS, 1)
+    gemm_bf16_split(const __grid_constant__ TcMaps maps, float* __restrict__ C, int M, int N, int K, int64_t ldc,
+                    int* err, const int* skip) {
+  using G = Cfg<T>;
+  if (skip != nullptr && *skip) return;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * G::STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accf = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 1);
+  volatile int* verr = err;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * G::BN;
+  const int nkb = (K + BK - 1) / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accf, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(G::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  int issued = 0;
+  if (warp == 0 && lane == 0) {
+    // producer: stage s of block kb waits until the MMAs of block kb - STAGES released it
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES;
+      if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) & 1) ^ 1, verr)) break;
+      unsigned char* st = smem + s * G::STAGE_BYTES;
+      mbar_expect_tx(&full[s], G::STAGE_BYTES);
+#pragma unroll
+      for (int t = 0; t < T; ++t) {
+        tma_load_2d(st + t * G::A_TILE, &maps.a[t], &full[s], kb * BK, m0);
+        tma_load_2d(st + T * G::A_TILE + t * G::B_TILE, &maps.x[t], &full[s], kb * BK, n0);
+      }
+      issued = kb + 1;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    constexpr uint32_t idesc = idesc_bf16(BM, G::BN);
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(&full[s], (kb / STAGES) & 1, verr)) break;
+      fence_after();
+      const uint32_t base = smem_u32(smem + s * G::STAGE_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint32_t off = kk * 32;  // 16 bf16 along K
+#pragma unroll
+        for (int q = 0; q < G::NPROD; ++q) {
+          const uint64_t a = sdesc_k128(base + kProdA[q] * G::A_TILE + off);
+          const uint64_t b = sdesc_k128(base + T * G::A_TILE + kProdX[q] * G::B_TILE + off);
+          umma(tmem, a, b, idesc, (kb | kk | q) != 0 ? 1u : 0u);
+        }
+      }
+      umma_commit(&empty[s]);
+    }
+    umma_commit(accf);  // always: it also tracks every MMA issued before a failure
+  }
+  __syncwarp();
+
+  // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w + 31
+  mbar_drain(accf, 0, verr);
+  fence_after();
+  __syncwarp();
+  // tcgen05.ld is warp-collective: take lane 0's reading of the flag
+  const bool ready = __shfl_sync(0xffffffffu, *verr, 0) == 0;
+  const int row = m0 + warp * 32 + lane;
+  if (ready) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < G::BN; c0 += 32) {
+      uint32_t r[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+      if (row < M) {
+        float* dst = C + (int64_t)row * ldc + n0 + c0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (n0 + c0 + j < N) dst[j] = __uint_as_float(r[j]);
+      }
+    }
+  }
+  if (warp == 0 && lane == 0) {
+    // drain the copies this CTA issued (all consumed unless the pipeline failed)
+    for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
+      mbar_drain(&full[kb % STAGES], (kb / STAGES) & 1, verr);
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G::TMEM_COLS) : "memory");
+}
+
+// Split v into T bf16 terms (t[0] = bf16(v), t[i] = bf16(v - t[0] - ... )).
+template <int T> __device__ __forceinline__ void split_terms(float v, __nv_bfloat16 (&t)[3]) {
+  float rem = v;
+#pragma unroll
+  for (int i = 0; i < T; ++i) {
+    t[i] = __float2bfloat16_rn(rem);
+    rem -= __bfloat162float(t[i]);
+  }
+}
+
+// The interleaved complex64 matrix (row i at A + i * lda complex) as T bf16
+// terms of the real n x 2n matrix, term t at out + t * n * 2n.
+template <int T>
+__global__ void split_matrix(const float2* __restrict__ A, int64_t lda, int64_t n, __nv_bfloat16* __restrict__ out) {
+  const int64_t count = n * 2 * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / (2 * n), jj = e - i * 2 * n;
+    const float2 a = A[i * lda + (jj >> 1)];
+    __nv_bfloat16 t[3];
+    split_terms<T>((jj & 1) ? a.y : a.x, t);
+#pragma unroll
+    for (int q = 0; q < T; ++q) out[q * count + e] = t[q];
+  }
+}
+
+// Xh^T as T bf16 terms (2k rows x 2n, term t at out + t * 2k * 2n) from the
+// row-major block X (n x k complex): row 2c = (re x_c[j], -im x_c[j])_j,
+// row 2c + 1 = (im x_c[j], re x_c[j])_j.
+template <int T>
+__global__ void split_block(const float2* __restrict__ X, int64_t n, int k, __nv_bfloat16* __restrict__ out) {
+  __shared__ float2 tile[32][33];
+  const int64_t j0 = (int64_t)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  const int64_t count = (int64_t)2 * k * 2 * n;
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t j = j0 + r;
+    const int c = c0 + tx;
+    tile[r][tx] = (j < n && c < k) ? X[j * k + c] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int c = c0 + r;
+    const int64_t j = j0 + tx;
+    if (c < k && j < n) {
+      const float2 x = tile[tx][r];
+      const float vals[4] = {x.x, -x.y, x.y, x.x};  // (2c, 2j), (2c, 2j+1), (2c+1, 2j), (2c+1, 2j+1)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t e = (int64_t)(2 * c + (q >> 1)) * (2 * n) + 2 * j + (q & 1);
+        __nv_bfloat16 t[3];
+        split_terms<T>(vals[q], t);
+#pragma unroll
+        for (int i = 0; i < T; ++i) out[i * count + e] = t[i];
+      }
+    }
+  }
+}
+
+typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                             const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                             CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeFn encoder() {
+  static EncodeFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(p);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2D bf16 tensor map over a row-major rows x cols matrix, box box_rows x 64.
+static bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int box_rows) {
+  EncodeFn enc = encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)(cols * 2)};
+  const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace tc
+
+bool tc_available(const ccg_operator* op) {
+  return op->kind == CCG_OPK_DENSE && op->dtype == CCG_C64 && op->n % 4 == 0 && tc::encoder() != nullptr;
+}
+
+template <int T>
+static int tc_product_t(ccg_handle* h, ccg_operator* op, const float2* X, float2* Y, int k, const int* skip) {
+  using G = tc::Cfg<T>;
+  const int64_t n = op->n;
+  cudaStream_t s = h->stream;
+  const size_t abytes = (size_t)n * 2 * n * sizeof(__nv_bfloat16);
+  if (op->tc_ready && op->tc_terms != T) tc_free(op);
+  if (!op->tc_ready) {
+    if (cudaMalloc(&op->tc_ahi, T * abytes) != cudaSuccess) {
+      cudaGetLastError();
+      op->tc_ahi = nullptr;
+      set_error("tensor-core operand allocation failed");
+      return CCG_ERR_NOMEM;
+    }
+    tc::split_matrix<T><<<2048, kBlock, 0, s>>>(static_cast<const float2*>(op->A), op->lda, n,
+                                                 static_cast<__nv_bfloat16*>(op->tc_ahi));
+    for (int t = 0; t < T; ++t)
+      if (!tc::make_map(reinterpret_cast<CUtensorMap*>(op->tc_map[t]), static_cast<char*>(op->tc_ahi) + t * abytes, n,
+                        2 * n, tc::BM)) {
+        set_error("cuTensorMapEncodeTiled failed for the matrix");
+        return CCG_ERR_CUDA;
+      }
+    op->tc_terms = T;
+    op->tc_ready = true;
+  }
+  // split X into the handle's bf16 staging (T terms of 2k x 2n)
+  const size_t xb = (size_t)2 * k * 2 * n * sizeof(__nv_bfloat16);
+  if (h->tc_bytes < T * xb + 256) {
+    if (h->tc_buf) {
+      cudaStreamSynchronize(s);
+      cudaFree(h->tc_buf);
+      h->tc_buf = nullptr;
+      h->tc_bytes = 0;
+    }
+    if (cudaMalloc(&h->tc_buf, T * xb + 256) != cudaSuccess) {
+      cudaGetLastError();
+      h->tc_buf = nullptr;
+      set_error("tensor-core staging allocation failed");
+      return CCG_ERR_NOMEM;
+    }
+    h->tc_bytes = T * xb + 256;
+    cudaMemsetAsync(h->tc_buf, 0, 256, s);
+  }
+  int* err = static_cast<int*>(h->tc_buf);
+  __nv_bfloat16* xs = reinterpret_cast<__nv_bfloat16*>(static_cast<char*>(h->tc_buf) + 256);
+  dim3 sg((unsigned)((n + 31) / 32), (unsigned)((k + 31) / 32));
+  tc::split_block<T><<<sg, kBlock, 0, s>>>(X, n, k, xs);
+  tc::TcMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  for (int t = 0; t < T; ++t) {
+    std::memcpy(&maps.a[t], op->tc_map[t], sizeof(CUtensorMap));
+    if (!tc::make_map(&maps.x[t], reinterpret_cast<char*>(xs) + t * xb, 2 * k, 2 * n, G::BN)) {
+      set_error("cuTensorMapEncodeTiled failed for the block");
+      return CCG_ERR_CUDA;
+    }
+  }
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(tc::gemm_bf16_split<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES) !=
+        cudaSuccess) {
+      set_error("tensor-core kernel: shared memory opt-in failed");
+      return CCG_ERR_CUDA;
+    }
+    attr = true;
+  }
+  const int Nr = 2 * k;
+  dim3 grid((unsigned)((Nr + G::BN - 1) / G::BN), (unsigned)((n + tc::BM - 1) / tc::BM));
+  tc::gemm_bf16_split<T><<<grid, tc::THREADS, G::SMEM_BYTES, s>>>(maps, reinterpret_cast<float*>(Y), (int)n, Nr,
+                                                                    (int)(2 * n), (int64_t)Nr, err, skip);
+  h->launches += 2;
+  return cudaGetLastError() == cudaSuccess ? CCG_OK : CCG_ERR_CUDA;
+}
+
+// Y = A X (row-major n x k complex64 blocks) on the tensor cores with the
+// handle's split (2 or 3 bf16 terms).
+int tc_block_product(ccg_handle* h, const ccg_operator* op_c, const float2* X, float2* Y, int k, const int* skip) {
+  ccg_operator* op = const_cast<ccg_operator*>(op_c);
+  return h->tc_terms == 2 ? tc_product_t<2>(h, op, X, Y, k, skip) : tc_product_t<3>(h, op, X, Y, k, skip);
+}
+
+// Error flag of the tensor-core pipeline (a bounded wait gave up): read and clear.
+int tc_check_error(ccg_handle* h) {
+  if (!h->tc_buf) return CCG_OK;
+  int e = 0;
+  if (cudaMemcpy(&e, h->tc_buf, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return CCG_ERR_CUDA;
+  if (e) {
+    cudaMemset(h->tc_buf, 0, sizeof(int));
+    set_error("tensor-core pipeline wait timed out");
+    return CCG_ERR_TIMEOUT;
+  }
+  return CCG_OK;
+}
+
+void tc_free(ccg_operator* op) {
+  if (op->tc_ahi) cudaFree(op->tc_ahi);
+  op->tc_ahi = nullptr;
+  op->tc_ready = false;
+  op->tc_terms = 0;
+}
+
+}  // namespace ccg
