@@ -44,7 +44,10 @@ def parse_args(argv=None):
     p.add_argument("--steps", type=int, default=None)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ccg", "reference"], default="ccg")
-    p.add_argument("--workload", choices=["dense", "dipole", "batched"], default="dense")
+    p.add_argument("--workload", choices=["dense", "dipole", "batched", "serving"], default="dense")
+    p.add_argument("--requests", type=int, default=200)
+    p.add_argument("--slots", type=int, default=4)
+    p.add_argument("--baseline-requests", type=int, default=40)
     p.add_argument("--nrhs", type=int, default=256)
     p.add_argument("--n", type=int, default=8192)
     p.add_argument("--L", type=int, default=64)
@@ -295,6 +298,86 @@ def run_reference(args):
     return 0
 
 
+# ----------------------------------------------------------------- serving
+def serving_stream(count, seed=2):
+    """The mixed request stream: Poisson arrivals (mean 200/s); half dense
+    systems (n log-uniform in [512, 8192], 1..64 right-hand sides), half
+    dipole spheres (edge 16, 24, 32, 48 or 64); tolerance 1e-6 or 1e-10."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / 200.0, count))
+    reqs = []
+    for i in range(count):
+        tol = 1e-6 if rng.random() < 0.5 else 1e-10
+        if rng.random() < 0.5:
+            n = int(round(np.exp(rng.uniform(np.log(512), np.log(8192))) / 4.0)) * 4
+            reqs.append(dict(kind="dense", n=n, nrhs=int(rng.integers(1, 65)), shift=3.0, seed=1000 + i, tol=tol))
+        else:
+            reqs.append(dict(kind="dipole", L=int(rng.choice([16, 24, 32, 48, 64])), tol=tol))
+    return t, reqs
+
+
+def run_serving(args):
+    import numpy as np
+    import torch
+    from paper_1208_4869_gb300 import build as B
+    from paper_1208_4869_gb300 import ccg
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist_init(world, "nccl")
+    B.build()
+    arrivals, reqs = serving_stream(args.requests)
+
+    def serve(slots, items, times, mode):
+        sv = ccg.Server(device=local, slots=slots, budget_bytes=120 << 30)
+        # warm the slots' handles and caches on the first requests' shapes
+        for r in items[:min(len(items), slots)]:
+            sv.wait(sv.submit(**r, mode=mode))
+        t0 = time.perf_counter()
+        tickets = []
+        for r, ta in zip(items, times):
+            now = time.perf_counter() - t0
+            if times is not None and ta > now:
+                time.sleep(ta - now)
+            tickets.append(sv.submit(**r, mode=mode))
+        res = [sv.wait(t)[0] for t in tickets]
+        sv.close()
+        return res
+
+    clocks = ClockSampler(local)
+    barrier(world)
+    clocks.start()
+    res = serve(args.slots, reqs, arrivals - arrivals[0], 0)
+    clk = clocks.stop()
+    first = min(r["t_submit"] for r in res)
+    span = max(r["t_done"] for r in res) - first
+    lat = sorted(r["t_done"] - r["t_submit"] for r in res)
+    ok = all(r["status"] == 0 for r in res)
+    span_max = reduce_max(span, world)
+    solves = reduce_sum(len(res), world)
+    nb = min(args.baseline_requests, len(reqs))
+    base = serve(1, reqs[:nb], np.zeros(nb), 1)        # complex128, one request and one RHS at a time
+    bspan = max(r["t_done"] for r in base) - min(r["t_submit"] for r in base)
+    if rank == 0:
+        p = lambda q: 1e3 * lat[int(q * (len(lat) - 1))]
+        line = {
+            "metric": METRIC, "value": solves / span_max, "unit": "solves/s", "n_gpus": world, "steps": 1,
+            "warmup": args.slots, "ms_per_step": 1e3 * span_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64+c128", "data": "synthetic",
+            "config": {"workload": "serving stream: %d requests, Poisson 200/s, 50%% dense n in [512, 8192] with "
+                                   "1-64 RHS, 50%% dipole L in {16..64}, tol 1e-6 or 1e-10, HBM budget 120 GB"
+                                   % len(reqs), "slots": args.slots, "requests": len(reqs),
+                       "l2": "inputs larger than L2 (matrices up to 1.07 GB)"},
+            "latency_ms": {"p50": p(0.5), "p99": p(0.99), "max": 1e3 * lat[-1]},
+            "all_converged": ok,
+            "other_paths": {"fp64_one_at_a_time": {"value": nb / bspan, "unit": "solves/s", "requests": nb,
+                                                   "all_converged": all(r["status"] == 0 for r in base)}},
+            "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clk,
+        }
+        print(json.dumps(line))
+    return 0
+
+
 # ----------------------------------------------------------------- our arm
 def timed_region(h, ccg, torch, stream, step, steps, world, dev, clocks=None):
     """Run `steps` steps between CUDA events on the solve stream, with the
@@ -498,6 +581,8 @@ def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 

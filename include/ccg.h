@@ -249,6 +249,67 @@ ccg_status ccg_block_matvec(ccg_handle* h, const ccg_operator* op, int64_t nrhs,
 #define CCG_OPT_TC_SPLIT 2
 ccg_status ccg_set_option(ccg_handle* h, int option, int value);
 
+/* ---------------------------------------------------------------------------
+ * Serving: a queue of solve requests of mixed sizes, admitted to worker slots
+ * as slots and device memory (an HBM budget) free up.  Each slot owns a
+ * handle and a CUDA stream, so admitted requests' work overlaps on the GPU;
+ * a request's Krylov state stays resident on its slot until it finishes.
+ * Requests are synthetic problems generated on the device from a seed with
+ * the counter-based Philox4x32-10 generator (Salmon et al., SC'11):
+ *  - CCG_REQ_DENSE: A = (shift + 0.5 + 0.5i) I + G / sqrt(n), G complex
+ *    normal; nrhs complex-normal right-hand sides (the Sec. 1 problem);
+ *  - CCG_REQ_DIPOLE: the discrete-dipole operator of an L^3 inscribed sphere
+ *    (see ccg_op_dipole) with the x-polarised plane wave along z.
+ * Precision follows the tolerance: tol >= 1e-7 runs complex64 solves,
+ * smaller tol the mixed-precision refinement (complex128 residuals).  Dense
+ * requests use BiCGSTAB (batched when nrhs > 1); dipole requests COCG.
+ * -------------------------------------------------------------------------- */
+typedef struct ccg_server ccg_server;
+
+#define CCG_REQ_DENSE 0
+#define CCG_REQ_DIPOLE 1
+
+typedef struct {
+  int32_t kind;      /* CCG_REQ_DENSE or CCG_REQ_DIPOLE                         */
+  int32_t nrhs;      /* dense: right-hand sides, 1 .. 256                      */
+  int64_t n;         /* dense: matrix order                                     */
+  double shift;      /* dense: diagonal shift                                   */
+  uint64_t seed;     /* dense: generator seed (matrix and right-hand sides)     */
+  int32_t L;         /* dipole: lattice edge (2L must be 2^a 3^b, <= 256)       */
+  int32_t maxit;     /* iteration cap of each (inner) solve                     */
+  double kd, m_re, m_im; /* dipole: wavenumber x spacing, refractive index      */
+  double tol;        /* relative residual target                                */
+  int32_t keep_x;    /* 1: keep the solution for ccg_server_wait to copy out   */
+  int32_t mode;      /* 0: precision by tolerance (above); 1: plain complex128
+                        solves, one right-hand side at a time (a baseline)     */
+} ccg_request;
+
+typedef struct {
+  int32_t status;    /* worst column status (ccg_status)                        */
+  int32_t iters;     /* largest iteration count (corrections for refinement)    */
+  double relres;     /* largest final relative residual                         */
+  double t_submit, t_start, t_done; /* seconds on the server's steady clock     */
+  int64_t n;         /* unknowns per right-hand side                            */
+  int32_t nrhs;
+  int32_t slot;      /* worker slot that ran the request                        */
+} ccg_result;
+
+/* Create a server on CUDA device `device` with `slots` workers (1..32) and
+ * an HBM budget in bytes for admitted requests (0: 120 GB). */
+ccg_status ccg_server_create(ccg_server** s, int device, int slots, uint64_t hbm_budget_bytes);
+/* Queue a request; *ticket identifies it.  Never blocks on the GPU. */
+ccg_status ccg_server_submit(ccg_server* s, const ccg_request* req, int64_t* ticket);
+/* *done = 1 once the request has finished. */
+ccg_status ccg_server_poll(ccg_server* s, int64_t ticket, int* done);
+/* Block until the request has finished; fill *res.  With keep_x set and x
+ * non-NULL, copy the solution (n * nrhs complex values, column-major,
+ * complex128) into the host buffer x and release it. */
+ccg_status ccg_server_wait(ccg_server* s, int64_t ticket, ccg_result* res, void* x);
+/* Seconds on the server's clock (the clock of ccg_result times). */
+double ccg_server_now(const ccg_server* s);
+/* Finish queued work, stop the workers and free everything. */
+ccg_status ccg_server_destroy(ccg_server* s);
+
 /* Kinds of operator sweep, for timing. */
 typedef enum {
   CCG_SWEEP_N = 0,    /* y = A x                          */

@@ -45,6 +45,25 @@ class Info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("nrhs", ctypes.c_int32), ("n", ctypes.c_int64), ("shift", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("L", ctypes.c_int32), ("maxit", ctypes.c_int32), ("kd", ctypes.c_double),
+                ("m_re", ctypes.c_double), ("m_im", ctypes.c_double), ("tol", ctypes.c_double),
+                ("keep_x", ctypes.c_int32), ("mode", ctypes.c_int32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("relres", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("n", ctypes.c_int64), ("nrhs", ctypes.c_int32), ("slot", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+REQ_DENSE, REQ_DIPOLE = 0, 1
+
+
 def lib():
     """Load libccg.so (built by paper_1208_4869_gb300.build); raise if absent."""
     global _lib
@@ -80,11 +99,19 @@ def lib():
     L.ccg_solve_batched_refined.argtypes = [vp, i32, vp, vp, i64, vp, i64, vp, i64, dbl, i32, dbl, i32, vp, vp, vp, vp]
     L.ccg_block_matvec.argtypes = [vp, vp, i64, vp, i64, vp, i64]
     L.ccg_set_option.argtypes = [vp, i32, i32]
+    L.ccg_server_create.argtypes = [ctypes.POINTER(vp), i32, i32, ctypes.c_uint64]
+    L.ccg_server_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(i64)]
+    L.ccg_server_poll.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_int)]
+    L.ccg_server_wait.argtypes = [vp, i64, ctypes.POINTER(Result), vp]
+    L.ccg_server_now.restype = dbl
+    L.ccg_server_now.argtypes = [vp]
+    L.ccg_server_destroy.argtypes = [vp]
     L.ccg_launch_count.restype = i64
     L.ccg_launch_count.argtypes = [vp]
     for name in ("ccg_create", "ccg_destroy", "ccg_set_stream", "ccg_op_dense", "ccg_op_dipole", "ccg_op_destroy", "ccg_matvec",
                  "ccg_dot", "ccg_solve", "ccg_solve_refined", "ccg_solve_batched", "ccg_solve_batched_refined",
-                 "ccg_block_matvec", "ccg_set_option",
+                 "ccg_block_matvec", "ccg_set_option", "ccg_server_create", "ccg_server_submit", "ccg_server_poll",
+                 "ccg_server_wait", "ccg_server_destroy",
                  "ccg_timing_enable", "ccg_timing_read", "ccg_timing_reset"):
         getattr(L, name).restype = i32
     if L.ccg_abi_version() != 1:
@@ -286,5 +313,50 @@ class Operator:
         if getattr(self, "op", None) and self.op.value:
             lib().ccg_op_destroy(self.op)
             self.op = ctypes.c_void_p()
+
+    __del__ = close
+
+
+class Server:
+    """ccg_server_*: a queue of solve requests served by `slots` workers on one
+    GPU under an HBM budget (bytes; 0 = 120 GB)."""
+
+    def __init__(self, device=0, slots=4, budget_bytes=0):
+        sv = ctypes.c_void_p()
+        _check(lib().ccg_server_create(ctypes.byref(sv), int(device), int(slots), int(budget_bytes)))
+        self.sv = sv
+        self._sizes = {}
+
+    def submit(self, kind="dense", n=0, nrhs=1, shift=3.0, seed=0, L=0, kd=0.5, m=1.5 + 0.01j, tol=1e-10,
+               maxit=0, keep_x=False, mode=0):
+        r = Request()
+        r.kind = REQ_DENSE if kind == "dense" else REQ_DIPOLE
+        r.n, r.nrhs, r.shift, r.seed, r.L, r.maxit = int(n), int(nrhs), float(shift), int(seed), int(L), int(maxit)
+        r.kd, r.m_re, r.m_im, r.tol, r.keep_x = float(kd), complex(m).real, complex(m).imag, float(tol), int(keep_x)
+        r.mode = int(mode)
+        t = ctypes.c_int64()
+        _check(lib().ccg_server_submit(self.sv, ctypes.byref(r), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket):
+        d = ctypes.c_int()
+        _check(lib().ccg_server_poll(self.sv, int(ticket), ctypes.byref(d)))
+        return bool(d.value)
+
+    def wait(self, ticket, x_size=0):
+        """Result dict, and the solution (complex128, column-major n x nrhs) if x_size > 0."""
+        res = Result()
+        x = np.zeros(x_size, np.complex128) if x_size else None
+        _check(lib().ccg_server_wait(self.sv, int(ticket), ctypes.byref(res),
+                                     ctypes.c_void_p(x.ctypes.data) if x_size else ctypes.c_void_p(0)))
+        return res.as_dict(), x
+
+    def now(self):
+        return lib().ccg_server_now(self.sv)
+
+    def close(self):
+        if getattr(self, "sv", None) and self.sv.value:
+            lib().ccg_server_destroy(self.sv)
+            self.sv = ctypes.c_void_p()
 
     __del__ = close

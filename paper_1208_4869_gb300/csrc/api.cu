@@ -228,10 +228,7 @@ ccg_status ccg_op_destroy(ccg_operator* op) {
     cudaDeviceSynchronize();
     dipole_free(op);
   }
-  if (op && op->tc_ready) {
-    cudaDeviceSynchronize();
-    tc_free(op);
-  }
+  if (op && op->tc_ready) tc_free(op);  // stream-ordered after the operator's last use
   delete op;
   return CCG_OK;
 }

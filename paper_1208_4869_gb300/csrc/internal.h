@@ -45,6 +45,7 @@ struct ccg_operator {
   bool tc_ready = false;
   int tc_terms = 0;                            // bf16 terms per entry (2 or 3)
   void* tc_ahi = nullptr;                      // the terms, one n x 2n bf16 matrix each
+  cudaStream_t tc_stream = nullptr;            // stream they were allocated (and are freed) on
   alignas(64) unsigned char tc_map[3][128] = {};  // their TMA descriptors
 };
 

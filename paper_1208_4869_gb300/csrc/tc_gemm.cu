@@ -369,7 +369,8 @@ static int tc_product_t(ccg_handle* h, ccg_operator* op, const float2* X, float2
   const size_t abytes = (size_t)n * 2 * n * sizeof(__nv_bfloat16);
   if (op->tc_ready && op->tc_terms != T) tc_free(op);
   if (!op->tc_ready) {
-    if (cudaMalloc(&op->tc_ahi, T * abytes) != cudaSuccess) {
+    op->tc_stream = s;  // stream-ordered: freeing never synchronises the device
+    if (cudaMallocAsync(&op->tc_ahi, T * abytes, s) != cudaSuccess) {
       cudaGetLastError();
       op->tc_ahi = nullptr;
       set_error("tensor-core operand allocation failed");
@@ -455,7 +456,7 @@ int tc_check_error(ccg_handle* h) {
 }
 
 void tc_free(ccg_operator* op) {
-  if (op->tc_ahi) cudaFree(op->tc_ahi);
+  if (op->tc_ahi) cudaFreeAsync(op->tc_ahi, op->tc_stream);
   op->tc_ahi = nullptr;
   op->tc_ready = false;
   op->tc_terms = 0;
