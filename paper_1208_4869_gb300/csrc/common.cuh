@@ -106,7 +106,7 @@ struct SolveState {
   int maxit;
   int half;       // BiCGSTAB took the half-step exit in this iteration
   int zero_rhs;   // y = 0: the host zeroes x
-  int pad;
+  int skip_mv;    // the start vector is zero: the first product is skipped (reset by the first phase)
   double tol;
   double snorm;   // BiCGSTAB ||s|| / ||y||
   // complex method scalars

@@ -52,7 +52,7 @@ static DipGeom geom(const ccg_operator* op) {
 }
 
 __device__ __forceinline__ bool skip_state(const SolveState* st) {
-  return st != nullptr && (st->poll.done || st->half);
+  return st != nullptr && (st->poll.done || st->half || st->skip_mv);
 }
 
 // K1: gather the lattice z-line (i, j) of component q from the site vector,

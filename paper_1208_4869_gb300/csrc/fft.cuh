@@ -167,7 +167,7 @@ template <class R, int N = 0, int BL = 0>
 __global__ void __launch_bounds__(kBlock) fft_strided(cx<R>* __restrict__ data, StridedPass g,
                                                       const cx<R>* __restrict__ W, int sign,
                                                       const SolveState* __restrict__ st) {
-  if (st != nullptr && (st->poll.done || st->half)) return;
+  if (st != nullptr && (st->poll.done || st->half || st->skip_mv)) return;
   extern __shared__ unsigned char smem_raw[];
   const int n = N > 0 ? N : g.n;
   const int ls = N > 0 ? fft_ls<N>() : g.n;

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kBlock) gemv_n_rows(const cx<R>* __restrict__ 
                                                       const SolveState* __restrict__ st) {
   typedef Unit<R, U> Un;
   typedef typename Un::L L;
-  if (st != nullptr && (st->poll.done || st->half)) return;
+  if (st != nullptr && (st->poll.done || st->half || st->skip_mv)) return;
   const int lane = threadIdx.x & 31;
   const int64_t nunits = n / U;
   const L* xv = reinterpret_cast<const L*>(x);
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kBlock) gemv_tile(const cx<R>* __restrict__ A,
   typedef Unit<R, U> Un;
   typedef typename Un::L L;
   constexpr int CBU = 32 * E;  // units per column chunk
-  if (st != nullptr && (st->poll.done || st->half)) return;
+  if (st != nullptr && (st->poll.done || st->half || st->skip_mv)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t nunits = n / U;
   const int64_t unit0 = (int64_t)blockIdx.x * CBU;
