@@ -3,44 +3,61 @@
 // sides stored row-major (row i holds the k values of unknown i, leading
 // dimension k), in complex128 or complex64.
 //
-// A block computes a 64 x 64 tile of C; each of its 256 threads owns a 4 x 4
-// sub-tile (16 complex accumulators in registers).  K advances 8 complex
-// values at a time through shared memory (A transposed so that a thread's
-// four rows are one broadcast-friendly load).  complex128 is bound by the
-// FP64 pipe (4 DFMA per complex multiply-add); complex64 by the FP32 pipe.
+// A block of 16 x 16 threads computes a (16 TM) x (16 TN) tile of C; each
+// thread owns a TM x TN sub-tile of complex accumulators in registers.  K
+// advances 8 complex values at a time through shared memory (A transposed so
+// that a thread's rows are one broadcast-friendly load).  complex128 is bound
+// by the FP64 pipe (4 DFMA per complex multiply-add); complex64 by the FP32
+// pipe.
 #pragma once
 
 #include "common.cuh"
 
 namespace ccg {
 
-constexpr int kGemmBM = 64, kGemmBN = 64, kGemmBK = 8;
+// Tile shape per precision: complex64 64 x 64 (4 x 4 per thread, FP32 pipe
+// and shared-memory bandwidth balanced); complex128 32 x 32 (2 x 2 per
+// thread): the FP64 pipe is so much slower than shared memory that smaller
+// tiles cost nothing, and 4x more blocks fill the 152 SMs in ~14 waves
+// instead of ~3.4 (a partial last wave alone cost 16%).
+template <class R> struct GemmTile;
+template <> struct GemmTile<float> { static constexpr int TM = 4, TN = 4; };
+template <> struct GemmTile<double> { static constexpr int TM = 2, TN = 2; };
+constexpr int kGemmBK = 8;
+template <class R> constexpr int gemm_bm() { return 16 * GemmTile<R>::TM; }
+template <class R> constexpr int gemm_bn() { return 16 * GemmTile<R>::TN; }
 
 template <class R>
 __global__ void __launch_bounds__(kBlock) cgemm_rows(const cx<R>* __restrict__ A, int64_t lda,
                                                      const cx<R>* __restrict__ B, cx<R>* __restrict__ C, int64_t n,
                                                      int k, const int* __restrict__ skip) {
+  constexpr int TM = GemmTile<R>::TM, TN = GemmTile<R>::TN;
+  constexpr int BM = 16 * TM, BN = 16 * TN;
+  constexpr int A_PER = BM * kGemmBK / kBlock, B_PER = kGemmBK * BN / kBlock;
   if (skip != nullptr && *skip) return;
-  __shared__ cx<R> As[kGemmBK][kGemmBM];
-  __shared__ cx<R> Bs[kGemmBK][kGemmBN];
+  __shared__ cx<R> As[kGemmBK][BM];
+  __shared__ cx<R> Bs[kGemmBK][BN];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  const int64_t row0 = (int64_t)blockIdx.y * kGemmBM;
-  const int col0 = blockIdx.x * kGemmBN;
-  cx<R> acc[4][4];
+  const int64_t row0 = (int64_t)blockIdx.y * BM;
+  const int col0 = blockIdx.x * BN;
+  cx<R> acc[TM][TN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = mk<R>(0, 0);
+    for (int j = 0; j < TN; ++j) acc[i][j] = mk<R>(0, 0);
 
-  // load mapping: A tile 64 rows x 8 k, B tile 8 k x 64 cols, two elements per thread each
   for (int64_t k0 = 0; k0 < n; k0 += kGemmBK) {
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int idx = threadIdx.x + e * kBlock;        // 0..511
-      const int ar = idx / kGemmBK, ak = idx % kGemmBK; // A: row-major reads along k
+    for (int e = 0; e < A_PER; ++e) {
+      const int idx = threadIdx.x + e * kBlock;
+      const int ar = idx / kGemmBK, ak = idx % kGemmBK;   // A: row-major reads along k
       const int64_t gr = row0 + ar, gk = k0 + ak;
       As[ak][ar] = (gr < n && gk < n) ? A[gr * lda + gk] : mk<R>(0, 0);
-      const int bk = idx / kGemmBN, bc = idx % kGemmBN; // B: rows of k values
+    }
+#pragma unroll
+    for (int e = 0; e < B_PER; ++e) {
+      const int idx = threadIdx.x + e * kBlock;
+      const int bk = idx / BN, bc = idx % BN;             // B: rows of k values
       const int64_t gbk = k0 + bk;
       const int gc = col0 + bc;
       Bs[bk][bc] = (gbk < n && gc < k) ? B[gbk * k + gc] : mk<R>(0, 0);
@@ -48,25 +65,25 @@ __global__ void __launch_bounds__(kBlock) cgemm_rows(const cx<R>* __restrict__ A
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < kGemmBK; ++kk) {
-      cx<R> a[4], b[4];
+      cx<R> a[TM], b[TN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = cfma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < TN; ++j) acc[i][j] = cfma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int64_t gr = row0 + ty * 4 + i;
+  for (int i = 0; i < TM; ++i) {
+    const int64_t gr = row0 + ty * TM + i;
     if (gr >= n) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int gc = col0 + tx * 4 + j;
+    for (int j = 0; j < TN; ++j) {
+      const int gc = col0 + tx * TN + j;
       if (gc < k) C[gr * k + gc] = acc[i][j];
     }
   }
