@@ -295,7 +295,9 @@ typedef struct {
 } ccg_result;
 
 /* Create a server on CUDA device `device` with `slots` workers (1..32) and
- * an HBM budget in bytes for admitted requests (0: 120 GB). */
+ * an HBM budget in bytes for admitted requests (0: 120 GB).  Returns once
+ * every slot has its stream and handle, so slot set-up is not part of any
+ * request's latency. */
 ccg_status ccg_server_create(ccg_server** s, int device, int slots, uint64_t hbm_budget_bytes);
 /* Queue a request; *ticket identifies it.  Never blocks on the GPU. */
 ccg_status ccg_server_submit(ccg_server* s, const ccg_request* req, int64_t* ticket);

@@ -128,6 +128,7 @@ struct ccg_server {
   int64_t next_ticket = 1;
   bool stop = false;
   int running = 0;
+  int ready = 0;  // slots whose stream and handle exist
   std::vector<std::thread> workers;
 
   double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
@@ -317,6 +318,11 @@ void worker(ccg_server* sv, int slot) {
   cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
   ccg_handle* h = nullptr;
   ccg_create(&h, s);
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    ++sv->ready;
+  }
+  sv->cv.notify_all();
   std::map<int, DipoleOps> cache;
   for (;;) {
     std::shared_ptr<Entry> e;
@@ -385,6 +391,12 @@ ccg_status ccg_server_create(ccg_server** out, int device, int slots, uint64_t b
   sv->budget = budget ? budget : (uint64_t)120 << 30;
   sv->t0 = Clock::now();
   for (int i = 0; i < slots; ++i) sv->workers.emplace_back(worker, sv, i);
+  {
+    // return once every slot can take work, so that slot set-up is not
+    // charged to the first requests' latency
+    std::unique_lock<std::mutex> lk(sv->mu);
+    sv->cv.wait(lk, [&] { return sv->ready == slots; });
+  }
   *out = sv;
   return CCG_OK;
 }

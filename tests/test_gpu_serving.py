@@ -68,9 +68,10 @@ def test_budget_admission_serialises(ccg):
     for a, b in zip(res, res[1:]):
         assert b["t_start"] >= a["t_done"] - 1e-6
     sv = ccg.Server(slots=4)
-    ts = [sv.submit(kind="dense", n=n, nrhs=1, seed=20 + i, tol=1e-10) for i in range(4)]
+    ts = [sv.submit(kind="dense", n=2048, nrhs=1, seed=20 + i, tol=1e-10) for i in range(4)]
     res = sorted((sv.wait(t)[0] for t in ts), key=lambda d: d["t_start"])
     sv.close()
+    assert len({r["slot"] for r in res}) > 1
     assert any(b["t_start"] < a["t_done"] for a, b in zip(res, res[1:]))   # overlap when the budget allows
 
 
