@@ -200,7 +200,18 @@ def profiled_traffic(kernel, src_files):
 SWEEP_KERNELS = {0: ("gemv_n_rows", 1), 1: ("gemv_tile_c", 1), 2: ("gemv_tile_both", 2), 3: ("cgemm_rows", 1)}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flops x max SM clock
 DIPOLE_KERNELS = {0: ("dipole_fft_matvec", 1), 1: ("dipole_fft_matvec_h", 1), 2: ("dipole_fft_both", 2)}
-KERNEL_SOURCES = ["paper_1208_4869_gb300/csrc/gemv.cuh", "paper_1208_4869_gb300/csrc/common.cuh"]
+CSRC = "paper_1208_4869_gb300/csrc/"
+
+
+def kernel_sources(tag):
+    """Source files whose change invalidates the recorded traffic of a kernel."""
+    if tag.startswith("cgemm_rows"):
+        files = ["blockmv.cuh"]
+    elif tag.startswith("dipole"):
+        files = ["fft.cuh", "dipole.cu"]
+    else:
+        files = ["gemv.cuh"]
+    return [CSRC + f for f in files + ["common.cuh"]]
 
 
 def roofline(ccg, sweep_stats, n, dipole=False, nrhs=1):
@@ -223,7 +234,7 @@ def roofline(ccg, sweep_stats, n, dipole=False, nrhs=1):
     top = max(kinds, key=lambda k: kinds[k]["total_ms"])
     k = kinds[top]
     hbm, hbm_src = peaks()
-    traffic = profiled_traffic(top, KERNEL_SOURCES)
+    traffic = profiled_traffic(top, kernel_sources(top))
     if top.endswith("c128") and not dipole:   # FP64 FMA pipe bound (4 DFMA per 16-byte element)
         roof = {"kernel": top, "bound": "alu", "achieved": k["tflops"], "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": k["tflops"] / FP64_PEAK_TFLOPS,
@@ -503,7 +514,10 @@ def run_ours(args):
         return step
 
     runs = {}
-    for path in [headline] + [p for p in ("mixed", "fp64") if p != headline]:
+    # auto: the mixed headline plus the complex128 path for comparison; an
+    # explicit --path runs that path alone
+    paths = [headline] + ([p for p in ("mixed", "fp64") if p != headline] if args.path == "auto" else [])
+    for path in paths:
         step = make_step(path)
         for _ in range(args.warmup):
             step()
