@@ -24,7 +24,7 @@ struct DipoleData {
   double alpha_inv[2] = {0.0, 0.0};
   int* idx = nullptr;           // site number of each lattice cell, or -1
   void* work = nullptr;         // 3 FFT grids
-  void* ghat = nullptr;         // 6 transformed field-tensor components
+  void* ghat = nullptr;         // octant (0..M/2 per axis) of the 6 transformed field-tensor components
   void* tw[3] = {nullptr, nullptr, nullptr};  // twiddle tables along x, y, z
   int bl = 8;                   // lines per block of the FFT passes
   double sweep_bytes = 0.0;     // algorithmic bytes of one application
