@@ -67,18 +67,20 @@ __device__ __forceinline__ bool skip_state(const SolveState* st) {
   return st != nullptr && (st->poll.done || st->half || st->skip_mv);
 }
 
+// ---------------------------------------------------------------------------
+// Runtime-length kernels (FFT lengths without a register factorisation):
+// shared-memory Stockham transforms, bl lines per block.
+
 // K1: gather the lattice z-line (i, j) of component q from the site vector,
 // zero-pad to Mz, forward FFT, store grid[q][i][j][:].
-template <class R, int N, int BL>
+template <class R>
 __global__ void __launch_bounds__(kBlock) dip_fwd_z(const cx<R>* __restrict__ x, cx<R>* __restrict__ grid,
-                                                    const int* __restrict__ idx, DipGeom g, int bl_rt,
+                                                    const int* __restrict__ idx, DipGeom g, int bl,
                                                     const cx<R>* __restrict__ W, int conj_in,
                                                     const SolveState* __restrict__ st) {
   if (skip_state(st)) return;
   extern __shared__ unsigned char smem_raw[];
-  const int Mz = N > 0 ? N : g.Mz;
-  const int ls = N > 0 ? fft_ls<N>() : g.Mz;
-  const int bl = BL > 0 ? BL : bl_rt;
+  const int Mz = g.Mz, ls = g.Mz;
   cx<R>* buf0 = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* buf1 = buf0 + bl * ls;
   const int q = blockIdx.y;
@@ -99,7 +101,7 @@ __global__ void __launch_bounds__(kBlock) dip_fwd_z(const cx<R>* __restrict__ x,
     buf0[b * ls + l] = v;
   }
   __syncthreads();
-  const cx<R>* res = fft_lines<R, N, BL>(buf0, buf1, Mz, bl, W, -1);
+  const cx<R>* res = block_fft<R>(buf0, buf1, Mz, bl, W, -1);
   cx<R>* gq = grid + (int64_t)q * g.G;
   for (int t = threadIdx.x; t < bl * Mz; t += blockDim.x) {
     const int b = t / Mz, kz = t - b * Mz;
@@ -113,15 +115,13 @@ __global__ void __launch_bounds__(kBlock) dip_fwd_z(const cx<R>* __restrict__ x,
 
 // K3: x-lines (ky, kz0 .. kz0+bl-1) of all three components: forward FFT
 // (input i < nx), tensor multiply, inverse FFT, store i < nx.
-template <class R, int N, int BL>
+template <class R>
 __global__ void __launch_bounds__(kBlock) dip_x_mul(cx<R>* __restrict__ grid, const cx<R>* __restrict__ ghat,
-                                                    DipGeom g, int bl_rt, const cx<R>* __restrict__ W,
+                                                    DipGeom g, int bl, const cx<R>* __restrict__ W,
                                                     const SolveState* __restrict__ st) {
   if (skip_state(st)) return;
   extern __shared__ unsigned char smem_raw[];
-  const int Mx = N > 0 ? N : g.Mx;
-  const int ls = N > 0 ? fft_ls<N>() : g.Mx;
-  const int bl = BL > 0 ? BL : bl_rt;
+  const int Mx = g.Mx, ls = g.Mx;
   const int per = bl * ls;                      // one component's lines
   cx<R>* buf0 = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* buf1 = buf0 + 3 * per;
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kBlock) dip_x_mul(cx<R>* __restrict__ grid, co
     buf0[q * per + b * ls + i] = v;
   }
   __syncthreads();
-  cx<R>* fw = fft_lines<R, N, 3 * BL>(buf0, buf1, Mx, 3 * bl, W, -1);
+  cx<R>* fw = block_fft<R>(buf0, buf1, Mx, 3 * bl, W, -1);
   cx<R>* other = fw == buf0 ? buf1 : buf0;
   for (int t = threadIdx.x; t < bl * Mx; t += blockDim.x) {
     const int b = t % bl, kx = t / bl;
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kBlock) dip_x_mul(cx<R>* __restrict__ grid, co
     }
   }
   __syncthreads();
-  const cx<R>* res = fft_lines<R, N, 3 * BL>(fw, other, Mx, 3 * bl, W, +1);
+  const cx<R>* res = block_fft<R>(fw, other, Mx, 3 * bl, W, +1);
   for (int t = threadIdx.x; t < 3 * bl * g.nx; t += blockDim.x) {
     const int q = t / (bl * g.nx), r = t - q * (bl * g.nx);
     const int b = r % bl, i = r / bl;
@@ -172,16 +172,14 @@ __global__ void __launch_bounds__(kBlock) dip_x_mul(cx<R>* __restrict__ grid, co
 
 // K5: inverse FFT of z-line (i, j) of component q, then for occupied sites
 // y = x / alpha - (G * x) (conjugated in and out for A^H).
-template <class R, int N, int BL>
+template <class R>
 __global__ void __launch_bounds__(kBlock) dip_inv_z(const cx<R>* __restrict__ x, cx<R>* __restrict__ y,
                                                     cx<R>* __restrict__ grid, const int* __restrict__ idx, DipGeom g,
-                                                    int bl_rt, const cx<R>* __restrict__ W, cx<R> alpha_inv, int conj,
+                                                    int bl, const cx<R>* __restrict__ W, cx<R> alpha_inv, int conj,
                                                     const SolveState* __restrict__ st) {
   if (skip_state(st)) return;
   extern __shared__ unsigned char smem_raw[];
-  const int Mz = N > 0 ? N : g.Mz;
-  const int ls = N > 0 ? fft_ls<N>() : g.Mz;
-  const int bl = BL > 0 ? BL : bl_rt;
+  const int Mz = g.Mz, ls = g.Mz;
   cx<R>* buf0 = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* buf1 = buf0 + bl * ls;
   const int q = blockIdx.y;
@@ -199,7 +197,7 @@ __global__ void __launch_bounds__(kBlock) dip_inv_z(const cx<R>* __restrict__ x,
     buf0[b * ls + kz] = v;
   }
   __syncthreads();
-  const cx<R>* res = fft_lines<R, N, BL>(buf0, buf1, Mz, bl, W, +1);
+  const cx<R>* res = block_fft<R>(buf0, buf1, Mz, bl, W, +1);
   const cx<R>* xq = x + (int64_t)q * g.N;
   cx<R>* yq = y + (int64_t)q * g.N;
   for (int t = threadIdx.x; t < bl * g.nz; t += blockDim.x) {
@@ -211,6 +209,206 @@ __global__ void __launch_bounds__(kBlock) dip_inv_z(const cx<R>* __restrict__ x,
         cx<R> xi = xq[s];
         if (conj) xi = cconj(xi);
         cx<R> v = csub(cmul(alpha_inv, xi), res[b * ls + l]);
+        if (conj) v = cconj(v);
+        yq[s] = v;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Register-FFT kernels (lengths with a factorisation in fft.cuh).  BL lattice
+// lines per block, one line per lane, so that global accesses along the
+// lines' common contiguous axis coalesce.
+
+// Lines per block: 32 (complex64) / 16 (complex128): 256 contiguous bytes per warp access.
+template <class R> constexpr int reg_bl() { return sizeof(R) == 4 ? 32 : 16; }
+// Shared memory of the z kernels: staging U (N rows of BL + 1, an odd stride
+// so the transposes are conflict-free) and the exchange buffer E (N x BL).
+template <class R, int N> constexpr size_t z_reg_smem() {
+  return (size_t)N * (reg_bl<R>() + 1) * sizeof(cx<R>) + (size_t)N * reg_bl<R>() * sizeof(cx<R>);
+}
+
+// K1: gather the z-lines of BL lattice columns (i, j) from the site vector
+// into shared memory (coalesced along z), forward z FFT, store the
+// transformed lines through shared memory (coalesced along z).
+template <class R, int N>
+__global__ void __launch_bounds__(kBlock) dip_fwd_z_reg(const cx<R>* __restrict__ x, cx<R>* __restrict__ grid,
+                                                        const int* __restrict__ idx, DipGeom g,
+                                                        const cx<R>* __restrict__ W, int conj_in,
+                                                        const SolveState* __restrict__ st) {
+  if (skip_state(st)) return;
+  constexpr int BL = reg_bl<R>(), LS = BL + 1, NZ = N / 2;
+  extern __shared__ unsigned char smem_raw[];
+  cx<R>* U = reinterpret_cast<cx<R>*>(smem_raw);
+  cx<R>* E = U + N * LS;
+  const int q = blockIdx.y;
+  const int64_t nlines = (int64_t)g.nx * g.ny;
+  const int64_t l0 = (int64_t)blockIdx.x * BL;
+  const cx<R>* xq = x + (int64_t)q * g.N;
+  for (int t = threadIdx.x; t < BL * NZ; t += kBlock) {
+    const int z = t % NZ, b = t / NZ;
+    const int64_t line = l0 + b;
+    cx<R> v = mk<R>(0, 0);
+    if (line < nlines) {
+      const int s = __ldg(&idx[line * NZ + z]);
+      if (s >= 0) {
+        v = xq[s];
+        if (conj_in) v = cconj(v);
+      }
+    }
+    U[z * LS + b] = v;
+  }
+  __syncthreads();
+  auto load = [&](int j, int b) { return U[j * LS + b]; };
+  auto store = [&](int k, int b, cx<R> v) { U[k * LS + b] = v; };
+  fft2<R, N, BL, -1, NZ, N>(load, store, E, W);
+  __syncthreads();
+  cx<R>* gq = grid + (int64_t)q * g.G;
+  for (int t = threadIdx.x; t < BL * N; t += kBlock) {
+    const int kz = t % N, b = t / N;
+    const int64_t line = l0 + b;
+    if (line < nlines) {
+      const int64_t i = line / g.ny, j = line - i * g.ny;
+      gq[(i * g.My + j) * N + kz] = U[kz * LS + b];
+    }
+  }
+}
+
+// K3: x-lines (ky, kz0 .. kz0 + BL - 1) of the three components.  Forward
+// step 1 over the input i < nx; then each thread, for its (line, k1), takes
+// forward step 2, the tensor multiply Y_a = sum_b Ghat_ab X_b at the N2
+// frequencies k1 + N1 k2 it holds, and inverse step 1, in place in the
+// exchange buffer; inverse step 2 stores the outputs i < nx.
+template <class R, int N>
+__global__ void __launch_bounds__(kBlock) dip_x_mul_reg(cx<R>* __restrict__ grid, const cx<R>* __restrict__ ghat,
+                                                        DipGeom g, const cx<R>* __restrict__ W,
+                                                        const SolveState* __restrict__ st) {
+  if (skip_state(st)) return;
+  constexpr int BL = reg_bl<R>(), N1 = Fac<N>::N1, N2 = Fac<N>::N2, CS = N * BL;
+  static_assert(N1 % 2 == 0, "the input and output halves need an even N1");
+  extern __shared__ unsigned char smem_raw[];
+  cx<R>* E = reinterpret_cast<cx<R>*>(smem_raw);  // [component][k1][j2][line]
+  const int cblocks = (g.Mz + BL - 1) / BL;
+  const int ky = blockIdx.x / cblocks;
+  const int kz0 = (blockIdx.x - ky * cblocks) * BL;
+  const int nb = min(BL, g.Mz - kz0);
+  const int64_t sx = (int64_t)g.My * g.Mz;
+  const int64_t off = (int64_t)ky * g.Mz + kz0;
+#pragma unroll 1
+  for (int t = threadIdx.x; t < 3 * BL * N2; t += kBlock) {
+    const int b = t % BL, j2 = (t / BL) % N2, q = t / (BL * N2);
+    const cx<R>* src = grid + (int64_t)q * g.G + off + b;
+    cx<R> u[N1];
+#pragma unroll
+    for (int j1 = 0; j1 < N1; ++j1)
+      u[j1] = (j1 < N1 / 2 && b < nb) ? src[(int64_t)(N2 * j1 + j2) * sx] : mk<R>(0, 0);
+    dft<N1, -1, R>(u);
+    cx<R>* Eq = E + q * CS;
+    Eq[j2 * BL + b] = u[0];
+#pragma unroll
+    for (int k1 = 1; k1 < N1; ++k1) Eq[(k1 * N2 + j2) * BL + b] = cmul(u[k1], line_tw<-1, R>(W, j2 * k1));
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int t = threadIdx.x; t < BL * N1; t += kBlock) {
+    const int b = t % BL, k1 = t / BL;
+    cx<R> X[3][N2];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+#pragma unroll
+      for (int j2 = 0; j2 < N2; ++j2) X[q][j2] = E[q * CS + (k1 * N2 + j2) * BL + b];
+      dft<N2, -1, R>(X[q]);
+    }
+    if (b < nb) {
+      const int kz = kz0 + b;
+      const bool fy = ky > g.ny, fz = kz > g.nz;
+      const int64_t hyz = (int64_t)(fy ? g.My - ky : ky) * g.Hz + (fz ? g.Mz - kz : kz);
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        const int kx = k1 + N1 * k2;
+        const bool fx = kx > g.nx;
+        const int64_t hi = (int64_t)(fx ? g.Mx - kx : kx) * g.Hy * g.Hz + hyz;
+        cx<R> c[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) c[k] = __ldg(&ghat[(int64_t)k * g.H + hi]);
+        if (fx ^ fy) c[1] = cscale((R)-1, c[1]);
+        if (fx ^ fz) c[2] = cscale((R)-1, c[2]);
+        if (fy ^ fz) c[4] = cscale((R)-1, c[4]);
+        const cx<R> X0 = X[0][k2], X1 = X[1][k2], X2 = X[2][k2];
+        // components xx, xy, xz, yy, yz, zz
+        X[0][k2] = cfma(c[2], X2, cfma(c[1], X1, cmul(c[0], X0)));
+        X[1][k2] = cfma(c[4], X2, cfma(c[3], X1, cmul(c[1], X0)));
+        X[2][k2] = cfma(c[5], X2, cfma(c[4], X1, cmul(c[2], X0)));
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      dft<N2, +1, R>(X[q]);
+      E[q * CS + (k1 * N2) * BL + b] = X[q][0];
+#pragma unroll
+      for (int n1 = 1; n1 < N2; ++n1) E[q * CS + (k1 * N2 + n1) * BL + b] = cmul(X[q][n1], line_tw<+1, R>(W, k1 * n1));
+    }
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int t = threadIdx.x; t < 3 * BL * N2; t += kBlock) {
+    const int b = t % BL, n1 = (t / BL) % N2, q = t / (BL * N2);
+    cx<R> v[N1];
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) v[k1] = E[q * CS + (k1 * N2 + n1) * BL + b];
+    dft<N1, +1, R>(v);
+    if (b < nb) {
+      cx<R>* dst = grid + (int64_t)q * g.G + off + b;
+#pragma unroll
+      for (int n2 = 0; n2 < N1 / 2; ++n2) dst[(int64_t)(n1 + N2 * n2) * sx] = v[n2];
+    }
+  }
+}
+
+// K5: the transformed z-lines of BL lattice columns through shared memory
+// (coalesced along z), inverse z FFT, then for occupied sites
+// y = x / alpha - (G * x) (conjugated in and out for A^H), coalesced along z.
+template <class R, int N>
+__global__ void __launch_bounds__(kBlock) dip_inv_z_reg(const cx<R>* __restrict__ x, cx<R>* __restrict__ y,
+                                                        const cx<R>* __restrict__ grid, const int* __restrict__ idx,
+                                                        DipGeom g, const cx<R>* __restrict__ W, cx<R> alpha_inv,
+                                                        int conj, const SolveState* __restrict__ st) {
+  if (skip_state(st)) return;
+  constexpr int BL = reg_bl<R>(), LS = BL + 1, NZ = N / 2;
+  extern __shared__ unsigned char smem_raw[];
+  cx<R>* U = reinterpret_cast<cx<R>*>(smem_raw);
+  cx<R>* E = U + N * LS;
+  const int q = blockIdx.y;
+  const int64_t nlines = (int64_t)g.nx * g.ny;
+  const int64_t l0 = (int64_t)blockIdx.x * BL;
+  const cx<R>* gq = grid + (int64_t)q * g.G;
+  for (int t = threadIdx.x; t < BL * N; t += kBlock) {
+    const int kz = t % N, b = t / N;
+    const int64_t line = l0 + b;
+    cx<R> v = mk<R>(0, 0);
+    if (line < nlines) {
+      const int64_t i = line / g.ny, j = line - i * g.ny;
+      v = gq[(i * g.My + j) * N + kz];
+    }
+    U[kz * LS + b] = v;
+  }
+  __syncthreads();
+  auto load = [&](int j, int b) { return U[j * LS + b]; };
+  auto store = [&](int k, int b, cx<R> v) { U[k * LS + b] = v; };
+  fft2<R, N, BL, +1, N, NZ>(load, store, E, W);
+  __syncthreads();
+  const cx<R>* xq = x + (int64_t)q * g.N;
+  cx<R>* yq = y + (int64_t)q * g.N;
+  for (int t = threadIdx.x; t < BL * NZ; t += kBlock) {
+    const int z = t % NZ, b = t / NZ;
+    const int64_t line = l0 + b;
+    if (line < nlines) {
+      const int s = __ldg(&idx[line * NZ + z]);
+      if (s >= 0) {
+        cx<R> xi = xq[s];
+        if (conj) xi = cconj(xi);
+        cx<R> v = csub(cmul(alpha_inv, xi), U[z * LS + b]);
         if (conj) v = cconj(v);
         yq[s] = v;
       }
@@ -325,8 +523,8 @@ static int strided_launch_d(double2* data, const StridedPass& p, int ncomp, cons
                             cudaStream_t s) {
   const int cblocks = (p.nc + p.bl - 1) / p.bl;
   const size_t smem = (size_t)2 * p.bl * p.n * sizeof(double2);
-  if (set_smem<double>((const void*)fft_strided<double, 0, 0>, smem) != CCG_OK) return CCG_ERR_CUDA;
-  fft_strided<double, 0, 0><<<dim3(p.na * cblocks, ncomp), kBlock, smem, s>>>(data, p, W, sign, nullptr);
+  if (set_smem<double>((const void*)fft_strided<double>, smem) != CCG_OK) return CCG_ERR_CUDA;
+  fft_strided<double><<<dim3(p.na * cblocks, ncomp), kBlock, smem, s>>>(data, p, W, sign, nullptr);
   return CCG_OK;
 }
 
@@ -405,10 +603,10 @@ template <class R> static int create_t(ccg_operator* op, const uint8_t* occ, cud
   // opt in to large dynamic shared memory for the runtime-size kernels
   const int M = std::max(g.Mx, std::max(g.My, g.Mz));
   const size_t sm1 = (size_t)2 * bl * M * sizeof(cx<R>), sm3 = 3 * sm1;
-  if (set_smem<R>((const void*)dip_fwd_z<R, 0, 0>, sm1) != CCG_OK) return CCG_ERR_CUDA;
-  if (set_smem<R>((const void*)dip_inv_z<R, 0, 0>, sm1) != CCG_OK) return CCG_ERR_CUDA;
-  if (set_smem<R>((const void*)fft_strided<R, 0, 0>, sm1) != CCG_OK) return CCG_ERR_CUDA;
-  if (set_smem<R>((const void*)dip_x_mul<R, 0, 0>, sm3) != CCG_OK) return CCG_ERR_CUDA;
+  if (set_smem<R>((const void*)dip_fwd_z<R>, sm1) != CCG_OK) return CCG_ERR_CUDA;
+  if (set_smem<R>((const void*)dip_inv_z<R>, sm1) != CCG_OK) return CCG_ERR_CUDA;
+  if (set_smem<R>((const void*)fft_strided<R>, sm1) != CCG_OK) return CCG_ERR_CUDA;
+  if (set_smem<R>((const void*)dip_x_mul<R>, sm3) != CCG_OK) return CCG_ERR_CUDA;
   // algorithmic bytes of one application (each pass reads and writes its
   // pruned region once; the field-tensor octant is read once)
   const double e = sizeof(cx<R>);
@@ -439,70 +637,95 @@ void dipole_free(ccg_operator* op) {
   op->dip.work = op->dip.ghat = nullptr;
 }
 
-// Lines per block of each pass for FFT length N: z-lines (K1, K5) about
-// 1024 points per block; strided y passes 16 (complex64) / 8 (complex128)
-// consecutive lines; the three-component x pass 8 / 4.  At N = 128 each
-// keeps shared memory at or below 48 KB.
-template <class R, int N> constexpr int bl_z() { return N >= 1024 ? 1 : 1024 / N; }
-template <class R> constexpr int bl_y() { return sizeof(R) == 4 ? 16 : 8; }
-template <class R> constexpr int bl_x() { return sizeof(R) == 4 ? 8 : 4; }
-
 template <class F> static void smem_opt_in(F* fn, size_t bytes, bool& done) {
   if (!done && bytes > 48 * 1024) cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   done = true;
 }
 
+// Launchers: N > 0 selects the register kernels of that length, N == 0 the
+// runtime-length kernels (op->dip.bl lines per block).
 template <class R, int N>
 static void k1(const cx<R>* x, cx<R>* grid, const ccg_operator* op, const DipGeom& g, const cx<R>* W, int conj,
                const SolveState* st, cudaStream_t s) {
-  constexpr int BL = N > 0 ? bl_z<R, N>() : 0;
-  const int bl = N > 0 ? BL : op->dip.bl;
   const int64_t nlines = (int64_t)g.nx * g.ny;
-  const size_t sm = (size_t)2 * bl * (N > 0 ? fft_ls<N>() : g.Mz) * sizeof(cx<R>);
   static bool opted = false;
-  smem_opt_in(dip_fwd_z<R, N, BL>, sm, opted);
-  dip_fwd_z<R, N, BL><<<dim3((unsigned)((nlines + bl - 1) / bl), 3), kBlock, sm, s>>>(x, grid, op->dip.idx, g, bl, W,
-                                                                                      conj, st);
+  if constexpr (N > 0) {
+    constexpr int BL = reg_bl<R>();
+    constexpr size_t sm = z_reg_smem<R, N>();
+    smem_opt_in(dip_fwd_z_reg<R, N>, sm, opted);
+    dip_fwd_z_reg<R, N><<<dim3((unsigned)((nlines + BL - 1) / BL), 3), kBlock, sm, s>>>(x, grid, op->dip.idx, g, W,
+                                                                                       conj, st);
+  } else {
+    const int bl = op->dip.bl;
+    const size_t sm = (size_t)2 * bl * g.Mz * sizeof(cx<R>);
+    dip_fwd_z<R><<<dim3((unsigned)((nlines + bl - 1) / bl), 3), kBlock, sm, s>>>(x, grid, op->dip.idx, g, bl, W,
+                                                                                 conj, st);
+  }
 }
 template <class R, int N>
 static void k5(const cx<R>* x, cx<R>* y, cx<R>* grid, const ccg_operator* op, const DipGeom& g, const cx<R>* W,
                cx<R> ainv, int conj, const SolveState* st, cudaStream_t s) {
-  constexpr int BL = N > 0 ? bl_z<R, N>() : 0;
-  const int bl = N > 0 ? BL : op->dip.bl;
   const int64_t nlines = (int64_t)g.nx * g.ny;
-  const size_t sm = (size_t)2 * bl * (N > 0 ? fft_ls<N>() : g.Mz) * sizeof(cx<R>);
   static bool opted = false;
-  smem_opt_in(dip_inv_z<R, N, BL>, sm, opted);
-  dip_inv_z<R, N, BL><<<dim3((unsigned)((nlines + bl - 1) / bl), 3), kBlock, sm, s>>>(x, y, grid, op->dip.idx, g, bl,
-                                                                                      W, ainv, conj, st);
+  if constexpr (N > 0) {
+    constexpr int BL = reg_bl<R>();
+    constexpr size_t sm = z_reg_smem<R, N>();
+    smem_opt_in(dip_inv_z_reg<R, N>, sm, opted);
+    dip_inv_z_reg<R, N><<<dim3((unsigned)((nlines + BL - 1) / BL), 3), kBlock, sm, s>>>(x, y, grid, op->dip.idx, g,
+                                                                                       W, ainv, conj, st);
+  } else {
+    const int bl = op->dip.bl;
+    const size_t sm = (size_t)2 * bl * g.Mz * sizeof(cx<R>);
+    dip_inv_z<R><<<dim3((unsigned)((nlines + bl - 1) / bl), 3), kBlock, sm, s>>>(x, y, grid, op->dip.idx, g, bl, W,
+                                                                                 ainv, conj, st);
+  }
 }
 template <class R, int N>
 static void ky(cx<R>* grid, const ccg_operator* op, const DipGeom& g, const cx<R>* W, int sign,
                const SolveState* st, cudaStream_t s) {
-  constexpr int BL = N > 0 ? bl_y<R>() : 0;
-  const int bl = N > 0 ? BL : op->dip.bl;
-  StridedPass p = {g.G, (int64_t)g.My * g.Mz, g.Mz, g.nx, g.Mz, g.My, sign < 0 ? g.ny : g.My,
-                   sign < 0 ? g.My : g.ny, bl};
-  const int cb = (g.Mz + bl - 1) / bl;
-  const size_t sm = (size_t)2 * bl * (N > 0 ? fft_ls<N>() : g.My) * sizeof(cx<R>);
-  static bool opted = false;
-  smem_opt_in(fft_strided<R, N, BL>, sm, opted);
-  fft_strided<R, N, BL><<<dim3(g.nx * cb, 3), kBlock, sm, s>>>(grid, p, W, sign, st);
+  static bool opted_f = false, opted_i = false;
+  if constexpr (N > 0) {
+    constexpr int BL = reg_bl<R>();
+    StridedPass p = {g.G, (int64_t)g.My * g.Mz, g.Mz, g.nx, g.Mz, N, 0, 0, BL};
+    const int cb = (g.Mz + BL - 1) / BL;
+    constexpr size_t sm = (size_t)N * BL * sizeof(cx<R>);
+    const dim3 grd((unsigned)(g.nx * cb), 3);
+    if (sign < 0) {
+      smem_opt_in(fft_strided_reg<R, N, BL, -1, N / 2, N>, sm, opted_f);
+      fft_strided_reg<R, N, BL, -1, N / 2, N><<<grd, kBlock, sm, s>>>(grid, p, W, st);
+    } else {
+      smem_opt_in(fft_strided_reg<R, N, BL, +1, N, N / 2>, sm, opted_i);
+      fft_strided_reg<R, N, BL, +1, N, N / 2><<<grd, kBlock, sm, s>>>(grid, p, W, st);
+    }
+  } else {
+    const int bl = op->dip.bl;
+    StridedPass p = {g.G, (int64_t)g.My * g.Mz, g.Mz, g.nx, g.Mz, g.My, sign < 0 ? g.ny : g.My,
+                     sign < 0 ? g.My : g.ny, bl};
+    const int cb = (g.Mz + bl - 1) / bl;
+    const size_t sm = (size_t)2 * bl * g.My * sizeof(cx<R>);
+    fft_strided<R><<<dim3(g.nx * cb, 3), kBlock, sm, s>>>(grid, p, W, sign, st);
+  }
 }
 template <class R, int N>
 static void k3(cx<R>* grid, const ccg_operator* op, const DipGeom& g, const cx<R>* W, const SolveState* st,
                cudaStream_t s) {
-  constexpr int BL = N > 0 ? bl_x<R>() : 0;
-  const int bl = N > 0 ? BL : op->dip.bl;
-  const int cb = (g.Mz + bl - 1) / bl;
-  const size_t sm = (size_t)3 * 2 * bl * (N > 0 ? fft_ls<N>() : g.Mx) * sizeof(cx<R>);
   static bool opted = false;
-  smem_opt_in(dip_x_mul<R, N, BL>, sm, opted);
-  dip_x_mul<R, N, BL><<<g.My * cb, kBlock, sm, s>>>(grid, static_cast<const cx<R>*>(op->dip.ghat), g, bl, W, st);
+  if constexpr (N > 0) {
+    constexpr int BL = reg_bl<R>();
+    const int cb = (g.Mz + BL - 1) / BL;
+    constexpr size_t sm = (size_t)3 * N * BL * sizeof(cx<R>);
+    smem_opt_in(dip_x_mul_reg<R, N>, sm, opted);
+    dip_x_mul_reg<R, N><<<g.My * cb, kBlock, sm, s>>>(grid, static_cast<const cx<R>*>(op->dip.ghat), g, W, st);
+  } else {
+    const int bl = op->dip.bl;
+    const int cb = (g.Mz + bl - 1) / bl;
+    const size_t sm = (size_t)3 * 2 * bl * g.Mx * sizeof(cx<R>);
+    dip_x_mul<R><<<g.My * cb, kBlock, sm, s>>>(grid, static_cast<const cx<R>*>(op->dip.ghat), g, bl, W, st);
+  }
 }
 
-// FFT lengths with compile-time kernels; other 2^a 3^b lengths use the
-// runtime kernels.
+// FFT lengths with register kernels; other 2^a 3^b lengths use the runtime
+// kernels.
 #define CCG_FFT_SIZES(X) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256)
 
 template <class R>
