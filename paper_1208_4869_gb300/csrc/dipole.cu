@@ -233,7 +233,7 @@ template <class R, int N> constexpr size_t z_reg_smem() {
 // into shared memory (coalesced along z), forward z FFT, store the
 // transformed lines through shared memory (coalesced along z).
 template <class R, int N>
-__global__ void __launch_bounds__(kBlock) dip_fwd_z_reg(const cx<R>* __restrict__ x, cx<R>* __restrict__ grid,
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 3 : 2) dip_fwd_z_reg(const cx<R>* __restrict__ x, cx<R>* __restrict__ grid,
                                                         const int* __restrict__ idx, DipGeom g,
                                                         const cx<R>* __restrict__ W, int conj_in,
                                                         const SolveState* __restrict__ st) {
@@ -246,6 +246,7 @@ __global__ void __launch_bounds__(kBlock) dip_fwd_z_reg(const cx<R>* __restrict_
   const int64_t nlines = (int64_t)g.nx * g.ny;
   const int64_t l0 = (int64_t)blockIdx.x * BL;
   const cx<R>* xq = x + (int64_t)q * g.N;
+#pragma unroll
   for (int t = threadIdx.x; t < BL * NZ; t += kBlock) {
     const int z = t % NZ, b = t / NZ;
     const int64_t line = l0 + b;
@@ -265,6 +266,7 @@ __global__ void __launch_bounds__(kBlock) dip_fwd_z_reg(const cx<R>* __restrict_
   fft2<R, N, BL, -1, NZ, N>(load, store, E, W);
   __syncthreads();
   cx<R>* gq = grid + (int64_t)q * g.G;
+#pragma unroll 4
   for (int t = threadIdx.x; t < BL * N; t += kBlock) {
     const int kz = t % N, b = t / N;
     const int64_t line = l0 + b;
@@ -281,7 +283,7 @@ __global__ void __launch_bounds__(kBlock) dip_fwd_z_reg(const cx<R>* __restrict_
 // frequencies k1 + N1 k2 it holds, and inverse step 1, in place in the
 // exchange buffer; inverse step 2 stores the outputs i < nx.
 template <class R, int N>
-__global__ void __launch_bounds__(kBlock) dip_x_mul_reg(cx<R>* __restrict__ grid, const cx<R>* __restrict__ ghat,
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 2 : 1) dip_x_mul_reg(cx<R>* __restrict__ grid, const cx<R>* __restrict__ ghat,
                                                         DipGeom g, const cx<R>* __restrict__ W,
                                                         const SolveState* __restrict__ st) {
   if (skip_state(st)) return;
@@ -296,18 +298,27 @@ __global__ void __launch_bounds__(kBlock) dip_x_mul_reg(cx<R>* __restrict__ grid
   const int64_t sx = (int64_t)g.My * g.Mz;
   const int64_t off = (int64_t)ky * g.Mz + kz0;
 #pragma unroll 1
-  for (int t = threadIdx.x; t < 3 * BL * N2; t += kBlock) {
-    const int b = t % BL, j2 = (t / BL) % N2, q = t / (BL * N2);
-    const cx<R>* src = grid + (int64_t)q * g.G + off + b;
-    cx<R> u[N1];
+  for (int t = threadIdx.x; t < BL * N2; t += kBlock) {
+    const int b = t % BL, j2 = t / BL;
+    // the three components' inputs (i < nx: j1 < N1 / 2) are loaded together
+    cx<R> in[3][N1 / 2];
 #pragma unroll
-    for (int j1 = 0; j1 < N1; ++j1)
-      u[j1] = (j1 < N1 / 2 && b < nb) ? src[(int64_t)(N2 * j1 + j2) * sx] : mk<R>(0, 0);
-    dft<N1, -1, R>(u);
-    cx<R>* Eq = E + q * CS;
-    Eq[j2 * BL + b] = u[0];
+    for (int q = 0; q < 3; ++q) {
+      const cx<R>* src = grid + (int64_t)q * g.G + off + b;
 #pragma unroll
-    for (int k1 = 1; k1 < N1; ++k1) Eq[(k1 * N2 + j2) * BL + b] = cmul(u[k1], line_tw<-1, R>(W, j2 * k1));
+      for (int j1 = 0; j1 < N1 / 2; ++j1) in[q][j1] = b < nb ? src[(int64_t)(N2 * j1 + j2) * sx] : mk<R>(0, 0);
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      cx<R> u[N1];
+#pragma unroll
+      for (int j1 = 0; j1 < N1; ++j1) u[j1] = j1 < N1 / 2 ? in[q][j1] : mk<R>(0, 0);
+      dft<N1, -1, R>(u);
+      cx<R>* Eq = E + q * CS;
+      Eq[j2 * BL + b] = u[0];
+#pragma unroll
+      for (int k1 = 1; k1 < N1; ++k1) Eq[(k1 * N2 + j2) * BL + b] = cmul(u[k1], line_tw<-1, R>(W, j2 * k1));
+    }
   }
   __syncthreads();
 #pragma unroll 1
@@ -352,16 +363,19 @@ __global__ void __launch_bounds__(kBlock) dip_x_mul_reg(cx<R>* __restrict__ grid
   }
   __syncthreads();
 #pragma unroll 1
-  for (int t = threadIdx.x; t < 3 * BL * N2; t += kBlock) {
-    const int b = t % BL, n1 = (t / BL) % N2, q = t / (BL * N2);
-    cx<R> v[N1];
+  for (int t = threadIdx.x; t < BL * N2; t += kBlock) {
+    const int b = t % BL, n1 = t / BL;
 #pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) v[k1] = E[q * CS + (k1 * N2 + n1) * BL + b];
-    dft<N1, +1, R>(v);
-    if (b < nb) {
-      cx<R>* dst = grid + (int64_t)q * g.G + off + b;
+    for (int q = 0; q < 3; ++q) {
+      cx<R> v[N1];
 #pragma unroll
-      for (int n2 = 0; n2 < N1 / 2; ++n2) dst[(int64_t)(n1 + N2 * n2) * sx] = v[n2];
+      for (int k1 = 0; k1 < N1; ++k1) v[k1] = E[q * CS + (k1 * N2 + n1) * BL + b];
+      dft<N1, +1, R>(v);
+      if (b < nb) {
+        cx<R>* dst = grid + (int64_t)q * g.G + off + b;
+#pragma unroll
+        for (int n2 = 0; n2 < N1 / 2; ++n2) dst[(int64_t)(n1 + N2 * n2) * sx] = v[n2];
+      }
     }
   }
 }
@@ -370,7 +384,7 @@ __global__ void __launch_bounds__(kBlock) dip_x_mul_reg(cx<R>* __restrict__ grid
 // (coalesced along z), inverse z FFT, then for occupied sites
 // y = x / alpha - (G * x) (conjugated in and out for A^H), coalesced along z.
 template <class R, int N>
-__global__ void __launch_bounds__(kBlock) dip_inv_z_reg(const cx<R>* __restrict__ x, cx<R>* __restrict__ y,
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 3 : 2) dip_inv_z_reg(const cx<R>* __restrict__ x, cx<R>* __restrict__ y,
                                                         const cx<R>* __restrict__ grid, const int* __restrict__ idx,
                                                         DipGeom g, const cx<R>* __restrict__ W, cx<R> alpha_inv,
                                                         int conj, const SolveState* __restrict__ st) {
@@ -383,6 +397,7 @@ __global__ void __launch_bounds__(kBlock) dip_inv_z_reg(const cx<R>* __restrict_
   const int64_t nlines = (int64_t)g.nx * g.ny;
   const int64_t l0 = (int64_t)blockIdx.x * BL;
   const cx<R>* gq = grid + (int64_t)q * g.G;
+#pragma unroll 4
   for (int t = threadIdx.x; t < BL * N; t += kBlock) {
     const int kz = t % N, b = t / N;
     const int64_t line = l0 + b;
@@ -400,6 +415,7 @@ __global__ void __launch_bounds__(kBlock) dip_inv_z_reg(const cx<R>* __restrict_
   __syncthreads();
   const cx<R>* xq = x + (int64_t)q * g.N;
   cx<R>* yq = y + (int64_t)q * g.N;
+#pragma unroll 4
   for (int t = threadIdx.x; t < BL * NZ; t += kBlock) {
     const int z = t % NZ, b = t / NZ;
     const int64_t line = l0 + b;
