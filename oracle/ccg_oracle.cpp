@@ -11,11 +11,14 @@
 // tolerance `epsilon_err` and iteration cap `maxit` (Sec. 5, `cgmodule`), in
 // single or double precision (abstract, Sec. 5 `ddprecision`).  It prints
 // no recurrences, so each method below is the unpreconditioned textbook form
-// of the source the manual names for it (Sec. 2.1 PIM: BiCGSTAB, CGNR, QMR;
-// Sec. 2.2 Sarkar: the complex-symmetric CG).  Readings where the manual is
-// silent:
+// of the source the manual names for it (Sec. 2.1 PIM: BiCGSTAB, CGNR, QMR,
+// BiCG (`bigcg`); Sec. 2.2 Sarkar: the complex-symmetric CG; Sec. 3.4: COCR
+// of Sogabe and Zhang).  Readings where the manual is silent:
 //   * stopping rule: ||r_k||_2 / ||y||_2 <= tol on the recurrence residual;
-//   * shadow vectors (BiCGSTAB r^, QMR w~_1) equal r_0;
+//   * shadow vectors (BiCGSTAB r^, QMR w~_1, BiCG r~_0) equal r_0;
+//   * complex BiCG pairs A with A^H and conjugated products (the shadow
+//     recurrences take conj(alpha), conj(beta));
+//   * COCR uses the unconjugated form like COCG and needs A = A^T;
 //   * BiCGSTAB exits at the half step when ||s|| meets tol (one iteration);
 //   * complex QMR uses A^H and conjugated products (the real bilinear form
 //     with A^T carried to conjugated vectors);
@@ -51,7 +54,7 @@ template <class R> using C = std::complex<R>;
 using Z = std::complex<double>;
 
 enum Status { ORC_OK = 0, ORC_NOT_CONVERGED = 1, ORC_BREAKDOWN = 2, ORC_INVALID = -1 };
-enum Method { ORC_BICGSTAB = 0, ORC_CGNR = 1, ORC_QMR = 2, ORC_COCG = 3 };
+enum Method { ORC_BICGSTAB = 0, ORC_CGNR = 1, ORC_QMR = 2, ORC_COCG = 3, ORC_COCR = 4, ORC_BICG = 5 };
 // Which scalar vanished when a method breaks down.
 enum Breakdown { BD_NONE = 0, BD_RHO = 1, BD_SIGMA = 2, BD_TT = 3, BD_OMEGA = 4, BD_GAMMA = 5,
                  BD_WW = 6, BD_XI = 7, BD_DELTA = 8, BD_EPS = 9, BD_BETA = 10, BD_MU = 11 };
@@ -492,6 +495,78 @@ Result cocg(const Operator<R>& A, const C<R>* y, C<R>* x, double tol, int maxit,
   return {maxit, ORC_NOT_CONVERGED, BD_NONE};
 }
 
+// COCR: conjugate A-orthogonal conjugate residual (Sogabe & Zhang 2007; the
+// manual's Sec. 3.4), unconjugated form, one product A r per iteration with
+// q = A p carried by recurrence.  Requires A = A^T.
+template <class R>
+Result cocr(const Operator<R>& A, const C<R>* y, C<R>* x, double tol, int maxit, double* hist) {
+  const int64_t n = A.n;
+  std::vector<C<R>> r(n), p(n), q(n), w(n);
+  const double ynorm = start(A, y, x, r.data());
+  if (ynorm == 0) { hist[0] = 0; return {0, ORC_OK, BD_NONE}; }
+  hist[0] = nrm2(n, r.data()) / ynorm;
+  if (hist[0] <= tol) return {0, ORC_OK, BD_NONE};
+  A.apply(r.data(), w.data());  // w = A r
+  p = r;
+  q = w;                        // q = A p
+  Z rho = dotu(n, r.data(), w.data());
+  for (int k = 1; k <= maxit; ++k) {
+    if (tiny<R>(rho)) return {k - 1, ORC_BREAKDOWN, BD_RHO};
+    const Z mu = dotu(n, q.data(), q.data());
+    if (tiny<R>(mu)) return {k - 1, ORC_BREAKDOWN, BD_MU};
+    const C<R> al = C<R>(rho / mu);
+    for (int64_t i = 0; i < n; ++i) { x[i] += al * p[i]; r[i] -= al * q[i]; }
+    hist[k] = nrm2(n, r.data()) / ynorm;
+    if (hist[k] <= tol) return {k, ORC_OK, BD_NONE};
+    A.apply(r.data(), w.data());
+    const Z rho_new = dotu(n, r.data(), w.data());
+    const C<R> be = C<R>(rho_new / rho);
+    for (int64_t i = 0; i < n; ++i) { p[i] = r[i] + be * p[i]; q[i] = w[i] + be * q[i]; }
+    rho = rho_new;
+  }
+  return {maxit, ORC_NOT_CONVERGED, BD_NONE};
+}
+
+// BiCG (Fletcher; PIM's `bigcg`, Sec. 2.1), complex form: the shadow
+// system runs with A^H, products are conjugated, shadow r~_0 = r_0.
+template <class R>
+Result bicg(const Operator<R>& A, const C<R>* y, C<R>* x, double tol, int maxit, double* hist) {
+  const int64_t n = A.n;
+  std::vector<C<R>> r(n), rt(n), p(n), pt(n), q(n), qt(n);
+  const double ynorm = start(A, y, x, r.data());
+  if (ynorm == 0) { hist[0] = 0; return {0, ORC_OK, BD_NONE}; }
+  hist[0] = nrm2(n, r.data()) / ynorm;
+  if (hist[0] <= tol) return {0, ORC_OK, BD_NONE};
+  rt = r;
+  Z rho = dotc(n, rt.data(), r.data());
+  for (int k = 1; k <= maxit; ++k) {
+    if (tiny<R>(rho)) return {k - 1, ORC_BREAKDOWN, BD_RHO};
+    if (k == 1) {
+      p = r;
+      pt = rt;
+    }
+    A.apply(p.data(), q.data());
+    A.apply_h(pt.data(), qt.data());
+    const Z sigma = dotc(n, pt.data(), q.data());
+    if (tiny<R>(sigma)) return {k - 1, ORC_BREAKDOWN, BD_SIGMA};
+    const Z alpha = rho / sigma;
+    const C<R> al = C<R>(alpha), alc = C<R>(std::conj(alpha));
+    for (int64_t i = 0; i < n; ++i) {
+      x[i] += al * p[i];
+      r[i] -= al * q[i];
+      rt[i] -= alc * qt[i];
+    }
+    hist[k] = nrm2(n, r.data()) / ynorm;
+    if (hist[k] <= tol) return {k, ORC_OK, BD_NONE};
+    const Z rho_new = dotc(n, rt.data(), r.data());
+    const Z beta = rho_new / rho;
+    const C<R> be = C<R>(beta), bec = C<R>(std::conj(beta));
+    for (int64_t i = 0; i < n; ++i) { p[i] = r[i] + be * p[i]; pt[i] = rt[i] + bec * pt[i]; }
+    rho = rho_new;
+  }
+  return {maxit, ORC_NOT_CONVERGED, BD_NONE};
+}
+
 template <class R>
 Result solve(int method, const Operator<R>& A, const C<R>* y, C<R>* x, double tol, int maxit, double* hist,
              double* tau) {
@@ -502,6 +577,10 @@ Result solve(int method, const Operator<R>& A, const C<R>* y, C<R>* x, double to
     case ORC_COCG:
       if (!A.symmetric) return {0, ORC_INVALID, BD_NONE};
       return cocg(A, y, x, tol, maxit, hist);
+    case ORC_COCR:
+      if (!A.symmetric) return {0, ORC_INVALID, BD_NONE};
+      return cocr(A, y, x, tol, maxit, hist);
+    case ORC_BICG: return bicg(A, y, x, tol, maxit, hist);
   }
   return {0, ORC_INVALID, BD_NONE};
 }
@@ -553,7 +632,7 @@ extern "C" {
 
 int orc_abi_version() { return 1; }
 
-// symmetric != 0 asserts A = A^T (checked by the caller), which COCG requires.
+// symmetric != 0 asserts A = A^T (checked by the caller), which COCG and COCR require.
 void* orc_op_dense_c128(int64_t n, int64_t lda, const void* A, int symmetric) {
   auto* b = new OpBox;
   b->z.reset(new Dense<double>(n, static_cast<const Z*>(A), lda));

@@ -2,9 +2,9 @@
 
 TEST INFRASTRUCTURE ONLY.  Everything here is a thin marshalling layer:
 the arithmetic lives in ccg_oracle.cpp, which restates the textbook methods
-the CCGPAK manual names (Sec. 2.1 PIM: BiCGSTAB, CGNR, QMR; Sec. 2.2 the
-Sarkar complex-symmetric CG) and the discrete-dipole operator of its DDSCAT
-application (Sec. 1).
+the CCGPAK manual names (Sec. 2.1 PIM: BiCGSTAB, CGNR, QMR, BiCG; Sec. 2.2
+the Sarkar complex-symmetric CG; Sec. 3.4 COCR) and the discrete-dipole
+operator of its DDSCAT application (Sec. 1).
 """
 import ctypes
 import threading
@@ -13,8 +13,8 @@ import numpy as np
 
 from . import build as _build
 
-BICGSTAB, CGNR, QMR, COCG = 0, 1, 2, 3
-METHODS = {"bicgstab": BICGSTAB, "cgnr": CGNR, "qmr": QMR, "cocg": COCG}
+BICGSTAB, CGNR, QMR, COCG, COCR, BICG = 0, 1, 2, 3, 4, 5
+METHODS = {"bicgstab": BICGSTAB, "cgnr": CGNR, "qmr": QMR, "cocg": COCG, "cocr": COCR, "bicg": BICG}
 OK, NOT_CONVERGED, BREAKDOWN, INVALID = 0, 1, 2, -1
 
 _lib = None

@@ -5,8 +5,11 @@ The manual (Sec. 2.1, Sec. 2.2) names the methods but prints no recurrences,
 iterates or worked examples, so every pin here is a property of the method
 or an independent implementation of the same textbook algorithm:
   * LAPACK (numpy.linalg.solve) on small systems;
-  * scipy's BiCGSTAB / QMR / CG iterates (independent code, same conventions:
-    shadow vector r_0, conjugated products);
+  * scipy's BiCGSTAB / QMR / CG / BiCG / MINRES iterates (independent code,
+    same conventions: shadow vector r_0, conjugated products);
+  * each Krylov method's defining condition solved directly on tiny systems
+    (x_k - x_0 in K_k(A, r_0) and the residual orthogonal to the method's
+    test space), iterate by iterate;
   * finite termination, eigenvalue-count termination on diagonal operators,
     CGNR's monotone residual, QMR's quasi-residual bound, breakdown cases.
 """
@@ -18,6 +21,8 @@ import oracle as O
 from paper_1208_4869_gb300 import workloads as W
 
 METHODS = ["bicgstab", "cgnr", "qmr"]
+SYM = ("cocg", "cocr")                 # methods for complex-symmetric A
+ALL = METHODS + ["cocg", "cocr", "bicg"]
 
 
 def relres(A, x, y):
@@ -35,14 +40,14 @@ def test_dense_matvec_matches_numpy(dtype, tol):
     assert np.abs(op.matvec(x, trans=True) - refh).max() / np.abs(refh).max() < tol
 
 
-@pytest.mark.parametrize("method", METHODS + ["cocg"])
+@pytest.mark.parametrize("method", ALL)
 def test_solution_matches_lapack(method):
     n = 48
     A, y = W.dense_system(n, 2.0, 11)
-    if method == "cocg":
+    if method in SYM:
         A = (A + A.T) / 2
     xs = np.linalg.solve(A, y)
-    op = O.DenseOp(A, symmetric=(method == "cocg"))
+    op = O.DenseOp(A, symmetric=(method in SYM))
     r = O.solve(op, method, y, tol=1e-12, maxit=500)
     assert r.status == O.OK
     assert np.linalg.norm(r.x - xs) / np.linalg.norm(xs) < 1e-10
@@ -107,21 +112,21 @@ def test_cocg_differs_from_conjugated_cg_on_complex_symmetric():
     assert r.status == O.OK and relres(A, r.x, y) < 1e-10
 
 
-@pytest.mark.parametrize("method", METHODS + ["cocg"])
+@pytest.mark.parametrize("method", ALL)
 def test_finite_termination_small(method):
     """Exact arithmetic ends in at most n steps; in floating point the relative
     residual after n steps (n+1 for CGNR) is tiny on a well-conditioned system."""
     n = 6
     A, y = W.dense_system(n, 4.0, 21)
-    if method == "cocg":
+    if method in SYM:
         A = (A + A.T) / 2
-    op = O.DenseOp(A, symmetric=(method == "cocg"))
+    op = O.DenseOp(A, symmetric=(method in SYM))
     steps = n + 1 if method == "cgnr" else n
     r = O.solve(op, method, y, tol=0.0, maxit=steps)
     assert relres(A, r.x, y) < 1e-8
 
 
-@pytest.mark.parametrize("method", METHODS + ["cocg"])
+@pytest.mark.parametrize("method", ALL)
 def test_diagonal_operator_distinct_eigenvalues(method):
     """A diagonal A with d distinct eigenvalues (distinct moduli, so A^H A has d
     distinct eigenvalues too) and a RHS with every component nonzero: the
@@ -167,7 +172,7 @@ def test_qmr_quasi_residual_bound():
     assert np.all(r.hist * yn <= np.sqrt(i + 1) * r.tau * (1 + 1e-10))
 
 
-@pytest.mark.parametrize("method", METHODS + ["cocg"])
+@pytest.mark.parametrize("method", ALL)
 def test_identity_converges_in_one(method):
     n = 20
     A = np.eye(n, dtype=np.complex128)
@@ -177,7 +182,7 @@ def test_identity_converges_in_one(method):
     assert np.allclose(r.x, y, rtol=1e-14, atol=1e-15)
 
 
-@pytest.mark.parametrize("method", METHODS + ["cocg"])
+@pytest.mark.parametrize("method", ALL)
 def test_zero_rhs(method):
     A, _ = W.dense_system(10, 1.0, 1)
     A = (A + A.T) / 2
@@ -195,10 +200,23 @@ def test_breakdowns():
     # COCG: [r0, r0] = 1 + i^2 = 0 with r0 != 0.
     r = O.solve(O.DenseOp(np.eye(2, dtype=complex), symmetric=True), "cocg", np.array([1, 1j]), tol=1e-12, maxit=5)
     assert r.status == O.BREAKDOWN and r.detail == 1
-    # COCG refuses an operator not marked symmetric.
+    # COCG and COCR refuse an operator not marked symmetric.
     A, y = W.dense_system(8, 1.0, 1)
-    r = O.solve(O.DenseOp(A), "cocg", y, tol=1e-12, maxit=5)
-    assert r.status == O.INVALID
+    for m in SYM:
+        r = O.solve(O.DenseOp(A), m, y, tol=1e-12, maxit=5)
+        assert r.status == O.INVALID
+    # COCR: [r0, A r0] = 0 with A = I and r0 = (1, i).
+    r = O.solve(O.DenseOp(np.eye(2, dtype=complex), symmetric=True), "cocr", np.array([1, 1j]), tol=1e-12, maxit=5)
+    assert r.status == O.BREAKDOWN and r.detail == 1 and r.iters == 0
+    # COCR: [q, q] = [A r0, A r0] = 0 while [r0, A r0] != 0 (A = diag(1, i), r0 = (1, 1)):
+    # A r0 = (1, i), [r0, A r0] = 1 + i, [A r0, A r0] = 1 - 1 = 0.
+    r = O.solve(O.DenseOp(np.diag([1, 1j]).astype(complex), symmetric=True), "cocr", np.array([1, 1], complex),
+                tol=1e-12, maxit=5)
+    assert r.status == O.BREAKDOWN and r.detail == 11 and r.iters == 0
+    # BiCG: sigma = <p~, A p> = 0 on the swap matrix with y = e_1.
+    A = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+    r = O.solve(O.DenseOp(A), "bicg", np.array([1, 0], dtype=complex), tol=1e-12, maxit=5)
+    assert r.status == O.BREAKDOWN and r.detail == 2 and r.iters == 0
 
 
 def test_maxit_not_converged():
@@ -232,3 +250,93 @@ def test_small_config_iteration_counts():
     op = O.DenseOp(A)
     its = {m: O.solve(op, m, y, tol=1e-10, maxit=1000).iters for m in METHODS}
     assert all(3 <= v <= 30 for v in its.values()), its
+
+
+# ---- the methods' defining conditions, solved directly -----------------------
+def krylov_basis(A, v, k):
+    """Orthonormal basis of K_k(A, v) = span{v, A v, ..., A^(k-1) v}."""
+    V = np.empty((len(v), k), dtype=np.complex128)
+    w = v.copy()
+    for j in range(k):
+        V[:, j] = w
+        w = A @ w
+    return np.linalg.qr(V)[0]
+
+
+def galerkin_iterate(method, A, y, x0, k):
+    """x_k = x_0 + V c, V spanning K_k(A, r_0), with the residual r_k = r_0 - A V c
+    orthogonal to the method's test space:
+      COCG  [v, r_k] = 0 for v in K_k(A, r_0)          (v^T r_k, A = A^T)
+      COCR  [A v, r_k] = 0 for v in K_k(A, r_0)        ((A v)^T r_k)
+      BiCG  <w, r_k> = 0 for w in K_k(A^H, r_0)        (w^H r_k)"""
+    r0 = y - A @ x0
+    V = krylov_basis(A, r0, k)
+    if method == "cocg":
+        T = V.T
+    elif method == "cocr":
+        T = (A @ V).T
+    else:
+        T = krylov_basis(A.conj().T, r0, k).conj().T
+    c = np.linalg.solve(T @ (A @ V), T @ r0)
+    return x0 + V @ c
+
+
+@pytest.mark.parametrize("method", ["cocg", "cocr", "bicg"])
+def test_iterates_satisfy_the_defining_condition(method):
+    n = 40
+    A, y = W.dense_system(n, 3.0, 13)
+    if method in SYM:
+        A = (A + A.T) / 2
+    x0 = W.random_vector(n, 14)
+    op = O.DenseOp(A, symmetric=(method in SYM))
+    for k in range(1, 7):
+        r = O.solve(op, method, y, x0=x0, tol=0.0, maxit=k)
+        assert r.iters == k
+        xk = galerkin_iterate(method, A, y, x0, k)
+        assert np.linalg.norm(r.x - xk) / np.linalg.norm(xk) < 1e-10, (method, k)
+
+
+def test_galerkin_pin_catches_a_conjugated_form():
+    """The COCR condition is not met by the conjugated variant (conjugate
+    residual with <., .>): a dropped-conjugate mistake would fail the pin."""
+    n = 40
+    A, y = W.dense_system(n, 3.0, 13)
+    A = (A + A.T) / 2
+    x0 = np.zeros(n, complex)
+    r0 = y - A @ x0
+    V = krylov_basis(A, r0, 3)
+    AV = A @ V
+    c = np.linalg.solve(AV.conj().T @ AV, AV.conj().T @ r0)      # minimal residual (conjugated)
+    wrong = x0 + V @ c
+    assert np.linalg.norm(wrong - galerkin_iterate("cocr", A, y, x0, 3)) > 1e-6 * np.linalg.norm(wrong)
+
+
+def test_cocr_is_minres_on_real_spd():
+    """With real SPD A and real y, COCR is the conjugate residual method, whose
+    iterates equal MINRES's (scipy, independent code); its residual decreases."""
+    rng = np.random.default_rng(2)
+    B = rng.standard_normal((40, 40))
+    S = B @ B.T + 40 * np.eye(40)
+    b = rng.standard_normal(40)
+    xs = []
+    sla.minres(S, b, rtol=1e-15, maxiter=8, callback=lambda xk: xs.append(xk.copy()))
+    op = O.DenseOp(S.astype(np.complex128), symmetric=True)
+    for k in range(1, 7):
+        r = O.solve(op, "cocr", b.astype(np.complex128), tol=0.0, maxit=k)
+        assert np.linalg.norm(r.x - xs[k - 1]) / np.linalg.norm(xs[k - 1]) < 1e-11
+        assert np.abs(r.x.imag).max() == 0.0
+    r = O.solve(op, "cocr", b.astype(np.complex128), tol=1e-12, maxit=100)
+    assert np.all(np.diff(r.hist) <= 0)
+
+
+def test_bicg_iterates_match_scipy():
+    """scipy's BiCG (independent code): shadow r~_0 = r_0, A^H, conjugated products."""
+    A, y = W.dense_system(64, 1.0, 7)
+    x0 = W.random_vector(64, 8)
+    xs = []
+    sla.bicg(A, y, x0=x0.copy(), rtol=1e-15, atol=0.0, maxiter=10, callback=lambda xk: xs.append(xk.copy()))
+    op = O.DenseOp(A)
+    for k in range(1, 9):
+        r = O.solve(op, "bicg", y, x0=x0, tol=0.0, maxit=k)
+        assert r.iters == k
+        assert np.linalg.norm(r.x - xs[k - 1]) / np.linalg.norm(xs[k - 1]) < 1e-12
