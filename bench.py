@@ -74,6 +74,9 @@ def parse_args(argv=None):
         a.methods = "bicgstab"
     if a.inner_maxit is None:
         a.inner_maxit = 200 if dense else 2000
+    if dense and {"cocg", "cocr"} & set(a.methods.split(",")):
+        p.error("cocg and cocr need a complex-symmetric operator; the dense workloads' matrix is not "
+                "(use --workload dipole)")
     return a
 
 

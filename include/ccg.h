@@ -7,8 +7,8 @@
  * iteration (Sec. 5: `matvec` for A x and `cmatvec` for A^H x), and the
  * solve takes a tolerance and an iteration cap (Sec. 5 `cgmodule`:
  * `epsilon_err`, `maxit`).  The methods are those of Sec. 2.1 (PIM:
- * `bicgstab`, `cgnr`, `qmr`) and Sec. 2.2 (the Sarkar complex-symmetric CG),
- * in their unpreconditioned textbook forms.
+ * `bicgstab`, `cgnr`, `qmr`, `bigcg`), Sec. 2.2 (the Sarkar complex-symmetric
+ * CG) and Sec. 3.4 (COCR), in their unpreconditioned textbook forms.
  *
  * Conventions shared by every entry point:
  *  - Complex vectors and matrices are interleaved (re, im) pairs in the
@@ -40,7 +40,10 @@ typedef enum {
   CCG_BICGSTAB = 0, /* van der Vorst BiCGSTAB (Sec. 2.1, PIM `bicgstab`)      */
   CCG_CGNR = 1,     /* CG on A^H A x = A^H y (Sec. 2.1, PIM `cgnr`)          */
   CCG_QMR = 2,      /* Freund-Nachtigal QMR, no look-ahead (Sec. 2.1 `qmr`)  */
-  CCG_COCG = 3      /* complex-symmetric CG, unconjugated form (Sec. 2.2)    */
+  CCG_COCG = 3,     /* complex-symmetric CG, unconjugated form (Sec. 2.2)    */
+  CCG_COCR = 4,     /* Sogabe-Zhang conjugate A-orthogonal CR (Sec. 3.4)     */
+  CCG_BICG = 5      /* Fletcher BiCG with A^H, shadow r~0 = r0 (Sec. 2.1
+                       PIM `bigcg`)                                         */
 } ccg_method;
 
 typedef enum { CCG_C64 = 0, CCG_C128 = 1 } ccg_dtype;
@@ -65,7 +68,7 @@ typedef enum {
 } ccg_breakdown;
 
 /* Operator flags. */
-#define CCG_OP_SYMMETRIC 1 /* caller asserts A = A^T (required by CCG_COCG) */
+#define CCG_OP_SYMMETRIC 1 /* caller asserts A = A^T (required by CCG_COCG, CCG_COCR) */
 
 typedef struct ccg_handle ccg_handle;
 typedef struct ccg_operator ccg_operator;
@@ -160,8 +163,10 @@ ccg_status ccg_dot(ccg_handle* h, ccg_dtype dtype, int64_t n, const void* u, con
  *  info     optional host struct receiving the result; info->true_relres is
  *           computed (one extra operator application) only when info is not
  *           NULL.
- * y = 0 gives x = 0, iters = 0, CCG_OK.  CCG_COCG needs an operator made
- * with CCG_OP_SYMMETRIC (else CCG_ERR_INVALID).  Blocks the calling thread
+ * y = 0 gives x = 0, iters = 0, CCG_OK.  CCG_COCG and CCG_COCR need an
+ * operator made with CCG_OP_SYMMETRIC (else CCG_ERR_INVALID).  Products per
+ * iteration: BiCGSTAB and CGNR two; QMR and BiCG A p and A^H q (one read of
+ * a dense A); COCG and COCR one.  Blocks the calling thread
  * until the solve has finished on the handle's stream.  Returns the solve's
  * status (CCG_OK, CCG_NOT_CONVERGED, CCG_BREAKDOWN) or an error. */
 ccg_status ccg_solve(ccg_handle* h, ccg_method method, const ccg_operator* op, const void* y, void* x, double tol,

@@ -17,8 +17,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libccg.so")
 
-BICGSTAB, CGNR, QMR, COCG = 0, 1, 2, 3
-METHODS = {"bicgstab": BICGSTAB, "cgnr": CGNR, "qmr": QMR, "cocg": COCG}
+BICGSTAB, CGNR, QMR, COCG, COCR, BICG = 0, 1, 2, 3, 4, 5
+METHODS = {"bicgstab": BICGSTAB, "cgnr": CGNR, "qmr": QMR, "cocg": COCG, "cocr": COCR, "bicg": BICG}
 C64, C128 = 0, 1
 OK, NOT_CONVERGED, BREAKDOWN = 0, 1, 2
 ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6

@@ -253,10 +253,10 @@ ccg_status ccg_dot(ccg_handle* h, ccg_dtype dtype, int64_t n, const void* u, con
 ccg_status ccg_solve(ccg_handle* h, ccg_method method, const ccg_operator* op, const void* y, void* x, double tol,
                      int maxit, double* res_hist, ccg_info* info) {
   if (!h || !op || !y || !x) { set_error("ccg_solve: NULL argument"); return CCG_ERR_INVALID; }
-  if (method < CCG_BICGSTAB || method > CCG_COCG) { set_error("ccg_solve: unknown method"); return CCG_ERR_INVALID; }
+  if (method < CCG_BICGSTAB || method > CCG_BICG) { set_error("ccg_solve: unknown method"); return CCG_ERR_INVALID; }
   if (maxit < 0 || !(tol >= 0.0)) { set_error("ccg_solve: need maxit >= 0 and tol >= 0"); return CCG_ERR_INVALID; }
-  if (method == CCG_COCG && !(op->flags & CCG_OP_SYMMETRIC)) {
-    set_error("ccg_solve: COCG needs an operator flagged CCG_OP_SYMMETRIC");
+  if ((method == CCG_COCG || method == CCG_COCR) && !(op->flags & CCG_OP_SYMMETRIC)) {
+    set_error("ccg_solve: COCG and COCR need an operator flagged CCG_OP_SYMMETRIC");
     return CCG_ERR_INVALID;
   }
   const size_t esz = op->dtype == CCG_C128 ? 16 : 8;
@@ -268,7 +268,7 @@ ccg_status ccg_solve_refined(ccg_handle* h, ccg_method method, const ccg_operato
                              const void* y, void* x, double tol, int max_outer, double inner_tol, int inner_maxit,
                              double* res_hist, int* inner_iters, ccg_info* info) {
   if (!h || !op || !op_in || !y || !x) { set_error("ccg_solve_refined: NULL argument"); return CCG_ERR_INVALID; }
-  if (method < CCG_BICGSTAB || method > CCG_COCG) { set_error("ccg_solve_refined: unknown method"); return CCG_ERR_INVALID; }
+  if (method < CCG_BICGSTAB || method > CCG_BICG) { set_error("ccg_solve_refined: unknown method"); return CCG_ERR_INVALID; }
   if (op->dtype != CCG_C128 || op_in->dtype != CCG_C64 || op->n != op_in->n) {
     set_error("ccg_solve_refined: need a complex128 operator and a complex64 operator of the same size");
     return CCG_ERR_INVALID;
@@ -277,8 +277,8 @@ ccg_status ccg_solve_refined(ccg_handle* h, ccg_method method, const ccg_operato
     set_error("ccg_solve_refined: need tol >= 0, max_outer >= 0, inner_tol > 0, inner_maxit >= 1");
     return CCG_ERR_INVALID;
   }
-  if (method == CCG_COCG && !(op_in->flags & CCG_OP_SYMMETRIC)) {
-    set_error("ccg_solve_refined: COCG needs an inner operator flagged CCG_OP_SYMMETRIC");
+  if ((method == CCG_COCG || method == CCG_COCR) && !(op_in->flags & CCG_OP_SYMMETRIC)) {
+    set_error("ccg_solve_refined: COCG and COCR need an inner operator flagged CCG_OP_SYMMETRIC");
     return CCG_ERR_INVALID;
   }
   if (!aligned(y, 16) || !aligned(x, 16)) { set_error("ccg_solve_refined: misaligned vector"); return CCG_ERR_INVALID; }

@@ -91,7 +91,8 @@ __device__ __forceinline__ void set_breakdown(SolveState* st, int which) {
   st->poll.done = 1;
 }
 
-enum { M_BICGSTAB = CCG_BICGSTAB, M_CGNR = CCG_CGNR, M_QMR = CCG_QMR, M_COCG = CCG_COCG };
+enum { M_BICGSTAB = CCG_BICGSTAB, M_CGNR = CCG_CGNR, M_QMR = CCG_QMR, M_COCG = CCG_COCG, M_COCR = CCG_COCR,
+       M_BICG = CCG_BICG };
 
 // Clears st->skip_mv (set to 1 beforehand) when any entry of x is nonzero.
 template <class R> __global__ void __launch_bounds__(kBlock) x_zero_check(const cx<R>* __restrict__ x, int64_t n,
@@ -168,7 +169,11 @@ template <class R> struct InitR : PhaseBase {
         st->rho = mkc(t[3], t[4]);
         if (tiny<R>(st->rho)) set_breakdown(st, CCG_BD_RHO);
         break;
-      default:
+      case M_BICG:
+        st->rho = mkc(t[1], 0.0);  // <r~, r> with r~ = r
+        if (tiny<R>(st->rho)) set_breakdown(st, CCG_BD_RHO);
+        break;
+      default:  // COCR forms its first scalars after the product A r0
         break;
     }
   }
@@ -626,6 +631,154 @@ template <class R> struct CoP : PhaseBase {  // p = r + beta p
 };
 
 // ---------------------------------------------------------------------------
+// COCR (Sogabe-Zhang; Sec. 3.4): one product w = A r per iteration, q = A p
+// carried by recurrence, unconjugated form.
+// ---------------------------------------------------------------------------
+template <class R> struct CrRho : PhaseBase {  // w = A r; rho' = [r, w]; beta = rho' / rho after the first
+  static constexpr int NQ = 2;
+  int64_t n;
+  MvOut<R> mv;
+  cx<R>* w;
+  const cx<R>* r;
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    const cx<R> wi = mv.get(i);
+    if (mv.P) w[i] = wi;
+    acc_dotu(acc, r[i], wi);
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    const double2 rho_new = mkc(t[0], t[1]);
+    if (tiny<R>(rho_new)) { set_breakdown(st, CCG_BD_RHO); return; }
+    if (st->poll.k > 0) st->beta = cdiv(rho_new, st->rho);
+    st->rho = rho_new;
+  }
+};
+template <class R> struct CrPQ : PhaseBase {  // p = r + beta p, q = w + beta q (first: p = r, q = w); mu = [q, q]
+  static constexpr int NQ = 2;
+  int64_t n;
+  const cx<R>* r;
+  const cx<R>* w;
+  cx<R>* p;
+  cx<R>* q;
+  cx<R> beta;
+  bool first;
+  __device__ __forceinline__ void load(const SolveState* st) {
+    first = st->poll.k == 0;
+    beta = narrow<R>(st->beta);
+  }
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    cx<R> pi = r[i], qi = w[i];
+    if (!first) {
+      pi = cfma(beta, p[i], pi);
+      qi = cfma(beta, q[i], qi);
+    }
+    p[i] = pi;
+    q[i] = qi;
+    acc_dotu(acc, qi, qi);
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    const double2 mu = mkc(t[0], t[1]);
+    if (tiny<R>(mu)) { set_breakdown(st, CCG_BD_MU); return; }
+    st->alpha = cdiv(st->rho, mu);
+  }
+};
+template <class R> struct CrXR : PhaseBase {  // x += alpha p; r -= alpha q
+  static constexpr int NQ = 1;
+  int64_t n;
+  cx<R>* x;
+  cx<R>* r;
+  const cx<R>* p;
+  const cx<R>* q;
+  cx<R> alpha;
+  __device__ __forceinline__ void load(const SolveState* st) { alpha = narrow<R>(st->alpha); }
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    x[i] = cadd(x[i], cmul(alpha, p[i]));
+    const cx<R> ri = csub(r[i], cmul(alpha, q[i]));
+    r[i] = ri;
+    acc_nrm2(acc, ri);
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    end_iteration(st, st->poll.k + 1, sqrt(t[0]) / st->poll.ynorm, 0);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// BiCG (Fletcher; PIM `bigcg`, Sec. 2.1): A p and A^H p~ from one read of a
+// dense A, conjugated products, shadow r~_0 = r_0.
+// ---------------------------------------------------------------------------
+template <class R> struct BgP : PhaseBase {  // p = r + beta p, p~ = r~ + conj(beta) p~ (first: p = r, p~ = r~)
+  static constexpr bool kReduce = false;
+  static constexpr int NQ = 1;
+  int64_t n;
+  const cx<R>* r;
+  const cx<R>* rt;
+  cx<R>* p;
+  cx<R>* pt;
+  cx<R> beta;
+  bool first;
+  __device__ __forceinline__ void load(const SolveState* st) {
+    first = st->poll.k == 0;
+    beta = narrow<R>(st->beta);
+  }
+  __device__ __forceinline__ void element(int64_t i, double*) {
+    if (first) {
+      p[i] = r[i];
+      pt[i] = rt[i];
+    } else {
+      p[i] = cfma(beta, p[i], r[i]);
+      pt[i] = cfma(cconj(beta), pt[i], rt[i]);
+    }
+  }
+  __device__ void finish(const double*, SolveState*) {}
+};
+template <class R> struct BgSigma : PhaseBase {  // q = A p, q~ = A^H p~; sigma = <p~, q>, alpha = rho / sigma
+  static constexpr int NQ = 2;
+  int64_t n;
+  MvOut<R> mv1, mv2;
+  cx<R>* q;
+  cx<R>* qt;
+  const cx<R>* pt;
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    const cx<R> qi = mv1.get(i), qti = mv2.get(i);
+    if (mv1.P) q[i] = qi;
+    if (mv2.P) qt[i] = qti;
+    acc_dotc(acc, pt[i], qi);
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    const double2 sigma = mkc(t[0], t[1]);
+    if (tiny<R>(sigma)) { set_breakdown(st, CCG_BD_SIGMA); return; }
+    st->alpha = cdiv(st->rho, sigma);
+  }
+};
+template <class R> struct BgXR : PhaseBase {  // x += alpha p; r -= alpha q; r~ -= conj(alpha) q~; rho' = <r~, r>
+  static constexpr int NQ = 3;
+  int64_t n;
+  cx<R>* x;
+  cx<R>* r;
+  cx<R>* rt;
+  const cx<R>* p;
+  const cx<R>* q;
+  const cx<R>* qt;
+  cx<R> alpha;
+  __device__ __forceinline__ void load(const SolveState* st) { alpha = narrow<R>(st->alpha); }
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    x[i] = cadd(x[i], cmul(alpha, p[i]));
+    const cx<R> ri = csub(r[i], cmul(alpha, q[i]));
+    const cx<R> rti = csub(rt[i], cmul(cconj(alpha), qt[i]));
+    r[i] = ri;
+    rt[i] = rti;
+    acc_nrm2(acc, ri);
+    acc_dotc(acc + 1, rti, ri);
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    if (end_iteration(st, st->poll.k + 1, sqrt(t[0]) / st->poll.ynorm, 0)) return;
+    const double2 rho_new = mkc(t[1], t[2]);
+    if (tiny<R>(rho_new)) { set_breakdown(st, CCG_BD_RHO); return; }
+    st->beta = cdiv(rho_new, st->rho);
+    st->rho = rho_new;
+  }
+};
+
+// ---------------------------------------------------------------------------
 // Host side.
 // ---------------------------------------------------------------------------
 #define CCG_CUDA(call)                                                                 \
@@ -864,6 +1017,7 @@ static int solve_core(ccg_handle* h, int method, const ccg_operator* op, const W
       case M_BICGSTAB: p.c1 = V[1]; break;               // r^
       case M_QMR: p.c1 = V[1]; p.c2 = V[2]; break;       // v~, w~
       case M_COCG: p.c1 = V[1]; break;                   // p
+      case M_BICG: p.c1 = V[1]; break;                   // r~
       default: break;
     }
     if (x0_zero) {
@@ -905,12 +1059,31 @@ static int solve_core(ccg_handle* h, int method, const ccg_operator* op, const W
       QDX<R> e; e.n = n; e.p = pv; e.pt = pt; e.d = dv; e.s = sv; e.x = x; e.r = r; e.vt = vt; e.wt = wt; e.v = v;
       e.w = wv; run.phase(e);
     };
-  } else {  // COCG
+  } else if (method == M_COCG) {
     cx<R>*r = V[0], *pv = V[1], *q = V[2];
     step = [=, &run]() {
       CoMu<R> a; a.n = n; a.q = q; a.p = pv; a.mv = run.apply_n(pv, q, st); run.phase(a);
       CoXR<R> b; b.n = n; b.x = x; b.r = r; b.p = pv; b.q = q; run.phase(b);
       CoP<R> c; c.n = n; c.r = r; c.p = pv; run.phase(c);
+    };
+  } else if (method == M_COCR) {
+    cx<R>*r = V[0], *pv = V[1], *q = V[2], *wv = V[3];
+    auto rho_pq = [=, &run]() {
+      CrRho<R> a; a.n = n; a.w = wv; a.r = r; a.mv = run.apply_n(r, wv, st); run.phase(a);
+      CrPQ<R> b; b.n = n; b.r = r; b.w = wv; b.p = pv; b.q = q; run.phase(b);
+    };
+    rho_pq();  // w = A r0, rho, p = r0, q = w, alpha
+    step = [=, &run]() {
+      CrXR<R> c; c.n = n; c.x = x; c.r = r; c.p = pv; c.q = q; run.phase(c);
+      rho_pq();
+    };
+  } else {  // BiCG
+    cx<R>*r = V[0], *rt = V[1], *pv = V[2], *pt = V[3], *q = V[4], *qt = V[5];
+    step = [=, &run]() {
+      BgP<R> a; a.n = n; a.r = r; a.rt = rt; a.p = pv; a.pt = pt; run.phase(a);
+      BgSigma<R> b; b.n = n; b.q = q; b.qt = qt; b.pt = pt; run.apply_both(pv, pt, q, qt, b.mv1, b.mv2, st);
+      run.phase(b);
+      BgXR<R> c; c.n = n; c.x = x; c.r = r; c.rt = rt; c.p = pv; c.q = q; c.qt = qt; run.phase(c);
     };
   }
   CCG_CUDA(cudaGetLastError());

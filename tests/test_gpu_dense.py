@@ -98,7 +98,7 @@ def test_dot_products(h, dtype, n):
 
 
 # ------------------------------------------------------------------ solvers
-SMALL = [("bicgstab", False), ("cgnr", False), ("qmr", False), ("cocg", True)]
+SMALL = [("bicgstab", False), ("cgnr", False), ("qmr", False), ("cocg", True), ("cocr", True), ("bicg", False)]
 
 
 def system(n, shift, seed, symmetric, dtype=np.complex128):
@@ -207,10 +207,11 @@ def test_edge_cases(h, ccg):
     # iteration cap
     st, info, hist = h.solve("bicgstab", op, dev(y), torch.zeros_like(xd), 1e-15, 2)
     assert st == ccg.NOT_CONVERGED and info["iters"] == 2 and len(hist) == 3
-    # COCG needs the symmetric flag
+    # COCG and COCR need the symmetric flag
     op2 = h.op_dense(dev(A))
-    with pytest.raises(ccg.CcgError):
-        h.solve("cocg", op2, dev(y), torch.zeros_like(xd), 1e-10, 10)
+    for m in ("cocg", "cocr"):
+        with pytest.raises(ccg.CcgError):
+            h.solve(m, op2, dev(y), torch.zeros_like(xd), 1e-10, 10)
     # non-finite right-hand side
     yb = y.copy()
     yb[3] = np.nan
@@ -230,9 +231,26 @@ def test_breakdowns_match_oracle(h, ccg):
     I2 = np.eye(2, dtype=np.complex128)
     op = h.op_dense(dev(I2), symmetric=True)
     yb = np.array([1, 1j])
-    st, info, _ = h.solve("cocg", op, dev(yb), torch.zeros(2, dtype=torch.complex128, device="cuda"), 1e-12, 5)
-    ref = O.solve(O.DenseOp(I2, symmetric=True), "cocg", yb, tol=1e-12, maxit=5)
-    assert st == ccg.BREAKDOWN == ref.status and info["breakdown"] == ref.detail
+    for m in ("cocg", "cocr"):
+        st, info, _ = h.solve(m, op, dev(yb), torch.zeros(2, dtype=torch.complex128, device="cuda"), 1e-12, 5)
+        ref = O.solve(O.DenseOp(I2, symmetric=True), m, yb, tol=1e-12, maxit=5)
+        assert st == ccg.BREAKDOWN == ref.status and info["breakdown"] == ref.detail and info["iters"] == ref.iters
+    # COCR: [A r0, A r0] = 0 with [r0, A r0] != 0
+    D = np.diag([1, 1j]).astype(np.complex128)
+    y1 = np.array([1, 1], dtype=np.complex128)
+    op = h.op_dense(dev(D), symmetric=True)
+    st, info, _ = h.solve("cocr", op, dev(y1), torch.zeros(2, dtype=torch.complex128, device="cuda"), 1e-12, 5)
+    ref = O.solve(O.DenseOp(D, symmetric=True), "cocr", y1, tol=1e-12, maxit=5)
+    assert st == ccg.BREAKDOWN == ref.status and info["breakdown"] == ref.detail == ccg_bd_mu()
+    # BiCG: <p~, A p> = 0 on the swap matrix
+    op = h.op_dense(dev(A))
+    st, info, _ = h.solve("bicg", op, dev(y), torch.zeros(2, dtype=torch.complex128, device="cuda"), 1e-12, 5)
+    ref = O.solve(O.DenseOp(A), "bicg", y, tol=1e-12, maxit=5)
+    assert st == ccg.BREAKDOWN == ref.status and info["breakdown"] == ref.detail and info["iters"] == ref.iters
+
+
+def ccg_bd_mu():
+    return 11   # CCG_BD_MU
 
 
 def test_host_buffers_equal_device_buffers(h):

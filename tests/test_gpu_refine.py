@@ -45,11 +45,11 @@ def relres(A, x, y):
     return np.linalg.norm(y - A @ x) / np.linalg.norm(y)
 
 
-@pytest.mark.parametrize("method", ["bicgstab", "cgnr", "qmr", "cocg"])
+@pytest.mark.parametrize("method", ["bicgstab", "cgnr", "qmr", "cocg", "cocr", "bicg"])
 @pytest.mark.parametrize("n", [256, 1000])
 def test_refined_matches_oracle(h, method, n):
     A, y = W.dense_system(n, 3.0, 17)
-    sym = method == "cocg"
+    sym = method in ("cocg", "cocr")
     if sym:
         A = (A + A.T) / 2
     op64, op32, _keep = ops(h, A, sym)
