@@ -12,13 +12,20 @@
 // single or double precision (abstract, Sec. 5 `ddprecision`).  It prints
 // no recurrences, so each method below is the unpreconditioned textbook form
 // of the source the manual names for it (Sec. 2.1 PIM: BiCGSTAB, CGNR, QMR,
-// BiCG (`bigcg`); Sec. 2.2 Sarkar: the complex-symmetric CG; Sec. 3.4: COCR
-// of Sogabe and Zhang).  Readings where the manual is silent:
+// BiCG (`bigcg`), restarted GMRES (`rgmres`); Sec. 2.2 Sarkar: the
+// complex-symmetric CG; Sec. 3.4: COCR of Sogabe and Zhang).  Readings where
+// the manual is silent:
 //   * stopping rule: ||r_k||_2 / ||y||_2 <= tol on the recurrence residual;
 //   * shadow vectors (BiCGSTAB r^, QMR w~_1, BiCG r~_0) equal r_0;
 //   * complex BiCG pairs A with A^H and conjugated products (the shadow
 //     recurrences take conj(alpha), conj(beta));
 //   * COCR uses the unconjugated form like COCG and needs A = A^T;
+//   * GMRES(m): an iteration is one Arnoldi step (one product); its residual
+//     is the least-squares residual |g_{j+1}| the Givens rotations give,
+//     the true residual of the cycle's minimiser; x is formed at the end of
+//     a cycle (m steps, convergence or the cap), and a cycle restarts from
+//     r = y - A x, stopping at once if that residual meets tol; the restart
+//     length m (default 30) is a parameter;
 //   * BiCGSTAB exits at the half step when ||s|| meets tol (one iteration);
 //   * complex QMR uses A^H and conjugated products (the real bilinear form
 //     with A^T carried to conjugated vectors);
@@ -54,10 +61,13 @@ template <class R> using C = std::complex<R>;
 using Z = std::complex<double>;
 
 enum Status { ORC_OK = 0, ORC_NOT_CONVERGED = 1, ORC_BREAKDOWN = 2, ORC_INVALID = -1 };
-enum Method { ORC_BICGSTAB = 0, ORC_CGNR = 1, ORC_QMR = 2, ORC_COCG = 3, ORC_COCR = 4, ORC_BICG = 5 };
+enum Method { ORC_BICGSTAB = 0, ORC_CGNR = 1, ORC_QMR = 2, ORC_COCG = 3, ORC_COCR = 4, ORC_BICG = 5, ORC_GMRES = 6 };
 // Which scalar vanished when a method breaks down.
 enum Breakdown { BD_NONE = 0, BD_RHO = 1, BD_SIGMA = 2, BD_TT = 3, BD_OMEGA = 4, BD_GAMMA = 5,
-                 BD_WW = 6, BD_XI = 7, BD_DELTA = 8, BD_EPS = 9, BD_BETA = 10, BD_MU = 11 };
+                 BD_WW = 6, BD_XI = 7, BD_DELTA = 8, BD_EPS = 9, BD_BETA = 10, BD_MU = 11, BD_HESS = 12 };
+
+// Restart length of GMRES(m), set through orc_set_restart.
+int g_restart = 30;
 
 template <class R> double guard();
 template <> double guard<double>() { return 1e-300; }
@@ -567,6 +577,85 @@ Result bicg(const Operator<R>& A, const C<R>* y, C<R>* x, double tol, int maxit,
   return {maxit, ORC_NOT_CONVERGED, BD_NONE};
 }
 
+// Restarted GMRES(m) (Saad & Schultz 1986; PIM's `rgmres`, Sec. 2.1),
+// complex form: Arnoldi with modified Gram-Schmidt in <u, v> = sum conj(u_i)
+// v_i, the Hessenberg least-squares problem reduced by complex Givens
+// rotations G = [c, s; -conj(s), c] (c real) as columns arrive.
+template <class R>
+Result gmres(const Operator<R>& A, const C<R>* y, C<R>* x, double tol, int maxit, double* hist, int m) {
+  const int64_t n = A.n;
+  std::vector<C<R>> r(n), w(n);
+  std::vector<std::vector<C<R>>> V(m + 1, std::vector<C<R>>(n));
+  std::vector<Z> H((size_t)(m + 1) * m), g(m + 1), sn(m), yv(m);
+  std::vector<double> cs(m);
+  auto h = [&](int i, int c) -> Z& { return H[(size_t)i * m + c]; };
+  const double ynorm = start(A, y, x, r.data());
+  if (ynorm == 0) { hist[0] = 0; return {0, ORC_OK, BD_NONE}; }
+  double beta = nrm2(n, r.data());
+  hist[0] = beta / ynorm;
+  if (hist[0] <= tol) return {0, ORC_OK, BD_NONE};
+  int k = 0;
+  for (;;) {
+    const R binv = R(1.0 / beta);
+    for (int64_t e = 0; e < n; ++e) V[0][e] = r[e] * binv;
+    std::fill(g.begin(), g.end(), Z(0.0));
+    g[0] = beta;
+    int cols = 0;
+    for (int j = 0; j < m; ++j) {
+      ++k;
+      A.apply(V[j].data(), w.data());
+      for (int i = 0; i <= j; ++i) {
+        const Z hij = dotc(n, V[i].data(), w.data());
+        h(i, j) = hij;
+        const C<R> hc = C<R>(hij);
+        for (int64_t e = 0; e < n; ++e) w[e] -= hc * V[i][e];
+      }
+      const double eta = nrm2(n, w.data());
+      for (int i = 0; i < j; ++i) {  // earlier rotations on the new column
+        const Z a = h(i, j), b = h(i + 1, j);
+        h(i, j) = cs[i] * a + sn[i] * b;
+        h(i + 1, j) = -std::conj(sn[i]) * a + cs[i] * b;
+      }
+      const Z a = h(j, j);
+      const double nu = std::sqrt(std::norm(a) + eta * eta);
+      if (nu == 0.0) return {k - 1, ORC_BREAKDOWN, BD_HESS};
+      if (std::abs(a) == 0.0) {
+        cs[j] = 0.0;
+        sn[j] = 1.0;
+        h(j, j) = eta;
+      } else {
+        const Z ph = a / std::abs(a);
+        cs[j] = std::abs(a) / nu;
+        sn[j] = ph * (eta / nu);
+        h(j, j) = ph * nu;
+      }
+      h(j + 1, j) = 0.0;
+      g[j + 1] = -std::conj(sn[j]) * g[j];
+      g[j] = cs[j] * g[j];
+      hist[k] = std::abs(g[j + 1]) / ynorm;
+      cols = j + 1;
+      if (hist[k] <= tol || k == maxit) break;
+      const R einv = R(1.0 / eta);
+      for (int64_t e = 0; e < n; ++e) V[j + 1][e] = w[e] * einv;
+    }
+    for (int i = cols - 1; i >= 0; --i) {  // R y = g by back substitution
+      Z t = g[i];
+      for (int l = i + 1; l < cols; ++l) t -= h(i, l) * yv[l];
+      yv[i] = t / h(i, i);
+    }
+    for (int i = 0; i < cols; ++i) {
+      const C<R> yi = C<R>(yv[i]);
+      for (int64_t e = 0; e < n; ++e) x[e] += yi * V[i][e];
+    }
+    if (hist[k] <= tol) return {k, ORC_OK, BD_NONE};
+    if (k == maxit) return {k, ORC_NOT_CONVERGED, BD_NONE};
+    A.apply(x, r.data());
+    for (int64_t e = 0; e < n; ++e) r[e] = y[e] - r[e];
+    beta = nrm2(n, r.data());
+    if (beta / ynorm <= tol) return {k, ORC_OK, BD_NONE};
+  }
+}
+
 template <class R>
 Result solve(int method, const Operator<R>& A, const C<R>* y, C<R>* x, double tol, int maxit, double* hist,
              double* tau) {
@@ -581,6 +670,7 @@ Result solve(int method, const Operator<R>& A, const C<R>* y, C<R>* x, double to
       if (!A.symmetric) return {0, ORC_INVALID, BD_NONE};
       return cocr(A, y, x, tol, maxit, hist);
     case ORC_BICG: return bicg(A, y, x, tol, maxit, hist);
+    case ORC_GMRES: return gmres(A, y, x, tol, maxit, hist, g_restart);
   }
   return {0, ORC_INVALID, BD_NONE};
 }
@@ -631,6 +721,9 @@ struct OpBox {
 extern "C" {
 
 int orc_abi_version() { return 1; }
+
+// Restart length m of GMRES(m) for later solves (1 <= m <= 256).
+void orc_set_restart(int m) { g_restart = m < 1 ? 1 : (m > 256 ? 256 : m); }
 
 // symmetric != 0 asserts A = A^T (checked by the caller), which COCG and COCR require.
 void* orc_op_dense_c128(int64_t n, int64_t lda, const void* A, int symmetric) {

@@ -22,7 +22,7 @@ from paper_1208_4869_gb300 import workloads as W
 
 METHODS = ["bicgstab", "cgnr", "qmr"]
 SYM = ("cocg", "cocr")                 # methods for complex-symmetric A
-ALL = METHODS + ["cocg", "cocr", "bicg"]
+ALL = METHODS + ["cocg", "cocr", "bicg", "gmres"]
 
 
 def relres(A, x, y):
@@ -213,6 +213,9 @@ def test_breakdowns():
     r = O.solve(O.DenseOp(np.diag([1, 1j]).astype(complex), symmetric=True), "cocr", np.array([1, 1], complex),
                 tol=1e-12, maxit=5)
     assert r.status == O.BREAKDOWN and r.detail == 11 and r.iters == 0
+    # GMRES: a zero Hessenberg column (A = 0) leaves the projected system singular.
+    r = O.solve(O.DenseOp(np.zeros((4, 4), complex)), "gmres", np.ones(4, complex), tol=1e-12, maxit=5)
+    assert r.status == O.BREAKDOWN and r.detail == 12 and r.iters == 0
     # BiCG: sigma = <p~, A p> = 0 on the swap matrix with y = e_1.
     A = np.array([[0, 1], [1, 0]], dtype=np.complex128)
     r = O.solve(O.DenseOp(A), "bicg", np.array([1, 0], dtype=complex), tol=1e-12, maxit=5)
@@ -340,3 +343,47 @@ def test_bicg_iterates_match_scipy():
         r = O.solve(op, "bicg", y, x0=x0, tol=0.0, maxit=k)
         assert r.iters == k
         assert np.linalg.norm(r.x - xs[k - 1]) / np.linalg.norm(xs[k - 1]) < 1e-12
+
+
+def minres_iterate(A, y, x0, k):
+    """argmin ||y - A x|| over x in x0 + K_k(A, r_0), by least squares."""
+    r0 = y - A @ x0
+    V = krylov_basis(A, r0, k)
+    c = np.linalg.lstsq(A @ V, r0, rcond=None)[0]
+    return x0 + V @ c
+
+
+def test_gmres_first_cycle_is_the_least_squares_minimiser():
+    """Iterate k of a cycle minimises the residual over x0 + K_k(A, r0); its
+    recorded residual is that minimum (the Givens estimate is exact)."""
+    n = 40
+    A, y = W.dense_system(n, 2.0, 15)
+    x0 = W.random_vector(n, 16)
+    op = O.DenseOp(A)
+    for k in range(1, 8):
+        r = O.solve(op, "gmres", y, x0=x0, tol=0.0, maxit=k, restart=30)
+        assert r.iters == k
+        xk = minres_iterate(A, y, x0, k)
+        assert np.linalg.norm(r.x - xk) / np.linalg.norm(xk) < 1e-10, k
+        assert abs(r.hist[k] - relres(A, xk, y)) < 1e-12
+    # the ordering of the residuals is that of a minimiser over growing spaces
+    r = O.solve(op, "gmres", y, x0=x0, tol=0.0, maxit=12, restart=30)
+    assert np.all(np.diff(r.hist) <= 1e-15)
+
+
+def test_gmres_restarts_from_the_cycle_end():
+    """GMRES(3): after a cycle, x_3 is the minimiser over x0 + K_3; the next
+    cycle minimises over x_3 + K_j(A, y - A x_3)."""
+    n = 40
+    A, y = W.dense_system(n, 2.0, 17)
+    x0 = W.random_vector(n, 18)
+    op = O.DenseOp(A)
+    x3 = minres_iterate(A, y, x0, 3)
+    for k, want in [(3, x3), (4, minres_iterate(A, y, x3, 1)), (5, minres_iterate(A, y, x3, 2)),
+                    (6, minres_iterate(A, y, x3, 3))]:
+        r = O.solve(op, "gmres", y, x0=x0, tol=0.0, maxit=k, restart=3)
+        assert r.iters == k and r.status == O.NOT_CONVERGED
+        assert np.linalg.norm(r.x - want) / np.linalg.norm(want) < 1e-10, k
+    r = O.solve(op, "gmres", y, x0=x0, tol=1e-12, maxit=400, restart=3)
+    assert r.status == O.OK and np.all(np.diff(r.hist) <= 1e-15)
+    assert relres(A, r.x, y) < 1e-11
