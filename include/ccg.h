@@ -42,8 +42,10 @@ typedef enum {
   CCG_QMR = 2,      /* Freund-Nachtigal QMR, no look-ahead (Sec. 2.1 `qmr`)  */
   CCG_COCG = 3,     /* complex-symmetric CG, unconjugated form (Sec. 2.2)    */
   CCG_COCR = 4,     /* Sogabe-Zhang conjugate A-orthogonal CR (Sec. 3.4)     */
-  CCG_BICG = 5      /* Fletcher BiCG with A^H, shadow r~0 = r0 (Sec. 2.1
+  CCG_BICG = 5,     /* Fletcher BiCG with A^H, shadow r~0 = r0 (Sec. 2.1
                        PIM `bigcg`)                                         */
+  CCG_GMRES = 6     /* restarted GMRES(m) (Sec. 2.1 PIM `rgmres`); m set by
+                       ccg_set_option(CCG_OPT_GMRES_RESTART), default 30    */
 } ccg_method;
 
 typedef enum { CCG_C64 = 0, CCG_C128 = 1 } ccg_dtype;
@@ -64,7 +66,8 @@ typedef enum {
 typedef enum {
   CCG_BD_NONE = 0, CCG_BD_RHO = 1, CCG_BD_SIGMA = 2, CCG_BD_TT = 3, CCG_BD_OMEGA = 4,
   CCG_BD_GAMMA = 5, CCG_BD_WW = 6, CCG_BD_XI = 7, CCG_BD_DELTA = 8, CCG_BD_EPS = 9,
-  CCG_BD_BETA = 10, CCG_BD_MU = 11
+  CCG_BD_BETA = 10, CCG_BD_MU = 11,
+  CCG_BD_HESS = 12 /* GMRES: a zero Hessenberg column (singular projected system) */
 } ccg_breakdown;
 
 /* Operator flags. */
@@ -249,9 +252,12 @@ ccg_status ccg_block_matvec(ccg_handle* h, const ccg_operator* op, int64_t nrhs,
  * products) or 3 (six products).  The tensor cores' fp32 accumulation bounds
  * both to ~1e-5 relative at K ~ 10^3 and ~1e-4 at K ~ 10^4, so the third
  * term rarely pays; refined batched solves correct the difference with one
- * exact complex64 residual per correction. */
+ * exact complex64 residual per correction.
+ * CCG_OPT_GMRES_RESTART: the cycle length m of CCG_GMRES, 1..64 (default
+ * 30); the solve holds m + 1 basis vectors in the handle's workspace. */
 #define CCG_OPT_TENSOR_CORES 1
 #define CCG_OPT_TC_SPLIT 2
+#define CCG_OPT_GMRES_RESTART 3
 ccg_status ccg_set_option(ccg_handle* h, int option, int value);
 
 /* ---------------------------------------------------------------------------

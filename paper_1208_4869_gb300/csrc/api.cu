@@ -253,7 +253,7 @@ ccg_status ccg_dot(ccg_handle* h, ccg_dtype dtype, int64_t n, const void* u, con
 ccg_status ccg_solve(ccg_handle* h, ccg_method method, const ccg_operator* op, const void* y, void* x, double tol,
                      int maxit, double* res_hist, ccg_info* info) {
   if (!h || !op || !y || !x) { set_error("ccg_solve: NULL argument"); return CCG_ERR_INVALID; }
-  if (method < CCG_BICGSTAB || method > CCG_BICG) { set_error("ccg_solve: unknown method"); return CCG_ERR_INVALID; }
+  if (method < CCG_BICGSTAB || method > CCG_GMRES) { set_error("ccg_solve: unknown method"); return CCG_ERR_INVALID; }
   if (maxit < 0 || !(tol >= 0.0)) { set_error("ccg_solve: need maxit >= 0 and tol >= 0"); return CCG_ERR_INVALID; }
   if ((method == CCG_COCG || method == CCG_COCR) && !(op->flags & CCG_OP_SYMMETRIC)) {
     set_error("ccg_solve: COCG and COCR need an operator flagged CCG_OP_SYMMETRIC");
@@ -268,7 +268,7 @@ ccg_status ccg_solve_refined(ccg_handle* h, ccg_method method, const ccg_operato
                              const void* y, void* x, double tol, int max_outer, double inner_tol, int inner_maxit,
                              double* res_hist, int* inner_iters, ccg_info* info) {
   if (!h || !op || !op_in || !y || !x) { set_error("ccg_solve_refined: NULL argument"); return CCG_ERR_INVALID; }
-  if (method < CCG_BICGSTAB || method > CCG_BICG) { set_error("ccg_solve_refined: unknown method"); return CCG_ERR_INVALID; }
+  if (method < CCG_BICGSTAB || method > CCG_GMRES) { set_error("ccg_solve_refined: unknown method"); return CCG_ERR_INVALID; }
   if (op->dtype != CCG_C128 || op_in->dtype != CCG_C64 || op->n != op_in->n) {
     set_error("ccg_solve_refined: need a complex128 operator and a complex64 operator of the same size");
     return CCG_ERR_INVALID;
@@ -351,7 +351,11 @@ ccg_status ccg_set_option(ccg_handle* h, int option, int value) {
     h->tc_terms = value;
     return CCG_OK;
   }
-  set_error("ccg_set_option: unknown option");
+  if (option == CCG_OPT_GMRES_RESTART && value >= 1 && value <= kMaxBasis) {
+    h->gm_restart = value;
+    return CCG_OK;
+  }
+  set_error("ccg_set_option: unknown option or value out of range");
   return CCG_ERR_INVALID;
 }
 

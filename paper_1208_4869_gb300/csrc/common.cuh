@@ -12,6 +12,7 @@ constexpr int kBlock = 256;          // threads per block of every kernel here
 constexpr int kWarps = kBlock / 32;
 constexpr int kMaxRedBlocks = 2048;  // upper bound on the grid of a reducing kernel
 constexpr int kMaxNQ = 8;            // reduction slots per reducing kernel
+constexpr int kMaxBasis = 64;        // largest GMRES restart length
 
 // ---------------------------------------------------------------------------
 // Complex storage types and arithmetic.
@@ -113,6 +114,10 @@ struct SolveState {
   double2 rho, rho_old, alpha, omega, beta, delta, eps, eta, cp, cq;
   // real method scalars
   double gamma, gamma_prev, theta, theta_prev, xi, rho_n, xi_n, c, qrho;
+  // GMRES(m): the solve ends with this cycle; Hessenberg columns of the
+  // cycle; ||r|| at the cycle start; norm of the last orthogonalised vector
+  int gm_final, gm_cols;
+  double gm_beta, gm_eta;
   double* hist;   // device residual history, maxit + 1 entries
   double* aux;    // spare device doubles for standalone results
 };

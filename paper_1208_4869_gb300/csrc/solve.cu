@@ -1,5 +1,6 @@
-// Krylov iterations on the GPU: BiCGSTAB, CGNR, QMR (Sec. 2.1, the PIM
-// methods) and the complex-symmetric CG (Sec. 2.2), unpreconditioned.
+// Krylov iterations on the GPU: BiCGSTAB, CGNR, QMR, BiCG, GMRES(m) (Sec.
+// 2.1, the PIM methods), the complex-symmetric CG (Sec. 2.2) and COCR (Sec.
+// 3.4), unpreconditioned.
 //
 // One iteration is a fixed sequence of kernels on the handle's stream:
 // operator sweeps (gemv.cuh) and "phase" kernels.  A phase kernel makes one
@@ -23,6 +24,7 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <memory>
 
 #include "common.cuh"
 #include "gemv.cuh"
@@ -92,7 +94,7 @@ __device__ __forceinline__ void set_breakdown(SolveState* st, int which) {
 }
 
 enum { M_BICGSTAB = CCG_BICGSTAB, M_CGNR = CCG_CGNR, M_QMR = CCG_QMR, M_COCG = CCG_COCG, M_COCR = CCG_COCR,
-       M_BICG = CCG_BICG };
+       M_BICG = CCG_BICG, M_GMRES = CCG_GMRES };
 
 // Clears st->skip_mv (set to 1 beforehand) when any entry of x is nonzero.
 template <class R> __global__ void __launch_bounds__(kBlock) x_zero_check(const cx<R>* __restrict__ x, int64_t n,
@@ -172,6 +174,9 @@ template <class R> struct InitR : PhaseBase {
       case M_BICG:
         st->rho = mkc(t[1], 0.0);  // <r~, r> with r~ = r
         if (tiny<R>(st->rho)) set_breakdown(st, CCG_BD_RHO);
+        break;
+      case M_GMRES:
+        st->gm_beta = sqrt(t[1]);
         break;
       default:  // COCR forms its first scalars after the product A r0
         break;
@@ -779,6 +784,249 @@ template <class R> struct BgXR : PhaseBase {  // x += alpha p; r -= alpha q; r~ 
 };
 
 // ---------------------------------------------------------------------------
+// GMRES(m) (Saad-Schultz; PIM `rgmres`, Sec. 2.1), complex form.  Arnoldi
+// step j orthogonalises w = A v_j against v_0 .. v_j by classical
+// Gram-Schmidt applied twice: h1 = V^H w in one pass, w -= V h1 with
+// h2 = V^H w in a second, w -= V h2 with ||w|| in a third (three passes and
+// three grid reductions per step instead of j + 1 dependent ones; in exact
+// arithmetic the same basis and Hessenberg column as modified Gram-Schmidt).
+// The last block of the third pass applies the earlier Givens rotations to
+// the column, forms the new one and the least-squares residual |g_{j+1}|.
+// `half` marks a cycle that stopped early (convergence, the iteration cap):
+// its remaining products and passes skip, and the cycle end forms x.
+// ---------------------------------------------------------------------------
+struct GmBuf {
+  double2* H;             // (m + 1) x m Hessenberg matrix, H[i * m + j]
+  double2* g;             // m + 1: the rotated right-hand side
+  double* cs;             // m rotation cosines
+  double2* sn;            // m rotation sines
+  double2* h2;            // m + 1: the second projection of the step
+  double2* yv;            // m: the least-squares solution of the cycle
+  double2* part;          // grid x (m + 1) per-block partial sums
+  unsigned int* counter;  // arrival counter of the passes, 0 between them
+  int m;
+};
+
+enum { GM_DOT = 0, GM_UPD_DOT = 1, GM_UPD_NORM = 2 };
+
+// Column j of the Hessenberg matrix after orthogonalisation (||w|| = eta):
+// rotations, residual, stopping test.  One thread.
+__device__ void gm_column(const GmBuf& b, int j, double eta, SolveState* st) {
+  const int m = b.m;
+  for (int i = 0; i <= j; ++i) b.H[i * m + j] = cadd(b.H[i * m + j], b.h2[i]);
+  for (int i = 0; i < j; ++i) {
+    const double2 a = b.H[i * m + j], c = b.H[(i + 1) * m + j];
+    b.H[i * m + j] = cadd(cscale(b.cs[i], a), cmul(b.sn[i], c));
+    b.H[(i + 1) * m + j] = csub(cscale(b.cs[i], c), cmul(cconj(b.sn[i]), a));
+  }
+  const double2 a = b.H[j * m + j];
+  const double aa = cabs(a);
+  const double nu = sqrt(aa * aa + eta * eta);
+  if (nu == 0.0) {  // singular projected system: x stays at the cycle start
+    set_breakdown(st, CCG_BD_HESS);
+    return;
+  }
+  if (aa == 0.0) {
+    b.cs[j] = 0.0;
+    b.sn[j] = mkc(1.0, 0.0);
+    b.H[j * m + j] = mkc(eta, 0.0);
+  } else {
+    const double2 ph = cscale(1.0 / aa, a);
+    b.cs[j] = aa / nu;
+    b.sn[j] = cscale(eta / nu, ph);
+    b.H[j * m + j] = cscale(nu, ph);
+  }
+  b.H[(j + 1) * m + j] = mkc(0.0, 0.0);
+  const double2 gj = b.g[j];
+  b.g[j + 1] = cscale(-1.0, cmul(cconj(b.sn[j]), gj));
+  b.g[j] = cscale(b.cs[j], gj);
+  const int k = st->poll.k + 1;
+  const double rel = cabs(b.g[j + 1]) / st->poll.ynorm;
+  st->poll.k = k;
+  st->poll.relres = rel;
+  st->hist[k] = rel;
+  st->gm_cols = j + 1;
+  st->gm_eta = eta;
+  bool stop = true;
+  if (nonfinite(rel)) st->poll.status = ST_NONFINITE;
+  else if (rel <= st->tol) st->poll.status = ST_OK;
+  else if (k >= st->maxit) st->poll.status = ST_NOT_CONVERGED;
+  else stop = false;
+  if (stop) {
+    st->half = 1;
+    st->gm_final = 1;
+  }
+}
+
+// One orthogonalisation pass over w and the basis v_0 .. v_j (columns of V,
+// leading dimension ldv), E rows per thread kept in registers:
+//   GM_DOT       h1 = V^H w into Hessenberg column j;
+//   GM_UPD_DOT   w -= V h1, then h2 = V^H w;
+//   GM_UPD_NORM  w -= V h2, then ||w|| and the column's rotations.
+// The j + 1 dot products reduce per warp by shuffles, per block through
+// shared memory, and over the grid in the last block to arrive, in block
+// order (deterministic).
+template <class R, int E, int MODE>
+__global__ void __launch_bounds__(kBlock) gm_pass(const cx<R>* __restrict__ V, int64_t ldv, cx<R>* __restrict__ w,
+                                                  int64_t n, int j, GmBuf b, SolveState* st) {
+  if (st->poll.done || st->half) return;
+  __shared__ double2 red[kMaxBasis + 1][kWarps];
+  __shared__ bool is_last;
+  const int J = j + 1, m = b.m;
+  const int64_t i0 = (int64_t)blockIdx.x * (kBlock * E) + threadIdx.x;
+  cx<R> u[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int64_t i = i0 + (int64_t)e * kBlock;
+    u[e] = i < n ? w[i] : mk<R>(0, 0);
+  }
+  if (MODE != GM_DOT) {
+    for (int l = 0; l < J; ++l) {
+      const cx<R> c = narrow<R>(MODE == GM_UPD_DOT ? b.H[l * m + j] : b.h2[l]);
+      const cx<R>* Vl = V + (int64_t)l * ldv;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int64_t i = i0 + (int64_t)e * kBlock;
+        if (i < n) u[e] = csub(u[e], cmul(c, Vl[i]));
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int64_t i = i0 + (int64_t)e * kBlock;
+      if (i < n) w[i] = u[e];
+    }
+  }
+  if (MODE == GM_UPD_NORM) {
+    double acc[1] = {0.0};
+#pragma unroll
+    for (int e = 0; e < E; ++e) acc_nrm2(acc, u[e]);
+    double tot[1];
+    if (grid_reduce<1>(acc, reinterpret_cast<double*>(b.part), b.counter, tot) && threadIdx.x == 0)
+      gm_column(b, j, sqrt(tot[0]), st);
+    return;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int l = 0; l < J; ++l) {
+    const cx<R>* Vl = V + (int64_t)l * ldv;
+    double acc[2] = {0.0, 0.0};
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int64_t i = i0 + (int64_t)e * kBlock;
+      if (i < n) acc_dotc(acc, Vl[i], u[e]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      acc[0] += __shfl_down_sync(0xffffffffu, acc[0], o);
+      acc[1] += __shfl_down_sync(0xffffffffu, acc[1], o);
+    }
+    if (lane == 0) red[l][warp] = mkc(acc[0], acc[1]);
+  }
+  __syncthreads();
+  double2* part = b.part + (int64_t)blockIdx.x * (m + 1);
+  for (int t = threadIdx.x; t < J; t += kBlock) {
+    double2 sum = mkc(0.0, 0.0);
+#pragma unroll
+    for (int q = 0; q < kWarps; ++q) sum = cadd(sum, red[t][q]);
+    part[t] = sum;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(b.counter, 1u) == gridDim.x - 1u;
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  for (int t = threadIdx.x; t < J; t += kBlock) {
+    double2 sum = mkc(0.0, 0.0);
+    for (int q = 0; q < (int)gridDim.x; ++q) sum = cadd(sum, __ldcg(&b.part[(int64_t)q * (m + 1) + t]));
+    if (MODE == GM_DOT) b.H[t * m + j] = sum;
+    else b.h2[t] = sum;
+  }
+  if (threadIdx.x == 0) *b.counter = 0u;
+}
+
+template <class R> struct GmBegin : PhaseBase {  // v_0 = r / beta, g = (beta, 0, ...): a new cycle
+  static constexpr int NQ = 1;
+  int64_t n;
+  const cx<R>* r;
+  cx<R>* v0;
+  GmBuf b;
+  R binv;
+  __device__ __forceinline__ void load(const SolveState* st) { binv = (R)(1.0 / st->gm_beta); }
+  __device__ __forceinline__ void element(int64_t i, double*) { v0[i] = cscale(binv, r[i]); }
+  __device__ void finish(const double*, SolveState* st) {
+    b.g[0] = mkc(st->gm_beta, 0.0);
+    for (int i = 1; i <= b.m; ++i) b.g[i] = mkc(0.0, 0.0);
+    st->gm_cols = 0;
+    st->half = 0;
+  }
+};
+template <class R> struct GmScale : PhaseBase {  // v_{j+1} = w / ||w||
+  static constexpr bool kReduce = false;
+  static constexpr int NQ = 1;
+  int64_t n;
+  const cx<R>* w;
+  cx<R>* v;
+  R einv;
+  __device__ __forceinline__ bool skip(const SolveState* st) const { return st->half != 0; }
+  __device__ __forceinline__ void load(const SolveState* st) { einv = (R)(1.0 / st->gm_eta); }
+  __device__ __forceinline__ void element(int64_t i, double*) { v[i] = cscale(einv, w[i]); }
+  __device__ void finish(const double*, SolveState*) {}
+};
+// Cycle end: R y = g by back substitution (one thread).  Enqueued after
+// every step: at the last step of a cycle (always = 1) it runs while the
+// solve is live, elsewhere only once the cycle has stopped early.
+__global__ void gm_solve(GmBuf b, SolveState* st, int always) {
+  if (st->poll.done || threadIdx.x != 0 || (!always && !st->half)) return;
+  const int cols = st->gm_cols, m = b.m;
+  for (int i = cols - 1; i >= 0; --i) {
+    double2 t = b.g[i];
+    for (int l = i + 1; l < cols; ++l) t = csub(t, cmul(b.H[i * m + l], b.yv[l]));
+    b.yv[i] = cdiv(t, b.H[i * m + i]);
+  }
+}
+template <class R> struct GmXUpd : PhaseBase {  // x += V y; the solve ends here after a final cycle
+  static constexpr int NQ = 1;
+  int64_t n;
+  cx<R>* x;
+  const cx<R>* V;
+  int64_t ldv;
+  const double2* yv;
+  int cols;
+  bool always;  // as for gm_solve
+  __device__ __forceinline__ bool skip(const SolveState* st) const { return !always && !st->half; }
+  __device__ __forceinline__ void load(const SolveState* st) { cols = st->gm_cols; }
+  __device__ __forceinline__ void element(int64_t i, double*) {
+    cx<R> xi = x[i];
+    for (int l = 0; l < cols; ++l) xi = cadd(xi, cmul(narrow<R>(yv[l]), V[(int64_t)l * ldv + i]));
+    x[i] = xi;
+  }
+  __device__ void finish(const double*, SolveState* st) {
+    if (st->gm_final) st->poll.done = 1;
+  }
+};
+template <class R> struct GmRestart : PhaseBase {  // r = y - A x, beta = ||r||; stop if it meets tol
+  static constexpr int NQ = 1;
+  int64_t n;
+  const cx<R>* y;
+  MvOut<R> ax;
+  cx<R>* r;
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    const cx<R> ri = csub(y[i], ax.get(i));
+    r[i] = ri;
+    acc_nrm2(acc, ri);
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    const double beta = sqrt(t[0]);
+    if (beta / st->poll.ynorm <= st->tol) {
+      st->poll.status = ST_OK;
+      st->poll.done = 1;
+      return;
+    }
+    st->gm_beta = beta;
+  }
+};
+
+// ---------------------------------------------------------------------------
 // Host side.
 // ---------------------------------------------------------------------------
 #define CCG_CUDA(call)                                                                 \
@@ -826,8 +1074,21 @@ template <class R> struct Dense {
   double sweep_bytes() const { return dense ? (double)n * (double)n * sizeof(cx<R>) : dip_bytes; }
 };
 
+// Rows per thread and grid of the GMRES orthogonalisation passes.
+static int gm_rows_per_thread(int64_t n) {
+  return n <= (int64_t)kBlock * 1024 ? 1 : (n <= (int64_t)kBlock * 2048 ? 2 : (n <= (int64_t)kBlock * 4096 ? 4 : 8));
+}
+static int gm_grid(int64_t n) {
+  const int64_t per = (int64_t)kBlock * gm_rows_per_thread(n);
+  return (int)std::max<int64_t>(1, (n + per - 1) / per);
+}
+static int64_t gm_ldv(int64_t n) { return (n + 63) / 64 * 64; }
+
 template <class R> struct Ws {
   cx<R>* vec[12];
+  cx<R>* basis;     // GMRES: m + 1 vectors, leading dimension ldv
+  int64_t ldv;
+  GmBuf gm;
   cx<R>* P1;
   cx<R>* P2;
   cx<R>* ystage;
@@ -839,8 +1100,16 @@ template <class R> struct Ws {
   double* scratch;  // a few doubles for standalone results
 };
 
-template <class R> static size_t ws_bytes(int64_t n, const Dense<R>& d, int maxit) {
+// basis = m + 1 GMRES basis vectors (0 for the other methods).
+template <class R> static size_t ws_bytes(int64_t n, const Dense<R>& d, int maxit, int basis = 0) {
   size_t b = 0;
+  if (basis > 0) {
+    const int m = basis - 1;
+    b += align256((size_t)basis * gm_ldv(n) * sizeof(cx<R>));
+    b += align256((size_t)(m + 1) * m * sizeof(double2)) + 4 * align256((size_t)(m + 1) * sizeof(double2)) +
+         align256((size_t)m * sizeof(double));
+    b += align256((size_t)gm_grid(n) * (m + 1) * sizeof(double2)) + align256(sizeof(unsigned int));
+  }
   b += 12 * align256(n * sizeof(cx<R>));
   b += align256(std::max(d.p1_elems(), d.p2_elems()) * sizeof(cx<R>));
   b += align256(d.p2_elems() * sizeof(cx<R>));
@@ -853,10 +1122,26 @@ template <class R> static size_t ws_bytes(int64_t n, const Dense<R>& d, int maxi
   return b;
 }
 
-template <class R> static Ws<R> ws_carve(char* base, int64_t n, const Dense<R>& d, int maxit) {
+template <class R> static Ws<R> ws_carve(char* base, int64_t n, const Dense<R>& d, int maxit, int basis = 0) {
   Ws<R> w;
   size_t off = 0;
   auto take = [&](size_t bytes) { char* p = base + off; off += align256(bytes); return p; };
+  w.basis = nullptr;
+  w.ldv = gm_ldv(n);
+  std::memset(&w.gm, 0, sizeof(w.gm));
+  if (basis > 0) {
+    const int m = basis - 1;
+    w.basis = reinterpret_cast<cx<R>*>(take((size_t)basis * w.ldv * sizeof(cx<R>)));
+    w.gm.H = reinterpret_cast<double2*>(take((size_t)(m + 1) * m * sizeof(double2)));
+    w.gm.g = reinterpret_cast<double2*>(take((size_t)(m + 1) * sizeof(double2)));
+    w.gm.sn = reinterpret_cast<double2*>(take((size_t)(m + 1) * sizeof(double2)));
+    w.gm.h2 = reinterpret_cast<double2*>(take((size_t)(m + 1) * sizeof(double2)));
+    w.gm.yv = reinterpret_cast<double2*>(take((size_t)(m + 1) * sizeof(double2)));
+    w.gm.cs = reinterpret_cast<double*>(take((size_t)m * sizeof(double)));
+    w.gm.part = reinterpret_cast<double2*>(take((size_t)gm_grid(n) * (m + 1) * sizeof(double2)));
+    w.gm.counter = reinterpret_cast<unsigned int*>(take(sizeof(unsigned int)));
+    w.gm.m = m;
+  }
   for (int i = 0; i < 12; ++i) w.vec[i] = reinterpret_cast<cx<R>*>(take(n * sizeof(cx<R>)));
   w.P1 = reinterpret_cast<cx<R>*>(take(std::max(d.p1_elems(), d.p2_elems()) * sizeof(cx<R>)));
   w.P2 = reinterpret_cast<cx<R>*>(take(d.p2_elems() * sizeof(cx<R>)));
@@ -894,6 +1179,18 @@ template <class R> struct Runner {
   }
 
   MvOut<R> plain(const cx<R>* y) const { MvOut<R> m; m.y = y; m.P = nullptr; m.ld = d.n; m.nparts = 1; return m; }
+
+  // One GMRES orthogonalisation pass of step j over the basis.
+  template <int MODE> void gm_pass_launch(cx<R>* wv, int j) {
+    const int grid = gm_grid(d.n);
+    switch (gm_rows_per_thread(d.n)) {
+      case 1: gm_pass<R, 1, MODE><<<grid, kBlock, 0, s>>>(w.basis, w.ldv, wv, d.n, j, w.gm, w.st); break;
+      case 2: gm_pass<R, 2, MODE><<<grid, kBlock, 0, s>>>(w.basis, w.ldv, wv, d.n, j, w.gm, w.st); break;
+      case 4: gm_pass<R, 4, MODE><<<grid, kBlock, 0, s>>>(w.basis, w.ldv, wv, d.n, j, w.gm, w.st); break;
+      default: gm_pass<R, 8, MODE><<<grid, kBlock, 0, s>>>(w.basis, w.ldv, wv, d.n, j, w.gm, w.st); break;
+    }
+    ++h->launches;
+  }
 
   // y = A x.  timed = false for products the device may skip (x0 = 0), which
   // would otherwise enter the sweep timing with a near-zero duration.
@@ -1000,6 +1297,7 @@ static int solve_core(ccg_handle* h, int method, const ccg_operator* op, const W
   init.skip_mv = x0_zero ? 0 : 1;   // without a known-zero start, the device checks x0
   CCG_CUDA(cudaMemcpyAsync(w.st, &init, sizeof(init), cudaMemcpyHostToDevice, s));
   CCG_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(unsigned int), s));
+  if (w.gm.counter) CCG_CUDA(cudaMemsetAsync(w.gm.counter, 0, sizeof(unsigned int), s));
   if (x0_zero) CCG_CUDA(cudaMemsetAsync(x, 0, n * sizeof(cx<R>), s));
   else {
     x_zero_check<R><<<run.grid_vec, kBlock, 0, s>>>(x, n, w.st);
@@ -1077,6 +1375,40 @@ static int solve_core(ccg_handle* h, int method, const ccg_operator* op, const W
       CrXR<R> c; c.n = n; c.x = x; c.r = r; c.p = pv; c.q = q; run.phase(c);
       rho_pq();
     };
+  } else if (method == M_GMRES) {
+    if (w.gm.m < 1) {
+      set_error("GMRES workspace missing");
+      return CCG_ERR_INVALID;
+    }
+    const int m = w.gm.m;
+    cx<R>*r = V[0], *wv = V[1], *t = V[2];
+    const Ws<R> ws = w;
+    auto begin = [=, &run]() {
+      GmBegin<R> b0; b0.n = n; b0.r = r; b0.v0 = ws.basis; b0.b = ws.gm; run.phase(b0);
+    };
+    begin();
+    auto count = std::make_shared<int>(0);
+    step = [=, &run]() {
+      const int j = *count % m;
+      ++*count;
+      cx<R>* vj = ws.basis + (int64_t)j * ws.ldv;
+      run.apply_n(vj, wv, st);
+      run.template gm_pass_launch<GM_DOT>(wv, j);
+      run.template gm_pass_launch<GM_UPD_DOT>(wv, j);
+      run.template gm_pass_launch<GM_UPD_NORM>(wv, j);
+      GmScale<R> sc; sc.n = n; sc.w = wv; sc.v = vj + ws.ldv; run.phase(sc);
+      // cycle end (x += V y): at the last step of a cycle, or at once if the
+      // cycle stopped early; then the restart
+      const bool end = j == m - 1 || *count == maxit;
+      gm_solve<<<1, 32, 0, run.s>>>(ws.gm, st, end ? 1 : 0);
+      ++run.h->launches;
+      GmXUpd<R> xu; xu.n = n; xu.x = x; xu.V = ws.basis; xu.ldv = ws.ldv; xu.yv = ws.gm.yv; xu.always = end;
+      run.phase(xu);
+      if (end && *count < maxit) {
+        GmRestart<R> rs; rs.n = n; rs.y = y; rs.r = r; rs.ax = run.apply_n(x, t, st); run.phase(rs);
+        begin();
+      }
+    };
   } else {  // BiCG
     cx<R>*r = V[0], *rt = V[1], *pv = V[2], *pt = V[3], *q = V[4], *qt = V[5];
     step = [=, &run]() {
@@ -1144,9 +1476,10 @@ static int run_dense(ccg_handle* h, int method, const ccg_operator* op, const vo
                      int maxit, double* res_hist, ccg_info* info) {
   const int64_t n = op->n;
   Dense<R> dl(op, h->num_sms);
-  int rc = arena_reserve(h, ws_bytes<R>(n, dl, maxit));
+  const int basis = method == M_GMRES ? h->gm_restart + 1 : 0;
+  int rc = arena_reserve(h, ws_bytes<R>(n, dl, maxit, basis));
   if (rc != CCG_OK) return rc;
-  Ws<R> w = ws_carve<R>(h->arena, n, dl, maxit);
+  Ws<R> w = ws_carve<R>(h->arena, n, dl, maxit, basis);
   cudaStream_t s = h->stream;
   bool host = false;
   if ((rc = classify(y_in, x_in, &host)) != CCG_OK) return rc;
@@ -1251,10 +1584,11 @@ int solve_refined(ccg_handle* h, int method, const ccg_operator* op, const ccg_o
   Dense<double> d64(op, h->num_sms);
   Dense<float> d32(op_in, h->num_sms);
   const size_t b64 = ws_bytes<double>(n, d64, max_outer);
-  int rc = arena_reserve(h, b64 + ws_bytes<float>(n, d32, inner_maxit));
+  const int basis = method == M_GMRES ? h->gm_restart + 1 : 0;
+  int rc = arena_reserve(h, b64 + ws_bytes<float>(n, d32, inner_maxit, basis));
   if (rc != CCG_OK) return rc;
   Ws<double> w = ws_carve<double>(h->arena, n, d64, max_outer);
-  Ws<float> wi = ws_carve<float>(h->arena + b64, n, d32, inner_maxit);
+  Ws<float> wi = ws_carve<float>(h->arena + b64, n, d32, inner_maxit, basis);
   cudaStream_t s = h->stream;
   bool host = false;
   if ((rc = classify(y_in, x_in, &host)) != CCG_OK) return rc;

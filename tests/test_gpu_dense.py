@@ -98,7 +98,8 @@ def test_dot_products(h, dtype, n):
 
 
 # ------------------------------------------------------------------ solvers
-SMALL = [("bicgstab", False), ("cgnr", False), ("qmr", False), ("cocg", True), ("cocr", True), ("bicg", False)]
+SMALL = [("bicgstab", False), ("cgnr", False), ("qmr", False), ("cocg", True), ("cocr", True), ("bicg", False),
+         ("gmres", False)]
 
 
 def system(n, shift, seed, symmetric, dtype=np.complex128):
@@ -122,6 +123,33 @@ def test_iterates_match_oracle_fp64(h, method, sym):
         assert info["iters"] == ref.iters == k
         assert relerr(xd.cpu().numpy(), ref.x) < 1e-9, (method, k)
         assert np.allclose(hist, ref.hist, rtol=1e-9, atol=0), (method, k)
+
+
+@pytest.mark.parametrize("dtype", [np.complex128, np.complex64])
+def test_gmres_restarts_match_oracle(h, ccg, dtype):
+    """GMRES(5): iterates across several restarts, and the residual history,
+    against the oracle's GMRES(5); ragged n against every tile."""
+    A, y = system(1000, 1.0, 9, False, dtype)
+    x0 = (W.random_vector(1000, 10) * 0.1).astype(dtype)
+    h.set_option(ccg.OPT_GMRES_RESTART, 5)
+    try:
+        op = h.op_dense(dev(A))
+        oop = O.DenseOp(A)
+        tol = 1e-9 if dtype == np.complex128 else 2e-4
+        for k in (1, 4, 5, 6, 11, 17):
+            ref = O.solve(oop, "gmres", y, x0=x0, tol=0.0, maxit=k, restart=5)
+            xd = dev(x0.copy())
+            st, info, hist = h.solve("gmres", op, dev(y), xd, tol=0.0, maxit=k)
+            assert info["iters"] == ref.iters == k
+            assert relerr(xd.cpu().numpy(), ref.x) < tol, k
+            assert np.allclose(hist, ref.hist, rtol=tol, atol=0), k
+        ref = O.solve(oop, "gmres", y, tol=1e-5 if dtype == np.complex64 else 1e-10, maxit=400, restart=5)
+        xd = torch.zeros(1000, dtype=xd.dtype, device="cuda")
+        st, info, hist = h.solve("gmres", op, dev(y), xd, tol=1e-5 if dtype == np.complex64 else 1e-10, maxit=400)
+        assert st == 0 == ref.status
+        assert abs(info["iters"] - ref.iters) <= 1
+    finally:
+        h.set_option(ccg.OPT_GMRES_RESTART, 30)
 
 
 @pytest.mark.parametrize("method,sym", SMALL)
