@@ -12,11 +12,13 @@
 // single or double precision (abstract, Sec. 5 `ddprecision`).  It prints
 // no recurrences, so each method below is the unpreconditioned textbook form
 // of the source the manual names for it (Sec. 2.1 PIM: BiCGSTAB, CGNR, QMR,
-// BiCG (`bigcg`), restarted GMRES (`rgmres`); Sec. 2.2 Sarkar: the
-// complex-symmetric CG; Sec. 3.4: COCR of Sogabe and Zhang).  Readings where
-// the manual is silent:
+// BiCG (`bigcg`), restarted GMRES (`rgmres`), CGS, CGNE; Sec. 2.2 Sarkar:
+// the complex-symmetric CG; Sec. 3.4: COCR of Sogabe and Zhang).  Readings
+// where the manual is silent:
 //   * stopping rule: ||r_k||_2 / ||y||_2 <= tol on the recurrence residual;
-//   * shadow vectors (BiCGSTAB r^, QMR w~_1, BiCG r~_0) equal r_0;
+//   * shadow vectors (BiCGSTAB r^, QMR w~_1, BiCG r~_0, CGS r^) equal r_0;
+//   * CGNE is Craig's method: CG on A A^H u = y with x = A^H u, residual
+//     r = y - A x;
 //   * complex BiCG pairs A with A^H and conjugated products (the shadow
 //     recurrences take conj(alpha), conj(beta));
 //   * COCR uses the unconjugated form like COCG and needs A = A^T;
@@ -61,7 +63,8 @@ template <class R> using C = std::complex<R>;
 using Z = std::complex<double>;
 
 enum Status { ORC_OK = 0, ORC_NOT_CONVERGED = 1, ORC_BREAKDOWN = 2, ORC_INVALID = -1 };
-enum Method { ORC_BICGSTAB = 0, ORC_CGNR = 1, ORC_QMR = 2, ORC_COCG = 3, ORC_COCR = 4, ORC_BICG = 5, ORC_GMRES = 6 };
+enum Method { ORC_BICGSTAB = 0, ORC_CGNR = 1, ORC_QMR = 2, ORC_COCG = 3, ORC_COCR = 4, ORC_BICG = 5, ORC_GMRES = 6,
+              ORC_CGS = 7, ORC_CGNE = 8 };
 // Which scalar vanished when a method breaks down.
 enum Breakdown { BD_NONE = 0, BD_RHO = 1, BD_SIGMA = 2, BD_TT = 3, BD_OMEGA = 4, BD_GAMMA = 5,
                  BD_WW = 6, BD_XI = 7, BD_DELTA = 8, BD_EPS = 9, BD_BETA = 10, BD_MU = 11, BD_HESS = 12 };
@@ -577,6 +580,82 @@ Result bicg(const Operator<R>& A, const C<R>* y, C<R>* x, double tol, int maxit,
   return {maxit, ORC_NOT_CONVERGED, BD_NONE};
 }
 
+// CGS (Sonneveld 1989; PIM's `cgs`, Sec. 2.1), complex form with
+// conjugated products and shadow r^ = r_0: two products per iteration, the
+// BiCG polynomial applied twice.
+template <class R>
+Result cgs(const Operator<R>& A, const C<R>* y, C<R>* x, double tol, int maxit, double* hist) {
+  const int64_t n = A.n;
+  std::vector<C<R>> r(n), rh(n), u(n), p(n), q(n), v(n), uh(n), qh(n);
+  const double ynorm = start(A, y, x, r.data());
+  if (ynorm == 0) { hist[0] = 0; return {0, ORC_OK, BD_NONE}; }
+  hist[0] = nrm2(n, r.data()) / ynorm;
+  if (hist[0] <= tol) return {0, ORC_OK, BD_NONE};
+  rh = r;
+  Z rho_old = 1.0;
+  for (int k = 1; k <= maxit; ++k) {
+    const Z rho = dotc(n, rh.data(), r.data());
+    if (tiny<R>(rho)) return {k - 1, ORC_BREAKDOWN, BD_RHO};
+    if (k == 1) {
+      u = r;
+      p = u;
+    } else {
+      const C<R> be = C<R>(rho / rho_old);
+      for (int64_t i = 0; i < n; ++i) {
+        u[i] = r[i] + be * q[i];
+        p[i] = u[i] + be * (q[i] + be * p[i]);
+      }
+    }
+    A.apply(p.data(), v.data());
+    const Z sigma = dotc(n, rh.data(), v.data());
+    if (tiny<R>(sigma)) return {k - 1, ORC_BREAKDOWN, BD_SIGMA};
+    const C<R> al = C<R>(rho / sigma);
+    for (int64_t i = 0; i < n; ++i) {
+      q[i] = u[i] - al * v[i];
+      uh[i] = u[i] + q[i];
+      x[i] += al * uh[i];
+    }
+    A.apply(uh.data(), qh.data());
+    for (int64_t i = 0; i < n; ++i) r[i] -= al * qh[i];
+    hist[k] = nrm2(n, r.data()) / ynorm;
+    if (hist[k] <= tol) return {k, ORC_OK, BD_NONE};
+    rho_old = rho;
+  }
+  return {maxit, ORC_NOT_CONVERGED, BD_NONE};
+}
+
+// CGNE (Craig's method; PIM's `cgne`, Sec. 2.1): CG on A A^H u = y with
+// x = A^H u, carried in x directly; the residual is r = y - A x.
+template <class R>
+Result cgne(const Operator<R>& A, const C<R>* y, C<R>* x, double tol, int maxit, double* hist) {
+  const int64_t n = A.n;
+  std::vector<C<R>> r(n), p(n), w(n), z(n);
+  const double ynorm = start(A, y, x, r.data());
+  if (ynorm == 0) { hist[0] = 0; return {0, ORC_OK, BD_NONE}; }
+  hist[0] = nrm2(n, r.data()) / ynorm;
+  if (hist[0] <= tol) return {0, ORC_OK, BD_NONE};
+  A.apply_h(r.data(), p.data());
+  double gamma = dotc(n, r.data(), r.data()).real();
+  for (int k = 1; k <= maxit; ++k) {
+    const double pp = dotc(n, p.data(), p.data()).real();
+    if (tiny<R>(pp)) return {k - 1, ORC_BREAKDOWN, BD_WW};
+    const R al = R(gamma / pp);
+    A.apply(p.data(), w.data());
+    for (int64_t i = 0; i < n; ++i) {
+      x[i] += al * p[i];
+      r[i] -= al * w[i];
+    }
+    hist[k] = nrm2(n, r.data()) / ynorm;
+    if (hist[k] <= tol) return {k, ORC_OK, BD_NONE};
+    const double gamma_new = dotc(n, r.data(), r.data()).real();
+    const R be = R(gamma_new / gamma);
+    A.apply_h(r.data(), z.data());
+    for (int64_t i = 0; i < n; ++i) p[i] = z[i] + be * p[i];
+    gamma = gamma_new;
+  }
+  return {maxit, ORC_NOT_CONVERGED, BD_NONE};
+}
+
 // Restarted GMRES(m) (Saad & Schultz 1986; PIM's `rgmres`, Sec. 2.1),
 // complex form: Arnoldi with modified Gram-Schmidt in <u, v> = sum conj(u_i)
 // v_i, the Hessenberg least-squares problem reduced by complex Givens
@@ -671,6 +750,8 @@ Result solve(int method, const Operator<R>& A, const C<R>* y, C<R>* x, double to
       return cocr(A, y, x, tol, maxit, hist);
     case ORC_BICG: return bicg(A, y, x, tol, maxit, hist);
     case ORC_GMRES: return gmres(A, y, x, tol, maxit, hist, g_restart);
+    case ORC_CGS: return cgs(A, y, x, tol, maxit, hist);
+    case ORC_CGNE: return cgne(A, y, x, tol, maxit, hist);
   }
   return {0, ORC_INVALID, BD_NONE};
 }

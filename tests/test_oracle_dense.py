@@ -22,7 +22,7 @@ from paper_1208_4869_gb300 import workloads as W
 
 METHODS = ["bicgstab", "cgnr", "qmr"]
 SYM = ("cocg", "cocr")                 # methods for complex-symmetric A
-ALL = METHODS + ["cocg", "cocr", "bicg", "gmres"]
+ALL = METHODS + ["cocg", "cocr", "bicg", "gmres", "cgs", "cgne"]
 
 
 def relres(A, x, y):
@@ -121,7 +121,7 @@ def test_finite_termination_small(method):
     if method in SYM:
         A = (A + A.T) / 2
     op = O.DenseOp(A, symmetric=(method in SYM))
-    steps = n + 1 if method == "cgnr" else n
+    steps = n + 1 if method in ("cgnr", "cgne") else n
     r = O.solve(op, method, y, tol=0.0, maxit=steps)
     assert relres(A, r.x, y) < 1e-8
 
@@ -216,10 +216,15 @@ def test_breakdowns():
     # GMRES: a zero Hessenberg column (A = 0) leaves the projected system singular.
     r = O.solve(O.DenseOp(np.zeros((4, 4), complex)), "gmres", np.ones(4, complex), tol=1e-12, maxit=5)
     assert r.status == O.BREAKDOWN and r.detail == 12 and r.iters == 0
-    # BiCG: sigma = <p~, A p> = 0 on the swap matrix with y = e_1.
+    # BiCG and CGS: sigma = <p~, A p> = 0 on the swap matrix with y = e_1.
     A = np.array([[0, 1], [1, 0]], dtype=np.complex128)
-    r = O.solve(O.DenseOp(A), "bicg", np.array([1, 0], dtype=complex), tol=1e-12, maxit=5)
-    assert r.status == O.BREAKDOWN and r.detail == 2 and r.iters == 0
+    for m in ("bicg", "cgs"):
+        r = O.solve(O.DenseOp(A), m, np.array([1, 0], dtype=complex), tol=1e-12, maxit=5)
+        assert r.status == O.BREAKDOWN and r.detail == 2 and r.iters == 0
+    # CGNE: p = A^H r0 = 0 with r0 != 0 (r0 in the null space of A^H).
+    A = np.array([[1, 1], [1, 1]], dtype=np.complex128)
+    r = O.solve(O.DenseOp(A), "cgne", np.array([1, -1], dtype=complex), tol=1e-12, maxit=5)
+    assert r.status == O.BREAKDOWN and r.detail == 6 and r.iters == 0
 
 
 def test_maxit_not_converged():
@@ -387,3 +392,35 @@ def test_gmres_restarts_from_the_cycle_end():
     r = O.solve(op, "gmres", y, x0=x0, tol=1e-12, maxit=400, restart=3)
     assert r.status == O.OK and np.all(np.diff(r.hist) <= 1e-15)
     assert relres(A, r.x, y) < 1e-11
+
+
+def test_cgs_iterates_match_scipy():
+    """scipy's CGS (independent code): shadow r^ = r_0, conjugated products."""
+    A, y = W.dense_system(64, 1.5, 19)
+    x0 = W.random_vector(64, 20)
+    xs = []
+    sla.cgs(A, y, x0=x0.copy(), rtol=1e-15, atol=0.0, maxiter=10, callback=lambda xk: xs.append(xk.copy()))
+    op = O.DenseOp(A)
+    for k in range(1, 9):
+        r = O.solve(op, "cgs", y, x0=x0, tol=0.0, maxit=k)
+        assert r.iters == k
+        assert np.linalg.norm(r.x - xs[k - 1]) / np.linalg.norm(xs[k - 1]) < 1e-11
+
+
+def test_cgne_is_cg_on_the_adjoint_normal_equations():
+    """CGNE is CG on A A^H u = r_0 with x = x_0 + A^H u (scipy's CG on that
+    Hermitian matrix, independent code); its error ||x* - x_k|| decreases."""
+    A, y = W.dense_system(40, 1.0, 23)
+    x0 = W.random_vector(40, 24)
+    r0 = y - A @ x0
+    us = []
+    sla.cg(A @ A.conj().T, r0, rtol=1e-15, atol=0.0, maxiter=8, callback=lambda uk: us.append(uk.copy()))
+    op = O.DenseOp(A)
+    xstar = np.linalg.solve(A, y)
+    errs = []
+    for k in range(1, 7):
+        r = O.solve(op, "cgne", y, x0=x0, tol=0.0, maxit=k)
+        want = x0 + A.conj().T @ us[k - 1]
+        assert np.linalg.norm(r.x - want) / np.linalg.norm(want) < 1e-11
+        errs.append(np.linalg.norm(r.x - xstar))
+    assert np.all(np.diff(errs) < 0)
