@@ -12,13 +12,18 @@
 // single or double precision (abstract, Sec. 5 `ddprecision`).  It prints
 // no recurrences, so each method below is the unpreconditioned textbook form
 // of the source the manual names for it (Sec. 2.1 PIM: BiCGSTAB, CGNR, QMR,
-// BiCG (`bigcg`), restarted GMRES (`rgmres`), CGS, CGNE; Sec. 2.2 Sarkar:
+// BiCG (`bigcg`), restarted GMRES (`rgmres`), CGS, CGNE, TFQMR; Sec. 2.2 Sarkar:
 // the complex-symmetric CG; Sec. 3.4: COCR of Sogabe and Zhang).  Readings
 // where the manual is silent:
 //   * stopping rule: ||r_k||_2 / ||y||_2 <= tol on the recurrence residual;
 //   * shadow vectors (BiCGSTAB r^, QMR w~_1, BiCG r~_0, CGS r^) equal r_0;
 //   * CGNE is Craig's method: CG on A A^H u = y with x = A^H u, residual
 //     r = y - A x;
+//   * TFQMR (Freund): an iteration is its two half-steps (two products); it
+//     keeps no residual vector, so its recorded residual and stopping test
+//     use the bound ||r_{m+1}|| <= sqrt(m + 2) tau_{m+1} after half-step m,
+//     tested after every half-step (an exit after the first half counts as
+//     the iteration); shadow r^ = r_0;
 //   * complex BiCG pairs A with A^H and conjugated products (the shadow
 //     recurrences take conj(alpha), conj(beta));
 //   * COCR uses the unconjugated form like COCG and needs A = A^T;
@@ -64,7 +69,7 @@ using Z = std::complex<double>;
 
 enum Status { ORC_OK = 0, ORC_NOT_CONVERGED = 1, ORC_BREAKDOWN = 2, ORC_INVALID = -1 };
 enum Method { ORC_BICGSTAB = 0, ORC_CGNR = 1, ORC_QMR = 2, ORC_COCG = 3, ORC_COCR = 4, ORC_BICG = 5, ORC_GMRES = 6,
-              ORC_CGS = 7, ORC_CGNE = 8 };
+              ORC_CGS = 7, ORC_CGNE = 8, ORC_TFQMR = 9 };
 // Which scalar vanished when a method breaks down.
 enum Breakdown { BD_NONE = 0, BD_RHO = 1, BD_SIGMA = 2, BD_TT = 3, BD_OMEGA = 4, BD_GAMMA = 5,
                  BD_WW = 6, BD_XI = 7, BD_DELTA = 8, BD_EPS = 9, BD_BETA = 10, BD_MU = 11, BD_HESS = 12 };
@@ -656,6 +661,68 @@ Result cgne(const Operator<R>& A, const C<R>* y, C<R>* x, double tol, int maxit,
   return {maxit, ORC_NOT_CONVERGED, BD_NONE};
 }
 
+// TFQMR (Freund 1993; PIM's `tfqmr`, Sec. 2.1), complex form: two
+// half-steps per iteration, w the BiCG-squared residual, d the QMR search
+// direction, tau the quasi-residual norm, conjugated products with r^ = r_0.
+template <class R>
+Result tfqmr(const Operator<R>& A, const C<R>* y, C<R>* x, double tol, int maxit, double* hist) {
+  const int64_t n = A.n;
+  std::vector<C<R>> r(n), w(n), u(n), un(n), v(n), uh(n), d(n), rh(n);
+  const double ynorm = start(A, y, x, r.data());
+  if (ynorm == 0) { hist[0] = 0; return {0, ORC_OK, BD_NONE}; }
+  hist[0] = nrm2(n, r.data()) / ynorm;
+  if (hist[0] <= tol) return {0, ORC_OK, BD_NONE};
+  w = r;
+  u = r;
+  rh = r;
+  A.apply(u.data(), uh.data());  // uh = A u_0
+  v = uh;
+  double tau = nrm2(n, r.data()), theta = 0.0;
+  Z eta = 0.0, alpha = 0.0;
+  Z rho = dotc(n, rh.data(), r.data());
+  for (int k = 1; k <= maxit; ++k) {
+    for (int half = 0; half < 2; ++half) {
+      const int m = 2 * (k - 1) + half;
+      if (half == 0) {
+        const Z sigma = dotc(n, rh.data(), v.data());
+        if (tiny<R>(sigma)) return {k - 1, ORC_BREAKDOWN, BD_SIGMA};
+        alpha = rho / sigma;
+        const C<R> al = C<R>(alpha);
+        for (int64_t i = 0; i < n; ++i) un[i] = u[i] - al * v[i];
+      }
+      const std::vector<C<R>>& um = half == 0 ? u : un;  // u_m; uh holds A u_m
+      const C<R> al = C<R>(alpha), f = C<R>(theta * theta / alpha * eta);
+      for (int64_t i = 0; i < n; ++i) {
+        w[i] -= al * uh[i];
+        d[i] = um[i] + f * d[i];
+      }
+      theta = nrm2(n, w.data()) / tau;
+      const double c = 1.0 / std::sqrt(1.0 + theta * theta);
+      tau = tau * theta * c;
+      eta = c * c * alpha;
+      const C<R> et = C<R>(eta);
+      for (int64_t i = 0; i < n; ++i) x[i] += et * d[i];
+      hist[k] = tau * std::sqrt(m + 2.0) / ynorm;
+      if (hist[k] <= tol) return {k, ORC_OK, BD_NONE};
+      if (half == 0) {
+        A.apply(un.data(), uh.data());  // A u_{m+1}
+      } else {
+        const Z rho_new = dotc(n, rh.data(), w.data());
+        if (tiny<R>(rho_new)) return {k, ORC_BREAKDOWN, BD_RHO};
+        const C<R> be = C<R>(rho_new / rho), be2 = be * be;
+        rho = rho_new;
+        for (int64_t i = 0; i < n; ++i) {
+          u[i] = w[i] + be * un[i];
+          v[i] = be * uh[i] + be2 * v[i];
+        }
+        A.apply(u.data(), uh.data());   // A u_{m+1}
+        for (int64_t i = 0; i < n; ++i) v[i] += uh[i];
+      }
+    }
+  }
+  return {maxit, ORC_NOT_CONVERGED, BD_NONE};
+}
+
 // Restarted GMRES(m) (Saad & Schultz 1986; PIM's `rgmres`, Sec. 2.1),
 // complex form: Arnoldi with modified Gram-Schmidt in <u, v> = sum conj(u_i)
 // v_i, the Hessenberg least-squares problem reduced by complex Givens
@@ -752,6 +819,7 @@ Result solve(int method, const Operator<R>& A, const C<R>* y, C<R>* x, double to
     case ORC_GMRES: return gmres(A, y, x, tol, maxit, hist, g_restart);
     case ORC_CGS: return cgs(A, y, x, tol, maxit, hist);
     case ORC_CGNE: return cgne(A, y, x, tol, maxit, hist);
+    case ORC_TFQMR: return tfqmr(A, y, x, tol, maxit, hist);
   }
   return {0, ORC_INVALID, BD_NONE};
 }

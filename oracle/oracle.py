@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY.  Everything here is a thin marshalling layer:
 the arithmetic lives in ccg_oracle.cpp, which restates the textbook methods
 the CCGPAK manual names (Sec. 2.1 PIM: BiCGSTAB, CGNR, QMR, BiCG, GMRES(m), CGS,
-CGNE; Sec. 2.2
+CGNE, TFQMR; Sec. 2.2
 the Sarkar complex-symmetric CG; Sec. 3.4 COCR) and the discrete-dipole
 operator of its DDSCAT application (Sec. 1).
 """
@@ -14,9 +14,9 @@ import numpy as np
 
 from . import build as _build
 
-BICGSTAB, CGNR, QMR, COCG, COCR, BICG, GMRES, CGS, CGNE = 0, 1, 2, 3, 4, 5, 6, 7, 8
+BICGSTAB, CGNR, QMR, COCG, COCR, BICG, GMRES, CGS, CGNE, TFQMR = 0, 1, 2, 3, 4, 5, 6, 7, 8, 9
 METHODS = {"bicgstab": BICGSTAB, "cgnr": CGNR, "qmr": QMR, "cocg": COCG, "cocr": COCR, "bicg": BICG,
-           "gmres": GMRES, "cgs": CGS, "cgne": CGNE}
+           "gmres": GMRES, "cgs": CGS, "cgne": CGNE, "tfqmr": TFQMR}
 OK, NOT_CONVERGED, BREAKDOWN, INVALID = 0, 1, 2, -1
 
 _lib = None

@@ -22,7 +22,7 @@ from paper_1208_4869_gb300 import workloads as W
 
 METHODS = ["bicgstab", "cgnr", "qmr"]
 SYM = ("cocg", "cocr")                 # methods for complex-symmetric A
-ALL = METHODS + ["cocg", "cocr", "bicg", "gmres", "cgs", "cgne"]
+ALL = METHODS + ["cocg", "cocr", "bicg", "gmres", "cgs", "cgne", "tfqmr"]
 
 
 def relres(A, x, y):
@@ -218,7 +218,7 @@ def test_breakdowns():
     assert r.status == O.BREAKDOWN and r.detail == 12 and r.iters == 0
     # BiCG and CGS: sigma = <p~, A p> = 0 on the swap matrix with y = e_1.
     A = np.array([[0, 1], [1, 0]], dtype=np.complex128)
-    for m in ("bicg", "cgs"):
+    for m in ("bicg", "cgs", "tfqmr"):
         r = O.solve(O.DenseOp(A), m, np.array([1, 0], dtype=complex), tol=1e-12, maxit=5)
         assert r.status == O.BREAKDOWN and r.detail == 2 and r.iters == 0
     # CGNE: p = A^H r0 = 0 with r0 != 0 (r0 in the null space of A^H).
@@ -424,3 +424,19 @@ def test_cgne_is_cg_on_the_adjoint_normal_equations():
         assert np.linalg.norm(r.x - want) / np.linalg.norm(want) < 1e-11
         errs.append(np.linalg.norm(r.x - xstar))
     assert np.all(np.diff(errs) < 0)
+
+
+def test_tfqmr_iterates_match_scipy():
+    """scipy's TFQMR (independent code) calls back after every half-step; an
+    iteration here is two half-steps (two products)."""
+    A, y = W.dense_system(64, 1.5, 19)
+    x0 = W.random_vector(64, 20)
+    xs = []
+    sla.tfqmr(A, y, x0=x0.copy(), rtol=1e-15, atol=0.0, maxiter=20, callback=lambda xk: xs.append(xk.copy()))
+    op = O.DenseOp(A)
+    for k in range(1, 8):
+        r = O.solve(op, "tfqmr", y, x0=x0, tol=0.0, maxit=k)
+        assert r.iters == k
+        assert np.linalg.norm(r.x - xs[2 * k - 1]) / np.linalg.norm(xs[2 * k - 1]) < 1e-12
+        # the recorded quantity bounds the true residual
+        assert relres(A, r.x, y) <= r.hist[k] * (1 + 1e-12)
