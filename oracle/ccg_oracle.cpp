@@ -13,8 +13,8 @@
 // no recurrences, so each method below is the unpreconditioned textbook form
 // of the source the manual names for it (Sec. 2.1 PIM: BiCGSTAB, CGNR, QMR,
 // BiCG (`bigcg`), restarted GMRES (`rgmres`), CGS, CGNE, TFQMR; Sec. 2.2 Sarkar:
-// the complex-symmetric CG; Sec. 3.4: COCR of Sogabe and Zhang).  Readings
-// where the manual is silent:
+// the complex-symmetric CG; Sec. 3.1: BiCGstab(l); Sec. 3.4: COCR of Sogabe
+// and Zhang).  Readings where the manual is silent:
 //   * stopping rule: ||r_k||_2 / ||y||_2 <= tol on the recurrence residual;
 //   * shadow vectors (BiCGSTAB r^, QMR w~_1, BiCG r~_0, CGS r^) equal r_0;
 //   * CGNE is Craig's method: CG on A A^H u = y with x = A^H u, residual
@@ -24,6 +24,12 @@
 //     use the bound ||r_{m+1}|| <= sqrt(m + 2) tau_{m+1} after half-step m,
 //     tested after every half-step (an exit after the first half counts as
 //     the iteration); shadow r^ = r_0;
+//   * BiCGstab(l) is the vanilla algorithm of Sleijpen and Fokkema (the base
+//     form of Fokkema's thesis, Sec. 3.1), without the two enhancements the
+//     manual names; an iteration is one cycle of l BiCG steps and the
+//     l-dimensional minimal-residual update (2 l products); the residual
+//     r^_0 is tested after every BiCG step (an exit there counts as the
+//     iteration) and at the cycle end; l (default 2) is a parameter;
 //   * complex BiCG pairs A with A^H and conjugated products (the shadow
 //     recurrences take conj(alpha), conj(beta));
 //   * COCR uses the unconjugated form like COCG and needs A = A^T;
@@ -69,13 +75,15 @@ using Z = std::complex<double>;
 
 enum Status { ORC_OK = 0, ORC_NOT_CONVERGED = 1, ORC_BREAKDOWN = 2, ORC_INVALID = -1 };
 enum Method { ORC_BICGSTAB = 0, ORC_CGNR = 1, ORC_QMR = 2, ORC_COCG = 3, ORC_COCR = 4, ORC_BICG = 5, ORC_GMRES = 6,
-              ORC_CGS = 7, ORC_CGNE = 8, ORC_TFQMR = 9 };
+              ORC_CGS = 7, ORC_CGNE = 8, ORC_TFQMR = 9, ORC_BICGSTABL = 10 };
 // Which scalar vanished when a method breaks down.
 enum Breakdown { BD_NONE = 0, BD_RHO = 1, BD_SIGMA = 2, BD_TT = 3, BD_OMEGA = 4, BD_GAMMA = 5,
                  BD_WW = 6, BD_XI = 7, BD_DELTA = 8, BD_EPS = 9, BD_BETA = 10, BD_MU = 11, BD_HESS = 12 };
 
-// Restart length of GMRES(m), set through orc_set_restart.
+// Restart length of GMRES(m) and degree l of BiCGstab(l), set through
+// orc_set_restart and orc_set_bicgstab_l.
 int g_restart = 30;
+int g_bicgstab_l = 2;
 
 template <class R> double guard();
 template <> double guard<double>() { return 1e-300; }
@@ -723,6 +731,93 @@ Result tfqmr(const Operator<R>& A, const C<R>* y, C<R>* x, double tol, int maxit
   return {maxit, ORC_NOT_CONVERGED, BD_NONE};
 }
 
+// BiCGstab(l) (Sleijpen & Fokkema 1993, vanilla form; manual Sec. 3.1),
+// complex: l BiCG steps on the vectors r^_0..r^_l, u^_0..u^_l, then the
+// minimal-residual polynomial of degree l by modified Gram-Schmidt on
+// r^_1..r^_l.  Shadow r~ = r_0, <a, b> = sum conj(a_i) b_i.
+template <class R>
+Result bicgstabl(const Operator<R>& A, const C<R>* y, C<R>* x, double tol, int maxit, double* hist, int L) {
+  const int64_t n = A.n;
+  std::vector<std::vector<C<R>>> rh(L + 1, std::vector<C<R>>(n)), uh(L + 1, std::vector<C<R>>(n));
+  std::vector<C<R>> rt(n);
+  const double ynorm = start(A, y, x, rh[0].data());
+  if (ynorm == 0) { hist[0] = 0; return {0, ORC_OK, BD_NONE}; }
+  hist[0] = nrm2(n, rh[0].data()) / ynorm;
+  if (hist[0] <= tol) return {0, ORC_OK, BD_NONE};
+  rt = rh[0];
+  Z rho0 = 1.0, alpha = 0.0, omega = 1.0;
+  std::vector<Z> tau((size_t)(L + 1) * (L + 1)), gp(L + 1), g(L + 1), gpp(L + 1);
+  std::vector<double> sigma(L + 1);
+  auto T = [&](int i, int j) -> Z& { return tau[(size_t)i * (L + 1) + j]; };
+  for (int k = 1; k <= maxit; ++k) {
+    rho0 = -omega * rho0;
+    for (int j = 0; j < L; ++j) {  // BiCG part
+      const Z rho1 = dotc(n, rt.data(), rh[j].data());
+      if (tiny<R>(rho0)) return {k - 1, ORC_BREAKDOWN, BD_RHO};
+      const C<R> be = C<R>(alpha * rho1 / rho0);
+      rho0 = rho1;
+      for (int i = 0; i <= j; ++i)
+        for (int64_t e = 0; e < n; ++e) uh[i][e] = rh[i][e] - be * uh[i][e];
+      A.apply(uh[j].data(), uh[j + 1].data());
+      const Z gam = dotc(n, rt.data(), uh[j + 1].data());
+      if (tiny<R>(gam)) return {k - 1, ORC_BREAKDOWN, BD_SIGMA};
+      alpha = rho0 / gam;
+      const C<R> al = C<R>(alpha);
+      for (int i = 0; i <= j; ++i)
+        for (int64_t e = 0; e < n; ++e) rh[i][e] -= al * uh[i + 1][e];
+      for (int64_t e = 0; e < n; ++e) x[e] += al * uh[0][e];
+      const double rel = nrm2(n, rh[0].data()) / ynorm;
+      if (rel <= tol) {
+        hist[k] = rel;
+        return {k, ORC_OK, BD_NONE};
+      }
+      A.apply(rh[j].data(), rh[j + 1].data());
+    }
+    for (int j = 1; j <= L; ++j) {  // minimal-residual part
+      for (int i = 1; i < j; ++i) {
+        T(i, j) = dotc(n, rh[i].data(), rh[j].data()) / sigma[i];
+        const C<R> t = C<R>(T(i, j));
+        for (int64_t e = 0; e < n; ++e) rh[j][e] -= t * rh[i][e];
+      }
+      sigma[j] = dotc(n, rh[j].data(), rh[j].data()).real();
+      if (tiny<R>(sigma[j])) return {k - 1, ORC_BREAKDOWN, BD_MU};
+      gp[j] = dotc(n, rh[j].data(), rh[0].data()) / sigma[j];
+    }
+    g[L] = gp[L];
+    omega = g[L];
+    for (int j = L - 1; j >= 1; --j) {
+      Z t = gp[j];
+      for (int i = j + 1; i <= L; ++i) t -= T(j, i) * g[i];
+      g[j] = t;
+    }
+    for (int j = 1; j < L; ++j) {
+      Z t = g[j + 1];
+      for (int i = j + 1; i < L; ++i) t += T(j, i) * g[i + 1];
+      gpp[j] = t;
+    }
+    {
+      const C<R> g1 = C<R>(g[1]), gpl = C<R>(gp[L]), gl = C<R>(g[L]);
+      for (int64_t e = 0; e < n; ++e) {
+        x[e] += g1 * rh[0][e];
+        rh[0][e] -= gpl * rh[L][e];
+        uh[0][e] -= gl * uh[L][e];
+      }
+    }
+    for (int j = 1; j < L; ++j) {
+      const C<R> gj = C<R>(g[j]), gppj = C<R>(gpp[j]), gpj = C<R>(gp[j]);
+      for (int64_t e = 0; e < n; ++e) {
+        uh[0][e] -= gj * uh[j][e];
+        x[e] += gppj * rh[j][e];
+        rh[0][e] -= gpj * rh[j][e];
+      }
+    }
+    hist[k] = nrm2(n, rh[0].data()) / ynorm;
+    if (hist[k] <= tol) return {k, ORC_OK, BD_NONE};
+    if (tiny<R>(omega)) return {k, ORC_BREAKDOWN, BD_OMEGA};
+  }
+  return {maxit, ORC_NOT_CONVERGED, BD_NONE};
+}
+
 // Restarted GMRES(m) (Saad & Schultz 1986; PIM's `rgmres`, Sec. 2.1),
 // complex form: Arnoldi with modified Gram-Schmidt in <u, v> = sum conj(u_i)
 // v_i, the Hessenberg least-squares problem reduced by complex Givens
@@ -820,6 +915,7 @@ Result solve(int method, const Operator<R>& A, const C<R>* y, C<R>* x, double to
     case ORC_CGS: return cgs(A, y, x, tol, maxit, hist);
     case ORC_CGNE: return cgne(A, y, x, tol, maxit, hist);
     case ORC_TFQMR: return tfqmr(A, y, x, tol, maxit, hist);
+    case ORC_BICGSTABL: return bicgstabl(A, y, x, tol, maxit, hist, g_bicgstab_l);
   }
   return {0, ORC_INVALID, BD_NONE};
 }
@@ -873,6 +969,8 @@ int orc_abi_version() { return 1; }
 
 // Restart length m of GMRES(m) for later solves (1 <= m <= 256).
 void orc_set_restart(int m) { g_restart = m < 1 ? 1 : (m > 256 ? 256 : m); }
+// Degree l of BiCGstab(l) for later solves (1 <= l <= 8).
+void orc_set_bicgstab_l(int l) { g_bicgstab_l = l < 1 ? 1 : (l > 8 ? 8 : l); }
 
 // symmetric != 0 asserts A = A^T (checked by the caller), which COCG and COCR require.
 void* orc_op_dense_c128(int64_t n, int64_t lda, const void* A, int symmetric) {

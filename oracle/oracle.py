@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY.  Everything here is a thin marshalling layer:
 the arithmetic lives in ccg_oracle.cpp, which restates the textbook methods
 the CCGPAK manual names (Sec. 2.1 PIM: BiCGSTAB, CGNR, QMR, BiCG, GMRES(m), CGS,
-CGNE, TFQMR; Sec. 2.2
+CGNE, TFQMR; Sec. 3.1 BiCGstab(l); Sec. 2.2
 the Sarkar complex-symmetric CG; Sec. 3.4 COCR) and the discrete-dipole
 operator of its DDSCAT application (Sec. 1).
 """
@@ -14,9 +14,9 @@ import numpy as np
 
 from . import build as _build
 
-BICGSTAB, CGNR, QMR, COCG, COCR, BICG, GMRES, CGS, CGNE, TFQMR = 0, 1, 2, 3, 4, 5, 6, 7, 8, 9
+BICGSTAB, CGNR, QMR, COCG, COCR, BICG, GMRES, CGS, CGNE, TFQMR, BICGSTABL = range(11)
 METHODS = {"bicgstab": BICGSTAB, "cgnr": CGNR, "qmr": QMR, "cocg": COCG, "cocr": COCR, "bicg": BICG,
-           "gmres": GMRES, "cgs": CGS, "cgne": CGNE, "tfqmr": TFQMR}
+           "gmres": GMRES, "cgs": CGS, "cgne": CGNE, "tfqmr": TFQMR, "bicgstabl": BICGSTABL}
 OK, NOT_CONVERGED, BREAKDOWN, INVALID = 0, 1, 2, -1
 
 _lib = None
@@ -53,6 +53,7 @@ def lib():
             L.orc_refine.argtypes = [vp, vp, i32, vp, vp, dbl, i32, dbl, i32, vp, vp]
             L.orc_fft3d.argtypes = [vp, i64, i64, i64, i32]
             L.orc_set_restart.argtypes = [i32]
+            L.orc_set_bicgstab_l.argtypes = [i32]
             _lib = L
     return _lib
 
@@ -170,11 +171,12 @@ class SolveResult:
             self.iters, self.status, self.detail, self.hist[-1] if len(self.hist) else float("nan"))
 
 
-def solve(op, method, y, x0=None, tol=1e-10, maxit=1000, want_tau=False, restart=30):
+def solve(op, method, y, x0=None, tol=1e-10, maxit=1000, want_tau=False, restart=30, ell=2):
     """Run one oracle method; returns SolveResult with hist[k] = ||r_k||/||y||
-    (restart: the cycle length m of GMRES(m))."""
+    (restart: the cycle length m of GMRES(m); ell: the degree of BiCGstab(l))."""
     m = METHODS[method] if isinstance(method, str) else int(method)
     lib().orc_set_restart(int(restart))
+    lib().orc_set_bicgstab_l(int(ell))
     y = np.ascontiguousarray(y, dtype=op.dtype)
     x = np.zeros(op.n, dtype=op.dtype) if x0 is None else np.array(x0, dtype=op.dtype, copy=True)
     hist = np.full(maxit + 1, np.nan)
@@ -187,13 +189,15 @@ def solve(op, method, y, x0=None, tol=1e-10, maxit=1000, want_tau=False, restart
     return SolveResult(x, it, int(out[1]), int(out[2]), hist[: it + 1], None if tau is None else tau[: it + 1])
 
 
-def refine(op64, op32, method, y, x0=None, tol=1e-10, max_outer=20, inner_tol=1e-4, inner_maxit=50, restart=30):
+def refine(op64, op32, method, y, x0=None, tol=1e-10, max_outer=20, inner_tol=1e-4, inner_maxit=50, restart=30,
+           ell=2):
     """FP64 iterative refinement around an FP32 inner solve.
 
     Returns (x, outer_steps, status, inner_iterations, hist_outer).
     """
     m = METHODS[method] if isinstance(method, str) else int(method)
     lib().orc_set_restart(int(restart))
+    lib().orc_set_bicgstab_l(int(ell))
     y = np.ascontiguousarray(y, dtype=np.complex128)
     x = np.zeros(op64.n, dtype=np.complex128) if x0 is None else np.array(x0, dtype=np.complex128, copy=True)
     hist = np.full(max_outer + 1, np.nan)

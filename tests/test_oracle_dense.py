@@ -22,7 +22,7 @@ from paper_1208_4869_gb300 import workloads as W
 
 METHODS = ["bicgstab", "cgnr", "qmr"]
 SYM = ("cocg", "cocr")                 # methods for complex-symmetric A
-ALL = METHODS + ["cocg", "cocr", "bicg", "gmres", "cgs", "cgne", "tfqmr"]
+ALL = METHODS + ["cocg", "cocr", "bicg", "gmres", "cgs", "cgne", "tfqmr", "bicgstabl"]
 
 
 def relres(A, x, y):
@@ -138,7 +138,8 @@ def test_diagonal_operator_distinct_eigenvalues(method):
     op = O.DenseOp(A, symmetric=True)
     r = O.solve(op, method, y, tol=1e-10, maxit=50)
     assert r.status == O.OK
-    assert r.iters == len(lam)
+    # BiCGstab(2): an iteration is two BiCG steps
+    assert r.iters == (len(lam) + 1) // 2 if method == "bicgstabl" else r.iters == len(lam)
     assert relres(A, r.x, y) < 1e-10
 
 
@@ -218,7 +219,7 @@ def test_breakdowns():
     assert r.status == O.BREAKDOWN and r.detail == 12 and r.iters == 0
     # BiCG and CGS: sigma = <p~, A p> = 0 on the swap matrix with y = e_1.
     A = np.array([[0, 1], [1, 0]], dtype=np.complex128)
-    for m in ("bicg", "cgs", "tfqmr"):
+    for m in ("bicg", "cgs", "tfqmr", "bicgstabl"):
         r = O.solve(O.DenseOp(A), m, np.array([1, 0], dtype=complex), tol=1e-12, maxit=5)
         assert r.status == O.BREAKDOWN and r.detail == 2 and r.iters == 0
     # CGNE: p = A^H r0 = 0 with r0 != 0 (r0 in the null space of A^H).
@@ -440,3 +441,37 @@ def test_tfqmr_iterates_match_scipy():
         assert np.linalg.norm(r.x - xs[2 * k - 1]) / np.linalg.norm(xs[2 * k - 1]) < 1e-12
         # the recorded quantity bounds the true residual
         assert relres(A, r.x, y) <= r.hist[k] * (1 + 1e-12)
+
+
+def test_bicgstab1_is_bicgstab():
+    """BiCGstab(1) is BiCGSTAB: scipy's BiCGSTAB iterates (independent code)."""
+    A, y = W.dense_system(64, 1.0, 7)
+    x0 = W.random_vector(64, 8)
+    xs = []
+    sla.bicgstab(A, y, x0=x0.copy(), rtol=1e-15, atol=0.0, maxiter=10, callback=lambda xk: xs.append(xk.copy()))
+    op = O.DenseOp(A)
+    for k in range(1, 7):
+        r = O.solve(op, "bicgstabl", y, x0=x0, tol=0.0, maxit=k, ell=1)
+        assert np.linalg.norm(r.x - xs[k - 1]) / np.linalg.norm(xs[k - 1]) < 1e-12
+
+
+@pytest.mark.parametrize("ell", [2, 3, 4])
+def test_bicgstabl_first_cycle_from_its_definition(ell):
+    """After one cycle from x0, BiCGstab(l) is the BiCG iterate of step l,
+    s = y - A x_l (Petrov-Galerkin, solved directly), corrected by the
+    degree-l minimal-residual polynomial: r = s - sum_j g_j A^j s with g
+    minimising ||r|| (least squares), x = x_l + sum_j g_j A^(j-1) s."""
+    n = 40
+    A, y = W.dense_system(n, 2.0, 25)
+    x0 = W.random_vector(n, 26)
+    xb = galerkin_iterate("bicg", A, y, x0, ell)
+    s = y - A @ xb
+    K = [s]
+    for _ in range(ell):
+        K.append(A @ K[-1])
+    g = np.linalg.lstsq(np.stack(K[1:], axis=1), s, rcond=None)[0]
+    want = xb + sum(g[j] * K[j] for j in range(ell))
+    r = O.solve(O.DenseOp(A), "bicgstabl", y, x0=x0, tol=0.0, maxit=1, ell=ell)
+    assert r.iters == 1
+    assert np.linalg.norm(r.x - want) / np.linalg.norm(want) < 1e-10
+    assert abs(r.hist[1] - relres(A, want, y)) < 1e-11
