@@ -7,8 +7,10 @@
  * iteration (Sec. 5: `matvec` for A x and `cmatvec` for A^H x), and the
  * solve takes a tolerance and an iteration cap (Sec. 5 `cgmodule`:
  * `epsilon_err`, `maxit`).  The methods are those of Sec. 2.1 (PIM:
- * `bicgstab`, `cgnr`, `qmr`, `bigcg`), Sec. 2.2 (the Sarkar complex-symmetric
- * CG) and Sec. 3.4 (COCR), in their unpreconditioned textbook forms.
+ * `bicgstab`, `cgnr`, `qmr`, `bigcg`, `rgmres`, `cgs`, `cgne`, `tfqmr`), Sec. 2.2 (the
+ * Sarkar complex-symmetric CG), Sec. 3.1 (BiCGstab(l)) and Sec. 3.4 (COCR), in
+ * their unpreconditioned
+ * textbook forms.
  *
  * Conventions shared by every entry point:
  *  - Complex vectors and matrices are interleaved (re, im) pairs in the
@@ -44,8 +46,15 @@ typedef enum {
   CCG_COCR = 4,     /* Sogabe-Zhang conjugate A-orthogonal CR (Sec. 3.4)     */
   CCG_BICG = 5,     /* Fletcher BiCG with A^H, shadow r~0 = r0 (Sec. 2.1
                        PIM `bigcg`)                                         */
-  CCG_GMRES = 6     /* restarted GMRES(m) (Sec. 2.1 PIM `rgmres`); m set by
+  CCG_GMRES = 6,    /* restarted GMRES(m) (Sec. 2.1 PIM `rgmres`); m set by
                        ccg_set_option(CCG_OPT_GMRES_RESTART), default 30    */
+  CCG_CGS = 7,      /* Sonneveld CGS, shadow r^ = r0 (Sec. 2.1 PIM `cgs`)    */
+  CCG_CGNE = 8,     /* Craig's CG on A A^H u = y, x = A^H u (PIM `cgne`)     */
+  CCG_TFQMR = 9,    /* Freund TFQMR, two half-steps per iteration; residual
+                       = the quasi-residual bound (Sec. 2.1 PIM `tfqmr`)     */
+  CCG_BICGSTABL = 10 /* vanilla BiCGstab(l) (Sec. 3.1); an iteration is one
+                       cycle of l BiCG steps (2 l products); l set by
+                       ccg_set_option(CCG_OPT_BICGSTAB_L), default 2        */
 } ccg_method;
 
 typedef enum { CCG_C64 = 0, CCG_C128 = 1 } ccg_dtype;
@@ -168,8 +177,9 @@ ccg_status ccg_dot(ccg_handle* h, ccg_dtype dtype, int64_t n, const void* u, con
  *           NULL.
  * y = 0 gives x = 0, iters = 0, CCG_OK.  CCG_COCG and CCG_COCR need an
  * operator made with CCG_OP_SYMMETRIC (else CCG_ERR_INVALID).  Products per
- * iteration: BiCGSTAB and CGNR two; QMR and BiCG A p and A^H q (one read of
- * a dense A); COCG and COCR one.  Blocks the calling thread
+ * iteration: BiCGSTAB, CGS, TFQMR, CGNR and CGNE two, BiCGstab(l) 2 l; QMR
+ * and BiCG A p and A^H q
+ * (one read of a dense A); COCG, COCR and GMRES one.  Blocks the calling thread
  * until the solve has finished on the handle's stream.  Returns the solve's
  * status (CCG_OK, CCG_NOT_CONVERGED, CCG_BREAKDOWN) or an error. */
 ccg_status ccg_solve(ccg_handle* h, ccg_method method, const ccg_operator* op, const void* y, void* x, double tol,
@@ -254,10 +264,12 @@ ccg_status ccg_block_matvec(ccg_handle* h, const ccg_operator* op, int64_t nrhs,
  * term rarely pays; refined batched solves correct the difference with one
  * exact complex64 residual per correction.
  * CCG_OPT_GMRES_RESTART: the cycle length m of CCG_GMRES, 1..64 (default
- * 30); the solve holds m + 1 basis vectors in the handle's workspace. */
+ * 30); the solve holds m + 1 basis vectors in the handle's workspace.
+ * CCG_OPT_BICGSTAB_L: the degree l of CCG_BICGSTABL, 1..4 (default 2). */
 #define CCG_OPT_TENSOR_CORES 1
 #define CCG_OPT_TC_SPLIT 2
 #define CCG_OPT_GMRES_RESTART 3
+#define CCG_OPT_BICGSTAB_L 4
 ccg_status ccg_set_option(ccg_handle* h, int option, int value);
 
 /* ---------------------------------------------------------------------------

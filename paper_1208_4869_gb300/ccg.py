@@ -17,9 +17,9 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libccg.so")
 
-BICGSTAB, CGNR, QMR, COCG, COCR, BICG, GMRES = 0, 1, 2, 3, 4, 5, 6
+BICGSTAB, CGNR, QMR, COCG, COCR, BICG, GMRES, CGS, CGNE, TFQMR, BICGSTABL = range(11)
 METHODS = {"bicgstab": BICGSTAB, "cgnr": CGNR, "qmr": QMR, "cocg": COCG, "cocr": COCR, "bicg": BICG,
-           "gmres": GMRES}
+           "gmres": GMRES, "cgs": CGS, "cgne": CGNE, "tfqmr": TFQMR, "bicgstabl": BICGSTABL}
 C64, C128 = 0, 1
 OK, NOT_CONVERGED, BREAKDOWN = 0, 1, 2
 ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
@@ -27,6 +27,7 @@ OP_SYMMETRIC = 1
 OPT_TENSOR_CORES = 1
 OPT_TC_SPLIT = 2
 OPT_GMRES_RESTART = 3
+OPT_BICGSTAB_L = 4
 SWEEP_N, SWEEP_C, SWEEP_BOTH, SWEEP_BLOCK = 0, 1, 2, 3
 
 _lib = None

@@ -2,12 +2,14 @@
 // workspace, timing, and dispatch to the solver and operator code.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstdint>
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -68,10 +70,25 @@ void timing_end(ccg_handle* h, int dtype, int kind, double bytes) {
   h->bytes_per_sweep[slot] = bytes;
 }
 
-// Sum the recorded sweep durations (the stream must be idle) and recycle the events.
+int* timing_rec(ccg_handle* h) {
+  if (!h->timing || !h->skip_rec || h->tev_used / 2 >= h->skip_cap) return nullptr;
+  return h->skip_rec + h->tev_used / 2;
+}
+
+// Sum the recorded sweep durations (the stream must be idle) and recycle the
+// events.  Sweeps that found the solve already stopped (enqueued ahead of
+// the convergence test) returned at once and are left out.
 void timing_collect(ccg_handle* h) {
+  const size_t pairs = h->tev_used / 2;
+  std::vector<int> skipped(pairs, 0);
+  if (h->skip_rec && pairs > 0) {
+    const size_t m = std::min(pairs, h->skip_cap);
+    if (cudaMemcpy(skipped.data(), h->skip_rec, m * sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess)
+      cudaMemset(h->skip_rec, 0, m * sizeof(int));
+  }
   for (size_t i = 0; i + 1 < h->tev_used; i += 2) {
     float ms = 0.f;
+    if (skipped[i / 2]) continue;
     if (cudaEventElapsedTime(&ms, h->tev[i], h->tev[i + 1]) == cudaSuccess) {
       h->timed_ms[h->tev_kind[i]] += ms;
       h->timed_sweeps[h->tev_kind[i]] += 1;
@@ -142,6 +159,7 @@ ccg_status ccg_destroy(ccg_handle* h) {
   if (h->arena) cudaFree(h->arena);
   if (h->tc_buf) cudaFree(h->tc_buf);
   if (h->pinned) cudaFreeHost(h->pinned);
+  if (h->skip_rec) cudaFree(h->skip_rec);
   for (int i = 0; i < 2; ++i)
     if (h->poll_ev[i]) cudaEventDestroy(h->poll_ev[i]);
   for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
@@ -253,7 +271,7 @@ ccg_status ccg_dot(ccg_handle* h, ccg_dtype dtype, int64_t n, const void* u, con
 ccg_status ccg_solve(ccg_handle* h, ccg_method method, const ccg_operator* op, const void* y, void* x, double tol,
                      int maxit, double* res_hist, ccg_info* info) {
   if (!h || !op || !y || !x) { set_error("ccg_solve: NULL argument"); return CCG_ERR_INVALID; }
-  if (method < CCG_BICGSTAB || method > CCG_GMRES) { set_error("ccg_solve: unknown method"); return CCG_ERR_INVALID; }
+  if (method < CCG_BICGSTAB || method > CCG_BICGSTABL) { set_error("ccg_solve: unknown method"); return CCG_ERR_INVALID; }
   if (maxit < 0 || !(tol >= 0.0)) { set_error("ccg_solve: need maxit >= 0 and tol >= 0"); return CCG_ERR_INVALID; }
   if ((method == CCG_COCG || method == CCG_COCR) && !(op->flags & CCG_OP_SYMMETRIC)) {
     set_error("ccg_solve: COCG and COCR need an operator flagged CCG_OP_SYMMETRIC");
@@ -268,7 +286,7 @@ ccg_status ccg_solve_refined(ccg_handle* h, ccg_method method, const ccg_operato
                              const void* y, void* x, double tol, int max_outer, double inner_tol, int inner_maxit,
                              double* res_hist, int* inner_iters, ccg_info* info) {
   if (!h || !op || !op_in || !y || !x) { set_error("ccg_solve_refined: NULL argument"); return CCG_ERR_INVALID; }
-  if (method < CCG_BICGSTAB || method > CCG_GMRES) { set_error("ccg_solve_refined: unknown method"); return CCG_ERR_INVALID; }
+  if (method < CCG_BICGSTAB || method > CCG_BICGSTABL) { set_error("ccg_solve_refined: unknown method"); return CCG_ERR_INVALID; }
   if (op->dtype != CCG_C128 || op_in->dtype != CCG_C64 || op->n != op_in->n) {
     set_error("ccg_solve_refined: need a complex128 operator and a complex64 operator of the same size");
     return CCG_ERR_INVALID;
@@ -355,12 +373,28 @@ ccg_status ccg_set_option(ccg_handle* h, int option, int value) {
     h->gm_restart = value;
     return CCG_OK;
   }
+  if (option == CCG_OPT_BICGSTAB_L && value >= 1 && value <= kMaxEll) {
+    h->bicgstab_l = value;
+    return CCG_OK;
+  }
   set_error("ccg_set_option: unknown option or value out of range");
   return CCG_ERR_INVALID;
 }
 
 ccg_status ccg_timing_enable(ccg_handle* h, int enable) {
   if (!h) return CCG_ERR_INVALID;
+  if (enable && !h->skip_rec) {
+    const size_t cap = (size_t)1 << 20;  // sweeps between two collections
+    if (cudaMalloc(&h->skip_rec, cap * sizeof(int)) != cudaSuccess ||
+        cudaMemset(h->skip_rec, 0, cap * sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      if (h->skip_rec) cudaFree(h->skip_rec);
+      h->skip_rec = nullptr;
+      set_error("ccg_timing_enable: allocation failed");
+      return CCG_ERR_NOMEM;
+    }
+    h->skip_cap = cap;
+  }
   h->timing = enable != 0;
   return CCG_OK;
 }

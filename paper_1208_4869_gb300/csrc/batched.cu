@@ -500,7 +500,7 @@ template <class R> struct BRun {
       }
     }
     dim3 g((k + gemm_bn<R>() - 1) / gemm_bn<R>(), (unsigned)((n + gemm_bm<R>() - 1) / gemm_bm<R>()));
-    cgemm_rows<R><<<g, kBlock, 0, s>>>(static_cast<const cx<R>*>(op->A), op->lda, B, C, n, k, skip);
+    cgemm_rows<R><<<g, kBlock, 0, s>>>(static_cast<const cx<R>*>(op->A), op->lda, B, C, n, k, skip, timing_rec(h));
     ++h->launches;
     timing_end(h, sizeof(R) == 8 ? CCG_C128 : CCG_C64, CCG_SWEEP_BLOCK,
                (double)n * n * sizeof(cx<R>) + 2.0 * n * k * sizeof(cx<R>));

@@ -30,11 +30,14 @@ template <class R> constexpr int gemm_bn() { return 16 * GemmTile<R>::TN; }
 template <class R>
 __global__ void __launch_bounds__(kBlock) cgemm_rows(const cx<R>* __restrict__ A, int64_t lda,
                                                      const cx<R>* __restrict__ B, cx<R>* __restrict__ C, int64_t n,
-                                                     int k, const int* __restrict__ skip) {
+                                                     int k, const int* __restrict__ skip, int* skip_rec = nullptr) {
   constexpr int TM = GemmTile<R>::TM, TN = GemmTile<R>::TN;
   constexpr int BM = 16 * TM, BN = 16 * TN;
   constexpr int A_PER = BM * kGemmBK / kBlock, B_PER = kGemmBK * BN / kBlock;
-  if (skip != nullptr && *skip) return;
+  if (skip != nullptr && *skip) {  // every column has stopped
+    if (skip_rec != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *skip_rec = 1;
+    return;
+  }
   __shared__ cx<R> As[kGemmBK][BM];
   __shared__ cx<R> Bs[kGemmBK][BN];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;

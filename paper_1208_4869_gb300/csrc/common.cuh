@@ -11,7 +11,8 @@ namespace ccg {
 constexpr int kBlock = 256;          // threads per block of every kernel here
 constexpr int kWarps = kBlock / 32;
 constexpr int kMaxRedBlocks = 2048;  // upper bound on the grid of a reducing kernel
-constexpr int kMaxNQ = 8;            // reduction slots per reducing kernel
+constexpr int kMaxNQ = 32;           // reduction slots per reducing kernel
+constexpr int kMaxEll = 4;           // largest degree l of BiCGstab(l)
 constexpr int kMaxBasis = 64;        // largest GMRES restart length
 
 // ---------------------------------------------------------------------------
@@ -118,9 +119,20 @@ struct SolveState {
   // cycle; ||r|| at the cycle start; norm of the last orthogonalised vector
   int gm_final, gm_cols;
   double gm_beta, gm_eta;
+  double tau;     // TFQMR quasi-residual norm
+  double2 bl_g[kMaxEll];  // BiCGstab(l) minimal-residual coefficients
   double* hist;   // device residual history, maxit + 1 entries
   double* aux;    // spare device doubles for standalone results
 };
+
+// A sweep skips when the solve has stopped, is past a half-step exit, or
+// starts from x0 = 0.  skip_rec (timed sweeps only) is set by the first
+// thread, so that the sweep's duration is left out of the sweep timing.
+__device__ __forceinline__ bool sweep_skipped(const SolveState* st, int* skip_rec) {
+  if (st == nullptr || !(st->poll.done || st->half || st->skip_mv)) return false;
+  if (skip_rec != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *skip_rec = 1;
+  return true;
+}
 
 // Status codes mirrored from ccg.h for device code.
 enum { ST_OK = 0, ST_NOT_CONVERGED = 1, ST_BREAKDOWN = 2, ST_NONFINITE = -4 };

@@ -77,8 +77,8 @@ template <class R>
 __global__ void __launch_bounds__(kBlock) dip_fwd_z(const cx<R>* __restrict__ x, cx<R>* __restrict__ grid,
                                                     const int* __restrict__ idx, DipGeom g, int bl,
                                                     const cx<R>* __restrict__ W, int conj_in,
-                                                    const SolveState* __restrict__ st) {
-  if (skip_state(st)) return;
+                                                    const SolveState* __restrict__ st, int* skip_rec) {
+  if (sweep_skipped(st, skip_rec)) return;
   extern __shared__ unsigned char smem_raw[];
   const int Mz = g.Mz, ls = g.Mz;
   cx<R>* buf0 = reinterpret_cast<cx<R>*>(smem_raw);
@@ -236,8 +236,8 @@ template <class R, int N>
 __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 3 : 2) dip_fwd_z_reg(const cx<R>* __restrict__ x, cx<R>* __restrict__ grid,
                                                         const int* __restrict__ idx, DipGeom g,
                                                         const cx<R>* __restrict__ W, int conj_in,
-                                                        const SolveState* __restrict__ st) {
-  if (skip_state(st)) return;
+                                                        const SolveState* __restrict__ st, int* skip_rec) {
+  if (sweep_skipped(st, skip_rec)) return;
   constexpr int BL = reg_bl<R>(), LS = BL + 1, NZ = N / 2;
   extern __shared__ unsigned char smem_raw[];
   cx<R>* U = reinterpret_cast<cx<R>*>(smem_raw);
@@ -662,7 +662,7 @@ template <class F> static void smem_opt_in(F* fn, size_t bytes, bool& done) {
 // runtime-length kernels (op->dip.bl lines per block).
 template <class R, int N>
 static void k1(const cx<R>* x, cx<R>* grid, const ccg_operator* op, const DipGeom& g, const cx<R>* W, int conj,
-               const SolveState* st, cudaStream_t s) {
+               const SolveState* st, int* rec, cudaStream_t s) {
   const int64_t nlines = (int64_t)g.nx * g.ny;
   static bool opted = false;
   if constexpr (N > 0) {
@@ -670,12 +670,12 @@ static void k1(const cx<R>* x, cx<R>* grid, const ccg_operator* op, const DipGeo
     constexpr size_t sm = z_reg_smem<R, N>();
     smem_opt_in(dip_fwd_z_reg<R, N>, sm, opted);
     dip_fwd_z_reg<R, N><<<dim3((unsigned)((nlines + BL - 1) / BL), 3), kBlock, sm, s>>>(x, grid, op->dip.idx, g, W,
-                                                                                       conj, st);
+                                                                                       conj, st, rec);
   } else {
     const int bl = op->dip.bl;
     const size_t sm = (size_t)2 * bl * g.Mz * sizeof(cx<R>);
     dip_fwd_z<R><<<dim3((unsigned)((nlines + bl - 1) / bl), 3), kBlock, sm, s>>>(x, grid, op->dip.idx, g, bl, W,
-                                                                                 conj, st);
+                                                                                 conj, st, rec);
   }
 }
 template <class R, int N>
@@ -745,7 +745,8 @@ static void k3(cx<R>* grid, const ccg_operator* op, const DipGeom& g, const cx<R
 #define CCG_FFT_SIZES(X) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256)
 
 template <class R>
-static int apply_t(const ccg_operator* op, const cx<R>* x, cx<R>* y, bool conj, const SolveState* st, cudaStream_t s) {
+static int apply_t(const ccg_operator* op, const cx<R>* x, cx<R>* y, bool conj, const SolveState* st, int* rec,
+                   cudaStream_t s) {
   const DipGeom g = geom(op);
   cx<R>* grid = static_cast<cx<R>*>(op->dip.work);
   const cx<R>* Wx = static_cast<const cx<R>*>(op->dip.tw[0]);
@@ -753,8 +754,8 @@ static int apply_t(const ccg_operator* op, const cx<R>* x, cx<R>* y, bool conj, 
   const cx<R>* Wz = static_cast<const cx<R>*>(op->dip.tw[2]);
   const int cj = conj ? 1 : 0;
   const cx<R> ainv = mk<R>((R)op->dip.alpha_inv[0], (R)op->dip.alpha_inv[1]);
-#define CCG_CASE_K1(n) case n: k1<R, n>(x, grid, op, g, Wz, cj, st, s); break;
-  switch (g.Mz) { CCG_FFT_SIZES(CCG_CASE_K1) default: k1<R, 0>(x, grid, op, g, Wz, cj, st, s); }
+#define CCG_CASE_K1(n) case n: k1<R, n>(x, grid, op, g, Wz, cj, st, rec, s); break;
+  switch (g.Mz) { CCG_FFT_SIZES(CCG_CASE_K1) default: k1<R, 0>(x, grid, op, g, Wz, cj, st, rec, s); }
 #define CCG_CASE_KY(n) case n: ky<R, n>(grid, op, g, Wy, sign, st, s); break;
   for (int sign = -1; sign <= 1; sign += 2) {
     if (sign > 0) {
@@ -769,12 +770,12 @@ static int apply_t(const ccg_operator* op, const cx<R>* x, cx<R>* y, bool conj, 
 }
 
 int dipole_apply(const ccg_operator* op, const double2* x, double2* y, bool conj, const SolveState* st,
-                 cudaStream_t s) {
-  return apply_t<double>(op, x, y, conj, st, s);
+                 cudaStream_t s, int* skip_rec) {
+  return apply_t<double>(op, x, y, conj, st, skip_rec, s);
 }
 int dipole_apply(const ccg_operator* op, const float2* x, float2* y, bool conj, const SolveState* st,
-                 cudaStream_t s) {
-  return apply_t<float>(op, x, y, conj, st, s);
+                 cudaStream_t s, int* skip_rec) {
+  return apply_t<float>(op, x, y, conj, st, skip_rec, s);
 }
 
 }  // namespace ccg

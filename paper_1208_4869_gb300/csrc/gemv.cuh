@@ -69,40 +69,68 @@ template <class R> struct MvOut {
   }
 };
 
-// y[i] = (A x)_i, one warp per row.  Requires n % U == 0 and 16-byte aligned
-// rows when U * sizeof(cx<R>) == 16.
-template <class R, int U>
+// y[i] = (A x)_i with S warps per row, each over a contiguous 1/S of the
+// row's columns; the S partial sums meet in shared memory and are added in
+// warp order.  A block of kWarps warps takes kWarps / S rows at a time.
+// Splitting rows makes 4x more work units than one warp per row, so the
+// last wave of blocks is a small fraction of the sweep (one warp per row
+// left ~1.7 waves of 8-row blocks at n = 8192, the second one 68% full).
+// Requires n % U == 0 and 16-byte aligned rows when U * sizeof(cx<R>) == 16.
+template <class R, int U, int S = 1>
 __global__ void __launch_bounds__(kBlock) gemv_n_rows(const cx<R>* __restrict__ A, int64_t lda, int64_t n,
                                                       const cx<R>* __restrict__ x, cx<R>* __restrict__ y,
-                                                      const SolveState* __restrict__ st) {
+                                                      const SolveState* __restrict__ st, int* skip_rec = nullptr) {
   typedef Unit<R, U> Un;
   typedef typename Un::L L;
-  if (st != nullptr && (st->poll.done || st->half || st->skip_mv)) return;
-  const int lane = threadIdx.x & 31;
+  static_assert(kWarps % S == 0, "S must divide the warps of a block");
+  constexpr int RPB = kWarps / S;  // rows per block pass
+  __shared__ cx<R> part[kWarps];
+  if (sweep_skipped(st, skip_rec)) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int seg = warp % S;
   const int64_t nunits = n / U;
+  const int64_t u0 = nunits * seg / S, u1 = nunits * (seg + 1) / S;
   const L* xv = reinterpret_cast<const L*>(x);
-  for (int64_t row = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); row < n; row += (int64_t)gridDim.x * kWarps) {
-    const L* a = reinterpret_cast<const L*>(A + row * lda);
+  const int64_t nrb = (n + RPB - 1) / RPB;
+  for (int64_t rb = blockIdx.x; rb < nrb; rb += gridDim.x) {
+    const int64_t row = rb * RPB + warp / S;
     cx<R> s0 = mk<R>(0, 0), s1 = mk<R>(0, 0);
-    int64_t u = lane;
-    for (; u + 96 < nunits; u += 128) {
-      const L a0 = ld_stream(a + u), a1 = ld_stream(a + u + 32), a2 = ld_stream(a + u + 64), a3 = ld_stream(a + u + 96);
-      const L x0 = ldg_unit(xv + u), x1 = ldg_unit(xv + u + 32), x2 = ldg_unit(xv + u + 64), x3 = ldg_unit(xv + u + 96);
+    if (row < n) {
+      const L* a = reinterpret_cast<const L*>(A + row * lda);
+      int64_t u = u0 + lane;
+      for (; u + 96 < u1; u += 128) {
+        const L a0 = ld_stream(a + u), a1 = ld_stream(a + u + 32), a2 = ld_stream(a + u + 64),
+                a3 = ld_stream(a + u + 96);
+        const L x0 = ldg_unit(xv + u), x1 = ldg_unit(xv + u + 32), x2 = ldg_unit(xv + u + 64),
+                x3 = ldg_unit(xv + u + 96);
 #pragma unroll
-      for (int c = 0; c < U; ++c) {
-        s0 = cfma(Un::get(a0, c), Un::get(x0, c), s0);
-        s1 = cfma(Un::get(a1, c), Un::get(x1, c), s1);
-        s0 = cfma(Un::get(a2, c), Un::get(x2, c), s0);
-        s1 = cfma(Un::get(a3, c), Un::get(x3, c), s1);
+        for (int c = 0; c < U; ++c) {
+          s0 = cfma(Un::get(a0, c), Un::get(x0, c), s0);
+          s1 = cfma(Un::get(a1, c), Un::get(x1, c), s1);
+          s0 = cfma(Un::get(a2, c), Un::get(x2, c), s0);
+          s1 = cfma(Un::get(a3, c), Un::get(x3, c), s1);
+        }
+      }
+      for (; u < u1; u += 32) {
+        const L a0 = ld_stream(a + u), x0 = ldg_unit(xv + u);
+#pragma unroll
+        for (int c = 0; c < U; ++c) s0 = cfma(Un::get(a0, c), Un::get(x0, c), s0);
       }
     }
-    for (; u < nunits; u += 32) {
-      const L a0 = ld_stream(a + u), x0 = ldg_unit(xv + u);
+    const cx<R> ws = warp_csum(cadd(s0, s1));
+    if (S == 1) {
+      if (lane == 0 && row < n) y[row] = ws;
+    } else {
+      if (lane == 0) part[warp] = ws;
+      __syncthreads();
+      if (seg == 0 && lane == 0 && row < n) {
+        cx<R> t = part[warp];
 #pragma unroll
-      for (int c = 0; c < U; ++c) s0 = cfma(Un::get(a0, c), Un::get(x0, c), s0);
+        for (int q = 1; q < S; ++q) t = cadd(t, part[warp + q]);
+        y[row] = t;
+      }
+      __syncthreads();
     }
-    const cx<R> s = warp_csum(cadd(s0, s1));
-    if (lane == 0) y[row] = s;
   }
 }
 
@@ -114,11 +142,12 @@ template <class R, int U, int E, bool Y1, bool Y2>
 __global__ void __launch_bounds__(kBlock) gemv_tile(const cx<R>* __restrict__ A, int64_t lda, int64_t n,
                                                     int64_t rows_per_range, const cx<R>* __restrict__ x1,
                                                     const cx<R>* __restrict__ x2, cx<R>* __restrict__ P1,
-                                                    cx<R>* __restrict__ P2, const SolveState* __restrict__ st) {
+                                                    cx<R>* __restrict__ P2, const SolveState* __restrict__ st,
+                                                    int* skip_rec = nullptr) {
   typedef Unit<R, U> Un;
   typedef typename Un::L L;
   constexpr int CBU = 32 * E;  // units per column chunk
-  if (st != nullptr && (st->poll.done || st->half || st->skip_mv)) return;
+  if (sweep_skipped(st, skip_rec)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t nunits = n / U;
   const int64_t unit0 = (int64_t)blockIdx.x * CBU;

@@ -28,6 +28,7 @@ struct DipoleData {
   void* tw[3] = {nullptr, nullptr, nullptr};  // twiddle tables along x, y, z
   int bl = 8;                   // lines per block of the FFT passes
   double sweep_bytes = 0.0;     // algorithmic bytes of one application
+  int kernels = 5;              // kernels per application (3 when the z and y passes are fused)
 };
 
 struct ccg_operator {
@@ -64,6 +65,8 @@ struct ccg_handle {
   std::vector<cudaEvent_t> tev;  // start/stop pairs
   std::vector<int> tev_kind;     // dtype * CCG_SWEEP_KINDS + sweep kind of each pair
   size_t tev_used = 0;
+  int* skip_rec = nullptr;       // device, one flag per timed sweep: 1 if it found the solve stopped
+  size_t skip_cap = 0;
   int64_t timed_sweeps[2 * CCG_SWEEP_KINDS] = {};
   double timed_ms[2 * CCG_SWEEP_KINDS] = {};
   double bytes_per_sweep[2 * CCG_SWEEP_KINDS] = {};
@@ -74,6 +77,7 @@ struct ccg_handle {
   int tc_mode = 1;   // 0 never, 1 refined inner solves and block products, 2 also plain batched solves
   int tc_terms = 2;  // bf16 terms of the split operands (2 or 3; the fp32 accumulation limits both to ~1e-4 at K ~ 1e4)
   int gm_restart = 30;  // GMRES cycle length m
+  int bicgstab_l = 2;   // degree l of BiCGstab(l)
   void* tc_buf = nullptr;
   size_t tc_bytes = 0;
 };
@@ -88,6 +92,9 @@ int arena_reserve(ccg_handle* h, size_t bytes);
 void timing_begin(ccg_handle* h);
 void timing_end(ccg_handle* h, int dtype, int kind, double bytes);
 void timing_collect(ccg_handle* h);
+// Device flag of the sweep being timed (between timing_begin and timing_end),
+// or nullptr when timing is off.
+int* timing_rec(ccg_handle* h);
 
 // Entry points implemented in solve.cu.
 int solve_dense(ccg_handle* h, int method, const ccg_operator* op, const void* y, void* x, double tol, int maxit,
@@ -98,11 +105,12 @@ int solve_refined(ccg_handle* h, int method, const ccg_operator* op, const ccg_o
 int dipole_create(ccg_operator* op, const uint8_t* occ, cudaStream_t s);
 void dipole_free(ccg_operator* op);
 // y = A x (conj = false) or A^H x (conj = true), enqueued on s; kernels skip
-// when st says the solve has stopped (st may be null).
+// when st says the solve has stopped (st may be null), and then set
+// *skip_rec when it is given (timed sweeps).
 int dipole_apply(const ccg_operator* op, const double2* x, double2* y, bool conj, const SolveState* st,
-                 cudaStream_t s);
+                 cudaStream_t s, int* skip_rec = nullptr);
 int dipole_apply(const ccg_operator* op, const float2* x, float2* y, bool conj, const SolveState* st,
-                 cudaStream_t s);
+                 cudaStream_t s, int* skip_rec = nullptr);
 int solve_batched(ccg_handle* h, const ccg_operator* op, int64_t k, const void* Y, int64_t ldy, void* X, int64_t ldx,
                   double tol, int maxit, int32_t* iters, int32_t* status, double* relres);
 int solve_batched_refined(ccg_handle* h, const ccg_operator* op, const ccg_operator* op_in, int64_t k, const void* Y,

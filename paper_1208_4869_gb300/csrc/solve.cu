@@ -1,6 +1,6 @@
-// Krylov iterations on the GPU: BiCGSTAB, CGNR, QMR, BiCG, GMRES(m) (Sec.
-// 2.1, the PIM methods), the complex-symmetric CG (Sec. 2.2) and COCR (Sec.
-// 3.4), unpreconditioned.
+// Krylov iterations on the GPU: BiCGSTAB, CGNR, QMR, BiCG, GMRES(m), CGS,
+// CGNE, TFQMR (Sec. 2.1, the PIM methods), the complex-symmetric CG (Sec.
+// 2.2), BiCGstab(l) (Sec. 3.1) and COCR (Sec. 3.4), unpreconditioned.
 //
 // One iteration is a fixed sequence of kernels on the handle's stream:
 // operator sweeps (gemv.cuh) and "phase" kernels.  A phase kernel makes one
@@ -94,7 +94,8 @@ __device__ __forceinline__ void set_breakdown(SolveState* st, int which) {
 }
 
 enum { M_BICGSTAB = CCG_BICGSTAB, M_CGNR = CCG_CGNR, M_QMR = CCG_QMR, M_COCG = CCG_COCG, M_COCR = CCG_COCR,
-       M_BICG = CCG_BICG, M_GMRES = CCG_GMRES };
+       M_BICG = CCG_BICG, M_GMRES = CCG_GMRES, M_CGS = CCG_CGS, M_CGNE = CCG_CGNE, M_TFQMR = CCG_TFQMR,
+       M_BICGSTABL = CCG_BICGSTABL };
 
 // Clears st->skip_mv (set to 1 beforehand) when any entry of x is nonzero.
 template <class R> __global__ void __launch_bounds__(kBlock) x_zero_check(const cx<R>* __restrict__ x, int64_t n,
@@ -177,6 +178,24 @@ template <class R> struct InitR : PhaseBase {
         break;
       case M_GMRES:
         st->gm_beta = sqrt(t[1]);
+        break;
+      case M_CGS:
+        st->rho = mkc(t[1], 0.0);  // <r^, r> with r^ = r
+        if (tiny<R>(st->rho)) set_breakdown(st, CCG_BD_RHO);
+        break;
+      case M_CGNE:
+        st->gamma = t[1];          // ||r||^2
+        break;
+      case M_BICGSTABL:
+        st->rho_old = mkc(1.0, 0.0);  // rho_0
+        st->alpha = mkc(0.0, 0.0);
+        st->omega = mkc(1.0, 0.0);
+        break;
+      case M_TFQMR:
+        st->tau = sqrt(t[1]);
+        st->theta = 0.0;
+        st->eta = mkc(0.0, 0.0);
+        st->rho = mkc(t[1], 0.0);  // <r^, r_0> with r^ = r_0
         break;
       default:  // COCR forms its first scalars after the product A r0
         break;
@@ -784,6 +803,504 @@ template <class R> struct BgXR : PhaseBase {  // x += alpha p; r -= alpha q; r~ 
 };
 
 // ---------------------------------------------------------------------------
+// CGS (Sonneveld; PIM `cgs`, Sec. 2.1): two products per iteration,
+// conjugated products, shadow r^ = r_0.
+// ---------------------------------------------------------------------------
+template <class R> struct CsUP : PhaseBase {  // u = r + beta q, p = u + beta (q + beta p) (first: u = p = r)
+  static constexpr bool kReduce = false;
+  static constexpr int NQ = 1;
+  int64_t n;
+  const cx<R>* r;
+  const cx<R>* q;
+  cx<R>* u;
+  cx<R>* p;
+  cx<R> beta;
+  bool first;
+  __device__ __forceinline__ void load(const SolveState* st) {
+    first = st->poll.k == 0;
+    beta = narrow<R>(st->beta);
+  }
+  __device__ __forceinline__ void element(int64_t i, double*) {
+    if (first) {
+      u[i] = r[i];
+      p[i] = r[i];
+    } else {
+      const cx<R> qi = q[i];
+      const cx<R> ui = cfma(beta, qi, r[i]);
+      u[i] = ui;
+      p[i] = cfma(beta, cfma(beta, p[i], qi), ui);
+    }
+  }
+  __device__ void finish(const double*, SolveState*) {}
+};
+template <class R> struct CsSigma : PhaseBase {  // v = A p; sigma = <r^, v>, alpha = rho / sigma
+  static constexpr int NQ = 2;
+  int64_t n;
+  MvOut<R> mv;
+  cx<R>* v;
+  const cx<R>* rh;
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    const cx<R> vi = mv.get(i);
+    if (mv.P) v[i] = vi;
+    acc_dotc(acc, rh[i], vi);
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    const double2 sigma = mkc(t[0], t[1]);
+    if (tiny<R>(sigma)) { set_breakdown(st, CCG_BD_SIGMA); return; }
+    st->alpha = cdiv(st->rho, sigma);
+  }
+};
+template <class R> struct CsQ : PhaseBase {  // q = u - alpha v; u^ = u + q; x += alpha u^
+  static constexpr bool kReduce = false;
+  static constexpr int NQ = 1;
+  int64_t n;
+  const cx<R>* u;
+  const cx<R>* v;
+  cx<R>* q;
+  cx<R>* uh;
+  cx<R>* x;
+  cx<R> alpha;
+  __device__ __forceinline__ void load(const SolveState* st) { alpha = narrow<R>(st->alpha); }
+  __device__ __forceinline__ void element(int64_t i, double*) {
+    const cx<R> ui = u[i];
+    const cx<R> qi = csub(ui, cmul(alpha, v[i]));
+    const cx<R> uhi = cadd(ui, qi);
+    q[i] = qi;
+    uh[i] = uhi;
+    x[i] = cadd(x[i], cmul(alpha, uhi));
+  }
+  __device__ void finish(const double*, SolveState*) {}
+};
+template <class R> struct CsR : PhaseBase {  // r -= alpha A u^; rho' = <r^, r>, beta = rho' / rho
+  static constexpr int NQ = 3;
+  int64_t n;
+  MvOut<R> mv;
+  cx<R>* r;
+  const cx<R>* rh;
+  cx<R> alpha;
+  __device__ __forceinline__ void load(const SolveState* st) { alpha = narrow<R>(st->alpha); }
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    const cx<R> ri = csub(r[i], cmul(alpha, mv.get(i)));
+    r[i] = ri;
+    acc_nrm2(acc, ri);
+    acc_dotc(acc + 1, rh[i], ri);
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    if (end_iteration(st, st->poll.k + 1, sqrt(t[0]) / st->poll.ynorm, 0)) return;
+    const double2 rho_new = mkc(t[1], t[2]);
+    if (tiny<R>(rho_new)) { set_breakdown(st, CCG_BD_RHO); return; }
+    st->beta = cdiv(rho_new, st->rho);
+    st->rho = rho_new;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// CGNE (Craig's method; PIM `cgne`, Sec. 2.1): CG on A A^H u = y carried in
+// x = A^H u; products A p and A^H r per iteration.
+// ---------------------------------------------------------------------------
+template <class R> struct CnXR : PhaseBase {  // w = A p; x += alpha p; r -= alpha w; gamma' = ||r||^2
+  static constexpr int NQ = 1;
+  int64_t n;
+  MvOut<R> mv;
+  cx<R>* x;
+  cx<R>* r;
+  const cx<R>* p;
+  R alpha;
+  __device__ __forceinline__ void load(const SolveState* st) { alpha = (R)st->alpha.x; }
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    x[i] = cadd(x[i], cscale(alpha, p[i]));
+    const cx<R> ri = csub(r[i], cscale(alpha, mv.get(i)));
+    r[i] = ri;
+    acc_nrm2(acc, ri);
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    if (end_iteration(st, st->poll.k + 1, sqrt(t[0]) / st->poll.ynorm, 0)) return;
+    st->beta = mkc(t[0] / st->gamma, 0.0);
+    st->gamma = t[0];
+  }
+};
+template <class R> struct CnP : PhaseBase {  // z = A^H r; p = z + beta p (first: p = z); alpha = gamma / ||p||^2
+  static constexpr int NQ = 1;
+  int64_t n;
+  MvOut<R> mv;
+  cx<R>* p;
+  R beta;
+  bool first;
+  __device__ __forceinline__ void load(const SolveState* st) {
+    first = st->poll.k == 0;
+    beta = (R)st->beta.x;
+  }
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    const cx<R> zi = mv.get(i);
+    const cx<R> pi = first ? zi : cadd(zi, cscale(beta, p[i]));
+    p[i] = pi;
+    acc_nrm2(acc, pi);
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    if (tiny<R>(t[0])) { set_breakdown(st, CCG_BD_WW); return; }
+    st->alpha = mkc(st->gamma / t[0], 0.0);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// TFQMR (Freund; PIM `tfqmr`, Sec. 2.1), two half-steps per iteration,
+// conjugated products, shadow r^ = r_0.  The step x += eta d of a half-step
+// needs eta, which its own reduction forms, so it is applied in the next
+// half-step's pass; TqXStop applies it instead when the solve stops (or
+// breaks down) first, and ends the solve.  `half` marks that pending stop.
+// ---------------------------------------------------------------------------
+// theta^2 eta / alpha, the weight of d in d = u_m + (theta^2 eta / alpha) d.
+__device__ __forceinline__ double2 tq_f(const SolveState* st) {
+  return cmul(cdiv(mkc(st->theta * st->theta, 0.0), st->alpha), st->eta);
+}
+// Quasi-residual update after ||w||^2 = ww in half-step m (0-based) of
+// iteration k; records the bound sqrt(m + 2) tau / ||y||.  True if stopping.
+__device__ __forceinline__ bool tq_update(SolveState* st, double ww, int m, int k, bool odd) {
+  const double theta = sqrt(ww) / st->tau;
+  const double c = 1.0 / sqrt(1.0 + theta * theta);
+  st->tau = st->tau * theta * c;
+  st->theta = theta;
+  st->eta = cscale(c * c, st->alpha);
+  const double rel = st->tau * sqrt(m + 2.0) / st->poll.ynorm;
+  st->hist[k] = rel;
+  st->poll.relres = rel;
+  int status = -100;
+  if (nonfinite(rel)) status = ST_NONFINITE;
+  else if (rel <= st->tol) status = ST_OK;
+  else if (odd && k >= st->maxit) status = ST_NOT_CONVERGED;
+  if (odd || status != -100) st->poll.k = k;
+  if (status == -100) return false;
+  st->poll.status = status;
+  st->half = 1;
+  return true;
+}
+template <class R> struct TqInit : PhaseBase {  // v = 0, d = 0 (v gains A u in TqSigma)
+  static constexpr bool kReduce = false;
+  static constexpr int NQ = 1;
+  int64_t n;
+  cx<R>* v;
+  cx<R>* d;
+  __device__ __forceinline__ void element(int64_t i, double*) {
+    v[i] = mk<R>(0, 0);
+    d[i] = mk<R>(0, 0);
+  }
+  __device__ void finish(const double*, SolveState*) {}
+};
+template <class R> struct TqSigma : PhaseBase {  // v += A u; sigma = <r^, v>, alpha = rho / sigma
+  static constexpr int NQ = 2;
+  int64_t n;
+  MvOut<R> mv;
+  cx<R>* v;
+  const cx<R>* rh;
+  __device__ __forceinline__ bool skip(const SolveState* st) const { return st->half != 0; }
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    const cx<R> vi = cadd(v[i], mv.get(i));
+    v[i] = vi;
+    acc_dotc(acc, rh[i], vi);
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    const double2 sigma = mkc(t[0], t[1]);
+    if (tiny<R>(sigma)) {  // the pending x step still applies
+      st->poll.status = ST_BREAKDOWN;
+      st->poll.breakdown = CCG_BD_SIGMA;
+      st->half = 1;
+      return;
+    }
+    st->alpha = cdiv(st->rho, sigma);
+  }
+};
+// One half-step: x += eta d (the previous half-step's); even: u_{m+1} =
+// u_m - alpha v; w -= alpha A u_m; d = u_m + f d; ||w||^2 (odd: also <r^, w>).
+template <class R, bool ODD> struct TqHalf : PhaseBase {
+  static constexpr int NQ = ODD ? 3 : 1;
+  int64_t n;
+  cx<R>* x;
+  cx<R>* w;
+  cx<R>* d;
+  const cx<R>* um;   // u_m
+  cx<R>* un;         // even: u_{m+1} = u_m - alpha v
+  const cx<R>* v;
+  const cx<R>* uh;   // A u_m
+  const cx<R>* rh;
+  cx<R> alpha, eta, f;
+  __device__ __forceinline__ bool skip(const SolveState* st) const { return st->half != 0; }
+  __device__ __forceinline__ void load(const SolveState* st) {
+    alpha = narrow<R>(st->alpha);
+    eta = narrow<R>(st->eta);
+    f = narrow<R>(tq_f(st));
+  }
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    const cx<R> di = d[i], umi = um[i];
+    x[i] = cadd(x[i], cmul(eta, di));
+    if (!ODD) un[i] = csub(umi, cmul(alpha, v[i]));
+    const cx<R> wi = csub(w[i], cmul(alpha, uh[i]));
+    w[i] = wi;
+    d[i] = cadd(umi, cmul(f, di));
+    acc_nrm2(acc, wi);
+    if (ODD) acc_dotc(acc + 1, rh[i], wi);
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    const int k = st->poll.k + 1;
+    if (tq_update(st, t[0], ODD ? 2 * k - 1 : 2 * k - 2, k, ODD) || !ODD) return;
+    const double2 rho_new = mkc(t[1], t[2]);
+    if (tiny<R>(rho_new)) {
+      st->poll.status = ST_BREAKDOWN;
+      st->poll.breakdown = CCG_BD_RHO;
+      st->half = 1;
+      return;
+    }
+    st->beta = cdiv(rho_new, st->rho);
+    st->rho = rho_new;
+  }
+};
+template <class R> struct TqXStop : PhaseBase {  // after a stop: x += eta d, end the solve
+  static constexpr int NQ = 1;
+  int64_t n;
+  cx<R>* x;
+  const cx<R>* d;
+  cx<R> eta;
+  __device__ __forceinline__ bool skip(const SolveState* st) const { return st->half == 0; }
+  __device__ __forceinline__ void load(const SolveState* st) { eta = narrow<R>(st->eta); }
+  __device__ __forceinline__ void element(int64_t i, double*) { x[i] = cadd(x[i], cmul(eta, d[i])); }
+  __device__ void finish(const double*, SolveState* st) { st->poll.done = 1; }
+};
+template <class R> struct TqU : PhaseBase {  // u = w + beta u_{m+1}; v = beta A u_{m+1} + beta^2 v
+  static constexpr bool kReduce = false;
+  static constexpr int NQ = 1;
+  int64_t n;
+  const cx<R>* w;
+  const cx<R>* un;
+  const cx<R>* uh;
+  cx<R>* u;
+  cx<R>* v;
+  cx<R> beta, beta2;
+  __device__ __forceinline__ bool skip(const SolveState* st) const { return st->half != 0; }
+  __device__ __forceinline__ void load(const SolveState* st) {
+    beta = narrow<R>(st->beta);
+    beta2 = cmul(beta, beta);
+  }
+  __device__ __forceinline__ void element(int64_t i, double*) {
+    u[i] = cadd(w[i], cmul(beta, un[i]));
+    v[i] = cadd(cmul(beta, uh[i]), cmul(beta2, v[i]));
+  }
+  __device__ void finish(const double*, SolveState*) {}
+};
+
+// ---------------------------------------------------------------------------
+// BiCGstab(l) (Sleijpen-Fokkema, vanilla; Sec. 3.1): l BiCG steps on
+// r^_0..r^_l, u^_0..u^_l, then the minimal-residual update of degree l.  The
+// minimal-residual coefficients come from the Gram matrix of r^_0..r^_l
+// (one pass, every pair reduced at once) by a complex Cholesky solve of the
+// normal equations in one thread: in exact arithmetic the same solution as
+// modified Gram-Schmidt on the vectors, with one pass instead of l(l+1)/2.
+// With the coefficients g_j in the original vectors the update is
+//   x += sum_j g_j r^_{j-1},  r^_0 -= sum_j g_j r^_j,  u^_0 -= sum_j g_j u^_j.
+// ---------------------------------------------------------------------------
+struct BlVecs {
+  void* rh[kMaxEll + 1];
+  void* uh[kMaxEll + 1];
+};
+template <class R> struct BlRho : PhaseBase {  // rho1 = <r~, r^_j>; beta = alpha rho1 / rho0 (cycle start: rho0 = -omega rho0)
+  static constexpr int NQ = 2;
+  int64_t n;
+  MvOut<R> mv;
+  cx<R>* out;        // r^_j when mv holds partial sums
+  const cx<R>* rt;
+  bool start;
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    const cx<R> v = mv.get(i);
+    if (mv.P) out[i] = v;
+    acc_dotc(acc, rt[i], v);
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    if (start) st->rho_old = cmul(cscale(-1.0, st->omega), st->rho_old);
+    if (tiny<R>(st->rho_old)) { set_breakdown(st, CCG_BD_RHO); return; }
+    const double2 rho1 = mkc(t[0], t[1]);
+    st->beta = cdiv(cmul(st->alpha, rho1), st->rho_old);
+    st->rho_old = rho1;
+  }
+};
+template <class R> struct BlU : PhaseBase {  // u^_i = r^_i - beta u^_i, i <= j
+  static constexpr bool kReduce = false;
+  static constexpr int NQ = 1;
+  int64_t n;
+  BlVecs vv;
+  int j;
+  cx<R> beta;
+  __device__ __forceinline__ void load(const SolveState* st) { beta = narrow<R>(st->beta); }
+  __device__ __forceinline__ void element(int64_t e, double*) {
+    for (int i = 0; i <= j; ++i) {
+      const cx<R>* ri = static_cast<const cx<R>*>(vv.rh[i]);
+      cx<R>* ui = static_cast<cx<R>*>(vv.uh[i]);
+      ui[e] = csub(ri[e], cmul(beta, ui[e]));
+    }
+  }
+  __device__ void finish(const double*, SolveState*) {}
+};
+template <class R> struct BlGamma : PhaseBase {  // u^_{j+1} = A u^_j; gamma = <r~, u^_{j+1}>, alpha = rho0 / gamma
+  static constexpr int NQ = 2;
+  int64_t n;
+  MvOut<R> mv;
+  cx<R>* out;
+  const cx<R>* rt;
+  __device__ __forceinline__ void element(int64_t i, double* acc) {
+    const cx<R> v = mv.get(i);
+    if (mv.P) out[i] = v;
+    acc_dotc(acc, rt[i], v);
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    const double2 g = mkc(t[0], t[1]);
+    if (tiny<R>(g)) { set_breakdown(st, CCG_BD_SIGMA); return; }
+    st->alpha = cdiv(st->rho_old, g);
+  }
+};
+template <class R> struct BlR : PhaseBase {  // r^_i -= alpha u^_{i+1}, i <= j; x += alpha u^_0; ||r^_0||
+  static constexpr int NQ = 1;
+  int64_t n;
+  BlVecs vv;
+  int j;
+  cx<R>* x;
+  cx<R> alpha;
+  __device__ __forceinline__ void load(const SolveState* st) { alpha = narrow<R>(st->alpha); }
+  __device__ __forceinline__ void element(int64_t e, double* acc) {
+    const cx<R>* u0 = static_cast<const cx<R>*>(vv.uh[0]);
+    x[e] = cadd(x[e], cmul(alpha, u0[e]));
+    for (int i = 0; i <= j; ++i) {
+      cx<R>* ri = static_cast<cx<R>*>(vv.rh[i]);
+      const cx<R>* ui1 = static_cast<const cx<R>*>(vv.uh[i + 1]);
+      const cx<R> v = csub(ri[e], cmul(alpha, ui1[e]));
+      ri[e] = v;
+      if (i == 0) acc_nrm2(acc, v);
+    }
+  }
+  __device__ void finish(const double* t, SolveState* st) {  // a BiCG step may end the solve
+    const double rel = sqrt(t[0]) / st->poll.ynorm;
+    const int status = nonfinite(rel) ? ST_NONFINITE : (rel <= st->tol ? ST_OK : -100);
+    if (status == -100) return;
+    const int k = st->poll.k + 1;
+    st->poll.k = k;
+    st->poll.relres = rel;
+    st->hist[k] = rel;
+    st->poll.status = status;
+    st->poll.done = 1;
+  }
+};
+// Gram matrix of r^_0..r^_L (r^_L from the product just made): the pairs
+// (i, j) with 1 <= i <= j <= L and (i, 0); then the normal equations.
+template <class R, int L> struct BlGram : PhaseBase {
+  static constexpr int NP = L * (L + 1) / 2 + L;
+  static constexpr int NQ = 2 * NP;
+  int64_t n;
+  MvOut<R> mv;
+  BlVecs vv;
+  __device__ __forceinline__ void element(int64_t e, double* acc) {
+    cx<R> r[L + 1];
+#pragma unroll
+    for (int i = 0; i < L; ++i) r[i] = static_cast<const cx<R>*>(vv.rh[i])[e];
+    r[L] = mv.get(e);
+    if (mv.P) static_cast<cx<R>*>(vv.rh[L])[e] = r[L];
+    int q = 0;
+#pragma unroll
+    for (int i = 1; i <= L; ++i) {
+#pragma unroll
+      for (int j = i; j <= L; ++j) { acc_dotc(acc + 2 * q, r[i], r[j]); ++q; }
+      acc_dotc(acc + 2 * q, r[i], r[0]);
+      ++q;
+    }
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    double2 M[L][L], b[L];
+    int q = 0;
+    for (int i = 0; i < L; ++i) {
+      for (int j = i; j < L; ++j) {
+        M[i][j] = mkc(t[2 * q], t[2 * q + 1]);
+        M[j][i] = cconj(M[i][j]);
+        ++q;
+      }
+      b[i] = mkc(t[2 * q], t[2 * q + 1]);
+      ++q;
+    }
+    // M = C C^H (C lower triangular), then C c = b, C^H g = c
+    double2 Cm[L][L];
+    for (int i = 0; i < L; ++i)
+      for (int j = 0; j < L; ++j) Cm[i][j] = mkc(0.0, 0.0);
+    for (int j = 0; j < L; ++j) {
+      double d = M[j][j].x;
+      for (int k = 0; k < j; ++k) d -= Cm[j][k].x * Cm[j][k].x + Cm[j][k].y * Cm[j][k].y;
+      if (!(d > tiny_guard<R>() * M[j][j].x) || tiny<R>(d)) { set_breakdown(st, CCG_BD_MU); return; }
+      const double cjj = sqrt(d);
+      Cm[j][j] = mkc(cjj, 0.0);
+      for (int i = j + 1; i < L; ++i) {
+        double2 s = M[i][j];
+        for (int k = 0; k < j; ++k) s = csub(s, cmul(Cm[i][k], cconj(Cm[j][k])));
+        Cm[i][j] = cscale(1.0 / cjj, s);
+      }
+    }
+    double2 c[L], g[L];
+    for (int i = 0; i < L; ++i) {
+      double2 s = b[i];
+      for (int k = 0; k < i; ++k) s = csub(s, cmul(Cm[i][k], c[k]));
+      c[i] = cscale(1.0 / Cm[i][i].x, s);
+    }
+    for (int i = L - 1; i >= 0; --i) {
+      double2 s = c[i];
+      for (int k = i + 1; k < L; ++k) s = csub(s, cmul(cconj(Cm[k][i]), g[k]));
+      g[i] = cscale(1.0 / Cm[i][i].x, s);
+    }
+    for (int i = 0; i < L; ++i) st->bl_g[i] = g[i];
+    st->omega = g[L - 1];
+  }
+};
+template <class R> struct BlMR : PhaseBase {  // the minimal-residual update; ||r^_0||, <r~, r^_0>
+  static constexpr int NQ = 3;
+  int64_t n;
+  BlVecs vv;
+  int L;
+  cx<R>* x;
+  const cx<R>* rt;
+  cx<R> g[kMaxEll];
+  __device__ __forceinline__ void load(const SolveState* st) {
+    for (int i = 0; i < L; ++i) g[i] = narrow<R>(st->bl_g[i]);
+  }
+  __device__ __forceinline__ void element(int64_t e, double* acc) {
+    cx<R> xe = x[e];
+    cx<R>* r0 = static_cast<cx<R>*>(vv.rh[0]);
+    cx<R>* u0 = static_cast<cx<R>*>(vv.uh[0]);
+    cx<R> r0e = r0[e], u0e = u0[e];
+    const cx<R> r0_old = r0e;
+    for (int j = 1; j <= L; ++j) {
+      const cx<R> rprev = j == 1 ? r0_old : static_cast<const cx<R>*>(vv.rh[j - 1])[e];
+      xe = cadd(xe, cmul(g[j - 1], rprev));
+      r0e = csub(r0e, cmul(g[j - 1], static_cast<const cx<R>*>(vv.rh[j])[e]));
+      u0e = csub(u0e, cmul(g[j - 1], static_cast<const cx<R>*>(vv.uh[j])[e]));
+    }
+    x[e] = xe;
+    r0[e] = r0e;
+    u0[e] = u0e;
+    acc_nrm2(acc, r0e);
+    acc_dotc(acc + 1, rt[e], r0e);
+  }
+  __device__ void finish(const double* t, SolveState* st) {
+    if (end_iteration(st, st->poll.k + 1, sqrt(t[0]) / st->poll.ynorm, 0)) return;
+    if (tiny<R>(st->omega)) { set_breakdown(st, CCG_BD_OMEGA); return; }
+    // start of the next cycle: rho0 = -omega rho0, then step 0's rho1 and beta
+    st->rho_old = cmul(cscale(-1.0, st->omega), st->rho_old);
+    if (tiny<R>(st->rho_old)) { set_breakdown(st, CCG_BD_RHO); return; }
+    const double2 rho1 = mkc(t[1], t[2]);
+    st->beta = cdiv(cmul(st->alpha, rho1), st->rho_old);
+    st->rho_old = rho1;
+  }
+};
+template <class R> struct ZeroVec : PhaseBase {
+  static constexpr bool kReduce = false;
+  static constexpr int NQ = 1;
+  int64_t n;
+  cx<R>* v;
+  __device__ __forceinline__ void element(int64_t i, double*) { v[i] = mk<R>(0, 0); }
+  __device__ void finish(const double*, SolveState*) {}
+};
+
+// ---------------------------------------------------------------------------
 // GMRES(m) (Saad-Schultz; PIM `rgmres`, Sec. 2.1), complex form.  Arnoldi
 // step j orthogonalises w = A v_j against v_0 .. v_j by classical
 // Gram-Schmidt applied twice: h1 = V^H w in one pass, w -= V h1 with
@@ -1040,6 +1557,9 @@ template <class R> struct GmRestart : PhaseBase {  // r = y - A x, beta = ||r||;
 
 static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// Warps per matrix row in the row sweep (gemv_n_rows).
+constexpr int kRowSplit = 4;
+
 // Launch geometry of the dense sweeps for one operator.
 template <class R> struct Dense {
   const cx<R>* A;
@@ -1056,7 +1576,8 @@ template <class R> struct Dense {
     n = op->n;
     unit = op->unit;
     const int64_t rows_blocks = (n + kWarps - 1) / kWarps;
-    grid_rows = (int)std::min<int64_t>(rows_blocks, (int64_t)num_sms * 16);
+    grid_rows = (int)std::min<int64_t>((n + kWarps / kRowSplit - 1) / (kWarps / kRowSplit), 1 << 30);
+    (void)rows_blocks;
     const int64_t nunits = n / unit;
     ncb = (int)((nunits + 32 * E - 1) / (32 * E));
     const int64_t target = (int64_t)num_sms * 4;
@@ -1196,15 +1717,18 @@ template <class R> struct Runner {
   // would otherwise enter the sweep timing with a near-zero duration.
   MvOut<R> apply_n(const cx<R>* x, cx<R>* y, const SolveState* st, bool timed = true) {
     if (timed) timing_begin(h);
+    int* rec = timed ? timing_rec(h) : nullptr;
     if (op->kind == CCG_OPK_DIPOLE) {
-      dipole_apply(op, x, y, false, st, s);
-      h->launches += 5;
+      dipole_apply(op, x, y, false, st, s, rec);
+      h->launches += op->dip.kernels;
     } else {
       if constexpr (sizeof(R) == 4) {
-        if (d.unit == 2) gemv_n_rows<R, 2><<<d.grid_rows, kBlock, 0, s>>>(d.A, d.lda, d.n, x, y, st);
-        else gemv_n_rows<R, 1><<<d.grid_rows, kBlock, 0, s>>>(d.A, d.lda, d.n, x, y, st);
+        if (d.unit == 2)
+          gemv_n_rows<R, 2, kRowSplit><<<d.grid_rows, kBlock, 0, s>>>(d.A, d.lda, d.n, x, y, st, rec);
+        else
+          gemv_n_rows<R, 1, kRowSplit><<<d.grid_rows, kBlock, 0, s>>>(d.A, d.lda, d.n, x, y, st, rec);
       } else {
-        gemv_n_rows<R, 1><<<d.grid_rows, kBlock, 0, s>>>(d.A, d.lda, d.n, x, y, st);
+        gemv_n_rows<R, 1, kRowSplit><<<d.grid_rows, kBlock, 0, s>>>(d.A, d.lda, d.n, x, y, st, rec);
       }
       ++h->launches;
     }
@@ -1214,20 +1738,21 @@ template <class R> struct Runner {
   // A^H x: dense operators leave nsplit partial vectors in P2; others write y.
   MvOut<R> apply_c(const cx<R>* x, cx<R>* y, const SolveState* st) {
     timing_begin(h);
+    int* rec = timing_rec(h);
     if (op->kind == CCG_OPK_DIPOLE) {
-      dipole_apply(op, x, y, true, st, s);
-      h->launches += 5;
+      dipole_apply(op, x, y, true, st, s, rec);
+      h->launches += op->dip.kernels;
       timing_end(h, kDt, CCG_SWEEP_C, d.sweep_bytes());
       return plain(y);
     }
     dim3 grid(d.ncb, d.nsplit);
     if constexpr (sizeof(R) == 4) {
       if (d.unit == 2)
-        gemv_tile<R, 2, Dense<R>::E, false, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, nullptr, x, nullptr, w.P2, st);
+        gemv_tile<R, 2, Dense<R>::E, false, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, nullptr, x, nullptr, w.P2, st, rec);
       else
-        gemv_tile<R, 1, Dense<R>::E, false, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, nullptr, x, nullptr, w.P2, st);
+        gemv_tile<R, 1, Dense<R>::E, false, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, nullptr, x, nullptr, w.P2, st, rec);
     } else {
-      gemv_tile<R, 1, Dense<R>::E, false, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, nullptr, x, nullptr, w.P2, st);
+      gemv_tile<R, 1, Dense<R>::E, false, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, nullptr, x, nullptr, w.P2, st, rec);
     }
     ++h->launches;
     timing_end(h, kDt, CCG_SWEEP_C, d.sweep_bytes());
@@ -1245,13 +1770,14 @@ template <class R> struct Runner {
     }
     dim3 grid(d.ncb, d.nsplit);
     timing_begin(h);
+    int* rec = timing_rec(h);
     if constexpr (sizeof(R) == 4) {
       if (d.unit == 2)
-        gemv_tile<R, 2, Dense<R>::E, true, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, x1, x2, w.P1, w.P2, st);
+        gemv_tile<R, 2, Dense<R>::E, true, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, x1, x2, w.P1, w.P2, st, rec);
       else
-        gemv_tile<R, 1, Dense<R>::E, true, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, x1, x2, w.P1, w.P2, st);
+        gemv_tile<R, 1, Dense<R>::E, true, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, x1, x2, w.P1, w.P2, st, rec);
     } else {
-      gemv_tile<R, 1, Dense<R>::E, true, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, x1, x2, w.P1, w.P2, st);
+      gemv_tile<R, 1, Dense<R>::E, true, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, x1, x2, w.P1, w.P2, st, rec);
     }
     ++h->launches;
     timing_end(h, kDt, CCG_SWEEP_BOTH, d.sweep_bytes());
@@ -1316,6 +1842,9 @@ static int solve_core(ccg_handle* h, int method, const ccg_operator* op, const W
       case M_QMR: p.c1 = V[1]; p.c2 = V[2]; break;       // v~, w~
       case M_COCG: p.c1 = V[1]; break;                   // p
       case M_BICG: p.c1 = V[1]; break;                   // r~
+      case M_CGS: p.c1 = V[1]; break;                    // r^
+      case M_TFQMR: p.c1 = V[1]; p.c2 = V[2]; break;     // w, u (r itself is r^)
+      case M_BICGSTABL: p.c1 = V[2 * kMaxEll + 2]; break; // r~
       default: break;
     }
     if (x0_zero) {
@@ -1374,6 +1903,70 @@ static int solve_core(ccg_handle* h, int method, const ccg_operator* op, const W
     step = [=, &run]() {
       CrXR<R> c; c.n = n; c.x = x; c.r = r; c.p = pv; c.q = q; run.phase(c);
       rho_pq();
+    };
+  } else if (method == M_CGS) {
+    cx<R>*r = V[0], *rh = V[1], *u = V[2], *pv = V[3], *q = V[4], *v = V[5], *uh = V[6], *qh = V[7];
+    step = [=, &run]() {
+      CsUP<R> a; a.n = n; a.r = r; a.q = q; a.u = u; a.p = pv; run.phase(a);
+      CsSigma<R> b; b.n = n; b.v = v; b.rh = rh; b.mv = run.apply_n(pv, v, st); run.phase(b);
+      CsQ<R> c; c.n = n; c.u = u; c.v = v; c.q = q; c.uh = uh; c.x = x; run.phase(c);
+      CsR<R> e; e.n = n; e.r = r; e.rh = rh; e.mv = run.apply_n(uh, qh, st); run.phase(e);
+    };
+  } else if (method == M_CGNE) {
+    cx<R>*r = V[0], *pv = V[1], *wv = V[2], *z = V[3];
+    CnP<R> p0; p0.n = n; p0.p = pv; p0.mv = run.apply_c(r, z, st); run.phase(p0);
+    step = [=, &run]() {
+      CnXR<R> a; a.n = n; a.x = x; a.r = r; a.p = pv; a.mv = run.apply_n(pv, wv, st); run.phase(a);
+      CnP<R> b; b.n = n; b.p = pv; b.mv = run.apply_c(r, z, st); run.phase(b);
+    };
+  } else if (method == M_BICGSTABL) {
+    const int L = h->bicgstab_l;
+    BlVecs vv;
+    for (int i = 0; i <= kMaxEll; ++i) {
+      vv.rh[i] = V[i];
+      vv.uh[i] = V[kMaxEll + 1 + i];
+    }
+    const cx<R>* rt = V[2 * kMaxEll + 2];
+    { ZeroVec<R> z; z.n = n; z.v = static_cast<cx<R>*>(vv.uh[0]); run.phase(z); }
+    { BlRho<R> a; a.n = n; a.mv = run.plain(V[0]); a.out = V[0]; a.rt = rt; a.start = true; run.phase(a); }
+    step = [=, &run]() {
+      for (int j = 0; j < L; ++j) {
+        cx<R>* uj = static_cast<cx<R>*>(vv.uh[j]);
+        cx<R>* uj1 = static_cast<cx<R>*>(vv.uh[j + 1]);
+        cx<R>* rj = static_cast<cx<R>*>(vv.rh[j]);
+        cx<R>* rj1 = static_cast<cx<R>*>(vv.rh[j + 1]);
+        BlU<R> a; a.n = n; a.vv = vv; a.j = j; run.phase(a);
+        BlGamma<R> b; b.n = n; b.out = uj1; b.rt = rt; b.mv = run.apply_n(uj, uj1, st); run.phase(b);
+        BlR<R> c; c.n = n; c.vv = vv; c.j = j; c.x = x; run.phase(c);
+        MvOut<R> mv = run.apply_n(rj, rj1, st);
+        if (j + 1 < L) {
+          BlRho<R> e; e.n = n; e.mv = mv; e.out = rj1; e.rt = rt; e.start = false; run.phase(e);
+        } else {
+          switch (L) {
+            case 1: { BlGram<R, 1> gm; gm.n = n; gm.mv = mv; gm.vv = vv; run.phase(gm); break; }
+            case 2: { BlGram<R, 2> gm; gm.n = n; gm.mv = mv; gm.vv = vv; run.phase(gm); break; }
+            case 3: { BlGram<R, 3> gm; gm.n = n; gm.mv = mv; gm.vv = vv; run.phase(gm); break; }
+            default: { BlGram<R, 4> gm; gm.n = n; gm.mv = mv; gm.vv = vv; run.phase(gm); break; }
+          }
+        }
+      }
+      BlMR<R> f; f.n = n; f.vv = vv; f.L = L; f.x = x; f.rt = rt; run.phase(f);
+    };
+  } else if (method == M_TFQMR) {
+    cx<R>*rh = V[0], *wv = V[1], *u = V[2], *un = V[3], *v = V[4], *uh = V[5], *dv = V[6];
+    TqInit<R> t0; t0.n = n; t0.v = v; t0.d = dv; run.phase(t0);
+    run.apply_n(u, uh, st);  // A u_0
+    step = [=, &run]() {
+      TqSigma<R> a; a.n = n; a.v = v; a.rh = rh; a.mv = run.plain(uh); run.phase(a);
+      TqHalf<R, false> e; e.n = n; e.x = x; e.w = wv; e.d = dv; e.um = u; e.un = un; e.v = v; e.uh = uh; e.rh = rh;
+      run.phase(e);
+      TqXStop<R> s1; s1.n = n; s1.x = x; s1.d = dv; run.phase(s1);
+      run.apply_n(un, uh, st);  // A u_{m+1}
+      TqHalf<R, true> o; o.n = n; o.x = x; o.w = wv; o.d = dv; o.um = un; o.un = nullptr; o.v = v; o.uh = uh; o.rh = rh;
+      run.phase(o);
+      TqXStop<R> s2; s2.n = n; s2.x = x; s2.d = dv; run.phase(s2);
+      TqU<R> uu; uu.n = n; uu.w = wv; uu.un = un; uu.uh = uh; uu.u = u; uu.v = v; run.phase(uu);
+      run.apply_n(u, uh, st);   // A u for the next iteration
     };
   } else if (method == M_GMRES) {
     if (w.gm.m < 1) {

@@ -162,9 +162,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 template <int T>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_bf16_split(const __grid_constant__ TcMaps maps, float* __restrict__ C, int M, int N, int K, int64_t ldc,
-                    int* err, const int* skip) {
+                    int* err, const int* skip, int* skip_rec) {
   using G = Cfg<T>;
-  if (skip != nullptr && *skip) return;
+  if (skip != nullptr && *skip) {  // every column has stopped
+    if (skip_rec != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *skip_rec = 1;
+    return;
+  }
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * G::STAGE_BYTES);
@@ -430,7 +433,8 @@ static int tc_product_t(ccg_handle* h, ccg_operator* op, const float2* X, float2
   const int Nr = 2 * k;
   dim3 grid((unsigned)((Nr + G::BN - 1) / G::BN), (unsigned)((n + tc::BM - 1) / tc::BM));
   tc::gemm_bf16_split<T><<<grid, tc::THREADS, G::SMEM_BYTES, s>>>(maps, reinterpret_cast<float*>(Y), (int)n, Nr,
-                                                                    (int)(2 * n), (int64_t)Nr, err, skip);
+                                                                    (int)(2 * n), (int64_t)Nr, err, skip,
+                                                                    timing_rec(h));
   h->launches += 2;
   return cudaGetLastError() == cudaSuccess ? CCG_OK : CCG_ERR_CUDA;
 }

@@ -99,7 +99,7 @@ def test_dot_products(h, dtype, n):
 
 # ------------------------------------------------------------------ solvers
 SMALL = [("bicgstab", False), ("cgnr", False), ("qmr", False), ("cocg", True), ("cocr", True), ("bicg", False),
-         ("gmres", False)]
+         ("gmres", False), ("cgs", False), ("cgne", False), ("tfqmr", False), ("bicgstabl", False)]
 
 
 def system(n, shift, seed, symmetric, dtype=np.complex128):
@@ -150,6 +150,32 @@ def test_gmres_restarts_match_oracle(h, ccg, dtype):
         assert abs(info["iters"] - ref.iters) <= 1
     finally:
         h.set_option(ccg.OPT_GMRES_RESTART, 30)
+
+
+@pytest.mark.parametrize("ell", [1, 3, 4])
+def test_bicgstabl_degrees_match_oracle(h, ccg, ell):
+    """BiCGstab(l) for l = 1, 3, 4 (2 is the default, in the tests above):
+    iterates and residual history against the oracle's; ragged n."""
+    A, y = system(1000, 0.8, 11, False)
+    x0 = W.random_vector(1000, 12) * 0.1
+    h.set_option(ccg.OPT_BICGSTAB_L, ell)
+    try:
+        op = h.op_dense(dev(A))
+        oop = O.DenseOp(A)
+        for k in (1, 2, 5):
+            ref = O.solve(oop, "bicgstabl", y, x0=x0, tol=0.0, maxit=k, ell=ell)
+            xd = dev(x0.copy())
+            st, info, hist = h.solve("bicgstabl", op, dev(y), xd, tol=0.0, maxit=k)
+            assert info["iters"] == ref.iters == k
+            assert relerr(xd.cpu().numpy(), ref.x) < 1e-9, (ell, k)
+            assert np.allclose(hist, ref.hist, rtol=1e-9, atol=0), (ell, k)
+        ref = O.solve(oop, "bicgstabl", y, tol=1e-10, maxit=300, ell=ell)
+        xd = torch.zeros(1000, dtype=torch.complex128, device="cuda")
+        st, info, hist = h.solve("bicgstabl", op, dev(y), xd, tol=1e-10, maxit=300)
+        assert st == 0 == ref.status and abs(info["iters"] - ref.iters) <= 1
+        assert info["true_relres"] <= 1e-10
+    finally:
+        h.set_option(ccg.OPT_BICGSTAB_L, 2)
 
 
 @pytest.mark.parametrize("method,sym", SMALL)
@@ -270,10 +296,18 @@ def test_breakdowns_match_oracle(h, ccg):
     st, info, _ = h.solve("cocr", op, dev(y1), torch.zeros(2, dtype=torch.complex128, device="cuda"), 1e-12, 5)
     ref = O.solve(O.DenseOp(D, symmetric=True), "cocr", y1, tol=1e-12, maxit=5)
     assert st == ccg.BREAKDOWN == ref.status and info["breakdown"] == ref.detail == ccg_bd_mu()
-    # BiCG: <p~, A p> = 0 on the swap matrix
+    # BiCG and CGS: <p~, A p> = 0 on the swap matrix
     op = h.op_dense(dev(A))
-    st, info, _ = h.solve("bicg", op, dev(y), torch.zeros(2, dtype=torch.complex128, device="cuda"), 1e-12, 5)
-    ref = O.solve(O.DenseOp(A), "bicg", y, tol=1e-12, maxit=5)
+    for m in ("bicg", "cgs", "tfqmr", "bicgstabl"):
+        st, info, _ = h.solve(m, op, dev(y), torch.zeros(2, dtype=torch.complex128, device="cuda"), 1e-12, 5)
+        ref = O.solve(O.DenseOp(A), m, y, tol=1e-12, maxit=5)
+        assert st == ccg.BREAKDOWN == ref.status and info["breakdown"] == ref.detail and info["iters"] == ref.iters
+    # CGNE: A^H r0 = 0 with r0 != 0
+    S = np.array([[1, 1], [1, 1]], dtype=np.complex128)
+    y2 = np.array([1, -1], dtype=np.complex128)
+    op = h.op_dense(dev(S))
+    st, info, _ = h.solve("cgne", op, dev(y2), torch.zeros(2, dtype=torch.complex128, device="cuda"), 1e-12, 5)
+    ref = O.solve(O.DenseOp(S), "cgne", y2, tol=1e-12, maxit=5)
     assert st == ccg.BREAKDOWN == ref.status and info["breakdown"] == ref.detail and info["iters"] == ref.iters
 
 

@@ -90,7 +90,7 @@ def test_dipole_full_size_sampled_rows(h):
         del op
 
 
-@pytest.mark.parametrize("method", ["cocg", "bicgstab", "qmr", "cgnr", "cocr", "bicg", "gmres"])
+@pytest.mark.parametrize("method", ["cocg", "bicgstab", "qmr", "cgnr", "cocr", "bicg", "gmres", "cgs", "cgne", "tfqmr", "bicgstabl"])
 def test_dipole_solve_iterates_match_oracle(h, method):
     occ = W.sphere_occupancy(12)
     ref = O.DipoleOp(occ, KD, M, use_fft=True)

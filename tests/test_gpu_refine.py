@@ -45,7 +45,7 @@ def relres(A, x, y):
     return np.linalg.norm(y - A @ x) / np.linalg.norm(y)
 
 
-@pytest.mark.parametrize("method", ["bicgstab", "cgnr", "qmr", "cocg", "cocr", "bicg", "gmres"])
+@pytest.mark.parametrize("method", ["bicgstab", "cgnr", "qmr", "cocg", "cocr", "bicg", "gmres", "cgs", "cgne", "tfqmr", "bicgstabl"])
 @pytest.mark.parametrize("n", [256, 1000])
 def test_refined_matches_oracle(h, method, n):
     A, y = W.dense_system(n, 3.0, 17)
