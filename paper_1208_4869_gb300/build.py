@@ -72,7 +72,9 @@ def build(force=False, verbose=False):
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + ".tmp.%d" % os.getpid()
-    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs
+    # every symbol must resolve at link time (a declaration without its
+    # definition would otherwise surface only when the library is loaded)
+    cmd = [cc] + ARCH + ["-shared", "-Xlinker", "--no-undefined", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))

@@ -51,6 +51,8 @@ struct DipGeom {
   int64_t H;  // octant points (Mx/2 + 1)(My/2 + 1)(Mz/2 + 1)
 };
 
+template <class R> static bool dipole_fused(const DipGeom& g);
+
 static DipGeom geom(const ccg_operator* op) {
   DipGeom g;
   g.nx = op->dip.nx; g.ny = op->dip.ny; g.nz = op->dip.nz;
@@ -432,6 +434,129 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 3 : 2) dip_inv_z_reg(
   }
 }
 
+// ---------------------------------------------------------------------------
+// Fused z-and-y kernels for cubic lattices (nx = ny = nz = N / 2): one block
+// transforms a group of lines of one x-plane in both directions, so the z
+// and y passes of each direction become one kernel (3 kernels per
+// application instead of 5) and the half-transformed plane never leaves
+// shared memory.  Groups of BL lines keep 3 x N/2 x N/BL blocks in flight.
+// ---------------------------------------------------------------------------
+template <class R, int N> constexpr size_t fwd_zy_smem() {
+  return ((size_t)(N / 2) * (N / 2 + 1) + (size_t)(N / 2) * (reg_bl<R>() + 1) + (size_t)N * reg_bl<R>()) *
+         sizeof(cx<R>);
+}
+template <class R, int N> constexpr size_t inv_yz_smem() {
+  return ((size_t)reg_bl<R>() * (N + 1) + (size_t)N * reg_bl<R>()) * sizeof(cx<R>);
+}
+// Lengths with the fused kernels: complex64 (each block recomputes its
+// plane's z transform, N / BL times over the plane, and the inverse y
+// transform twice; cheap on the FP32 pipe, but in complex128 the FP64 pipe
+// makes the recomputation cost more than the passes it saves: 1.96 ms per
+// application against 1.09 ms for five passes at L = 64), register-FFT
+// lengths whose half is a multiple of the line group, forward buffers that
+// fit in shared memory.
+template <class R, int N> constexpr bool fused_ok() {
+  return sizeof(R) == 4 && Fac<N>::N1 > 0 && (N / 2) % reg_bl<R>() == 0 && fwd_zy_smem<R, N>() <= 200 * 1024;
+}
+
+// Forward: gather the (j, z) plane i of component q from the site vector,
+// z FFT of its N/2 j-lines keeping kz0 .. kz0 + BL - 1, y FFT of those BL
+// kz-lines (input j < N/2), write grid[q][i][ky][kz0 ..].
+template <class R, int N>
+__global__ void __launch_bounds__(kBlock) dip_fwd_zy(const cx<R>* __restrict__ x, cx<R>* __restrict__ grid,
+                                                     const int* __restrict__ idx, DipGeom g,
+                                                     const cx<R>* __restrict__ Wz, const cx<R>* __restrict__ Wy,
+                                                     int conj_in, const SolveState* __restrict__ st,
+                                                     int* skip_rec) {
+  if (sweep_skipped(st, skip_rec)) return;
+  constexpr int BL = reg_bl<R>(), NH = N / 2, G = N / BL;
+  constexpr int PS = NH + 1, TS = BL + 1;  // odd strides: conflict-free transposes
+  extern __shared__ unsigned char smem_raw[];
+  cx<R>* P = reinterpret_cast<cx<R>*>(smem_raw);  // P[z * PS + j]
+  cx<R>* T = P + NH * PS;                          // T[j * TS + kz - kz0]
+  cx<R>* E = T + NH * TS;
+  const int q = blockIdx.y;
+  const int i = blockIdx.x / G;
+  const int kz0 = (blockIdx.x - i * G) * BL;
+  const cx<R>* xq = x + (int64_t)q * g.N;
+#pragma unroll 4
+  for (int t = threadIdx.x; t < NH * NH; t += kBlock) {
+    const int z = t % NH, j = t / NH;
+    const int sidx = __ldg(&idx[((int64_t)i * NH + j) * NH + z]);
+    cx<R> v = mk<R>(0, 0);
+    if (sidx >= 0) {
+      v = xq[sidx];
+      if (conj_in) v = cconj(v);
+    }
+    P[z * PS + j] = v;
+  }
+  __syncthreads();
+  for (int jb = 0; jb < NH; jb += BL) {
+    auto load = [&](int z, int b) { return P[z * PS + jb + b]; };
+    auto store = [&](int kz, int b, cx<R> v) {
+      const int kl = kz - kz0;
+      if (kl >= 0 && kl < BL) T[(jb + b) * TS + kl] = v;
+    };
+    fft2<R, N, BL, -1, NH, N>(load, store, E, Wz);
+    __syncthreads();  // E is reused by the next batch
+  }
+  cx<R>* gq = grid + (int64_t)q * g.G + (int64_t)i * N * N + kz0;
+  auto load = [&](int j, int b) { return T[j * TS + b]; };
+  auto store = [&](int ky, int b, cx<R> v) { gq[(int64_t)ky * N + b] = v; };
+  fft2<R, N, BL, -1, NH, N>(load, store, E, Wy);
+}
+
+// Inverse: inverse y FFT of the N kz-lines of plane i (in batches of BL)
+// keeping j0 .. j0 + BL - 1, inverse z FFT of those BL j-lines (z < N/2),
+// then y = x / alpha - conv on the occupied sites (conjugated for A^H).
+template <class R, int N>
+__global__ void __launch_bounds__(kBlock) dip_inv_yz(const cx<R>* __restrict__ x, cx<R>* __restrict__ y,
+                                                     const cx<R>* __restrict__ grid, const int* __restrict__ idx,
+                                                     DipGeom g, const cx<R>* __restrict__ Wz,
+                                                     const cx<R>* __restrict__ Wy, cx<R> alpha_inv, int conj,
+                                                     const SolveState* __restrict__ st) {
+  if (skip_state(st)) return;
+  constexpr int BL = reg_bl<R>(), NH = N / 2, G = NH / BL;
+  constexpr int VS = N + 1, OS = BL + 1;
+  extern __shared__ unsigned char smem_raw[];
+  cx<R>* Vb = reinterpret_cast<cx<R>*>(smem_raw);  // Vb[jl * VS + kz]
+  cx<R>* E = Vb + BL * VS;
+  cx<R>* O = Vb;                                     // O[z * OS + jl], written after Vb's last read
+  const int q = blockIdx.y;
+  const int i = blockIdx.x / G;
+  const int j0 = (blockIdx.x - i * G) * BL;
+  const cx<R>* gq = grid + (int64_t)q * g.G + (int64_t)i * N * N;
+  for (int kb = 0; kb < N; kb += BL) {
+    auto load = [&](int ky, int b) { return gq[(int64_t)ky * N + kb + b]; };
+    auto store = [&](int j, int b, cx<R> v) {
+      const int jl = j - j0;
+      if (jl >= 0 && jl < BL) Vb[jl * VS + kb + b] = v;
+    };
+    fft2<R, N, BL, +1, N, N>(load, store, E, Wy);
+    __syncthreads();
+  }
+  {
+    auto load = [&](int kz, int b) { return Vb[b * VS + kz]; };
+    auto store = [&](int z, int b, cx<R> v) { O[z * OS + b] = v; };
+    fft2<R, N, BL, +1, N, NH>(load, store, E, Wz);
+  }
+  __syncthreads();
+  const cx<R>* xq = x + (int64_t)q * g.N;
+  cx<R>* yq = y + (int64_t)q * g.N;
+#pragma unroll 4
+  for (int t = threadIdx.x; t < BL * NH; t += kBlock) {
+    const int z = t % NH, jl = t / NH;
+    const int sidx = __ldg(&idx[((int64_t)i * NH + j0 + jl) * NH + z]);
+    if (sidx >= 0) {
+      cx<R> xi = xq[sidx];
+      if (conj) xi = cconj(xi);
+      cx<R> v = csub(cmul(alpha_inv, xi), O[z * OS + jl]);
+      if (conj) v = cconj(v);
+      yq[sidx] = v;
+    }
+  }
+}
+
 // One-time setup: the circulant-embedded field tensor on the grid (double).
 __global__ void dip_green(double2* __restrict__ g6, DipGeom g, double k) {
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < g.G; p += (int64_t)gridDim.x * blockDim.x) {
@@ -629,8 +754,12 @@ template <class R> static int create_t(ccg_operator* op, const uint8_t* occ, cud
   const double zl = 3.0 * g.nx * g.ny * g.Mz * e;     // z-line region
   const double yl = 3.0 * g.nx * g.My * g.Mz * e;     // after the y pass
   const double vec = 3.0 * count * e;
-  op->dip.sweep_bytes = (vec + zl) + (zl + yl) + (yl + 6.0 * g.H * e + yl) + (yl + zl) + (zl + 2 * vec) +
-                        2.0 * cells * 4.0;
+  op->dip.kernels = dipole_fused<R>(g) ? 3 : 5;
+  if (dipole_fused<R>(g))  // gather + one write of the y-transformed region; x pass; one read + scatter
+    op->dip.sweep_bytes = (vec + cells * 4.0 + yl) + (yl + 6.0 * g.H * e + yl) + (yl + cells * 4.0 + 2 * vec);
+  else
+    op->dip.sweep_bytes = (vec + zl) + (zl + yl) + (yl + 6.0 * g.H * e + yl) + (yl + zl) + (zl + 2 * vec) +
+                          2.0 * cells * 4.0;
   return CCG_OK;
 }
 
@@ -740,9 +869,52 @@ static void k3(cx<R>* grid, const ccg_operator* op, const DipGeom& g, const cx<R
   }
 }
 
+
 // FFT lengths with register kernels; other 2^a 3^b lengths use the runtime
 // kernels.
 #define CCG_FFT_SIZES(X) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256)
+
+template <class R, int N>
+static void fused_fwd(const cx<R>* x, cx<R>* grid, const ccg_operator* op, const DipGeom& g, const cx<R>* Wz,
+                      const cx<R>* Wy, int conj, const SolveState* st, int* rec, cudaStream_t s) {
+  static bool opted = false;
+  constexpr size_t sm = fwd_zy_smem<R, N>();
+  smem_opt_in(dip_fwd_zy<R, N>, sm, opted);
+  dip_fwd_zy<R, N><<<dim3((unsigned)(g.nx * (N / reg_bl<R>())), 3), kBlock, sm, s>>>(x, grid, op->dip.idx, g, Wz, Wy,
+                                                                                    conj, st, rec);
+}
+template <class R, int N>
+static void fused_inv(const cx<R>* x, cx<R>* y, const cx<R>* grid, const ccg_operator* op, const DipGeom& g,
+                      const cx<R>* Wz, const cx<R>* Wy, cx<R> ainv, int conj, const SolveState* st, cudaStream_t s) {
+  static bool opted = false;
+  constexpr size_t sm = inv_yz_smem<R, N>();
+  smem_opt_in(dip_inv_yz<R, N>, sm, opted);
+  dip_inv_yz<R, N><<<dim3((unsigned)(g.nx * (N / 2 / reg_bl<R>())), 3), kBlock, sm, s>>>(x, y, grid, op->dip.idx, g,
+                                                                                        Wz, Wy, ainv, conj, st);
+}
+// Three-kernel application for cubic lattices of a fused length; false if
+// the lattice or the length has none.
+template <class R, int N>
+static bool apply_fused_n(const ccg_operator* op, const DipGeom& g, const cx<R>* x, cx<R>* y, cx<R>* grid,
+                          const cx<R>* Wx, const cx<R>* Wy, const cx<R>* Wz, cx<R> ainv, int cj,
+                          const SolveState* st, int* rec, cudaStream_t s) {
+  if constexpr (fused_ok<R, N>()) {
+    fused_fwd<R, N>(x, grid, op, g, Wz, Wy, cj, st, rec, s);
+    k3<R, N>(grid, op, g, Wx, st, s);
+    fused_inv<R, N>(x, y, grid, op, g, Wz, Wy, ainv, cj, st, s);
+    return true;
+  } else {
+    return false;
+  }
+}
+template <class R> static bool dipole_fused(const DipGeom& g) {
+  if (!(g.nx == g.ny && g.ny == g.nz)) return false;
+  switch (g.Mx) {
+#define CCG_FUSED_OK(n) case n: return fused_ok<R, n>();
+    CCG_FFT_SIZES(CCG_FUSED_OK)
+    default: return false;
+  }
+}
 
 template <class R>
 static int apply_t(const ccg_operator* op, const cx<R>* x, cx<R>* y, bool conj, const SolveState* st, int* rec,
@@ -754,6 +926,15 @@ static int apply_t(const ccg_operator* op, const cx<R>* x, cx<R>* y, bool conj, 
   const cx<R>* Wz = static_cast<const cx<R>*>(op->dip.tw[2]);
   const int cj = conj ? 1 : 0;
   const cx<R> ainv = mk<R>((R)op->dip.alpha_inv[0], (R)op->dip.alpha_inv[1]);
+  if (dipole_fused<R>(g)) {
+    bool done = false;
+    switch (g.Mx) {
+#define CCG_CASE_FUSED(n) case n: done = apply_fused_n<R, n>(op, g, x, y, grid, Wx, Wy, Wz, ainv, cj, st, rec, s); break;
+      CCG_FFT_SIZES(CCG_CASE_FUSED)
+      default: break;
+    }
+    if (done) return cudaGetLastError() == cudaSuccess ? CCG_OK : CCG_ERR_CUDA;
+  }
 #define CCG_CASE_K1(n) case n: k1<R, n>(x, grid, op, g, Wz, cj, st, rec, s); break;
   switch (g.Mz) { CCG_FFT_SIZES(CCG_CASE_K1) default: k1<R, 0>(x, grid, op, g, Wz, cj, st, rec, s); }
 #define CCG_CASE_KY(n) case n: ky<R, n>(grid, op, g, Wy, sign, st, s); break;

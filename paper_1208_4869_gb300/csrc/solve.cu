@@ -1561,13 +1561,51 @@ static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 constexpr int kRowSplit = 4;
 
 // Launch geometry of the dense sweeps for one operator.
+// Resident blocks per SM of the column-tiled sweep (A^H x alone, or A x1 with
+// A^H x2), from the occupancy calculator.
+template <class R> static int tile_occupancy(int unit, bool both) {
+  static int cache[2][2] = {{0, 0}, {0, 0}};
+  int& c = cache[unit == 2 ? 1 : 0][both ? 1 : 0];
+  if (c == 0) {
+    const void* fn = nullptr;
+    if constexpr (sizeof(R) == 4) {
+      if (unit == 2) fn = both ? (const void*)gemv_tile<R, 2, 4, true, true> : (const void*)gemv_tile<R, 2, 4, false, true>;
+      else fn = both ? (const void*)gemv_tile<R, 1, 4, true, true> : (const void*)gemv_tile<R, 1, 4, false, true>;
+    } else {
+      fn = both ? (const void*)gemv_tile<R, 1, 4, true, true> : (const void*)gemv_tile<R, 1, 4, false, true>;
+    }
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kBlock, 0) != cudaSuccess) {
+      cudaGetLastError();
+      occ = 2;
+    }
+    c = std::max(1, occ);
+  }
+  return c;
+}
+
+// Row ranges of a column-tiled sweep: enough (column chunk, row range)
+// blocks to fill every SM once at the kernel's occupancy.
+struct TileSplit {
+  int nsplit;
+  int64_t rows_per_range;
+};
+static TileSplit tile_split(int64_t n, int ncb, int64_t target) {
+  int64_t ns = (target + ncb - 1) / ncb;
+  ns = std::max<int64_t>(1, std::min<int64_t>(ns, std::min<int64_t>(32, (n + kWarps - 1) / kWarps)));
+  TileSplit t;
+  t.rows_per_range = (n + ns - 1) / ns;
+  t.nsplit = (int)((n + t.rows_per_range - 1) / t.rows_per_range);
+  return t;
+}
+
 template <class R> struct Dense {
   const cx<R>* A;
   int64_t lda, n;
   int unit;
   int grid_rows;            // gemv_n_rows blocks
-  int ncb, nsplit;          // gemv_tile grid
-  int64_t rows_per_range;
+  int ncb;                  // gemv_tile column chunks
+  TileSplit tc, tb;         // row ranges for A^H x, and for A x1 with A^H x2
   static constexpr int E = 4;
 
   Dense(const ccg_operator* op, int num_sms) {
@@ -1580,18 +1618,19 @@ template <class R> struct Dense {
     (void)rows_blocks;
     const int64_t nunits = n / unit;
     ncb = (int)((nunits + 32 * E - 1) / (32 * E));
-    const int64_t target = (int64_t)num_sms * 4;
-    int64_t ns = (target + ncb - 1) / ncb;
-    ns = std::max<int64_t>(1, std::min<int64_t>(ns, std::min<int64_t>(32, (n + kWarps - 1) / kWarps)));
-    rows_per_range = (n + ns - 1) / ns;
-    nsplit = (int)((n + rows_per_range - 1) / rows_per_range);
     dense = op->kind == CCG_OPK_DENSE;
+    if (dense) {
+      tc = tile_split(n, ncb, (int64_t)num_sms * tile_occupancy<R>(unit, false));
+      tb = tile_split(n, ncb, (int64_t)num_sms * tile_occupancy<R>(unit, true));
+    } else {
+      tc = tb = TileSplit{1, n};
+    }
     dip_bytes = op->dip.sweep_bytes;
   }
   bool dense = true;
   double dip_bytes = 0.0;
   size_t p1_elems() const { return dense ? (size_t)ncb * n : 0; }
-  size_t p2_elems() const { return dense ? (size_t)nsplit * n : 0; }
+  size_t p2_elems() const { return dense ? (size_t)std::max(tc.nsplit, tb.nsplit) * n : 0; }
   double sweep_bytes() const { return dense ? (double)n * (double)n * sizeof(cx<R>) : dip_bytes; }
 };
 
@@ -1745,18 +1784,19 @@ template <class R> struct Runner {
       timing_end(h, kDt, CCG_SWEEP_C, d.sweep_bytes());
       return plain(y);
     }
-    dim3 grid(d.ncb, d.nsplit);
+    dim3 grid(d.ncb, d.tc.nsplit);
+    const int64_t rpr = d.tc.rows_per_range;
     if constexpr (sizeof(R) == 4) {
       if (d.unit == 2)
-        gemv_tile<R, 2, Dense<R>::E, false, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, nullptr, x, nullptr, w.P2, st, rec);
+        gemv_tile<R, 2, Dense<R>::E, false, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, rpr, nullptr, x, nullptr, w.P2, st, rec);
       else
-        gemv_tile<R, 1, Dense<R>::E, false, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, nullptr, x, nullptr, w.P2, st, rec);
+        gemv_tile<R, 1, Dense<R>::E, false, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, rpr, nullptr, x, nullptr, w.P2, st, rec);
     } else {
-      gemv_tile<R, 1, Dense<R>::E, false, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, nullptr, x, nullptr, w.P2, st, rec);
+      gemv_tile<R, 1, Dense<R>::E, false, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, rpr, nullptr, x, nullptr, w.P2, st, rec);
     }
     ++h->launches;
     timing_end(h, kDt, CCG_SWEEP_C, d.sweep_bytes());
-    MvOut<R> m; m.y = nullptr; m.P = w.P2; m.ld = d.n; m.nparts = d.nsplit;
+    MvOut<R> m; m.y = nullptr; m.P = w.P2; m.ld = d.n; m.nparts = d.tc.nsplit;
     return m;
   }
   // A x1 and A^H x2: dense operators from one sweep (ncb partials in P1,
@@ -1768,21 +1808,22 @@ template <class R> struct Runner {
       o2 = apply_c(x2, y2, st);
       return;
     }
-    dim3 grid(d.ncb, d.nsplit);
+    dim3 grid(d.ncb, d.tb.nsplit);
+    const int64_t rpr = d.tb.rows_per_range;
     timing_begin(h);
     int* rec = timing_rec(h);
     if constexpr (sizeof(R) == 4) {
       if (d.unit == 2)
-        gemv_tile<R, 2, Dense<R>::E, true, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, x1, x2, w.P1, w.P2, st, rec);
+        gemv_tile<R, 2, Dense<R>::E, true, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, rpr, x1, x2, w.P1, w.P2, st, rec);
       else
-        gemv_tile<R, 1, Dense<R>::E, true, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, x1, x2, w.P1, w.P2, st, rec);
+        gemv_tile<R, 1, Dense<R>::E, true, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, rpr, x1, x2, w.P1, w.P2, st, rec);
     } else {
-      gemv_tile<R, 1, Dense<R>::E, true, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, d.rows_per_range, x1, x2, w.P1, w.P2, st, rec);
+      gemv_tile<R, 1, Dense<R>::E, true, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, rpr, x1, x2, w.P1, w.P2, st, rec);
     }
     ++h->launches;
     timing_end(h, kDt, CCG_SWEEP_BOTH, d.sweep_bytes());
     o1.y = nullptr; o1.P = w.P1; o1.ld = d.n; o1.nparts = d.ncb;
-    o2.y = nullptr; o2.P = w.P2; o2.ld = d.n; o2.nparts = d.nsplit;
+    o2.y = nullptr; o2.P = w.P2; o2.ld = d.n; o2.nparts = d.tb.nsplit;
   }
 };
 
