@@ -61,10 +61,20 @@ template <class R> struct MvOut {
   const cx<R>* P;
   int64_t ld;
   int nparts;
+  // The partials are added in order 0, 1, ..., nparts - 1; eight loads are
+  // issued before their adds so that the reads overlap.
   __device__ __forceinline__ cx<R> get(int64_t i) const {
     if (P == nullptr) return y != nullptr ? y[i] : mk<R>(0, 0);
     cx<R> s = P[i];
-    for (int q = 1; q < nparts; ++q) s = cadd(s, P[(int64_t)q * ld + i]);
+    int q = 1;
+    for (; q + 7 < nparts; q += 8) {
+      cx<R> v[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) v[t] = P[(int64_t)(q + t) * ld + i];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) s = cadd(s, v[t]);
+    }
+    for (; q < nparts; ++q) s = cadd(s, P[(int64_t)q * ld + i]);
     return s;
   }
 };
@@ -139,11 +149,11 @@ __global__ void __launch_bounds__(kBlock) gemv_n_rows(const cx<R>* __restrict__ 
 // with Y2 it writes P2[range * n + col] = sum over the range's rows of
 // conj(A[row, col]) x2[row].
 template <class R, int U, int E, bool Y1, bool Y2>
-__global__ void __launch_bounds__(kBlock) gemv_tile(const cx<R>* __restrict__ A, int64_t lda, int64_t n,
-                                                    int64_t rows_per_range, const cx<R>* __restrict__ x1,
-                                                    const cx<R>* __restrict__ x2, cx<R>* __restrict__ P1,
-                                                    cx<R>* __restrict__ P2, const SolveState* __restrict__ st,
-                                                    int* skip_rec = nullptr) {
+__device__ __forceinline__ void gemv_tile_body(const cx<R>* __restrict__ A, int64_t lda, int64_t n,
+                                               int64_t rows_per_range, const cx<R>* __restrict__ x1,
+                                               const cx<R>* __restrict__ x2, cx<R>* __restrict__ P1,
+                                               cx<R>* __restrict__ P2, const SolveState* __restrict__ st,
+                                               int* skip_rec) {
   typedef Unit<R, U> Un;
   typedef typename Un::L L;
   constexpr int CBU = 32 * E;  // units per column chunk
@@ -262,6 +272,26 @@ __global__ void __launch_bounds__(kBlock) gemv_tile(const cx<R>* __restrict__ A,
       }
     }
   }
+}
+
+// Entry points: with Y1 (A x1, optionally with A^H x2) the compiler's own
+// register choice keeps 4 blocks per SM at complex64; A^H x alone is held to
+// 3 (complex64) / 2 (complex128) blocks per SM for its two-row loop.
+template <class R, int U, int E, bool Y1, bool Y2>
+__global__ void __launch_bounds__(kBlock) gemv_tile(const cx<R>* __restrict__ A, int64_t lda, int64_t n,
+                                                    int64_t rows_per_range, const cx<R>* __restrict__ x1,
+                                                    const cx<R>* __restrict__ x2, cx<R>* __restrict__ P1,
+                                                    cx<R>* __restrict__ P2, const SolveState* __restrict__ st,
+                                                    int* skip_rec = nullptr) {
+  static_assert(Y1, "A^H x alone runs in gemv_tile_h");
+  gemv_tile_body<R, U, E, Y1, Y2>(A, lda, n, rows_per_range, x1, x2, P1, P2, st, skip_rec);
+}
+template <class R, int U, int E>
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 3 : 2)
+    gemv_tile_h(const cx<R>* __restrict__ A, int64_t lda, int64_t n, int64_t rows_per_range,
+                const cx<R>* __restrict__ x2, cx<R>* __restrict__ P2, const SolveState* __restrict__ st,
+                int* skip_rec = nullptr) {
+  gemv_tile_body<R, U, E, false, true>(A, lda, n, rows_per_range, nullptr, x2, nullptr, P2, st, skip_rec);
 }
 
 }  // namespace ccg

@@ -102,10 +102,10 @@ int run(const DeviceSetup& dev, int64_t n, const void* A_, int64_t lda, const vo
   dim3 grid(ncb, nsplit);
   if (unit == 2) {
     if constexpr (sizeof(R) == 4)
-      gemv_tile<R, 2, E, false, true><<<grid, kBlock, 0, stream>>>(A, lda, n, rows_per_range, nullptr, x, nullptr, P,
+      gemv_tile_h<R, 2, E><<<grid, kBlock, 0, stream>>>(A, lda, n, rows_per_range, x, P,
                                                                    nullptr);
   } else {
-    gemv_tile<R, 1, E, false, true><<<grid, kBlock, 0, stream>>>(A, lda, n, rows_per_range, nullptr, x, nullptr, P,
+    gemv_tile_h<R, 1, E><<<grid, kBlock, 0, stream>>>(A, lda, n, rows_per_range, x, P,
                                                                  nullptr);
   }
   int gsum = (int)((n + kBlock - 1) / kBlock);

@@ -1569,10 +1569,10 @@ template <class R> static int tile_occupancy(int unit, bool both) {
   if (c == 0) {
     const void* fn = nullptr;
     if constexpr (sizeof(R) == 4) {
-      if (unit == 2) fn = both ? (const void*)gemv_tile<R, 2, 4, true, true> : (const void*)gemv_tile<R, 2, 4, false, true>;
-      else fn = both ? (const void*)gemv_tile<R, 1, 4, true, true> : (const void*)gemv_tile<R, 1, 4, false, true>;
+      if (unit == 2) fn = both ? (const void*)gemv_tile<R, 2, 4, true, true> : (const void*)gemv_tile_h<R, 2, 4>;
+      else fn = both ? (const void*)gemv_tile<R, 1, 4, true, true> : (const void*)gemv_tile_h<R, 1, 4>;
     } else {
-      fn = both ? (const void*)gemv_tile<R, 1, 4, true, true> : (const void*)gemv_tile<R, 1, 4, false, true>;
+      fn = both ? (const void*)gemv_tile<R, 1, 4, true, true> : (const void*)gemv_tile_h<R, 1, 4>;
     }
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kBlock, 0) != cudaSuccess) {
@@ -1788,11 +1788,11 @@ template <class R> struct Runner {
     const int64_t rpr = d.tc.rows_per_range;
     if constexpr (sizeof(R) == 4) {
       if (d.unit == 2)
-        gemv_tile<R, 2, Dense<R>::E, false, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, rpr, nullptr, x, nullptr, w.P2, st, rec);
+        gemv_tile_h<R, 2, Dense<R>::E><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, rpr, x, w.P2, st, rec);
       else
-        gemv_tile<R, 1, Dense<R>::E, false, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, rpr, nullptr, x, nullptr, w.P2, st, rec);
+        gemv_tile_h<R, 1, Dense<R>::E><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, rpr, x, w.P2, st, rec);
     } else {
-      gemv_tile<R, 1, Dense<R>::E, false, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, rpr, nullptr, x, nullptr, w.P2, st, rec);
+      gemv_tile_h<R, 1, Dense<R>::E><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, rpr, x, w.P2, st, rec);
     }
     ++h->launches;
     timing_end(h, kDt, CCG_SWEEP_C, d.sweep_bytes());
