@@ -182,17 +182,26 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def profiled_traffic(kernel, src_files):
+def kernel_digest(tag):
+    """sha256[:16] of the source text of the kernel behind a sweep tag (its
+    section of the source file) and of the shared device helpers."""
+    h = hashlib.sha256()
+    for f, start, end in kernel_sources(tag):
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            text = fh.read()
+        i = text.index(start.encode()) if start else 0
+        j = text.index(end.encode(), i) if end else len(text)
+        h.update(text[i:j])
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
-    when the summary is missing or the kernel's sources changed since."""
+    when the summary is missing or the kernel's source changed since."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
-    h = hashlib.sha256()
-    for f in src_files:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
-    sha = h.hexdigest()[:16]
+    sha = kernel_digest(kernel)
     for line in open(path):
         m = re.match(r"\s*(\S+)\s+(\S+)\s+(\d+)\s+sha=(\w+)", line)
         if m and m.group(1) == kernel and m.group(4) == sha:
@@ -207,14 +216,18 @@ CSRC = "paper_1208_4869_gb300/csrc/"
 
 
 def kernel_sources(tag):
-    """Source files whose change invalidates the recorded traffic of a kernel."""
+    """(file, start marker, end marker) of the source whose change invalidates
+    the recorded traffic of a kernel: the kernel's own section, and the shared
+    device helpers."""
     if tag.startswith("cgemm_rows"):
-        files = ["blockmv.cuh"]
+        own = [(CSRC + "blockmv.cuh", "template <class R> struct GemmTile;", "// Column-major user block")]
     elif tag.startswith("dipole"):
-        files = ["fft.cuh", "dipole.cu"]
+        own = [(CSRC + "fft.cuh", None, None), (CSRC + "dipole.cu", None, None)]
+    elif tag.startswith("gemv_n_rows"):
+        own = [(CSRC + "gemv.cuh", "// y[i] = (A x)_i with S warps per row", "// Column-tiled sweep.")]
     else:
-        files = ["gemv.cuh"]
-    return [CSRC + f for f in files + ["common.cuh"]]
+        own = [(CSRC + "gemv.cuh", "// Column-tiled sweep.", None)]
+    return own + [(CSRC + "common.cuh", None, None)]
 
 
 def roofline(ccg, sweep_stats, n, dipole=False, nrhs=1):
@@ -237,7 +250,7 @@ def roofline(ccg, sweep_stats, n, dipole=False, nrhs=1):
     top = max(kinds, key=lambda k: kinds[k]["total_ms"])
     k = kinds[top]
     hbm, hbm_src = peaks()
-    traffic = profiled_traffic(top, kernel_sources(top))
+    traffic = profiled_traffic(top)
     if top.endswith("c128") and not dipole:   # FP64 FMA pipe bound (4 DFMA per 16-byte element)
         roof = {"kernel": top, "bound": "alu", "achieved": k["tflops"], "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": k["tflops"] / FP64_PEAK_TFLOPS,

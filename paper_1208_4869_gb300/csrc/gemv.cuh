@@ -204,12 +204,28 @@ __device__ __forceinline__ void gemv_tile_body(const cx<R>* __restrict__ A, int6
       s = warp_csum(s);
       if (lane == 0) P1[(int64_t)blockIdx.x * n + r] = s;
     }
+  } else if constexpr (sizeof(R) == 8) {
+    // A^H x2 alone, complex128: bound by the FP64 pipe, one row per iteration
+    for (int64_t r = r0 + warp; r < r1; r += kWarps) {
+      const L* a = reinterpret_cast<const L*>(A + r * lda);
+      L av[E];
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        const int64_t u = unit0 + lane + 32 * j;
+        av[j] = u < nunits ? ld_stream(a + u) : Un::zero();
+      }
+      const cx<R> xr = x2[r];
+#pragma unroll
+      for (int j = 0; j < E; ++j)
+#pragma unroll
+        for (int c = 0; c < U; ++c) acc[j][c] = cfma_conj(Un::get(av[j], c), xr, acc[j][c]);
+    }
   } else {
-    // A^H x2 alone: the warp's rows r0 + warp + kWarps t take their x2 values
-    // 32 at a time in one coalesced load, passed out by shuffles, and two
-    // rows are streamed per iteration (2 E loads per lane in flight): 0.115
-    // -> 0.109 ms at n = 8192 complex64.  (With Y1 the extra registers
-    // would cut the resident blocks and cost more than they save.)
+    // A^H x2 alone, complex64: the warp's rows r0 + warp + kWarps t take their
+    // x2 values 32 at a time in one coalesced load, passed out by shuffles,
+    // and two rows are streamed per iteration (2 E loads per lane in flight):
+    // 0.115 -> 0.097 ms at n = 8192.  (With Y1 the extra registers would cut
+    // the resident blocks and cost more than they save.)
     const int64_t rw = r0 + warp;
     const int64_t nrw = rw < r1 ? (r1 - rw + kWarps - 1) / kWarps : 0;
     for (int64_t t0 = 0; t0 < nrw; t0 += 32) {
@@ -275,8 +291,8 @@ __device__ __forceinline__ void gemv_tile_body(const cx<R>* __restrict__ A, int6
 }
 
 // Entry points: with Y1 (A x1, optionally with A^H x2) the compiler's own
-// register choice keeps 4 blocks per SM at complex64; A^H x alone is held to
-// 3 (complex64) / 2 (complex128) blocks per SM for its two-row loop.
+// register choice keeps 4 blocks per SM at complex64; A^H x alone in
+// complex64 is held to 3 blocks per SM.
 template <class R, int U, int E, bool Y1, bool Y2>
 __global__ void __launch_bounds__(kBlock) gemv_tile(const cx<R>* __restrict__ A, int64_t lda, int64_t n,
                                                     int64_t rows_per_range, const cx<R>* __restrict__ x1,
@@ -287,7 +303,7 @@ __global__ void __launch_bounds__(kBlock) gemv_tile(const cx<R>* __restrict__ A,
   gemv_tile_body<R, U, E, Y1, Y2>(A, lda, n, rows_per_range, x1, x2, P1, P2, st, skip_rec);
 }
 template <class R, int U, int E>
-__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 3 : 1)
     gemv_tile_h(const cx<R>* __restrict__ A, int64_t lda, int64_t n, int64_t rows_per_range,
                 const cx<R>* __restrict__ x2, cx<R>* __restrict__ P2, const SolveState* __restrict__ st,
                 int* skip_rec = nullptr) {
