@@ -60,6 +60,8 @@ def parse_args(argv=None):
     p.add_argument("--inner-maxit", type=int, default=None)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--fp64-tc", type=int, choices=[0, 1], default=1,
+                   help="complex128 block products on the tensor cores (integer digit slices)")
     a = p.parse_args(argv)
     dense = a.workload != "dipole"
     if a.methods is None:
@@ -182,6 +184,17 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def bf16_peak():
+    """Sustained bf16 tensor peak (the block products run inside seconds-long
+    solves under the power cap)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["bf16_tflops_sustained"]), "measured sustained"
+    except (OSError, KeyError, ValueError):
+        return 1700.0, "fallback sustained"
+
+
 def kernel_digest(tag):
     """sha256[:16] of the source text of the kernel behind a sweep tag (its
     section of the source file) and of the shared device helpers."""
@@ -209,7 +222,12 @@ def profiled_traffic(kernel):
     return None
 
 
-SWEEP_KERNELS = {0: ("gemv_n_rows", 1), 1: ("gemv_tile_c", 1), 2: ("gemv_tile_both", 2), 3: ("cgemm_rows", 1)}
+SWEEP_KERNELS = {0: ("gemv_n_rows", 1), 1: ("gemv_tile_c", 1), 2: ("gemv_tile_both", 2), 3: ("cgemm_rows", 1),
+                 4: ("tc_block", 1)}
+TC_KERNELS = {"c64": "gemm_bf16_split", "c128": "ozaki_gemm"}
+# bf16 MMAs per real product term: digit pairs of the complex128 integer-slice
+# scheme (8 levels, 36 pairs) and term pairs of the two-term complex64 split
+TC_PRODUCTS = {"c64": 3, "c128": 36}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flops x max SM clock
 DIPOLE_KERNELS = {0: ("dipole_fft_matvec", 1), 1: ("dipole_fft_matvec_h", 1), 2: ("dipole_fft_both", 2)}
 CSRC = "paper_1208_4869_gb300/csrc/"
@@ -221,6 +239,10 @@ def kernel_sources(tag):
     device helpers."""
     if tag.startswith("cgemm_rows"):
         own = [(CSRC + "blockmv.cuh", "template <class R> struct GemmTile;", "// Column-major user block")]
+    elif tag.startswith("ozaki_gemm"):
+        own = [(CSRC + "tc_ozaki.cu", None, None), (CSRC + "tcgen05.cuh", None, None)]
+    elif tag.startswith("gemm_bf16_split"):
+        own = [(CSRC + "tc_gemm.cu", None, None), (CSRC + "tcgen05.cuh", None, None)]
     elif tag.startswith("dipole"):
         own = [(CSRC + "fft.cuh", None, None), (CSRC + "dipole.cu", None, None)]
     elif tag.startswith("gemv_n_rows"):
@@ -239,19 +261,31 @@ def roofline(ccg, sweep_stats, n, dipole=False, nrhs=1):
     for (dt, kind), (cnt, ms, nbytes) in sweep_stats.items():
         if cnt:
             name, products = (DIPOLE_KERNELS if dipole else SWEEP_KERNELS)[kind]
-            tag = "%s_%s" % (name, "c128" if dt == ccg.C128 else "c64")
+            prec = "c128" if dt == ccg.C128 else "c64"
+            if kind == 4:
+                name = TC_KERNELS[prec]
+            tag = "%s_%s" % (name, prec)
             avg = ms / cnt
-            cols = nrhs if kind == 3 else 1
+            cols = nrhs if kind in (3, 4) else 1
             kinds[tag] = {"launches": cnt, "total_ms": ms, "avg_ms": avg,
                           "tflops": None if dipole else 8.0 * products * n * n * cols / (avg * 1e-3) / 1e12,
                           "gbs": nbytes / (avg * 1e-3) / 1e9, "bytes": nbytes}
+            if kind == 4:   # bf16 tensor work actually issued
+                kinds[tag]["tensor_tflops"] = kinds[tag]["tflops"] * TC_PRODUCTS[prec]
     if not kinds:
         return None
     top = max(kinds, key=lambda k: kinds[k]["total_ms"])
     k = kinds[top]
     hbm, hbm_src = peaks()
     traffic = profiled_traffic(top)
-    if top.endswith("c128") and not dipole:   # FP64 FMA pipe bound (4 DFMA per 16-byte element)
+    if top.startswith("ozaki_gemm") or top.startswith("gemm_bf16_split"):   # bf16 tensor cores
+        bf, bf_src = bf16_peak()
+        roof = {"kernel": top, "bound": "tensor", "achieved": k["tensor_tflops"], "peak": bf,
+                "unit": "TFLOP/s", "frac": k["tensor_tflops"] / bf,
+                "peak_source": "%s bf16 (cuBLAS)" % bf_src,
+                "fp64_equivalent_tflops" if top.endswith("c128") else "c64_equivalent_tflops": k["tflops"],
+                "products_per_term": TC_PRODUCTS[top.rsplit("_", 1)[1]]}
+    elif top.endswith("c128") and not dipole:   # FP64 FMA pipe bound (4 DFMA per 16-byte element)
         roof = {"kernel": top, "bound": "alu", "achieved": k["tflops"], "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": k["tflops"] / FP64_PEAK_TFLOPS,
                 "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (no measured FP64 peak)"}
@@ -426,7 +460,7 @@ def timed_region(h, ccg, torch, stream, step, steps, world, dev, clocks=None):
     clk = clocks.stop() if clocks else None
     barrier(world)
     stats = {(dt, k): h.timing(kind=k, dtype=dt) for dt in (ccg.C128, ccg.C64)
-             for k in (ccg.SWEEP_N, ccg.SWEEP_C, ccg.SWEEP_BOTH, ccg.SWEEP_BLOCK)}
+             for k in (ccg.SWEEP_N, ccg.SWEEP_C, ccg.SWEEP_BOTH, ccg.SWEEP_BLOCK, ccg.SWEEP_BLOCK_TC)}
     h.timing(enable=False)
     return e0.elapsed_time(e1), lat, results, stats, h.launch_count() - launches0, clk
 
@@ -450,6 +484,7 @@ def run_ours(args):
     headline = "mixed" if args.path == "auto" else args.path
     stream = torch.cuda.current_stream(dev)
     h = ccg.Handle(stream)
+    h.set_option(ccg.OPT_TC_FP64, args.fp64_tc)
     dipole = args.workload == "dipole"
     if dipole:
         occ = W.sphere_occupancy(args.L)
@@ -615,7 +650,8 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": workload, "n": n, "methods": methods, "tol": args.tol, "path": headline,
                        "inner_tol": args.inner_tol if headline == "mixed" else None,
-                       "parallelism": "replicas" if world > 1 else "single", "l2": l2},
+                       "parallelism": "replicas" if world > 1 else "single", "l2": l2,
+                       "fp64_tensor_cores": bool(args.fp64_tc) if batched else None},
             "iters": {m: [it, inner] for m, _, it, inner, _ in results[: len(methods)]},
             "all_converged": ok,
             "latency_ms": {"p50": 1e3 * statistics.median(lat_sorted),

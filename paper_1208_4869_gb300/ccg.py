@@ -28,7 +28,8 @@ OPT_TENSOR_CORES = 1
 OPT_TC_SPLIT = 2
 OPT_GMRES_RESTART = 3
 OPT_BICGSTAB_L = 4
-SWEEP_N, SWEEP_C, SWEEP_BOTH, SWEEP_BLOCK = 0, 1, 2, 3
+OPT_TC_FP64 = 5
+SWEEP_N, SWEEP_C, SWEEP_BOTH, SWEEP_BLOCK, SWEEP_BLOCK_TC = 0, 1, 2, 3, 4
 
 _lib = None
 

@@ -158,6 +158,7 @@ ccg_status ccg_destroy(ccg_handle* h) {
   cudaStreamSynchronize(h->stream);
   if (h->arena) cudaFree(h->arena);
   if (h->tc_buf) cudaFree(h->tc_buf);
+  if (h->oz_buf) cudaFree(h->oz_buf);
   if (h->pinned) cudaFreeHost(h->pinned);
   if (h->skip_rec) cudaFree(h->skip_rec);
   for (int i = 0; i < 2; ++i)
@@ -247,6 +248,7 @@ ccg_status ccg_op_destroy(ccg_operator* op) {
     dipole_free(op);
   }
   if (op && op->tc_ready) tc_free(op);  // stream-ordered after the operator's last use
+  if (op && op->oz_a) oz_free(op);
   delete op;
   return CCG_OK;
 }
@@ -363,6 +365,10 @@ ccg_status ccg_set_option(ccg_handle* h, int option, int value) {
   if (!h) { set_error("ccg_set_option: NULL handle"); return CCG_ERR_INVALID; }
   if (option == CCG_OPT_TENSOR_CORES && value >= 0 && value <= 2) {
     h->tc_mode = value;
+    return CCG_OK;
+  }
+  if (option == CCG_OPT_TC_FP64 && (value == 0 || value == 1)) {
+    h->tc_fp64 = value;
     return CCG_OK;
   }
   if (option == CCG_OPT_TC_SPLIT && (value == 2 || value == 3)) {

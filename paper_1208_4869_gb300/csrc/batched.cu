@@ -489,13 +489,20 @@ template <class R> struct BRun {
     bphase_kernel<P><<<grid, kBlock, 0, s>>>(p, w.ctl, w.cols, red);
     ++h->launches;
   }
-  // C = A B; complex64 products go to the tensor cores when enabled.
+  // C = A B; complex64 products go to the tensor cores when enabled, and
+  // complex128 ones to the FP64-accurate integer-slice product.
   int gemm(const cx<R>* B, cx<R>* C, const int* skip) {
     timing_begin(h);
-    if constexpr (sizeof(R) == 4) {
+    if constexpr (sizeof(R) == 8) {
+      if (h->tc_fp64 && oz_available(op)) {
+        const int rc = oz_block_product(h, op, B, C, k, skip);
+        timing_end(h, CCG_C128, CCG_SWEEP_BLOCK_TC, (double)n * n * 16.0 + 2.0 * n * k * sizeof(cx<R>));
+        return rc;
+      }
+    } else {
       if (allow_tc && tc_available(op)) {
         const int rc = tc_block_product(h, op, B, C, k, skip);
-        timing_end(h, CCG_C64, CCG_SWEEP_BLOCK, (double)n * n * 8.0 + 2.0 * n * k * sizeof(cx<R>));
+        timing_end(h, CCG_C64, CCG_SWEEP_BLOCK_TC, (double)n * n * 8.0 + 2.0 * n * k * sizeof(cx<R>));
         return rc;
       }
     }
@@ -627,6 +634,7 @@ static int batched_t(ccg_handle* h, const ccg_operator* op, int64_t k, const voi
   B_CUDA(cudaStreamSynchronize(h->stream));
   timing_collect(h);
   if ((rc = tc_check_error(h)) != CCG_OK) return rc;
+  if ((rc = oz_check_error(h)) != CCG_OK) return rc;
   return worst_status(st);
 }
 
@@ -656,7 +664,8 @@ static int block_matvec_t(ccg_handle* h, const ccg_operator* op, int64_t k, cons
   h->launches += 2;
   B_CUDA(cudaStreamSynchronize(h->stream));
   timing_collect(h);
-  return tc_check_error(h);
+  if ((rc = tc_check_error(h)) != CCG_OK) return rc;
+  return oz_check_error(h);
 }
 
 int block_matvec(ccg_handle* h, const ccg_operator* op, int64_t k, const void* X, int64_t ldx, void* Y, int64_t ldy) {
@@ -783,6 +792,7 @@ int solve_batched_refined(ccg_handle* h, const ccg_operator* op, const ccg_opera
   if (inner_out) std::memcpy(inner_out, inner_total.data(), kk * sizeof(int));
   timing_collect(h);
   if ((rc = tc_check_error(h)) != CCG_OK) return rc;
+  if ((rc = oz_check_error(h)) != CCG_OK) return rc;
   return worst_status(st);
 }
 
