@@ -255,12 +255,12 @@ __global__ void __launch_bounds__(kBlock) oz_slice_rows(const double2* __restric
   for (int w = 0; w < kWarps; ++w) m = fmax(m, red[w]);
   const int ex = exp_above(m);
   if (threadIdx.x == 0) e[i] = ex;
-  const double scale = ldexp(1.0, 7 - (ex >= kNonFinite ? 0 : ex));
+  const int sh = 7 - (ex >= kNonFinite ? 0 : ex);  // applied by ldexp: 2^sh alone may overflow
   const int64_t cnt = n * 2 * n;
   for (int64_t j = threadIdx.x; j < 2 * n; j += kBlock) {
     const double2 z = a[j >> 1];
     __nv_bfloat16 d[S];
-    digits(((j & 1) ? z.y : z.x) * scale, d);
+    digits(ldexp((j & 1) ? z.y : z.x, sh), d);
 #pragma unroll
     for (int t = 0; t < S; ++t) out[t * cnt + i * 2 * n + j] = d[t];
   }
@@ -309,10 +309,10 @@ __global__ void oz_slice_block(const double2* __restrict__ X, int64_t n, int k, 
     const int64_t j = j0 + tx;
     if (c < k && j < n) {
       const double2 z = tile[tx][r];
-      const double scale = ldexp(1.0, 7 - (f[c] >= kNonFinite ? 0 : f[c]));
+      const int sh = 7 - (f[c] >= kNonFinite ? 0 : f[c]);
       __nv_bfloat16 dre[S], dim[S];
-      digits(z.x * scale, dre);
-      digits(z.y * scale, dim);
+      digits(ldexp(z.x, sh), dre);
+      digits(ldexp(z.y, sh), dim);
       const int64_t e0 = (int64_t)(2 * c) * (2 * n) + 2 * j;  // row 2c
       const int64_t e1 = e0 + 2 * n;                          // row 2c + 1
 #pragma unroll

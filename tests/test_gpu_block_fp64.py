@@ -84,6 +84,7 @@ def check_sampled(A, X, Y, entries, typical=True):
 def sample(n, k, count, seed):
     rng = np.random.default_rng(seed)
     pts = {(0, 0), (n - 1, k - 1), (n - 1, 0), (0, k - 1)}
+    count = min(count, n * k)
     while len(pts) < count:
         pts.add((int(rng.integers(n)), int(rng.integers(k))))
     return sorted(pts)
@@ -116,6 +117,12 @@ def test_fp64_tc_scales(ccg):
     X = X * np.ldexp(1.0, rng.integers(-300, 300, k))[None, :]
     Y = product(ccg, A, X)
     check_sampled(A, X, Y, sample(n, k, 32, 3))
+    # rows of subnormal magnitude (row exponents near -1030)
+    A2 = A.copy()
+    A2[:4] = A[:4] / np.abs(A[:4]).max(1)[:, None] * 1e-310
+    X2 = W.dense_rhs_block(n, k, seed=8)
+    Y2 = product(ccg, A2, X2)
+    check_sampled(A2, X2, Y2, [(i, c) for i in range(4) for c in (0, k - 1)], typical=False)
 
 
 def test_fp64_tc_adversarial_digits(ccg):
