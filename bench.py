@@ -60,8 +60,8 @@ def parse_args(argv=None):
     p.add_argument("--inner-maxit", type=int, default=None)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--fp64-tc", type=int, choices=[0, 1], default=1,
-                   help="complex128 block products on the tensor cores (integer digit slices)")
+    p.add_argument("--tc-exact", type=int, choices=[0, 1], default=1,
+                   help="exact block products on the tensor cores (integer digit slices)")
     a = p.parse_args(argv)
     dense = a.workload != "dipole"
     if a.methods is None:
@@ -223,11 +223,11 @@ def profiled_traffic(kernel):
 
 
 SWEEP_KERNELS = {0: ("gemv_n_rows", 1), 1: ("gemv_tile_c", 1), 2: ("gemv_tile_both", 2), 3: ("cgemm_rows", 1),
-                 4: ("tc_block", 1)}
-TC_KERNELS = {"c64": "gemm_bf16_split", "c128": "ozaki_gemm"}
-# bf16 MMAs per real product term: digit pairs of the complex128 integer-slice
-# scheme (8 levels, 36 pairs) and term pairs of the two-term complex64 split
-TC_PRODUCTS = {"c64": 3, "c128": 36}
+                 4: ("gemm_bf16_split", 1), 5: ("ozaki_gemm", 1)}
+# bf16 MMA work per real product term: term pairs of the two-term complex64
+# split (3), digit pairs of the integer-slice scheme (36 for complex128's 8
+# digits, 10 for complex64's 4)
+TC_PRODUCTS = {("gemm_bf16_split", "c64"): 3, ("ozaki_gemm", "c128"): 36, ("ozaki_gemm", "c64"): 10}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flops x max SM clock
 DIPOLE_KERNELS = {0: ("dipole_fft_matvec", 1), 1: ("dipole_fft_matvec_h", 1), 2: ("dipole_fft_both", 2)}
 CSRC = "paper_1208_4869_gb300/csrc/"
@@ -262,16 +262,14 @@ def roofline(ccg, sweep_stats, n, dipole=False, nrhs=1):
         if cnt:
             name, products = (DIPOLE_KERNELS if dipole else SWEEP_KERNELS)[kind]
             prec = "c128" if dt == ccg.C128 else "c64"
-            if kind == 4:
-                name = TC_KERNELS[prec]
             tag = "%s_%s" % (name, prec)
             avg = ms / cnt
-            cols = nrhs if kind in (3, 4) else 1
+            cols = nrhs if kind >= 3 else 1
             kinds[tag] = {"launches": cnt, "total_ms": ms, "avg_ms": avg,
                           "tflops": None if dipole else 8.0 * products * n * n * cols / (avg * 1e-3) / 1e12,
                           "gbs": nbytes / (avg * 1e-3) / 1e9, "bytes": nbytes}
-            if kind == 4:   # bf16 tensor work actually issued
-                kinds[tag]["tensor_tflops"] = kinds[tag]["tflops"] * TC_PRODUCTS[prec]
+            if kind >= 4:   # bf16 tensor work actually issued
+                kinds[tag]["tensor_tflops"] = kinds[tag]["tflops"] * TC_PRODUCTS[(name, prec)]
     if not kinds:
         return None
     top = max(kinds, key=lambda k: kinds[k]["total_ms"])
@@ -284,7 +282,7 @@ def roofline(ccg, sweep_stats, n, dipole=False, nrhs=1):
                 "unit": "TFLOP/s", "frac": k["tensor_tflops"] / bf,
                 "peak_source": "%s bf16 (cuBLAS)" % bf_src,
                 "fp64_equivalent_tflops" if top.endswith("c128") else "c64_equivalent_tflops": k["tflops"],
-                "products_per_term": TC_PRODUCTS[top.rsplit("_", 1)[1]]}
+                "products_per_term": TC_PRODUCTS[tuple(top.rsplit("_", 1))]}
     elif top.endswith("c128") and not dipole:   # FP64 FMA pipe bound (4 DFMA per 16-byte element)
         roof = {"kernel": top, "bound": "alu", "achieved": k["tflops"], "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": k["tflops"] / FP64_PEAK_TFLOPS,
@@ -460,7 +458,8 @@ def timed_region(h, ccg, torch, stream, step, steps, world, dev, clocks=None):
     clk = clocks.stop() if clocks else None
     barrier(world)
     stats = {(dt, k): h.timing(kind=k, dtype=dt) for dt in (ccg.C128, ccg.C64)
-             for k in (ccg.SWEEP_N, ccg.SWEEP_C, ccg.SWEEP_BOTH, ccg.SWEEP_BLOCK, ccg.SWEEP_BLOCK_TC)}
+             for k in (ccg.SWEEP_N, ccg.SWEEP_C, ccg.SWEEP_BOTH, ccg.SWEEP_BLOCK, ccg.SWEEP_BLOCK_TC,
+                       ccg.SWEEP_BLOCK_EXACT)}
     h.timing(enable=False)
     return e0.elapsed_time(e1), lat, results, stats, h.launch_count() - launches0, clk
 
@@ -484,7 +483,7 @@ def run_ours(args):
     headline = "mixed" if args.path == "auto" else args.path
     stream = torch.cuda.current_stream(dev)
     h = ccg.Handle(stream)
-    h.set_option(ccg.OPT_TC_FP64, args.fp64_tc)
+    h.set_option(ccg.OPT_TC_EXACT, args.tc_exact)
     dipole = args.workload == "dipole"
     if dipole:
         occ = W.sphere_occupancy(args.L)
@@ -651,7 +650,7 @@ def run_ours(args):
             "config": {"workload": workload, "n": n, "methods": methods, "tol": args.tol, "path": headline,
                        "inner_tol": args.inner_tol if headline == "mixed" else None,
                        "parallelism": "replicas" if world > 1 else "single", "l2": l2,
-                       "fp64_tensor_cores": bool(args.fp64_tc) if batched else None},
+                       "exact_tensor_core_products": bool(args.tc_exact) if batched else None},
             "iters": {m: [it, inner] for m, _, it, inner, _ in results[: len(methods)]},
             "all_converged": ok,
             "latency_ms": {"p50": 1e3 * statistics.median(lat_sorted),

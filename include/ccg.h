@@ -247,11 +247,12 @@ ccg_status ccg_solve_batched_refined(ccg_handle* h, ccg_method inner_method, con
  * 256; dense operators only.  complex64 products run on the tensor cores
  * (split-bf16 operands, fp32 accumulation; see CCG_OPT_TC_SPLIT) unless
  * disabled with ccg_set_option(h, CCG_OPT_TENSOR_CORES, 0); complex128
- * products run on the tensor cores too, as exact integer products of 8
- * seven-bit digit slices per entry (FP64-accurate; see CCG_OPT_TC_FP64),
- * for n divisible by 4 and n <= 32768; other products use CUDA cores.
- * Synchronises the stream; returns CCG_ERR_TIMEOUT if a bounded wait of a
- * tensor-core pipeline gave up. */
+ * products, and complex64 ones with that option off, run on the tensor
+ * cores as exact integer products of seven-bit digit slices
+ * (CCG_OPT_TC_EXACT: FP64-accurate for complex128, FP32-accurate for
+ * complex64) for n divisible by 4 and n <= 32768; other products use CUDA
+ * cores.  Synchronises the stream; returns CCG_ERR_TIMEOUT if a bounded wait
+ * of a tensor-core pipeline gave up. */
 ccg_status ccg_block_matvec(ccg_handle* h, const ccg_operator* op, int64_t nrhs, const void* X, int64_t ldx, void* Y,
                             int64_t ldy);
 
@@ -268,19 +269,23 @@ ccg_status ccg_block_matvec(ccg_handle* h, const ccg_operator* op, int64_t nrhs,
  * CCG_OPT_GMRES_RESTART: the cycle length m of CCG_GMRES, 1..64 (default
  * 30); the solve holds m + 1 basis vectors in the handle's workspace.
  * CCG_OPT_BICGSTAB_L: the degree l of CCG_BICGSTABL, 1..4 (default 2).
- * CCG_OPT_TC_FP64: 1 (default) runs complex128 block products (batched
- * complex128 solves, the complex128 residuals of refined batched solves,
- * ccg_block_matvec) on the tensor cores by the integer-slice scheme: each
- * row of A and column of X is scaled by a power of two and cut into 8
- * signed 7-bit digits, the digit pairs of 8 significance levels are summed
- * exactly by bf16 MMAs with fp32 accumulation and combined in int64 -- the
- * result is as accurate as an FP64 GEMM (error ~ K 2^-53 max|a| max|x| per
- * entry).  0 uses FP64 CUDA cores. */
+ * CCG_OPT_TC_EXACT: 1 (default) runs the block products that must be
+ * accurate in their own precision -- every complex128 one (batched
+ * complex128 solves, the residuals of refined batched solves,
+ * ccg_block_matvec) and the complex64 ones that do not take the split-bf16
+ * path (the exact complex64 residuals of refined batched solves, plain
+ * complex64 batched solves) -- on the tensor cores by the integer-slice
+ * scheme: each row of A and column of X is scaled by a power of two and cut
+ * into S signed 7-bit digits (S = 8 for complex128, 4 for complex64), the
+ * digit pairs of S significance levels are summed exactly by bf16 MMAs with
+ * fp32 accumulation and combined in int64.  The result is as accurate as a
+ * GEMM in the operands' precision (error ~ K 2^-53, resp. K 2^-24, times
+ * max|a| max|x| per entry).  0 uses CUDA cores for them. */
 #define CCG_OPT_TENSOR_CORES 1
 #define CCG_OPT_TC_SPLIT 2
 #define CCG_OPT_GMRES_RESTART 3
 #define CCG_OPT_BICGSTAB_L 4
-#define CCG_OPT_TC_FP64 5
+#define CCG_OPT_TC_EXACT 5
 ccg_status ccg_set_option(ccg_handle* h, int option, int value);
 
 /* ---------------------------------------------------------------------------
@@ -352,9 +357,10 @@ typedef enum {
   CCG_SWEEP_C = 1,    /* y = A^H x                        */
   CCG_SWEEP_BOTH = 2, /* A p and A^H q from one read of A */
   CCG_SWEEP_BLOCK = 3, /* A X for a block of right-hand sides (CUDA cores) */
-  CCG_SWEEP_BLOCK_TC = 4, /* A X for a block on the tensor cores (complex64:
-                             split bf16; complex128: integer digit slices) */
-  CCG_SWEEP_KINDS = 5
+  CCG_SWEEP_BLOCK_TC = 4, /* A X for a block on the tensor cores, split bf16 */
+  CCG_SWEEP_BLOCK_EXACT = 5, /* A X for a block on the tensor cores, exact
+                                integer digit slices */
+  CCG_SWEEP_KINDS = 6
 } ccg_sweep_kind;
 
 /* Per-kernel timing of the operator sweeps: when enabled, each sweep that a

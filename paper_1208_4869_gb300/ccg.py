@@ -28,8 +28,8 @@ OPT_TENSOR_CORES = 1
 OPT_TC_SPLIT = 2
 OPT_GMRES_RESTART = 3
 OPT_BICGSTAB_L = 4
-OPT_TC_FP64 = 5
-SWEEP_N, SWEEP_C, SWEEP_BOTH, SWEEP_BLOCK, SWEEP_BLOCK_TC = 0, 1, 2, 3, 4
+OPT_TC_EXACT = 5
+SWEEP_N, SWEEP_C, SWEEP_BOTH, SWEEP_BLOCK, SWEEP_BLOCK_TC, SWEEP_BLOCK_EXACT = 0, 1, 2, 3, 4, 5
 
 _lib = None
 

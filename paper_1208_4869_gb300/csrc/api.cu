@@ -367,8 +367,8 @@ ccg_status ccg_set_option(ccg_handle* h, int option, int value) {
     h->tc_mode = value;
     return CCG_OK;
   }
-  if (option == CCG_OPT_TC_FP64 && (value == 0 || value == 1)) {
-    h->tc_fp64 = value;
+  if (option == CCG_OPT_TC_EXACT && (value == 0 || value == 1)) {
+    h->tc_exact = value;
     return CCG_OK;
   }
   if (option == CCG_OPT_TC_SPLIT && (value == 2 || value == 3)) {

@@ -489,22 +489,24 @@ template <class R> struct BRun {
     bphase_kernel<P><<<grid, kBlock, 0, s>>>(p, w.ctl, w.cols, red);
     ++h->launches;
   }
-  // C = A B; complex64 products go to the tensor cores when enabled, and
-  // complex128 ones to the FP64-accurate integer-slice product.
+  // C = A B.  complex64 products go to the split-bf16 tensor-core product
+  // when allowed (fast, ~1e-4 accurate); otherwise both precisions go to the
+  // exact integer-slice product (as accurate as a GEMM in their own
+  // precision) when enabled, else to the CUDA cores.
   int gemm(const cx<R>* B, cx<R>* C, const int* skip) {
     timing_begin(h);
-    if constexpr (sizeof(R) == 8) {
-      if (h->tc_fp64 && oz_available(op)) {
-        const int rc = oz_block_product(h, op, B, C, k, skip);
-        timing_end(h, CCG_C128, CCG_SWEEP_BLOCK_TC, (double)n * n * 16.0 + 2.0 * n * k * sizeof(cx<R>));
-        return rc;
-      }
-    } else {
+    const int dt = sizeof(R) == 8 ? CCG_C128 : CCG_C64;
+    if constexpr (sizeof(R) == 4) {
       if (allow_tc && tc_available(op)) {
         const int rc = tc_block_product(h, op, B, C, k, skip);
         timing_end(h, CCG_C64, CCG_SWEEP_BLOCK_TC, (double)n * n * 8.0 + 2.0 * n * k * sizeof(cx<R>));
         return rc;
       }
+    }
+    if (h->tc_exact && oz_available(op)) {
+      const int rc = oz_block_product(h, op, B, C, k, skip);
+      timing_end(h, dt, CCG_SWEEP_BLOCK_EXACT, (double)n * n * sizeof(cx<R>) + 2.0 * n * k * sizeof(cx<R>));
+      return rc;
     }
     dim3 g((k + gemm_bn<R>() - 1) / gemm_bn<R>(), (unsigned)((n + gemm_bm<R>() - 1) / gemm_bm<R>()));
     cgemm_rows<R><<<g, kBlock, 0, s>>>(static_cast<const cx<R>*>(op->A), op->lda, B, C, n, k, skip, timing_rec(h));
@@ -749,12 +751,13 @@ int solve_batched_refined(ccg_handle* h, const ccg_operator* op, const ccg_opera
     B_CUDA(cudaMemcpyAsync(&all, &ro.w.ctl->all_done, sizeof(int), cudaMemcpyDeviceToHost, s));
     B_CUDA(cudaStreamSynchronize(s));
     if (all) break;
-    // Correction D32 for A D = R32.  Tensor-core products are ~1e-4
-    // accurate at this size (their fp32 accumulation), so a tensor-core solve
-    // is followed by one exact complex64 residual R32 - A D32 on CUDA cores
-    // and a second tensor-core solve of it: the correction is then as good as
-    // an all-CUDA-core inner solve, with one CUDA-core product instead of
-    // one per iteration.
+    // Correction D32 for A D = R32.  Split-bf16 tensor-core products are
+    // ~1e-4 accurate at this size (their fp32 accumulation), so a
+    // tensor-core solve is followed by one complex64 residual R32 - A D32
+    // accurate to FP32 (the integer-slice tensor-core product, or CUDA
+    // cores) and a second split-bf16 solve of it: the correction is then as
+    // good as an inner solve with FP32-accurate products, with one such
+    // product instead of one per iteration.
     const bool tc_inner = ri.allow_tc && tc_available(op_in);
     const int mid_steps = tc_inner ? 2 : 1;
     for (int mid = 0; mid < mid_steps; ++mid) {
@@ -770,7 +773,7 @@ int solve_batched_refined(ccg_handle* h, const ccg_operator* op, const ccg_opera
         ro.phase(a);
       }
       if (mid + 1 < mid_steps) {
-        ri.allow_tc = false;           // the exact complex64 product
+        ri.allow_tc = false;           // the FP32-accurate complex64 product
         if ((rc = ri.gemm(D32, AD32, nullptr)) != CCG_OK) return rc;
         ri.allow_tc = true;
         BMidResid m;

@@ -48,9 +48,9 @@ struct ccg_operator {
   void* tc_ahi = nullptr;                      // the terms, one n x 2n bf16 matrix each
   cudaStream_t tc_stream = nullptr;            // stream they were allocated (and are freed) on
   alignas(64) unsigned char tc_map[3][128] = {};  // their TMA descriptors
-  // integer digit slices of a complex128 dense matrix for the FP64-accurate
-  // tensor-core product (made on first use): 8 n x 2n bf16 slices, then the
-  // row exponents
+  // integer digit slices of a dense matrix for the exact tensor-core product
+  // (made on first use): 8 (complex128) or 4 (complex64) n x 2n bf16
+  // slices, then the row exponents
   bool oz_ready = false;
   void* oz_a = nullptr;
   cudaStream_t oz_stream = nullptr;
@@ -87,10 +87,10 @@ struct ccg_handle {
   int bicgstab_l = 2;   // degree l of BiCGstab(l)
   void* tc_buf = nullptr;
   size_t tc_bytes = 0;
-  // FP64-accurate tensor-core products of complex128 blocks (integer digit
-  // slices): enabled flag, staging for the block's slices and the
-  // pipeline's error flag (first 256 bytes)
-  int tc_fp64 = 1;
+  // exact tensor-core block products (integer digit slices; FP64-accurate
+  // for complex128, FP32-accurate for complex64): enabled flag, staging for
+  // the block's slices and the pipeline's error flag (first 256 bytes)
+  int tc_exact = 1;
   void* oz_buf = nullptr;
   size_t oz_bytes = 0;
 };
@@ -135,6 +135,7 @@ int tc_check_error(ccg_handle* h);
 void tc_free(ccg_operator* op);
 bool oz_available(const ccg_operator* op);
 int oz_block_product(ccg_handle* h, const ccg_operator* op, const double2* X, double2* Y, int k, const int* skip);
+int oz_block_product(ccg_handle* h, const ccg_operator* op, const float2* X, float2* Y, int k, const int* skip);
 int oz_check_error(ccg_handle* h);
 void oz_free(ccg_operator* op);
 int block_matvec(ccg_handle* h, const ccg_operator* op, int64_t k, const void* X, int64_t ldx, void* Y, int64_t ldy);

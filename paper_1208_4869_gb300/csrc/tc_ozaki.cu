@@ -1,41 +1,47 @@
-// FP64-accurate block product for complex128 operators on the bf16 tensor
-// cores (an Ozaki-style scheme of exact integer slices): Y = A X for a block
-// of k right-hand sides, used for the complex128 residuals of the batched
-// refinement.
+// Exact-integer block products on the bf16 tensor cores (an Ozaki-style
+// scheme of digit slices): Y = A X for a block of k right-hand sides, as
+// accurate as a GEMM in the operands' own precision -- FP64 for complex128
+// (8 digits), FP32 for complex64 (4 digits).  Used for the complex128
+// residuals of the batched refinement, its exact complex64 residuals,
+// batched solves and ccg_block_matvec.
 //
 // With the complex product read as one real GEMM (Ah = A as a real n x 2n
 // matrix, Xh the 2n x 2k matrix with columns (re x_c, -im x_c) and
-// (im x_c, re x_c), as for the complex64 tensor-core product), every row i
-// of Ah is scaled by 2^-e_i and every column pair c of Xh by 2^-f_c so that
-// its entries lie in (-1, 1), and each scaled entry is cut into S = 8 signed
+// (im x_c, re x_c), as for the split-bf16 product), every row i of Ah is
+// scaled by 2^-e_i and every column pair c of Xh by 2^-f_c so that its
+// entries lie in (-1, 1), and each scaled entry is cut into S signed
 // digits:
 //     a = sum_t d_t 2^(-7(t+1)),  d_0 = rint(2^7 a) in [-128, 128],
 //     d_t (t >= 1) = rint of the remainder times 2^7, in [-64, 64],
 // all exact in double and exactly representable in bf16.  Then
 //     (Ah Xh)_ic = 2^(e_i + f_c) sum_l 2^(-7(l + 2)) L_l,
 //     L_l = sum over digit pairs t + u = l of D^A_t D^X_u   (integer GEMMs),
-// truncated at l = 7 (36 pairs; the dropped levels are below 2^-40 of
-// 2^(e_i + f_c) even with every product aligned).  The tensor cores form
-// each level's integer sum in an fp32 accumulator, exactly: a pair product
-// is at most 2^14 (2^13 with one leading digit, 2^12 with none), so a
-// level's products are at most 2.5 * 2^14 and over a chunk of K = 256 its
-// sum stays below 2^23.4 (fp32 represents every integer up to 2^24).  After each chunk the epilogue warps read the eight levels and
-// fold them, as exact integers, into two int64 accumulators per output,
+// truncated at l = S - 1 (S (S + 1) / 2 pairs: 36 for S = 8, whose dropped
+// levels are below 2^-54 of 2^(e_i + f_c) per term; 10 for S = 4, below
+// 2^-26).  The tensor cores form each level's integer sum in an fp32
+// accumulator, exactly: a pair product is at most 2^14 (2^13 with one
+// leading digit, 2^12 with none), so a level's products are at most
+// 2.5 * 2^14 (1.5 * 2^14 for S = 4), and over a chunk of K = 256 (K = 512)
+// its sum stays below 2^23.4 (2^23.6); fp32 represents every integer up to
+// 2^24.  After each chunk the epilogue warps read the levels and fold them,
+// as exact integers, into int64 accumulators per output,
 //     A = sum_{l<4} L_l 2^(7(3-l)),   B = sum_{l>=4} L_l 2^(7(7-l))
-// (below 2^51 for K <= 2^16), and at the end
+// (below 2^52 for K <= 2^16), and at the end
 //     (Ah Xh)_ic = 2^(e_i + f_c - 35) A + 2^(e_i + f_c - 63) B
-// with one rounding.  The only errors are that rounding and the dropped
-// levels: the product is as accurate as a double-precision GEMM.
+// with one rounding (a second one to float for complex64).  The only other
+// errors are the dropped levels and digit remainders.
 //
-// Kernel: one CTA per 128 x 32 output tile, 6 warps.  Lane 0 of warp 0
-// feeds a 2-stage ring (8 digit tiles of A, 128 x 32 bf16, and 8 of X,
-// 32 x 32; 64-byte swizzle) with cp.async.bulk.tensor; lane 0 of warp 1
-// issues the 36 tcgen05.mma of every K = 16 step into the level
-// accumulators of one of two tensor-memory buffers (8 levels x 32 columns
-// each, 512 columns in all), commits each stage and each chunk; warps 2-5
-// read a finished chunk's buffer while the next chunk accumulates into the
-// other.  Every mbarrier wait is bounded (tcgen05.cuh) and tensor memory is
-// always freed.
+// Kernel: one CTA per 128 x BN output tile (BN = 32 for S = 8, 64 for
+// S = 4), 6 warps.  Lane 0 of warp 0 feeds a ring of stages (S digit tiles
+// of A, 128 x 32 bf16, and S of X, BN x 32; 64-byte swizzle) with
+// cp.async.bulk.tensor; lane 0 of warp 1 issues S tcgen05.mma per K = 16
+// step -- A digit t against the X digits 0 .. S - 1 - t stacked along N
+// (N = (S - t) BN), into the level accumulators from level t on -- in one
+// of two tensor-memory buffers (S levels x BN columns each, 512 columns in
+// all), commits each stage and each chunk, so each A digit tile is read
+// from shared memory once per step; warps 2-5 read a finished chunk's
+// buffer while the next chunk accumulates into the other.  Every mbarrier
+// wait is bounded (tcgen05.cuh) and tensor memory is always freed.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -50,28 +56,44 @@
 namespace ccg {
 namespace oz {
 
-constexpr int S = 8;                                // digits per entry
-constexpr int LEVELS = 8;                           // digit-pair levels t + u = 0 .. 7
-constexpr int BM = 128, BN = 32, BK = 32, STAGES = 2;
-constexpr int CHUNK_KB = 8;                         // K blocks per exact chunk (K = 256)
+constexpr int BM = 128, BK = 32;
 constexpr int A_TILE = BM * BK * 2;                 // one A digit tile, bytes
-constexpr int B_TILE = BN * BK * 2;                 // one X digit tile, bytes
-constexpr int STAGE_BYTES = S * (A_TILE + B_TILE);  // 80 KB
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr int THREADS = 192;
-constexpr uint32_t TMEM_COLS = 512;                 // 2 buffers x 8 levels x 32 columns
+constexpr uint32_t TMEM_COLS = 512;                 // 2 buffers x S levels x BN columns
 constexpr int64_t kMaxK = 65536;                    // the int64 sums stay below 2^52
 constexpr int kNonFinite = 1 << 20;                 // exponent recorded for a row or column with inf / NaN
 
-struct Maps {
+// S digits per entry (levels t + u = 0 .. S - 1), BN real output columns
+// per tile, pipeline stages and K blocks per exact chunk.
+template <int S> struct Cfg;
+template <> struct Cfg<8> {
+  static constexpr int BN = 32, STAGES = 2, CHUNK_KB = 8;    // chunk K = 256; stage 80 KB
+};
+template <> struct Cfg<4> {
+  static constexpr int BN = 64, STAGES = 4, CHUNK_KB = 16;   // chunk K = 512; stage 48 KB
+};
+template <int S> struct Geo {
+  static constexpr int BN = Cfg<S>::BN, STAGES = Cfg<S>::STAGES, CHUNK_KB = Cfg<S>::CHUNK_KB;
+  static constexpr int B_TILE = BN * BK * 2;                 // one X digit tile, bytes
+  static constexpr int STAGE_BYTES = S * (A_TILE + B_TILE);
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+  static_assert(2 * S * BN == (int)TMEM_COLS, "two buffers of S levels fill tensor memory");
+  static_assert(S * BN <= 256, "the stacked X digits fit one MMA's N");
+};
+
+template <int S> struct Maps {
   CUtensorMap a[S];
   CUtensorMap x[S];
 };
 
+template <int S, class Out>
 __global__ void __launch_bounds__(THREADS, 1)
-    ozaki_gemm(const __grid_constant__ Maps maps, const int* __restrict__ erow, const int* __restrict__ fcol,
-               double* __restrict__ C, int M, int N, int K, int64_t ldc, int* err, const int* skip, int* skip_rec) {
+    ozaki_gemm(const __grid_constant__ Maps<S> maps, const int* __restrict__ erow, const int* __restrict__ fcol,
+               Out* __restrict__ C, int M, int N, int K, int64_t ldc, int* err, const int* skip, int* skip_rec) {
   using namespace tc;
+  using G = Geo<S>;
+  constexpr int LEVELS = S, BN = G::BN, STAGES = G::STAGES, CHUNK_KB = G::CHUNK_KB;
+  constexpr int B_TILE = G::B_TILE, STAGE_BYTES = G::STAGE_BYTES;
   if (skip != nullptr && *skip) {  // every column has stopped
     if (skip_rec != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *skip_rec = 1;
     return;
@@ -130,8 +152,11 @@ __global__ void __launch_bounds__(THREADS, 1)
       issued = kb + 1;
     }
   } else if (warp == 1 && lane == 0) {
-    // MMA issuer: level l of chunk c accumulates into buffer (c & 1), columns 32 l
-    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    // MMA issuer: level l of chunk c accumulates into buffer (c & 1),
+    // columns BN l.  One MMA per A digit t covers all its pairs: B is the X
+    // digits 0 .. S - 1 - t stacked along N (their tiles are consecutive in
+    // the stage, rows BN u .. BN u + BN - 1 for digit u), and D starts at
+    // level t, so the product with digit u lands in level t + u.
     for (int kb = 0; kb < nkb; ++kb) {
       const int c = kb / CHUNK_KB, kin = kb - c * CHUNK_KB, b = c & 1;
       if (kin == 0 && c >= 2 && !mbar_wait(&tempty[b], ((c >> 1) - 1) & 1, verr)) break;
@@ -142,14 +167,13 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
       for (int kk = 0; kk < BK / 16; ++kk) {
         const uint32_t off = kk * 32;  // 16 bf16 along K
+        const uint64_t bd = sdesc_k64(base + S * A_TILE + off);
 #pragma unroll
-        for (int l = 0; l < LEVELS; ++l) {
-#pragma unroll
-          for (int t = 0; t <= l; ++t) {
-            const uint64_t a = sdesc_k64(base + t * A_TILE + off);
-            const uint64_t bd = sdesc_k64(base + S * A_TILE + (l - t) * B_TILE + off);
-            umma(tmem + (uint32_t)(b * LEVELS * BN + l * BN), a, bd, idesc, (kin | kk | t) != 0 ? 1u : 0u);
-          }
+        for (int t = 0; t < S; ++t) {
+          // t = 0 writes every level first (N = S BN): it alone overwrites
+          const uint64_t a = sdesc_k64(base + t * A_TILE + off);
+          umma(tmem + (uint32_t)(b * LEVELS * BN + t * BN), a, bd, idesc_bf16(BM, (LEVELS - t) * BN),
+               (kin | kk | t) != 0 ? 1u : 0u);
         }
       }
       umma_commit(&empty[s]);
@@ -160,9 +184,12 @@ __global__ void __launch_bounds__(THREADS, 1)
     // epilogue: warp w reads tensor-memory lanes (rows) 32 (w % 4) .. + 31
     const int q = warp & 3;
     const int row = m0 + q * 32 + lane;
-    long long accA[BN], accB[BN];
+    constexpr int NB = S > 4 ? BN : 1;  // the second accumulator only with levels 4 ..
+    long long accA[BN], accB[NB];
 #pragma unroll
-    for (int j = 0; j < BN; ++j) accA[j] = accB[j] = 0;
+    for (int j = 0; j < BN; ++j) accA[j] = 0;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) accB[j] = 0;
     bool ok = true;
     for (int c = 0; c < nchunks && ok; ++c) {
       const int b = c & 1;
@@ -171,33 +198,38 @@ __global__ void __launch_bounds__(THREADS, 1)
       fence_after();
 #pragma unroll 1
       for (int l = 0; l < LEVELS; ++l) {
-        uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * LEVELS * BN + l * BN), r);
-        if (l == LEVELS - 1) {  // the buffer is free once its last level is in registers
-          fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&tempty[b]);
-        }
         const int sh = 7 * (3 - (l & 3));
 #pragma unroll
-        for (int j = 0; j < BN; ++j) {
-          const long long v = (long long)__float2int_rn(__uint_as_float(r[j])) << sh;
-          if (l < 4) accA[j] += v;
-          else accB[j] += v;
+        for (int h = 0; h < BN / 32; ++h) {
+          uint32_t r[32];
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * LEVELS * BN + l * BN + 32 * h), r);
+          if (l == LEVELS - 1 && h == BN / 32 - 1) {  // the buffer is free once its last level is in registers
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const long long v = (long long)__float2int_rn(__uint_as_float(r[j])) << sh;
+            if (S <= 4 || l < 4) accA[32 * h + j] += v;
+            else accB[(32 * h + j) % NB] += v;
+          }
         }
       }
     }
     if (ok && __shfl_sync(0xffffffffu, *verr, 0) == 0 && row < M) {
       const int er = erow[row];
-      double* dst = C + (int64_t)row * ldc;
+      Out* dst = C + (int64_t)row * ldc;
 #pragma unroll
       for (int j = 0; j < BN; ++j) {
         const int gc = n0 + j;
         if (gc < N) {
           const int fc = fcol[gc >> 1];
           const int sc = er + fc;
-          dst[gc] = (er >= kNonFinite || fc >= kNonFinite) ? __longlong_as_double(0x7ff8000000000000LL)
-                                                           : ldexp((double)accA[j], sc - 35) + ldexp((double)accB[j], sc - 63);
+          double v = ldexp((double)accA[j], sc - 35);
+          if (S > 4) v += ldexp((double)accB[j % NB], sc - 63);
+          if (er >= kNonFinite || fc >= kNonFinite) v = __longlong_as_double(0x7ff8000000000000LL);
+          dst[gc] = (Out)v;
         }
       }
     }
@@ -226,7 +258,8 @@ __device__ __forceinline__ int exp_above(double m) {
   return ex;
 }
 
-// 8 signed digits of v (|v| < 2^7 after scaling): rint and carry the remainder.
+// S signed digits of v (|v| < 2^7 after scaling): rint and carry the remainder.
+template <int S>
 __device__ __forceinline__ void digits(double v, __nv_bfloat16 (&d)[S]) {
 #pragma unroll
   for (int t = 0; t < S; ++t) {
@@ -236,14 +269,15 @@ __device__ __forceinline__ void digits(double v, __nv_bfloat16 (&d)[S]) {
   }
 }
 
-// Row exponents (|Ah[i][j]| < 2^e[i]) and the digit slices of the complex128
-// matrix read as a real n x 2n matrix; slice t at out + t * n * 2n.  One
-// block per row.
-__global__ void __launch_bounds__(kBlock) oz_slice_rows(const double2* __restrict__ A, int64_t lda, int64_t n,
+// Row exponents (|Ah[i][j]| < 2^e[i]) and the digit slices of the matrix
+// read as a real n x 2n matrix; slice t at out + t * n * 2n.  One block per
+// row.
+template <int S, class R>
+__global__ void __launch_bounds__(kBlock) oz_slice_rows(const cx<R>* __restrict__ A, int64_t lda, int64_t n,
                                                         __nv_bfloat16* __restrict__ out, int* __restrict__ e) {
   __shared__ double red[kWarps];
   const int64_t i = blockIdx.x;
-  const double2* a = A + i * lda;
+  const cx<R>* a = A + i * lda;
   double m = 0.0;
   for (int64_t j = threadIdx.x; j < n; j += kBlock) m = amax(amax(m, a[j].x), a[j].y);
 #pragma unroll
@@ -258,24 +292,25 @@ __global__ void __launch_bounds__(kBlock) oz_slice_rows(const double2* __restric
   const int sh = 7 - (ex >= kNonFinite ? 0 : ex);  // applied by ldexp: 2^sh alone may overflow
   const int64_t cnt = n * 2 * n;
   for (int64_t j = threadIdx.x; j < 2 * n; j += kBlock) {
-    const double2 z = a[j >> 1];
+    const cx<R> z = a[j >> 1];
     __nv_bfloat16 d[S];
-    digits(ldexp((j & 1) ? z.y : z.x, sh), d);
+    digits<S>(ldexp((double)((j & 1) ? z.y : z.x), sh), d);
 #pragma unroll
     for (int t = 0; t < S; ++t) out[t * cnt + i * 2 * n + j] = d[t];
   }
 }
 
-// Column exponents of the block X (row-major n x k complex128): |re|, |im|
-// of column c below 2^f[c].  One block per column.
-__global__ void __launch_bounds__(kBlock) oz_col_exp(const double2* __restrict__ X, int64_t n, int k,
+// Column exponents of the block X (row-major n x k): |re|, |im| of column
+// c below 2^f[c].  One block per column.
+template <class R>
+__global__ void __launch_bounds__(kBlock) oz_col_exp(const cx<R>* __restrict__ X, int64_t n, int k,
                                                      int* __restrict__ f) {
   __shared__ double red[kWarps];
   const int c = blockIdx.x;
   double m = 0.0;
   for (int64_t j = threadIdx.x; j < n; j += kBlock) {
-    const double2 z = X[j * k + c];
-    m = amax(amax(m, z.x), z.y);
+    const cx<R> z = X[j * k + c];
+    m = amax(amax(m, (double)z.x), (double)z.y);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
@@ -291,9 +326,10 @@ __global__ void __launch_bounds__(kBlock) oz_col_exp(const double2* __restrict__
 // Digit slices of Xh^T (2k rows x 2n): row 2c = (re x_c[j], -im x_c[j])_j,
 // row 2c + 1 = (im x_c[j], re x_c[j])_j, each scaled by 2^(7 - f[c]); slice
 // t at out + t * 2k * 2n.  32 x 32 tiles through shared memory.
-__global__ void oz_slice_block(const double2* __restrict__ X, int64_t n, int k, const int* __restrict__ f,
+template <int S, class R>
+__global__ void oz_slice_block(const cx<R>* __restrict__ X, int64_t n, int k, const int* __restrict__ f,
                                __nv_bfloat16* __restrict__ out) {
-  __shared__ double2 tile[32][33];
+  __shared__ cx<R> tile[32][33];
   const int64_t j0 = (int64_t)blockIdx.x * 32;
   const int c0 = blockIdx.y * 32;
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
@@ -301,18 +337,18 @@ __global__ void oz_slice_block(const double2* __restrict__ X, int64_t n, int k, 
   for (int r = ty; r < 32; r += 8) {
     const int64_t j = j0 + r;
     const int c = c0 + tx;
-    tile[r][tx] = (j < n && c < k) ? X[j * k + c] : make_double2(0.0, 0.0);
+    tile[r][tx] = (j < n && c < k) ? X[j * k + c] : cx<R>{R(0), R(0)};
   }
   __syncthreads();
   for (int r = ty; r < 32; r += 8) {
     const int c = c0 + r;
     const int64_t j = j0 + tx;
     if (c < k && j < n) {
-      const double2 z = tile[tx][r];
+      const cx<R> z = tile[tx][r];
       const int sh = 7 - (f[c] >= kNonFinite ? 0 : f[c]);
       __nv_bfloat16 dre[S], dim[S];
-      digits(ldexp(z.x, sh), dre);
-      digits(ldexp(z.y, sh), dim);
+      digits<S>(ldexp((double)z.x, sh), dre);
+      digits<S>(ldexp((double)z.y, sh), dim);
       const int64_t e0 = (int64_t)(2 * c) * (2 * n) + 2 * j;  // row 2c
       const int64_t e1 = e0 + 2 * n;                          // row 2c + 1
 #pragma unroll
@@ -330,16 +366,18 @@ __global__ void oz_slice_block(const double2* __restrict__ X, int64_t n, int k, 
 }  // namespace oz
 
 bool oz_available(const ccg_operator* op) {
-  return op->kind == CCG_OPK_DENSE && op->dtype == CCG_C128 && op->n % 4 == 0 && 2 * op->n <= oz::kMaxK &&
-         tc::encoder() != nullptr;
+  return op->kind == CCG_OPK_DENSE && op->n % 4 == 0 && 2 * op->n <= oz::kMaxK && tc::encoder() != nullptr;
 }
 
-// Y = A X (row-major n x k complex128 blocks) by the integer-slice scheme on
-// the tensor cores.  The matrix digits are made on first use and kept with
-// the operator; the block's digits go to the handle's staging buffer.
-int oz_block_product(ccg_handle* h, const ccg_operator* op_c, const double2* X, double2* Y, int k, const int* skip) {
+// Y = A X (row-major n x k blocks) by the integer-slice scheme on the tensor
+// cores, S = 8 digits for complex128 and 4 for complex64.  The matrix digits
+// are made on first use and kept with the operator; the block's digits go to
+// the handle's staging buffer.
+template <class R>
+static int oz_product_t(ccg_handle* h, ccg_operator* op, const cx<R>* X, cx<R>* Y, int k, const int* skip) {
   using namespace oz;
-  ccg_operator* op = const_cast<ccg_operator*>(op_c);
+  constexpr int S = sizeof(R) == 8 ? 8 : 4;
+  using G = Geo<S>;
   const int64_t n = op->n;
   cudaStream_t s = h->stream;
   const size_t abytes = (size_t)n * 2 * n * sizeof(__nv_bfloat16);
@@ -348,12 +386,13 @@ int oz_block_product(ccg_handle* h, const ccg_operator* op_c, const double2* X, 
     if (cudaMallocAsync(&op->oz_a, S * abytes + 256 + (size_t)n * sizeof(int), s) != cudaSuccess) {
       cudaGetLastError();
       op->oz_a = nullptr;
-      set_error("FP64 tensor-core operand allocation failed");
+      set_error("exact tensor-core operand allocation failed");
       return CCG_ERR_NOMEM;
     }
     __nv_bfloat16* slices = static_cast<__nv_bfloat16*>(op->oz_a);
     int* e = reinterpret_cast<int*>(static_cast<char*>(op->oz_a) + S * abytes + 256);
-    oz_slice_rows<<<(unsigned)n, kBlock, 0, s>>>(static_cast<const double2*>(op->A), op->lda, n, slices, e);
+    oz_slice_rows<S, R><<<(unsigned)n, kBlock, 0, s>>>(static_cast<const cx<R>*>(op->A), op->lda, n, slices, e);
+    ++h->launches;
     for (int t = 0; t < S; ++t)
       if (!tc::make_map(reinterpret_cast<CUtensorMap*>(op->oz_map[t]), reinterpret_cast<char*>(slices) + t * abytes, n,
                         2 * n, BM, BK)) {
@@ -377,7 +416,7 @@ int oz_block_product(ccg_handle* h, const ccg_operator* op_c, const double2* X, 
     if (cudaMalloc(&h->oz_buf, need) != cudaSuccess) {
       cudaGetLastError();
       h->oz_buf = nullptr;
-      set_error("FP64 tensor-core staging allocation failed");
+      set_error("exact tensor-core staging allocation failed");
       return CCG_ERR_NOMEM;
     }
     h->oz_bytes = need;
@@ -386,42 +425,50 @@ int oz_block_product(ccg_handle* h, const ccg_operator* op_c, const double2* X, 
   int* err = static_cast<int*>(h->oz_buf);
   int* fcol = reinterpret_cast<int*>(static_cast<char*>(h->oz_buf) + 256);
   __nv_bfloat16* xs = reinterpret_cast<__nv_bfloat16*>(static_cast<char*>(h->oz_buf) + 256 + fbytes);
-  oz_col_exp<<<k, kBlock, 0, s>>>(X, n, k, fcol);
+  oz_col_exp<R><<<k, kBlock, 0, s>>>(X, n, k, fcol);
   dim3 sg((unsigned)((n + 31) / 32), (unsigned)((k + 31) / 32));
-  oz_slice_block<<<sg, kBlock, 0, s>>>(X, n, k, fcol, xs);
-  Maps maps;
+  oz_slice_block<S, R><<<sg, kBlock, 0, s>>>(X, n, k, fcol, xs);
+  Maps<S> maps;
   std::memset(&maps, 0, sizeof(maps));
   for (int t = 0; t < S; ++t) {
     std::memcpy(&maps.a[t], op->oz_map[t], sizeof(CUtensorMap));
-    if (!tc::make_map(&maps.x[t], reinterpret_cast<char*>(xs) + t * xb, 2 * k, 2 * n, BN, BK)) {
+    if (!tc::make_map(&maps.x[t], reinterpret_cast<char*>(xs) + t * xb, 2 * k, 2 * n, G::BN, BK)) {
       set_error("cuTensorMapEncodeTiled failed for the block digits");
       return CCG_ERR_CUDA;
     }
   }
   static bool attr = false;
   if (!attr) {
-    if (cudaFuncSetAttribute(ozaki_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess) {
-      set_error("FP64 tensor-core kernel: shared memory opt-in failed");
+    if (cudaFuncSetAttribute(ozaki_gemm<S, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES) !=
+        cudaSuccess) {
+      set_error("exact tensor-core kernel: shared memory opt-in failed");
       return CCG_ERR_CUDA;
     }
     attr = true;
   }
   const int Nr = 2 * k;
-  dim3 grid((unsigned)((Nr + BN - 1) / BN), (unsigned)((n + BM - 1) / BM));
-  ozaki_gemm<<<grid, THREADS, SMEM_BYTES, s>>>(maps, erow, fcol, reinterpret_cast<double*>(Y), (int)n, Nr,
-                                               (int)(2 * n), (int64_t)Nr, err, skip, timing_rec(h));
+  dim3 grid((unsigned)((Nr + G::BN - 1) / G::BN), (unsigned)((n + BM - 1) / BM));
+  ozaki_gemm<S, R><<<grid, THREADS, G::SMEM_BYTES, s>>>(maps, erow, fcol, reinterpret_cast<R*>(Y), (int)n, Nr,
+                                                        (int)(2 * n), (int64_t)Nr, err, skip, timing_rec(h));
   h->launches += 3;
   return cudaGetLastError() == cudaSuccess ? CCG_OK : CCG_ERR_CUDA;
 }
 
-// Error flag of the FP64 tensor-core pipeline: read and clear.
+int oz_block_product(ccg_handle* h, const ccg_operator* op, const double2* X, double2* Y, int k, const int* skip) {
+  return oz_product_t<double>(h, const_cast<ccg_operator*>(op), X, Y, k, skip);
+}
+int oz_block_product(ccg_handle* h, const ccg_operator* op, const float2* X, float2* Y, int k, const int* skip) {
+  return oz_product_t<float>(h, const_cast<ccg_operator*>(op), X, Y, k, skip);
+}
+
+// Error flag of the exact tensor-core pipeline: read and clear.
 int oz_check_error(ccg_handle* h) {
   if (!h->oz_buf) return CCG_OK;
   int e = 0;
   if (cudaMemcpy(&e, h->oz_buf, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return CCG_ERR_CUDA;
   if (e) {
     cudaMemset(h->oz_buf, 0, sizeof(int));
-    set_error("FP64 tensor-core pipeline wait timed out");
+    set_error("exact tensor-core pipeline wait timed out");
     return CCG_ERR_TIMEOUT;
   }
   return CCG_OK;
