@@ -53,6 +53,12 @@ struct BCols {                // per-column state, arrays of k
   int hist_ld;
 };
 
+// Blocks per first-level group of the phase kernels' cross-block reduction,
+// and the counter words a grid needs (the all-groups counter, then one per
+// group).
+constexpr int kRedGroup = 8;
+static inline size_t counter_words(int grid) { return 1 + (size_t)(grid + kRedGroup - 1) / kRedGroup; }
+
 struct BPhaseBase {
   static constexpr bool kReduce = true;
   static constexpr bool kCheckAll = false;
@@ -79,19 +85,52 @@ __global__ void __launch_bounds__(kBlock) bphase_kernel(P p, BCtl* ctl, BCols co
 #pragma unroll
   for (int q = 0; q < P::NQ; ++q) sred[q][threadIdx.x] = acc[q];
   __syncthreads();
+  auto slot = [&](int b, int q) { return &red.partials[((int64_t)b * P::NQ + q) * k + threadIdx.x]; };
   if (threadIdx.x < k) {
 #pragma unroll
     for (int q = 0; q < P::NQ; ++q) {
       double v = 0.0;
       for (int r = 0; r < rpar; ++r) v += sred[q][r * k + threadIdx.x];
-      red.partials[((int64_t)blockIdx.x * P::NQ + q) * k + threadIdx.x] = v;
+      *slot(blockIdx.x, q) = v;
+    }
+    __threadfence();
+  }
+  // Two-level deterministic reduction: the last block of each group of
+  // kRedGroup blocks sums the group's partials (all loads in flight at once)
+  // into the group's first slot; the last group to finish sums the group
+  // sums.  Each column's thread walks a fixed order, so results do not depend
+  // on which block finishes last.
+  const int g = blockIdx.x / kRedGroup, g0 = g * kRedGroup;
+  const int gsize = min(kRedGroup, (int)gridDim.x - g0);
+  const int ngroups = ((int)gridDim.x + kRedGroup - 1) / kRedGroup;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int t = atomicAdd(&red.counter[1 + g], 1u);
+    is_last = (t == (unsigned)gsize - 1u);
+    if (is_last) red.counter[1 + g] = 0u;
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  if (threadIdx.x < k) {
+    double v[kRedGroup][P::NQ];
+#pragma unroll
+    for (int b = 0; b < kRedGroup; ++b)
+#pragma unroll
+      for (int q = 0; q < P::NQ; ++q) v[b][q] = b < gsize ? __ldcg(slot(g0 + b, q)) : 0.0;
+#pragma unroll
+    for (int q = 0; q < P::NQ; ++q) {
+      double t = 0.0;
+#pragma unroll
+      for (int b = 0; b < kRedGroup; ++b) t += v[b][q];
+      *slot(g0, q) = t;
     }
     __threadfence();
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned int t = atomicAdd(red.counter, 1u);
-    is_last = (t == gridDim.x - 1u);
+    const unsigned int t = atomicAdd(&red.counter[0], 1u);
+    is_last = (t == (unsigned)ngroups - 1u);
   }
   __syncthreads();
   if (!is_last) return;
@@ -100,9 +139,18 @@ __global__ void __launch_bounds__(kBlock) bphase_kernel(P p, BCtl* ctl, BCols co
     double tot[P::NQ];
 #pragma unroll
     for (int q = 0; q < P::NQ; ++q) tot[q] = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b)
+    for (int g1 = 0; g1 < ngroups; g1 += kRedGroup) {
+      double v[kRedGroup][P::NQ];
 #pragma unroll
-      for (int q = 0; q < P::NQ; ++q) tot[q] += __ldcg(&red.partials[((int64_t)b * P::NQ + q) * k + threadIdx.x]);
+      for (int b = 0; b < kRedGroup; ++b)
+#pragma unroll
+        for (int q = 0; q < P::NQ; ++q)
+          v[b][q] = g1 + b < ngroups ? __ldcg(slot((g1 + b) * kRedGroup, q)) : 0.0;
+#pragma unroll
+      for (int b = 0; b < kRedGroup; ++b)
+#pragma unroll
+        for (int q = 0; q < P::NQ; ++q) tot[q] += v[b][q];
+    }
     p.finish(threadIdx.x, tot, cols, ctl);
   }
   __syncthreads();
@@ -110,7 +158,7 @@ __global__ void __launch_bounds__(kBlock) bphase_kernel(P p, BCtl* ctl, BCols co
     const int nd = __syncthreads_count(threadIdx.x < k && cols.done[threadIdx.x]);
     if (threadIdx.x == 0 && nd == k) ctl->all_done = 1;
   }
-  if (threadIdx.x == 0) *red.counter = 0u;
+  if (threadIdx.x == 0) red.counter[0] = 0u;
 }
 
 template <class T> __device__ __forceinline__ void b_dotc(double* acc, T u, T v) {
@@ -436,13 +484,14 @@ static size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 template <class R> struct BWs {
   cx<R>* vec[8];   // r, r^, p, v, s, t, and two staging blocks
   double* partials;
-  unsigned int* counter;
+  unsigned int* counter;  // the reduction's counters: all groups, then one per group
+  size_t counter_bytes = 0;
   BCtl* ctl;
   BCols cols;
   static size_t bytes(int64_t n, int k, int maxit, int grid) {
     size_t b = 8 * al256((size_t)n * k * sizeof(cx<R>));
     b += al256((size_t)grid * 4 * k * sizeof(double));
-    b += al256(sizeof(unsigned int)) + al256(sizeof(BCtl));
+    b += al256(counter_words(grid) * sizeof(unsigned int)) + al256(sizeof(BCtl));
     b += 5 * al256(k * sizeof(double2)) + 3 * al256(k * sizeof(double)) + 6 * al256(k * sizeof(int));
     b += al256((size_t)k * (maxit + 1) * sizeof(double));
     return b;
@@ -452,7 +501,8 @@ template <class R> struct BWs {
     auto take = [&](size_t nb) { char* p = base + off; off += al256(nb); return p; };
     for (int i = 0; i < 8; ++i) vec[i] = reinterpret_cast<cx<R>*>(take((size_t)n * k * sizeof(cx<R>)));
     partials = reinterpret_cast<double*>(take((size_t)grid * 4 * k * sizeof(double)));
-    counter = reinterpret_cast<unsigned int*>(take(sizeof(unsigned int)));
+    counter = reinterpret_cast<unsigned int*>(take(counter_words(grid) * sizeof(unsigned int)));
+    counter_bytes = counter_words(grid) * sizeof(unsigned int);
     ctl = reinterpret_cast<BCtl*>(take(sizeof(BCtl)));
     double2** c2[5] = {&cols.rho, &cols.alpha, &cols.omega, &cols.beta, nullptr};
     for (int i = 0; i < 4; ++i) *c2[i] = reinterpret_cast<double2*>(take(k * sizeof(double2)));
@@ -533,7 +583,7 @@ static int bicgstab_core(BRun<R>& run, const cx<R>* Y, cx<R>* X, double tol, int
   init.maxit = maxit;
   init.tol = tol;
   B_CUDA(cudaMemcpyAsync(w.ctl, &init, sizeof(init), cudaMemcpyHostToDevice, s));
-  B_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(unsigned int), s));
+  B_CUDA(cudaMemsetAsync(w.counter, 0, w.counter_bytes, s));
   B_CUDA(cudaMemsetAsync(w.cols.done, 0, k * sizeof(int), s));
   B_CUDA(cudaMemsetAsync(w.cols.half, 0, k * sizeof(int), s));
   B_CUDA(cudaMemsetAsync(w.cols.zero_rhs, 0, k * sizeof(int), s));
@@ -727,7 +777,7 @@ int solve_batched_refined(ccg_handle* h, const ccg_operator* op, const ccg_opera
   init.tol = tol;
   init.skip_mv = 1;
   B_CUDA(cudaMemcpyAsync(ro.w.ctl, &init, sizeof(init), cudaMemcpyHostToDevice, s));
-  B_CUDA(cudaMemsetAsync(ro.w.counter, 0, sizeof(unsigned int), s));
+  B_CUDA(cudaMemsetAsync(ro.w.counter, 0, ro.w.counter_bytes, s));
   B_CUDA(cudaMemsetAsync(ro.w.cols.done, 0, kk * sizeof(int), s));
   B_CUDA(cudaMemsetAsync(ro.w.cols.zero_rhs, 0, kk * sizeof(int), s));
   B_CUDA(cudaMemsetAsync(ro.w.cols.status, 0, kk * sizeof(int), s));
