@@ -53,11 +53,14 @@ struct BCols {                // per-column state, arrays of k
   int hist_ld;
 };
 
-// Blocks per first-level group of the phase kernels' cross-block reduction,
-// and the counter words a grid needs (the all-groups counter, then one per
-// group).
+// Fan-in of the phase kernels' cross-block reduction tree, and the counter
+// words a grid needs (one per group of every level).
 constexpr int kRedGroup = 8;
-static inline size_t counter_words(int grid) { return 1 + (size_t)(grid + kRedGroup - 1) / kRedGroup; }
+static inline size_t counter_words(int grid) {
+  size_t w = 0;
+  for (int cnt = grid; cnt > 1; cnt = (cnt + kRedGroup - 1) / kRedGroup) w += (cnt + kRedGroup - 1) / kRedGroup;
+  return w > 0 ? w : 1;
+}
 
 struct BPhaseBase {
   static constexpr bool kReduce = true;
@@ -95,62 +98,50 @@ __global__ void __launch_bounds__(kBlock) bphase_kernel(P p, BCtl* ctl, BCols co
     }
     __threadfence();
   }
-  // Two-level deterministic reduction: the last block of each group of
-  // kRedGroup blocks sums the group's partials (all loads in flight at once)
-  // into the group's first slot; the last group to finish sums the group
-  // sums.  Each column's thread walks a fixed order, so results do not depend
-  // on which block finishes last.
-  const int g = blockIdx.x / kRedGroup, g0 = g * kRedGroup;
-  const int gsize = min(kRedGroup, (int)gridDim.x - g0);
-  const int ngroups = ((int)gridDim.x + kRedGroup - 1) / kRedGroup;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned int t = atomicAdd(&red.counter[1 + g], 1u);
-    is_last = (t == (unsigned)gsize - 1u);
-    if (is_last) red.counter[1 + g] = 0u;
-  }
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-  if (threadIdx.x < k) {
-    double v[kRedGroup][P::NQ];
-#pragma unroll
-    for (int b = 0; b < kRedGroup; ++b)
-#pragma unroll
-      for (int q = 0; q < P::NQ; ++q) v[b][q] = b < gsize ? __ldcg(slot(g0 + b, q)) : 0.0;
-#pragma unroll
-    for (int q = 0; q < P::NQ; ++q) {
-      double t = 0.0;
-#pragma unroll
-      for (int b = 0; b < kRedGroup; ++b) t += v[b][q];
-      *slot(g0, q) = t;
+  // Deterministic tree reduction with fan-in kRedGroup: at each level the
+  // last block of a group sums the group's slots (all loads in flight at
+  // once) into the group's first slot and moves up; the block that sums the
+  // last remaining group holds the total in slot 0.  Each column's thread
+  // walks a fixed order, so results do not depend on which blocks finish
+  // last.
+  int idx = blockIdx.x, cnt = gridDim.x, stride = 1, base = 0;
+  while (cnt > 1) {
+    const int g = idx / kRedGroup, g0 = g * kRedGroup;
+    const int gsize = min(kRedGroup, cnt - g0);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned int t = atomicAdd(&red.counter[base + g], 1u);
+      is_last = (t == (unsigned)gsize - 1u);
+      if (is_last) red.counter[base + g] = 0u;
     }
+    __syncthreads();
+    if (!is_last) return;
     __threadfence();
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned int t = atomicAdd(&red.counter[0], 1u);
-    is_last = (t == (unsigned)ngroups - 1u);
-  }
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-  if (threadIdx.x < k && !cols.done[threadIdx.x]) {
-    double tot[P::NQ];
-#pragma unroll
-    for (int q = 0; q < P::NQ; ++q) tot[q] = 0.0;
-    for (int g1 = 0; g1 < ngroups; g1 += kRedGroup) {
+    if (threadIdx.x < k) {
       double v[kRedGroup][P::NQ];
 #pragma unroll
       for (int b = 0; b < kRedGroup; ++b)
 #pragma unroll
-        for (int q = 0; q < P::NQ; ++q)
-          v[b][q] = g1 + b < ngroups ? __ldcg(slot((g1 + b) * kRedGroup, q)) : 0.0;
+        for (int q = 0; q < P::NQ; ++q) v[b][q] = b < gsize ? __ldcg(slot((g0 + b) * stride, q)) : 0.0;
 #pragma unroll
-      for (int b = 0; b < kRedGroup; ++b)
+      for (int q = 0; q < P::NQ; ++q) {
+        double t = 0.0;
 #pragma unroll
-        for (int q = 0; q < P::NQ; ++q) tot[q] += v[b][q];
+        for (int b = 0; b < kRedGroup; ++b) t += v[b][q];
+        *slot(g0 * stride, q) = t;
+      }
+      __threadfence();
     }
+    base += (cnt + kRedGroup - 1) / kRedGroup;
+    idx = g;
+    cnt = (cnt + kRedGroup - 1) / kRedGroup;
+    stride *= kRedGroup;
+  }
+  __syncthreads();
+  if (threadIdx.x < k && !cols.done[threadIdx.x]) {
+    double tot[P::NQ];
+#pragma unroll
+    for (int q = 0; q < P::NQ; ++q) tot[q] = __ldcg(slot(0, q));
     p.finish(threadIdx.x, tot, cols, ctl);
   }
   __syncthreads();
@@ -158,7 +149,6 @@ __global__ void __launch_bounds__(kBlock) bphase_kernel(P p, BCtl* ctl, BCols co
     const int nd = __syncthreads_count(threadIdx.x < k && cols.done[threadIdx.x]);
     if (threadIdx.x == 0 && nd == k) ctl->all_done = 1;
   }
-  if (threadIdx.x == 0) red.counter[0] = 0u;
 }
 
 template <class T> __device__ __forceinline__ void b_dotc(double* acc, T u, T v) {
@@ -521,7 +511,7 @@ template <class R> struct BWs {
 static int phase_grid(const ccg_handle* h, int64_t n, int k) {
   const int rpar = kBlock / k;
   const int64_t want = (n + rpar - 1) / rpar;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)h->num_sms * 2));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)h->num_sms * 4));
 }
 
 template <class R> struct BRun {

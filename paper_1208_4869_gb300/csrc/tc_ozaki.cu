@@ -11,9 +11,10 @@
 // scaled by 2^-e_i and every column pair c of Xh by 2^-f_c so that its
 // entries lie in (-1, 1), and each scaled entry is cut into S signed
 // digits:
-//     a = sum_t d_t 2^(-7(t+1)),  d_0 = rint(2^7 a) in [-128, 128],
-//     d_t (t >= 1) = rint of the remainder times 2^7, in [-64, 64],
-// all exact in double and exactly representable in bf16.  Then
+//     a = sum_t d_t 2^(-7(t+1)) + rho,   |rho| <= 2^(-7S-1),
+// the balanced base-128 digits of the integer N = rint(2^(7S) a), taken of
+// |N| and signed: |d_t| <= 64 for t >= 1, |d_0| <= 128, all exactly
+// representable in bf16.  Then
 //     (Ah Xh)_ic = 2^(e_i + f_c) sum_l 2^(-7(l + 2)) L_l,
 //     L_l = sum over digit pairs t + u = l of D^A_t D^X_u   (integer GEMMs),
 // truncated at l = S - 1 (S (S + 1) / 2 pairs: 36 for S = 8, whose dropped
@@ -258,15 +259,26 @@ __device__ __forceinline__ int exp_above(double m) {
   return ex;
 }
 
-// S signed digits of v (|v| < 2^7 after scaling): rint and carry the remainder.
+// S signed digits of v 2^(7 - ex) (|v| < 2^ex): N = rint(v 2^(7S - ex)),
+// |N| <= 2^(7S); |N| is cut into balanced base-128 digits from the bottom
+// (each remainder in [-64, 63], the top digit in [0, 128]) and the sign is
+// applied to every digit, so that
+//     v = 2^ex sum_t d_t 2^(-7(t+1))
+// up to the rounding of N, with |d_t| <= 64 (t >= 1), |d_0| <= 128, and the
+// digits of -v the negated digits of v.  Two FP64 operations per value; the
+// rest is integer arithmetic.
 template <int S>
-__device__ __forceinline__ void digits(double v, __nv_bfloat16 (&d)[S]) {
+__device__ __forceinline__ void digits(double v, int ex, __nv_bfloat16 (&d)[S]) {
+  const long long Ns = llrint(ldexp(v, 7 * S - ex));
+  const int sg = Ns < 0 ? -1 : 1;
+  long long N = Ns < 0 ? -Ns : Ns;
 #pragma unroll
-  for (int t = 0; t < S; ++t) {
-    const double r = rint(v);
-    d[t] = __float2bfloat16_rn((float)r);
-    v = (v - r) * 128.0;
+  for (int t = S - 1; t >= 1; --t) {
+    const int r = (int)((N + 64) & 127) - 64;
+    d[t] = __int2bfloat16_rn(sg * r);
+    N = (N - r) >> 7;
   }
+  d[0] = __int2bfloat16_rn(sg * (int)N);
 }
 
 // Row exponents (|Ah[i][j]| < 2^e[i]) and the digit slices of the matrix
@@ -289,12 +301,12 @@ __global__ void __launch_bounds__(kBlock) oz_slice_rows(const cx<R>* __restrict_
   for (int w = 0; w < kWarps; ++w) m = fmax(m, red[w]);
   const int ex = exp_above(m);
   if (threadIdx.x == 0) e[i] = ex;
-  const int sh = 7 - (ex >= kNonFinite ? 0 : ex);  // applied by ldexp: 2^sh alone may overflow
+  const int ex_s = ex >= kNonFinite ? 0 : ex;
   const int64_t cnt = n * 2 * n;
   for (int64_t j = threadIdx.x; j < 2 * n; j += kBlock) {
     const cx<R> z = a[j >> 1];
     __nv_bfloat16 d[S];
-    digits<S>(ldexp((double)((j & 1) ? z.y : z.x), sh), d);
+    digits<S>((double)((j & 1) ? z.y : z.x), ex_s, d);
 #pragma unroll
     for (int t = 0; t < S; ++t) out[t * cnt + i * 2 * n + j] = d[t];
   }
@@ -345,10 +357,10 @@ __global__ void oz_slice_block(const cx<R>* __restrict__ X, int64_t n, int k, co
     const int64_t j = j0 + tx;
     if (c < k && j < n) {
       const cx<R> z = tile[tx][r];
-      const int sh = 7 - (f[c] >= kNonFinite ? 0 : f[c]);
+      const int fx = f[c] >= kNonFinite ? 0 : f[c];
       __nv_bfloat16 dre[S], dim[S];
-      digits<S>(ldexp((double)z.x, sh), dre);
-      digits<S>(ldexp((double)z.y, sh), dim);
+      digits<S>((double)z.x, fx, dre);
+      digits<S>((double)z.y, fx, dim);
       const int64_t e0 = (int64_t)(2 * c) * (2 * n) + 2 * j;  // row 2c
       const int64_t e1 = e0 + 2 * n;                          // row 2c + 1
 #pragma unroll
