@@ -62,7 +62,10 @@ static inline size_t counter_words(int grid) {
   return w > 0 ? w : 1;
 }
 
+template <class R> using BAcc = acc_t<R>;
+
 struct BPhaseBase {
+  using Acc = double;
   static constexpr bool kReduce = true;
   static constexpr bool kCheckAll = false;
   __device__ __forceinline__ bool active(int c, const BCols& s) const { return !s.done[c]; }
@@ -74,9 +77,9 @@ __global__ void __launch_bounds__(kBlock) bphase_kernel(P p, BCtl* ctl, BCols co
   const int k = p.k;
   const int rpar = kBlock / k;
   const int c = threadIdx.x % k, rs = threadIdx.x / k;
-  double acc[P::NQ];
+  typename P::Acc acc[P::NQ];
 #pragma unroll
-  for (int q = 0; q < P::NQ; ++q) acc[q] = 0.0;
+  for (int q = 0; q < P::NQ; ++q) acc_zero(acc[q]);
   if (rs < rpar && p.active(c, cols)) {
     typename P::Col cs = p.col(c, cols);
     for (int64_t row = (int64_t)blockIdx.x * rpar + rs; row < p.n; row += (int64_t)gridDim.x * rpar)
@@ -86,7 +89,7 @@ __global__ void __launch_bounds__(kBlock) bphase_kernel(P p, BCtl* ctl, BCols co
   __shared__ double sred[P::NQ][kBlock];
   __shared__ bool is_last;
 #pragma unroll
-  for (int q = 0; q < P::NQ; ++q) sred[q][threadIdx.x] = acc[q];
+  for (int q = 0; q < P::NQ; ++q) sred[q][threadIdx.x] = acc_value(acc[q]);
   __syncthreads();
   auto slot = [&](int b, int q) { return &red.partials[((int64_t)b * P::NQ + q) * k + threadIdx.x]; };
   if (threadIdx.x < k) {
@@ -160,6 +163,16 @@ template <class T> __device__ __forceinline__ void b_nrm2(double* acc, T u) {
   const double2 a = widen(u);
   acc[0] += a.x * a.x + a.y * a.y;
 }
+__device__ __forceinline__ void b_dotc(FF* acc, float2 a, float2 b) {
+  ff_add_prod(acc[0], a.x, b.x);
+  ff_add_prod(acc[0], a.y, b.y);
+  ff_add_prod(acc[1], a.x, b.y);
+  ff_add_prod(acc[1], -a.y, b.x);
+}
+__device__ __forceinline__ void b_nrm2(FF* acc, float2 a) {
+  ff_add_prod(acc[0], a.x, a.x);
+  ff_add_prod(acc[0], a.y, a.y);
+}
 template <class R> __device__ __forceinline__ bool b_tiny(double2 s) { return cabs(s) < tiny_guard<R>(); }
 template <class R> __device__ __forceinline__ bool b_tiny(double s) { return fabs(s) < tiny_guard<R>(); }
 __device__ __forceinline__ bool b_nonfinite(double v) { return !(v == v) || isinf(v); }
@@ -184,6 +197,7 @@ __device__ __forceinline__ bool col_end(const BCols& s, const BCtl* ctl, int c, 
 
 // R = Y - A X0 (ax null: X0 = 0), R^ = R; per-column ||y||, ||r||, start scalars.
 template <class R> struct BInit : BPhaseBase {
+  using Acc = BAcc<R>;
   static constexpr int NQ = 3;
   static constexpr bool kCheckAll = true;
   struct Col {};
@@ -195,7 +209,7 @@ template <class R> struct BInit : BPhaseBase {
   cx<R>* rh;
   __device__ __forceinline__ bool active(int c, const BCols& s) const { return !s.done[c] && !(s.skip && s.skip[c]); }
   __device__ __forceinline__ Col col(int, const BCols&) const { return Col(); }
-  __device__ __forceinline__ void element(int64_t row, int c, const Col&, double* acc) const {
+  __device__ __forceinline__ void element(int64_t row, int c, const Col&, Acc* acc) const {
     const int64_t e = row * k + c;
     const cx<R> yi = y[e];
     const cx<R> ri = ax ? csub(yi, ax[e]) : yi;
@@ -203,7 +217,7 @@ template <class R> struct BInit : BPhaseBase {
     rh[e] = ri;
     b_nrm2(acc, yi);
     b_nrm2(acc + 1, ri);
-    if (!(isfinite((double)yi.x) && isfinite((double)yi.y))) acc[2] += 1.0;
+    if (!(isfinite((double)yi.x) && isfinite((double)yi.y))) acc_add1(acc[2]);
   }
   __device__ void finish(int c, const double* t, const BCols& s, const BCtl* ctl) const {
     s.iters[c] = 0;
@@ -254,6 +268,7 @@ template <class R> struct BP : BPhaseBase {  // p = r (first) or r + beta (p - o
 };
 
 template <class R> struct BSigma : BPhaseBase {  // alpha = rho / <r^, v>
+  using Acc = BAcc<R>;
   static constexpr int NQ = 2;
   struct Col {};
   int64_t n;
@@ -261,7 +276,7 @@ template <class R> struct BSigma : BPhaseBase {  // alpha = rho / <r^, v>
   const cx<R>* rh;
   const cx<R>* v;
   __device__ __forceinline__ Col col(int, const BCols&) const { return Col(); }
-  __device__ __forceinline__ void element(int64_t row, int c, const Col&, double* acc) const {
+  __device__ __forceinline__ void element(int64_t row, int c, const Col&, Acc* acc) const {
     const int64_t e = row * k + c;
     b_dotc(acc, rh[e], v[e]);
   }
@@ -273,6 +288,7 @@ template <class R> struct BSigma : BPhaseBase {  // alpha = rho / <r^, v>
 };
 
 template <class R> struct BS : BPhaseBase {  // s = r - alpha v; half-step exit test on ||s||
+  using Acc = BAcc<R>;
   static constexpr int NQ = 1;
   struct Col { cx<R> alpha; };
   int64_t n;
@@ -281,7 +297,7 @@ template <class R> struct BS : BPhaseBase {  // s = r - alpha v; half-step exit 
   const cx<R>* v;
   cx<R>* sv;
   __device__ __forceinline__ Col col(int c, const BCols& s) const { Col o; o.alpha = narrow<R>(s.alpha[c]); return o; }
-  __device__ __forceinline__ void element(int64_t row, int c, const Col& o, double* acc) const {
+  __device__ __forceinline__ void element(int64_t row, int c, const Col& o, Acc* acc) const {
     const int64_t e = row * k + c;
     const cx<R> si = csub(r[e], cmul(o.alpha, v[e]));
     sv[e] = si;
@@ -294,6 +310,7 @@ template <class R> struct BS : BPhaseBase {  // s = r - alpha v; half-step exit 
 };
 
 template <class R> struct BOmega : BPhaseBase {  // omega = <t, s> / <t, t>
+  using Acc = BAcc<R>;
   static constexpr int NQ = 3;
   struct Col {};
   int64_t n;
@@ -302,7 +319,7 @@ template <class R> struct BOmega : BPhaseBase {  // omega = <t, s> / <t, t>
   const cx<R>* sv;
   __device__ __forceinline__ bool active(int c, const BCols& s) const { return !s.done[c] && !s.half[c]; }
   __device__ __forceinline__ Col col(int, const BCols&) const { return Col(); }
-  __device__ __forceinline__ void element(int64_t row, int c, const Col&, double* acc) const {
+  __device__ __forceinline__ void element(int64_t row, int c, const Col&, Acc* acc) const {
     const int64_t e = row * k + c;
     b_dotc(acc, t[e], sv[e]);
     b_nrm2(acc + 2, t[e]);
@@ -316,6 +333,7 @@ template <class R> struct BOmega : BPhaseBase {  // omega = <t, s> / <t, t>
 };
 
 template <class R> struct BXR : BPhaseBase {  // x += alpha p + omega s; r = s - omega t; next rho
+  using Acc = BAcc<R>;
   static constexpr int NQ = 3;
   static constexpr bool kCheckAll = true;
   struct Col { cx<R> alpha, omega; bool half; };
@@ -334,7 +352,7 @@ template <class R> struct BXR : BPhaseBase {  // x += alpha p + omega s; r = s -
     o.half = s.half[c] != 0;
     return o;
   }
-  __device__ __forceinline__ void element(int64_t row, int c, const Col& o, double* acc) const {
+  __device__ __forceinline__ void element(int64_t row, int c, const Col& o, Acc* acc) const {
     const int64_t e = row * k + c;
     if (o.half) {
       x[e] = cadd(x[e], cmul(o.alpha, p[e]));

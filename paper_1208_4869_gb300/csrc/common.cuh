@@ -202,6 +202,34 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[NQ], double* __restrict_
   return true;
 }
 
+// Per-thread accumulators of the phase kernels' sums: double for complex128
+// data; for complex64 data a float-float pair -- each product formed
+// exactly (fma) and added by TwoSum -- which keeps about 44 bits of the sum
+// on the FP32 pipe instead of widening every element for the (narrow) FP64
+// pipe.  The pair becomes a double once per thread, before the block and
+// grid reductions.
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ void acc_zero(double& a) { a = 0.0; }
+__device__ __forceinline__ void acc_zero(FF& a) { a.hi = a.lo = 0.f; }
+__device__ __forceinline__ double acc_value(double a) { return a; }
+__device__ __forceinline__ double acc_value(const FF& a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ void acc_add1(double& a) { a += 1.0; }
+__device__ __forceinline__ void acc_add1(FF& a) { a.hi += 1.f; }
+__device__ __forceinline__ void ff_add_prod(FF& s, float x, float y) {
+  const float p = x * y;
+  const float e = fmaf(x, y, -p);  // x y = p + e exactly
+  const float t = s.hi + p;        // TwoSum(s.hi, p) = t + err exactly
+  const float bp = t - s.hi;
+  const float err = (s.hi - (t - bp)) + (p - bp);
+  s.hi = t;
+  s.lo += err + e;
+}
+template <class R> struct AccT { typedef double T; };
+template <> struct AccT<float> { typedef FF T; };
+template <class R> using acc_t = typename AccT<R>::T;
+
 // Workspace pointers a reducing kernel needs.
 struct Red {
   double* partials;       // kMaxRedBlocks * kMaxNQ doubles

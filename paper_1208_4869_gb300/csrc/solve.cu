@@ -41,18 +41,22 @@ struct PhaseBase {
   __device__ __forceinline__ void load(const SolveState*) {}
 };
 
-template <class P>
+// One elementwise pass with its sums; A is the per-thread accumulator
+// (double, or a float-float pair for complex64 data).
+template <class P, class A>
 __global__ void __launch_bounds__(kBlock) phase_kernel(P p, SolveState* st, Red red) {
   if (st->poll.done || p.skip(st)) return;
   p.load(st);
-  double acc[P::NQ];
+  A acc[P::NQ];
 #pragma unroll
-  for (int q = 0; q < P::NQ; ++q) acc[q] = 0.0;
+  for (int q = 0; q < P::NQ; ++q) acc_zero(acc[q]);
   const int64_t stride = (int64_t)gridDim.x * kBlock;
   for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < p.n; i += stride) p.element(i, acc);
   if (P::kReduce) {
-    double tot[P::NQ];
-    if (grid_reduce<P::NQ>(acc, red.partials, red.counter, tot) && threadIdx.x == 0) p.finish(tot, st);
+    double v[P::NQ], tot[P::NQ];
+#pragma unroll
+    for (int q = 0; q < P::NQ; ++q) v[q] = acc_value(acc[q]);
+    if (grid_reduce<P::NQ>(v, red.partials, red.counter, tot) && threadIdx.x == 0) p.finish(tot, st);
   }
 }
 
@@ -69,6 +73,22 @@ template <class T> __device__ __forceinline__ void acc_dotu(double* acc, T u, T 
 template <class T> __device__ __forceinline__ void acc_nrm2(double* acc, T u) {
   const double2 a = widen(u);
   acc[0] += a.x * a.x + a.y * a.y;
+}
+__device__ __forceinline__ void acc_dotc(FF* acc, float2 a, float2 b) {  // conj(a) b
+  ff_add_prod(acc[0], a.x, b.x);
+  ff_add_prod(acc[0], a.y, b.y);
+  ff_add_prod(acc[1], a.x, b.y);
+  ff_add_prod(acc[1], -a.y, b.x);
+}
+__device__ __forceinline__ void acc_dotu(FF* acc, float2 a, float2 b) {  // a b
+  ff_add_prod(acc[0], a.x, b.x);
+  ff_add_prod(acc[0], -a.y, b.y);
+  ff_add_prod(acc[1], a.x, b.y);
+  ff_add_prod(acc[1], a.y, b.x);
+}
+__device__ __forceinline__ void acc_nrm2(FF* acc, float2 a) {
+  ff_add_prod(acc[0], a.x, a.x);
+  ff_add_prod(acc[0], a.y, a.y);
 }
 template <class R> __device__ __forceinline__ bool tiny(double2 s) { return cabs(s) < tiny_guard<R>(); }
 template <class R> __device__ __forceinline__ bool tiny(double s) { return fabs(s) < tiny_guard<R>(); }
@@ -123,7 +143,7 @@ template <class R> struct InitR : PhaseBase {
   int method;
   bool ax_zero;
   __device__ __forceinline__ void load(const SolveState* st) { ax_zero = st->skip_mv != 0; }
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     const cx<R> yi = y[i];
     const cx<R> ri = ax_zero ? yi : csub(yi, ax.get(i));
     r[i] = ri;
@@ -131,7 +151,7 @@ template <class R> struct InitR : PhaseBase {
     if (c2) c2[i] = ri;
     acc_nrm2(acc, yi);
     acc_nrm2(acc + 1, ri);
-    if (!(isfinite((double)yi.x) && isfinite((double)yi.y))) acc[2] += 1.0;
+    if (!(isfinite((double)yi.x) && isfinite((double)yi.y))) acc_add1(acc[2]);
     if (method == M_COCG) acc_dotu(acc + 3, ri, ri);
   }
   __device__ void finish(const double* t, SolveState* st) {
@@ -210,7 +230,7 @@ template <class R> struct TrueRes : PhaseBase {
   const cx<R>* y;
   MvOut<R> ax;
   double* out;
-  __device__ __forceinline__ void element(int64_t i, double* acc) { acc_nrm2(acc, csub(y[i], ax.get(i))); }
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) { acc_nrm2(acc, csub(y[i], ax.get(i))); }
   __device__ void finish(const double* t, SolveState*) { *out = t[0]; }
 };
 
@@ -221,7 +241,7 @@ template <class R> struct SumParts : PhaseBase {
   int64_t n;
   MvOut<R> mv;
   cx<R>* y;
-  __device__ __forceinline__ void element(int64_t i, double*) { y[i] = mv.get(i); }
+  template <class A> __device__ __forceinline__ void element(int64_t i, A*) { y[i] = mv.get(i); }
   __device__ void finish(const double*, SolveState*) {}
 };
 template <class R> struct DotPhase : PhaseBase {
@@ -231,7 +251,7 @@ template <class R> struct DotPhase : PhaseBase {
   const cx<R>* v;
   int conj;
   double* out;
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     if (conj) acc_dotc(acc, u[i], v[i]);
     else acc_dotu(acc, u[i], v[i]);
   }
@@ -255,7 +275,7 @@ template <class R> struct BiP : PhaseBase {  // p = r, or p = r + beta (p - omeg
     beta = narrow<R>(st->beta);
     omega = narrow<R>(st->omega);
   }
-  __device__ __forceinline__ void element(int64_t i, double*) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A*) {
     p[i] = first ? r[i] : cadd(r[i], cmul(beta, csub(p[i], cmul(omega, v[i]))));
   }
   __device__ void finish(const double*, SolveState*) {}
@@ -266,7 +286,7 @@ template <class R> struct BiSigma : PhaseBase {  // sigma = <r^, v>, alpha = rho
   MvOut<R> mv;
   cx<R>* v;
   const cx<R>* rh;
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     const cx<R> vi = mv.get(i);
     if (mv.P) v[i] = vi;
     acc_dotc(acc, rh[i], vi);
@@ -285,7 +305,7 @@ template <class R> struct BiS : PhaseBase {  // s = r - alpha v; half-step exit 
   cx<R>* s;
   cx<R> alpha;
   __device__ __forceinline__ void load(const SolveState* st) { alpha = narrow<R>(st->alpha); }
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     const cx<R> si = csub(r[i], cmul(alpha, v[i]));
     s[i] = si;
     acc_nrm2(acc, si);
@@ -302,7 +322,7 @@ template <class R> struct BiOmega : PhaseBase {  // omega = <t, s> / <t, t>
   cx<R>* t;
   const cx<R>* s;
   __device__ __forceinline__ bool skip(const SolveState* st) const { return st->half != 0; }
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     const cx<R> ti = mv.get(i);
     if (mv.P) t[i] = ti;
     acc_dotc(acc, ti, s[i]);
@@ -330,7 +350,7 @@ template <class R> struct BiXR : PhaseBase {  // x += alpha p + omega s; r = s -
     alpha = narrow<R>(st->alpha);
     omega = narrow<R>(st->omega);
   }
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     if (half) {
       x[i] = cadd(x[i], cmul(alpha, p[i]));
       return;
@@ -370,7 +390,7 @@ template <class R> struct CgZ : PhaseBase {  // z = A^H r (from partials), gamma
   MvOut<R> mv;
   cx<R>* z;
   cx<R>* p;  // non-null on the first call
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     const cx<R> zi = mv.get(i);
     if (mv.P) z[i] = zi;
     if (p) p[i] = zi;
@@ -388,7 +408,7 @@ template <class R> struct CgAlpha : PhaseBase {  // w = A p, alpha = gamma / ||w
   int64_t n;
   MvOut<R> mv;
   cx<R>* w;
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     const cx<R> wi = mv.get(i);
     if (mv.P) w[i] = wi;
     acc_nrm2(acc, wi);
@@ -407,7 +427,7 @@ template <class R> struct CgXR : PhaseBase {  // x += alpha p; r -= alpha w
   const cx<R>* w;
   R alpha;
   __device__ __forceinline__ void load(const SolveState* st) { alpha = (R)st->alpha.x; }
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     x[i] = cadd(x[i], cscale(alpha, p[i]));
     const cx<R> ri = csub(r[i], cscale(alpha, w[i]));
     r[i] = ri;
@@ -425,7 +445,7 @@ template <class R> struct CgP : PhaseBase {  // p = z + beta p
   cx<R>* p;
   R beta;
   __device__ __forceinline__ void load(const SolveState* st) { beta = (R)st->beta.x; }
-  __device__ __forceinline__ void element(int64_t i, double*) { p[i] = cadd(z[i], cscale(beta, p[i])); }
+  template <class A> __device__ __forceinline__ void element(int64_t i, A*) { p[i] = cadd(z[i], cscale(beta, p[i])); }
   __device__ void finish(const double*, SolveState*) {}
 };
 
@@ -450,7 +470,7 @@ template <class R> struct QVW : PhaseBase {  // first iteration: v = v~/rho, w =
     rinv = (R)(1.0 / st->qrho);
     xinv = (R)(1.0 / st->xi);
   }
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     const cx<R> vi = cscale(rinv, vt[i]), wi = cscale(xinv, wt[i]);
     v[i] = vi;
     w[i] = wi;
@@ -476,7 +496,7 @@ template <class R> struct QPQ : PhaseBase {  // p = v - cp p, q = w - cq q (firs
     cp = narrow<R>(st->cp);
     cq = narrow<R>(st->cq);
   }
-  __device__ __forceinline__ void element(int64_t i, double*) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A*) {
     if (first) {
       p[i] = v[i];
       q[i] = w[i];
@@ -494,7 +514,7 @@ template <class R> struct QEps : PhaseBase {  // p~ = A p, u = A^H q; eps = <q, 
   cx<R>* pt;
   cx<R>* u;
   const cx<R>* q;
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     const cx<R> pti = mv1.get(i), ui = mv2.get(i);
     if (mv1.P) pt[i] = pti;
     if (mv2.P) u[i] = ui;
@@ -522,7 +542,7 @@ template <class R> struct QVT : PhaseBase {  // v~ = p~ - beta v, w~ = u - conj(
     beta = narrow<R>(st->beta);
     betac = cconj(beta);
   }
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     const cx<R> a = csub(pt[i], cmul(beta, v[i])), b = csub(u[i], cmul(betac, w[i]));
     vt[i] = a;
     wt[i] = b;
@@ -568,7 +588,7 @@ template <class R> struct QDX : PhaseBase {
     rinv = (R)(1.0 / st->rho_n);
     xinv = (R)(1.0 / st->xi_n);
   }
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     cx<R> di = cmul(eta, p[i]), si = cmul(eta, pt[i]);
     if (!first) {
       di = cadd(di, cscale(c, d[i]));
@@ -607,7 +627,7 @@ template <class R> struct CoMu : PhaseBase {  // q = A p, mu = [p, q], alpha = r
   MvOut<R> mv;
   cx<R>* q;
   const cx<R>* p;
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     const cx<R> qi = mv.get(i);
     if (mv.P) q[i] = qi;
     acc_dotu(acc, p[i], qi);
@@ -627,7 +647,7 @@ template <class R> struct CoXR : PhaseBase {  // x += alpha p; r -= alpha q; rho
   const cx<R>* q;
   cx<R> alpha;
   __device__ __forceinline__ void load(const SolveState* st) { alpha = narrow<R>(st->alpha); }
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     x[i] = cadd(x[i], cmul(alpha, p[i]));
     const cx<R> ri = csub(r[i], cmul(alpha, q[i]));
     r[i] = ri;
@@ -650,7 +670,7 @@ template <class R> struct CoP : PhaseBase {  // p = r + beta p
   cx<R>* p;
   cx<R> beta;
   __device__ __forceinline__ void load(const SolveState* st) { beta = narrow<R>(st->beta); }
-  __device__ __forceinline__ void element(int64_t i, double*) { p[i] = cadd(r[i], cmul(beta, p[i])); }
+  template <class A> __device__ __forceinline__ void element(int64_t i, A*) { p[i] = cadd(r[i], cmul(beta, p[i])); }
   __device__ void finish(const double*, SolveState*) {}
 };
 
@@ -664,7 +684,7 @@ template <class R> struct CrRho : PhaseBase {  // w = A r; rho' = [r, w]; beta =
   MvOut<R> mv;
   cx<R>* w;
   const cx<R>* r;
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     const cx<R> wi = mv.get(i);
     if (mv.P) w[i] = wi;
     acc_dotu(acc, r[i], wi);
@@ -689,7 +709,7 @@ template <class R> struct CrPQ : PhaseBase {  // p = r + beta p, q = w + beta q 
     first = st->poll.k == 0;
     beta = narrow<R>(st->beta);
   }
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     cx<R> pi = r[i], qi = w[i];
     if (!first) {
       pi = cfma(beta, p[i], pi);
@@ -714,7 +734,7 @@ template <class R> struct CrXR : PhaseBase {  // x += alpha p; r -= alpha q
   const cx<R>* q;
   cx<R> alpha;
   __device__ __forceinline__ void load(const SolveState* st) { alpha = narrow<R>(st->alpha); }
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     x[i] = cadd(x[i], cmul(alpha, p[i]));
     const cx<R> ri = csub(r[i], cmul(alpha, q[i]));
     r[i] = ri;
@@ -743,7 +763,7 @@ template <class R> struct BgP : PhaseBase {  // p = r + beta p, p~ = r~ + conj(b
     first = st->poll.k == 0;
     beta = narrow<R>(st->beta);
   }
-  __device__ __forceinline__ void element(int64_t i, double*) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A*) {
     if (first) {
       p[i] = r[i];
       pt[i] = rt[i];
@@ -761,7 +781,7 @@ template <class R> struct BgSigma : PhaseBase {  // q = A p, q~ = A^H p~; sigma 
   cx<R>* q;
   cx<R>* qt;
   const cx<R>* pt;
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     const cx<R> qi = mv1.get(i), qti = mv2.get(i);
     if (mv1.P) q[i] = qi;
     if (mv2.P) qt[i] = qti;
@@ -784,7 +804,7 @@ template <class R> struct BgXR : PhaseBase {  // x += alpha p; r -= alpha q; r~ 
   const cx<R>* qt;
   cx<R> alpha;
   __device__ __forceinline__ void load(const SolveState* st) { alpha = narrow<R>(st->alpha); }
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     x[i] = cadd(x[i], cmul(alpha, p[i]));
     const cx<R> ri = csub(r[i], cmul(alpha, q[i]));
     const cx<R> rti = csub(rt[i], cmul(cconj(alpha), qt[i]));
@@ -820,7 +840,7 @@ template <class R> struct CsUP : PhaseBase {  // u = r + beta q, p = u + beta (q
     first = st->poll.k == 0;
     beta = narrow<R>(st->beta);
   }
-  __device__ __forceinline__ void element(int64_t i, double*) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A*) {
     if (first) {
       u[i] = r[i];
       p[i] = r[i];
@@ -839,7 +859,7 @@ template <class R> struct CsSigma : PhaseBase {  // v = A p; sigma = <r^, v>, al
   MvOut<R> mv;
   cx<R>* v;
   const cx<R>* rh;
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     const cx<R> vi = mv.get(i);
     if (mv.P) v[i] = vi;
     acc_dotc(acc, rh[i], vi);
@@ -861,7 +881,7 @@ template <class R> struct CsQ : PhaseBase {  // q = u - alpha v; u^ = u + q; x +
   cx<R>* x;
   cx<R> alpha;
   __device__ __forceinline__ void load(const SolveState* st) { alpha = narrow<R>(st->alpha); }
-  __device__ __forceinline__ void element(int64_t i, double*) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A*) {
     const cx<R> ui = u[i];
     const cx<R> qi = csub(ui, cmul(alpha, v[i]));
     const cx<R> uhi = cadd(ui, qi);
@@ -879,7 +899,7 @@ template <class R> struct CsR : PhaseBase {  // r -= alpha A u^; rho' = <r^, r>,
   const cx<R>* rh;
   cx<R> alpha;
   __device__ __forceinline__ void load(const SolveState* st) { alpha = narrow<R>(st->alpha); }
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     const cx<R> ri = csub(r[i], cmul(alpha, mv.get(i)));
     r[i] = ri;
     acc_nrm2(acc, ri);
@@ -907,7 +927,7 @@ template <class R> struct CnXR : PhaseBase {  // w = A p; x += alpha p; r -= alp
   const cx<R>* p;
   R alpha;
   __device__ __forceinline__ void load(const SolveState* st) { alpha = (R)st->alpha.x; }
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     x[i] = cadd(x[i], cscale(alpha, p[i]));
     const cx<R> ri = csub(r[i], cscale(alpha, mv.get(i)));
     r[i] = ri;
@@ -930,7 +950,7 @@ template <class R> struct CnP : PhaseBase {  // z = A^H r; p = z + beta p (first
     first = st->poll.k == 0;
     beta = (R)st->beta.x;
   }
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     const cx<R> zi = mv.get(i);
     const cx<R> pi = first ? zi : cadd(zi, cscale(beta, p[i]));
     p[i] = pi;
@@ -980,7 +1000,7 @@ template <class R> struct TqInit : PhaseBase {  // v = 0, d = 0 (v gains A u in 
   int64_t n;
   cx<R>* v;
   cx<R>* d;
-  __device__ __forceinline__ void element(int64_t i, double*) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A*) {
     v[i] = mk<R>(0, 0);
     d[i] = mk<R>(0, 0);
   }
@@ -993,7 +1013,7 @@ template <class R> struct TqSigma : PhaseBase {  // v += A u; sigma = <r^, v>, a
   cx<R>* v;
   const cx<R>* rh;
   __device__ __forceinline__ bool skip(const SolveState* st) const { return st->half != 0; }
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     const cx<R> vi = cadd(v[i], mv.get(i));
     v[i] = vi;
     acc_dotc(acc, rh[i], vi);
@@ -1029,7 +1049,7 @@ template <class R, bool ODD> struct TqHalf : PhaseBase {
     eta = narrow<R>(st->eta);
     f = narrow<R>(tq_f(st));
   }
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     const cx<R> di = d[i], umi = um[i];
     x[i] = cadd(x[i], cmul(eta, di));
     if (!ODD) un[i] = csub(umi, cmul(alpha, v[i]));
@@ -1061,7 +1081,7 @@ template <class R> struct TqXStop : PhaseBase {  // after a stop: x += eta d, en
   cx<R> eta;
   __device__ __forceinline__ bool skip(const SolveState* st) const { return st->half == 0; }
   __device__ __forceinline__ void load(const SolveState* st) { eta = narrow<R>(st->eta); }
-  __device__ __forceinline__ void element(int64_t i, double*) { x[i] = cadd(x[i], cmul(eta, d[i])); }
+  template <class A> __device__ __forceinline__ void element(int64_t i, A*) { x[i] = cadd(x[i], cmul(eta, d[i])); }
   __device__ void finish(const double*, SolveState* st) { st->poll.done = 1; }
 };
 template <class R> struct TqU : PhaseBase {  // u = w + beta u_{m+1}; v = beta A u_{m+1} + beta^2 v
@@ -1079,7 +1099,7 @@ template <class R> struct TqU : PhaseBase {  // u = w + beta u_{m+1}; v = beta A
     beta = narrow<R>(st->beta);
     beta2 = cmul(beta, beta);
   }
-  __device__ __forceinline__ void element(int64_t i, double*) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A*) {
     u[i] = cadd(w[i], cmul(beta, un[i]));
     v[i] = cadd(cmul(beta, uh[i]), cmul(beta2, v[i]));
   }
@@ -1107,7 +1127,7 @@ template <class R> struct BlRho : PhaseBase {  // rho1 = <r~, r^_j>; beta = alph
   cx<R>* out;        // r^_j when mv holds partial sums
   const cx<R>* rt;
   bool start;
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     const cx<R> v = mv.get(i);
     if (mv.P) out[i] = v;
     acc_dotc(acc, rt[i], v);
@@ -1128,7 +1148,7 @@ template <class R> struct BlU : PhaseBase {  // u^_i = r^_i - beta u^_i, i <= j
   int j;
   cx<R> beta;
   __device__ __forceinline__ void load(const SolveState* st) { beta = narrow<R>(st->beta); }
-  __device__ __forceinline__ void element(int64_t e, double*) {
+  template <class A> __device__ __forceinline__ void element(int64_t e, A*) {
     for (int i = 0; i <= j; ++i) {
       const cx<R>* ri = static_cast<const cx<R>*>(vv.rh[i]);
       cx<R>* ui = static_cast<cx<R>*>(vv.uh[i]);
@@ -1143,7 +1163,7 @@ template <class R> struct BlGamma : PhaseBase {  // u^_{j+1} = A u^_j; gamma = <
   MvOut<R> mv;
   cx<R>* out;
   const cx<R>* rt;
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     const cx<R> v = mv.get(i);
     if (mv.P) out[i] = v;
     acc_dotc(acc, rt[i], v);
@@ -1162,7 +1182,7 @@ template <class R> struct BlR : PhaseBase {  // r^_i -= alpha u^_{i+1}, i <= j; 
   cx<R>* x;
   cx<R> alpha;
   __device__ __forceinline__ void load(const SolveState* st) { alpha = narrow<R>(st->alpha); }
-  __device__ __forceinline__ void element(int64_t e, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t e, A* acc) {
     const cx<R>* u0 = static_cast<const cx<R>*>(vv.uh[0]);
     x[e] = cadd(x[e], cmul(alpha, u0[e]));
     for (int i = 0; i <= j; ++i) {
@@ -1193,7 +1213,7 @@ template <class R, int L> struct BlGram : PhaseBase {
   int64_t n;
   MvOut<R> mv;
   BlVecs vv;
-  __device__ __forceinline__ void element(int64_t e, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t e, A* acc) {
     cx<R> r[L + 1];
 #pragma unroll
     for (int i = 0; i < L; ++i) r[i] = static_cast<const cx<R>*>(vv.rh[i])[e];
@@ -1262,7 +1282,7 @@ template <class R> struct BlMR : PhaseBase {  // the minimal-residual update; ||
   __device__ __forceinline__ void load(const SolveState* st) {
     for (int i = 0; i < L; ++i) g[i] = narrow<R>(st->bl_g[i]);
   }
-  __device__ __forceinline__ void element(int64_t e, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t e, A* acc) {
     cx<R> xe = x[e];
     cx<R>* r0 = static_cast<cx<R>*>(vv.rh[0]);
     cx<R>* u0 = static_cast<cx<R>*>(vv.uh[0]);
@@ -1296,7 +1316,7 @@ template <class R> struct ZeroVec : PhaseBase {
   static constexpr int NQ = 1;
   int64_t n;
   cx<R>* v;
-  __device__ __forceinline__ void element(int64_t i, double*) { v[i] = mk<R>(0, 0); }
+  template <class A> __device__ __forceinline__ void element(int64_t i, A*) { v[i] = mk<R>(0, 0); }
   __device__ void finish(const double*, SolveState*) {}
 };
 
@@ -1469,7 +1489,7 @@ template <class R> struct GmBegin : PhaseBase {  // v_0 = r / beta, g = (beta, 0
   GmBuf b;
   R binv;
   __device__ __forceinline__ void load(const SolveState* st) { binv = (R)(1.0 / st->gm_beta); }
-  __device__ __forceinline__ void element(int64_t i, double*) { v0[i] = cscale(binv, r[i]); }
+  template <class A> __device__ __forceinline__ void element(int64_t i, A*) { v0[i] = cscale(binv, r[i]); }
   __device__ void finish(const double*, SolveState* st) {
     b.g[0] = mkc(st->gm_beta, 0.0);
     for (int i = 1; i <= b.m; ++i) b.g[i] = mkc(0.0, 0.0);
@@ -1486,7 +1506,7 @@ template <class R> struct GmScale : PhaseBase {  // v_{j+1} = w / ||w||
   R einv;
   __device__ __forceinline__ bool skip(const SolveState* st) const { return st->half != 0; }
   __device__ __forceinline__ void load(const SolveState* st) { einv = (R)(1.0 / st->gm_eta); }
-  __device__ __forceinline__ void element(int64_t i, double*) { v[i] = cscale(einv, w[i]); }
+  template <class A> __device__ __forceinline__ void element(int64_t i, A*) { v[i] = cscale(einv, w[i]); }
   __device__ void finish(const double*, SolveState*) {}
 };
 // Cycle end: R y = g by back substitution (one thread).  Enqueued after
@@ -1512,7 +1532,7 @@ template <class R> struct GmXUpd : PhaseBase {  // x += V y; the solve ends here
   bool always;  // as for gm_solve
   __device__ __forceinline__ bool skip(const SolveState* st) const { return !always && !st->half; }
   __device__ __forceinline__ void load(const SolveState* st) { cols = st->gm_cols; }
-  __device__ __forceinline__ void element(int64_t i, double*) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A*) {
     cx<R> xi = x[i];
     for (int l = 0; l < cols; ++l) xi = cadd(xi, cmul(narrow<R>(yv[l]), V[(int64_t)l * ldv + i]));
     x[i] = xi;
@@ -1527,7 +1547,7 @@ template <class R> struct GmRestart : PhaseBase {  // r = y - A x, beta = ||r||;
   const cx<R>* y;
   MvOut<R> ax;
   cx<R>* r;
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     const cx<R> ri = csub(y[i], ax.get(i));
     r[i] = ri;
     acc_nrm2(acc, ri);
@@ -1734,7 +1754,7 @@ template <class R> struct Runner {
   }
 
   template <class P> void phase(const P& p) {
-    phase_kernel<P><<<grid_vec, kBlock, 0, s>>>(p, w.st, red);
+    phase_kernel<P, acc_t<R>><<<grid_vec, kBlock, 0, s>>>(p, w.st, red);
     ++h->launches;
   }
 
@@ -2167,7 +2187,7 @@ struct RefResid : PhaseBase {  // r = y - A x (double); r32 = round(r); d32 = 0
   int outer;
   bool ax_zero;
   __device__ __forceinline__ void load(const SolveState* st) { ax_zero = st->skip_mv != 0; }
-  __device__ __forceinline__ void element(int64_t i, double* acc) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A* acc) {
     const double2 yi = y[i];
     const double2 ri = ax_zero ? yi : csub(yi, ax.get(i));
     r32[i] = make_float2((float)ri.x, (float)ri.y);
@@ -2204,7 +2224,7 @@ struct RefUpdate : PhaseBase {  // x += widen(d32)
   int64_t n;
   double2* x;
   const float2* d32;
-  __device__ __forceinline__ void element(int64_t i, double*) {
+  template <class A> __device__ __forceinline__ void element(int64_t i, A*) {
     const float2 d = d32[i];
     x[i] = cadd(x[i], make_double2((double)d.x, (double)d.y));
   }
@@ -2353,7 +2373,7 @@ template <class R> static int dot_t(ccg_handle* h, int64_t n, const void* u, con
   red.counter = w.counter;
   int grid = (int)std::min<int64_t>((n + kBlock - 1) / kBlock, (int64_t)h->num_sms * 8);
   grid = std::max(1, std::min(grid, kMaxRedBlocks));
-  phase_kernel<DotPhase<R>><<<grid, kBlock, 0, h->stream>>>(p, w.st, red);
+  phase_kernel<DotPhase<R>, double><<<grid, kBlock, 0, h->stream>>>(p, w.st, red);  // the API dot: double
   ++h->launches;
   CCG_CUDA(cudaGetLastError());
   CCG_CUDA(cudaMemcpyAsync(out2, w.scratch, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
