@@ -239,10 +239,13 @@ def kernel_sources(tag):
     device helpers."""
     if tag.startswith("cgemm_rows"):
         own = [(CSRC + "blockmv.cuh", "template <class R> struct GemmTile;", "// Column-major user block")]
-    elif tag.startswith("ozaki_gemm"):
-        own = [(CSRC + "tc_ozaki.cu", None, None), (CSRC + "tcgen05.cuh", None, None)]
+    elif tag.startswith("ozaki_gemm"):   # the GEMM kernel and the tcgen05 helpers (no common.cuh code)
+        return [(CSRC + "tc_ozaki.cu", "template <int S, class Out>", "// max(m, |v|)"),
+                (CSRC + "tcgen05.cuh", None, None)]
     elif tag.startswith("gemm_bf16_split"):
-        own = [(CSRC + "tc_gemm.cu", None, None), (CSRC + "tcgen05.cuh", None, None)]
+        return [(CSRC + "tc_gemm.cu", "// C (M x N fp32, leading dimension ldc)", "// Xh^T as T bf16 terms"),
+                (CSRC + "tc_gemm.cu", "template <int T> struct Cfg {", "// C (M x N fp32, leading dimension ldc)"),
+                (CSRC + "tcgen05.cuh", None, None)]
     elif tag.startswith("dipole"):
         own = [(CSRC + "fft.cuh", None, None), (CSRC + "dipole.cu", None, None)]
     elif tag.startswith("gemv_n_rows"):

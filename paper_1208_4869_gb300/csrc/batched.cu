@@ -53,14 +53,6 @@ struct BCols {                // per-column state, arrays of k
   int hist_ld;
 };
 
-// Fan-in of the phase kernels' cross-block reduction tree, and the counter
-// words a grid needs (one per group of every level).
-constexpr int kRedGroup = 8;
-static inline size_t counter_words(int grid) {
-  size_t w = 0;
-  for (int cnt = grid; cnt > 1; cnt = (cnt + kRedGroup - 1) / kRedGroup) w += (cnt + kRedGroup - 1) / kRedGroup;
-  return w > 0 ? w : 1;
-}
 
 template <class R> using BAcc = acc_t<R>;
 

@@ -230,6 +230,16 @@ template <class R> struct AccT { typedef double T; };
 template <> struct AccT<float> { typedef FF T; };
 template <class R> using acc_t = typename AccT<R>::T;
 
+// Fan-in of the cross-block reduction trees (batched phases, the GMRES
+// passes), and the counter words a grid needs (one per group of every
+// level).
+constexpr int kRedGroup = 8;
+static inline size_t counter_words(int grid) {
+  size_t w = 0;
+  for (int cnt = grid; cnt > 1; cnt = (cnt + kRedGroup - 1) / kRedGroup) w += (cnt + kRedGroup - 1) / kRedGroup;
+  return w > 0 ? w : 1;
+}
+
 // Workspace pointers a reducing kernel needs.
 struct Red {
   double* partials;       // kMaxRedBlocks * kMaxNQ doubles

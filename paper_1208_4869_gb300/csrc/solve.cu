@@ -1434,23 +1434,27 @@ __global__ void __launch_bounds__(kBlock) gm_pass(const cx<R>* __restrict__ V, i
     }
   }
   if (MODE == GM_UPD_NORM) {
-    double acc[1] = {0.0};
+    acc_t<R> acc[1];
+    acc_zero(acc[0]);
 #pragma unroll
     for (int e = 0; e < E; ++e) acc_nrm2(acc, u[e]);
-    double tot[1];
-    if (grid_reduce<1>(acc, reinterpret_cast<double*>(b.part), b.counter, tot) && threadIdx.x == 0)
+    double v[1] = {acc_value(acc[0])}, tot[1];
+    if (grid_reduce<1>(v, reinterpret_cast<double*>(b.part), b.counter, tot) && threadIdx.x == 0)
       gm_column(b, j, sqrt(tot[0]), st);
     return;
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int l = 0; l < J; ++l) {
     const cx<R>* Vl = V + (int64_t)l * ldv;
-    double acc[2] = {0.0, 0.0};
+    acc_t<R> a2[2];
+    acc_zero(a2[0]);
+    acc_zero(a2[1]);
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int64_t i = i0 + (int64_t)e * kBlock;
-      if (i < n) acc_dotc(acc, Vl[i], u[e]);
+      if (i < n) acc_dotc(a2, Vl[i], u[e]);
     }
+    double acc[2] = {acc_value(a2[0]), acc_value(a2[1])};
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       acc[0] += __shfl_down_sync(0xffffffffu, acc[0], o);
@@ -1459,26 +1463,52 @@ __global__ void __launch_bounds__(kBlock) gm_pass(const cx<R>* __restrict__ V, i
     if (lane == 0) red[l][warp] = mkc(acc[0], acc[1]);
   }
   __syncthreads();
-  double2* part = b.part + (int64_t)blockIdx.x * (m + 1);
+  const int64_t ld = m + 1;
   for (int t = threadIdx.x; t < J; t += kBlock) {
     double2 sum = mkc(0.0, 0.0);
 #pragma unroll
     for (int q = 0; q < kWarps; ++q) sum = cadd(sum, red[t][q]);
-    part[t] = sum;
+    b.part[(int64_t)blockIdx.x * ld + t] = sum;
   }
   __threadfence();
+  // Grid sum in a fan-in-kRedGroup tree: at each level the last block of a
+  // group sums its group's rows (all loads in flight) into the group's
+  // first row; the block that sums the last group holds the total in row 0.
+  // Fixed order: deterministic.
+  int idx = blockIdx.x, cnt = gridDim.x, stride = 1, base = 0;
+  while (cnt > 1) {
+    const int g = idx / kRedGroup, g0 = g * kRedGroup;
+    const int gsize = min(kRedGroup, cnt - g0);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      is_last = atomicAdd(&b.counter[base + g], 1u) == (unsigned)gsize - 1u;
+      if (is_last) b.counter[base + g] = 0u;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    for (int t = threadIdx.x; t < J; t += kBlock) {
+      double2 v[kRedGroup];
+#pragma unroll
+      for (int q = 0; q < kRedGroup; ++q)
+        v[q] = q < gsize ? __ldcg(&b.part[(int64_t)(g0 + q) * stride * ld + t]) : mkc(0.0, 0.0);
+      double2 sum = mkc(0.0, 0.0);
+#pragma unroll
+      for (int q = 0; q < kRedGroup; ++q) sum = cadd(sum, v[q]);
+      b.part[(int64_t)g0 * stride * ld + t] = sum;
+    }
+    __threadfence();
+    base += (cnt + kRedGroup - 1) / kRedGroup;
+    idx = g;
+    cnt = (cnt + kRedGroup - 1) / kRedGroup;
+    stride *= kRedGroup;
+  }
   __syncthreads();
-  if (threadIdx.x == 0) is_last = atomicAdd(b.counter, 1u) == gridDim.x - 1u;
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
   for (int t = threadIdx.x; t < J; t += kBlock) {
-    double2 sum = mkc(0.0, 0.0);
-    for (int q = 0; q < (int)gridDim.x; ++q) sum = cadd(sum, __ldcg(&b.part[(int64_t)q * (m + 1) + t]));
+    const double2 sum = __ldcg(&b.part[t]);
     if (MODE == GM_DOT) b.H[t * m + j] = sum;
     else b.h2[t] = sum;
   }
-  if (threadIdx.x == 0) *b.counter = 0u;
 }
 
 template <class R> struct GmBegin : PhaseBase {  // v_0 = r / beta, g = (beta, 0, ...): a new cycle
@@ -1688,7 +1718,7 @@ template <class R> static size_t ws_bytes(int64_t n, const Dense<R>& d, int maxi
     b += align256((size_t)basis * gm_ldv(n) * sizeof(cx<R>));
     b += align256((size_t)(m + 1) * m * sizeof(double2)) + 4 * align256((size_t)(m + 1) * sizeof(double2)) +
          align256((size_t)m * sizeof(double));
-    b += align256((size_t)gm_grid(n) * (m + 1) * sizeof(double2)) + align256(sizeof(unsigned int));
+    b += align256((size_t)gm_grid(n) * (m + 1) * sizeof(double2)) + align256(counter_words(gm_grid(n)) * sizeof(unsigned int));
   }
   b += 12 * align256(n * sizeof(cx<R>));
   b += align256(std::max(d.p1_elems(), d.p2_elems()) * sizeof(cx<R>));
@@ -1719,7 +1749,7 @@ template <class R> static Ws<R> ws_carve(char* base, int64_t n, const Dense<R>& 
     w.gm.yv = reinterpret_cast<double2*>(take((size_t)(m + 1) * sizeof(double2)));
     w.gm.cs = reinterpret_cast<double*>(take((size_t)m * sizeof(double)));
     w.gm.part = reinterpret_cast<double2*>(take((size_t)gm_grid(n) * (m + 1) * sizeof(double2)));
-    w.gm.counter = reinterpret_cast<unsigned int*>(take(sizeof(unsigned int)));
+    w.gm.counter = reinterpret_cast<unsigned int*>(take(counter_words(gm_grid(n)) * sizeof(unsigned int)));
     w.gm.m = m;
   }
   for (int i = 0; i < 12; ++i) w.vec[i] = reinterpret_cast<cx<R>*>(take(n * sizeof(cx<R>)));
@@ -1884,7 +1914,7 @@ static int solve_core(ccg_handle* h, int method, const ccg_operator* op, const W
   init.skip_mv = x0_zero ? 0 : 1;   // without a known-zero start, the device checks x0
   CCG_CUDA(cudaMemcpyAsync(w.st, &init, sizeof(init), cudaMemcpyHostToDevice, s));
   CCG_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(unsigned int), s));
-  if (w.gm.counter) CCG_CUDA(cudaMemsetAsync(w.gm.counter, 0, sizeof(unsigned int), s));
+  if (w.gm.counter) CCG_CUDA(cudaMemsetAsync(w.gm.counter, 0, counter_words(gm_grid(n)) * sizeof(unsigned int), s));
   if (x0_zero) CCG_CUDA(cudaMemsetAsync(x, 0, n * sizeof(cx<R>), s));
   else {
     x_zero_check<R><<<run.grid_vec, kBlock, 0, s>>>(x, n, w.st);
