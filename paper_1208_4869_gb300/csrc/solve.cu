@@ -53,10 +53,8 @@ __global__ void __launch_bounds__(kBlock) phase_kernel(P p, SolveState* st, Red 
   const int64_t stride = (int64_t)gridDim.x * kBlock;
   for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < p.n; i += stride) p.element(i, acc);
   if (P::kReduce) {
-    double v[P::NQ], tot[P::NQ];
-#pragma unroll
-    for (int q = 0; q < P::NQ; ++q) v[q] = acc_value(acc[q]);
-    if (grid_reduce<P::NQ>(v, red.partials, red.counter, tot) && threadIdx.x == 0) p.finish(tot, st);
+    double tot[P::NQ];
+    if (grid_reduce<P::NQ>(acc, red.partials, red.counter, tot) && threadIdx.x == 0) p.finish(tot, st);
   }
 }
 
@@ -1438,8 +1436,8 @@ __global__ void __launch_bounds__(kBlock) gm_pass(const cx<R>* __restrict__ V, i
     acc_zero(acc[0]);
 #pragma unroll
     for (int e = 0; e < E; ++e) acc_nrm2(acc, u[e]);
-    double v[1] = {acc_value(acc[0])}, tot[1];
-    if (grid_reduce<1>(v, reinterpret_cast<double*>(b.part), b.counter, tot) && threadIdx.x == 0)
+    double tot[1];
+    if (grid_reduce<1>(acc, reinterpret_cast<double*>(b.part), b.counter, tot) && threadIdx.x == 0)
       gm_column(b, j, sqrt(tot[0]), st);
     return;
   }
@@ -1454,13 +1452,8 @@ __global__ void __launch_bounds__(kBlock) gm_pass(const cx<R>* __restrict__ V, i
       const int64_t i = i0 + (int64_t)e * kBlock;
       if (i < n) acc_dotc(a2, Vl[i], u[e]);
     }
-    double acc[2] = {acc_value(a2[0]), acc_value(a2[1])};
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      acc[0] += __shfl_down_sync(0xffffffffu, acc[0], o);
-      acc[1] += __shfl_down_sync(0xffffffffu, acc[1], o);
-    }
-    if (lane == 0) red[l][warp] = mkc(acc[0], acc[1]);
+    const double s0 = warp_acc_sum(a2[0]), s1 = warp_acc_sum(a2[1]);
+    if (lane == 0) red[l][warp] = mkc(s0, s1);
   }
   __syncthreads();
   const int64_t ld = m + 1;
