@@ -22,6 +22,7 @@
 
 #include "blockmv.cuh"
 #include "common.cuh"
+#include "reduce.cuh"
 #include "internal.h"
 
 namespace ccg {

@@ -27,6 +27,7 @@
 #include <memory>
 
 #include "common.cuh"
+#include "reduce.cuh"
 #include "gemv.cuh"
 #include "internal.h"
 
