@@ -6,6 +6,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -141,6 +142,10 @@ ccg_status ccg_create(ccg_handle** out, void* stream) {
   h->device = dev;
   cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
   if (h->num_sms <= 0) h->num_sms = 1;
+  if (const char* e = std::getenv("CCG_PHASE_MIN_ELEMS")) {  // tuning override of the fused-kernel grid
+    const int v = std::atoi(e);
+    if (v >= 1 && v <= 64) h->phase_elems = v;
+  }
   if (cudaHostAlloc(&h->pinned, 2 * sizeof(Poll), cudaHostAllocDefault) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->poll_ev[0], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->poll_ev[1], cudaEventDisableTiming) != cudaSuccess) {

@@ -83,6 +83,7 @@ struct ccg_handle {
   // the pipeline's error flag (first 256 bytes)
   int tc_mode = 1;   // 0 never, 1 refined inner solves and block products, 2 also plain batched solves
   int tc_terms = 2;  // bf16 terms of the split operands (2 or 3; the fp32 accumulation limits both to ~1e-4 at K ~ 1e4)
+  int phase_elems = 1;  // floor on the elements per thread of the fused update kernels' grid
   int gm_restart = 30;  // GMRES cycle length m
   int bicgstab_l = 2;   // degree l of BiCGstab(l)
   void* tc_buf = nullptr;

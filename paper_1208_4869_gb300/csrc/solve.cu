@@ -1773,7 +1773,8 @@ template <class R> struct Runner {
       : h(h_), op(op_), s(h_->stream), d(op_, h_->num_sms), w(w_) {
     red.partials = w.partials;
     red.counter = w.counter;
-    grid_vec = (int)std::min<int64_t>((d.n + kBlock - 1) / kBlock, (int64_t)h->num_sms * 8);
+    const int64_t per_block = (int64_t)kBlock * h->phase_elems;
+    grid_vec = (int)std::min<int64_t>((d.n + per_block - 1) / per_block, (int64_t)h->num_sms * 8);
     grid_vec = std::max(1, std::min(grid_vec, kMaxRedBlocks));
   }
 
