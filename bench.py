@@ -125,12 +125,14 @@ def barrier(world):
 
 
 # ----------------------------------------------------------------- clocks
+PREWARM_S = 1.5   # untimed seconds of headline steps before the warm-up steps
+
 class ClockSampler:
     """nvidia-smi samples every 200 ms while the timed region runs."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,clocks.mem")
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
@@ -155,7 +157,7 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
+        sm, smax, mem, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
@@ -169,9 +171,14 @@ class ClockSampler:
             for nm, v in zip(names, f[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
+            if len(f) > 9:
+                try:
+                    mem.append(float(f[9]))
+                except ValueError:
+                    pass
         os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "mem_mhz": statistics.median(mem) if mem else None, "reasons": sorted(reasons), "samples": len(sm)}
 
 
 # ----------------------------------------------------------------- roofline helpers
@@ -570,6 +577,13 @@ def run_ours(args):
     # auto: the mixed headline plus the complex128 path for comparison; an
     # explicit --path runs that path alone
     paths = [headline] + ([p for p in ("mixed", "fp64") if p != headline] if args.path == "auto" else [])
+    # untimed pre-warm: about PREWARM_S seconds of headline steps, so that the
+    # GPU's clocks have left any idle state before the warm-up steps proper
+    pre_step = make_step(headline)
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < PREWARM_S:
+        pre_step()
+        torch.cuda.synchronize()
     for path in paths:
         step = make_step(path)
         for _ in range(args.warmup):
@@ -647,7 +661,8 @@ def run_ours(args):
         lat_sorted = sorted(lat)
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_max_ms / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "prewarm_s": PREWARM_S, "ms_per_step": t_max_ms / args.steps,
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64+c128" if headline == "mixed" else "c128",
             "data": "synthetic",
             "config": {"workload": workload, "n": n, "methods": methods, "tol": args.tol, "path": headline,
