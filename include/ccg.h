@@ -98,7 +98,10 @@ typedef struct {
 
 /* Create a handle bound to `stream` (a cudaStream_t; NULL = legacy default
  * stream) on the current CUDA device.  *h receives the handle.  Returns
- * CCG_ERR_CUDA when no device is usable. */
+ * CCG_ERR_CUDA when no device is usable.  The environment variable
+ * CCG_PHASE_MIN_ELEMS (1..64, read here) sets a floor on the vector elements
+ * per thread of the fused update kernels of single-right-hand-side solves
+ * (a tuning override; default 1). */
 ccg_status ccg_create(ccg_handle** h, void* stream);
 /* Destroy a handle and free its workspace (after synchronising its stream). */
 ccg_status ccg_destroy(ccg_handle* h);
