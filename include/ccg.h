@@ -146,6 +146,27 @@ ccg_status ccg_op_dipole(ccg_handle* h, ccg_dtype dtype, int nx, int ny, int nz,
                          double m_re, double m_im, ccg_operator** op);
 /* Number of occupied sites N of a dipole operator (0 for other operators). */
 int64_t ccg_dipole_sites(const ccg_operator* op);
+/* A user-supplied operator: the manual's `matvec` and `cmatvec` (Sec. 5),
+ * kept apart from the iteration.  Each is a host function that ENQUEUES
+ *   y = A x   (matvec)   or   y = A^H x   (cmatvec)
+ * on `stream` (the handle's cudaStream_t) for device vectors x and y of n
+ * complex values in the operator's precision (interleaved re, im; 16-byte
+ * aligned), and returns 0 on success.  The library calls it from the thread
+ * that runs the solve, possibly a few iterations ahead of the GPU and,
+ * near the end of a solve, for products whose results are not used; x and
+ * y are library workspace that stays valid until the enqueued work has run.
+ * It must not synchronise with work it has not enqueued itself on `stream`,
+ * and must not call the handle that invoked it.  A nonzero return ends the
+ * solve with CCG_ERR_CUDA (the message names the callback). */
+typedef int (*ccg_matvec_fn)(void* ctx, int64_t n, const void* x, void* y, void* stream);
+/* Operator from callbacks (see ccg_matvec_fn); ctx is passed through.
+ * cmatvec may be NULL: the methods that need A^H (CGNR, QMR, BiCG, CGNE)
+ * then return CCG_ERR_UNSUPPORTED.  flags: CCG_OP_SYMMETRIC or 0.  Usable
+ * with ccg_matvec, ccg_solve and ccg_solve_refined (either operator); the
+ * batched solves and ccg_block_matvec need a dense operator.  Errors:
+ * CCG_ERR_INVALID for n < 1, a NULL matvec or unknown flags. */
+ccg_status ccg_op_callback(ccg_handle* h, ccg_dtype dtype, int64_t n, ccg_matvec_fn matvec, ccg_matvec_fn cmatvec,
+                           void* ctx, int flags, ccg_operator** op);
 /* Free an operator (not the caller's matrix). */
 ccg_status ccg_op_destroy(ccg_operator* op);
 /* Number of unknowns of an operator. */

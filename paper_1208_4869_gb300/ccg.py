@@ -29,6 +29,10 @@ OPT_TC_SPLIT = 2
 OPT_GMRES_RESTART = 3
 OPT_BICGSTAB_L = 4
 OPT_TC_EXACT = 5
+
+# ccg_matvec_fn: int (*)(void* ctx, int64_t n, const void* x, void* y, void* stream)
+MATVEC_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                             ctypes.c_void_p)
 SWEEP_N, SWEEP_C, SWEEP_BOTH, SWEEP_BLOCK, SWEEP_BLOCK_TC, SWEEP_BLOCK_EXACT = 0, 1, 2, 3, 4, 5
 
 _lib = None
@@ -87,6 +91,7 @@ def lib():
     L.ccg_op_dense.argtypes = [vp, i32, i64, vp, i64, i32, ctypes.POINTER(vp)]
     L.ccg_op_destroy.argtypes = [vp]
     L.ccg_op_dipole.argtypes = [vp, i32, i32, i32, i32, vp, dbl, dbl, dbl, ctypes.POINTER(vp)]
+    L.ccg_op_callback.argtypes = [vp, i32, i64, MATVEC_FN, MATVEC_FN, vp, i32, ctypes.POINTER(vp)]
     L.ccg_dipole_sites.restype = i64
     L.ccg_dipole_sites.argtypes = [vp]
     L.ccg_op_size.restype = i64
@@ -172,6 +177,26 @@ class Handle:
 
     def set_stream(self, stream):
         _check(lib().ccg_set_stream(self.h, _stream_ptr(stream)))
+
+    def op_callback(self, n, dtype, matvec, cmatvec=None, symmetric=False):
+        """ccg_op_callback: an operator given by Python callables matvec(x_ptr, y_ptr, stream_ptr) and,
+        optionally, cmatvec(...) that enqueue y = A x (resp. A^H x) for device vectors of n complex
+        values on the given CUDA stream and return 0 (the manual's matvec / cmatvec)."""
+        def wrap(f):
+            if f is None:
+                return MATVEC_FN()
+            def fn(ctx, nn, x, y, stream):
+                try:
+                    return int(f(x or 0, y or 0, stream or 0) or 0)
+                except Exception:  # an exception cannot cross the C boundary: report failure
+                    return 1
+            return MATVEC_FN(fn)
+        code = _dtype_code(dtype)
+        fns = (wrap(matvec), wrap(cmatvec))
+        op = ctypes.c_void_p()
+        _check(lib().ccg_op_callback(self.h, code, int(n), fns[0], fns[1], None,
+                                     OP_SYMMETRIC if symmetric else 0, ctypes.byref(op)))
+        return Operator(op, fns, code)
 
     def op_dense(self, A, symmetric=False):
         """ccg_op_dense on a CUDA tensor A (n x n, row-major, complex64/128); A is not copied."""

@@ -245,6 +245,33 @@ ccg_status ccg_op_dipole(ccg_handle* h, ccg_dtype dtype, int nx, int ny, int nz,
   return CCG_OK;
 }
 
+ccg_status ccg_op_callback(ccg_handle* h, ccg_dtype dtype, int64_t n, ccg_matvec_fn matvec, ccg_matvec_fn cmatvec,
+                           void* ctx, int flags, ccg_operator** op) {
+  if (!op) { set_error("ccg_op_callback: NULL output"); return CCG_ERR_INVALID; }
+  *op = nullptr;
+  if (!h || !matvec) { set_error("ccg_op_callback: NULL handle or matvec"); return CCG_ERR_INVALID; }
+  if (dtype != CCG_C64 && dtype != CCG_C128) { set_error("ccg_op_callback: bad dtype"); return CCG_ERR_INVALID; }
+  if (n < 1 || n > (int64_t(1) << 31)) { set_error("ccg_op_callback: need 1 <= n <= 2^31"); return CCG_ERR_INVALID; }
+  if (flags & ~CCG_OP_SYMMETRIC) { set_error("ccg_op_callback: unknown flags"); return CCG_ERR_INVALID; }
+  ccg_operator* o = new (std::nothrow) ccg_operator();
+  if (!o) { set_error("ccg_op_callback: host allocation failed"); return CCG_ERR_NOMEM; }
+  o->kind = CCG_OPK_CALLBACK;
+  o->dtype = dtype;
+  o->n = n;
+  o->flags = flags;
+  o->unit = 1;
+  o->cb_matvec = matvec;
+  o->cb_cmatvec = cmatvec;
+  o->cb_ctx = ctx;
+  *op = o;
+  return CCG_OK;
+}
+
+// Methods whose iterations apply A^H.
+static bool needs_ah(int method) {
+  return method == CCG_CGNR || method == CCG_QMR || method == CCG_BICG || method == CCG_CGNE;
+}
+
 int64_t ccg_dipole_sites(const ccg_operator* op) { return (op && op->kind == CCG_OPK_DIPOLE) ? op->dip.nsites : 0; }
 
 ccg_status ccg_op_destroy(ccg_operator* op) {
@@ -265,6 +292,10 @@ ccg_status ccg_matvec(ccg_handle* h, const ccg_operator* op, int trans, const vo
   if (trans != 0 && trans != 1) { set_error("ccg_matvec: trans must be 0 or 1"); return CCG_ERR_INVALID; }
   const size_t esz = op->dtype == CCG_C128 ? 16 : 8;
   if (!aligned(x, op->unit * esz) || !aligned(y, esz)) { set_error("ccg_matvec: misaligned vector"); return CCG_ERR_INVALID; }
+  if (trans && op->kind == CCG_OPK_CALLBACK && !op->cb_cmatvec) {
+    set_error("ccg_matvec: the callback operator has no cmatvec");
+    return CCG_ERR_UNSUPPORTED;
+  }
   return static_cast<ccg_status>(matvec_dense(h, op, trans, x, y));
 }
 
@@ -286,6 +317,10 @@ ccg_status ccg_solve(ccg_handle* h, ccg_method method, const ccg_operator* op, c
   }
   const size_t esz = op->dtype == CCG_C128 ? 16 : 8;
   if (!aligned(y, esz) || !aligned(x, op->unit * esz)) { set_error("ccg_solve: misaligned vector"); return CCG_ERR_INVALID; }
+  if (needs_ah(method) && op->kind == CCG_OPK_CALLBACK && !op->cb_cmatvec) {
+    set_error("ccg_solve: this method needs A^H and the callback operator has no cmatvec");
+    return CCG_ERR_UNSUPPORTED;
+  }
   return static_cast<ccg_status>(solve_dense(h, method, op, y, x, tol, maxit, res_hist, info));
 }
 
@@ -307,6 +342,10 @@ ccg_status ccg_solve_refined(ccg_handle* h, ccg_method method, const ccg_operato
     return CCG_ERR_INVALID;
   }
   if (!aligned(y, 16) || !aligned(x, 16)) { set_error("ccg_solve_refined: misaligned vector"); return CCG_ERR_INVALID; }
+  if (needs_ah(method) && op_in->kind == CCG_OPK_CALLBACK && !op_in->cb_cmatvec) {
+    set_error("ccg_solve_refined: this method needs A^H and the inner callback operator has no cmatvec");
+    return CCG_ERR_UNSUPPORTED;
+  }
   return static_cast<ccg_status>(
       solve_refined(h, method, op, op_in, y, x, tol, max_outer, inner_tol, inner_maxit, res_hist, inner_iters, info));
 }

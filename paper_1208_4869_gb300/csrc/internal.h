@@ -14,7 +14,7 @@ struct SolveState;
 void set_error(const std::string& msg);
 }  // namespace ccg
 
-enum { CCG_OPK_DENSE = 0, CCG_OPK_DIPOLE = 1 };
+enum { CCG_OPK_DENSE = 0, CCG_OPK_DIPOLE = 1, CCG_OPK_CALLBACK = 2 };
 
 // Device data of a discrete-dipole operator (owned by the operator).
 struct DipoleData {
@@ -42,6 +42,10 @@ struct ccg_operator {
   int unit = 1;  // complex numbers per 16-byte load (2 only for aligned complex64 with even n, lda)
   // dipole
   DipoleData dip;
+  // user callbacks (the manual's matvec / cmatvec)
+  ccg_matvec_fn cb_matvec = nullptr;
+  ccg_matvec_fn cb_cmatvec = nullptr;
+  void* cb_ctx = nullptr;
   // tensor-core copies of a complex64 dense matrix (made on first use)
   bool tc_ready = false;
   int tc_terms = 0;                            // bf16 terms per entry (2 or 3)
@@ -79,6 +83,8 @@ struct ccg_handle {
   double bytes_per_sweep[2 * CCG_SWEEP_KINDS] = {};
   // kernels launched by this handle
   int64_t launches = 0;
+  // first nonzero return of an operator callback during the current call
+  int cb_status = 0;
   // tensor-core block products: enabled flag, staging for split blocks and
   // the pipeline's error flag (first 256 bytes)
   int tc_mode = 1;   // 0 never, 1 refined inner solves and block products, 2 also plain batched solves

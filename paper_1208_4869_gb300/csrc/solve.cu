@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <string>
 #include <functional>
 #include <memory>
 
@@ -1803,10 +1804,20 @@ template <class R> struct Runner {
 
   // y = A x.  timed = false for products the device may skip (x0 = 0), which
   // would otherwise enter the sweep timing with a near-zero duration.
+  // A user operator's matvec or cmatvec, enqueued by the caller's function
+  // on this stream; the first nonzero return is kept on the handle.
+  void callback(bool conj, const cx<R>* x, cx<R>* y) {
+    const ccg_matvec_fn f = conj ? op->cb_cmatvec : op->cb_matvec;
+    const int rc = f ? f(op->cb_ctx, op->n, x, y, s) : -1;
+    if (rc != 0 && h->cb_status == 0) h->cb_status = rc;
+  }
+
   MvOut<R> apply_n(const cx<R>* x, cx<R>* y, const SolveState* st, bool timed = true) {
     if (timed) timing_begin(h);
     int* rec = timed ? timing_rec(h) : nullptr;
-    if (op->kind == CCG_OPK_DIPOLE) {
+    if (op->kind == CCG_OPK_CALLBACK) {
+      callback(false, x, y);
+    } else if (op->kind == CCG_OPK_DIPOLE) {
       dipole_apply(op, x, y, false, st, s, rec);
       h->launches += op->dip.kernels;
     } else {
@@ -1827,6 +1838,11 @@ template <class R> struct Runner {
   MvOut<R> apply_c(const cx<R>* x, cx<R>* y, const SolveState* st) {
     timing_begin(h);
     int* rec = timing_rec(h);
+    if (op->kind == CCG_OPK_CALLBACK) {
+      callback(true, x, y);
+      timing_end(h, kDt, CCG_SWEEP_C, d.sweep_bytes());
+      return plain(y);
+    }
     if (op->kind == CCG_OPK_DIPOLE) {
       dipole_apply(op, x, y, true, st, s, rec);
       h->launches += op->dip.kernels;
@@ -1852,7 +1868,7 @@ template <class R> struct Runner {
   // nsplit in P2); others by two applications into y1, y2.
   void apply_both(const cx<R>* x1, const cx<R>* x2, cx<R>* y1, cx<R>* y2, MvOut<R>& o1, MvOut<R>& o2,
                   const SolveState* st) {
-    if (op->kind == CCG_OPK_DIPOLE) {
+    if (op->kind != CCG_OPK_DENSE) {
       o1 = apply_n(x1, y1, st);
       o2 = apply_c(x2, y2, st);
       return;
@@ -1898,6 +1914,16 @@ static int classify(const void* y, const void* x, bool* host) {
 // One solve on device vectors y, x with the workspace w: r0, the method's
 // iterations, polling; returns with the stream idle and the final state in
 // *fin.  x0_zero skips the A x0 sweep (x is then set to zero on entry).
+// A failed operator callback ends the call: read and clear the handle's
+// callback status.
+static int cb_check(ccg_handle* h) {
+  if (h->cb_status == 0) return CCG_OK;
+  const int rc = h->cb_status;
+  h->cb_status = 0;
+  set_error("operator callback returned " + std::to_string(rc));
+  return CCG_ERR_CUDA;
+}
+
 template <class R>
 static int solve_core(ccg_handle* h, int method, const ccg_operator* op, const Ws<R>& w, const cx<R>* y, cx<R>* x,
                       double tol, int maxit, bool x0_zero, SolveState* fin) {
@@ -2106,6 +2132,8 @@ static int solve_core(ccg_handle* h, int method, const ccg_operator* op, const W
   // Enqueue iterations in chunks; poll the device record of the chunk before.
   Poll* pin = static_cast<Poll*>(h->pinned);
   const int chunk = poll_chunk(run.d);
+  int rc0 = cb_check(h);   // a product enqueued before the loop may have failed
+  if (rc0 != CCG_OK) return rc0;
   int launched = 0, npoll = 0;
   for (;;) {
     if (launched < maxit) {
@@ -2113,6 +2141,10 @@ static int solve_core(ccg_handle* h, int method, const ccg_operator* op, const W
       for (int j = 0; j < c; ++j) step();
       launched += c;
       CCG_CUDA(cudaGetLastError());
+      if (h->cb_status) {
+        CCG_CUDA(cudaStreamSynchronize(s));
+        return cb_check(h);
+      }
     }
     const int slot = npoll & 1;
     CCG_CUDA(cudaMemcpyAsync(&pin[slot], &st->poll, sizeof(Poll), cudaMemcpyDeviceToHost, s));
@@ -2125,6 +2157,7 @@ static int solve_core(ccg_handle* h, int method, const ccg_operator* op, const W
     if (launched >= maxit) break;
   }
   CCG_CUDA(cudaStreamSynchronize(s));
+  if ((rc0 = cb_check(h)) != CCG_OK) return rc0;
   CCG_CUDA(cudaMemcpy(fin, st, sizeof(SolveState), cudaMemcpyDeviceToHost));
   if (!fin->poll.done) {  // cannot happen: maxit bounds the loop and the last iteration stops the solve
     set_error("solve did not record its end");
@@ -2147,6 +2180,7 @@ static int true_residual(ccg_handle* h, const ccg_operator* op, const Ws<R>& w, 
   tr.ax = run.apply_n(x, w.vec[11], w.st);
   run.phase(tr);
   CCG_CUDA(cudaGetLastError());
+  if (int rc = cb_check(h)) return rc;
   double rr = 0.0;
   CCG_CUDA(cudaMemcpyAsync(&rr, w.scratch, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CCG_CUDA(cudaStreamSynchronize(h->stream));
@@ -2307,6 +2341,7 @@ int solve_refined(ccg_handle* h, int method, const ccg_operator* op, const ccg_o
     rp.ax = run.apply_n(x, w.vec[0], w.st, outer > 0);
     run.phase(rp);
     CCG_CUDA(cudaGetLastError());
+    if ((rc = cb_check(h)) != CCG_OK) return rc;
     CCG_CUDA(cudaMemcpyAsync(h->pinned, &w.st->poll, sizeof(Poll), cudaMemcpyDeviceToHost, s));
     CCG_CUDA(cudaStreamSynchronize(s));
     const Poll pl = *static_cast<Poll*>(h->pinned);
@@ -2370,7 +2405,7 @@ template <class R> static int matvec_t(ccg_handle* h, const ccg_operator* op, in
     }
   }
   CCG_CUDA(cudaGetLastError());
-  return CCG_OK;
+  return cb_check(h);
 }
 
 int matvec_dense(ccg_handle* h, const ccg_operator* op, int trans, const void* x, void* y) {

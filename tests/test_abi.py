@@ -57,3 +57,16 @@ def test_binding_raises_when_library_missing(monkeypatch, tmp_path):
     monkeypatch.setattr(ccg, "_lib", None)
     with pytest.raises(ImportError):
         ccg.lib()
+
+
+def test_callback_operator_rejects_bad_arguments_without_gpu(libpath):
+    """ccg_op_callback validates its arguments before touching a device."""
+    L = ctypes.CDLL(libpath)
+    fn = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                          ctypes.c_void_p)
+    L.ccg_op_callback.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, fn, fn, ctypes.c_void_p,
+                                  ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+    op = ctypes.c_void_p(1)
+    good = fn(lambda ctx, n, x, y, s: 0)
+    assert L.ccg_op_callback(None, 1, 8, good, fn(), None, 0, ctypes.byref(op)) == -1   # no handle
+    assert not op.value
