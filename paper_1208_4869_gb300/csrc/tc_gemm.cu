@@ -291,14 +291,13 @@ static int tc_product_t(ccg_handle* h, ccg_operator* op, const float2* X, float2
       return CCG_ERR_CUDA;
     }
   }
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(tc::gemm_bf16_split<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES) !=
-        cudaSuccess) {
-      set_error("tensor-core kernel: shared memory opt-in failed");
-      return CCG_ERR_CUDA;
-    }
-    attr = true;
+  // once per process: a function-local static is initialised exactly once,
+  // also when several threads (serving slots) make their first product together
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(tc::gemm_bf16_split<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES);
+  if (attr != cudaSuccess) {
+    set_error("tensor-core kernel: shared memory opt-in failed");
+    return CCG_ERR_CUDA;
   }
   const int Nr = 2 * k;
   dim3 grid((unsigned)((Nr + G::BN - 1) / G::BN), (unsigned)((n + tc::BM - 1) / tc::BM));

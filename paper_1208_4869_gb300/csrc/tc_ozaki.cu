@@ -449,14 +449,13 @@ static int oz_product_t(ccg_handle* h, ccg_operator* op, const cx<R>* X, cx<R>* 
       return CCG_ERR_CUDA;
     }
   }
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(ozaki_gemm<S, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES) !=
-        cudaSuccess) {
-      set_error("exact tensor-core kernel: shared memory opt-in failed");
-      return CCG_ERR_CUDA;
-    }
-    attr = true;
+  // once per process: a function-local static is initialised exactly once,
+  // also when several threads (serving slots) make their first product together
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(ozaki_gemm<S, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES);
+  if (attr != cudaSuccess) {
+    set_error("exact tensor-core kernel: shared memory opt-in failed");
+    return CCG_ERR_CUDA;
   }
   const int Nr = 2 * k;
   dim3 grid((unsigned)((Nr + G::BN - 1) / G::BN), (unsigned)((n + BM - 1) / BM));
