@@ -317,3 +317,16 @@ def test_refined_batched_same_with_and_without_exact_products(ccg):
         assert np.all(np.linalg.norm(Y - A @ Xh, axis=0) / np.linalg.norm(Y, axis=0) <= 1e-10)
         out.append(Xh)
     assert np.linalg.norm(out[0] - out[1]) / np.linalg.norm(out[0]) < 1e-9
+
+
+@pytest.mark.parametrize("dtype", [np.complex128, np.complex64])
+def test_exact_products_fallback_and_widest_block(ccg, dtype):
+    """n not divisible by 4 falls back to the CUDA-core product (same
+    accuracy class); n = 4 with the widest block, 256 right-hand sides."""
+    for n, k in ((258, 5), (4, 256)):
+        A, _ = W.dense_system(n, 1.0, n, dtype=dtype)
+        X = W.dense_rhs_block(n, k, seed=3, dtype=dtype)
+        Y = product(ccg, A, X)
+        ref = A.astype(np.complex128) @ X.astype(np.complex128)
+        e = np.abs(Y - ref).max() / np.abs(ref).max()
+        assert e < (1e-13 if dtype == np.complex128 else 2e-6), (n, k, e)
