@@ -329,4 +329,4 @@ def test_exact_products_fallback_and_widest_block(ccg, dtype):
         Y = product(ccg, A, X)
         ref = A.astype(np.complex128) @ X.astype(np.complex128)
         e = np.abs(Y - ref).max() / np.abs(ref).max()
-        assert e < (1e-13 if dtype == np.complex128 else 2e-6), (n, k, e)
+        assert e < (1e-13 if dtype == np.complex128 else 2e-5), (n, k, e)   # fp32 CUDA-core bound
