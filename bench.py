@@ -422,6 +422,8 @@ def run_serving(args):
     span = max(r["t_done"] for r in res) - first
     lat = sorted(r["t_done"] - r["t_submit"] for r in res)
     ok = all(r["status"] == 0 for r in res)
+    failures = [dict(req=reqs[i], status=r["status"], iters=r["iters"], relres=r["relres"], n=r["n"],
+                     nrhs=r["nrhs"], slot=r["slot"]) for i, r in enumerate(res) if r["status"] != 0]
     span_max = reduce_max(span, world)
     solves = reduce_sum(len(res), world)
     nb = min(args.baseline_requests, len(reqs))
@@ -439,6 +441,7 @@ def run_serving(args):
                        "l2": "inputs larger than L2 (matrices up to 1.07 GB)"},
             "latency_ms": {"p50": p(0.5), "p99": p(0.99), "max": 1e3 * lat[-1]},
             "all_converged": ok,
+            "failures": {"count": len(failures), "first": failures[:8]},
             "other_paths": {"fp64_one_at_a_time": {"value": nb / bspan, "unit": "solves/s", "requests": nb,
                                                    "all_converged": all(r["status"] == 0 for r in base)}},
             "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clk,
