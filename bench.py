@@ -47,6 +47,8 @@ def parse_args(argv=None):
     p.add_argument("--workload", choices=["dense", "dipole", "batched", "serving"], default="dense")
     p.add_argument("--requests", type=int, default=200)
     p.add_argument("--slots", type=int, default=4)
+    p.add_argument("--serving-kinds", choices=["both", "dense", "dipole"], default="both",
+                   help="keep only these requests of the serving stream")
     p.add_argument("--baseline-requests", type=int, default=40)
     p.add_argument("--nrhs", type=int, default=256)
     p.add_argument("--n", type=int, default=8192)
@@ -396,6 +398,9 @@ def run_serving(args):
     dist_init(world, "nccl")
     B.build()
     arrivals, reqs = serving_stream(args.requests)
+    if args.serving_kinds != "both":
+        keep = [i for i, r in enumerate(reqs) if r["kind"] == args.serving_kinds]
+        arrivals, reqs = arrivals[keep], [reqs[i] for i in keep]
 
     def serve(slots, items, times, mode):
         sv = ccg.Server(device=local, slots=slots, budget_bytes=120 << 30)

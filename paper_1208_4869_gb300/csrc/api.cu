@@ -85,7 +85,7 @@ void timing_collect(ccg_handle* h) {
   if (h->skip_rec && pairs > 0) {
     const size_t m = std::min(pairs, h->skip_cap);
     if (cudaMemcpy(skipped.data(), h->skip_rec, m * sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess)
-      cudaMemset(h->skip_rec, 0, m * sizeof(int));
+      cudaMemsetAsync(h->skip_rec, 0, m * sizeof(int), h->stream);
   }
   for (size_t i = 0; i + 1 < h->tev_used; i += 2) {
     float ms = 0.f;
@@ -436,7 +436,7 @@ ccg_status ccg_timing_enable(ccg_handle* h, int enable) {
   if (enable && !h->skip_rec) {
     const size_t cap = (size_t)1 << 20;  // sweeps between two collections
     if (cudaMalloc(&h->skip_rec, cap * sizeof(int)) != cudaSuccess ||
-        cudaMemset(h->skip_rec, 0, cap * sizeof(int)) != cudaSuccess) {
+        cudaMemsetAsync(h->skip_rec, 0, cap * sizeof(int), h->stream) != cudaSuccess) {
       cudaGetLastError();
       if (h->skip_rec) cudaFree(h->skip_rec);
       h->skip_rec = nullptr;

@@ -650,12 +650,15 @@ template <class R> static std::vector<cx<R>> twiddles(int n) {
 }
 
 // Per-operator device data, owned through ccg_operator::dip.
-template <class R> static int upload_twiddles(ccg_operator* op, const DipGeom& g) {
+// Uploads go on the creation stream s: a plain cudaMemcpy from pageable
+// memory may return before its DMA lands and is not ordered with a
+// non-blocking stream's kernels.
+template <class R> static int upload_twiddles(ccg_operator* op, const DipGeom& g, cudaStream_t s) {
   const int dims[3] = {g.Mx, g.My, g.Mz};
   for (int a = 0; a < 3; ++a) {
     std::vector<cx<R>> w = twiddles<R>(dims[a]);
     DIP_CUDA(cudaMalloc(&op->dip.tw[a], w.size() * sizeof(cx<R>)));
-    DIP_CUDA(cudaMemcpy(op->dip.tw[a], w.data(), w.size() * sizeof(cx<R>), cudaMemcpyHostToDevice));
+    DIP_CUDA(cudaMemcpyAsync(op->dip.tw[a], w.data(), w.size() * sizeof(cx<R>), cudaMemcpyHostToDevice, s));
   }
   return CCG_OK;
 }
@@ -683,7 +686,7 @@ template <class R> static int build_ghat(ccg_operator* op, const DipGeom& g, cud
   for (int a = 0; a < 3 && rc == CCG_OK; ++a) {
     std::vector<double2> w = twiddles<double>(dims[a]);
     if (cudaMalloc(&twd[a], w.size() * sizeof(double2)) != cudaSuccess ||
-        cudaMemcpy(twd[a], w.data(), w.size() * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMemcpyAsync(twd[a], w.data(), w.size() * sizeof(double2), cudaMemcpyHostToDevice, s) != cudaSuccess) {
       set_error(std::string("ccg_op_dipole: ") + cudaGetErrorString(cudaGetLastError()));
       rc = CCG_ERR_CUDA;
     }
@@ -733,9 +736,9 @@ template <class R> static int create_t(ccg_operator* op, const uint8_t* occ, cud
   op->dip.nsites = count;
   op->n = 3 * count;
   DIP_CUDA(cudaMalloc(&op->dip.idx, cells * sizeof(int)));
-  DIP_CUDA(cudaMemcpy(op->dip.idx, idx.data(), cells * sizeof(int), cudaMemcpyHostToDevice));
+  DIP_CUDA(cudaMemcpyAsync(op->dip.idx, idx.data(), cells * sizeof(int), cudaMemcpyHostToDevice, s));
   DIP_CUDA(cudaMalloc(&op->dip.work, (size_t)3 * g.G * sizeof(cx<R>)));
-  int rc = upload_twiddles<R>(op, geom(op));
+  int rc = upload_twiddles<R>(op, geom(op), s);
   if (rc != CCG_OK) return rc;
   rc = build_ghat<R>(op, geom(op), s);
   if (rc != CCG_OK) return rc;

@@ -321,7 +321,7 @@ int tc_check_error(ccg_handle* h) {
   int e = 0;
   if (cudaMemcpy(&e, h->tc_buf, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return CCG_ERR_CUDA;
   if (e) {
-    cudaMemset(h->tc_buf, 0, sizeof(int));
+    cudaMemsetAsync(h->tc_buf, 0, sizeof(int), h->stream);
     set_error("tensor-core pipeline wait timed out");
     return CCG_ERR_TIMEOUT;
   }

@@ -478,7 +478,7 @@ int oz_check_error(ccg_handle* h) {
   int e = 0;
   if (cudaMemcpy(&e, h->oz_buf, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return CCG_ERR_CUDA;
   if (e) {
-    cudaMemset(h->oz_buf, 0, sizeof(int));
+    cudaMemsetAsync(h->oz_buf, 0, sizeof(int), h->stream);
     set_error("exact tensor-core pipeline wait timed out");
     return CCG_ERR_TIMEOUT;
   }

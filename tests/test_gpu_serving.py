@@ -118,3 +118,28 @@ def test_generated_problem_matches_host_philox(ccg):
     ref = O.solve(O.DenseOp(np.ascontiguousarray(A)), "bicgstab", np.ascontiguousarray(Y[:, 0]), tol=1e-12,
                   maxit=200)
     assert np.linalg.norm(X[:, 0] - ref.x) / np.linalg.norm(ref.x) < 1e-9
+
+
+def test_concurrent_operator_creation_under_load(ccg):
+    """Sixteen slots that create dipole operators of several sizes at the same
+    time, on non-blocking streams, while dense requests load the GPU: every
+    mixed-precision dipole request converges and equals its result from a
+    single slot (operator uploads must be ordered with the slot's stream)."""
+    reqs = []
+    for i in range(32):
+        reqs.append(dict(kind="dipole", L=[16, 24, 32, 48][i % 4], tol=1e-10))
+        reqs.append(dict(kind="dense", n=1024 + 256 * (i % 4), nrhs=1 + i % 8, seed=100 + i, tol=1e-10))
+    sv = ccg.Server(slots=16)
+    tickets = [sv.submit(keep_x=True, **r) for r in reqs]
+    got = [sv.wait(t, size_of(r)) for t, r in zip(tickets, reqs)]
+    sv.close()
+    alone = {}
+    sv = ccg.Server(slots=1)
+    for L in (16, 24, 32, 48):
+        r = dict(kind="dipole", L=L, tol=1e-10)
+        alone[L] = sv.wait(sv.submit(keep_x=True, **r), size_of(r))
+    sv.close()
+    for r, (res, x) in zip(reqs, got):
+        assert res["status"] == 0 and res["relres"] <= 3e-10, (r, res)
+        if r["kind"] == "dipole":
+            assert np.array_equal(x, alone[r["L"]][1]), r
