@@ -304,7 +304,10 @@ ccg_status ccg_block_matvec(ccg_handle* h, const ccg_operator* op, int64_t nrhs,
  * digit pairs of S significance levels are summed exactly by bf16 MMAs with
  * fp32 accumulation and combined in int64.  The result is as accurate as a
  * GEMM in the operands' precision (error ~ K 2^-53, resp. K 2^-24, times
- * max|a| max|x| per entry).  0 uses CUDA cores for them. */
+ * max|a| max|x| per entry).  0 uses CUDA cores for them.
+ * ccg_set_option returns CCG_ERR_INVALID (and leaves the handle unchanged)
+ * for a NULL handle, an unknown option or a value out of range; options
+ * apply to the handle's later calls. */
 #define CCG_OPT_TENSOR_CORES 1
 #define CCG_OPT_TC_SPLIT 2
 #define CCG_OPT_GMRES_RESTART 3
@@ -392,7 +395,10 @@ typedef enum {
  * stream.  ccg_timing_read returns, for one precision (ccg_dtype) and one
  * sweep kind, the number of sweeps timed since the last reset, their total
  * device milliseconds, and the algorithmic bytes of one sweep (the matrix
- * bytes read).  It synchronises the handle's stream. */
+ * bytes read).  It synchronises the handle's stream.  ccg_timing_reset
+ * synchronises the stream and sets every count and total to zero.  All three
+ * return CCG_ERR_INVALID for a NULL handle (ccg_timing_read also for a bad
+ * dtype or kind). */
 ccg_status ccg_timing_enable(ccg_handle* h, int enable);
 ccg_status ccg_timing_read(ccg_handle* h, int dtype, int kind, int64_t* sweeps, double* total_ms,
                            double* bytes_per_sweep);
