@@ -144,7 +144,12 @@ uint64_t estimate_bytes(const ccg_request& r) {
     return (uint64_t)(40.0 * N3 * 16 + 2.0 * G * 16);
   }
   const double n = (double)r.n, k = std::max(1, r.nrhs);
-  return (uint64_t)(16 * n * n + 8 * n * n + 8 * n * n + 40.0 * n * std::max(k, 8.0) * 16 + 64.0 * n * 16);
+  // complex128 and complex64 matrices, the split-bf16 terms, blocks and workspace
+  double b = 16 * n * n + 8 * n * n + 8 * n * n + 40.0 * n * std::max(k, 8.0) * 16 + 64.0 * n * 16;
+  // batched requests also keep the exact products' digit slices of both
+  // matrices (8 and 4 bf16 slices of n x 2n) where those products apply
+  if (k > 1 && r.n % 4 == 0 && 2 * r.n <= 65536) b += 32 * n * n + 16 * n * n;
+  return (uint64_t)b;
 }
 
 int run_dense(ccg_handle* h, cudaStream_t s, const ccg_request& r, ccg_result& res, std::vector<double2>* xout) {
