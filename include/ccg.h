@@ -167,7 +167,13 @@ typedef int (*ccg_matvec_fn)(void* ctx, int64_t n, const void* x, void* y, void*
  * CCG_ERR_INVALID for n < 1, a NULL matvec or unknown flags. */
 ccg_status ccg_op_callback(ccg_handle* h, ccg_dtype dtype, int64_t n, ccg_matvec_fn matvec, ccg_matvec_fn cmatvec,
                            void* ctx, int flags, ccg_operator** op);
-/* Free an operator (not the caller's matrix). */
+/* Free an operator (not the caller's matrix).  A dense operator's
+ * tensor-core copies (split-bf16 terms, digit slices: made by its first
+ * block product of each kind, on that call's stream) are freed in stream
+ * order on the stream that made them, so an operator must be destroyed
+ * before that stream is.  Calls on other streams that use the operator
+ * after such a first call must be ordered after it (synchronise that
+ * call's stream, or wait on an event recorded after it). */
 ccg_status ccg_op_destroy(ccg_operator* op);
 /* Number of unknowns of an operator. */
 int64_t ccg_op_size(const ccg_operator* op);
