@@ -429,15 +429,17 @@ int64_t ccg_launch_count(const ccg_handle* h);
  * stream) and the call returns without synchronising.
  *
  * Scratch: the partial sums live in one fixed device array of
- * CCG_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads
- * the library holds until the process exits.  n above CCG_NOALLOC_MAX_N is
+ * CCG_NOALLOC_SCRATCH_BYTES inside the library, resident on each device
+ * from the first ccg_matvec_h_noalloc call there (or from library load
+ * under eager module loading) until the process exits.  n above CCG_NOALLOC_MAX_N is
  * rejected with CCG_ERR_INVALID before anything is launched.  All calls on a
  * device share that array, so two calls whose work overlaps on the GPU (on
  * different streams, or from different threads) race and give wrong results:
  * order them on one stream or synchronise between them.  Each call writes
  * every scratch entry it reads, so nothing carries over from the last call.
  * The first call on each device looks up the array's device address (with
- * that device current); make that first call before any stream capture.
+ * that device current) and loads every kernel the entry point uses (both
+ * precisions); make that first call before any stream capture.
  * Returns CCG_OK, CCG_ERR_INVALID (NULL or misaligned pointer, bad dtype,
  * n < 1, lda < n, n too large) or CCG_ERR_CUDA (no device, launch error). */
 #define CCG_NOALLOC_MAX_N 65536

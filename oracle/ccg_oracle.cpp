@@ -67,6 +67,9 @@
 #include <cstring>
 #include <memory>
 #include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace {
 
@@ -122,22 +125,34 @@ template <class R> struct Operator {
   virtual void apply_h(const C<R>* x, C<R>* y) const = 0;
 };
 
-// Dense row-major A with leading dimension lda; plain double loops.
+// Dense row-major A with leading dimension lda; plain double loops.  Each
+// output element is one sum taken in index order (j for A x, i for A^H x).
+// The OpenMP build (liboracle_omp.so, the all-core CPU baseline) only hands
+// independent output elements to different threads -- rows of A x, blocks
+// of columns of A^H x -- so every sum keeps its order and both builds give
+// bit-identical results; the plain build ignores the pragmas.
 template <class R> struct Dense : Operator<R> {
   const C<R>* A;
   int64_t lda;
   Dense(int64_t n_, const C<R>* A_, int64_t lda_) : A(A_), lda(lda_) { this->n = n_; }
   void apply(const C<R>* x, C<R>* y) const override {
-    for (int64_t i = 0; i < this->n; ++i) {
+    const int64_t n = this->n;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
       C<R> acc = 0;
-      for (int64_t j = 0; j < this->n; ++j) acc += A[i * lda + j] * x[j];
+      for (int64_t j = 0; j < n; ++j) acc += A[i * lda + j] * x[j];
       y[i] = acc;
     }
   }
   void apply_h(const C<R>* x, C<R>* y) const override {
-    for (int64_t j = 0; j < this->n; ++j) y[j] = 0;
-    for (int64_t i = 0; i < this->n; ++i)
-      for (int64_t j = 0; j < this->n; ++j) y[j] += std::conj(A[i * lda + j]) * x[i];
+    const int64_t n = this->n, cb = 256;
+#pragma omp parallel for schedule(static)
+    for (int64_t j0 = 0; j0 < n; j0 += cb) {
+      const int64_t j1 = j0 + cb < n ? j0 + cb : n;
+      for (int64_t j = j0; j < j1; ++j) y[j] = 0;
+      for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = j0; j < j1; ++j) y[j] += std::conj(A[i * lda + j]) * x[i];
+    }
   }
 };
 
@@ -966,6 +981,14 @@ struct OpBox {
 extern "C" {
 
 int orc_abi_version() { return 1; }
+// Threads the dense products may use: 1 in the plain build.
+int orc_threads() {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 // Restart length m of GMRES(m) for later solves (1 <= m <= 256).
 void orc_set_restart(int m) { g_restart = m < 1 ? 1 : (m > 256 ? 256 : m); }

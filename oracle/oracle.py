@@ -19,18 +19,21 @@ METHODS = {"bicgstab": BICGSTAB, "cgnr": CGNR, "qmr": QMR, "cocg": COCG, "cocr":
            "gmres": GMRES, "cgs": CGS, "cgne": CGNE, "tfqmr": TFQMR, "bicgstabl": BICGSTABL}
 OK, NOT_CONVERGED, BREAKDOWN, INVALID = 0, 1, 2, -1
 
-_lib = None
+_libs = {}
 _lock = threading.Lock()
 
 
-def lib():
-    global _lib
+def lib(parallel=False):
+    """The serial oracle library, or with parallel=True its OpenMP build
+    (same source; the dense products' independent output elements on all
+    allowed host cores, bit-identical results)."""
     with _lock:
-        if _lib is None:
-            path = _build.build()
+        if parallel not in _libs:
+            path = _build.build_omp() if parallel else _build.build()
             L = ctypes.CDLL(path)
             vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
             L.orc_abi_version.restype = i32
+            L.orc_threads.restype = i32
             L.orc_op_dense_c128.restype = vp
             L.orc_op_dense_c128.argtypes = [i64, i64, vp, i32]
             L.orc_op_dense_c64.restype = vp
@@ -54,8 +57,13 @@ def lib():
             L.orc_fft3d.argtypes = [vp, i64, i64, i64, i32]
             L.orc_set_restart.argtypes = [i32]
             L.orc_set_bicgstab_l.argtypes = [i32]
-            _lib = L
-    return _lib
+            _libs[parallel] = L
+    return _libs[parallel]
+
+
+def threads(parallel=False):
+    """Host threads the dense products of that build use."""
+    return int(lib(parallel).orc_threads())
 
 
 def _ptr(a):
@@ -65,22 +73,23 @@ def _ptr(a):
 class _Op:
     """Owns an oracle operator handle and the arrays it points into."""
 
-    def __init__(self, handle, n, dtype, keep=()):
+    def __init__(self, handle, n, dtype, keep=(), L=None):
         self.h = handle
         self.n = int(n)
         self.dtype = np.dtype(dtype)
         self._keep = keep
+        self.L = lib() if L is None else L   # the library that owns the handle
 
     def __del__(self):
         if getattr(self, "h", None):
-            lib().orc_op_destroy(self.h)
+            self.L.orc_op_destroy(self.h)
             self.h = None
 
     def matvec(self, x, trans=False):
         """A x (trans=False) or A^H x (trans=True)."""
         x = np.ascontiguousarray(x, dtype=self.dtype)
         y = np.empty(self.n, dtype=self.dtype)
-        fn = lib().orc_matvec_c128 if self.dtype == np.complex128 else lib().orc_matvec_c64
+        fn = self.L.orc_matvec_c128 if self.dtype == np.complex128 else self.L.orc_matvec_c64
         fn(self.h, int(bool(trans)), _ptr(x), _ptr(y))
         return y
 
@@ -89,17 +98,19 @@ class DenseOp(_Op):
     """Dense row-major complex matrix (complex128 or complex64).
 
     symmetric=True marks A = A^T (verified here exactly), which COCG needs.
+    parallel=True applies it with the OpenMP build (same results).
     """
 
-    def __init__(self, A, symmetric=False):
+    def __init__(self, A, symmetric=False, parallel=False):
         A = np.ascontiguousarray(A)
         assert A.ndim == 2 and A.shape[0] == A.shape[1]
         assert A.dtype in (np.complex128, np.complex64)
         if symmetric:
             assert np.array_equal(A, A.T), "matrix is not complex symmetric"
         n = A.shape[0]
-        fn = lib().orc_op_dense_c128 if A.dtype == np.complex128 else lib().orc_op_dense_c64
-        super().__init__(fn(n, n, _ptr(A), int(bool(symmetric))), n, A.dtype, keep=(A,))
+        L = lib(parallel)
+        fn = L.orc_op_dense_c128 if A.dtype == np.complex128 else L.orc_op_dense_c64
+        super().__init__(fn(n, n, _ptr(A), int(bool(symmetric))), n, A.dtype, keep=(A,), L=L)
 
 
 class DipoleOp(_Op):
@@ -149,6 +160,7 @@ class _View(_Op):
         self.h = owner.h
         self.n = owner.n
         self.dtype = np.dtype(dtype)
+        self.L = owner.L
         self._owner = owner
 
     def __del__(self):
@@ -175,14 +187,15 @@ def solve(op, method, y, x0=None, tol=1e-10, maxit=1000, want_tau=False, restart
     """Run one oracle method; returns SolveResult with hist[k] = ||r_k||/||y||
     (restart: the cycle length m of GMRES(m); ell: the degree of BiCGstab(l))."""
     m = METHODS[method] if isinstance(method, str) else int(method)
-    lib().orc_set_restart(int(restart))
-    lib().orc_set_bicgstab_l(int(ell))
+    L = op.L
+    L.orc_set_restart(int(restart))
+    L.orc_set_bicgstab_l(int(ell))
     y = np.ascontiguousarray(y, dtype=op.dtype)
     x = np.zeros(op.n, dtype=op.dtype) if x0 is None else np.array(x0, dtype=op.dtype, copy=True)
     hist = np.full(maxit + 1, np.nan)
     tau = np.full(maxit + 1, np.nan) if want_tau else None
     out = np.zeros(3, dtype=np.int32)
-    fn = lib().orc_solve_c128 if op.dtype == np.complex128 else lib().orc_solve_c64
+    fn = L.orc_solve_c128 if op.dtype == np.complex128 else L.orc_solve_c64
     fn(op.h, m, _ptr(y), _ptr(x), float(tol), int(maxit), _ptr(out), _ptr(hist),
        _ptr(tau) if want_tau else ctypes.c_void_p(0))
     it = int(out[0])
@@ -196,13 +209,15 @@ def refine(op64, op32, method, y, x0=None, tol=1e-10, max_outer=20, inner_tol=1e
     Returns (x, outer_steps, status, inner_iterations, hist_outer).
     """
     m = METHODS[method] if isinstance(method, str) else int(method)
-    lib().orc_set_restart(int(restart))
-    lib().orc_set_bicgstab_l(int(ell))
+    L = op64.L
+    assert op32.L is L, "both operators must come from the same oracle build"
+    L.orc_set_restart(int(restart))
+    L.orc_set_bicgstab_l(int(ell))
     y = np.ascontiguousarray(y, dtype=np.complex128)
     x = np.zeros(op64.n, dtype=np.complex128) if x0 is None else np.array(x0, dtype=np.complex128, copy=True)
     hist = np.full(max_outer + 1, np.nan)
     out = np.zeros(4, dtype=np.int32)
-    lib().orc_refine(op64.h, op32.h, m, _ptr(y), _ptr(x), float(tol), int(max_outer), float(inner_tol),
+    L.orc_refine(op64.h, op32.h, m, _ptr(y), _ptr(x), float(tol), int(max_outer), float(inner_tol),
                      int(inner_maxit), _ptr(out), _ptr(hist))
     return x, int(out[0]), int(out[1]), int(out[3]), hist[: int(out[0]) + 1]
 

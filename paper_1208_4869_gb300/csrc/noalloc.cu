@@ -4,7 +4,8 @@
 // The column-tiled sweep (gemv.cuh, gemv_tile) leaves one partial vector per
 // row range; here those partials live in a fixed file-scope device array
 // instead of a handle's workspace, and a small kernel sums them into y.
-// Every GPU that loads this library holds the array until the process exits.
+// The array is resident on a device from the first call there (or from
+// library load under eager module loading) until the process exits.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -23,6 +24,16 @@ constexpr int kMaxDevices = 64;
 // Partial sums of the sweep.  Shared by every call on a device; each call
 // overwrites every entry it later reads, so nothing needs clearing.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+template <class R>
+__global__ void __launch_bounds__(kBlock) sum_partials(const cx<R>* __restrict__ P, int nparts, int64_t n,
+                                                       cx<R>* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock) {
+    cx<R> s = P[i];
+    for (int q = 1; q < nparts; ++q) s = cadd(s, P[(int64_t)q * n + i]);
+    y[i] = s;
+  }
+}
 
 struct DeviceSetup {
   bool ready = false;
@@ -61,22 +72,27 @@ int setup_current_device(DeviceSetup** out) {
       cudaGetLastError();
       sms = 1;
     }
+    // Load every kernel this entry point can launch now, so that under lazy
+    // module loading no later call (of either precision or load width)
+    // loads a kernel, e.g. inside a stream capture.
+    const void* kernels[] = {(const void*)gemv_tile_h<double, 1, 4>, (const void*)gemv_tile_h<float, 1, 4>,
+                             (const void*)gemv_tile_h<float, 2, 4>, (const void*)sum_partials<double>,
+                             (const void*)sum_partials<float>};
+    for (const void* k : kernels) {
+      cudaFuncAttributes attr;
+      const cudaError_t ek = cudaFuncGetAttributes(&attr, k);
+      if (ek != cudaSuccess) {
+        cudaGetLastError();
+        set_error(std::string("ccg_matvec_h_noalloc: cannot load a kernel: ") + cudaGetErrorString(ek));
+        return CCG_ERR_CUDA;
+      }
+    }
     s.scratch = p;
     s.num_sms = sms;
     s.ready = true;
   }
   *out = &s;
   return CCG_OK;
-}
-
-template <class R>
-__global__ void __launch_bounds__(kBlock) sum_partials(const cx<R>* __restrict__ P, int nparts, int64_t n,
-                                                       cx<R>* __restrict__ y) {
-  for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock) {
-    cx<R> s = P[i];
-    for (int q = 1; q < nparts; ++q) s = cadd(s, P[(int64_t)q * n + i]);
-    y[i] = s;
-  }
 }
 
 template <class R>
@@ -96,6 +112,9 @@ int run(const DeviceSetup& dev, int64_t n, const void* A_, int64_t lda, const vo
   const int64_t cap_rows = (n + kWarps - 1) / kWarps;
   ns = ns > 32 ? 32 : ns;
   ns = ns > cap_rows ? cap_rows : ns;
+  // Guard for GPUs with many more SMs: on 152 SMs ns * n stays below
+  // 4 * 152 * 128 + n (about 0.2 M elements at the n cap), far inside the
+  // array, so this never trims there.
   while (ns > 1 && (size_t)ns * (size_t)n * sizeof(cx<R>) > kScratchBytes) --ns;
   const int64_t rows_per_range = (n + ns - 1) / ns;
   const int nsplit = (int)((n + rows_per_range - 1) / rows_per_range);

@@ -59,3 +59,32 @@ def test_bench_defaults():
     assert d.L == 64 and d.methods == "cocg,bicgstab" and d.tol == 1e-8
     b = bench.parse_args(["--workload", "batched"])
     assert b.nrhs == 256 and b.methods == "bicgstab"
+    assert a.default_run and not a.no_other and a.requests == 2000 and a.baseline_requests >= 200
+    assert not d.default_run and not b.default_run
+
+
+def test_cpu_baseline_rows_and_reference_line(capsys, monkeypatch):
+    """The CPU baseline times the oracle's serial and OpenMP builds on both
+    paths with every method, and states the threads used; the reference arm
+    prints one JSON line of the same metric (a small system here)."""
+    import json
+
+    import bench
+    from paper_1208_4869_gb300 import workloads as W
+    A, y = W.dense_system(96, 3.0, 0)
+    rows = bench.cpu_baseline_rows(A, y, ["bicgstab", "cgnr", "qmr"], 1e-10, 300, 1e-5, budget_s=0.0)
+    got = {(r["build"], r.get("path")) for r in rows}
+    assert ("serial", "mixed") in got and ("serial", "fp64") in got
+    for r in rows:
+        if "unavailable" in r:
+            continue
+        assert r["solves"] == 3 and r["value"] > 0 and r["threads"] >= 1
+        assert r["max_true_relres"] <= 1e-10
+    monkeypatch.delenv("RANK", raising=False)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    assert bench.run_reference(bench.parse_args(["--impl", "reference", "--n", "96", "--steps", "3",
+                                                 "--warmup", "0"])) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["steps"] == 3
+    assert line["cpu_baseline"]["cores"] >= 1 and line["max_true_relres"] <= 1e-10
+    assert line["config"]["path"] == "mixed"

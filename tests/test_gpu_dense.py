@@ -206,20 +206,6 @@ def test_solve_fp32_reaches_1e6(h, method, sym):
     assert abs(info["iters"] - ref.iters) <= 2
 
 
-def test_full_size_bicgstab_fp64(h):
-    """n = 8192, shift 3 (the single-RHS workload), complex128: whole solve vs
-    the oracle's, at the launch configuration the benchmark times."""
-    A, y = W.dense_system(**W.DENSE_LARGE)
-    op = h.op_dense(dev(A))
-    ref = O.solve(O.DenseOp(A), "bicgstab", y, tol=1e-10, maxit=300)
-    xd = torch.zeros(8192, dtype=torch.complex128, device="cuda")
-    st, info, hist = h.solve("bicgstab", op, dev(y), xd, tol=1e-10, maxit=300)
-    assert st == 0 and info["iters"] == ref.iters
-    assert info["true_relres"] <= 1e-10
-    assert relerr(xd.cpu().numpy(), ref.x) < 1e-9
-    assert np.allclose(hist, ref.hist, rtol=1e-8, atol=0)
-
-
 def test_full_size_matvec(h):
     """n = 8192 complex128 and complex64 products against the oracle's full
     products (the oracle finishes one in well under a second)."""

@@ -68,25 +68,33 @@ def test_dipole_matvec_matches_direct_sum(h, dtype, kind, L):
         assert np.abs(got - want).max() <= tol * np.abs(want).max(), (kind, L, trans)
 
 
-def test_dipole_full_size_sampled_rows(h):
-    """The 64^3 sphere (137376 dipoles, 128^3 FFT grid): sampled outputs of
-    A x against the oracle's direct sum evaluated at those sites only."""
-    occ = W.sphere_occupancy(64)
+@pytest.mark.parametrize("L", [24, 32, 48, 64])
+def test_dipole_large_sampled_rows(h, L):
+    """The sphere lattices of the serving stream and the 64^3 workload (FFT
+    grids 48^3 and 96^3 with radix-3 register transforms, 64^3, and 128^3 with
+    137376 dipoles): sampled outputs of A x and A^H x against the oracle's
+    direct sum evaluated at those sites only (A^H x = conj(A conj(x)), A
+    being complex symmetric)."""
+    occ = W.sphere_occupancy(L)
     ref = O.DipoleOp(occ, KD, M)
-    rng = np.random.default_rng(3)
+    rng = np.random.default_rng(3 + L)
     sel = np.sort(rng.choice(ref.nsites, 24, replace=False))
     sel = np.concatenate([[0, ref.nsites - 1], sel])
     for dtype, tol in (("complex128", 1e-12), ("complex64", 2e-5)):
         op = h.op_dipole(occ, KD, M, dtype=dtype)
-        assert op.nsites == 137376
+        assert op.nsites == ref.nsites
+        if L == 64:
+            assert op.nsites == 137376
         npd = np.complex128 if dtype == "complex128" else np.complex64
         x = W.random_vector(op.n, 4, npd)
-        yd = torch.empty(op.n, dtype=getattr(torch, dtype), device="cuda")
-        h.matvec(op, dev(x), yd)
-        torch.cuda.synchronize()
-        got = yd.cpu().numpy().reshape(3, -1)[:, sel].astype(np.complex128)
-        want = ref.rows(x.astype(np.complex128), sel)
-        assert np.abs(got - want).max() <= tol * np.abs(want).max(), dtype
+        for trans in (False, True):
+            yd = torch.empty(op.n, dtype=getattr(torch, dtype), device="cuda")
+            h.matvec(op, dev(x), yd, trans=trans)
+            torch.cuda.synchronize()
+            got = yd.cpu().numpy().reshape(3, -1)[:, sel].astype(np.complex128)
+            xx = x.astype(np.complex128)
+            want = np.conj(ref.rows(np.conj(xx), sel)) if trans else ref.rows(xx, sel)
+            assert np.abs(got - want).max() <= tol * np.abs(want).max(), (dtype, trans)
         del op
 
 

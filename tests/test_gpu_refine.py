@@ -70,20 +70,6 @@ def test_refined_matches_oracle(h, method, n):
     assert 0 < inner <= 300 * info["iters"]
 
 
-def test_refined_full_size_bicgstab(h):
-    """n = 8192 (the single-RHS workload): complex128 accuracy from complex64
-    sweeps; solution vs the oracle's complex128 BiCGSTAB solution."""
-    A, y = W.dense_system(**W.DENSE_LARGE)
-    op64, op32, _keep = ops(h, A)
-    xd = torch.zeros(8192, dtype=torch.complex128, device="cuda")
-    st, info, hist, inner = h.solve_refined("bicgstab", op64, op32, dev(y), xd, tol=1e-10)
-    assert st == 0 and info["relres"] <= 1e-10
-    ref = O.solve(O.DenseOp(A), "bicgstab", y, tol=1e-12, maxit=300)
-    x = xd.cpu().numpy()
-    assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) < 1e-9
-    assert relres(A, x, y) <= 1e-10
-
-
 def test_refined_edge_cases(h, ccg):
     n = 128
     A, y = W.dense_system(n, 3.0, 5)
