@@ -332,8 +332,10 @@ ccg_status ccg_set_option(ccg_handle* h, int option, int value);
  *    normal; nrhs complex-normal right-hand sides (the Sec. 1 problem);
  *  - CCG_REQ_DIPOLE: the discrete-dipole operator of an L^3 inscribed sphere
  *    (see ccg_op_dipole) with the x-polarised plane wave along z.
- * Precision follows the tolerance: tol >= 1e-7 runs complex64 solves,
- * smaller tol the mixed-precision refinement (complex128 residuals).  Dense
+ * Precision follows the tolerance: tol >= 1e-5 runs complex64 solves,
+ * smaller tol the mixed-precision refinement (complex128 residuals: a
+ * complex64 residual carries ~1e-6 relative rounding on these operators and
+ * cannot certify tighter tolerances).  Dense
  * requests use BiCGSTAB (batched when nrhs > 1); dipole requests COCG.
  * -------------------------------------------------------------------------- */
 typedef struct ccg_server ccg_server;
@@ -381,6 +383,14 @@ ccg_status ccg_server_poll(ccg_server* s, int64_t ticket, int* done);
 ccg_status ccg_server_wait(ccg_server* s, int64_t ticket, ccg_result* res, void* x);
 /* Seconds on the server's clock (the clock of ccg_result times). */
 double ccg_server_now(const ccg_server* s);
+/* Device bytes the admission test charges for a request: its matrices,
+ * blocks and workspace while it runs, and for a dipole request its
+ * operators, which the slot that ran it keeps cached (and charged) until
+ * the server is destroyed.  CCG_ERR_INVALID for NULL or a bad kind. */
+ccg_status ccg_server_estimate(const ccg_request* req, uint64_t* bytes);
+/* Bytes currently charged against the server's budget (running requests
+ * and cached operators). */
+ccg_status ccg_server_charged(ccg_server* s, uint64_t* bytes);
 /* Finish queued work, stop the workers and free everything. */
 ccg_status ccg_server_destroy(ccg_server* s);
 

@@ -114,13 +114,15 @@ def lib():
     L.ccg_server_wait.argtypes = [vp, i64, ctypes.POINTER(Result), vp]
     L.ccg_server_now.restype = dbl
     L.ccg_server_now.argtypes = [vp]
+    L.ccg_server_estimate.argtypes = [ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+    L.ccg_server_charged.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
     L.ccg_server_destroy.argtypes = [vp]
     L.ccg_launch_count.restype = i64
     L.ccg_launch_count.argtypes = [vp]
     for name in ("ccg_create", "ccg_destroy", "ccg_set_stream", "ccg_op_dense", "ccg_op_dipole", "ccg_op_destroy", "ccg_matvec",
                  "ccg_dot", "ccg_solve", "ccg_solve_refined", "ccg_solve_batched", "ccg_solve_batched_refined",
                  "ccg_block_matvec", "ccg_set_option", "ccg_server_create", "ccg_server_submit", "ccg_server_poll",
-                 "ccg_server_wait", "ccg_server_destroy",
+                 "ccg_server_wait", "ccg_server_destroy", "ccg_server_estimate", "ccg_server_charged",
                  "ccg_timing_enable", "ccg_timing_read", "ccg_timing_reset"):
         getattr(L, name).restype = i32
     if L.ccg_abi_version() != 1:
@@ -346,6 +348,23 @@ class Operator:
     __del__ = close
 
 
+def make_request(kind="dense", n=0, nrhs=1, shift=3.0, seed=0, L=0, kd=0.5, m=1.5 + 0.01j, tol=1e-10, maxit=0,
+                 keep_x=False, mode=0):
+    r = Request()
+    r.kind = REQ_DENSE if kind == "dense" else REQ_DIPOLE
+    r.n, r.nrhs, r.shift, r.seed, r.L, r.maxit = int(n), int(nrhs), float(shift), int(seed), int(L), int(maxit)
+    r.kd, r.m_re, r.m_im, r.tol, r.keep_x = float(kd), complex(m).real, complex(m).imag, float(tol), int(keep_x)
+    r.mode = int(mode)
+    return r
+
+
+def server_estimate(**req):
+    """ccg_server_estimate: device bytes the serving admission charges for a request."""
+    b = ctypes.c_uint64()
+    _check(lib().ccg_server_estimate(ctypes.byref(make_request(**req)), ctypes.byref(b)))
+    return b.value
+
+
 class Server:
     """ccg_server_*: a queue of solve requests served by `slots` workers on one
     GPU under an HBM budget (bytes; 0 = 120 GB)."""
@@ -358,11 +377,7 @@ class Server:
 
     def submit(self, kind="dense", n=0, nrhs=1, shift=3.0, seed=0, L=0, kd=0.5, m=1.5 + 0.01j, tol=1e-10,
                maxit=0, keep_x=False, mode=0):
-        r = Request()
-        r.kind = REQ_DENSE if kind == "dense" else REQ_DIPOLE
-        r.n, r.nrhs, r.shift, r.seed, r.L, r.maxit = int(n), int(nrhs), float(shift), int(seed), int(L), int(maxit)
-        r.kd, r.m_re, r.m_im, r.tol, r.keep_x = float(kd), complex(m).real, complex(m).imag, float(tol), int(keep_x)
-        r.mode = int(mode)
+        r = make_request(kind, n, nrhs, shift, seed, L, kd, m, tol, maxit, keep_x, mode)
         t = ctypes.c_int64()
         _check(lib().ccg_server_submit(self.sv, ctypes.byref(r), ctypes.byref(t)))
         return t.value
@@ -382,6 +397,12 @@ class Server:
 
     def now(self):
         return lib().ccg_server_now(self.sv)
+
+    def charged(self):
+        """ccg_server_charged: bytes charged against the budget now."""
+        b = ctypes.c_uint64()
+        _check(lib().ccg_server_charged(self.sv, ctypes.byref(b)))
+        return b.value
 
     def close(self):
         if getattr(self, "sv", None) and self.sv.value:

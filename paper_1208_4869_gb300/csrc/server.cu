@@ -136,12 +136,27 @@ struct ccg_server {
 
 namespace {
 
-// Device bytes a request holds while it runs (matrices, blocks, workspace).
+// Device bytes of the complex128 and complex64 dipole operators of an L^3
+// lattice that a slot caches: per precision three FFT grids of (2L)^3
+// points and the field-tensor octant of 6 (L+1)^3 components, plus the
+// site-index grids and twiddle tables.
+// Loosest tolerance that still needs complex128 residuals: a complex64
+// solve's own residual carries single-precision rounding of ~1e-6 relative on
+// the dipole operators, so it certifies only tolerances of 1e-5 and above.
+constexpr double kSingleTol = 1e-5;
+
+uint64_t dipole_op_bytes(int L) {
+  const double G = 8.0 * L * L * L, O = 6.0 * (L + 1.0) * (L + 1.0) * (L + 1.0);
+  return (uint64_t)((3.0 * G + O) * (16 + 8) + 2.0 * 4.0 * L * L * L + 6.0 * 2 * L * 16);
+}
+
+// Device bytes a request holds while it runs (matrices, blocks, workspace);
+// for a dipole request also its operators, which the slot that runs it
+// keeps cached afterwards (charged to the budget for as long as it does).
 uint64_t estimate_bytes(const ccg_request& r) {
   if (r.kind == CCG_REQ_DIPOLE) {
-    const double G = 8.0 * r.L * r.L * r.L;
     const double N3 = 3.0 * 0.55 * r.L * r.L * r.L;
-    return (uint64_t)(40.0 * N3 * 16 + 2.0 * G * 16);
+    return (uint64_t)(40.0 * N3 * 16) + dipole_op_bytes(r.L);
   }
   const double n = (double)r.n, k = std::max(1, r.nrhs);
   // complex128 and complex64 matrices, the split-bf16 terms, blocks and workspace
@@ -157,7 +172,7 @@ int run_dense(ccg_handle* h, cudaStream_t s, const ccg_request& r, ccg_result& r
   const int k = std::max(1, r.nrhs);
   double2 *A64 = nullptr, *Y = nullptr, *X = nullptr;
   float2 *A32 = nullptr, *Y32 = nullptr, *X32 = nullptr;
-  const bool single = r.tol >= 1e-7 && r.mode == 0;
+  const bool single = r.tol >= kSingleTol && r.mode == 0;
   auto freeall = [&]() {
     for (void* p : {(void*)A64, (void*)A32, (void*)Y, (void*)X, (void*)Y32, (void*)X32})
       if (p) cudaFreeAsync(p, s);
@@ -240,9 +255,10 @@ int run_dense(ccg_handle* h, cudaStream_t s, const ccg_request& r, ccg_result& r
 }
 
 int run_dipole(ccg_handle* h, cudaStream_t s, std::map<int, DipoleOps>& cache, const ccg_request& r, ccg_result& res,
-               std::vector<double2>* xout) {
+               std::vector<double2>* xout, bool* created) {
   const int L = r.L;
   auto it = cache.find(L);
+  *created = false;
   if (it == cache.end()) {
     DipoleOps d;
     std::vector<uint8_t> occ((size_t)L * L * L);
@@ -269,12 +285,13 @@ int run_dipole(ccg_handle* h, cudaStream_t s, std::map<int, DipoleOps>& cache, c
       d.y[q] = make_double2(e.real(), e.imag());
     }
     it = cache.emplace(L, std::move(d)).first;
+    *created = true;
   }
   DipoleOps& d = it->second;
   const int64_t n = (int64_t)d.y.size();
   double2 *Y = nullptr, *X = nullptr;
   float2 *Y32 = nullptr, *X32 = nullptr;
-  const bool single = r.tol >= 1e-7 && r.mode == 0;
+  const bool single = r.tol >= kSingleTol && r.mode == 0;
   cudaMallocAsync(&Y, n * sizeof(double2), s);
   cudaMallocAsync(&X, n * sizeof(double2), s);
   if (single) {
@@ -329,6 +346,7 @@ void worker(ccg_server* sv, int slot) {
   }
   sv->cv.notify_all();
   std::map<int, DipoleOps> cache;
+  uint64_t cached_bytes = 0;   // budget charged for this slot's cached operators
   for (;;) {
     std::shared_ptr<Entry> e;
     uint64_t bytes = 0;
@@ -352,14 +370,22 @@ void worker(ccg_server* sv, int slot) {
     sv->cv.notify_all();
     std::vector<double2>* xo = e->req.keep_x ? &e->x : nullptr;
     int st = h ? CCG_OK : CCG_ERR_CUDA;
+    bool created = false;
     if (st == CCG_OK)
-      st = e->req.kind == CCG_REQ_DIPOLE ? run_dipole(h, s, cache, e->req, e->res, xo) : run_dense(h, s, e->req, e->res, xo);
+      st = e->req.kind == CCG_REQ_DIPOLE ? run_dipole(h, s, cache, e->req, e->res, xo, &created)
+                                         : run_dense(h, s, e->req, e->res, xo);
     {
       std::lock_guard<std::mutex> lk(sv->mu);
       e->res.status = st;
       e->res.t_done = sv->now();
       e->done = true;
       sv->used -= bytes;
+      // operators this slot now caches stay charged until the slot exits
+      if (created) {
+        const uint64_t ob = dipole_op_bytes(e->req.L);
+        sv->used += ob;
+        cached_bytes += ob;
+      }
       --sv->running;
     }
     sv->cv.notify_all();
@@ -367,6 +393,10 @@ void worker(ccg_server* sv, int slot) {
   for (auto& kv : cache) {
     ccg_op_destroy(kv.second.op64);
     ccg_op_destroy(kv.second.op32);
+  }
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->used -= cached_bytes;
   }
   if (h) ccg_destroy(h);
   cudaStreamDestroy(s);
@@ -458,6 +488,20 @@ ccg_status ccg_server_wait(ccg_server* sv, int64_t ticket, ccg_result* res, void
 }
 
 double ccg_server_now(const ccg_server* sv) { return sv ? sv->now() : 0.0; }
+
+ccg_status ccg_server_estimate(const ccg_request* r, uint64_t* bytes) {
+  if (!r || !bytes) { set_error("ccg_server_estimate: NULL argument"); return CCG_ERR_INVALID; }
+  if (r->kind != CCG_REQ_DENSE && r->kind != CCG_REQ_DIPOLE) { set_error("ccg_server_estimate: bad kind"); return CCG_ERR_INVALID; }
+  *bytes = estimate_bytes(*r);
+  return CCG_OK;
+}
+
+ccg_status ccg_server_charged(ccg_server* sv, uint64_t* bytes) {
+  if (!sv || !bytes) { set_error("ccg_server_charged: NULL argument"); return CCG_ERR_INVALID; }
+  std::lock_guard<std::mutex> lk(sv->mu);
+  *bytes = sv->used;
+  return CCG_OK;
+}
 
 ccg_status ccg_server_destroy(ccg_server* sv) {
   if (!sv) return CCG_OK;

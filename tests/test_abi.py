@@ -70,3 +70,19 @@ def test_callback_operator_rejects_bad_arguments_without_gpu(libpath):
     good = fn(lambda ctx, n, x, y, s: 0)
     assert L.ccg_op_callback(None, 1, 8, good, fn(), None, 0, ctypes.byref(op)) == -1   # no handle
     assert not op.value
+
+
+def test_server_estimate_without_gpu():
+    """The serving admission's byte estimate is host arithmetic: dense
+    requests hold both matrices (24 n^2 bytes at least); dipole requests also
+    their cached operators (three FFT grids and the field-tensor octant per
+    precision), so a larger lattice costs more."""
+    from paper_1208_4869_gb300 import build as B
+    B.build()
+    from paper_1208_4869_gb300 import ccg
+    d = ccg.server_estimate(kind="dense", n=1024, nrhs=1)
+    assert d >= 24 * 1024 * 1024
+    assert ccg.server_estimate(kind="dense", n=1024, nrhs=8) > d
+    small, big = ccg.server_estimate(kind="dipole", L=16), ccg.server_estimate(kind="dipole", L=32)
+    assert big > 7 * small
+    assert big >= 3 * 8 * 32 ** 3 * 24

@@ -7,7 +7,8 @@ A p + A^H q sweeps).  Each of the benchmark's three methods (Sec. 2.1
 `bicgstab`, `cgnr`, `qmr`) is solved
 
   * in complex128: the whole solve against the oracle's -- equal iteration
-    counts, residual history within 1e-8 relative, x within 1e-9;
+    counts, residual history within 1e-8 relative (above an absolute floor
+    of 1e-13 ||y||), x within 1e-9;
   * with complex64 inner solves inside complex128 refinement (the
     benchmark's headline path): final true residual <= 1e-10, x within 1e-9
     of the oracle's complex128 solution (the forward error a 1e-10 residual
@@ -82,7 +83,12 @@ def test_full_size_fp64_matches_oracle(h, system, dev_ops, method):
     xd = torch.zeros(N, dtype=torch.complex128, device="cuda")
     st, info, hist = h.solve(method, op64, torch.from_numpy(y).cuda(), xd, tol=1e-10, maxit=300)
     assert st == 0 and info["iters"] == ref.iters
-    assert np.allclose(hist, ref.hist, rtol=1e-8, atol=0)
+    # The recurrence residuals (r -= alpha w, r -= s, r = s - omega t) keep
+    # the rounding of every earlier update at the scale of ||r_0|| = ||y||,
+    # so late entries are compared on that scale: rtol 1e-8, plus an absolute
+    # floor of 1e-13 ||y|| (about sqrt(n) eps: matrix-vector sums in another
+    # order than the oracle's).
+    assert np.allclose(hist, ref.hist, rtol=1e-8, atol=1e-13)
     x = xd.cpu().numpy()
     assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) < 1e-9
     assert info["relres"] <= 1e-10
