@@ -245,7 +245,7 @@ def profiled_traffic(kernel):
 
 
 SWEEP_KERNELS = {0: ("gemv_n_rows", 1), 1: ("gemv_tile_c", 1), 2: ("gemv_tile_both", 2), 3: ("cgemm_rows", 1),
-                 4: ("gemm_bf16_split", 1), 5: ("ozaki_gemm", 1)}
+                 4: ("gemm_bf16_split", 1), 5: ("ozaki_gemm", 1), 6: ("pk_solve", 1)}
 # bf16 MMA work per real product term: term pairs of the two-term complex64
 # split (3), digit pairs of the integer-slice scheme (36 for complex128's 8
 # digits, 10 for complex64's 4)
@@ -268,6 +268,9 @@ def kernel_sources(tag):
         return [(CSRC + "tc_gemm.cu", "// C (M x N fp32, leading dimension ldc)", "// Xh^T as T bf16 terms"),
                 (CSRC + "tc_gemm.cu", "template <int T> struct Cfg {", "// C (M x N fp32, leading dimension ldc)"),
                 (CSRC + "tcgen05.cuh", None, None)]
+    elif tag.startswith("pk_solve"):    # the persistent solve: its file, the phases and the sweep bodies
+        return [(CSRC + "persist.cu", None, None), (CSRC + "phases.cuh", None, None), (CSRC + "gemv.cuh", None, None),
+                (CSRC + "reduce.cuh", None, None), (CSRC + "common.cuh", None, None)]
     elif tag.startswith("dipole"):
         own = [(CSRC + "fft.cuh", None, None), (CSRC + "dipole.cu", None, None)]
     elif tag.startswith("gemv_n_rows"):
@@ -289,11 +292,11 @@ def roofline(ccg, sweep_stats, n, dipole=False, nrhs=1):
             prec = "c128" if dt == ccg.C128 else "c64"
             tag = "%s_%s" % (name, prec)
             avg = ms / cnt
-            cols = nrhs if kind >= 3 else 1
+            cols = nrhs if kind in (3, 4, 5) else 1
             kinds[tag] = {"launches": cnt, "total_ms": ms, "avg_ms": avg,
                           "tflops": None if dipole else 8.0 * products * n * n * cols / (avg * 1e-3) / 1e12,
                           "gbs": nbytes / (avg * 1e-3) / 1e9, "bytes": nbytes}
-            if kind >= 4:   # bf16 tensor work actually issued
+            if kind in (4, 5):   # bf16 tensor work actually issued
                 kinds[tag]["tensor_tflops"] = kinds[tag]["tflops"] * TC_PRODUCTS[(name, prec)]
     if not kinds:
         return None
@@ -545,7 +548,7 @@ def run_serving(args):
 def sweep_stats(h, ccg):
     return {(dt, k): h.timing(kind=k, dtype=dt) for dt in (ccg.C128, ccg.C64)
             for k in (ccg.SWEEP_N, ccg.SWEEP_C, ccg.SWEEP_BOTH, ccg.SWEEP_BLOCK, ccg.SWEEP_BLOCK_TC,
-                      ccg.SWEEP_BLOCK_EXACT)}
+                      ccg.SWEEP_BLOCK_EXACT, ccg.SWEEP_PERSIST)}
 
 
 def timed_region(h, torch, stream, step, steps, world, clocks=None):

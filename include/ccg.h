@@ -271,6 +271,45 @@ ccg_status ccg_solve_batched_refined(ccg_handle* h, ccg_method inner_method, con
                                      int64_t ldx, double tol, int max_outer, double inner_tol, int inner_maxit,
                                      int32_t* outer, int32_t* inner, int32_t* status, double* relres);
 
+/* Many independent systems A_k x_k = y_k (the Sec. 1 problem, k = 0 ..
+ * count-1) of uneven sizes, solved together in one cooperative launch: the
+ * GPU's resident blocks are split into one group per system, in proportion
+ * to its matrix bytes (every system at least one block), and each group runs
+ * its system's iteration with barriers among its own blocks only, so
+ * systems of different sizes and iteration counts advance independently.  A
+ * system's result is bitwise that of ccg_solve with CCG_OPT_PERSISTENT = 0
+ * (the same sweeps and fused updates, reduced in the same order).  Meant for
+ * small systems, whose solves are otherwise bound by launch latency.
+ *  method    CCG_BICGSTAB, CCG_CGNR, CCG_QMR or CCG_COCG (else
+ *            CCG_ERR_UNSUPPORTED)
+ *  count     1 .. the resident blocks of the launch (about 3 per SM)
+ *  ops       count dense operators of one precision (COCG: flagged
+ *            CCG_OP_SYMMETRIC); the same operator may appear more than once
+ *  y, x      count device vectors each (x: start vector in, solution out)
+ *  tol       count relative residual targets
+ *  maxit     iteration cap of every system
+ *  iters, status, relres  optional host arrays of count entries: iterations,
+ *            ccg_status, and ||y - A x|| / ||y|| recomputed from x
+ * Returns the worst status (an error, else CCG_BREAKDOWN > CCG_NOT_CONVERGED
+ * > CCG_OK); CCG_ERR_TIMEOUT if a group barrier gave up (CCG_OPT_WAIT_LIMIT).
+ * Synchronises the handle's stream. */
+ccg_status ccg_solve_multi(ccg_handle* h, ccg_method method, int64_t count, const ccg_operator* const* ops,
+                           const void* const* y, void* const* x, const double* tol, int maxit, int32_t* iters,
+                           int32_t* status, double* relres);
+/* The same with mixed precision (as ccg_solve_refined, per system): each
+ * outer step is one launch over the systems still refining -- x += d, the
+ * residual r = y - A x in complex128 and its test -- and one launch of their
+ * complex64 corrections A d = r.  ops: complex128 operators; ops_inner:
+ * complex64 operators of the same matrices.  outer, inner: optional host
+ * arrays (corrections applied, inner iterations in total); relres: the last
+ * complex128 residual of each system.  Other arguments as above and in
+ * ccg_solve_refined. */
+ccg_status ccg_solve_multi_refined(ccg_handle* h, ccg_method inner_method, int64_t count,
+                                   const ccg_operator* const* ops, const ccg_operator* const* ops_inner,
+                                   const void* const* y, void* const* x, const double* tol, int max_outer,
+                                   double inner_tol, int inner_maxit, int32_t* outer, int32_t* inner,
+                                   int32_t* status, double* relres);
+
 /* Y = A X for a block of right-hand sides: the manual's `matvec` (Sec. 5)
  * applied to nrhs columns at once.  X, Y: device column-major blocks of the
  * operator's precision (column c at X + c*ldx; ldx, ldy >= n), 1 <= nrhs <=
@@ -311,6 +350,33 @@ ccg_status ccg_block_matvec(ccg_handle* h, const ccg_operator* op, int64_t nrhs,
  * fp32 accumulation and combined in int64.  The result is as accurate as a
  * GEMM in the operands' precision (error ~ K 2^-53, resp. K 2^-24, times
  * max|a| max|x| per entry).  0 uses CUDA cores for them.
+ * CCG_OPT_PERSISTENT selects how ccg_solve and the inner solves of
+ * ccg_solve_refined run BiCGSTAB, CGNR, QMR or COCG on a dense operator: 1 as
+ * one cooperative launch per solve (the iteration's sweeps and fused updates
+ * back to back inside the kernel, separated by grid barriers); 0 as the
+ * kernel-per-step loop, which every other method and operator uses; 2 (the
+ * default) as the library's tuned table says for the precision, method and
+ * order (measured on GB300 by the package's autotune.py).  Both forms run
+ * the same arithmetic in the same order: results are bitwise equal.
+ * CCG_OPT_PK_BLOCKS: resident blocks per SM of that launch, 1..32 (0, the
+ * default: the tuned value, else the occupancy limit).
+ * CCG_OPT_WAIT_LIMIT: the bounded wait of the persistent launch's barriers,
+ * in units of 1024 SM clock cycles (0: the default, 2^22 units, about 2 s at
+ * 2 GHz).  A block that waits longer gives up, the call returns
+ * CCG_ERR_TIMEOUT and the handle stays usable.
+ * CCG_OPT_FP64_SWEEP selects how y = A x runs for a complex128 dense
+ * operator: 1 (default) in 53-bit fixed point on the integer pipe -- each row
+ * of A and the vector scaled by its largest power of two and cut into two
+ * 26-bit digits, the products summed exactly in 64-bit integers -- reading a
+ * digit copy of A that the operator makes on its first such product (16
+ * bytes per entry, freed with the operator; a matrix with a non-finite entry
+ * keeps the FP64 pipe); error <= 2.5 n 2^-52 max_j|a_ij| max_j|x_j| per entry
+ * (times the powers of two above those maxima); 0 on the FP64 pipe (FMA,
+ * error ~ n 2^-53 sum_j |a_ij||x_j|).  GB300's FP64 pipe holds that sweep to a
+ * third of HBM bandwidth; the integer form runs near it.
+ * CCG_OPT_TEST_WITHHOLD: test hook; 1 makes one block of the next persistent
+ * launches leave without arriving at the first barrier, so that the others'
+ * waits expire (use with a small CCG_OPT_WAIT_LIMIT); 0 (default) off.
  * ccg_set_option returns CCG_ERR_INVALID (and leaves the handle unchanged)
  * for a NULL handle, an unknown option or a value out of range; options
  * apply to the handle's later calls. */
@@ -319,6 +385,11 @@ ccg_status ccg_block_matvec(ccg_handle* h, const ccg_operator* op, int64_t nrhs,
 #define CCG_OPT_GMRES_RESTART 3
 #define CCG_OPT_BICGSTAB_L 4
 #define CCG_OPT_TC_EXACT 5
+#define CCG_OPT_PERSISTENT 6
+#define CCG_OPT_PK_BLOCKS 7
+#define CCG_OPT_WAIT_LIMIT 8
+#define CCG_OPT_TEST_WITHHOLD 9
+#define CCG_OPT_FP64_SWEEP 10
 ccg_status ccg_set_option(ccg_handle* h, int option, int value);
 
 /* ---------------------------------------------------------------------------
@@ -403,7 +474,9 @@ typedef enum {
   CCG_SWEEP_BLOCK_TC = 4, /* A X for a block on the tensor cores, split bf16 */
   CCG_SWEEP_BLOCK_EXACT = 5, /* A X for a block on the tensor cores, exact
                                 integer digit slices */
-  CCG_SWEEP_KINDS = 6
+  CCG_SWEEP_PERSIST = 6, /* a persistent solve's launch, counted as the
+                            sweeps it ran (see CCG_OPT_PERSISTENT) */
+  CCG_SWEEP_KINDS = 7
 } ccg_sweep_kind;
 
 /* Per-kernel timing of the operator sweeps: when enabled, each sweep that a

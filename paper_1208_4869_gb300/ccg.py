@@ -29,11 +29,16 @@ OPT_TC_SPLIT = 2
 OPT_GMRES_RESTART = 3
 OPT_BICGSTAB_L = 4
 OPT_TC_EXACT = 5
+OPT_PERSISTENT = 6
+OPT_PK_BLOCKS = 7
+OPT_WAIT_LIMIT = 8
+OPT_TEST_WITHHOLD = 9
+OPT_FP64_SWEEP = 10
 
 # ccg_matvec_fn: int (*)(void* ctx, int64_t n, const void* x, void* y, void* stream)
 MATVEC_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                              ctypes.c_void_p)
-SWEEP_N, SWEEP_C, SWEEP_BOTH, SWEEP_BLOCK, SWEEP_BLOCK_TC, SWEEP_BLOCK_EXACT = 0, 1, 2, 3, 4, 5
+SWEEP_N, SWEEP_C, SWEEP_BOTH, SWEEP_BLOCK, SWEEP_BLOCK_TC, SWEEP_BLOCK_EXACT, SWEEP_PERSIST = 0, 1, 2, 3, 4, 5, 6
 
 _lib = None
 
@@ -108,6 +113,8 @@ def lib():
     L.ccg_solve_batched_refined.argtypes = [vp, i32, vp, vp, i64, vp, i64, vp, i64, dbl, i32, dbl, i32, vp, vp, vp, vp]
     L.ccg_block_matvec.argtypes = [vp, vp, i64, vp, i64, vp, i64]
     L.ccg_set_option.argtypes = [vp, i32, i32]
+    L.ccg_solve_multi.argtypes = [vp, i32, i64, vp, vp, vp, vp, i32, vp, vp, vp]
+    L.ccg_solve_multi_refined.argtypes = [vp, i32, i64, vp, vp, vp, vp, vp, i32, dbl, i32, vp, vp, vp, vp]
     L.ccg_server_create.argtypes = [ctypes.POINTER(vp), i32, i32, ctypes.c_uint64]
     L.ccg_server_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(i64)]
     L.ccg_server_poll.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_int)]
@@ -121,7 +128,7 @@ def lib():
     L.ccg_launch_count.argtypes = [vp]
     for name in ("ccg_create", "ccg_destroy", "ccg_set_stream", "ccg_op_dense", "ccg_op_dipole", "ccg_op_destroy", "ccg_matvec",
                  "ccg_dot", "ccg_solve", "ccg_solve_refined", "ccg_solve_batched", "ccg_solve_batched_refined",
-                 "ccg_block_matvec", "ccg_set_option", "ccg_server_create", "ccg_server_submit", "ccg_server_poll",
+                 "ccg_block_matvec", "ccg_set_option", "ccg_solve_multi", "ccg_solve_multi_refined", "ccg_server_create", "ccg_server_submit", "ccg_server_poll",
                  "ccg_server_wait", "ccg_server_destroy", "ccg_server_estimate", "ccg_server_charged",
                  "ccg_timing_enable", "ccg_timing_read", "ccg_timing_reset"):
         getattr(L, name).restype = i32
@@ -201,11 +208,12 @@ class Handle:
         return Operator(op, fns, code)
 
     def op_dense(self, A, symmetric=False):
-        """ccg_op_dense on a CUDA tensor A (n x n, row-major, complex64/128); A is not copied."""
+        """ccg_op_dense on a CUDA tensor A (n x n, row-major, complex64/128; rows may be
+        padded: a view with stride(1) == 1 and stride(0) = lda >= n); A is not copied."""
         assert A.dim() == 2 and A.shape[0] == A.shape[1] and A.is_cuda
-        assert A.stride(1) == 1
+        assert A.stride(1) == 1 and A.stride(0) >= A.shape[1]
         op = ctypes.c_void_p()
-        _check(lib().ccg_op_dense(self.h, _dtype_code(A.dtype), A.shape[0], _ptr(A), A.stride(0),
+        _check(lib().ccg_op_dense(self.h, _dtype_code(A.dtype), A.shape[0], ctypes.c_void_p(A.data_ptr()), A.stride(0),
                                   OP_SYMMETRIC if symmetric else 0, ctypes.byref(op)))
         return Operator(op, A, _dtype_code(A.dtype))
 
@@ -309,6 +317,46 @@ class Handle:
                                              int(max_outer), float(inner_tol), int(inner_maxit),
                                              ctypes.c_void_p(outer.ctypes.data), ctypes.c_void_p(inner.ctypes.data),
                                              ctypes.c_void_p(sts.ctypes.data), ctypes.c_void_p(rr.ctypes.data))
+        _check(st)
+        return st, outer, inner, sts, rr
+
+    @staticmethod
+    def _ptr_array(items):
+        arr = (ctypes.c_void_p * len(items))()
+        for i, it in enumerate(items):
+            arr[i] = it if isinstance(it, int) else (it.op.value if isinstance(it, Operator) else _ptr(it).value)
+        return arr
+
+    def solve_multi(self, method, ops, ys, xs, tol=1e-10, maxit=1000):
+        """ccg_solve_multi: many dense systems in one launch.  ops, ys, xs are lists
+        (xs: start vectors in, solutions out).  Returns (status, iters, statuses, relres)."""
+        k = len(ops)
+        m = METHODS[method] if isinstance(method, str) else int(method)
+        tols = np.ascontiguousarray(np.broadcast_to(np.asarray(tol, dtype=np.float64), (k,)))
+        iters = np.zeros(k, np.int32)
+        sts = np.zeros(k, np.int32)
+        rr = np.zeros(k)
+        st = lib().ccg_solve_multi(self.h, m, k, self._ptr_array(ops), self._ptr_array(ys), self._ptr_array(xs),
+                                   ctypes.c_void_p(tols.ctypes.data), int(maxit), ctypes.c_void_p(iters.ctypes.data),
+                                   ctypes.c_void_p(sts.ctypes.data), ctypes.c_void_p(rr.ctypes.data))
+        _check(st)
+        return st, iters, sts, rr
+
+    def solve_multi_refined(self, method, ops, ops_inner, ys, xs, tol=1e-10, max_outer=30, inner_tol=1e-5,
+                            inner_maxit=200):
+        """ccg_solve_multi_refined.  Returns (status, outer, inner, statuses, relres)."""
+        k = len(ops)
+        m = METHODS[method] if isinstance(method, str) else int(method)
+        tols = np.ascontiguousarray(np.broadcast_to(np.asarray(tol, dtype=np.float64), (k,)))
+        outer = np.zeros(k, np.int32)
+        inner = np.zeros(k, np.int32)
+        sts = np.zeros(k, np.int32)
+        rr = np.zeros(k)
+        st = lib().ccg_solve_multi_refined(self.h, m, k, self._ptr_array(ops), self._ptr_array(ops_inner),
+                                           self._ptr_array(ys), self._ptr_array(xs), ctypes.c_void_p(tols.ctypes.data),
+                                           int(max_outer), float(inner_tol), int(inner_maxit),
+                                           ctypes.c_void_p(outer.ctypes.data), ctypes.c_void_p(inner.ctypes.data),
+                                           ctypes.c_void_p(sts.ctypes.data), ctypes.c_void_p(rr.ctypes.data))
         _check(st)
         return st, outer, inner, sts, rr
 

@@ -57,6 +57,8 @@ void timing_begin(ccg_handle* h) {
       cudaEventCreate(&e);
       h->tev.push_back(e);
       h->tev_kind.push_back(0);
+      h->tev_units.push_back(1);
+      h->tev_bytes.push_back(0.0);
     }
   }
   cudaEventRecord(h->tev[h->tev_used], h->stream);
@@ -67,8 +69,16 @@ void timing_end(ccg_handle* h, int dtype, int kind, double bytes) {
   const int slot = dtype * CCG_SWEEP_KINDS + kind;
   cudaEventRecord(h->tev[h->tev_used + 1], h->stream);
   h->tev_kind[h->tev_used] = slot;
+  h->tev_units[h->tev_used] = 1;
+  h->tev_bytes[h->tev_used] = bytes;
   h->tev_used += 2;
   h->bytes_per_sweep[slot] = bytes;
+}
+
+void timing_set_units(ccg_handle* h, int64_t units, double bytes) {
+  if (!h->timing || h->tev_used < 2) return;
+  h->tev_units[h->tev_used - 2] = units;
+  h->tev_bytes[h->tev_used - 2] = bytes;
 }
 
 int* timing_rec(ccg_handle* h) {
@@ -89,10 +99,11 @@ void timing_collect(ccg_handle* h) {
   }
   for (size_t i = 0; i + 1 < h->tev_used; i += 2) {
     float ms = 0.f;
-    if (skipped[i / 2]) continue;
+    if (skipped[i / 2] || h->tev_units[i] <= 0) continue;
     if (cudaEventElapsedTime(&ms, h->tev[i], h->tev[i + 1]) == cudaSuccess) {
       h->timed_ms[h->tev_kind[i]] += ms;
-      h->timed_sweeps[h->tev_kind[i]] += 1;
+      h->timed_sweeps[h->tev_kind[i]] += h->tev_units[i];
+      h->timed_bytes[h->tev_kind[i]] += h->tev_bytes[i];   // a pair's bytes in total
     }
   }
   cudaGetLastError();
@@ -281,6 +292,7 @@ ccg_status ccg_op_destroy(ccg_operator* op) {
   }
   if (op && op->tc_ready) tc_free(op);  // stream-ordered after the operator's last use
   if (op && op->oz_a) oz_free(op);
+  if (op && op->fx_a) fx_free(op);
   delete op;
   return CCG_OK;
 }
@@ -405,6 +417,71 @@ ccg_status ccg_block_matvec(ccg_handle* h, const ccg_operator* op, int64_t nrhs,
   return static_cast<ccg_status>(block_matvec(h, op, nrhs, X, ldx, Y, ldy));
 }
 
+// Arguments of the many-system solves: dense operators of one precision
+// (ops) and, when refining, their complex64 copies (ops_in).
+static int check_multi(ccg_handle* h, ccg_method method, int64_t count, const ccg_operator* const* ops,
+                       const ccg_operator* const* ops_in, const void* const* y, void* const* x, const double* tol,
+                       const char* who) {
+  if (!h || !ops || !y || !x || !tol) { set_error(std::string(who) + ": NULL argument"); return CCG_ERR_INVALID; }
+  if (method != CCG_BICGSTAB && method != CCG_CGNR && method != CCG_QMR && method != CCG_COCG) {
+    set_error(std::string(who) + ": method must be BiCGSTAB, CGNR, QMR or COCG");
+    return CCG_ERR_UNSUPPORTED;
+  }
+  const int dt = ops_in ? CCG_C64 : (count > 0 && ops[0] ? ops[0]->dtype : CCG_C128);
+  const int cap = pk_capacity(h, method, dt);
+  if (count < 1 || count > cap) {
+    set_error(std::string(who) + ": need 1 <= count <= " + std::to_string(cap) + " (resident blocks)");
+    return CCG_ERR_INVALID;
+  }
+  for (int64_t k = 0; k < count; ++k) {
+    const ccg_operator* op = ops[k];
+    if (!op || op->kind != CCG_OPK_DENSE) { set_error(std::string(who) + ": dense operators only"); return CCG_ERR_UNSUPPORTED; }
+    if (op->dtype != ops[0]->dtype) { set_error(std::string(who) + ": operators of one precision"); return CCG_ERR_INVALID; }
+    if (ops_in) {
+      const ccg_operator* oi = ops_in[k];
+      if (op->dtype != CCG_C128 || !oi || oi->kind != CCG_OPK_DENSE || oi->dtype != CCG_C64 || oi->n != op->n) {
+        set_error(std::string(who) + ": need complex128 operators and complex64 copies of the same sizes");
+        return CCG_ERR_INVALID;
+      }
+    }
+    if (method == CCG_COCG && !(op->flags & CCG_OP_SYMMETRIC)) {
+      set_error(std::string(who) + ": COCG needs operators flagged CCG_OP_SYMMETRIC");
+      return CCG_ERR_INVALID;
+    }
+    const size_t esz = op->dtype == CCG_C128 ? 16 : 8;
+    if (!y[k] || !x[k] || !aligned(y[k], esz) || !aligned(x[k], esz)) {
+      set_error(std::string(who) + ": y and x must be aligned device vectors");
+      return CCG_ERR_INVALID;
+    }
+    if (!(tol[k] >= 0.0)) { set_error(std::string(who) + ": need tol >= 0"); return CCG_ERR_INVALID; }
+  }
+  return CCG_OK;
+}
+
+ccg_status ccg_solve_multi(ccg_handle* h, ccg_method method, int64_t count, const ccg_operator* const* ops,
+                           const void* const* y, void* const* x, const double* tol, int maxit, int32_t* iters,
+                           int32_t* status, double* relres) {
+  int rc = check_multi(h, method, count, ops, nullptr, y, x, tol, "ccg_solve_multi");
+  if (rc != CCG_OK) return static_cast<ccg_status>(rc);
+  if (maxit < 0) { set_error("ccg_solve_multi: need maxit >= 0"); return CCG_ERR_INVALID; }
+  return static_cast<ccg_status>(solve_multi(h, method, (int)count, ops, y, x, tol, maxit, iters, status, relres));
+}
+
+ccg_status ccg_solve_multi_refined(ccg_handle* h, ccg_method inner_method, int64_t count,
+                                   const ccg_operator* const* ops, const ccg_operator* const* ops_inner,
+                                   const void* const* y, void* const* x, const double* tol, int max_outer,
+                                   double inner_tol, int inner_maxit, int32_t* outer, int32_t* inner,
+                                   int32_t* status, double* relres) {
+  int rc = check_multi(h, inner_method, count, ops, ops_inner, y, x, tol, "ccg_solve_multi_refined");
+  if (rc != CCG_OK) return static_cast<ccg_status>(rc);
+  if (max_outer < 0 || !(inner_tol > 0.0) || inner_maxit < 1) {
+    set_error("ccg_solve_multi_refined: need max_outer >= 0, inner_tol > 0, inner_maxit >= 1");
+    return CCG_ERR_INVALID;
+  }
+  return static_cast<ccg_status>(solve_multi_refined(h, inner_method, (int)count, ops, ops_inner, y, x, tol, max_outer,
+                                                     inner_tol, inner_maxit, outer, inner, status, relres));
+}
+
 ccg_status ccg_set_option(ccg_handle* h, int option, int value) {
   if (!h) { set_error("ccg_set_option: NULL handle"); return CCG_ERR_INVALID; }
   if (option == CCG_OPT_TENSOR_CORES && value >= 0 && value <= 2) {
@@ -425,6 +502,26 @@ ccg_status ccg_set_option(ccg_handle* h, int option, int value) {
   }
   if (option == CCG_OPT_BICGSTAB_L && value >= 1 && value <= kMaxEll) {
     h->bicgstab_l = value;
+    return CCG_OK;
+  }
+  if (option == CCG_OPT_FP64_SWEEP && (value == 0 || value == 1)) {
+    h->fx_mode = value;
+    return CCG_OK;
+  }
+  if (option == CCG_OPT_PERSISTENT && value >= 0 && value <= 2) {
+    h->persistent = value;
+    return CCG_OK;
+  }
+  if (option == CCG_OPT_PK_BLOCKS && value >= 0 && value <= 32) {
+    h->pk_blocks = value;
+    return CCG_OK;
+  }
+  if (option == CCG_OPT_WAIT_LIMIT && value >= 0) {
+    h->wait_limit = value == 0 ? (4ll << 30) : ((long long)value << 10);
+    return CCG_OK;
+  }
+  if (option == CCG_OPT_TEST_WITHHOLD && (value == 0 || value == 1)) {
+    h->test_withhold = value;
     return CCG_OK;
   }
   set_error("ccg_set_option: unknown option or value out of range");
@@ -460,7 +557,9 @@ ccg_status ccg_timing_read(ccg_handle* h, int dtype, int kind, int64_t* sweeps, 
   const int slot = dtype * CCG_SWEEP_KINDS + kind;
   if (sweeps) *sweeps = h->timed_sweeps[slot];
   if (total_ms) *total_ms = h->timed_ms[slot];
-  if (bytes_per_sweep) *bytes_per_sweep = h->bytes_per_sweep[slot];
+  if (bytes_per_sweep)
+    *bytes_per_sweep = h->timed_sweeps[slot] > 0 ? h->timed_bytes[slot] / (double)h->timed_sweeps[slot]
+                                                 : h->bytes_per_sweep[slot];
   return CCG_OK;
 }
 
@@ -471,6 +570,7 @@ ccg_status ccg_timing_reset(ccg_handle* h) {
   for (int k = 0; k < 2 * CCG_SWEEP_KINDS; ++k) {
     h->timed_sweeps[k] = 0;
     h->timed_ms[k] = 0.0;
+    h->timed_bytes[k] = 0.0;
   }
   return CCG_OK;
 }

@@ -123,6 +123,7 @@ struct SolveState {
   double2 bl_g[kMaxEll];  // BiCGstab(l) minimal-residual coefficients
   double* hist;   // device residual history, maxit + 1 entries
   double* aux;    // spare device doubles for standalone results
+  int sweeps;     // persistent solve: operator sweeps it ran
 };
 
 // A sweep skips when the solve has stopped, is past a half-step exit, or

@@ -1,0 +1,215 @@
+// Complex128 y = A x on the integer pipe instead of GB300's narrow FP64 pipe.
+//
+// A complex128 row sweep needs 4 DFMA per 16-byte element, and GB300 retires
+// 2 DFMA per SM clock (measured: 1.25 TFLOP/s), so the FP64 pipe caps the
+// sweep at about 2.3 TB/s, a third of HBM.  Here each row of A and the vector
+// x are written in fixed point with 53 significant bits (the row's, resp.
+// the vector's, largest binary exponent as the scale; the error-free
+// splitting of Ozaki et al. carried to integers, as in the block products of
+// tc_ozaki.cu), each 53-bit integer is cut into two balanced 26-bit digits,
+// and a product a x is formed exactly from the digit products
+// a1 x1 2^52 + (a1 x0 + a0 x1) 2^26 by 64-bit integer multiply-adds
+// (IMAD.WIDE, ~60 per SM clock); only a0 x0 < 2^50 units is left out.  The
+// row sums are exact in int64 and converted to double every 256 elements.
+//
+// Accuracy per output: |error| <= 2.5 n 2^(Fa + Fx - 52) where 2^Fa > max|a_ij|
+// over the row and 2^Fx > max|x_j| -- the bound of an FP64 GEMV relative to
+// the row's and vector's largest entries (an FP64 GEMV's is relative to
+// sum |a_ij||x_j|); entries far below their row's largest keep fewer bits.
+//
+// The digits of A are made once per operator (16 bytes per element, as A
+// itself) and read in place of A; those of x once per sweep.  A matrix with
+// a non-finite entry, or a vector with one, takes the FP64-pipe sweep.
+#pragma once
+
+#include "common.cuh"
+#include "gemv.cuh"
+
+namespace ccg {
+
+// Fixed-point digits (d1, d0) of v with d1 2^26 + d0 = round(v 2^(52 - F))
+// where F = max(emax, 1) - 1022 is the scale of the row or vector whose
+// largest biased exponent is emax; |d1| <= 2^26, -2^25 <= d0 < 2^25.
+__device__ __forceinline__ void fx_split(double v, int emax, int& d1, int& d0) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned hi = (unsigned)(b >> 32);
+  const int E = (hi >> 20) & 0x7FF;
+  const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | ((unsigned long long)(E != 0) << 52);
+  int d = max(emax, 1) - max(E, 1) + 1;  // >= 1 since emax >= E
+  d = min(d, 63);                         // M < 2^53: any d >= 54 rounds to 0
+  long long r = (long long)((M + (1ull << (d - 1))) >> d);
+  if (hi >> 31) r = -r;
+  const long long a1 = (r + (1ll << 25)) >> 26;
+  d1 = (int)a1;
+  d0 = (int)(r - (a1 << 26));
+}
+
+__device__ __forceinline__ int fx_exp(double v) { return (int)((unsigned long long)__double_as_longlong(v) >> 52) & 0x7FF; }
+
+// Vector digits for one sweep (one block): the largest exponent of x, then
+// the digits (xr1, xr0, xi1, xi0).  meta[0] = the exponent, meta[1] = 1 when
+// x holds an infinity or NaN.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) fx_split_vector(const double2* __restrict__ x, int64_t n,
+                                                           int4* __restrict__ xd, int* __restrict__ meta,
+                                                           const SolveState* __restrict__ st) {
+  if (sweep_skipped(st, nullptr)) return;
+  __shared__ int wm[THREADS / 32];
+  int m = 0;
+  for (int64_t j = threadIdx.x; j < n; j += THREADS) {
+    const double2 v = x[j];
+    m = max(m, max(fx_exp(v.x), fx_exp(v.y)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  m = 0;
+#pragma unroll
+  for (int w = 0; w < THREADS / 32; ++w) m = max(m, wm[w]);
+  if (threadIdx.x == 0) {
+    meta[0] = m;
+    meta[1] = m == 0x7FF ? 1 : 0;
+  }
+  for (int64_t j = threadIdx.x; j < n; j += THREADS) {
+    const double2 v = x[j];
+    int4 q;
+    fx_split(v.x, m, q.x, q.y);
+    fx_split(v.y, m, q.z, q.w);
+    xd[j] = q;
+  }
+}
+
+// Exact complex digit products into int64: re += ar xr - ai xi,
+// im += ar xi + ai xr, high digit products (x 2^52) apart from the middle
+// ones (x 2^26).
+struct FxAcc {
+  long long hre, mre, him, mim;
+  __device__ __forceinline__ void zero() { hre = mre = him = mim = 0; }
+  __device__ __forceinline__ void mac(const int4 a, const int4 x) {
+    const int nai1 = -a.z, nai0 = -a.w;
+    hre += (long long)a.x * x.x;
+    hre += (long long)nai1 * x.z;
+    mre += (long long)a.x * x.y;
+    mre += (long long)a.y * x.x;
+    mre += (long long)nai1 * x.w;
+    mre += (long long)nai0 * x.z;
+    him += (long long)a.x * x.z;
+    him += (long long)a.z * x.x;
+    mim += (long long)a.x * x.w;
+    mim += (long long)a.y * x.z;
+    mim += (long long)a.z * x.y;
+    mim += (long long)a.w * x.x;
+  }
+  // the sums so far in units of 2^(Fa + Fx - 78), exactly up to the rounding
+  // of the int64 -> double conversions
+  __device__ __forceinline__ void flush(double& re, double& im) {
+    re += (double)hre * 67108864.0 + (double)mre;
+    im += (double)him * 67108864.0 + (double)mim;
+    zero();
+  }
+};
+
+__device__ __forceinline__ int4 ld_stream_i4(const int4* p) {
+  int4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.s32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+__device__ __forceinline__ int4 ldc_i4(const int4* p) {
+  int4 v;
+  asm volatile("ld.global.v4.s32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+  return v;
+}
+
+// y = A x from the digits: S warps per row as in gemv_rows_body, 4 loads in
+// flight per lane, int64 sums flushed to double every 256 elements.  With
+// meta[1] set (x not finite) the rows are summed from A on the FP64 pipe.
+// KC as in gemv_rows_body (the digits of x are rewritten between sweeps of a
+// persistent solve).
+template <int S, bool KC>
+__device__ __forceinline__ void gemv_fx_rows_body(const double2* __restrict__ A, int64_t lda, const int4* __restrict__ C,
+                                                  const int* __restrict__ rowexp, int64_t n, const double2* x,
+                                                  const int4* xd, int xexp, bool xbad, double2* y, int64_t lb,
+                                                  int64_t G) {
+  constexpr int RPB = kWarps / S;
+  __shared__ double2 part[kWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int seg = warp % S;
+  const int64_t u0 = n * seg / S, u1 = n * (seg + 1) / S;
+  const int64_t nrb = (n + RPB - 1) / RPB;
+  for (int64_t rb = lb; rb < nrb; rb += G) {
+    const int64_t row = rb * RPB + warp / S;
+    double sre = 0.0, sim = 0.0;
+    int er = 0;
+    if (row < n) {
+      if (xbad) {
+        const double2* a = A + row * lda;
+        double2 s0 = make_double2(0.0, 0.0);
+        for (int64_t u = u0 + lane; u < u1; u += 32) s0 = cfma(ld_stream(a + u), ldv_unit<KC>(x + u), s0);
+        sre = s0.x;
+        sim = s0.y;
+      } else {
+        er = rowexp[row];
+        const int4* c = C + row * n;
+        int64_t u = u0 + lane;
+        FxAcc acc;
+        while (u < u1) {
+          acc.zero();
+          const int64_t uend = u + 256 * 32 < u1 ? u + 256 * 32 : u1;
+          for (; u + 96 < uend; u += 128) {
+            const int4 q0 = ld_stream_i4(c + u), q1 = ld_stream_i4(c + u + 32), q2 = ld_stream_i4(c + u + 64),
+                       q3 = ld_stream_i4(c + u + 96);
+            int4 x0, x1, x2, x3;
+            if constexpr (KC) {
+              x0 = ldc_i4(xd + u); x1 = ldc_i4(xd + u + 32); x2 = ldc_i4(xd + u + 64); x3 = ldc_i4(xd + u + 96);
+            } else {
+              x0 = __ldg(xd + u); x1 = __ldg(xd + u + 32); x2 = __ldg(xd + u + 64); x3 = __ldg(xd + u + 96);
+            }
+            acc.mac(q0, x0);
+            acc.mac(q1, x1);
+            acc.mac(q2, x2);
+            acc.mac(q3, x3);
+          }
+          for (; u < uend; u += 32) {
+            const int4 xv = KC ? ldc_i4(xd + u) : __ldg(xd + u);
+            acc.mac(ld_stream_i4(c + u), xv);
+          }
+          acc.flush(sre, sim);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sre += __shfl_down_sync(0xffffffffu, sre, o);
+      sim += __shfl_down_sync(0xffffffffu, sim, o);
+    }
+    if (lane == 0) part[warp] = make_double2(sre, sim);
+    __syncthreads();
+    if (seg == 0 && lane == 0 && row < n) {
+      double2 t = part[warp];
+#pragma unroll
+      for (int q = 1; q < S; ++q) t = cadd(t, part[warp + q]);
+      if (!xbad) {
+        const int e = max(er, 1) + max(xexp, 1) - 2122;  // units 2^(Fa + Fx - 78)
+        t = make_double2(ldexp(t.x, e), ldexp(t.y, e));
+      }
+      y[row] = t;
+    }
+    __syncthreads();
+  }
+}
+
+template <int S>
+__global__ void __launch_bounds__(kBlock) gemv_fx_rows(const double2* __restrict__ A, int64_t lda,
+                                                       const int4* __restrict__ C, const int* __restrict__ rowexp,
+                                                       int64_t n, const double2* __restrict__ x,
+                                                       const int4* __restrict__ xd, const int* __restrict__ meta,
+                                                       double2* __restrict__ y, const SolveState* __restrict__ st,
+                                                       int* skip_rec = nullptr) {
+  if (sweep_skipped(st, skip_rec)) return;
+  gemv_fx_rows_body<S, false>(A, lda, C, rowexp, n, x, xd, meta[0], meta[1] != 0, y, blockIdx.x, gridDim.x);
+}
+
+}  // namespace ccg

@@ -44,6 +44,30 @@ __device__ __forceinline__ double2 ldg_unit(const double2* p) { return __ldg(p);
 __device__ __forceinline__ float4 ldg_unit(const float4* p) { return __ldg(p); }
 __device__ __forceinline__ float2 ldg_unit(const float2* p) { return __ldg(p); }
 
+// Vector loads of a sweep.  A kernel launch that only reads the vector
+// (KC = false) takes the read-only path; inside a persistent solve the same
+// vector is rewritten between sweeps (KC = true), so it is read with plain
+// coherent loads, which the group barrier's acquire orders after the writes.
+__device__ __forceinline__ double2 ldc_unit(const double2* p) {
+  double2 v;
+  asm volatile("ld.global.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float4 ldc_unit(const float4* p) {
+  float4 v;
+  asm volatile("ld.global.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float2 ldc_unit(const float2* p) {
+  float2 v;
+  asm volatile("ld.global.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  return v;
+}
+template <bool KC, class L> __device__ __forceinline__ L ldv_unit(const L* p) {
+  if constexpr (KC) return ldc_unit(p);
+  else return ldg_unit(p);
+}
+
 template <class T> __device__ __forceinline__ T warp_csum(T s) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -86,23 +110,21 @@ template <class R> struct MvOut {
 // last wave of blocks is a small fraction of the sweep (one warp per row
 // left ~1.7 waves of 8-row blocks at n = 8192, the second one 68% full).
 // Requires n % U == 0 and 16-byte aligned rows when U * sizeof(cx<R>) == 16.
-template <class R, int U, int S = 1>
-__global__ void __launch_bounds__(kBlock) gemv_n_rows(const cx<R>* __restrict__ A, int64_t lda, int64_t n,
-                                                      const cx<R>* __restrict__ x, cx<R>* __restrict__ y,
-                                                      const SolveState* __restrict__ st, int* skip_rec = nullptr) {
+template <class R, int U, int S, bool KC>
+__device__ __forceinline__ void gemv_rows_body(const cx<R>* __restrict__ A, int64_t lda, int64_t n,
+                                               const cx<R>* x, cx<R>* y, int64_t lb, int64_t G) {
   typedef Unit<R, U> Un;
   typedef typename Un::L L;
   static_assert(kWarps % S == 0, "S must divide the warps of a block");
   constexpr int RPB = kWarps / S;  // rows per block pass
   __shared__ cx<R> part[kWarps];
-  if (sweep_skipped(st, skip_rec)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int seg = warp % S;
   const int64_t nunits = n / U;
   const int64_t u0 = nunits * seg / S, u1 = nunits * (seg + 1) / S;
   const L* xv = reinterpret_cast<const L*>(x);
   const int64_t nrb = (n + RPB - 1) / RPB;
-  for (int64_t rb = blockIdx.x; rb < nrb; rb += gridDim.x) {
+  for (int64_t rb = lb; rb < nrb; rb += G) {
     const int64_t row = rb * RPB + warp / S;
     cx<R> s0 = mk<R>(0, 0), s1 = mk<R>(0, 0);
     if (row < n) {
@@ -111,8 +133,8 @@ __global__ void __launch_bounds__(kBlock) gemv_n_rows(const cx<R>* __restrict__ 
       for (; u + 96 < u1; u += 128) {
         const L a0 = ld_stream(a + u), a1 = ld_stream(a + u + 32), a2 = ld_stream(a + u + 64),
                 a3 = ld_stream(a + u + 96);
-        const L x0 = ldg_unit(xv + u), x1 = ldg_unit(xv + u + 32), x2 = ldg_unit(xv + u + 64),
-                x3 = ldg_unit(xv + u + 96);
+        const L x0 = ldv_unit<KC>(xv + u), x1 = ldv_unit<KC>(xv + u + 32), x2 = ldv_unit<KC>(xv + u + 64),
+                x3 = ldv_unit<KC>(xv + u + 96);
 #pragma unroll
         for (int c = 0; c < U; ++c) {
           s0 = cfma(Un::get(a0, c), Un::get(x0, c), s0);
@@ -122,7 +144,7 @@ __global__ void __launch_bounds__(kBlock) gemv_n_rows(const cx<R>* __restrict__ 
         }
       }
       for (; u < u1; u += 32) {
-        const L a0 = ld_stream(a + u), x0 = ldg_unit(xv + u);
+        const L a0 = ld_stream(a + u), x0 = ldv_unit<KC>(xv + u);
 #pragma unroll
         for (int c = 0; c < U; ++c) s0 = cfma(Un::get(a0, c), Un::get(x0, c), s0);
       }
@@ -144,24 +166,45 @@ __global__ void __launch_bounds__(kBlock) gemv_n_rows(const cx<R>* __restrict__ 
   }
 }
 
+template <class R, int U, int S = 1>
+__global__ void __launch_bounds__(kBlock) gemv_n_rows(const cx<R>* __restrict__ A, int64_t lda, int64_t n,
+                                                      const cx<R>* __restrict__ x, cx<R>* __restrict__ y,
+                                                      const SolveState* __restrict__ st, int* skip_rec = nullptr) {
+  if (sweep_skipped(st, skip_rec)) return;
+  gemv_rows_body<R, U, S, false>(A, lda, n, x, y, blockIdx.x, gridDim.x);
+}
+
 // Column-tiled sweep.  grid = (column chunks, row ranges).  With Y1 it
 // writes P1[chunk * n + row] = sum over the chunk's columns of A[row, c] x1[c];
 // with Y2 it writes P2[range * n + col] = sum over the range's rows of
 // conj(A[row, col]) x2[row].
-template <class R, int U, int E, bool Y1, bool Y2>
+// x2 values of a row: read-only path in a plain launch, coherent loads in a
+// persistent solve (see ldv_unit).
+template <bool KC, class T> __device__ __forceinline__ T ldv_elem(const T* p) {
+  if constexpr (KC) {
+    return ldc_unit(p);
+  } else {
+    return __ldg(p);
+  }
+}
+
+// One tile: column chunk `chunk` (32 E units) and row range `range`.  KC as
+// in gemv_rows_body.
+// Shared memory of a tile's column sums: kWarps x 32 E U complex values.
+template <class R, int U, int E> constexpr int tile_smem_elems() { return kWarps * 32 * E * U; }
+
+template <class R, int U, int E, bool Y1, bool Y2, bool KC = false>
 __device__ __forceinline__ void gemv_tile_body(const cx<R>* __restrict__ A, int64_t lda, int64_t n,
-                                               int64_t rows_per_range, const cx<R>* __restrict__ x1,
-                                               const cx<R>* __restrict__ x2, cx<R>* __restrict__ P1,
-                                               cx<R>* __restrict__ P2, const SolveState* __restrict__ st,
-                                               int* skip_rec) {
+                                               int64_t rows_per_range, const cx<R>* x1, const cx<R>* x2,
+                                               cx<R>* P1, cx<R>* P2, int64_t chunk, int64_t range,
+                                               cx<R>* smem_ext = nullptr) {
   typedef Unit<R, U> Un;
   typedef typename Un::L L;
   constexpr int CBU = 32 * E;  // units per column chunk
-  if (sweep_skipped(st, skip_rec)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t nunits = n / U;
-  const int64_t unit0 = (int64_t)blockIdx.x * CBU;
-  const int64_t r0 = (int64_t)blockIdx.y * rows_per_range;
+  const int64_t unit0 = chunk * CBU;
+  const int64_t r0 = range * rows_per_range;
   const int64_t r1 = r0 + rows_per_range < n ? r0 + rows_per_range : n;
 
   L xl[E];
@@ -170,7 +213,7 @@ __device__ __forceinline__ void gemv_tile_body(const cx<R>* __restrict__ A, int6
 #pragma unroll
     for (int j = 0; j < E; ++j) {
       const int64_t u = unit0 + lane + 32 * j;
-      xl[j] = u < nunits ? ldg_unit(xv + u) : Un::zero();
+      xl[j] = u < nunits ? ldv_unit<KC>(xv + u) : Un::zero();
     }
   }
   cx<R> acc[E][U];
@@ -190,7 +233,7 @@ __device__ __forceinline__ void gemv_tile_body(const cx<R>* __restrict__ A, int6
         av[j] = u < nunits ? ld_stream(a + u) : Un::zero();
       }
       if (Y2) {
-        const cx<R> xr = x2[r];
+        const cx<R> xr = ldv_elem<KC>(x2 + r);
 #pragma unroll
         for (int j = 0; j < E; ++j)
 #pragma unroll
@@ -202,7 +245,7 @@ __device__ __forceinline__ void gemv_tile_body(const cx<R>* __restrict__ A, int6
 #pragma unroll
         for (int c = 0; c < U; ++c) s = cfma(Un::get(av[j], c), Un::get(xl[j], c), s);
       s = warp_csum(s);
-      if (lane == 0) P1[(int64_t)blockIdx.x * n + r] = s;
+      if (lane == 0) P1[chunk * n + r] = s;
     }
   } else if constexpr (sizeof(R) == 8) {
     // A^H x2 alone, complex128: bound by the FP64 pipe, one row per iteration
@@ -214,7 +257,7 @@ __device__ __forceinline__ void gemv_tile_body(const cx<R>* __restrict__ A, int6
         const int64_t u = unit0 + lane + 32 * j;
         av[j] = u < nunits ? ld_stream(a + u) : Un::zero();
       }
-      const cx<R> xr = x2[r];
+      const cx<R> xr = ldv_elem<KC>(x2 + r);
 #pragma unroll
       for (int j = 0; j < E; ++j)
 #pragma unroll
@@ -230,7 +273,7 @@ __device__ __forceinline__ void gemv_tile_body(const cx<R>* __restrict__ A, int6
     const int64_t nrw = rw < r1 ? (r1 - rw + kWarps - 1) / kWarps : 0;
     for (int64_t t0 = 0; t0 < nrw; t0 += 32) {
       cx<R> xlane = mk<R>(0, 0);
-      if (t0 + lane < nrw) xlane = x2[rw + kWarps * (t0 + lane)];
+      if (t0 + lane < nrw) xlane = ldv_elem<KC>(x2 + rw + kWarps * (t0 + lane));
       const int cnt = (int)(nrw - t0 < 32 ? nrw - t0 : 32);
       int t = 0;
       for (; t + 1 < cnt; t += 2) {
@@ -272,21 +315,29 @@ __device__ __forceinline__ void gemv_tile_body(const cx<R>* __restrict__ A, int6
     }
   }
   if (Y2) {
-    __shared__ cx<R> sm[kWarps][CBU * U];
+    // a persistent launch passes one buffer for all its tile shapes
+    cx<R>* sm;
+    if constexpr (KC) {
+      sm = smem_ext;
+    } else {
+      __shared__ cx<R> sm_own[kWarps * CBU * U];
+      sm = sm_own;
+    }
 #pragma unroll
     for (int j = 0; j < E; ++j)
 #pragma unroll
-      for (int c = 0; c < U; ++c) sm[warp][(lane + 32 * j) * U + c] = acc[j][c];
+      for (int c = 0; c < U; ++c) sm[warp * CBU * U + (lane + 32 * j) * U + c] = acc[j][c];
     __syncthreads();
     for (int t = threadIdx.x; t < CBU * U; t += kBlock) {
       const int64_t col = unit0 * U + t;
       if (col < n) {
-        cx<R> s = sm[0][t];
+        cx<R> s = sm[t];
 #pragma unroll
-        for (int w = 1; w < kWarps; ++w) s = cadd(s, sm[w][t]);
-        P2[(int64_t)blockIdx.y * n + col] = s;
+        for (int w = 1; w < kWarps; ++w) s = cadd(s, sm[w * CBU * U + t]);
+        P2[range * n + col] = s;
       }
     }
+    if (KC) __syncthreads();   // a persistent block's next tile reuses sm
   }
 }
 
@@ -300,14 +351,16 @@ __global__ void __launch_bounds__(kBlock) gemv_tile(const cx<R>* __restrict__ A,
                                                     cx<R>* __restrict__ P2, const SolveState* __restrict__ st,
                                                     int* skip_rec = nullptr) {
   static_assert(Y1, "A^H x alone runs in gemv_tile_h");
-  gemv_tile_body<R, U, E, Y1, Y2>(A, lda, n, rows_per_range, x1, x2, P1, P2, st, skip_rec);
+  if (sweep_skipped(st, skip_rec)) return;
+  gemv_tile_body<R, U, E, Y1, Y2>(A, lda, n, rows_per_range, x1, x2, P1, P2, blockIdx.x, blockIdx.y);
 }
 template <class R, int U, int E>
 __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 3 : 1)
     gemv_tile_h(const cx<R>* __restrict__ A, int64_t lda, int64_t n, int64_t rows_per_range,
                 const cx<R>* __restrict__ x2, cx<R>* __restrict__ P2, const SolveState* __restrict__ st,
                 int* skip_rec = nullptr) {
-  gemv_tile_body<R, U, E, false, true>(A, lda, n, rows_per_range, nullptr, x2, nullptr, P2, st, skip_rec);
+  if (sweep_skipped(st, skip_rec)) return;
+  gemv_tile_body<R, U, E, false, true>(A, lda, n, rows_per_range, nullptr, x2, nullptr, P2, blockIdx.x, blockIdx.y);
 }
 
 }  // namespace ccg

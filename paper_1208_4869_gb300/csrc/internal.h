@@ -59,6 +59,12 @@ struct ccg_operator {
   void* oz_a = nullptr;
   cudaStream_t oz_stream = nullptr;
   alignas(64) unsigned char oz_map[8][128] = {};
+  // fixed-point digits of a complex128 dense matrix for the integer-pipe
+  // sweep (fx.cuh), made on first use: n x n int4 digits (leading dimension
+  // n), then n row exponents and a flag word
+  int fx_state = 0;   // 0 not made, 1 ready, -1 unusable (non-finite entry, or no memory)
+  void* fx_a = nullptr;
+  cudaStream_t fx_stream = nullptr;
 };
 
 struct ccg_handle {
@@ -100,6 +106,18 @@ struct ccg_handle {
   int tc_exact = 1;
   void* oz_buf = nullptr;
   size_t oz_bytes = 0;
+  // persistent solves (persist.cu): enabled flag, blocks per SM (0: the
+  // occupancy limit), the group barriers' wait limit in SM clock cycles, and
+  // the test hook that withholds one block's arrival
+  int persistent = 2;   // 0 never, 1 always, 2 as the tuned table says (tune_table.h)
+  int pk_blocks = 0;
+  int fx_mode = 1;   // complex128 A x: 1 fixed-point digits on the integer pipe, 0 the FP64 pipe
+  long long wait_limit = 4ll << 30;
+  int test_withhold = 0;
+  // per timed pair: the units (sweeps) and bytes it stands for
+  std::vector<int64_t> tev_units;
+  std::vector<double> tev_bytes;
+  double timed_bytes[2 * CCG_SWEEP_KINDS] = {};
 };
 
 namespace ccg {
@@ -112,6 +130,9 @@ int arena_reserve(ccg_handle* h, size_t bytes);
 void timing_begin(ccg_handle* h);
 void timing_end(ccg_handle* h, int dtype, int kind, double bytes);
 void timing_collect(ccg_handle* h);
+// The last timed pair stands for `units` sweeps of `bytes` in total (a
+// persistent launch); 0 units leaves it out.
+void timing_set_units(ccg_handle* h, int64_t units, double bytes);
 // Device flag of the sweep being timed (between timing_begin and timing_end),
 // or nullptr when timing is off.
 int* timing_rec(ccg_handle* h);
@@ -145,7 +166,21 @@ int oz_block_product(ccg_handle* h, const ccg_operator* op, const double2* X, do
 int oz_block_product(ccg_handle* h, const ccg_operator* op, const float2* X, float2* Y, int k, const int* skip);
 int oz_check_error(ccg_handle* h);
 void oz_free(ccg_operator* op);
+// The fixed-point digits of a complex128 dense operator (made on first use,
+// on the handle's stream); false when the operator cannot use them.
+bool fx_prepare(ccg_handle* h, const ccg_operator* op);
+void fx_free(ccg_operator* op);
 int block_matvec(ccg_handle* h, const ccg_operator* op, int64_t k, const void* X, int64_t ldx, void* Y, int64_t ldy);
+// Many dense systems in one persistent launch each (persist.cu).
+int solve_multi(ccg_handle* h, int method, int count, const ccg_operator* const* ops, const void* const* y,
+                void* const* x, const double* tol, int maxit, int32_t* iters, int32_t* status, double* relres);
+int solve_multi_refined(ccg_handle* h, int method, int count, const ccg_operator* const* ops,
+                        const ccg_operator* const* ops_in, const void* const* y, void* const* x, const double* tol,
+                        int max_outer, double inner_tol, int inner_maxit, int32_t* outer, int32_t* inner,
+                        int32_t* status, double* relres);
+// Resident blocks of the persistent launch for `method` on complex64 (dtype
+// CCG_C64) or complex128 operators: the most systems one launch takes.
+int pk_capacity(ccg_handle* h, int method, int dtype);
 int matvec_dense(ccg_handle* h, const ccg_operator* op, int trans, const void* x, void* y);
 int dot_device(ccg_handle* h, ccg_dtype dtype, int64_t n, const void* u, const void* v, int conj, double* out2);
 

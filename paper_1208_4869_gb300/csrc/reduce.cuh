@@ -100,12 +100,12 @@ __device__ __forceinline__ void block_sum(A (&v)[NQ], double (&out)[NQ]) {
   __syncthreads();
 }
 
+// The same over a group of `nblocks` blocks (block `bid` of the group) of a
+// persistent launch; grid_reduce is the whole grid.
 template <int NQ, class A>
-__device__ __forceinline__ bool grid_reduce(A (&v)[NQ], double* __restrict__ partials,
-                                            unsigned int* counter, double (&tot)[NQ]) {
+__device__ __forceinline__ bool group_reduce(A (&v)[NQ], double* __restrict__ partials, unsigned int* counter,
+                                             double (&tot)[NQ], int bid, int nblocks) {
   __shared__ bool is_last;
-  const int nblocks = gridDim.x * gridDim.y;
-  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
   double bs[NQ];
   block_sum<NQ>(v, bs);
   if (threadIdx.x == 0) {
@@ -128,6 +128,12 @@ __device__ __forceinline__ bool grid_reduce(A (&v)[NQ], double* __restrict__ par
   block_sum<NQ>(s, tot);
   if (threadIdx.x == 0) *counter = 0u;
   return true;
+}
+
+template <int NQ, class A>
+__device__ __forceinline__ bool grid_reduce(A (&v)[NQ], double* __restrict__ partials,
+                                            unsigned int* counter, double (&tot)[NQ]) {
+  return group_reduce<NQ>(v, partials, counter, tot, blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y);
 }
 
 
