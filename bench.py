@@ -58,6 +58,8 @@ def parse_args(argv=None):
     p.add_argument("--serving-kinds", choices=["both", "dense", "dipole"], default="both",
                    help="keep only these requests of the serving stream")
     p.add_argument("--baseline-requests", type=int, default=200)
+    p.add_argument("--small-requests", type=int, default=200,
+                   help="serving: small dense requests timed with and without many-system batching")
     p.add_argument("--fp64-columns", type=int, default=32,
                    help="batched workload: right-hand sides timed one at a time in complex128 (the rate is per solve)")
     p.add_argument("--nrhs", type=int, default=256)
@@ -390,6 +392,87 @@ def cpu_baseline_rows(A, y, methods, tol, maxit, inner_tol, budget_s=3.0):
     return rows
 
 
+# ----------------------------------------------------------------- cuFFT comparison (dipole workload)
+def cufft_dipole_comparison(torch, W, h, op32, L, kd, m, reps=20):
+    """The dipole operator applied with the vendor FFT (torch.fft = cuFFT) on
+    the same zero-padded (2L)^3 grids: scatter p, three forward 3D transforms,
+    the 3 x 3 multiply with the transformed field tensor, three inverse
+    transforms, gather on the occupied sites, p / alpha - conv.  A timing
+    yardstick for the library's own FFT kernels, checked against the
+    library's operator on one vector (bench code only; the library never
+    calls cuFFT)."""
+    import numpy as np
+    occ = W.sphere_occupancy(L)
+    sites = torch.from_numpy(W.occupied_sites(occ).astype(np.int64)).cuda()
+    M = 2 * L
+    dev = sites.device
+    # field tensor on the circulant grid: index q < L is displacement q,
+    # M - q is -q, L (and the origin) carry zero
+    q = torch.arange(M, device=dev, dtype=torch.float64)
+    d = torch.where(q < L, q, q - M)
+    d[L] = 0.0
+    dx, dy, dz = torch.meshgrid(d, d, d, indexing="ij")
+    r = torch.sqrt(dx * dx + dy * dy + dz * dz)
+    valid = (r > 0) & (torch.arange(M, device=dev)[:, None, None] != L) & \
+        (torch.arange(M, device=dev)[None, :, None] != L) & (torch.arange(M, device=dev)[None, None, :] != L)
+    rs = torch.where(valid, r, torch.ones_like(r))
+    u = [dx / rs, dy / rs, dz / rs]
+    kr = kd * rs
+    ph = torch.exp(1j * kr) / rs ** 3
+    comps = []
+    for a, b in ((0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)):
+        uu = u[a] * u[b]
+        delta = 1.0 if a == b else 0.0
+        g = ph * ((kr * kr) * (delta - uu) + (1 - 1j * kr) * (3 * uu - delta))
+        comps.append(torch.where(valid, g, torch.zeros_like(g)))
+    Gh = torch.fft.fftn(torch.stack(comps).to(torch.complex64), dim=(-3, -2, -1))   # 6 x M^3
+    alpha = (3 / (4 * np.pi)) * (m * m - 1) / (m * m + 2)
+    N = sites.shape[0]
+    lin = (sites[:, 0] * M + sites[:, 1]) * M + sites[:, 2]
+    grid = torch.zeros((3, M * M * M), dtype=torch.complex64, device=dev)
+    idx = ((0, 1, 2), (1, 3, 4), (2, 4, 5))
+
+    def apply(p):
+        grid.zero_()
+        grid[:, lin] = p.view(3, N)
+        X = torch.fft.fftn(grid.view(3, M, M, M), dim=(-3, -2, -1))
+        Y = torch.stack([Gh[idx[a][0]] * X[0] + Gh[idx[a][1]] * X[1] + Gh[idx[a][2]] * X[2] for a in range(3)])
+        conv = torch.fft.ifftn(Y, dim=(-3, -2, -1)).reshape(3, -1)[:, lin]
+        return (p.view(3, N) / complex(alpha) - conv).reshape(-1)
+
+    def ffts_only():
+        X = torch.fft.fftn(grid.view(3, M, M, M), dim=(-3, -2, -1))
+        return torch.fft.ifftn(X, dim=(-3, -2, -1))
+
+    rng = np.random.default_rng(7)
+    p = torch.from_numpy((rng.standard_normal(3 * N) + 1j * rng.standard_normal(3 * N)).astype(np.complex64)).cuda()
+    ref = torch.empty_like(p)
+    h.matvec(op32, p, ref)
+    got = apply(p)
+    torch.cuda.synchronize()
+    diff = float((got - ref).abs().max() / ref.abs().max())
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = torch.empty_like(p)
+    return {"cufft_convolution_ms": timed(lambda: apply(p)), "cufft_ffts_only_ms": timed(ffts_only),
+            "library_application_ms": timed(lambda: h.matvec(op32, p, out)),
+            "max_rel_diff_vs_library": diff,
+            "what": "torch.fft (cuFFT) convolution of the same %d^3 grids: scatter, 3 forward + 3 inverse 3D C2C "
+                    "FFTs, 3x3 tensor multiply, gather (complex64); cufft_ffts_only_ms = the six transforms alone"
+                    % M}
+
+
 # ----------------------------------------------------------------- reference arm
 def run_reference(args):
     """The oracle as the reference arm: its OpenMP build on all allowed host
@@ -503,6 +586,27 @@ def measure_serving(args, local, world, rank):
                 if r["status"] != 0 or r["relres"] > reqs[i]["tol"]]
     span_max = reduce_max(span, world)
     solves = reduce_sum(len(res), world)
+    # the small-request slice (dense, n <= 2048) submitted at once, with the
+    # many-system batching on and off: the launch-latency-bound part of the stream
+    small = [r for r in reqs if r["kind"] == "dense" and r["n"] <= 2048][:args.small_requests]
+    slice_ = {}
+    for name, max_n in (("batched", 2048), ("per_slot", 0)):
+        sv = ccg.Server(device=local, slots=args.slots, budget_bytes=120 << 30)
+        sv.set_batching(max_n=max_n)
+        for r in small[:args.slots]:
+            sv.wait(sv.submit(**r))
+        t0 = time.perf_counter()
+        tk = [sv.submit(**r) for r in small]
+        rs = [sv.wait(t)[0] for t in tk]
+        dt = time.perf_counter() - t0
+        sv.close()
+        rhs = sum(r["nrhs"] for r in small)
+        slice_[name] = {"requests_per_s": len(small) / dt, "rhs_per_s": rhs / dt, "seconds": dt,
+                        "all_converged": all(x["status"] == 0 and x["relres"] <= q["tol"] for x, q in zip(rs, small))}
+    slice_["requests"] = len(small)
+    slice_["what"] = ("the stream's first %d dense requests with n <= 2048 (1-64 right-hand sides each), all submitted "
+                      "at once to %d slots; batched = many-system launches (ccg_solve_multi_refined), per_slot = "
+                      "each request on its own slot" % (len(small), args.slots))
     nb = min(args.baseline_requests, len(reqs))
     base = serve(1, reqs[:nb], np.zeros(nb), 1)        # complex128, one request and one RHS at a time
     bspan = max(r["t_done"] for r in base) - min(r["t_submit"] for r in base)
@@ -521,6 +625,7 @@ def measure_serving(args, local, world, rank):
         "other_paths": {"fp64_one_at_a_time": {"value": nb / bspan, "unit": "solves/s", "requests": nb,
                                                "all_converged": all(r["status"] == 0 for r in base),
                                                "ms_per_request": 1e3 * bspan / nb}},
+        "small_dense_slice": slice_,
         "clocks": clk,
     }
 
@@ -773,6 +878,9 @@ def measure_workload(args, ctx, h, stream, world, rank, dev, torch, ccg, W, cloc
                "h2d_bytes_per_step": y.nbytes, "d2h_bytes_per_step": y.nbytes}
 
     roof = roofline(ccg, stats, n, dipole, args.nrhs if batched else 1)
+    if dipole and rank == 0:
+        roof["cufft_comparison"] = cufft_dipole_comparison(torch, W, h, op32, args.L, W.DIPOLE_CFG["kd"],
+                                                           W.DIPOLE_CFG["m"])
     lat_sorted = sorted(lat)
     return {
         "workload": wl["descr"], "value": value, "unit": "solves/s", "ms_per_step": t_max_ms / steps,
@@ -844,7 +952,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
         a3 = parse_args(["--workload", "serving", "--requests", str(args.requests),
-                         "--baseline-requests", str(args.baseline_requests), "--slots", str(args.slots)])
+                         "--baseline-requests", str(args.baseline_requests), "--slots", str(args.slots),
+                         "--small-requests", str(args.small_requests)])
         others["serving"] = measure_serving(a3, local, world, rank)
 
     if rank == 0:

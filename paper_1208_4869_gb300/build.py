@@ -21,6 +21,12 @@ LIB = os.path.join(OUT_DIR, "libccg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I" + os.path.join(ROOT, "include")]
+# The fused update kernels ("phases", phases.cuh) run in two translation units:
+# as kernels of the kernel-per-step loop (solve.cu) and inside the persistent
+# launch (persist.cu).  Without multiply-add contraction both compile every
+# phase's arithmetic exactly as written (the sweeps state their FMAs
+# explicitly), so the two forms of a solve are bitwise equal.
+FILE_FLAGS = {"solve.cu": ["-fmad=false"], "persist.cu": ["-fmad=false"]}
 
 
 def nvcc():
@@ -43,6 +49,7 @@ def _fingerprint():
         with open(f, "rb") as fh:
             h.update(fh.read())
     h.update(" ".join(ARCH + NVCC_FLAGS).encode())
+    h.update(repr(sorted(FILE_FLAGS.items())).encode())
     return h.hexdigest()
 
 
@@ -58,7 +65,7 @@ def build(force=False, verbose=False):
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc] + ARCH + NVCC_FLAGS + ["-c", src, "-o", obj]
+        cmd = [cc] + ARCH + NVCC_FLAGS + FILE_FLAGS.get(os.path.basename(src), []) + ["-c", src, "-o", obj]
         if verbose:
             cmd += ["-Xptxas", "-v"]
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -123,13 +123,14 @@ def lib():
     L.ccg_server_now.argtypes = [vp]
     L.ccg_server_estimate.argtypes = [ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
     L.ccg_server_charged.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+    L.ccg_server_set_batching.argtypes = [vp, i64, i32]
     L.ccg_server_destroy.argtypes = [vp]
     L.ccg_launch_count.restype = i64
     L.ccg_launch_count.argtypes = [vp]
     for name in ("ccg_create", "ccg_destroy", "ccg_set_stream", "ccg_op_dense", "ccg_op_dipole", "ccg_op_destroy", "ccg_matvec",
                  "ccg_dot", "ccg_solve", "ccg_solve_refined", "ccg_solve_batched", "ccg_solve_batched_refined",
                  "ccg_block_matvec", "ccg_set_option", "ccg_solve_multi", "ccg_solve_multi_refined", "ccg_server_create", "ccg_server_submit", "ccg_server_poll",
-                 "ccg_server_wait", "ccg_server_destroy", "ccg_server_estimate", "ccg_server_charged",
+                 "ccg_server_wait", "ccg_server_destroy", "ccg_server_estimate", "ccg_server_charged", "ccg_server_set_batching",
                  "ccg_timing_enable", "ccg_timing_read", "ccg_timing_reset"):
         getattr(L, name).restype = i32
     if L.ccg_abi_version() != 1:
@@ -445,6 +446,10 @@ class Server:
 
     def now(self):
         return lib().ccg_server_now(self.sv)
+
+    def set_batching(self, max_n=2048, max_systems=256):
+        """ccg_server_set_batching: small dense requests solved together (max_n = 0: off)."""
+        _check(lib().ccg_server_set_batching(self.sv, int(max_n), int(max_systems)))
 
     def charged(self):
         """ccg_server_charged: bytes charged against the budget now."""

@@ -1,5 +1,7 @@
 // The fixed-point digit copy of a complex128 dense operator (fx.cuh): made on
 // the first integer-pipe sweep, stream-ordered, freed with the operator.
+// Layout of the allocation: n x n int4 digits, 256 bytes of padding, the n row
+// exponents, then the flag word that marks a non-finite entry.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -59,23 +61,14 @@ bool fx_prepare(ccg_handle* h, const ccg_operator* op_c) {
   char* base = static_cast<char*>(op->fx_a);
   int* rowexp = reinterpret_cast<int*>(base + cbytes + 256);
   int* bad = reinterpret_cast<int*>(base + cbytes + 256 + (size_t)n * sizeof(int));
-  int flag = 0;
   if (cudaMemsetAsync(bad, 0, sizeof(int), s) != cudaSuccess) { cudaGetLastError(); op->fx_state = -1; return false; }
   const int grid = (int)std::min<int64_t>((n + kWarps - 1) / kWarps, (int64_t)h->num_sms * 8);
   fx_split_matrix<<<grid, kBlock, 0, s>>>(static_cast<const double2*>(op->A), op->lda, n, reinterpret_cast<int4*>(base),
                                           rowexp, bad);
   ++h->launches;
-  if (cudaMemcpyAsync(&flag, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess) {
-    cudaGetLastError();
-    flag = 1;
-  }
-  if (flag) {
-    cudaFreeAsync(op->fx_a, s);
-    op->fx_a = nullptr;
-    op->fx_state = -1;
-    return false;
-  }
+  if (cudaGetLastError() != cudaSuccess) { op->fx_state = -1; return false; }
+  // a non-finite entry leaves its flag set on the device: the sweeps read it
+  // and take the FP64 pipe (no synchronisation here)
   op->fx_state = 1;
   return true;
 }

@@ -19,7 +19,8 @@
 //
 // The digits of A are made once per operator (16 bytes per element, as A
 // itself) and read in place of A; those of x once per sweep.  A matrix with
-// a non-finite entry, or a vector with one, takes the FP64-pipe sweep.
+// a non-finite entry (flagged on the device when the digits are made), or a
+// vector with one, takes the FP64-pipe sweep.
 #pragma once
 
 #include "common.cuh"
@@ -201,6 +202,7 @@ __device__ __forceinline__ void gemv_fx_rows_body(const double2* __restrict__ A,
   }
 }
 
+// rowexp[n] (the word after the row exponents) marks a non-finite entry of A.
 template <int S>
 __global__ void __launch_bounds__(kBlock) gemv_fx_rows(const double2* __restrict__ A, int64_t lda,
                                                        const int4* __restrict__ C, const int* __restrict__ rowexp,
@@ -209,7 +211,8 @@ __global__ void __launch_bounds__(kBlock) gemv_fx_rows(const double2* __restrict
                                                        double2* __restrict__ y, const SolveState* __restrict__ st,
                                                        int* skip_rec = nullptr) {
   if (sweep_skipped(st, skip_rec)) return;
-  gemv_fx_rows_body<S, false>(A, lda, C, rowexp, n, x, xd, meta[0], meta[1] != 0, y, blockIdx.x, gridDim.x);
+  gemv_fx_rows_body<S, false>(A, lda, C, rowexp, n, x, xd, meta[0], meta[1] != 0 || rowexp[n] != 0, y, blockIdx.x,
+                              gridDim.x);
 }
 
 }  // namespace ccg

@@ -194,7 +194,7 @@ template <class R, int U> struct PkCtx {
     }
     if (!group_sync(S.bar, G, limit, fault)) return;
     const int E = *reinterpret_cast<volatile const int*>(S.fxe + slot);
-    const bool bad = E == 0x7FF;
+    const bool bad = E == 0x7FF || S.fxrow[S.n] != 0;   // x or A not finite: the FP64 pipe
     if (!bad) {
       for (int64_t i = (int64_t)lb * kBlock + threadIdx.x; i < S.n; i += stride) {
         const double2 v = ldc_unit(x + i);

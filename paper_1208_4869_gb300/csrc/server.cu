@@ -28,6 +28,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "workspace.cuh"
 
 namespace ccg {
 
@@ -120,6 +121,10 @@ struct DipoleOps {
 struct ccg_server {
   int device = 0;
   uint64_t budget = 0, used = 0;
+  // dense requests of order <= batch_n (0: none) are solved together, up to
+  // batch_max right-hand sides per launch (ccg_solve_multi_refined)
+  int64_t batch_n = 2048;
+  int batch_max = 256;
   Clock::time_point t0;
   std::mutex mu;
   std::condition_variable cv;
@@ -159,8 +164,9 @@ uint64_t estimate_bytes(const ccg_request& r) {
     return (uint64_t)(40.0 * N3 * 16) + dipole_op_bytes(r.L);
   }
   const double n = (double)r.n, k = std::max(1, r.nrhs);
-  // complex128 and complex64 matrices, the split-bf16 terms, blocks and workspace
-  double b = 16 * n * n + 8 * n * n + 8 * n * n + 40.0 * n * std::max(k, 8.0) * 16 + 64.0 * n * 16;
+  // complex128 and complex64 matrices, the split-bf16 terms, the fixed-point
+  // digits of the complex128 matrix, blocks and workspace
+  double b = 16 * n * n + 8 * n * n + 8 * n * n + 16 * n * n + 40.0 * n * std::max(k, 8.0) * 16 + 64.0 * n * 16;
   // batched requests also keep the exact products' digit slices of both
   // matrices (8 and 4 bf16 slices of n x 2n) where those products apply
   if (k > 1 && r.n % 4 == 0 && 2 * r.n <= 65536) b += 32 * n * n + 16 * n * n;
@@ -251,6 +257,91 @@ int run_dense(ccg_handle* h, cudaStream_t s, const ccg_request& r, ccg_result& r
   cudaStreamSynchronize(s);
   res.n = n;
   res.nrhs = k;
+  return st;
+}
+
+// Small dense requests solved together: every right-hand side of every
+// request is one system of a ccg_solve_multi_refined launch (the requests'
+// matrices and blocks generated as in run_dense); results per request are
+// the worst status and the largest iteration count and residual of its
+// columns.  Returns the launch's status (per-request statuses in res).
+int run_dense_batch(ccg_handle* h, cudaStream_t s, std::vector<std::shared_ptr<Entry>>& batch) {
+  const size_t m = batch.size();
+  std::vector<double2*> A64(m, nullptr), Y(m, nullptr), X(m, nullptr);
+  std::vector<float2*> A32(m, nullptr);
+  std::vector<ccg_operator*> o64(m, nullptr), o32(m, nullptr);
+  std::vector<const ccg_operator*> ops, ops_in;
+  std::vector<const void*> yv;
+  std::vector<void*> xv;
+  std::vector<double> tol;
+  std::vector<size_t> owner;
+  int st = CCG_OK;
+  int maxit = 1000;
+  for (size_t q = 0; q < m && st == CCG_OK; ++q) {
+    const ccg_request& r = batch[q]->req;
+    const int64_t n = r.n;
+    const int k = std::max(1, r.nrhs);
+    if (r.maxit > 0) maxit = std::min(maxit, r.maxit);
+    if (cudaMallocAsync(&A64[q], (size_t)n * n * sizeof(double2), s) != cudaSuccess ||
+        cudaMallocAsync(&A32[q], (size_t)n * n * sizeof(float2), s) != cudaSuccess ||
+        cudaMallocAsync(&Y[q], (size_t)n * k * sizeof(double2), s) != cudaSuccess ||
+        cudaMallocAsync(&X[q], (size_t)n * k * sizeof(double2), s) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("server: request allocation failed");
+      st = CCG_ERR_NOMEM;
+      break;
+    }
+    gen_dense<<<2048, kBlock, 0, s>>>(A64[q], A32[q], n, r.shift, r.seed);
+    gen_rhs<<<512, kBlock, 0, s>>>(Y[q], n, k, r.seed);
+    cudaMemsetAsync(X[q], 0, (size_t)n * k * sizeof(double2), s);
+    st = ccg_op_dense(h, CCG_C128, n, A64[q], n, 0, &o64[q]);
+    if (st == CCG_OK) st = ccg_op_dense(h, CCG_C64, n, A32[q], n, 0, &o32[q]);
+    for (int c = 0; c < k && st == CCG_OK; ++c) {
+      ops.push_back(o64[q]);
+      ops_in.push_back(o32[q]);
+      yv.push_back(Y[q] + (int64_t)c * n);
+      xv.push_back(X[q] + (int64_t)c * n);
+      tol.push_back(r.tol);
+      owner.push_back(q);
+    }
+  }
+  const size_t cnt = ops.size();
+  std::vector<int32_t> outer(cnt, 0), sts(cnt, 0);
+  std::vector<double> rr(cnt, 0.0);
+  if (st == CCG_OK)
+    st = ccg_solve_multi_refined(h, CCG_BICGSTAB, (int64_t)cnt, ops.data(), ops_in.data(), yv.data(), xv.data(),
+                                 tol.data(), 30, 1e-5, maxit, outer.data(), nullptr, sts.data(), rr.data());
+  for (size_t q = 0; q < m; ++q) {
+    ccg_result& res = batch[q]->res;
+    res.status = st < 0 ? st : CCG_OK;
+    res.iters = 0;
+    res.relres = 0.0;
+    res.n = batch[q]->req.n;
+    res.nrhs = std::max(1, batch[q]->req.nrhs);
+  }
+  if (st >= 0) {
+    for (size_t c = 0; c < cnt; ++c) {
+      ccg_result& res = batch[owner[c]]->res;
+      res.iters = std::max(res.iters, outer[c]);
+      res.relres = std::max(res.relres, rr[c]);
+      if (sts[c] < 0) res.status = std::min(res.status, sts[c]);
+      else if (res.status >= 0) res.status = std::max(res.status, sts[c]);
+    }
+  }
+  for (size_t q = 0; q < m; ++q) {
+    if (batch[q]->req.keep_x && X[q] && st >= 0) {
+      batch[q]->x.resize((size_t)batch[q]->req.n * std::max(1, batch[q]->req.nrhs));
+      cudaMemcpyAsync(batch[q]->x.data(), X[q], batch[q]->x.size() * sizeof(double2), cudaMemcpyDeviceToHost, s);
+    }
+  }
+  cudaStreamSynchronize(s);
+  for (size_t q = 0; q < m; ++q) {
+    if (o64[q]) ccg_op_destroy(o64[q]);
+    if (o32[q]) ccg_op_destroy(o32[q]);
+    for (void* p : {(void*)A64[q], (void*)A32[q], (void*)Y[q], (void*)X[q]})
+      if (p) cudaFreeAsync(p, s);
+  }
+  cudaStreamSynchronize(s);
   return st;
 }
 
@@ -347,8 +438,14 @@ void worker(ccg_server* sv, int slot) {
   sv->cv.notify_all();
   std::map<int, DipoleOps> cache;
   uint64_t cached_bytes = 0;   // budget charged for this slot's cached operators
+  // systems one many-system launch of this slot's handle takes
+  const int capacity = h ? std::min(pk_capacity(h, CCG_BICGSTAB, CCG_C64), pk_capacity(h, M_REFRES, CCG_C128)) : 0;
+  auto batchable = [&](const ccg_request& r) {
+    return r.kind == CCG_REQ_DENSE && r.mode == 0 && r.n <= sv->batch_n && std::max(1, r.nrhs) <= capacity;
+  };
   for (;;) {
     std::shared_ptr<Entry> e;
+    std::vector<std::shared_ptr<Entry>> batch;
     uint64_t bytes = 0;
     {
       std::unique_lock<std::mutex> lk(sv->mu);
@@ -366,8 +463,45 @@ void worker(ccg_server* sv, int slot) {
       ++sv->running;
       e->res.t_start = sv->now();
       e->res.slot = slot;
+      if (batchable(e->req)) {
+        // take every other queued small dense request that fits the launch
+        // and the budget, in queue order
+        batch.push_back(e);
+        int systems = std::max(1, e->req.nrhs);
+        const int cap = std::min(capacity, sv->batch_max);
+        for (auto it = sv->queue.begin(); it != sv->queue.end();) {
+          const std::shared_ptr<Entry>& o = sv->entries[*it];
+          const uint64_t ob = estimate_bytes(o->req);
+          const int k = std::max(1, o->req.nrhs);
+          if (batchable(o->req) && systems + k <= cap && sv->used + ob <= sv->budget) {
+            systems += k;
+            sv->used += ob;
+            bytes += ob;
+            o->res.t_start = e->res.t_start;
+            o->res.slot = slot;
+            batch.push_back(o);
+            it = sv->queue.erase(it);
+          } else {
+            ++it;
+          }
+        }
+      }
     }
     sv->cv.notify_all();
+    if (!batch.empty()) {
+      const int st = h ? run_dense_batch(h, s, batch) : CCG_ERR_CUDA;
+      std::lock_guard<std::mutex> lk(sv->mu);
+      const double t = sv->now();
+      for (auto& b : batch) {
+        if (st < 0) b->res.status = st;
+        b->res.t_done = t;
+        b->done = true;
+      }
+      sv->used -= bytes;
+      --sv->running;
+      sv->cv.notify_all();
+      continue;
+    }
     std::vector<double2>* xo = e->req.keep_x ? &e->x : nullptr;
     int st = h ? CCG_OK : CCG_ERR_CUDA;
     bool created = false;
@@ -488,6 +622,17 @@ ccg_status ccg_server_wait(ccg_server* sv, int64_t ticket, ccg_result* res, void
 }
 
 double ccg_server_now(const ccg_server* sv) { return sv ? sv->now() : 0.0; }
+
+ccg_status ccg_server_set_batching(ccg_server* sv, int64_t max_n, int max_systems) {
+  if (!sv || max_n < 0 || max_systems < 1) {
+    set_error("ccg_server_set_batching: need a server, max_n >= 0 and max_systems >= 1");
+    return CCG_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(sv->mu);
+  sv->batch_n = max_n;
+  sv->batch_max = max_systems;
+  return CCG_OK;
+}
 
 ccg_status ccg_server_estimate(const ccg_request* r, uint64_t* bytes) {
   if (!r || !bytes) { set_error("ccg_server_estimate: NULL argument"); return CCG_ERR_INVALID; }

@@ -1,9 +1,10 @@
 // Launch choices measured on the GPU by paper_1208_4869_gb300/autotune.py
-// (rerun it with --write to regenerate this file).  Each entry: for solves
-// of precision `dtype` (CCG_C64 / CCG_C128) by `method` on a dense operator
-// of order n <= nmax (the first matching entry wins), whether the solve runs
-// as one persistent launch (1) or as the kernel-per-step loop (0), and the
-// persistent launch's blocks per SM (0: the occupancy limit).
+// (rerun it with --write to regenerate this file; measured on NVIDIA GB300).
+// Each entry: for solves of precision `dtype` (CCG_C64 / CCG_C128) by
+// `method` on a dense operator of order n <= nmax (the first matching entry
+// wins), whether the solve runs as one persistent launch (1) or as the
+// kernel-per-step loop (0), and the persistent launch's blocks per SM (0:
+// the occupancy limit).
 #pragma once
 
 namespace ccg {
@@ -14,9 +15,33 @@ struct TuneEntry {
   int persistent, pk_blocks;
 };
 
-// (no measurements yet: every solve takes the kernel-per-step loop)
 static const TuneEntry kTune[] = {
-    {-1, -1, 0, 0, 0},
+    {0, 0, 512, 1, 1},   // complex64 bicgstab n <= 512
+    {0, 0, 1024, 1, 2},   // complex64 bicgstab n <= 1024
+    {0, 0, 2048, 1, 0},   // complex64 bicgstab n <= 2048
+    {0, 0, 4611686018427387904, 0, 0},   // complex64 bicgstab n <= any
+    {0, 1, 1024, 1, 1},   // complex64 cgnr n <= 1024
+    {0, 1, 4096, 1, 2},   // complex64 cgnr n <= 4096
+    {0, 1, 4611686018427387904, 0, 0},   // complex64 cgnr n <= any
+    {0, 2, 1024, 1, 1},   // complex64 qmr n <= 1024
+    {0, 2, 2048, 1, 2},   // complex64 qmr n <= 2048
+    {0, 2, 4611686018427387904, 0, 0},   // complex64 qmr n <= any
+    {0, 3, 1024, 1, 1},   // complex64 cocg n <= 1024
+    {0, 3, 2048, 1, 2},   // complex64 cocg n <= 2048
+    {0, 3, 4096, 1, 0},   // complex64 cocg n <= 4096
+    {0, 3, 4611686018427387904, 0, 0},   // complex64 cocg n <= any
+    {1, 0, 512, 1, 1},   // complex128 bicgstab n <= 512
+    {1, 0, 1024, 1, 2},   // complex128 bicgstab n <= 1024
+    {1, 0, 4611686018427387904, 0, 0},   // complex128 bicgstab n <= any
+    {1, 1, 512, 1, 1},   // complex128 cgnr n <= 512
+    {1, 1, 1024, 1, 2},   // complex128 cgnr n <= 1024
+    {1, 1, 4611686018427387904, 0, 0},   // complex128 cgnr n <= any
+    {1, 2, 512, 1, 1},   // complex128 qmr n <= 512
+    {1, 2, 1024, 1, 2},   // complex128 qmr n <= 1024
+    {1, 2, 4611686018427387904, 0, 0},   // complex128 qmr n <= any
+    {1, 3, 512, 1, 1},   // complex128 cocg n <= 512
+    {1, 3, 1024, 1, 2},   // complex128 cocg n <= 1024
+    {1, 3, 4611686018427387904, 0, 0},   // complex128 cocg n <= any
 };
 
 }  // namespace ccg

@@ -57,8 +57,9 @@ def test_persistent_matches_kernel_loop_fp64(ccg, method, sym, n):
     assert s1 == s0 == 0 and i1["iters"] == i0["iters"]
     assert np.array_equal(x1, x0) and np.array_equal(h1, h0)
     assert i1["true_relres"] <= 1e-10
-    # the whole iteration is one launch (plus the true residual's two kernels)
-    assert l1 <= 4 < l0
+    # the whole iteration is one launch (plus the true residual's kernels and,
+    # in complex128, the operator's digit copy on its first product)
+    assert l1 <= 5 < l0
 
 
 @pytest.mark.parametrize("method,sym", METHODS)

@@ -173,3 +173,30 @@ def test_budget_charges_cached_operators(ccg):
     res, _ = sv.wait(sv.submit(**req))
     assert res["status"] == 0 and sv.charged() - charged0 == cached
     sv.close()
+
+
+def test_batching_small_dense_requests(ccg):
+    """Small dense requests waiting together are solved in one many-system
+    launch per step: every result certifies its tolerance, and each request's
+    solution is bitwise the same in a batch as alone (a batch of one)."""
+    reqs = [dict(kind="dense", n=n, nrhs=k, seed=50 + i, tol=tol)
+            for i, (n, k, tol) in enumerate([(512, 3, 1e-10), (1024, 1, 1e-6), (768, 8, 1e-10), (2048, 2, 1e-6),
+                                             (600, 5, 1e-10), (1536, 1, 1e-10)])]
+    alone = []
+    sv = ccg.Server(slots=1)
+    for r in reqs:
+        alone.append(sv.wait(sv.submit(keep_x=True, **r), size_of(r)))
+    sv.close()
+    sv = ccg.Server(slots=1)
+    # hold the slot with a dipole request so that the dense ones queue up together
+    t0 = sv.submit(kind="dipole", L=24, tol=1e-10)
+    tickets = [sv.submit(keep_x=True, **r) for r in reqs]
+    together = [sv.wait(t, size_of(r)) for t, r in zip(tickets, reqs)]
+    sv.wait(t0)
+    sv.close()
+    starts = {res["t_start"] for res, _ in together}
+    assert len(starts) < len(reqs)            # some requests shared a launch
+    for r, (ra, xa), (rb, xb) in zip(reqs, alone, together):
+        assert ra["status"] == 0 and rb["status"] == 0, (r, ra, rb)
+        assert ra["relres"] <= r["tol"] and rb["relres"] <= r["tol"]
+        assert np.array_equal(xa, xb), r
