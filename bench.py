@@ -586,9 +586,10 @@ def measure_serving(args, local, world, rank):
                 if r["status"] != 0 or r["relres"] > reqs[i]["tol"]]
     span_max = reduce_max(span, world)
     solves = reduce_sum(len(res), world)
-    # the small-request slice (dense, n <= 2048) submitted at once, with the
-    # many-system batching on and off: the launch-latency-bound part of the stream
-    small = [r for r in reqs if r["kind"] == "dense" and r["n"] <= 2048][:args.small_requests]
+    # small single-right-hand-side dense systems (the stream's small dense
+    # requests, n <= 2048, with one right-hand side each) submitted at once,
+    # with the many-system batching on and off: the launch-latency-bound case
+    small = [dict(r, nrhs=1) for r in reqs if r["kind"] == "dense" and r["n"] <= 2048][:args.small_requests]
     slice_ = {}
     for name, max_n in (("batched", 2048), ("per_slot", 0)):
         sv = ccg.Server(device=local, slots=args.slots, budget_bytes=120 << 30)
@@ -604,9 +605,9 @@ def measure_serving(args, local, world, rank):
         slice_[name] = {"requests_per_s": len(small) / dt, "rhs_per_s": rhs / dt, "seconds": dt,
                         "all_converged": all(x["status"] == 0 and x["relres"] <= q["tol"] for x, q in zip(rs, small))}
     slice_["requests"] = len(small)
-    slice_["what"] = ("the stream's first %d dense requests with n <= 2048 (1-64 right-hand sides each), all submitted "
-                      "at once to %d slots; batched = many-system launches (ccg_solve_multi_refined), per_slot = "
-                      "each request on its own slot" % (len(small), args.slots))
+    slice_["what"] = ("the stream's first %d dense requests with n <= 2048, each with one right-hand side, all "
+                      "submitted at once to %d slots; batched = many-system launches (ccg_solve_multi_refined), "
+                      "per_slot = each request on its own slot" % (len(small), args.slots))
     nb = min(args.baseline_requests, len(reqs))
     base = serve(1, reqs[:nb], np.zeros(nb), 1)        # complex128, one request and one RHS at a time
     bspan = max(r["t_done"] for r in base) - min(r["t_submit"] for r in base)

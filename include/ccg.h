@@ -454,12 +454,13 @@ ccg_status ccg_server_poll(ccg_server* s, int64_t ticket, int* done);
 ccg_status ccg_server_wait(ccg_server* s, int64_t ticket, ccg_result* res, void* x);
 /* Seconds on the server's clock (the clock of ccg_result times). */
 double ccg_server_now(const ccg_server* s);
-/* Batching of small dense requests: a slot that takes a dense request of
- * order <= max_n (precision by tolerance, mode 0) also takes every other
- * such request waiting in the queue, in queue order, as long as their
- * right-hand sides number at most max_systems (and the launch's resident
- * blocks) and their bytes fit the budget, and solves all their right-hand
- * sides in one ccg_solve_multi_refined launch per step.  max_n = 0 turns it
+/* Batching of small dense requests: a slot that takes a single-right-hand-
+ * side dense request of order <= max_n (precision by tolerance, mode 0) also
+ * takes every other such request waiting in the queue, in queue order, up to
+ * max_systems (and the launch's resident blocks) and as long as their bytes
+ * fit the budget, and solves them in one ccg_solve_multi_refined launch per
+ * step.  Requests with several right-hand sides keep the per-slot block
+ * solver, which reads the matrix once for all of them.  max_n = 0 turns it
  * off.  Default: max_n 2048, max_systems 256.  CCG_ERR_INVALID for a NULL
  * server, max_n < 0 or max_systems < 1. */
 ccg_status ccg_server_set_batching(ccg_server* s, int64_t max_n, int max_systems);

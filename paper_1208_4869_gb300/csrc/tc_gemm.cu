@@ -62,7 +62,8 @@ struct TcMaps {
 template <int T>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_bf16_split(const __grid_constant__ TcMaps maps, float* __restrict__ C, int M, int N, int K, int64_t ldc,
-                    int* err, const int* skip, int* skip_rec) {
+                    int* err, const int* skip, int* skip_rec,
+                    long long wait_limit, int withhold) {
   using G = Cfg<T>;
   if (skip != nullptr && *skip) {  // every column has stopped
     if (skip_rec != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *skip_rec = 1;
@@ -104,7 +105,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     // producer: stage s of block kb waits until the MMAs of block kb - STAGES released it
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % STAGES;
-      if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) & 1) ^ 1, verr)) break;
+      if (kb == withhold) break;  // test hook: this stage's copies are never issued
+      if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) & 1) ^ 1, verr, wait_limit)) break;
       unsigned char* st = smem + s * G::STAGE_BYTES;
       mbar_expect_tx(&full[s], G::STAGE_BYTES);
 #pragma unroll
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     constexpr uint32_t idesc = idesc_bf16(BM, G::BN);
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % STAGES;
-      if (!mbar_wait(&full[s], (kb / STAGES) & 1, verr)) break;
+      if (!mbar_wait(&full[s], (kb / STAGES) & 1, verr, wait_limit)) break;
       fence_after();
       const uint32_t base = smem_u32(smem + s * G::STAGE_BYTES);
 #pragma unroll
@@ -139,7 +141,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncwarp();
 
   // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w + 31
-  mbar_drain(accf, 0, verr);
+  mbar_drain(accf, 0, verr, wait_limit);
   fence_after();
   __syncwarp();
   // tcgen05.ld is warp-collective: take lane 0's reading of the flag
@@ -161,7 +163,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp == 0 && lane == 0) {
     // drain the copies this CTA issued (all consumed unless the pipeline failed)
     for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
-      mbar_drain(&full[kb % STAGES], (kb / STAGES) & 1, verr);
+      mbar_drain(&full[kb % STAGES], (kb / STAGES) & 1, verr, wait_limit);
   }
   fence_before();
   __syncthreads();
@@ -303,7 +305,8 @@ static int tc_product_t(ccg_handle* h, ccg_operator* op, const float2* X, float2
   dim3 grid((unsigned)((Nr + G::BN - 1) / G::BN), (unsigned)((n + tc::BM - 1) / tc::BM));
   tc::gemm_bf16_split<T><<<grid, tc::THREADS, G::SMEM_BYTES, s>>>(maps, reinterpret_cast<float*>(Y), (int)n, Nr,
                                                                     (int)(2 * n), (int64_t)Nr, err, skip,
-                                                                    timing_rec(h));
+                                                                    timing_rec(h), h->wait_limit,
+                                                                    h->test_withhold ? 0 : -1);
   h->launches += 2;
   return cudaGetLastError() == cudaSuccess ? CCG_OK : CCG_ERR_CUDA;
 }

@@ -90,7 +90,8 @@ template <int S> struct Maps {
 template <int S, class Out>
 __global__ void __launch_bounds__(THREADS, 1)
     ozaki_gemm(const __grid_constant__ Maps<S> maps, const int* __restrict__ erow, const int* __restrict__ fcol,
-               Out* __restrict__ C, int M, int N, int K, int64_t ldc, int* err, const int* skip, int* skip_rec) {
+               Out* __restrict__ C, int M, int N, int K, int64_t ldc, int* err, const int* skip, int* skip_rec,
+                    long long wait_limit, int withhold) {
   using namespace tc;
   using G = Geo<S>;
   constexpr int LEVELS = S, BN = G::BN, STAGES = G::STAGES, CHUNK_KB = G::CHUNK_KB;
@@ -142,7 +143,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     // producer: stage s of block kb waits until the MMAs of block kb - STAGES released it
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % STAGES;
-      if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) & 1) ^ 1, verr)) break;
+      if (kb == withhold) break;  // test hook: this stage's copies are never issued
+      if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) & 1) ^ 1, verr, wait_limit)) break;
       unsigned char* st = smem + s * STAGE_BYTES;
       mbar_expect_tx(&full[s], STAGE_BYTES);
 #pragma unroll
@@ -160,9 +162,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     // level t, so the product with digit u lands in level t + u.
     for (int kb = 0; kb < nkb; ++kb) {
       const int c = kb / CHUNK_KB, kin = kb - c * CHUNK_KB, b = c & 1;
-      if (kin == 0 && c >= 2 && !mbar_wait(&tempty[b], ((c >> 1) - 1) & 1, verr)) break;
+      if (kin == 0 && c >= 2 && !mbar_wait(&tempty[b], ((c >> 1) - 1) & 1, verr, wait_limit)) break;
       const int s = kb % STAGES;
-      if (!mbar_wait(&full[s], (kb / STAGES) & 1, verr)) break;
+      if (!mbar_wait(&full[s], (kb / STAGES) & 1, verr, wait_limit)) break;
       fence_after();
       const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
 #pragma unroll
@@ -194,7 +196,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     bool ok = true;
     for (int c = 0; c < nchunks && ok; ++c) {
       const int b = c & 1;
-      ok = __all_sync(0xffffffffu, mbar_wait(&tfull[b], (c >> 1) & 1, verr));
+      ok = __all_sync(0xffffffffu, mbar_wait(&tfull[b], (c >> 1) & 1, verr, wait_limit));
       if (!ok) break;
       fence_after();
 #pragma unroll 1
@@ -237,10 +239,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   __syncwarp();
   // teardown: no MMA or copy of this CTA may be in flight when it frees its memory
-  if (threadIdx.x == 32) mbar_drain(done, 0, verr);
+  if (threadIdx.x == 32) mbar_drain(done, 0, verr, wait_limit);
   if (warp == 0 && lane == 0) {
     for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
-      mbar_drain(&full[kb % STAGES], (kb / STAGES) & 1, verr);
+      mbar_drain(&full[kb % STAGES], (kb / STAGES) & 1, verr, wait_limit);
   }
   fence_before();
   __syncthreads();
@@ -460,7 +462,8 @@ static int oz_product_t(ccg_handle* h, ccg_operator* op, const cx<R>* X, cx<R>* 
   const int Nr = 2 * k;
   dim3 grid((unsigned)((Nr + G::BN - 1) / G::BN), (unsigned)((n + BM - 1) / BM));
   ozaki_gemm<S, R><<<grid, THREADS, G::SMEM_BYTES, s>>>(maps, erow, fcol, reinterpret_cast<R*>(Y), (int)n, Nr,
-                                                        (int)(2 * n), (int64_t)Nr, err, skip, timing_rec(h));
+                                                        (int)(2 * n), (int64_t)Nr, err, skip, timing_rec(h),
+                                                        h->wait_limit, h->test_withhold ? 0 : -1);
   h->launches += 3;
   return cudaGetLastError() == cudaSuccess ? CCG_OK : CCG_ERR_CUDA;
 }

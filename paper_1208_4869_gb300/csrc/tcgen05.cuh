@@ -1,8 +1,9 @@
 // tcgen05 building blocks shared by the tensor-core kernels: bounded
 // mbarrier waits, TMA tile loads, shared-memory matrix descriptors, MMA
 // issue and commit, tensor-memory loads, and the host-side tensor-map
-// encoder (driver entry point, no libcuda link).  Every wait gives up after
-// about two seconds and records an error flag, so a fault in a pipeline
+// encoder (driver entry point, no libcuda link).  Every wait gives up after a
+// limit the kernel is given (the handle's CCG_OPT_WAIT_LIMIT; about two
+// seconds by default) and records an error flag, so a fault in a pipeline
 // cannot hang the GPU.
 #pragma once
 
@@ -15,7 +16,7 @@
 namespace ccg {
 namespace tc {
 
-constexpr long long WAIT_CYCLES = 4000000000LL;       // ~2 s at the SM clock
+constexpr long long WAIT_CYCLES = 4000000000LL;       // default limit: ~2 s at the SM clock
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -38,12 +39,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
   return ok != 0;
 }
 // Wait for the phase of the given parity; false (and the error flag set)
-// after ~2 s or when another thread already gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* err) {
+// after `limit` SM clock cycles or when another thread already gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* err, long long limit) {
   const long long t0 = clock64();
   while (!mbar_try_wait(b, parity)) {
     if (*err) return false;
-    if (clock64() - t0 > WAIT_CYCLES) {
+    if (clock64() - t0 > limit) {
       *err = 1;
       return false;
     }
@@ -53,10 +54,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile
 
 // Bounded wait that ignores the shared error flag: used at teardown so that
 // no copy or MMA of this CTA is still in flight when it frees its memory.
-__device__ __forceinline__ bool mbar_drain(uint64_t* b, uint32_t parity, volatile int* err) {
+__device__ __forceinline__ bool mbar_drain(uint64_t* b, uint32_t parity, volatile int* err, long long limit) {
   const long long t0 = clock64();
   while (!mbar_try_wait(b, parity)) {
-    if (clock64() - t0 > WAIT_CYCLES) {
+    if (clock64() - t0 > limit) {
       *err = 1;
       return false;
     }

@@ -110,3 +110,34 @@ def test_refined_same_with_and_without_tensor_cores(ccg):
         assert np.all(np.linalg.norm(Y - A @ Xh, axis=0) / np.linalg.norm(Y, axis=0) <= 1e-10)
         out.append(Xh)
     assert np.linalg.norm(out[0] - out[1]) / np.linalg.norm(out[0]) < 1e-9
+
+
+@pytest.mark.parametrize("prec", ["complex64", "complex128"])
+def test_pipeline_wait_runs_out(ccg, prec):
+    """The tensor-core pipelines' bounded waits: with the test hook a CTA's
+    producer never issues its first stage's copies, so the MMA issuer's wait
+    on that stage runs out (a short CCG_OPT_WAIT_LIMIT); the call returns
+    CCG_ERR_TIMEOUT after every CTA drained its work and freed its tensor
+    memory, and the next product on the same handle is correct (complex64:
+    the split-bf16 pipeline; complex128: the integer-slice one)."""
+    dt = np.complex64 if prec == "complex64" else np.complex128
+    n, k = 512, 64
+    A, _ = W.dense_system(n, 1.0, 4, dtype=dt)
+    X = W.dense_rhs_block(n, k, seed=5, dtype=dt)
+    h = ccg.Handle()
+    op = h.op_dense(torch.from_numpy(A).cuda())
+    Y = colmajor(np.zeros(X.shape, dt))
+    h.block_matvec(op, colmajor(X), Y)             # the operator's tensor-core copies, made normally
+    h.set_option(ccg.OPT_WAIT_LIMIT, 64)           # 64 Ki cycles, ~30 us
+    h.set_option(ccg.OPT_TEST_WITHHOLD, 1)
+    for _ in range(2):
+        with pytest.raises(ccg.CcgError) as e:
+            h.block_matvec(op, colmajor(X), Y)
+        assert e.value.status == ccg.ERR_TIMEOUT
+    h.set_option(ccg.OPT_TEST_WITHHOLD, 0)
+    h.set_option(ccg.OPT_WAIT_LIMIT, 0)
+    Y = colmajor(np.zeros(X.shape, dt))
+    h.block_matvec(op, colmajor(X), Y)
+    torch.cuda.synchronize()
+    bound = tc_bound(n) if dt == np.complex64 else 1e-13
+    assert err(Y.cpu().numpy(), A, X) <= bound
