@@ -374,6 +374,10 @@ ccg_status ccg_block_matvec(ccg_handle* h, const ccg_operator* op, int64_t nrhs,
  * (times the powers of two above those maxima); 0 on the FP64 pipe (FMA,
  * error ~ n 2^-53 sum_j |a_ij||x_j|).  GB300's FP64 pipe holds that sweep to a
  * third of HBM bandwidth; the integer form runs near it.
+ * CCG_OPT_PDL: 1 (default) launches the kernels of the kernel-per-step loop
+ * with programmatic dependent launch (each starts launching while the one
+ * before finishes and waits for it inside); 0 plain stream order.  Results
+ * are the same either way.
  * CCG_OPT_TEST_WITHHOLD: test hook; 1 makes one block of the next persistent
  * launches leave without arriving at the first barrier, so that the others'
  * waits expire (use with a small CCG_OPT_WAIT_LIMIT); 0 (default) off.
@@ -390,6 +394,7 @@ ccg_status ccg_block_matvec(ccg_handle* h, const ccg_operator* op, int64_t nrhs,
 #define CCG_OPT_WAIT_LIMIT 8
 #define CCG_OPT_TEST_WITHHOLD 9
 #define CCG_OPT_FP64_SWEEP 10
+#define CCG_OPT_PDL 11
 ccg_status ccg_set_option(ccg_handle* h, int option, int value);
 
 /* ---------------------------------------------------------------------------

@@ -34,6 +34,7 @@ OPT_PK_BLOCKS = 7
 OPT_WAIT_LIMIT = 8
 OPT_TEST_WITHHOLD = 9
 OPT_FP64_SWEEP = 10
+OPT_PDL = 11
 
 # ccg_matvec_fn: int (*)(void* ctx, int64_t n, const void* x, void* y, void* stream)
 MATVEC_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,

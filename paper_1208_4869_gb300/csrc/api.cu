@@ -504,6 +504,10 @@ ccg_status ccg_set_option(ccg_handle* h, int option, int value) {
     h->bicgstab_l = value;
     return CCG_OK;
   }
+  if (option == CCG_OPT_PDL && (value == 0 || value == 1)) {
+    h->pdl = value;
+    return CCG_OK;
+  }
   if (option == CCG_OPT_FP64_SWEEP && (value == 0 || value == 1)) {
     h->fx_mode = value;
     return CCG_OK;

@@ -126,6 +126,15 @@ struct SolveState {
   int sweeps;     // persistent solve: operator sweeps it ran
 };
 
+// Programmatic dependent launch (the kernel-per-step loop launches its
+// kernels with it): pdl_wait blocks until the previous kernel in the stream
+// has completed and its memory is visible -- so every kernel calls it before
+// reading anything -- and pdl_launch lets the next kernel of the stream start
+// launching, its blocks then waiting in their own pdl_wait.  Both are no-ops
+// for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // A sweep skips when the solve has stopped, is past a half-step exit, or
 // starts from x0 = 0.  skip_rec (timed sweeps only) is set by the first
 // thread, so that the sweep's duration is left out of the sweep timing.

@@ -54,6 +54,8 @@ template <int THREADS>
 __global__ void __launch_bounds__(THREADS) fx_split_vector(const double2* __restrict__ x, int64_t n,
                                                            int4* __restrict__ xd, int* __restrict__ meta,
                                                            const SolveState* __restrict__ st) {
+  pdl_wait();
+  pdl_launch();
   if (sweep_skipped(st, nullptr)) return;
   __shared__ int wm[THREADS / 32];
   int m = 0;
@@ -210,9 +212,14 @@ __global__ void __launch_bounds__(kBlock) gemv_fx_rows(const double2* __restrict
                                                        const int4* __restrict__ xd, const int* __restrict__ meta,
                                                        double2* __restrict__ y, const SolveState* __restrict__ st,
                                                        int* skip_rec = nullptr) {
-  if (sweep_skipped(st, skip_rec)) return;
+  pdl_wait();
+  if (sweep_skipped(st, skip_rec)) {
+    pdl_launch();
+    return;
+  }
   gemv_fx_rows_body<S, false>(A, lda, C, rowexp, n, x, xd, meta[0], meta[1] != 0 || rowexp[n] != 0, y, blockIdx.x,
                               gridDim.x);
+  pdl_launch();
 }
 
 }  // namespace ccg

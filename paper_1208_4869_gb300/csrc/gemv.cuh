@@ -170,8 +170,13 @@ template <class R, int U, int S = 1>
 __global__ void __launch_bounds__(kBlock) gemv_n_rows(const cx<R>* __restrict__ A, int64_t lda, int64_t n,
                                                       const cx<R>* __restrict__ x, cx<R>* __restrict__ y,
                                                       const SolveState* __restrict__ st, int* skip_rec = nullptr) {
-  if (sweep_skipped(st, skip_rec)) return;
+  pdl_wait();
+  if (sweep_skipped(st, skip_rec)) {
+    pdl_launch();
+    return;
+  }
   gemv_rows_body<R, U, S, false>(A, lda, n, x, y, blockIdx.x, gridDim.x);
+  pdl_launch();
 }
 
 // Column-tiled sweep.  grid = (column chunks, row ranges).  With Y1 it
@@ -351,16 +356,26 @@ __global__ void __launch_bounds__(kBlock) gemv_tile(const cx<R>* __restrict__ A,
                                                     cx<R>* __restrict__ P2, const SolveState* __restrict__ st,
                                                     int* skip_rec = nullptr) {
   static_assert(Y1, "A^H x alone runs in gemv_tile_h");
-  if (sweep_skipped(st, skip_rec)) return;
+  pdl_wait();
+  if (sweep_skipped(st, skip_rec)) {
+    pdl_launch();
+    return;
+  }
   gemv_tile_body<R, U, E, Y1, Y2>(A, lda, n, rows_per_range, x1, x2, P1, P2, blockIdx.x, blockIdx.y);
+  pdl_launch();
 }
 template <class R, int U, int E>
 __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 3 : 1)
     gemv_tile_h(const cx<R>* __restrict__ A, int64_t lda, int64_t n, int64_t rows_per_range,
                 const cx<R>* __restrict__ x2, cx<R>* __restrict__ P2, const SolveState* __restrict__ st,
                 int* skip_rec = nullptr) {
-  if (sweep_skipped(st, skip_rec)) return;
+  pdl_wait();
+  if (sweep_skipped(st, skip_rec)) {
+    pdl_launch();
+    return;
+  }
   gemv_tile_body<R, U, E, false, true>(A, lda, n, rows_per_range, nullptr, x2, nullptr, P2, blockIdx.x, blockIdx.y);
+  pdl_launch();
 }
 
 }  // namespace ccg

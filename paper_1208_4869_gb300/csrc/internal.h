@@ -112,6 +112,7 @@ struct ccg_handle {
   int persistent = 2;   // 0 never, 1 always, 2 as the tuned table says (tune_table.h)
   int pk_blocks = 0;
   int fx_mode = 1;   // complex128 A x: 1 fixed-point digits on the integer pipe, 0 the FP64 pipe
+  int pdl = 1;       // kernel-per-step loop: programmatic dependent launch of its kernels
   long long wait_limit = 4ll << 30;
   int test_withhold = 0;
   // per timed pair: the units (sweeps) and bytes it stands for

@@ -27,6 +27,8 @@ struct PhaseBase {
 // (double, or a float-float pair for complex64 data).
 template <class P, class A>
 __global__ void __launch_bounds__(kBlock) phase_kernel(P p, SolveState* st, Red red) {
+  pdl_wait();
+  pdl_launch();
   if (st->poll.done || p.skip(st)) return;
   p.load(st);
   A acc[P::NQ];
@@ -100,6 +102,8 @@ enum { M_BICGSTAB = CCG_BICGSTAB, M_CGNR = CCG_CGNR, M_QMR = CCG_QMR, M_COCG = C
 // Clears st->skip_mv (set to 1 beforehand) when any entry of x is nonzero.
 template <class R> __global__ void __launch_bounds__(kBlock) x_zero_check(const cx<R>* __restrict__ x, int64_t n,
                                                                          SolveState* st) {
+  pdl_wait();
+  pdl_launch();
   int mine = 0;
   for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock) {
     const cx<R> v = x[i];

@@ -324,10 +324,30 @@ template <class R> struct Runner {
     grid_vec = phase_grid(h, d.n);
   }
 
-  template <class P> void phase(const P& p) {
-    phase_kernel<P, acc_t<R>><<<grid_vec, kBlock, 0, s>>>(p, w.st, red);
+  // A kernel of the loop: with programmatic dependent launch where the handle
+  // allows it, so that it starts launching while the previous one finishes
+  // (each kernel waits for its predecessor inside, pdl_wait).
+  template <class... KArgs, class... Args>
+  void launch(void (*kern)(KArgs...), dim3 grid, dim3 block, Args... args) {
+    if (h->pdl) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = grid;
+      cfg.blockDim = block;
+      cfg.dynamicSmemBytes = 0;
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      cudaLaunchKernelEx(&cfg, kern, args...);
+    } else {
+      kern<<<grid, block, 0, s>>>(args...);
+    }
     ++h->launches;
   }
+
+  template <class P> void phase(const P& p) { launch(phase_kernel<P, acc_t<R>>, dim3(grid_vec), dim3(kBlock), p, w.st, red); }
 
   MvOut<R> plain(const cx<R>* y) const { MvOut<R> m; m.y = y; m.P = nullptr; m.ld = d.n; m.nparts = 1; return m; }
 
@@ -362,26 +382,25 @@ template <class R> struct Runner {
       dipole_apply(op, x, y, false, st, s, rec);
       h->launches += op->dip.kernels;
     } else {
+      const cx<R>* A = d.A;
+      const int64_t lda = d.lda, n = d.n;
+      const SolveState* cst = st;
       if constexpr (sizeof(R) == 4) {
-        if (d.unit == 2)
-          gemv_n_rows<R, 2, kRowSplit><<<d.grid_rows, kBlock, 0, s>>>(d.A, d.lda, d.n, x, y, st, rec);
-        else
-          gemv_n_rows<R, 1, kRowSplit><<<d.grid_rows, kBlock, 0, s>>>(d.A, d.lda, d.n, x, y, st, rec);
+        if (d.unit == 2) launch(gemv_n_rows<R, 2, kRowSplit>, dim3(d.grid_rows), dim3(kBlock), A, lda, n, x, y, cst, rec);
+        else launch(gemv_n_rows<R, 1, kRowSplit>, dim3(d.grid_rows), dim3(kBlock), A, lda, n, x, y, cst, rec);
       } else if (h->fx_mode && w.xfx != nullptr && fx_prepare(h, op)) {
         // the integer-pipe sweep: the vector's digits, then the rows from the
         // operator's digit copy (both launches inside the sweep's timing)
         const char* base = static_cast<const char*>(op->fx_a);
         const int4* C = reinterpret_cast<const int4*>(base);
         const int* rowexp = reinterpret_cast<const int*>(base + (size_t)d.n * d.n * sizeof(int4) + 256);
-        fx_split_vector<1024><<<1, 1024, 0, s>>>(x, d.n, w.xfx, w.xmeta, st);
-        gemv_fx_rows<kRowSplit><<<d.grid_rows, kBlock, 0, s>>>(d.A, d.lda, C, rowexp, d.n, x, w.xfx, w.xmeta, y, st,
-                                                               rec);
-        h->launches += 2;
+        const int4* xd = w.xfx;
+        const int* meta = w.xmeta;
+        launch(fx_split_vector<1024>, dim3(1), dim3(1024), x, n, w.xfx, w.xmeta, cst);
+        launch(gemv_fx_rows<kRowSplit>, dim3(d.grid_rows), dim3(kBlock), A, lda, C, rowexp, n, x, xd, meta, y, cst, rec);
       } else {
-        gemv_n_rows<R, 1, kRowSplit><<<d.grid_rows, kBlock, 0, s>>>(d.A, d.lda, d.n, x, y, st, rec);
-        ++h->launches;
+        launch(gemv_n_rows<R, 1, kRowSplit>, dim3(d.grid_rows), dim3(kBlock), A, lda, n, x, y, cst, rec);
       }
-      if constexpr (sizeof(R) == 4) ++h->launches;
     }
     if (timed) timing_end(h, kDt, CCG_SWEEP_N, d.sweep_bytes());
     return plain(y);
@@ -403,15 +422,16 @@ template <class R> struct Runner {
     }
     dim3 grid(d.ncb, d.tc.nsplit);
     const int64_t rpr = d.tc.rows_per_range;
+    const cx<R>* A = d.A;
+    const int64_t lda = d.lda, n = d.n;
+    const SolveState* cst = st;
+    cx<R>* P2 = w.P2;
     if constexpr (sizeof(R) == 4) {
-      if (d.unit == 2)
-        gemv_tile_h<R, 2, Dense<R>::E><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, rpr, x, w.P2, st, rec);
-      else
-        gemv_tile_h<R, 1, Dense<R>::E><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, rpr, x, w.P2, st, rec);
+      if (d.unit == 2) launch(gemv_tile_h<R, 2, Dense<R>::E>, grid, dim3(kBlock), A, lda, n, rpr, x, P2, cst, rec);
+      else launch(gemv_tile_h<R, 1, Dense<R>::E>, grid, dim3(kBlock), A, lda, n, rpr, x, P2, cst, rec);
     } else {
-      gemv_tile_h<R, 1, Dense<R>::E><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, rpr, x, w.P2, st, rec);
+      launch(gemv_tile_h<R, 1, Dense<R>::E>, grid, dim3(kBlock), A, lda, n, rpr, x, P2, cst, rec);
     }
-    ++h->launches;
     timing_end(h, kDt, CCG_SWEEP_C, d.sweep_bytes());
     MvOut<R> m; m.y = nullptr; m.P = w.P2; m.ld = d.n; m.nparts = d.tc.nsplit;
     return m;
@@ -429,15 +449,19 @@ template <class R> struct Runner {
     const int64_t rpr = d.tb.rows_per_range;
     timing_begin(h);
     int* rec = timing_rec(h);
+    const cx<R>* A = d.A;
+    const int64_t lda = d.lda, n = d.n;
+    const SolveState* cst = st;
+    cx<R>* P1 = w.P1;
+    cx<R>* P2 = w.P2;
     if constexpr (sizeof(R) == 4) {
       if (d.unit == 2)
-        gemv_tile<R, 2, Dense<R>::E, true, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, rpr, x1, x2, w.P1, w.P2, st, rec);
+        launch(gemv_tile<R, 2, Dense<R>::E, true, true>, grid, dim3(kBlock), A, lda, n, rpr, x1, x2, P1, P2, cst, rec);
       else
-        gemv_tile<R, 1, Dense<R>::E, true, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, rpr, x1, x2, w.P1, w.P2, st, rec);
+        launch(gemv_tile<R, 1, Dense<R>::E, true, true>, grid, dim3(kBlock), A, lda, n, rpr, x1, x2, P1, P2, cst, rec);
     } else {
-      gemv_tile<R, 1, Dense<R>::E, true, true><<<grid, kBlock, 0, s>>>(d.A, d.lda, d.n, rpr, x1, x2, w.P1, w.P2, st, rec);
+      launch(gemv_tile<R, 1, Dense<R>::E, true, true>, grid, dim3(kBlock), A, lda, n, rpr, x1, x2, P1, P2, cst, rec);
     }
-    ++h->launches;
     timing_end(h, kDt, CCG_SWEEP_BOTH, d.sweep_bytes());
     o1.y = nullptr; o1.P = w.P1; o1.ld = d.n; o1.nparts = d.ncb;
     o2.y = nullptr; o2.P = w.P2; o2.ld = d.n; o2.nparts = d.tb.nsplit;

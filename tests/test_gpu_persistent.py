@@ -138,3 +138,24 @@ def test_persistent_barrier_wait_runs_out(ccg):
     ref = O.solve(O.DenseOp(A), "bicgstab", y, tol=1e-10, maxit=100)
     assert st == 0 and info["iters"] == ref.iters
     assert np.linalg.norm(xd.cpu().numpy() - ref.x) <= 1e-9 * np.linalg.norm(ref.x)
+
+
+@pytest.mark.parametrize("prec", ["complex128", "complex64"])
+def test_programmatic_dependent_launch_same_results(ccg, prec):
+    """The kernel-per-step loop with and without programmatic dependent
+    launch: the same kernels in the same order, so bitwise the same solves."""
+    dt = np.complex128 if prec == "complex128" else np.complex64
+    A, y = system(1500, 3.0, 13, False, dt)
+    outs = []
+    for pdl in (1, 0):
+        h = ccg.Handle()
+        h.set_option(ccg.OPT_PERSISTENT, 0)
+        h.set_option(ccg.OPT_PDL, pdl)
+        op = h.op_dense(torch.from_numpy(A).cuda())
+        for m in ("bicgstab", "cgnr", "qmr"):
+            xd = torch.zeros(1500, dtype=getattr(torch, prec), device="cuda")
+            st, info, hist = h.solve(m, op, torch.from_numpy(y).cuda(), xd, tol=1e-10 if dt == np.complex128 else 1e-6,
+                                     maxit=300)
+            outs.append((m, pdl, xd.cpu().numpy(), hist))
+    for (m1, _, x1, h1), (m0, _, x0, h0) in zip(outs[:3], outs[3:]):
+        assert m1 == m0 and np.array_equal(x1, x0) and np.array_equal(h1, h0), m1
