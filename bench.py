@@ -40,7 +40,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no FP64 entry in the measured peaks)
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 datasheet FP64 rate, used only when the live measurement fails
 METRIC = "solves/s at rel-res 1e-10, mixed vs FP64 GPU; % HBM roofline; p50/p99 ms"
 
 
@@ -277,6 +277,9 @@ def kernel_sources(tag):
                 (CSRC + "reduce.cuh", None, None), (CSRC + "common.cuh", None, None)]
     elif tag.startswith("dipole"):
         own = [(CSRC + "fft.cuh", None, None), (CSRC + "dipole.cu", None, None)]
+    elif tag.startswith("gemv_fx_rows"):   # the fixed-point sweep (fx.cuh) and the row body it falls back on
+        own = [(CSRC + "fx.cuh", None, None),
+               (CSRC + "gemv.cuh", "// y[i] = (A x)_i with S warps per row", "// Column-tiled sweep.")]
     elif tag.startswith("gemv_n_rows"):
         own = [(CSRC + "gemv.cuh", "// y[i] = (A x)_i with S warps per row", "// Column-tiled sweep.")]
     else:
@@ -284,7 +287,7 @@ def kernel_sources(tag):
     return own + [(CSRC + "common.cuh", None, None)]
 
 
-def roofline(ccg, sweep_stats, n, dipole=False, nrhs=1):
+def roofline(ccg, sweep_stats, n, dipole=False, nrhs=1, rates=None, fx=True):
     """Roofline of the sweep (precision, kind) that took the most device time
     in the timed region: algorithmic flops (8 n^2 per complex product; the
     fused QMR sweep forms two) and bytes (the matrix, read once per sweep)
@@ -294,6 +297,8 @@ def roofline(ccg, sweep_stats, n, dipole=False, nrhs=1):
         if cnt:
             name, products = (DIPOLE_KERNELS if dipole else SWEEP_KERNELS)[kind]
             prec = "c128" if dt == ccg.C128 else "c64"
+            if name == "gemv_n_rows" and prec == "c128" and fx:
+                name = "gemv_fx_rows"   # the fixed-point complex128 row sweep (the default)
             tag = "%s_%s" % (name, prec)
             avg = ms / cnt
             cols = nrhs if kind in (3, 4, 5) else 1
@@ -315,15 +320,20 @@ def roofline(ccg, sweep_stats, n, dipole=False, nrhs=1):
                 "peak_source": "%s bf16 (cuBLAS)" % bf_src,
                 "fp64_equivalent_tflops" if top.endswith("c128") else "c64_equivalent_tflops": k["tflops"],
                 "products_per_term": TC_PRODUCTS[tuple(top.rsplit("_", 1))]}
-    elif top.endswith("c128") and not dipole:   # FP64 FMA pipe bound (4 DFMA per 16-byte element)
-        roof = {"kernel": top, "bound": "alu", "achieved": k["tflops"], "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": k["tflops"] / FP64_PEAK_TFLOPS,
-                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (no measured FP64 peak)"}
+    elif top.endswith("c128") and not dipole and not top.startswith("gemv_fx_rows"):
+        # FP64 FMA pipe bound (4 DFMA per 16-byte element)
+        fp64 = (rates or {}).get("fp64_fma_tflops")
+        peak, src = (fp64, "measured FP64 FMA rate (ccg_pipe_rate)") if fp64 else \
+            (FP64_NOMINAL_TFLOPS, "nominal GB300 FP64 1.25 TFLOP/s (measurement failed)")
+        roof = {"kernel": top, "bound": "alu", "achieved": k["tflops"], "peak": peak,
+                "unit": "TFLOP/s", "frac": k["tflops"] / peak, "peak_source": src}
     elif top.startswith("cgemm_rows"):        # complex64 block product on the FP32 pipe
-        roof = {"kernel": top, "bound": "alu", "achieved": k["tflops"], "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": k["tflops"] / FP32_PEAK_TFLOPS,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
-    else:                      # HBM bound (complex64 sweeps; the FFT operator)
+        fp32 = (rates or {}).get("fp32_fma_tflops")
+        peak, src = (fp32, "measured FP32 FMA rate (ccg_pipe_rate)") if fp32 else \
+            (FP32_PEAK_TFLOPS, "152 SMs x 128 FP32 lanes x 2 x 2070 MHz")
+        roof = {"kernel": top, "bound": "alu", "achieved": k["tflops"], "peak": peak,
+                "unit": "TFLOP/s", "frac": k["tflops"] / peak, "peak_source": src}
+    else:   # HBM bound (complex64 sweeps, the fixed-point complex128 row sweep, the FFT operator)
         roof = {"kernel": top, "bound": "hbm", "achieved": k["gbs"], "peak": hbm,
                 "unit": "GB/s", "frac": k["gbs"] / hbm, "peak_source": "%s copy bandwidth" % hbm_src}
     roof["traffic"] = traffic[0] if traffic else None
@@ -700,6 +710,22 @@ class Ctx:
 
     def __init__(self):
         self.dense = None   # (A, y, op64, op32, tensors)
+        self.rates = None   # measured pipe rates (pipe_rates)
+
+
+def pipe_rates(h, ccg):
+    """Issue rates of the arithmetic pipes, measured on this GPU by the
+    library (ccg_pipe_rate) before any timed region: the denominators of the
+    arithmetic-bound rooflines."""
+    out = {}
+    for key, pipe, flops in (("fp64_fma_tflops", ccg.PIPE_FP64_FMA, 2), ("fp32_fma_tflops", ccg.PIPE_FP32_FMA, 2),
+                             ("imad_wide_tops", ccg.PIPE_IMAD_WIDE, 1)):
+        try:
+            out[key] = flops * h.pipe_rate(pipe) / 1e3
+        except Exception as e:  # reported, and the roofline falls back to the datasheet figure
+            out[key] = None
+            out.setdefault("errors", []).append(str(e)[:200])
+    return out
 
 
 def setup_workload(args, ctx, h, dev, torch, ccg, W):
@@ -818,6 +844,7 @@ def measure_workload(args, ctx, h, stream, world, rank, dev, torch, ccg, W, cloc
         runs[path] = timed_region(h, torch, stream, step, steps, world, clocks) + (steps,)
     # the roofline from a separate pass with per-sweep events
     stats = instrumented_pass(h, ccg, torch, make_step(headline), max(1, min(args.steps, 10 if not batched and not dipole else 1)))
+    other_stats = {p: instrumented_pass(h, ccg, torch, make_step(p), 1) for p in runs if p != headline}
 
     ms, lat, results, launches, clk, steps = runs[headline]
     t_max_ms = reduce_max(ms, world, dev)
@@ -835,6 +862,7 @@ def measure_workload(args, ctx, h, stream, world, rank, dev, torch, ccg, W, cloc
                        "iters": {m: it for m, _, it, _, _, _ in ores[: len(methods)]},
                        "all_converged": all(tol_ok(st, tr) for _, st, _, _, tr, _ in ores),
                        "max_true_relres": max(tr for _, _, _, _, tr, _ in ores)}
+        other[path]["roofline"] = roofline(ccg, other_stats[path], n, dipole, args.nrhs if batched else 1, ctx.rates)
         if batched:
             other[path]["sample"] = "%d of the %d right-hand sides per step, solved one at a time" % (
                 len(ycols), y.shape[1])
@@ -880,7 +908,7 @@ def measure_workload(args, ctx, h, stream, world, rank, dev, torch, ccg, W, cloc
         e2e = {"value": reduce_sum(steps * y.shape[1], world, dev) / dt, "unit": "solves/s",
                "h2d_bytes_per_step": y.nbytes, "d2h_bytes_per_step": y.nbytes}
 
-    roof = roofline(ccg, stats, n, dipole, args.nrhs if batched else 1)
+    roof = roofline(ccg, stats, n, dipole, args.nrhs if batched else 1, ctx.rates)
     if dipole and rank == 0:
         roof["cufft_comparison"] = cufft_dipole_comparison(torch, W, h, op32, args.L, W.DIPOLE_CFG["kd"],
                                                            W.DIPOLE_CFG["m"])
@@ -925,6 +953,7 @@ def run_ours(args):
     h = ccg.Handle(stream)
     h.set_option(ccg.OPT_TC_EXACT, args.tc_exact)
     ctx = Ctx()
+    ctx.rates = pipe_rates(h, ccg)
     r = measure_workload(args, ctx, h, stream, world, rank, dev, torch, ccg, W)
     A, y = r.pop("_A"), r.pop("_y")
     methods = args.methods.split(",")
@@ -970,6 +999,7 @@ def run_ours(args):
             "iters": r["iters"], "all_converged": r["all_converged"], "max_true_relres": r["max_true_relres"],
             "latency_ms": r["latency_ms"], "other_paths": r["other_paths"], "roofline": r["roofline"],
             "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
+            "pipe_rates": ctx.rates,
         }
         if others is not None:
             line["other_workloads"] = others

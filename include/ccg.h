@@ -511,6 +511,18 @@ ccg_status ccg_timing_reset(ccg_handle* h);
 /* Number of kernels this handle has launched since it was created. */
 int64_t ccg_launch_count(const ccg_handle* h);
 
+/* Measured issue rate of one arithmetic pipe on the handle's device, in
+ * giga-operations per second (one fused multiply-add = one operation):
+ * pipe 0 = FP64 fused multiply-add (the pipe of the complex128 sweeps on
+ * FP64), 1 = FP32 fused multiply-add, 2 = 32 x 32 -> 64-bit integer
+ * multiply-add (the pipe of the fixed-point complex128 sweep).  Runs six
+ * launches of about 10 ms on the handle's stream and synchronises it; the
+ * median of five timed launches is returned.  It is the denominator of the
+ * arithmetic-bound rooflines (the paper has no counterpart).  Returns
+ * CCG_ERR_INVALID for a NULL handle or output pointer or a pipe outside
+ * 0..2, CCG_ERR_CUDA when a CUDA call fails. */
+ccg_status ccg_pipe_rate(ccg_handle* h, int pipe, double* gops);
+
 /* Allocation-free y = A^H x for a dense matrix.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
  * device memory -- for instance a host program whose device memory is all

@@ -36,6 +36,10 @@ OPT_TEST_WITHHOLD = 9
 OPT_FP64_SWEEP = 10
 OPT_PDL = 11
 
+PIPE_FP64_FMA = 0
+PIPE_FP32_FMA = 1
+PIPE_IMAD_WIDE = 2
+
 # ccg_matvec_fn: int (*)(void* ctx, int64_t n, const void* x, void* y, void* stream)
 MATVEC_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                              ctypes.c_void_p)
@@ -128,6 +132,8 @@ def lib():
     L.ccg_server_destroy.argtypes = [vp]
     L.ccg_launch_count.restype = i64
     L.ccg_launch_count.argtypes = [vp]
+    L.ccg_pipe_rate.restype = i32
+    L.ccg_pipe_rate.argtypes = [vp, i32, ctypes.POINTER(dbl)]
     for name in ("ccg_create", "ccg_destroy", "ccg_set_stream", "ccg_op_dense", "ccg_op_dipole", "ccg_op_destroy", "ccg_matvec",
                  "ccg_dot", "ccg_solve", "ccg_solve_refined", "ccg_solve_batched", "ccg_solve_batched_refined",
                  "ccg_block_matvec", "ccg_set_option", "ccg_solve_multi", "ccg_solve_multi_refined", "ccg_server_create", "ccg_server_submit", "ccg_server_poll",
@@ -378,6 +384,13 @@ class Handle:
     def launch_count(self):
         """ccg_launch_count: kernels this handle has launched."""
         return int(lib().ccg_launch_count(self.h))
+
+    def pipe_rate(self, pipe):
+        """ccg_pipe_rate: measured Gop/s of an arithmetic pipe (PIPE_FP64_FMA,
+        PIPE_FP32_FMA, PIPE_IMAD_WIDE)."""
+        out = ctypes.c_double()
+        _check(lib().ccg_pipe_rate(self.h, pipe, ctypes.byref(out)))
+        return out.value
 
 
 class Operator:

@@ -205,7 +205,7 @@ template <class R, int U> struct PkCtx {
       }
     }
     if (!group_sync(S.bar, G, limit, fault)) return;
-    gemv_fx_rows_body<kRowSplit, true>(S.A, S.lda, S.fxC, S.fxrow, S.n, x, S.xfx, E, bad, y, lb, G);
+    gemv_fx_rows_body<kFxSplit, true>(S.A, S.lda, S.fxC, S.fxrow, S.n, x, S.xfx, E, bad, y, lb, G);
   }
   // A^H x as ns_c partial vectors in P2
   __device__ MvOut<R> sweep_c(const cx<R>* x) {

@@ -397,7 +397,7 @@ template <class R> struct Runner {
         const int4* xd = w.xfx;
         const int* meta = w.xmeta;
         launch(fx_split_vector<1024>, dim3(1), dim3(1024), x, n, w.xfx, w.xmeta, cst);
-        launch(gemv_fx_rows<kRowSplit>, dim3(d.grid_rows), dim3(kBlock), A, lda, C, rowexp, n, x, xd, meta, y, cst, rec);
+        launch(gemv_fx_rows<kFxSplit>, dim3(d.grid_fx), dim3(kBlock), A, lda, C, rowexp, n, x, xd, meta, y, cst, rec);
       } else {
         launch(gemv_n_rows<R, 1, kRowSplit>, dim3(d.grid_rows), dim3(kBlock), A, lda, n, x, y, cst, rec);
       }

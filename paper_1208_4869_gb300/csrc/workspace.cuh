@@ -29,8 +29,10 @@ struct GmBuf {
 
 static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-// Warps per matrix row in the row sweep (gemv_n_rows).
+// Warps per matrix row in the row sweep (gemv_n_rows), and in the
+// fixed-point complex128 row sweep (gemv_fx_rows).
 constexpr int kRowSplit = 4;
+constexpr int kFxSplit = 2;
 
 // Launch geometry of the dense sweeps for one operator.
 // Resident blocks per SM of the column-tiled sweep (A^H x alone, or A x1 with
@@ -76,6 +78,7 @@ template <class R> struct Dense {
   int64_t lda, n;
   int unit;
   int grid_rows;            // gemv_n_rows blocks
+  int grid_fx;              // gemv_fx_rows blocks
   int ncb;                  // gemv_tile column chunks
   TileSplit tc, tb;         // row ranges for A^H x, and for A x1 with A^H x2
   static constexpr int E = 4;
@@ -89,6 +92,7 @@ template <class R> struct Dense {
     unit = unit_override > 0 ? unit_override : op->unit;
     const int64_t rows_blocks = (n + kWarps - 1) / kWarps;
     grid_rows = (int)std::min<int64_t>((n + kWarps / kRowSplit - 1) / (kWarps / kRowSplit), 1 << 30);
+    grid_fx = (int)std::min<int64_t>((n + kWarps / kFxSplit - 1) / (kWarps / kFxSplit), 1 << 30);
     (void)rows_blocks;
     const int64_t nunits = n / unit;
     ncb = (int)((nunits + 32 * E - 1) / (32 * E));

@@ -4,7 +4,9 @@ report algorithmic bytes over the mean launch time against the copy
 bandwidth; tensor-core block products report the bf16 work they issue
 (3 products per term for the two-term split, 36 and 10 digit pairs for the
 complex128 and complex64 integer-slice products) against the sustained bf16
-peak; complex128 sweeps report FP64 flops against the FP64 rate."""
+peak; complex128 sweeps on the FP64 pipe report FP64 flops against the
+measured FP64 rate, the fixed-point complex128 row sweep bytes against the
+copy bandwidth."""
 import pytest
 
 import bench
@@ -47,12 +49,29 @@ def test_tensor_products_report_issued_bf16_work(kind, prec, name, products):
     assert r["frac"] == pytest.approx(equiv * products / r["peak"])
 
 
-def test_complex128_sweep_is_fp64_bound():
+def test_complex128_fp64_sweeps_use_the_measured_rate():
     n = 8192
-    stats = {(ccg.C128, 0): (10, 4.67, n * n * 16.0)}
-    r = bench.roofline(ccg, stats, n)
-    assert r["bound"] == "alu" and r["peak"] == bench.FP64_PEAK_TFLOPS
+    stats = {(ccg.C128, 1): (10, 4.67, n * n * 16.0)}     # A^H x on the FP64 pipe
+    r = bench.roofline(ccg, stats, n, rates={"fp64_fma_tflops": 1.254})
+    assert r["kernel"] == "gemv_tile_c_c128" and r["bound"] == "alu" and r["peak"] == 1.254
     assert r["achieved"] == pytest.approx(8.0 * n * n / 0.467e-3 / 1e12)
+    assert "measured" in r["peak_source"]
+    # without a measurement: the datasheet rate, said so
+    r = bench.roofline(ccg, stats, n)
+    assert r["peak"] == bench.FP64_NOMINAL_TFLOPS and "nominal" in r["peak_source"]
+    # the FP64-pipe row sweep (fixed-point sweep switched off)
+    r = bench.roofline(ccg, {(ccg.C128, 0): (10, 4.67, n * n * 16.0)}, n, rates={"fp64_fma_tflops": 1.25}, fx=False)
+    assert r["kernel"] == "gemv_n_rows_c128" and r["bound"] == "alu"
+
+
+def test_fixed_point_row_sweep_is_hbm_bound():
+    """The default complex128 row sweep reads 16 bytes of digits per element
+    on the integer pipe: bytes over time against the copy bandwidth."""
+    n = 8192
+    stats = {(ccg.C128, 0): (10, 1.9, n * n * 16.0)}
+    r = bench.roofline(ccg, stats, n, rates={"fp64_fma_tflops": 1.254})
+    assert r["kernel"] == "gemv_fx_rows_c128" and r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["achieved"] == pytest.approx(n * n * 16.0 / 0.19e-3 / 1e9)
 
 
 def test_no_sweeps_gives_none():
