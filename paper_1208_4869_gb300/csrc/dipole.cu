@@ -279,12 +279,32 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 3 : 2) dip_fwd_z_reg(
   }
 }
 
-// K3: x-lines (ky, kz0 .. kz0 + BL - 1) of the three components.  Forward
+// Class-major z order of the fused kernels (described with them below).
+constexpr int kFusedLine = 32;   // z positions per class; lines per block
+
+// z frequency at class-major position pos of a grid of N points per axis
+template <int N> __device__ __forceinline__ int fused_kz(int pos) {
+  return (N / kFusedLine) * (pos % kFusedLine) + pos / kFusedLine;
+}
+// class-major position of z frequency kz
+template <int N> __device__ __forceinline__ int fused_pos(int kz) {
+  return (kz % (N / kFusedLine)) * kFusedLine + kz / (N / kFusedLine);
+}
+// Index along z of frequency kz <= N/2 in the class-major octant: class 0
+// (kz = 0, G, .., N/2: 17 values) first, then classes c = 1 .. G-1 (16 values
+// each, kz = G m + c).
+__host__ __device__ __forceinline__ int fused_octant_z(int kz, int G) {
+  const int c = kz % G, m = kz / G;
+  return (c == 0 ? 0 : 16 * c + 1) + m;
+}
+
+// K3: x-lines (ky, kz0 .. kz0 + BL - 1) of the three components (with PZ,
+// z positions in the fused kernels' class-major order).  Forward
 // step 1 over the input i < nx; then each thread, for its (line, k1), takes
 // forward step 2, the tensor multiply Y_a = sum_b Ghat_ab X_b at the N2
 // frequencies k1 + N1 k2 it holds, and inverse step 1, in place in the
 // exchange buffer; inverse step 2 stores the outputs i < nx.
-template <class R, int N>
+template <class R, int N, bool PZ = false>
 __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 2 : 1) dip_x_mul_reg(cx<R>* __restrict__ grid, const cx<R>* __restrict__ ghat,
                                                         DipGeom g, const cx<R>* __restrict__ W,
                                                         const SolveState* __restrict__ st) {
@@ -334,9 +354,19 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 2 : 1) dip_x_mul_reg(
       dft<N2, -1, R>(X[q]);
     }
     if (b < nb) {
-      const int kz = kz0 + b;
-      const bool fy = ky > g.ny, fz = kz > g.nz;
-      const int64_t hyz = (int64_t)(fy ? g.My - ky : ky) * g.Hz + (fz ? g.Mz - kz : kz);
+      int kz, hz;
+      bool fz;
+      if constexpr (PZ) {  // class-major z positions and octant (the fused kernels' layout)
+        kz = fused_kz<N>(kz0 + b);
+        fz = kz > g.nz;
+        hz = fused_octant_z(fz ? g.Mz - kz : kz, N / kFusedLine);
+      } else {
+        kz = kz0 + b;
+        fz = kz > g.nz;
+        hz = fz ? g.Mz - kz : kz;
+      }
+      const bool fy = ky > g.ny;
+      const int64_t hyz = (int64_t)(fy ? g.My - ky : ky) * g.Hz + hz;
 #pragma unroll
       for (int k2 = 0; k2 < N2; ++k2) {
         const int kx = k1 + N1 * k2;
@@ -436,32 +466,48 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 3 : 2) dip_inv_z_reg(
 
 // ---------------------------------------------------------------------------
 // Fused z-and-y kernels for cubic lattices (nx = ny = nz = N / 2): one block
-// transforms a group of lines of one x-plane in both directions, so the z
-// and y passes of each direction become one kernel (3 kernels per
-// application instead of 5) and the half-transformed plane never leaves
-// shared memory.  Groups of BL lines keep 3 x N/2 x N/BL blocks in flight.
+// transforms one x-plane of one component in a class of 32 lines in both
+// directions, so the z and y passes of each direction become one kernel (3
+// kernels per application instead of 5) and the half-transformed plane never
+// leaves shared memory.
+//
+// The classes come from decimation in frequency, so that no block repeats
+// another's work.  Forward, with G = N / 32: the z frequencies kz = G m + r
+// (m < 32) of class r are a 32-point DFT of the folded line
+//     f_r(z') = sum_{p < G/2} x(z' + 32 p) W_N^(r (z' + 32 p)),   z' < 32
+// (x is zero for z >= N/2), so each block transforms its plane's N/2
+// z-lines at length 32 and then the 32 kz-lines of its class along y.  The
+// grid keeps the z frequencies class-major: position r 32 + m holds
+// kz = G m + r, so every block writes whole 256-byte rows; the x pass and
+// the field-tensor octant follow that order (fused_kz, fused_octant_z).
+// Inverse, with Gy = N / 64: the outputs j = Gy m + g (m < 32) of the
+// inverse y transform are a 64-point inverse DFT (its first 32 outputs) of
+//     h_g(ky') = sum_{p < Gy} X(ky' + 64 p) W_N^(-g (ky' + 64 p)),  ky' < 64,
+// so each block transforms the plane's N kz-lines at length 64, then its 32
+// j-lines along z (reading the class-major positions in frequency order).
 // ---------------------------------------------------------------------------
 template <class R, int N> constexpr size_t fwd_zy_smem() {
-  return ((size_t)(N / 2) * (N / 2 + 1) + (size_t)(N / 2) * (reg_bl<R>() + 1) + (size_t)N * reg_bl<R>()) *
-         sizeof(cx<R>);
+  // P (N/2 x (N/2 + 1)) -- reused as the y transform's exchange buffer
+  // (N x 32) --, T (N/2 x 33), the z transform's exchange buffer (32 x N/2)
+  constexpr size_t NH = N / 2, P = NH * (NH + 1), EY = (size_t)N * kFusedLine;
+  return ((P > EY ? P : EY) + NH * (kFusedLine + 1) + (size_t)kFusedLine * NH) * sizeof(cx<R>);
 }
 template <class R, int N> constexpr size_t inv_yz_smem() {
-  return ((size_t)reg_bl<R>() * (N + 1) + (size_t)N * reg_bl<R>()) * sizeof(cx<R>);
+  // Vb (32 x (N + 1)), then the exchange buffer (N x 32)
+  return ((size_t)kFusedLine * (N + 1) + (size_t)N * kFusedLine) * sizeof(cx<R>);
 }
-// Lengths with the fused kernels: complex64 (each block recomputes its
-// plane's z transform, N / BL times over the plane, and the inverse y
-// transform twice; cheap on the FP32 pipe, but in complex128 the FP64 pipe
-// makes the recomputation cost more than the passes it saves: 1.96 ms per
-// application against 1.09 ms for five passes at L = 64), register-FFT
-// lengths whose half is a multiple of the line group, forward buffers that
-// fit in shared memory.
+// Lengths with the fused kernels: complex64 (complex128 keeps the five
+// passes: its FP64 pipe makes the in-block transforms slower than the
+// passes they save), register-FFT lengths whose half is a multiple of the
+// class size, forward buffers that fit in shared memory.
 template <class R, int N> constexpr bool fused_ok() {
-  return sizeof(R) == 4 && Fac<N>::N1 > 0 && (N / 2) % reg_bl<R>() == 0 && fwd_zy_smem<R, N>() <= 200 * 1024;
+  return sizeof(R) == 4 && reg_bl<R>() == kFusedLine && Fac<N>::N1 > 0 && (N / 2) % kFusedLine == 0 &&
+         fwd_zy_smem<R, N>() <= 200 * 1024;
 }
 
 // Forward: gather the (j, z) plane i of component q from the site vector,
-// z FFT of its N/2 j-lines keeping kz0 .. kz0 + BL - 1, y FFT of those BL
-// kz-lines (input j < N/2), write grid[q][i][ky][kz0 ..].
+// the length-32 z transforms of class r for its N/2 j-lines, then the y FFT
+// of those 32 kz-lines (input j < N/2), written to grid[q][i][ky][r 32 ..].
 template <class R, int N>
 __global__ void __launch_bounds__(kBlock) dip_fwd_zy(const cx<R>* __restrict__ x, cx<R>* __restrict__ grid,
                                                      const int* __restrict__ idx, DipGeom g,
@@ -469,15 +515,16 @@ __global__ void __launch_bounds__(kBlock) dip_fwd_zy(const cx<R>* __restrict__ x
                                                      int conj_in, const SolveState* __restrict__ st,
                                                      int* skip_rec) {
   if (sweep_skipped(st, skip_rec)) return;
-  constexpr int BL = reg_bl<R>(), NH = N / 2, G = N / BL;
+  constexpr int BL = kFusedLine, NH = N / 2, G = N / BL;
   constexpr int PS = NH + 1, TS = BL + 1;  // odd strides: conflict-free transposes
+  constexpr size_t PE = (size_t)NH * PS > (size_t)N * BL ? (size_t)NH * PS : (size_t)N * BL;
   extern __shared__ unsigned char smem_raw[];
-  cx<R>* P = reinterpret_cast<cx<R>*>(smem_raw);  // P[z * PS + j]
-  cx<R>* T = P + NH * PS;                          // T[j * TS + kz - kz0]
-  cx<R>* E = T + NH * TS;
+  cx<R>* P = reinterpret_cast<cx<R>*>(smem_raw);  // P[z * PS + j]; then the y exchange buffer
+  cx<R>* T = P + PE;                               // T[j * TS + m], kz = G m + r
+  cx<R>* EZ = T + NH * TS;                         // z exchange buffer (BL x NH)
   const int q = blockIdx.y;
   const int i = blockIdx.x / G;
-  const int kz0 = (blockIdx.x - i * G) * BL;
+  const int r = blockIdx.x - i * G;
   const cx<R>* xq = x + (int64_t)q * g.N;
 #pragma unroll 4
   for (int t = threadIdx.x; t < NH * NH; t += kBlock) {
@@ -491,24 +538,32 @@ __global__ void __launch_bounds__(kBlock) dip_fwd_zy(const cx<R>* __restrict__ x
     P[z * PS + j] = v;
   }
   __syncthreads();
-  for (int jb = 0; jb < NH; jb += BL) {
-    auto load = [&](int z, int b) { return P[z * PS + jb + b]; };
-    auto store = [&](int kz, int b, cx<R> v) {
-      const int kl = kz - kz0;
-      if (kl >= 0 && kl < BL) T[(jb + b) * TS + kl] = v;
+  {
+    // all N/2 j-lines at once: the fold of class r, then a 32-point DFT
+    auto load = [&](int zp, int b) {
+      cx<R> f = mk<R>(0, 0);
+#pragma unroll
+      for (int p = 0; p < G / 2; ++p) {
+        const int z = zp + BL * p;
+        f = cfma(P[z * PS + b], line_tw<-1, R>(Wz, (r * z) % N), f);
+      }
+      return f;
     };
-    fft2<R, N, BL, -1, NH, N>(load, store, E, Wz);
-    __syncthreads();  // E is reused by the next batch
+    auto store = [&](int m, int b, cx<R> v) { T[b * TS + m] = v; };
+    fft2<R, BL, NH, -1, BL, BL, G>(load, store, EZ, Wz);
   }
-  cx<R>* gq = grid + (int64_t)q * g.G + (int64_t)i * N * N + kz0;
+  __syncthreads();  // T complete; P is free for the y exchange buffer
+  cx<R>* gq = grid + (int64_t)q * g.G + (int64_t)i * N * N + r * BL;
   auto load = [&](int j, int b) { return T[j * TS + b]; };
   auto store = [&](int ky, int b, cx<R> v) { gq[(int64_t)ky * N + b] = v; };
-  fft2<R, N, BL, -1, NH, N>(load, store, E, Wy);
+  fft2<R, N, BL, -1, NH, N>(load, store, P, Wy);
 }
 
-// Inverse: inverse y FFT of the N kz-lines of plane i (in batches of BL)
-// keeping j0 .. j0 + BL - 1, inverse z FFT of those BL j-lines (z < N/2),
-// then y = x / alpha - conv on the occupied sites (conjugated for A^H).
+// Inverse: the length-64 inverse y transforms of class g for the plane's N
+// kz-lines (in batches of 32), keeping the outputs j = Gy m + g (m < 32);
+// the inverse z FFT of those 32 j-lines (input in class-major positions,
+// output z < N/2); then y = x / alpha - conv on the occupied sites
+// (conjugated for A^H).
 template <class R, int N>
 __global__ void __launch_bounds__(kBlock) dip_inv_yz(const cx<R>* __restrict__ x, cx<R>* __restrict__ y,
                                                      const cx<R>* __restrict__ grid, const int* __restrict__ idx,
@@ -516,27 +571,32 @@ __global__ void __launch_bounds__(kBlock) dip_inv_yz(const cx<R>* __restrict__ x
                                                      const cx<R>* __restrict__ Wy, cx<R> alpha_inv, int conj,
                                                      const SolveState* __restrict__ st) {
   if (skip_state(st)) return;
-  constexpr int BL = reg_bl<R>(), NH = N / 2, G = NH / BL;
+  constexpr int BL = kFusedLine, NH = N / 2, GY = NH / BL, LY = N / GY;  // LY = 64
   constexpr int VS = N + 1, OS = BL + 1;
   extern __shared__ unsigned char smem_raw[];
-  cx<R>* Vb = reinterpret_cast<cx<R>*>(smem_raw);  // Vb[jl * VS + kz]
+  cx<R>* Vb = reinterpret_cast<cx<R>*>(smem_raw);  // Vb[m * VS + pos]
   cx<R>* E = Vb + BL * VS;
-  cx<R>* O = Vb;                                     // O[z * OS + jl], written after Vb's last read
+  cx<R>* O = Vb;                                     // O[z * OS + m], written after Vb's last read
   const int q = blockIdx.y;
-  const int i = blockIdx.x / G;
-  const int j0 = (blockIdx.x - i * G) * BL;
+  const int i = blockIdx.x / GY;
+  const int gc = blockIdx.x - i * GY;
   const cx<R>* gq = grid + (int64_t)q * g.G + (int64_t)i * N * N;
   for (int kb = 0; kb < N; kb += BL) {
-    auto load = [&](int ky, int b) { return gq[(int64_t)ky * N + kb + b]; };
-    auto store = [&](int j, int b, cx<R> v) {
-      const int jl = j - j0;
-      if (jl >= 0 && jl < BL) Vb[jl * VS + kb + b] = v;
+    auto load = [&](int kyp, int b) {
+      cx<R> f = mk<R>(0, 0);
+#pragma unroll
+      for (int p = 0; p < GY; ++p) {
+        const int ky = kyp + LY * p;
+        f = cfma(gq[(int64_t)ky * N + kb + b], line_tw<+1, R>(Wy, (gc * ky) % N), f);
+      }
+      return f;
     };
-    fft2<R, N, BL, +1, N, N>(load, store, E, Wy);
+    auto store = [&](int m, int b, cx<R> v) { Vb[m * VS + kb + b] = v; };
+    fft2<R, LY, BL, +1, LY, BL, GY>(load, store, E, Wy);
     __syncthreads();
   }
   {
-    auto load = [&](int kz, int b) { return Vb[b * VS + kz]; };
+    auto load = [&](int kz, int b) { return Vb[b * VS + fused_pos<N>(kz)]; };
     auto store = [&](int z, int b, cx<R> v) { O[z * OS + b] = v; };
     fft2<R, N, BL, +1, N, NH>(load, store, E, Wz);
   }
@@ -545,12 +605,13 @@ __global__ void __launch_bounds__(kBlock) dip_inv_yz(const cx<R>* __restrict__ x
   cx<R>* yq = y + (int64_t)q * g.N;
 #pragma unroll 4
   for (int t = threadIdx.x; t < BL * NH; t += kBlock) {
-    const int z = t % NH, jl = t / NH;
-    const int sidx = __ldg(&idx[((int64_t)i * NH + j0 + jl) * NH + z]);
+    const int z = t % NH, m = t / NH;
+    const int j = GY * m + gc;
+    const int sidx = __ldg(&idx[((int64_t)i * NH + j) * NH + z]);
     if (sidx >= 0) {
       cx<R> xi = xq[sidx];
       if (conj) xi = cconj(xi);
-      cx<R> v = csub(cmul(alpha_inv, xi), O[z * OS + jl]);
+      cx<R> v = csub(cmul(alpha_inv, xi), O[z * OS + m]);
       if (conj) v = cconj(v);
       yq[sidx] = v;
     }
@@ -595,13 +656,18 @@ __global__ void dip_green(double2* __restrict__ g6, DipGeom g, double k) {
 
 // The octant 0 <= k <= M/2 of each transformed component, scaled and
 // rounded to R.
+// With zclass = G > 0 the z index runs over the class-major octant order of
+// the fused kernels (fused_octant_z).
 template <class R>
-__global__ void dip_octant(const double2* __restrict__ src, cx<R>* __restrict__ dst, DipGeom g, double scale) {
+__global__ void dip_octant(const double2* __restrict__ src, cx<R>* __restrict__ dst, DipGeom g, double scale,
+                           int zclass) {
   const int64_t count = 6 * g.H;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < count; p += (int64_t)gridDim.x * blockDim.x) {
     const int64_t q = p / g.H, h = p - q * g.H;
     const int64_t kx = h / ((int64_t)g.Hy * g.Hz), rem = h - kx * g.Hy * g.Hz;
-    const int64_t ky = rem / g.Hz, kz = rem - ky * g.Hz;
+    const int64_t ky = rem / g.Hz, hz = rem - ky * g.Hz;
+    int64_t kz = hz;
+    if (zclass > 0) kz = hz <= 16 ? zclass * hz : zclass * ((hz - 1) % 16) + (hz - 1) / 16;
     const double2 v = src[q * g.G + (kx * g.My + ky) * g.Mz + kz];
     dst[p] = mk<R>((R)(v.x * scale), (R)(v.y * scale));
   }
@@ -712,7 +778,8 @@ template <class R> static int build_ghat(ccg_operator* op, const DipGeom& g, cud
         set_error("ccg_op_dipole: field-tensor allocation failed");
         rc = CCG_ERR_NOMEM;
       } else {
-        dip_octant<R><<<2048, kBlock, 0, s>>>(g6, static_cast<cx<R>*>(op->dip.ghat), g, 1.0 / (double)g.G);
+        const int zclass = dipole_fused<R>(g) ? g.Mz / kFusedLine : 0;
+        dip_octant<R><<<2048, kBlock, 0, s>>>(g6, static_cast<cx<R>*>(op->dip.ghat), g, 1.0 / (double)g.G, zclass);
       }
     }
     if (rc == CCG_OK && cudaStreamSynchronize(s) != cudaSuccess) {
@@ -854,7 +921,7 @@ static void ky(cx<R>* grid, const ccg_operator* op, const DipGeom& g, const cx<R
     fft_strided<R><<<dim3(g.nx * cb, 3), kBlock, sm, s>>>(grid, p, W, sign, st);
   }
 }
-template <class R, int N>
+template <class R, int N, bool PZ = false>
 static void k3(cx<R>* grid, const ccg_operator* op, const DipGeom& g, const cx<R>* W, const SolveState* st,
                cudaStream_t s) {
   static bool opted = false;
@@ -862,8 +929,8 @@ static void k3(cx<R>* grid, const ccg_operator* op, const DipGeom& g, const cx<R
     constexpr int BL = reg_bl<R>();
     const int cb = (g.Mz + BL - 1) / BL;
     constexpr size_t sm = (size_t)3 * N * BL * sizeof(cx<R>);
-    smem_opt_in(dip_x_mul_reg<R, N>, sm, opted);
-    dip_x_mul_reg<R, N><<<g.My * cb, kBlock, sm, s>>>(grid, static_cast<const cx<R>*>(op->dip.ghat), g, W, st);
+    smem_opt_in(dip_x_mul_reg<R, N, PZ>, sm, opted);
+    dip_x_mul_reg<R, N, PZ><<<g.My * cb, kBlock, sm, s>>>(grid, static_cast<const cx<R>*>(op->dip.ghat), g, W, st);
   } else {
     const int bl = op->dip.bl;
     const int cb = (g.Mz + bl - 1) / bl;
@@ -903,7 +970,7 @@ static bool apply_fused_n(const ccg_operator* op, const DipGeom& g, const cx<R>*
                           const SolveState* st, int* rec, cudaStream_t s) {
   if constexpr (fused_ok<R, N>()) {
     fused_fwd<R, N>(x, grid, op, g, Wz, Wy, cj, st, rec, s);
-    k3<R, N>(grid, op, g, Wx, st, s);
+    k3<R, N, true>(grid, op, g, Wx, st, s);
     fused_inv<R, N>(x, y, grid, op, g, Wz, Wy, ainv, cj, st, s);
     return true;
   } else {

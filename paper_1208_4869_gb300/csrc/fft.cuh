@@ -282,8 +282,10 @@ template <int SIGN, class R> __device__ __forceinline__ cx<R> line_tw(const cx<R
 // loaded.  store(k, b, v) receives output k of line b for k < OUT.  E is a
 // shared buffer of N * BL elements.  load may read, and store may write,
 // shared or global memory: every load happens before the block barrier
-// that precedes the first store.
-template <class R, int N, int BL, int SIGN, int IN, int OUT, class Load, class Store>
+// that precedes the first store.  W is the twiddle table of a length
+// TW * N (entry TW t is W_N^t), so a transform of a divisor of the line
+// length can use that line's table.
+template <class R, int N, int BL, int SIGN, int IN, int OUT, int TW = 1, class Load, class Store>
 __device__ __forceinline__ void fft2(const Load& load, const Store& store, cx<R>* E, const cx<R>* __restrict__ W) {
   constexpr int N1 = Fac<N>::N1, N2 = Fac<N>::N2;
   static_assert(N1 * N2 == N, "no register factorisation for this length");
@@ -301,7 +303,7 @@ __device__ __forceinline__ void fft2(const Load& load, const Store& store, cx<R>
     dft<N1, SIGN, R>(u);
     E[j2 * BL + b] = u[0];
 #pragma unroll
-    for (int k1 = 1; k1 < N1; ++k1) E[(k1 * N2 + j2) * BL + b] = cmul(u[k1], line_tw<SIGN, R>(W, j2 * k1));
+    for (int k1 = 1; k1 < N1; ++k1) E[(k1 * N2 + j2) * BL + b] = cmul(u[k1], line_tw<SIGN, R>(W, TW * j2 * k1));
   }
   __syncthreads();
 #pragma unroll 1

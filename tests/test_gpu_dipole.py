@@ -68,13 +68,14 @@ def test_dipole_matvec_matches_direct_sum(h, dtype, kind, L):
         assert np.abs(got - want).max() <= tol * np.abs(want).max(), (kind, L, trans)
 
 
-@pytest.mark.parametrize("L", [24, 32, 48, 64])
+@pytest.mark.parametrize("L", [24, 32, 48, 64, 96, 128])
 def test_dipole_large_sampled_rows(h, L):
     """The sphere lattices of the serving stream and the 64^3 workload (FFT
     grids 48^3 and 96^3 with radix-3 register transforms, 64^3, and 128^3 with
-    137376 dipoles): sampled outputs of A x and A^H x against the oracle's
-    direct sum evaluated at those sites only (A^H x = conj(A conj(x)), A
-    being complex symmetric)."""
+    137376 dipoles), and the larger ones whose complex64 applications also
+    take the fused kernels (grids 192^3 and 256^3): sampled outputs of A x
+    and A^H x against the oracle's direct sum evaluated at those sites only
+    (A^H x = conj(A conj(x)), A being complex symmetric)."""
     occ = W.sphere_occupancy(L)
     ref = O.DipoleOp(occ, KD, M)
     rng = np.random.default_rng(3 + L)
