@@ -80,6 +80,8 @@ __global__ void __launch_bounds__(kBlock) dip_fwd_z(const cx<R>* __restrict__ x,
                                                     const int* __restrict__ idx, DipGeom g, int bl,
                                                     const cx<R>* __restrict__ W, int conj_in,
                                                     const SolveState* __restrict__ st, int* skip_rec) {
+  pdl_wait();
+  pdl_launch();
   if (sweep_skipped(st, skip_rec)) return;
   extern __shared__ unsigned char smem_raw[];
   const int Mz = g.Mz, ls = g.Mz;
@@ -121,6 +123,8 @@ template <class R>
 __global__ void __launch_bounds__(kBlock) dip_x_mul(cx<R>* __restrict__ grid, const cx<R>* __restrict__ ghat,
                                                     DipGeom g, int bl, const cx<R>* __restrict__ W,
                                                     const SolveState* __restrict__ st) {
+  pdl_wait();
+  pdl_launch();
   if (skip_state(st)) return;
   extern __shared__ unsigned char smem_raw[];
   const int Mx = g.Mx, ls = g.Mx;
@@ -179,6 +183,8 @@ __global__ void __launch_bounds__(kBlock) dip_inv_z(const cx<R>* __restrict__ x,
                                                     cx<R>* __restrict__ grid, const int* __restrict__ idx, DipGeom g,
                                                     int bl, const cx<R>* __restrict__ W, cx<R> alpha_inv, int conj,
                                                     const SolveState* __restrict__ st) {
+  pdl_wait();
+  pdl_launch();
   if (skip_state(st)) return;
   extern __shared__ unsigned char smem_raw[];
   const int Mz = g.Mz, ls = g.Mz;
@@ -239,6 +245,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 3 : 2) dip_fwd_z_reg(
                                                         const int* __restrict__ idx, DipGeom g,
                                                         const cx<R>* __restrict__ W, int conj_in,
                                                         const SolveState* __restrict__ st, int* skip_rec) {
+  pdl_wait();
+  pdl_launch();
   if (sweep_skipped(st, skip_rec)) return;
   constexpr int BL = reg_bl<R>(), LS = BL + 1, NZ = N / 2;
   extern __shared__ unsigned char smem_raw[];
@@ -308,6 +316,8 @@ template <class R, int N, bool PZ = false>
 __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 2 : 1) dip_x_mul_reg(cx<R>* __restrict__ grid, const cx<R>* __restrict__ ghat,
                                                         DipGeom g, const cx<R>* __restrict__ W,
                                                         const SolveState* __restrict__ st) {
+  pdl_wait();
+  pdl_launch();
   if (skip_state(st)) return;
   constexpr int BL = reg_bl<R>(), N1 = Fac<N>::N1, N2 = Fac<N>::N2, CS = N * BL;
   static_assert(N1 % 2 == 0, "the input and output halves need an even N1");
@@ -420,6 +430,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 3 : 2) dip_inv_z_reg(
                                                         const cx<R>* __restrict__ grid, const int* __restrict__ idx,
                                                         DipGeom g, const cx<R>* __restrict__ W, cx<R> alpha_inv,
                                                         int conj, const SolveState* __restrict__ st) {
+  pdl_wait();
+  pdl_launch();
   if (skip_state(st)) return;
   constexpr int BL = reg_bl<R>(), LS = BL + 1, NZ = N / 2;
   extern __shared__ unsigned char smem_raw[];
@@ -514,6 +526,8 @@ __global__ void __launch_bounds__(kBlock) dip_fwd_zy(const cx<R>* __restrict__ x
                                                      const cx<R>* __restrict__ Wz, const cx<R>* __restrict__ Wy,
                                                      int conj_in, const SolveState* __restrict__ st,
                                                      int* skip_rec) {
+  pdl_wait();
+  pdl_launch();
   if (sweep_skipped(st, skip_rec)) return;
   constexpr int BL = kFusedLine, NH = N / 2, G = N / BL;
   constexpr int PS = NH + 1, TS = BL + 1;  // odd strides: conflict-free transposes
@@ -570,6 +584,8 @@ __global__ void __launch_bounds__(kBlock) dip_inv_yz(const cx<R>* __restrict__ x
                                                      DipGeom g, const cx<R>* __restrict__ Wz,
                                                      const cx<R>* __restrict__ Wy, cx<R> alpha_inv, int conj,
                                                      const SolveState* __restrict__ st) {
+  pdl_wait();
+  pdl_launch();
   if (skip_state(st)) return;
   constexpr int BL = kFusedLine, NH = N / 2, GY = NH / BL, LY = N / GY;  // LY = 64
   constexpr int VS = N + 1, OS = BL + 1;
@@ -857,47 +873,69 @@ template <class F> static void smem_opt_in(F* fn, size_t bytes, bool& done) {
   done = true;
 }
 
+// A kernel of one application: with programmatic dependent launch when the
+// caller's loop uses it (every application kernel waits for its predecessor
+// first, pdl_wait), else in plain stream order.
+template <class... KArgs, class... Args>
+static void dlaunch(bool pdl, void (*kern)(KArgs...), dim3 grid, size_t smem, cudaStream_t s, Args... args) {
+  if (pdl) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kBlock);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, args...);
+  } else {
+    kern<<<grid, kBlock, smem, s>>>(args...);
+  }
+}
+
 // Launchers: N > 0 selects the register kernels of that length, N == 0 the
 // runtime-length kernels (op->dip.bl lines per block).
 template <class R, int N>
 static void k1(const cx<R>* x, cx<R>* grid, const ccg_operator* op, const DipGeom& g, const cx<R>* W, int conj,
-               const SolveState* st, int* rec, cudaStream_t s) {
+               const SolveState* st, int* rec, cudaStream_t s, bool pdl) {
   const int64_t nlines = (int64_t)g.nx * g.ny;
   static bool opted = false;
   if constexpr (N > 0) {
     constexpr int BL = reg_bl<R>();
     constexpr size_t sm = z_reg_smem<R, N>();
     smem_opt_in(dip_fwd_z_reg<R, N>, sm, opted);
-    dip_fwd_z_reg<R, N><<<dim3((unsigned)((nlines + BL - 1) / BL), 3), kBlock, sm, s>>>(x, grid, op->dip.idx, g, W,
-                                                                                       conj, st, rec);
+    dlaunch(pdl, dip_fwd_z_reg<R, N>, dim3((unsigned)((nlines + BL - 1) / BL), 3), sm, s, x, grid,
+            (const int*)op->dip.idx, g, W, conj, st, rec);
   } else {
     const int bl = op->dip.bl;
     const size_t sm = (size_t)2 * bl * g.Mz * sizeof(cx<R>);
-    dip_fwd_z<R><<<dim3((unsigned)((nlines + bl - 1) / bl), 3), kBlock, sm, s>>>(x, grid, op->dip.idx, g, bl, W,
-                                                                                 conj, st, rec);
+    dlaunch(pdl, dip_fwd_z<R>, dim3((unsigned)((nlines + bl - 1) / bl), 3), sm, s, x, grid, (const int*)op->dip.idx,
+            g, bl, W, conj, st, rec);
   }
 }
 template <class R, int N>
 static void k5(const cx<R>* x, cx<R>* y, cx<R>* grid, const ccg_operator* op, const DipGeom& g, const cx<R>* W,
-               cx<R> ainv, int conj, const SolveState* st, cudaStream_t s) {
+               cx<R> ainv, int conj, const SolveState* st, cudaStream_t s, bool pdl) {
   const int64_t nlines = (int64_t)g.nx * g.ny;
   static bool opted = false;
   if constexpr (N > 0) {
     constexpr int BL = reg_bl<R>();
     constexpr size_t sm = z_reg_smem<R, N>();
     smem_opt_in(dip_inv_z_reg<R, N>, sm, opted);
-    dip_inv_z_reg<R, N><<<dim3((unsigned)((nlines + BL - 1) / BL), 3), kBlock, sm, s>>>(x, y, grid, op->dip.idx, g,
-                                                                                       W, ainv, conj, st);
+    dlaunch(pdl, dip_inv_z_reg<R, N>, dim3((unsigned)((nlines + BL - 1) / BL), 3), sm, s, x, y, (const cx<R>*)grid,
+            (const int*)op->dip.idx, g, W, ainv, conj, st);
   } else {
     const int bl = op->dip.bl;
     const size_t sm = (size_t)2 * bl * g.Mz * sizeof(cx<R>);
-    dip_inv_z<R><<<dim3((unsigned)((nlines + bl - 1) / bl), 3), kBlock, sm, s>>>(x, y, grid, op->dip.idx, g, bl, W,
-                                                                                 ainv, conj, st);
+    dlaunch(pdl, dip_inv_z<R>, dim3((unsigned)((nlines + bl - 1) / bl), 3), sm, s, x, y, grid,
+            (const int*)op->dip.idx, g, bl, W, ainv, conj, st);
   }
 }
 template <class R, int N>
 static void ky(cx<R>* grid, const ccg_operator* op, const DipGeom& g, const cx<R>* W, int sign,
-               const SolveState* st, cudaStream_t s) {
+               const SolveState* st, cudaStream_t s, bool pdl) {
   static bool opted_f = false, opted_i = false;
   if constexpr (N > 0) {
     constexpr int BL = reg_bl<R>();
@@ -907,10 +945,10 @@ static void ky(cx<R>* grid, const ccg_operator* op, const DipGeom& g, const cx<R
     const dim3 grd((unsigned)(g.nx * cb), 3);
     if (sign < 0) {
       smem_opt_in(fft_strided_reg<R, N, BL, -1, N / 2, N>, sm, opted_f);
-      fft_strided_reg<R, N, BL, -1, N / 2, N><<<grd, kBlock, sm, s>>>(grid, p, W, st);
+      dlaunch(pdl, fft_strided_reg<R, N, BL, -1, N / 2, N>, grd, sm, s, grid, p, W, st);
     } else {
       smem_opt_in(fft_strided_reg<R, N, BL, +1, N, N / 2>, sm, opted_i);
-      fft_strided_reg<R, N, BL, +1, N, N / 2><<<grd, kBlock, sm, s>>>(grid, p, W, st);
+      dlaunch(pdl, fft_strided_reg<R, N, BL, +1, N, N / 2>, grd, sm, s, grid, p, W, st);
     }
   } else {
     const int bl = op->dip.bl;
@@ -918,24 +956,25 @@ static void ky(cx<R>* grid, const ccg_operator* op, const DipGeom& g, const cx<R
                      sign < 0 ? g.My : g.ny, bl};
     const int cb = (g.Mz + bl - 1) / bl;
     const size_t sm = (size_t)2 * bl * g.My * sizeof(cx<R>);
-    fft_strided<R><<<dim3(g.nx * cb, 3), kBlock, sm, s>>>(grid, p, W, sign, st);
+    dlaunch(pdl, fft_strided<R>, dim3(g.nx * cb, 3), sm, s, grid, p, W, sign, st);
   }
 }
 template <class R, int N, bool PZ = false>
 static void k3(cx<R>* grid, const ccg_operator* op, const DipGeom& g, const cx<R>* W, const SolveState* st,
-               cudaStream_t s) {
+               cudaStream_t s, bool pdl) {
   static bool opted = false;
   if constexpr (N > 0) {
     constexpr int BL = reg_bl<R>();
     const int cb = (g.Mz + BL - 1) / BL;
     constexpr size_t sm = (size_t)3 * N * BL * sizeof(cx<R>);
     smem_opt_in(dip_x_mul_reg<R, N, PZ>, sm, opted);
-    dip_x_mul_reg<R, N, PZ><<<g.My * cb, kBlock, sm, s>>>(grid, static_cast<const cx<R>*>(op->dip.ghat), g, W, st);
+    dlaunch(pdl, dip_x_mul_reg<R, N, PZ>, dim3(g.My * cb), sm, s, grid, static_cast<const cx<R>*>(op->dip.ghat), g,
+            W, st);
   } else {
     const int bl = op->dip.bl;
     const int cb = (g.Mz + bl - 1) / bl;
     const size_t sm = (size_t)3 * 2 * bl * g.Mx * sizeof(cx<R>);
-    dip_x_mul<R><<<g.My * cb, kBlock, sm, s>>>(grid, static_cast<const cx<R>*>(op->dip.ghat), g, bl, W, st);
+    dlaunch(pdl, dip_x_mul<R>, dim3(g.My * cb), sm, s, grid, static_cast<const cx<R>*>(op->dip.ghat), g, bl, W, st);
   }
 }
 
@@ -946,32 +985,33 @@ static void k3(cx<R>* grid, const ccg_operator* op, const DipGeom& g, const cx<R
 
 template <class R, int N>
 static void fused_fwd(const cx<R>* x, cx<R>* grid, const ccg_operator* op, const DipGeom& g, const cx<R>* Wz,
-                      const cx<R>* Wy, int conj, const SolveState* st, int* rec, cudaStream_t s) {
+                      const cx<R>* Wy, int conj, const SolveState* st, int* rec, cudaStream_t s, bool pdl) {
   static bool opted = false;
   constexpr size_t sm = fwd_zy_smem<R, N>();
   smem_opt_in(dip_fwd_zy<R, N>, sm, opted);
-  dip_fwd_zy<R, N><<<dim3((unsigned)(g.nx * (N / reg_bl<R>())), 3), kBlock, sm, s>>>(x, grid, op->dip.idx, g, Wz, Wy,
-                                                                                    conj, st, rec);
+  dlaunch(pdl, dip_fwd_zy<R, N>, dim3((unsigned)(g.nx * (N / kFusedLine)), 3), sm, s, x, grid,
+          (const int*)op->dip.idx, g, Wz, Wy, conj, st, rec);
 }
 template <class R, int N>
 static void fused_inv(const cx<R>* x, cx<R>* y, const cx<R>* grid, const ccg_operator* op, const DipGeom& g,
-                      const cx<R>* Wz, const cx<R>* Wy, cx<R> ainv, int conj, const SolveState* st, cudaStream_t s) {
+                      const cx<R>* Wz, const cx<R>* Wy, cx<R> ainv, int conj, const SolveState* st, cudaStream_t s,
+                      bool pdl) {
   static bool opted = false;
   constexpr size_t sm = inv_yz_smem<R, N>();
   smem_opt_in(dip_inv_yz<R, N>, sm, opted);
-  dip_inv_yz<R, N><<<dim3((unsigned)(g.nx * (N / 2 / reg_bl<R>())), 3), kBlock, sm, s>>>(x, y, grid, op->dip.idx, g,
-                                                                                        Wz, Wy, ainv, conj, st);
+  dlaunch(pdl, dip_inv_yz<R, N>, dim3((unsigned)(g.nx * (N / 2 / kFusedLine)), 3), sm, s, x, y, grid,
+          (const int*)op->dip.idx, g, Wz, Wy, ainv, conj, st);
 }
 // Three-kernel application for cubic lattices of a fused length; false if
 // the lattice or the length has none.
 template <class R, int N>
 static bool apply_fused_n(const ccg_operator* op, const DipGeom& g, const cx<R>* x, cx<R>* y, cx<R>* grid,
                           const cx<R>* Wx, const cx<R>* Wy, const cx<R>* Wz, cx<R> ainv, int cj,
-                          const SolveState* st, int* rec, cudaStream_t s) {
+                          const SolveState* st, int* rec, cudaStream_t s, bool pdl) {
   if constexpr (fused_ok<R, N>()) {
-    fused_fwd<R, N>(x, grid, op, g, Wz, Wy, cj, st, rec, s);
-    k3<R, N, true>(grid, op, g, Wx, st, s);
-    fused_inv<R, N>(x, y, grid, op, g, Wz, Wy, ainv, cj, st, s);
+    fused_fwd<R, N>(x, grid, op, g, Wz, Wy, cj, st, rec, s, pdl);
+    k3<R, N, true>(grid, op, g, Wx, st, s, pdl);
+    fused_inv<R, N>(x, y, grid, op, g, Wz, Wy, ainv, cj, st, s, pdl);
     return true;
   } else {
     return false;
@@ -988,7 +1028,7 @@ template <class R> static bool dipole_fused(const DipGeom& g) {
 
 template <class R>
 static int apply_t(const ccg_operator* op, const cx<R>* x, cx<R>* y, bool conj, const SolveState* st, int* rec,
-                   cudaStream_t s) {
+                   cudaStream_t s, bool pdl) {
   const DipGeom g = geom(op);
   cx<R>* grid = static_cast<cx<R>*>(op->dip.work);
   const cx<R>* Wx = static_cast<const cx<R>*>(op->dip.tw[0]);
@@ -999,34 +1039,34 @@ static int apply_t(const ccg_operator* op, const cx<R>* x, cx<R>* y, bool conj, 
   if (dipole_fused<R>(g)) {
     bool done = false;
     switch (g.Mx) {
-#define CCG_CASE_FUSED(n) case n: done = apply_fused_n<R, n>(op, g, x, y, grid, Wx, Wy, Wz, ainv, cj, st, rec, s); break;
+#define CCG_CASE_FUSED(n) case n: done = apply_fused_n<R, n>(op, g, x, y, grid, Wx, Wy, Wz, ainv, cj, st, rec, s, pdl); break;
       CCG_FFT_SIZES(CCG_CASE_FUSED)
       default: break;
     }
     if (done) return cudaGetLastError() == cudaSuccess ? CCG_OK : CCG_ERR_CUDA;
   }
-#define CCG_CASE_K1(n) case n: k1<R, n>(x, grid, op, g, Wz, cj, st, rec, s); break;
-  switch (g.Mz) { CCG_FFT_SIZES(CCG_CASE_K1) default: k1<R, 0>(x, grid, op, g, Wz, cj, st, rec, s); }
-#define CCG_CASE_KY(n) case n: ky<R, n>(grid, op, g, Wy, sign, st, s); break;
+#define CCG_CASE_K1(n) case n: k1<R, n>(x, grid, op, g, Wz, cj, st, rec, s, pdl); break;
+  switch (g.Mz) { CCG_FFT_SIZES(CCG_CASE_K1) default: k1<R, 0>(x, grid, op, g, Wz, cj, st, rec, s, pdl); }
+#define CCG_CASE_KY(n) case n: ky<R, n>(grid, op, g, Wy, sign, st, s, pdl); break;
   for (int sign = -1; sign <= 1; sign += 2) {
     if (sign > 0) {
-#define CCG_CASE_K3(n) case n: k3<R, n>(grid, op, g, Wx, st, s); break;
-      switch (g.Mx) { CCG_FFT_SIZES(CCG_CASE_K3) default: k3<R, 0>(grid, op, g, Wx, st, s); }
+#define CCG_CASE_K3(n) case n: k3<R, n>(grid, op, g, Wx, st, s, pdl); break;
+      switch (g.Mx) { CCG_FFT_SIZES(CCG_CASE_K3) default: k3<R, 0>(grid, op, g, Wx, st, s, pdl); }
     }
-    switch (g.My) { CCG_FFT_SIZES(CCG_CASE_KY) default: ky<R, 0>(grid, op, g, Wy, sign, st, s); }
+    switch (g.My) { CCG_FFT_SIZES(CCG_CASE_KY) default: ky<R, 0>(grid, op, g, Wy, sign, st, s, pdl); }
   }
-#define CCG_CASE_K5(n) case n: k5<R, n>(x, y, grid, op, g, Wz, ainv, cj, st, s); break;
-  switch (g.Mz) { CCG_FFT_SIZES(CCG_CASE_K5) default: k5<R, 0>(x, y, grid, op, g, Wz, ainv, cj, st, s); }
+#define CCG_CASE_K5(n) case n: k5<R, n>(x, y, grid, op, g, Wz, ainv, cj, st, s, pdl); break;
+  switch (g.Mz) { CCG_FFT_SIZES(CCG_CASE_K5) default: k5<R, 0>(x, y, grid, op, g, Wz, ainv, cj, st, s, pdl); }
   return cudaGetLastError() == cudaSuccess ? CCG_OK : CCG_ERR_CUDA;
 }
 
 int dipole_apply(const ccg_operator* op, const double2* x, double2* y, bool conj, const SolveState* st,
-                 cudaStream_t s, int* skip_rec) {
-  return apply_t<double>(op, x, y, conj, st, skip_rec, s);
+                 cudaStream_t s, int* skip_rec, bool pdl) {
+  return apply_t<double>(op, x, y, conj, st, skip_rec, s, pdl);
 }
 int dipole_apply(const ccg_operator* op, const float2* x, float2* y, bool conj, const SolveState* st,
-                 cudaStream_t s, int* skip_rec) {
-  return apply_t<float>(op, x, y, conj, st, skip_rec, s);
+                 cudaStream_t s, int* skip_rec, bool pdl) {
+  return apply_t<float>(op, x, y, conj, st, skip_rec, s, pdl);
 }
 
 }  // namespace ccg

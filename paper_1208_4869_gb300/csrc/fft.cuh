@@ -122,6 +122,8 @@ template <class R>
 __global__ void __launch_bounds__(kBlock) fft_strided(cx<R>* __restrict__ data, StridedPass g,
                                                       const cx<R>* __restrict__ W, int sign,
                                                       const SolveState* __restrict__ st) {
+  pdl_wait();
+  pdl_launch();
   if (st != nullptr && (st->poll.done || st->half || st->skip_mv)) return;
   extern __shared__ unsigned char smem_raw[];
   const int n = g.n, ls = g.n, bl = g.bl;
@@ -328,6 +330,8 @@ template <class R, int N, int BL, int SIGN, int IN, int OUT>
 __global__ void __launch_bounds__(kBlock) fft_strided_reg(cx<R>* __restrict__ data, StridedPass g,
                                                           const cx<R>* __restrict__ W,
                                                           const SolveState* __restrict__ st) {
+  pdl_wait();
+  pdl_launch();
   if (st != nullptr && (st->poll.done || st->half || st->skip_mv)) return;
   extern __shared__ unsigned char smem_raw[];
   cx<R>* E = reinterpret_cast<cx<R>*>(smem_raw);

@@ -148,11 +148,12 @@ int dipole_create(ccg_operator* op, const uint8_t* occ, cudaStream_t s);
 void dipole_free(ccg_operator* op);
 // y = A x (conj = false) or A^H x (conj = true), enqueued on s; kernels skip
 // when st says the solve has stopped (st may be null), and then set
-// *skip_rec when it is given (timed sweeps).
+// *skip_rec when it is given (timed sweeps); pdl launches the kernels with
+// programmatic dependent launch.
 int dipole_apply(const ccg_operator* op, const double2* x, double2* y, bool conj, const SolveState* st,
-                 cudaStream_t s, int* skip_rec = nullptr);
+                 cudaStream_t s, int* skip_rec = nullptr, bool pdl = false);
 int dipole_apply(const ccg_operator* op, const float2* x, float2* y, bool conj, const SolveState* st,
-                 cudaStream_t s, int* skip_rec = nullptr);
+                 cudaStream_t s, int* skip_rec = nullptr, bool pdl = false);
 int solve_batched(ccg_handle* h, const ccg_operator* op, int64_t k, const void* Y, int64_t ldy, void* X, int64_t ldx,
                   double tol, int maxit, int32_t* iters, int32_t* status, double* relres);
 int solve_batched_refined(ccg_handle* h, const ccg_operator* op, const ccg_operator* op_in, int64_t k, const void* Y,

@@ -379,7 +379,7 @@ template <class R> struct Runner {
     if (op->kind == CCG_OPK_CALLBACK) {
       callback(false, x, y);
     } else if (op->kind == CCG_OPK_DIPOLE) {
-      dipole_apply(op, x, y, false, st, s, rec);
+      dipole_apply(op, x, y, false, st, s, rec, h->pdl != 0);
       h->launches += op->dip.kernels;
     } else {
       const cx<R>* A = d.A;
@@ -415,7 +415,7 @@ template <class R> struct Runner {
       return plain(y);
     }
     if (op->kind == CCG_OPK_DIPOLE) {
-      dipole_apply(op, x, y, true, st, s, rec);
+      dipole_apply(op, x, y, true, st, s, rec, h->pdl != 0);
       h->launches += op->dip.kernels;
       timing_end(h, kDt, CCG_SWEEP_C, d.sweep_bytes());
       return plain(y);

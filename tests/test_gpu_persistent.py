@@ -159,3 +159,23 @@ def test_programmatic_dependent_launch_same_results(ccg, prec):
             outs.append((m, pdl, xd.cpu().numpy(), hist))
     for (m1, _, x1, h1), (m0, _, x0, h0) in zip(outs[:3], outs[3:]):
         assert m1 == m0 and np.array_equal(x1, x0) and np.array_equal(h1, h0), m1
+
+
+@pytest.mark.parametrize("L,prec", [(32, "complex64"), (12, "complex128"), (64, "complex64")])
+def test_programmatic_dependent_launch_dipole(ccg, L, prec):
+    """Dipole solves (the fused three-kernel application at L = 32 and 64 in
+    complex64, the five-pass one in complex128) with and without
+    programmatic dependent launch: bitwise the same."""
+    occ = W.sphere_occupancy(L)
+    y = W.plane_wave_rhs(occ, W.DIPOLE_CFG["kd"]).astype(np.complex128 if prec == "complex128" else np.complex64)
+    outs = []
+    for pdl in (1, 0):
+        h = ccg.Handle()
+        h.set_option(ccg.OPT_PDL, pdl)
+        op = h.op_dipole(occ, W.DIPOLE_CFG["kd"], W.DIPOLE_CFG["m"], dtype=prec)
+        for m in ("cocg", "bicgstab"):
+            xd = torch.zeros(len(y), dtype=getattr(torch, prec), device="cuda")
+            st, info, hist = h.solve(m, op, torch.from_numpy(y).cuda(), xd, tol=1e-5, maxit=40)
+            outs.append((m, xd.cpu().numpy(), hist))
+    for (m1, x1, h1), (m0, x0, h0) in zip(outs[:2], outs[2:]):
+        assert m1 == m0 and np.array_equal(x1, x0) and np.array_equal(h1, h0), m1
