@@ -12,10 +12,10 @@
 // never wait for one another, so systems of different sizes and iteration
 // counts advance independently inside one launch.
 //
-// Barriers spin on a generation word with a bounded wait: after `limit` SM
-// clock cycles a block gives up, raises the launch's fault flag and leaves,
-// and the host returns CCG_ERR_TIMEOUT.  A test hook withholds one block's
-// arrival to exercise that path (CCG_OPT_TEST_WITHHOLD).
+// Barriers count arrivals on one word per group and spin with a bounded
+// wait: after `limit` SM clock cycles a block gives up, raises the launch's
+// fault flag and leaves, and the host returns CCG_ERR_TIMEOUT.  A test hook
+// withholds one block's arrival to exercise that path (CCG_OPT_TEST_WITHHOLD).
 //
 // Vectors are rewritten between sweeps inside the launch, so sweeps read them
 // with coherent loads (KC = true); the barrier's acquire orders those reads
@@ -47,21 +47,8 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned* p, unsigned v) {
-  unsigned old;
-  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-  return old;
-}
-__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ void st_relaxed_u32(unsigned* p, unsigned v) {
-  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ int ld_relaxed_s32(const int* p) {
   int v;
@@ -69,28 +56,32 @@ __device__ __forceinline__ int ld_relaxed_s32(const int* p) {
   return v;
 }
 
-// All G blocks of a group meet; false if this block gave up after `limit`
-// clock cycles (it then raises *fault) or another block already raised it.
-__device__ __forceinline__ bool group_sync(GroupBar* b, int G, long long limit, int* fault) {
+// All G blocks of a group meet at their epoch-th barrier (epoch counted by
+// each block, the same sequence in every block of the group): a block adds 1
+// to the group's arrival count with release semantics, without waiting for
+// the result, then polls the count with acquire loads until it reaches
+// epoch x G -- one L2 round trip per block instead of an arrival, a last
+// arriver's release and the waiters' observation of it.  The count only
+// grows during a launch (it is zeroed before), and the comparison is
+// modular.  False if this block gave up after `limit` clock cycles (it then
+// raises *fault) or another block already raised it.
+__device__ __forceinline__ bool group_sync(GroupBar* b, int G, unsigned& epoch, long long limit, int* fault) {
   __shared__ int ok;
   __syncthreads();
+  ++epoch;
   if (threadIdx.x == 0) {
     int good = 1;
     if (G > 1) {
-      const unsigned g = ld_relaxed_u32(&b->gen);
-      const unsigned prev = atom_add_acq_rel_u32(&b->count, 1u);
-      if (prev == (unsigned)G - 1u) {
-        st_relaxed_u32(&b->count, 0u);
-        st_release_u32(&b->gen, g + 1u);
-      } else {
+      red_release_add_u32(&b->count, 1u);
+      const unsigned target = epoch * (unsigned)G;
+      if ((int)(ld_acquire_u32(&b->count) - target) < 0) {
         const long long t0 = clock64();
-        while (ld_acquire_u32(&b->gen) == g) {
+        while ((int)(ld_acquire_u32(&b->count) - target) < 0) {
           if (clock64() - t0 > limit) {
             good = 0;
             atomicExch(fault, 1);
             break;
           }
-          __nanosleep(40);
         }
       }
     } else {
@@ -114,6 +105,7 @@ template <class R, int U> struct PkCtx {
   Red red;
   cx<R>* tsm;  // shared memory of the tile sweeps
   int nsw = 0; // sweeps so far (the parity picks the fixed-point sweep's exponent slot)
+  unsigned epoch = 0;  // barriers passed
 
   __device__ PkCtx(const PkSys<R>& s, int lb_, int G_, long long lim, int* f, cx<R>* sm)
       : S(s), lb(lb_), G(G_), limit(lim), fault(f), tsm(sm) {
@@ -122,7 +114,7 @@ template <class R, int U> struct PkCtx {
   }
   // Barrier, then: does the solve go on?
   __device__ __forceinline__ bool sync() {
-    if (!group_sync(S.bar, G, limit, fault)) return false;
+    if (!group_sync(S.bar, G, epoch, limit, fault)) return false;
     return *reinterpret_cast<volatile const int*>(&S.st->poll.done) == 0;
   }
   // A vector phase is cut into the same `nvb` virtual blocks as the phase
@@ -192,7 +184,7 @@ template <class R, int U> struct PkCtx {
       atomicMax(S.fxe + slot, m);
       if (lb == 0) atomicExch(S.fxe + (slot ^ 1), 0);  // the next sweep's slot, last read two barriers ago
     }
-    if (!group_sync(S.bar, G, limit, fault)) return;
+    if (!group_sync(S.bar, G, epoch, limit, fault)) return;
     const int E = *reinterpret_cast<volatile const int*>(S.fxe + slot);
     const bool bad = E == 0x7FF || S.fxrow[S.n] != 0;   // x or A not finite: the FP64 pipe
     if (!bad) {
@@ -204,7 +196,7 @@ template <class R, int U> struct PkCtx {
         S.xfx[i] = q;
       }
     }
-    if (!group_sync(S.bar, G, limit, fault)) return;
+    if (!group_sync(S.bar, G, epoch, limit, fault)) return;
     gemv_fx_rows_body<kFxSplit, true>(S.A, S.lda, S.fxC, S.fxrow, S.n, x, S.xfx, E, bad, y, lb, G);
   }
   // A^H x as ns_c partial vectors in P2
@@ -242,7 +234,7 @@ template <class R, int U, int method> __device__ void pk_run_group(PkCtx<R, U>& 
   if (!S.want_true || ld_relaxed_s32(c.fault)) return;
   // every block of the group left the iteration at the same barrier
   MvOut<R> ax = c.sweep_n(S.x, S.V[11]);
-  if (!group_sync(S.bar, c.G, c.limit, c.fault)) return;
+  if (!group_sync(S.bar, c.G, c.epoch, c.limit, c.fault)) return;
   TrueRes<R> tr;
   tr.n = S.n; tr.y = S.y; tr.out = S.scratch; tr.ax = ax;
   c.phase(tr);
@@ -261,22 +253,22 @@ template <class R, int U, int method> __device__ void pk_run_method(PkCtx<R, U>&
         RefUpdate u;
         u.n = n; u.x = x; u.d32 = S.d32;
         c.phase(u);
-        if (!group_sync(S.bar, c.G, c.limit, c.fault)) return;
+        if (!group_sync(S.bar, c.G, c.epoch, c.limit, c.fault)) return;
       }
       MvOut<R> ax;
       ax.y = nullptr; ax.P = nullptr; ax.ld = n; ax.nparts = 0;
       if (S.outer == 0 && !S.x0_zero) {
         { XNz<R> z; z.n = n; z.x = x; c.phase(z); }
-        if (!group_sync(S.bar, c.G, c.limit, c.fault)) return;
+        if (!group_sync(S.bar, c.G, c.epoch, c.limit, c.fault)) return;
       }
       if (!*reinterpret_cast<volatile const int*>(&st->skip_mv)) {
         ax = c.sweep_n(x, V[0]);
-        if (!group_sync(S.bar, c.G, c.limit, c.fault)) return;
+        if (!group_sync(S.bar, c.G, c.epoch, c.limit, c.fault)) return;
       }
       RefResid rp;
       rp.n = n; rp.y = S.y; rp.r32 = S.r32; rp.d32 = S.d32; rp.outer = S.outer; rp.ax = ax;
       c.phase(rp);
-      group_sync(S.bar, c.G, c.limit, c.fault);
+      group_sync(S.bar, c.G, c.epoch, c.limit, c.fault);
     }
     return;
   }
@@ -285,10 +277,10 @@ template <class R, int U, int method> __device__ void pk_run_method(PkCtx<R, U>&
   ax.y = nullptr; ax.P = nullptr; ax.ld = n; ax.nparts = 0;
   if (!S.x0_zero) {
     { XNz<R> z; z.n = n; z.x = x; c.phase(z); }
-    if (!group_sync(S.bar, c.G, c.limit, c.fault)) return;
+    if (!group_sync(S.bar, c.G, c.epoch, c.limit, c.fault)) return;
     if (!*reinterpret_cast<volatile const int*>(&st->skip_mv)) {
       ax = c.sweep_n(x, V[11]);
-      if (!group_sync(S.bar, c.G, c.limit, c.fault)) return;
+      if (!group_sync(S.bar, c.G, c.epoch, c.limit, c.fault)) return;
     }
   }
   {

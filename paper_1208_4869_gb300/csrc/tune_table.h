@@ -16,31 +16,19 @@ struct TuneEntry {
 };
 
 static const TuneEntry kTune[] = {
-    {0, 0, 512, 1, 1},   // complex64 bicgstab n <= 512
-    {0, 0, 1024, 1, 2},   // complex64 bicgstab n <= 1024
-    {0, 0, 2048, 1, 0},   // complex64 bicgstab n <= 2048
+    {0, 0, 128, 1, 1},   // complex64 bicgstab n <= 128
     {0, 0, 4611686018427387904, 0, 0},   // complex64 bicgstab n <= any
-    {0, 1, 1024, 1, 1},   // complex64 cgnr n <= 1024
-    {0, 1, 4096, 1, 2},   // complex64 cgnr n <= 4096
     {0, 1, 4611686018427387904, 0, 0},   // complex64 cgnr n <= any
-    {0, 2, 1024, 1, 1},   // complex64 qmr n <= 1024
-    {0, 2, 2048, 1, 2},   // complex64 qmr n <= 2048
+    {0, 2, 256, 0, 0},   // complex64 qmr n <= 256
+    {0, 2, 512, 1, 1},   // complex64 qmr n <= 512
     {0, 2, 4611686018427387904, 0, 0},   // complex64 qmr n <= any
-    {0, 3, 1024, 1, 1},   // complex64 cocg n <= 1024
-    {0, 3, 2048, 1, 2},   // complex64 cocg n <= 2048
-    {0, 3, 4096, 1, 0},   // complex64 cocg n <= 4096
+    {0, 3, 128, 1, 1},   // complex64 cocg n <= 128
+    {0, 3, 256, 0, 0},   // complex64 cocg n <= 256
+    {0, 3, 512, 1, 1},   // complex64 cocg n <= 512
     {0, 3, 4611686018427387904, 0, 0},   // complex64 cocg n <= any
-    {1, 0, 512, 1, 1},   // complex128 bicgstab n <= 512
-    {1, 0, 1024, 1, 2},   // complex128 bicgstab n <= 1024
     {1, 0, 4611686018427387904, 0, 0},   // complex128 bicgstab n <= any
-    {1, 1, 512, 1, 1},   // complex128 cgnr n <= 512
-    {1, 1, 1024, 1, 2},   // complex128 cgnr n <= 1024
     {1, 1, 4611686018427387904, 0, 0},   // complex128 cgnr n <= any
-    {1, 2, 512, 1, 1},   // complex128 qmr n <= 512
-    {1, 2, 1024, 1, 2},   // complex128 qmr n <= 1024
     {1, 2, 4611686018427387904, 0, 0},   // complex128 qmr n <= any
-    {1, 3, 512, 1, 1},   // complex128 cocg n <= 512
-    {1, 3, 1024, 1, 2},   // complex128 cocg n <= 1024
     {1, 3, 4611686018427387904, 0, 0},   // complex128 cocg n <= any
 };
 

@@ -218,9 +218,8 @@ template <class R> static Ws<R> ws_carve(char* base, int64_t n, const Dense<R>& 
 // Persistent solves (persist.cu).
 // ---------------------------------------------------------------------------
 struct GroupBar {
-  unsigned count;       // blocks arrived at the current barrier
-  unsigned gen;         // barriers completed
-  unsigned pad[30];     // one 128-byte line per group
+  unsigned count;       // arrivals since the launch began (G per barrier)
+  unsigned pad[31];     // one 128-byte line per group
 };
 
 // One system of a persistent launch: its operator geometry, workspace and
