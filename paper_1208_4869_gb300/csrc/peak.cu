@@ -49,16 +49,25 @@ __global__ void __launch_bounds__(256) rate_ffma(const float* in, float* out, in
   if (s == 12345.0f) out[0] = s;
 }
 
-// c <- (low 32 bits of c) * b + c: a true recurrence through the multiplier,
-// which no closed form replaces.
+// c += (int64) a * b, the accumulation of the fixed-point sweep.  An empty
+// asm statement makes each multiplier opaque to the compiler every
+// iteration (it emits no instruction), so no closed form of the sum can
+// replace the loop.
 __global__ void __launch_bounds__(256) rate_imad_wide(const int* in, long long* out, int iters) {
   const int b = in[threadIdx.x & 31];
+  int a[kChains];
   long long c[kChains];
 #pragma unroll
-  for (int k = 0; k < kChains; ++k) c[k] = in[(threadIdx.x + k) & 31];
+  for (int k = 0; k < kChains; ++k) {
+    a[k] = in[(threadIdx.x + k) & 31];
+    c[k] = in[(threadIdx.x + k + 3) & 31];
+  }
   for (int it = 0; it < iters; ++it) {
 #pragma unroll
-    for (int k = 0; k < kChains; ++k) c[k] = (long long)(int)c[k] * b + c[k];
+    for (int k = 0; k < kChains; ++k) {
+      c[k] += (long long)a[k] * b;
+      asm volatile("" : "+r"(a[k]));
+    }
   }
   long long s = 0;
 #pragma unroll
