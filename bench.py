@@ -280,6 +280,8 @@ def kernel_sources(tag):
     elif tag.startswith("gemv_fx_rows"):   # the fixed-point sweep (fx.cuh) and the row body it falls back on
         own = [(CSRC + "fx.cuh", None, None),
                (CSRC + "gemv.cuh", "// y[i] = (A x)_i with S warps per row", "// Column-tiled sweep.")]
+    elif tag.startswith("gemv_fx_tile"):   # the fixed-point tiles (fx.cuh) and the tile body they fall back on
+        own = [(CSRC + "fx.cuh", None, None), (CSRC + "gemv.cuh", "// Column-tiled sweep.", None)]
     elif tag.startswith("gemv_n_rows"):
         own = [(CSRC + "gemv.cuh", "// y[i] = (A x)_i with S warps per row", "// Column-tiled sweep.")]
     else:
@@ -297,8 +299,10 @@ def roofline(ccg, sweep_stats, n, dipole=False, nrhs=1, rates=None, fx=True):
         if cnt:
             name, products = (DIPOLE_KERNELS if dipole else SWEEP_KERNELS)[kind]
             prec = "c128" if dt == ccg.C128 else "c64"
-            if name == "gemv_n_rows" and prec == "c128" and fx:
-                name = "gemv_fx_rows"   # the fixed-point complex128 row sweep (the default)
+            if prec == "c128" and fx and name in ("gemv_n_rows", "gemv_tile_c", "gemv_tile_both"):
+                # the fixed-point complex128 sweeps on the integer pipe (the default)
+                name = {"gemv_n_rows": "gemv_fx_rows", "gemv_tile_c": "gemv_fx_tile_c",
+                        "gemv_tile_both": "gemv_fx_tile_both"}[name]
             tag = "%s_%s" % (name, prec)
             avg = ms / cnt
             cols = nrhs if kind in (3, 4, 5) else 1
@@ -320,7 +324,7 @@ def roofline(ccg, sweep_stats, n, dipole=False, nrhs=1, rates=None, fx=True):
                 "peak_source": "%s bf16 (cuBLAS)" % bf_src,
                 "fp64_equivalent_tflops" if top.endswith("c128") else "c64_equivalent_tflops": k["tflops"],
                 "products_per_term": TC_PRODUCTS[tuple(top.rsplit("_", 1))]}
-    elif top.endswith("c128") and not dipole and not top.startswith("gemv_fx_rows"):
+    elif top.endswith("c128") and not dipole and not top.startswith("gemv_fx_"):
         # FP64 FMA pipe bound (4 DFMA per 16-byte element)
         fp64 = (rates or {}).get("fp64_fma_tflops")
         peak, src = (fp64, "measured FP64 FMA rate (ccg_pipe_rate)") if fp64 else \
@@ -333,7 +337,7 @@ def roofline(ccg, sweep_stats, n, dipole=False, nrhs=1, rates=None, fx=True):
             (FP32_PEAK_TFLOPS, "152 SMs x 128 FP32 lanes x 2 x 2070 MHz")
         roof = {"kernel": top, "bound": "alu", "achieved": k["tflops"], "peak": peak,
                 "unit": "TFLOP/s", "frac": k["tflops"] / peak, "peak_source": src}
-    else:   # HBM bound (complex64 sweeps, the fixed-point complex128 row sweep, the FFT operator)
+    else:   # HBM bound (complex64 sweeps, the fixed-point complex128 sweeps, the FFT operator)
         roof = {"kernel": top, "bound": "hbm", "achieved": k["gbs"], "peak": hbm,
                 "unit": "GB/s", "frac": k["gbs"] / hbm, "peak_source": "%s copy bandwidth" % hbm_src}
     roof["traffic"] = traffic[0] if traffic else None

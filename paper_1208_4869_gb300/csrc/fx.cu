@@ -1,7 +1,8 @@
 // The fixed-point digit copy of a complex128 dense operator (fx.cuh): made on
 // the first integer-pipe sweep, stream-ordered, freed with the operator.
 // Layout of the allocation: n x n int4 digits, 256 bytes of padding, the n row
-// exponents, then the flag word that marks a non-finite entry.
+// exponents, then the flag word that marks a non-finite entry (rowexp[n]) and
+// the largest row exponent (rowexp[n + 1]).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -14,7 +15,8 @@ namespace ccg {
 
 // Operator digits: one warp per row finds the row's largest exponent, then
 // writes the row's digits (ar1, ar0, ai1, ai0) into C (leading dimension n).
-// *bad is set when A holds an infinity or NaN.
+// *bad is set when A holds an infinity or NaN; bad[1] receives the largest
+// row exponent.
 __global__ void __launch_bounds__(kBlock) fx_split_matrix(const double2* __restrict__ A, int64_t lda, int64_t n,
                                                           int4* __restrict__ C, int* __restrict__ rowexp,
                                                           int* __restrict__ bad) {
@@ -32,6 +34,7 @@ __global__ void __launch_bounds__(kBlock) fx_split_matrix(const double2* __restr
     if (lane == 0) {
       rowexp[row] = m;
       if (m == 0x7FF) atomicExch(bad, 1);
+      atomicMax(bad + 1, m);
     }
     int4* c = C + row * n;
     for (int64_t j = lane; j < n; j += 32) {
@@ -61,7 +64,7 @@ bool fx_prepare(ccg_handle* h, const ccg_operator* op_c) {
   char* base = static_cast<char*>(op->fx_a);
   int* rowexp = reinterpret_cast<int*>(base + cbytes + 256);
   int* bad = reinterpret_cast<int*>(base + cbytes + 256 + (size_t)n * sizeof(int));
-  if (cudaMemsetAsync(bad, 0, sizeof(int), s) != cudaSuccess) { cudaGetLastError(); op->fx_state = -1; return false; }
+  if (cudaMemsetAsync(bad, 0, 2 * sizeof(int), s) != cudaSuccess) { cudaGetLastError(); op->fx_state = -1; return false; }
   const int grid = (int)std::min<int64_t>((n + kWarps - 1) / kWarps, (int64_t)h->num_sms * 8);
   fx_split_matrix<<<grid, kBlock, 0, s>>>(static_cast<const double2*>(op->A), op->lda, n, reinterpret_cast<int4*>(base),
                                           rowexp, bad);

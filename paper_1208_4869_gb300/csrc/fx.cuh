@@ -47,20 +47,28 @@ __device__ __forceinline__ void fx_split(double v, int emax, int& d1, int& d0) {
 
 __device__ __forceinline__ int fx_exp(double v) { return (int)((unsigned long long)__double_as_longlong(v) >> 52) & 0x7FF; }
 
-// Vector digits for one sweep (one block): the largest exponent of x, then
-// the digits (xr1, xr0, xi1, xi0).  meta[0] = the exponent, meta[1] = 1 when
-// x holds an infinity or NaN.
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS) fx_split_vector(const double2* __restrict__ x, int64_t n,
-                                                           int4* __restrict__ xd, int* __restrict__ meta,
-                                                           const SolveState* __restrict__ st) {
-  pdl_wait();
-  pdl_launch();
-  if (sweep_skipped(st, nullptr)) return;
+// A^H x sums down the columns of A, whose rows have different scales, so the
+// vector of that sweep is first scaled row by row: x'_r = x_r 2^(F_r - Fm),
+// Fm the largest row scale (exact but for subnormal results), and every
+// product conj(a_rc) x_r then has the one scale 2^(Fm + Fx' - 104).
+__device__ __forceinline__ double2 fx_row_scaled(double2 v, int er, int fm) {
+  const int sh = max(er, 1) - fm;  // <= 0
+  return make_double2(ldexp(v.x, sh), ldexp(v.y, sh));
+}
+
+// Vector digits for one sweep (one block): the largest exponent of x (of x'
+// with ROWS: rowexp as the operator's, rowexp[n + 1] its largest row
+// exponent), then the digits (xr1, xr0, xi1, xi0).  meta[0] = the exponent,
+// meta[1] = 1 when x holds an infinity or NaN.
+template <int THREADS, bool ROWS>
+__device__ __forceinline__ void fx_split_block(const double2* __restrict__ x, int64_t n, int4* __restrict__ xd,
+                                               int* __restrict__ meta, const int* __restrict__ rowexp) {
   __shared__ int wm[THREADS / 32];
+  const int fm = ROWS ? max(rowexp[n + 1], 1) : 0;
   int m = 0;
   for (int64_t j = threadIdx.x; j < n; j += THREADS) {
-    const double2 v = x[j];
+    double2 v = x[j];
+    if (ROWS) v = fx_row_scaled(v, rowexp[j], fm);
     m = max(m, max(fx_exp(v.x), fx_exp(v.y)));
   }
 #pragma unroll
@@ -75,12 +83,39 @@ __global__ void __launch_bounds__(THREADS) fx_split_vector(const double2* __rest
     meta[1] = m == 0x7FF ? 1 : 0;
   }
   for (int64_t j = threadIdx.x; j < n; j += THREADS) {
-    const double2 v = x[j];
+    double2 v = x[j];
+    if (ROWS) v = fx_row_scaled(v, rowexp[j], fm);
     int4 q;
     fx_split(v.x, m, q.x, q.y);
     fx_split(v.y, m, q.z, q.w);
     xd[j] = q;
   }
+}
+
+template <int THREADS, bool ROWS>
+__global__ void __launch_bounds__(THREADS) fx_split_vector(const double2* __restrict__ x, int64_t n,
+                                                           int4* __restrict__ xd, int* __restrict__ meta,
+                                                           const SolveState* __restrict__ st,
+                                                           const int* __restrict__ rowexp) {
+  pdl_wait();
+  pdl_launch();
+  if (sweep_skipped(st, nullptr)) return;
+  fx_split_block<THREADS, ROWS>(x, n, xd, meta, rowexp);
+}
+
+// Both vectors of the fused sweep in one launch of two blocks: x1 plain
+// (block 0), x2 row-scaled (block 1).
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) fx_split_pair(const double2* __restrict__ x1, int4* __restrict__ xd1,
+                                                         int* __restrict__ meta1, const double2* __restrict__ x2,
+                                                         int4* __restrict__ xd2, int* __restrict__ meta2, int64_t n,
+                                                         const int* __restrict__ rowexp,
+                                                         const SolveState* __restrict__ st) {
+  pdl_wait();
+  pdl_launch();
+  if (sweep_skipped(st, nullptr)) return;
+  if (blockIdx.x == 0) fx_split_block<THREADS, false>(x1, n, xd1, meta1, rowexp);
+  else fx_split_block<THREADS, true>(x2, n, xd2, meta2, rowexp);
 }
 
 // Exact complex digit products into int64: re += ar xr - ai xi,
@@ -106,6 +141,32 @@ struct FxAcc {
   }
   // the sums so far in units of 2^(Fa + Fx - 78), exactly up to the rounding
   // of the int64 -> double conversions
+  __device__ __forceinline__ void flush(double& re, double& im) {
+    re += (double)hre * 67108864.0 + (double)mre;
+    im += (double)him * 67108864.0 + (double)mim;
+    zero();
+  }
+};
+
+// The same for conj(a) x: re += ar xr + ai xi, im += ar xi - ai xr.
+struct FxAccH {
+  long long hre, mre, him, mim;
+  __device__ __forceinline__ void zero() { hre = mre = him = mim = 0; }
+  __device__ __forceinline__ void mac(const int4 a, const int4 x) {
+    const int nai1 = -a.z, nai0 = -a.w;
+    hre += (long long)a.x * x.x;
+    hre += (long long)a.z * x.z;
+    mre += (long long)a.x * x.y;
+    mre += (long long)a.y * x.x;
+    mre += (long long)a.z * x.w;
+    mre += (long long)a.w * x.z;
+    him += (long long)a.x * x.z;
+    him += (long long)nai1 * x.x;
+    mim += (long long)a.x * x.w;
+    mim += (long long)a.y * x.z;
+    mim += (long long)nai1 * x.y;
+    mim += (long long)nai0 * x.x;
+  }
   __device__ __forceinline__ void flush(double& re, double& im) {
     re += (double)hre * 67108864.0 + (double)mre;
     im += (double)him * 67108864.0 + (double)mim;
@@ -217,6 +278,125 @@ __global__ void __launch_bounds__(kBlock) gemv_fx_rows(const double2* __restrict
   }
   gemv_fx_rows_body<S, false>(A, lda, C, rowexp, n, x, xd, meta[0], meta[1] != 0 || rowexp[n] != 0, y, blockIdx.x,
                               gridDim.x);
+  pdl_launch();
+}
+
+// The column-tiled complex128 sweeps on the integer pipe: A^H x2 alone
+// (Y1 = false) or with A x1 (Y1 = true) from one read of the digits, over the
+// tiles of gemv_tile_body (column chunk of 128 columns, a lane per 4 columns,
+// row range `range` of rows_per_range rows; the same partial-sum outputs).
+// xd1 holds the digits of x1 (exponent xexp1), xd2 those of the row-scaled
+// x2' (exponent xexp2, fm the operator's largest row exponent).  A^H x2
+// accumulates each column exactly in int64 per warp, converted to double
+// every 256 rows; A x1 forms each row's chunk sum exactly and converts it
+// once.  KC as in gemv_rows_body; smem_ext as in gemv_tile_body.
+template <bool Y1, bool KC>
+__device__ __forceinline__ void gemv_fx_tile_body(const int4* __restrict__ C, const int* __restrict__ rowexp,
+                                                  int64_t n, int64_t rows_per_range, const int4* xd1, int xexp1,
+                                                  const int4* xd2, int xexp2, double2* P1, double2* P2,
+                                                  int64_t chunk, int64_t range, double2* smem_ext = nullptr) {
+  constexpr int E = 4, CBU = 32 * E;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t col0 = chunk * CBU;
+  const int64_t r0 = range * rows_per_range;
+  const int64_t r1 = r0 + rows_per_range < n ? r0 + rows_per_range : n;
+  const int fm = max(rowexp[n + 1], 1);
+  int4 xl[E];
+  if constexpr (Y1) {
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const int64_t u = col0 + lane + 32 * j;
+      xl[j] = u < n ? (KC ? ldc_i4(xd1 + u) : __ldg(xd1 + u)) : make_int4(0, 0, 0, 0);
+    }
+  }
+  FxAccH acc[E];
+  double dre[E], dim[E];
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    acc[j].zero();
+    dre[j] = 0.0;
+    dim[j] = 0.0;
+  }
+  int cnt = 0;
+  for (int64_t r = r0 + warp; r < r1; r += kWarps) {
+    const int4* c = C + r * n;
+    int4 av[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const int64_t u = col0 + lane + 32 * j;
+      av[j] = u < n ? ld_stream_i4(c + u) : make_int4(0, 0, 0, 0);
+    }
+    const int4 xr = KC ? ldc_i4(xd2 + r) : __ldg(xd2 + r);
+#pragma unroll
+    for (int j = 0; j < E; ++j) acc[j].mac(av[j], xr);
+    if (++cnt == 256) {
+#pragma unroll
+      for (int j = 0; j < E; ++j) acc[j].flush(dre[j], dim[j]);
+      cnt = 0;
+    }
+    if constexpr (Y1) {
+      FxAcc s;
+      s.zero();
+#pragma unroll
+      for (int j = 0; j < E; ++j) s.mac(av[j], xl[j]);
+      double sre = 0.0, sim = 0.0;
+      s.flush(sre, sim);
+      double2 t = warp_csum(make_double2(sre, sim));
+      if (lane == 0) {
+        const int e = max(rowexp[r], 1) + max(xexp1, 1) - 2122;
+        P1[chunk * n + r] = make_double2(ldexp(t.x, e), ldexp(t.y, e));
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < E; ++j) acc[j].flush(dre[j], dim[j]);
+  double2* sm;
+  if constexpr (KC) {
+    sm = smem_ext;
+  } else {
+    __shared__ double2 sm_own[kWarps * CBU];
+    sm = sm_own;
+  }
+#pragma unroll
+  for (int j = 0; j < E; ++j) sm[warp * CBU + lane + 32 * j] = make_double2(dre[j], dim[j]);
+  __syncthreads();
+  const int e2 = fm + max(xexp2, 1) - 2122;  // units 2^(Fm + Fx' - 78)
+  for (int t = threadIdx.x; t < CBU; t += kBlock) {
+    const int64_t col = col0 + t;
+    if (col < n) {
+      double2 v = sm[t];
+#pragma unroll
+      for (int w = 1; w < kWarps; ++w) v = cadd(v, sm[w * CBU + t]);
+      P2[range * n + col] = make_double2(ldexp(v.x, e2), ldexp(v.y, e2));
+    }
+  }
+  if (KC) __syncthreads();  // a persistent block's next tile reuses sm
+}
+
+// Entry point of the column-tiled integer sweeps.  With a non-finite entry in
+// A (rowexp[n]) or in a vector (meta[1]) the tile is summed from A on the
+// FP64 pipe instead.
+template <bool Y1>
+__global__ void __launch_bounds__(kBlock, 2) gemv_fx_tile(const double2* __restrict__ A, int64_t lda,
+                                                       const int4* __restrict__ C, const int* __restrict__ rowexp,
+                                                       int64_t n, int64_t rows_per_range,
+                                                       const double2* __restrict__ x1, const double2* __restrict__ x2,
+                                                       const int4* __restrict__ xd1, const int* __restrict__ meta1,
+                                                       const int4* __restrict__ xd2, const int* __restrict__ meta2,
+                                                       double2* __restrict__ P1, double2* __restrict__ P2,
+                                                       const SolveState* __restrict__ st, int* skip_rec = nullptr) {
+  pdl_wait();
+  if (sweep_skipped(st, skip_rec)) {
+    pdl_launch();
+    return;
+  }
+  const bool bad = rowexp[n] != 0 || meta2[1] != 0 || (Y1 && meta1[1] != 0);
+  if (bad) {
+    gemv_tile_body<double, 1, 4, Y1, true>(A, lda, n, rows_per_range, x1, x2, P1, P2, blockIdx.x, blockIdx.y);
+  } else {
+    gemv_fx_tile_body<Y1, false>(C, rowexp, n, rows_per_range, xd1, Y1 ? meta1[0] : 0, xd2, meta2[0], P1, P2,
+                                 blockIdx.x, blockIdx.y);
+  }
   pdl_launch();
 }
 

@@ -162,49 +162,109 @@ template <class R, int U> struct PkCtx {
     count_sweep();
     return plain(y);
   }
-  // complex128 y = A x in fixed point: the group's largest exponent of x,
-  // its digits, then the rows from the operator's digits
-  __device__ void fx_sweep(const double2* x, double2* y) {
-    __shared__ int wm[kWarps];
-    const int slot = nsw & 1;
+  // The group's fixed-point digits of x1 into xd1 and of the row-scaled x2
+  // into xd2 (either may be null), with their exponents -- the loop's
+  // fx_split_vector across the group's blocks: the largest exponents meet in
+  // the sweep's pair of exponent words (two pairs alternate between sweeps;
+  // block 0 clears the other pair, last read two barriers ago), then each
+  // block writes its share of the digits.  bad: an operand is not finite (the
+  // sweep then takes the FP64 pipe).  False if a barrier gave up.
+  __device__ bool fx_split_group(const double2* x1, int4* xd1, const double2* x2, int4* xd2, int& e1, int& e2,
+                                 bool& bad) {
+    __shared__ int wm[2][kWarps];
+    int* pair = S.fxe + 2 * (nsw & 1);
+    int* other = S.fxe + 2 * ((nsw & 1) ^ 1);
     ++nsw;
-    int m = 0;
+    const int fm = max(S.fxrow[S.n + 1], 1);
+    int m1 = 0, m2 = 0;
     const int64_t stride = (int64_t)G * kBlock;
     for (int64_t i = (int64_t)lb * kBlock + threadIdx.x; i < S.n; i += stride) {
-      const double2 v = ldc_unit(x + i);
-      m = max(m, max(fx_exp(v.x), fx_exp(v.y)));
+      if (x1) {
+        const double2 v = ldc_unit(x1 + i);
+        m1 = max(m1, max(fx_exp(v.x), fx_exp(v.y)));
+      }
+      if (x2) {
+        const double2 v = fx_row_scaled(ldc_unit(x2 + i), S.fxrow[i], fm);
+        m2 = max(m2, max(fx_exp(v.x), fx_exp(v.y)));
+      }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    for (int o = 16; o > 0; o >>= 1) {
+      m1 = max(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+      m2 = max(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      wm[0][threadIdx.x >> 5] = m1;
+      wm[1][threadIdx.x >> 5] = m2;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
 #pragma unroll
-      for (int w = 1; w < kWarps; ++w) m = max(m, wm[w]);
-      atomicMax(S.fxe + slot, m);
-      if (lb == 0) atomicExch(S.fxe + (slot ^ 1), 0);  // the next sweep's slot, last read two barriers ago
-    }
-    if (!group_sync(S.bar, G, epoch, limit, fault)) return;
-    const int E = *reinterpret_cast<volatile const int*>(S.fxe + slot);
-    const bool bad = E == 0x7FF || S.fxrow[S.n] != 0;   // x or A not finite: the FP64 pipe
-    if (!bad) {
-      for (int64_t i = (int64_t)lb * kBlock + threadIdx.x; i < S.n; i += stride) {
-        const double2 v = ldc_unit(x + i);
-        int4 q;
-        fx_split(v.x, E, q.x, q.y);
-        fx_split(v.y, E, q.z, q.w);
-        S.xfx[i] = q;
+      for (int w = 1; w < kWarps; ++w) {
+        m1 = max(m1, wm[0][w]);
+        m2 = max(m2, wm[1][w]);
+      }
+      if (x1) atomicMax(pair, m1);
+      if (x2) atomicMax(pair + 1, m2);
+      if (lb == 0) {
+        atomicExch(other, 0);
+        atomicExch(other + 1, 0);
       }
     }
-    if (!group_sync(S.bar, G, epoch, limit, fault)) return;
-    gemv_fx_rows_body<kFxSplit, true>(S.A, S.lda, S.fxC, S.fxrow, S.n, x, S.xfx, E, bad, y, lb, G);
+    if (!group_sync(S.bar, G, epoch, limit, fault)) return false;
+    e1 = *reinterpret_cast<volatile const int*>(pair);
+    e2 = *reinterpret_cast<volatile const int*>(pair + 1);
+    bad = S.fxrow[S.n] != 0 || (x1 && e1 == 0x7FF) || (x2 && e2 == 0x7FF);
+    if (!bad) {
+      for (int64_t i = (int64_t)lb * kBlock + threadIdx.x; i < S.n; i += stride) {
+        int4 q;
+        if (x1) {
+          const double2 v = ldc_unit(x1 + i);
+          fx_split(v.x, e1, q.x, q.y);
+          fx_split(v.y, e1, q.z, q.w);
+          xd1[i] = q;
+        }
+        if (x2) {
+          const double2 v = fx_row_scaled(ldc_unit(x2 + i), S.fxrow[i], fm);
+          fx_split(v.x, e2, q.x, q.y);
+          fx_split(v.y, e2, q.z, q.w);
+          xd2[i] = q;
+        }
+      }
+    }
+    return group_sync(S.bar, G, epoch, limit, fault);
+  }
+  // complex128 y = A x in fixed point: the digits of x, then the rows from
+  // the operator's digits
+  __device__ void fx_sweep(const double2* x, double2* y) {
+    int e1 = 0, e2 = 0;
+    bool bad = false;
+    if (!fx_split_group(x, S.xfx, nullptr, nullptr, e1, e2, bad)) return;
+    gemv_fx_rows_body<kFxSplit, true>(S.A, S.lda, S.fxC, S.fxrow, S.n, x, S.xfx, e1, bad, y, lb, G);
   }
   // A^H x as ns_c partial vectors in P2
   __device__ MvOut<R> sweep_c(const cx<R>* x) {
     const int64_t nt = (int64_t)S.ncb * S.ns_c;
-    for (int64_t t = lb; t < nt; t += G)
-      gemv_tile_body<R, U, 4, false, true, true>(S.A, S.lda, S.n, S.rpr_c, nullptr, x, nullptr, S.P2, t % S.ncb,
-                                                 t / S.ncb, tsm);
+    bool fx = false;
+    if constexpr (sizeof(R) == 8) {
+      if (S.fxC != nullptr) {
+        int e1 = 0, e2 = 0;
+        bool bad = false;
+        if (fx_split_group(nullptr, nullptr, x, S.xfx2, e1, e2, bad)) {
+          fx = !bad;
+          if (fx)
+            for (int64_t t = lb; t < nt; t += G)
+              gemv_fx_tile_body<false, true>(S.fxC, S.fxrow, S.n, S.rpr_c, nullptr, 0, S.xfx2, e2, nullptr, S.P2,
+                                             t % S.ncb, t / S.ncb, tsm);
+        } else {
+          fx = true;  // a barrier gave up: the caller's next barrier returns
+        }
+      }
+    }
+    if (!fx)
+      for (int64_t t = lb; t < nt; t += G)
+        gemv_tile_body<R, U, 4, false, true, true>(S.A, S.lda, S.n, S.rpr_c, nullptr, x, nullptr, S.P2, t % S.ncb,
+                                                   t / S.ncb, tsm);
     count_sweep();
     MvOut<R> m;
     m.y = nullptr; m.P = S.P2; m.ld = S.n; m.nparts = S.ns_c;
@@ -213,9 +273,26 @@ template <class R, int U> struct PkCtx {
   // A x1 (ncb partials in P1) and A^H x2 (ns_b partials in P2) from one read of A
   __device__ void sweep_both(const cx<R>* x1, const cx<R>* x2, MvOut<R>& o1, MvOut<R>& o2) {
     const int64_t nt = (int64_t)S.ncb * S.ns_b;
-    for (int64_t t = lb; t < nt; t += G)
-      gemv_tile_body<R, U, 4, true, true, true>(S.A, S.lda, S.n, S.rpr_b, x1, x2, S.P1, S.P2, t % S.ncb, t / S.ncb,
-                                                tsm);
+    bool fx = false;
+    if constexpr (sizeof(R) == 8) {
+      if (S.fxC != nullptr) {
+        int e1 = 0, e2 = 0;
+        bool bad = false;
+        if (fx_split_group(x1, S.xfx, x2, S.xfx2, e1, e2, bad)) {
+          fx = !bad;
+          if (fx)
+            for (int64_t t = lb; t < nt; t += G)
+              gemv_fx_tile_body<true, true>(S.fxC, S.fxrow, S.n, S.rpr_b, S.xfx, e1, S.xfx2, e2, S.P1, S.P2,
+                                            t % S.ncb, t / S.ncb, tsm);
+        } else {
+          fx = true;
+        }
+      }
+    }
+    if (!fx)
+      for (int64_t t = lb; t < nt; t += G)
+        gemv_tile_body<R, U, 4, true, true, true>(S.A, S.lda, S.n, S.rpr_b, x1, x2, S.P1, S.P2, t % S.ncb,
+                                                  t / S.ncb, tsm);
     count_sweep();
     o1.y = nullptr; o1.P = S.P1; o1.ld = S.n; o1.nparts = S.ncb;
     o2.y = nullptr; o2.P = S.P2; o2.ld = S.n; o2.nparts = S.ns_b;
@@ -365,7 +442,7 @@ template <class R, int U, int method> __device__ void pk_run_method(PkCtx<R, U>&
 }
 
 template <class R, int U, int M>
-__global__ void __launch_bounds__(kBlock, 3) pk_solve(const PkSys<R>* __restrict__ sys, int count, long long limit,
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 8 ? 2 : 3) pk_solve(const PkSys<R>* __restrict__ sys, int count, long long limit,
                                                       int* fault, int withhold) {
   __shared__ cx<R> tsm[tile_smem_elems<R, U, 4>()];
   int lo = 0, hi = count - 1;  // the group of this block: largest g with sys[g].b0 <= blockIdx.x
@@ -522,12 +599,13 @@ int pk_solve_jobs(ccg_handle* h, int method, int count, const PkJob<R>* jobs, ch
     S.nvb = phase_grid(h, d.n);
     S.r32 = j.r32; S.d32 = j.d32; S.outer = j.outer;
     S.want_true = j.want_true ? 1 : 0; S.scratch = j.w.scratch;
-    S.fxC = nullptr; S.fxrow = nullptr; S.xfx = nullptr; S.fxe = dfxe + 4 * k;
+    S.fxC = nullptr; S.fxrow = nullptr; S.xfx = nullptr; S.xfx2 = nullptr; S.fxe = dfxe + 4 * k;
     if (sizeof(R) == 8 && h->fx_mode && j.w.xfx != nullptr && fx_prepare(h, j.op)) {
       const char* base = static_cast<const char*>(j.op->fx_a);
       S.fxC = reinterpret_cast<const int4*>(base);
       S.fxrow = reinterpret_cast<const int*>(base + (size_t)d.n * d.n * sizeof(int4) + 256);
       S.xfx = j.w.xfx;
+      S.xfx2 = j.w.xfx2;
     }
     b0 += nb[k];
 

@@ -351,6 +351,16 @@ template <class R> struct Runner {
 
   MvOut<R> plain(const cx<R>* y) const { MvOut<R> m; m.y = y; m.P = nullptr; m.ld = d.n; m.nparts = 1; return m; }
 
+  // The operator's fixed-point digits (complex128 dense, integer-pipe sweeps
+  // on; made on first use), or null: the FP64 pipe.
+  const int4* fx_digits() {
+    if (sizeof(R) != 8 || !h->fx_mode || w.xfx == nullptr || !fx_prepare(h, op)) return nullptr;
+    return static_cast<const int4*>(op->fx_a);
+  }
+  const int* fx_rowexp() const {
+    return reinterpret_cast<const int*>(static_cast<const char*>(op->fx_a) + (size_t)d.n * d.n * sizeof(int4) + 256);
+  }
+
   // One GMRES orthogonalisation pass of step j over the basis.
   template <int MODE> void gm_pass_launch(cx<R>* wv, int j) {
     const int grid = gm_grid(d.n);
@@ -388,15 +398,13 @@ template <class R> struct Runner {
       if constexpr (sizeof(R) == 4) {
         if (d.unit == 2) launch(gemv_n_rows<R, 2, kRowSplit>, dim3(d.grid_rows), dim3(kBlock), A, lda, n, x, y, cst, rec);
         else launch(gemv_n_rows<R, 1, kRowSplit>, dim3(d.grid_rows), dim3(kBlock), A, lda, n, x, y, cst, rec);
-      } else if (h->fx_mode && w.xfx != nullptr && fx_prepare(h, op)) {
+      } else if (const int4* C = fx_digits()) {
         // the integer-pipe sweep: the vector's digits, then the rows from the
         // operator's digit copy (both launches inside the sweep's timing)
-        const char* base = static_cast<const char*>(op->fx_a);
-        const int4* C = reinterpret_cast<const int4*>(base);
-        const int* rowexp = reinterpret_cast<const int*>(base + (size_t)d.n * d.n * sizeof(int4) + 256);
+        const int* rowexp = fx_rowexp();
         const int4* xd = w.xfx;
         const int* meta = w.xmeta;
-        launch(fx_split_vector<1024>, dim3(1), dim3(1024), x, n, w.xfx, w.xmeta, cst);
+        launch(fx_split_vector<1024, false>, dim3(1), dim3(1024), x, n, w.xfx, w.xmeta, cst, rowexp);
         launch(gemv_fx_rows<kFxSplit>, dim3(d.grid_fx), dim3(kBlock), A, lda, C, rowexp, n, x, xd, meta, y, cst, rec);
       } else {
         launch(gemv_n_rows<R, 1, kRowSplit>, dim3(d.grid_rows), dim3(kBlock), A, lda, n, x, y, cst, rec);
@@ -429,6 +437,13 @@ template <class R> struct Runner {
     if constexpr (sizeof(R) == 4) {
       if (d.unit == 2) launch(gemv_tile_h<R, 2, Dense<R>::E>, grid, dim3(kBlock), A, lda, n, rpr, x, P2, cst, rec);
       else launch(gemv_tile_h<R, 1, Dense<R>::E>, grid, dim3(kBlock), A, lda, n, rpr, x, P2, cst, rec);
+    } else if (const int4* C = fx_digits()) {
+      // the integer-pipe sweep: the row-scaled vector's digits, then the tiles
+      const int* rowexp = fx_rowexp();
+      launch(fx_split_vector<1024, true>, dim3(1), dim3(1024), x, n, w.xfx2, w.xmeta2, cst, rowexp);
+      launch(gemv_fx_tile<false>, grid, dim3(kBlock), A, lda, C, rowexp, n, rpr, static_cast<const cx<R>*>(nullptr),
+             x, static_cast<const int4*>(nullptr), static_cast<const int*>(nullptr), static_cast<const int4*>(w.xfx2),
+             static_cast<const int*>(w.xmeta2), static_cast<cx<R>*>(nullptr), P2, cst, rec);
     } else {
       launch(gemv_tile_h<R, 1, Dense<R>::E>, grid, dim3(kBlock), A, lda, n, rpr, x, P2, cst, rec);
     }
@@ -459,6 +474,14 @@ template <class R> struct Runner {
         launch(gemv_tile<R, 2, Dense<R>::E, true, true>, grid, dim3(kBlock), A, lda, n, rpr, x1, x2, P1, P2, cst, rec);
       else
         launch(gemv_tile<R, 1, Dense<R>::E, true, true>, grid, dim3(kBlock), A, lda, n, rpr, x1, x2, P1, P2, cst, rec);
+    } else if (const int4* C = fx_digits()) {
+      // the integer-pipe sweep: the digits of x1 and of the row-scaled x2 in
+      // one launch, then the tiles
+      const int* rowexp = fx_rowexp();
+      launch(fx_split_pair<1024>, dim3(2), dim3(1024), x1, w.xfx, w.xmeta, x2, w.xfx2, w.xmeta2, n, rowexp, cst);
+      launch(gemv_fx_tile<true>, grid, dim3(kBlock), A, lda, C, rowexp, n, rpr, x1, x2,
+             static_cast<const int4*>(w.xfx), static_cast<const int*>(w.xmeta), static_cast<const int4*>(w.xfx2),
+             static_cast<const int*>(w.xmeta2), P1, P2, cst, rec);
     } else {
       launch(gemv_tile<R, 1, Dense<R>::E, true, true>, grid, dim3(kBlock), A, lda, n, rpr, x1, x2, P1, P2, cst, rec);
     }

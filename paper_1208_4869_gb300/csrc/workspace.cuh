@@ -10,6 +10,7 @@
 #include "common.cuh"
 #include "reduce.cuh"
 #include "gemv.cuh"
+#include "fx.cuh"
 #include "internal.h"
 
 namespace ccg {
@@ -36,7 +37,9 @@ constexpr int kFxSplit = 2;
 
 // Launch geometry of the dense sweeps for one operator.
 // Resident blocks per SM of the column-tiled sweep (A^H x alone, or A x1 with
-// A^H x2), from the occupancy calculator.
+// A^H x2), from the occupancy calculator; for complex128 that of the
+// integer-pipe sweeps (the default; the FP64-pipe fallback runs the same
+// tiles).
 template <class R> static int tile_occupancy(int unit, bool both) {
   static int cache[2][2] = {{0, 0}, {0, 0}};
   int& c = cache[unit == 2 ? 1 : 0][both ? 1 : 0];
@@ -46,7 +49,7 @@ template <class R> static int tile_occupancy(int unit, bool both) {
       if (unit == 2) fn = both ? (const void*)gemv_tile<R, 2, 4, true, true> : (const void*)gemv_tile_h<R, 2, 4>;
       else fn = both ? (const void*)gemv_tile<R, 1, 4, true, true> : (const void*)gemv_tile_h<R, 1, 4>;
     } else {
-      fn = both ? (const void*)gemv_tile<R, 1, 4, true, true> : (const void*)gemv_tile_h<R, 1, 4>;
+      fn = both ? (const void*)gemv_fx_tile<true> : (const void*)gemv_fx_tile<false>;
     }
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kBlock, 0) != cudaSuccess) {
@@ -58,15 +61,28 @@ template <class R> static int tile_occupancy(int unit, bool both) {
   return c;
 }
 
-// Row ranges of a column-tiled sweep: enough (column chunk, row range)
-// blocks to fill every SM once at the kernel's occupancy.
+// Row ranges of a column-tiled sweep: the number of ranges ns (1 .. 32, at
+// least 8 rows each) whose ncb x ns tiles finish soonest on `slots`
+// resident blocks -- ceil(tiles / slots) waves of tiles of 1/tiles of the
+// work each -- the fewest ranges among equals.  (Filling the slots once with
+// a few tiles to spare left a second wave of those few.)
 struct TileSplit {
   int nsplit;
   int64_t rows_per_range;
 };
-static TileSplit tile_split(int64_t n, int ncb, int64_t target) {
-  int64_t ns = (target + ncb - 1) / ncb;
-  ns = std::max<int64_t>(1, std::min<int64_t>(ns, std::min<int64_t>(32, (n + kWarps - 1) / kWarps)));
+static TileSplit tile_split(int64_t n, int ncb, int64_t slots) {
+  const int64_t cap = std::max<int64_t>(1, std::min<int64_t>(32, (n + kWarps - 1) / kWarps));
+  slots = std::max<int64_t>(1, slots);
+  int64_t ns = 1;
+  double best = 1e300;
+  for (int64_t k = 1; k <= cap; ++k) {
+    const int64_t tiles = (int64_t)ncb * k;
+    const double t = (double)((tiles + slots - 1) / slots) / (double)tiles;
+    if (t < best * (1.0 - 1e-12)) {
+      best = t;
+      ns = k;
+    }
+  }
   TileSplit t;
   t.rows_per_range = (n + ns - 1) / ns;
   t.nsplit = (int)((n + t.rows_per_range - 1) / t.rows_per_range);
@@ -149,6 +165,8 @@ template <class R> struct Ws {
   double* scratch;  // a few doubles for standalone results
   int4* xfx;        // complex128: the digits of a sweep's vector (fx.cuh)
   int* xmeta;       // and its exponent and non-finite flag
+  int4* xfx2;       // the row-scaled vector of an A^H x sweep, and its exponent
+  int* xmeta2;
 };
 
 // basis = m + 1 GMRES basis vectors (0 for the other methods).
@@ -170,7 +188,7 @@ template <class R> static size_t ws_bytes(int64_t n, const Dense<R>& d, int maxi
   b += align256(sizeof(SolveState));
   b += align256((size_t)(maxit + 1) * sizeof(double));
   b += align256(16 * sizeof(double));
-  if (sizeof(R) == 8) b += align256(n * sizeof(int4)) + align256(4 * sizeof(int));
+  if (sizeof(R) == 8) b += 2 * (align256(n * sizeof(int4)) + align256(4 * sizeof(int)));
   return b;
 }
 
@@ -204,11 +222,13 @@ template <class R> static Ws<R> ws_carve(char* base, int64_t n, const Dense<R>& 
   w.st = reinterpret_cast<SolveState*>(take(sizeof(SolveState)));
   w.hist = reinterpret_cast<double*>(take((size_t)(maxit + 1) * sizeof(double)));
   w.scratch = reinterpret_cast<double*>(take(16 * sizeof(double)));
-  w.xfx = nullptr;
-  w.xmeta = nullptr;
+  w.xfx = w.xfx2 = nullptr;
+  w.xmeta = w.xmeta2 = nullptr;
   if (sizeof(R) == 8) {
     w.xfx = reinterpret_cast<int4*>(take(n * sizeof(int4)));
     w.xmeta = reinterpret_cast<int*>(take(4 * sizeof(int)));
+    w.xfx2 = reinterpret_cast<int4*>(take(n * sizeof(int4)));
+    w.xmeta2 = reinterpret_cast<int*>(take(4 * sizeof(int)));
   }
   return w;
 }
@@ -248,6 +268,7 @@ template <class R> struct PkSys {
   const int4* fxC;
   const int* fxrow;
   int4* xfx;
+  int4* xfx2;                // the row-scaled vector of an A^H x sweep
   int* fxe;
   // refinement step (M_REFRES): the inner solve's right-hand side and
   // correction (complex64), the outer step's index; and whether the group

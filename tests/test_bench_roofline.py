@@ -52,16 +52,24 @@ def test_tensor_products_report_issued_bf16_work(kind, prec, name, products):
 def test_complex128_fp64_sweeps_use_the_measured_rate():
     n = 8192
     stats = {(ccg.C128, 1): (10, 4.67, n * n * 16.0)}     # A^H x on the FP64 pipe
-    r = bench.roofline(ccg, stats, n, rates={"fp64_fma_tflops": 1.254})
+    r = bench.roofline(ccg, stats, n, rates={"fp64_fma_tflops": 1.254}, fx=False)
     assert r["kernel"] == "gemv_tile_c_c128" and r["bound"] == "alu" and r["peak"] == 1.254
     assert r["achieved"] == pytest.approx(8.0 * n * n / 0.467e-3 / 1e12)
     assert "measured" in r["peak_source"]
     # without a measurement: the datasheet rate, said so
-    r = bench.roofline(ccg, stats, n)
+    r = bench.roofline(ccg, stats, n, fx=False)
     assert r["peak"] == bench.FP64_NOMINAL_TFLOPS and "nominal" in r["peak_source"]
     # the FP64-pipe row sweep (fixed-point sweep switched off)
     r = bench.roofline(ccg, {(ccg.C128, 0): (10, 4.67, n * n * 16.0)}, n, rates={"fp64_fma_tflops": 1.25}, fx=False)
     assert r["kernel"] == "gemv_n_rows_c128" and r["bound"] == "alu"
+
+
+@pytest.mark.parametrize("kind,tag", [(0, "gemv_fx_rows_c128"), (1, "gemv_fx_tile_c_c128"),
+                                      (2, "gemv_fx_tile_both_c128")])
+def test_fixed_point_sweeps_are_tagged_hbm_bound(kind, tag):
+    n = 4096
+    r = bench.roofline(ccg, {(ccg.C128, kind): (4, 0.4, n * n * 16.0)}, n, rates={"fp64_fma_tflops": 1.25})
+    assert r["kernel"] == tag and r["bound"] == "hbm"
 
 
 def test_fixed_point_row_sweep_is_hbm_bound():

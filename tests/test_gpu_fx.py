@@ -76,13 +76,52 @@ def exact_matvec_error(A, x, y):
     return worst
 
 
-def matvec(ccg, A, x, fx):
+def exact_matvec_h_error(A, x, y):
+    """max over columns of |y_c - (A^H x)_c| / (2.5 n 2^(Fm + Fx' - 52)),
+    exactly: the A^H sweep's bound, with 2^Fm above every entry of A and
+    2^Fx' above every part of x_r 2^(F_r - Fm) (F_r: row r's scale)."""
+    n = A.shape[0]
+    ar, ae_r = exact_parts(A.real)
+    ai, ae_i = exact_parts(A.imag)
+    xr, xe_r = exact_parts(x.real)
+    xi, xe_i = exact_parts(x.imag)
+    frow = [max(math.frexp(float(v))[1] for v in np.concatenate([np.abs(A[r].real), np.abs(A[r].imag)]))
+            for r in range(n)]
+    fm = max(frow)
+    fx = max(math.frexp(math.ldexp(float(v), frow[r] - fm))[1]
+             for r in range(n) for v in (abs(x[r].real), abs(x[r].imag)))
+    base = int(min(ae_r.min(), ae_i.min()) + min(xe_r.min(), xe_i.min()))
+    worst = 0.0
+    for c in range(n):
+        re = 0
+        im = 0
+        for r in range(n):
+            p = int(ar[r, c]) * int(xr[r]) << int(ae_r[r, c] + xe_r[r] - base)
+            q = int(ai[r, c]) * int(xi[r]) << int(ae_i[r, c] + xe_i[r] - base)
+            re += p + q
+            s = int(ar[r, c]) * int(xi[r]) << int(ae_r[r, c] + xe_i[r] - base)
+            t = int(ai[r, c]) * int(xr[r]) << int(ae_i[r, c] + xe_r[r] - base)
+            im += s - t
+        for got, ex in ((y[c].real, re), (y[c].imag, im)):
+            g_m, g_e = math.frexp(float(got))
+            g_int = int(g_m * 2 ** 53)
+            g_sh = g_e - 53 - base
+            diff = (g_int << g_sh) - ex if g_sh >= 0 else g_int - (ex << -g_sh)
+            scale = base if g_sh >= 0 else base + g_sh
+            if diff == 0:
+                continue
+            lr = math.log2(abs(diff)) + scale - (math.log2(2.5 * n) + fm + fx - 52)
+            worst = max(worst, 2.0 ** min(lr, 64))
+    return worst
+
+
+def matvec(ccg, A, x, fx, trans=False):
     h = ccg.Handle()
     h.set_option(ccg.OPT_FP64_SWEEP, fx)
     Ad = torch.from_numpy(A).cuda()
     op = h.op_dense(Ad)
     y = torch.empty(A.shape[0], dtype=torch.complex128, device="cuda")
-    h.matvec(op, torch.from_numpy(x).cuda(), y)
+    h.matvec(op, torch.from_numpy(x).cuda(), y, trans=trans)
     torch.cuda.synchronize()
     return y.cpu().numpy()
 
@@ -117,6 +156,35 @@ def test_fixed_point_wide_range(ccg):
     assert exact_matvec_error(A, x, y) <= 1.0
 
 
+@pytest.mark.parametrize("n", [1, 7, 129, 300])
+def test_fixed_point_adjoint_within_bound(ccg, n):
+    """A^H x on the integer pipe (the row-scaled vector's digits against the
+    operator's): within its bound, and near double rounding in practice."""
+    A, _ = W.dense_system(n, 3.0, n + 40)
+    x = W.random_vector(n, n + 41)
+    y = matvec(ccg, A, x, 1, trans=True)
+    assert exact_matvec_h_error(A, x, y) <= 1.0
+    ref = O.DenseOp(A).matvec(x, trans=True)
+    scale = np.abs(A).T @ np.abs(x)
+    assert np.max(np.abs(y - ref) / scale) < 1e-14
+
+
+def test_fixed_point_adjoint_wide_range(ccg):
+    """Rows over 2^-300 .. 2^300 (the row scales folded into the vector),
+    subnormal entries, a zero row, zero entries of x: within the bound."""
+    n = 80
+    rng = np.random.default_rng(15)
+    A, _ = W.dense_system(n, 1.0, 4)
+    A = A * np.exp2(rng.integers(-300, 300, n))[:, None]
+    A[5] = 0
+    A[7, ::3] = 5e-320 + 3e-320j
+    x = W.random_vector(n, 5)
+    x[::7] = 0
+    x[3] *= 2.0 ** 60
+    y = matvec(ccg, A, x, 1, trans=True)
+    assert exact_matvec_h_error(A, x, y) <= 1.0
+
+
 def test_non_finite_takes_the_fp64_pipe(ccg):
     n = 200
     A, _ = W.dense_system(n, 3.0, 8)
@@ -136,14 +204,23 @@ def test_non_finite_takes_the_fp64_pipe(ccg):
     assert np.array_equal(np.isnan(y1), np.isnan(y0)) and np.isnan(y1[3]) and np.isfinite(y1[4])
     fin = np.isfinite(y0)
     assert np.allclose(y1[fin], y0[fin], rtol=1e-13, atol=0)
+    # the same for A^H x (the column-tiled sweep): an infinite x_17 reaches
+    # every column; a NaN at A[3, 4] only column 4
+    for Ax, xx, some_finite in ((A, xb, False), (Ab, x, True)):
+        y1, y0 = matvec(ccg, Ax, xx, 1, trans=True), matvec(ccg, Ax, xx, 0, trans=True)
+        assert np.array_equal(np.isnan(y1), np.isnan(y0)) and np.array_equal(np.isinf(y1), np.isinf(y0))
+        fin = np.isfinite(y0)
+        assert fin.any() == some_finite and np.allclose(y1[fin], y0[fin], rtol=1e-13, atol=0)
+    assert np.isnan(y1[4]) and np.isfinite(y1[3])
 
 
 def test_fixed_point_solves_match_oracle(ccg):
-    """complex128 solves on the fixed-point sweep: whole BiCGSTAB, CGNR and QMR
-    solves against the oracle (x to 1e-9) with both sweeps."""
+    """complex128 solves on the fixed-point sweeps (rows, A^H x, and A p with
+    A^H q from one read for QMR and BiCG): whole solves against the oracle (x
+    to 1e-9) with the integer and the FP64 sweeps."""
     n = 1000
     A, y = W.dense_system(n, 3.0, 21)
-    for m in ("bicgstab", "cgnr", "qmr"):
+    for m in ("bicgstab", "cgnr", "qmr", "bicg", "cgne"):
         ref = O.solve(O.DenseOp(A), m, y, tol=1e-10, maxit=300)
         for fx in (1, 0):
             h = ccg.Handle()
