@@ -118,6 +118,20 @@ __global__ void __launch_bounds__(THREADS) fx_split_pair(const double2* __restri
   else fx_split_block<THREADS, true>(x2, n, xd2, meta2, rowexp);
 }
 
+// A sum of two int64 values through 32-bit adds with carry (integer pipe).
+__device__ __forceinline__ long long add_i64(long long a, long long b) {
+  long long d;
+  asm("{\n\t.reg .u32 al, ah, bl, bh, dl, dh;\n\t"
+      "mov.b64 {al, ah}, %1;\n\tmov.b64 {bl, bh}, %2;\n\t"
+      "add.cc.u32 dl, al, bl;\n\taddc.u32 dh, ah, bh;\n\t"
+      "mov.b64 %0, {dl, dh};\n\t}"
+      : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ long long shfl_xor_add_i64(long long v, int o) {
+  return add_i64(v, __shfl_xor_sync(0xffffffffu, v, o));
+}
+
 // Exact complex digit products into int64: re += ar xr - ai xi,
 // im += ar xi + ai xr, high digit products (x 2^52) apart from the middle
 // ones (x 2^26).
@@ -281,6 +295,20 @@ __global__ void __launch_bounds__(kBlock) gemv_fx_rows(const double2* __restrict
   pdl_launch();
 }
 
+// One row's A x1 chunk sum from its exact int64 parts, scaled by
+// 2^(F_r + F_x1 - 78) into P1[row].  GB300's FP64 pipe does the int64 ->
+// double conversions at a warp instruction per conversion whatever the
+// active lanes, so the fused sweep batches them: a warp converts 32 rows
+// at once (one conversion per row each had held that sweep to the FP64
+// pipe, 80% busy at 1.2 TB/s).
+__device__ __forceinline__ void fx_tile_row_store(FxAcc q, int64_t row, const int* __restrict__ rowexp, int xexp1,
+                                                  double2* P1c) {
+  double re = 0.0, im = 0.0;
+  q.flush(re, im);
+  const int e = max(rowexp[row], 1) + max(xexp1, 1) - 2122;
+  P1c[row] = make_double2(ldexp(re, e), ldexp(im, e));
+}
+
 // The column-tiled complex128 sweeps on the integer pipe: A^H x2 alone
 // (Y1 = false) or with A x1 (Y1 = true) from one read of the digits, over the
 // tiles of gemv_tile_body (column chunk of 128 columns, a lane per 4 columns,
@@ -288,8 +316,9 @@ __global__ void __launch_bounds__(kBlock) gemv_fx_rows(const double2* __restrict
 // xd1 holds the digits of x1 (exponent xexp1), xd2 those of the row-scaled
 // x2' (exponent xexp2, fm the operator's largest row exponent).  A^H x2
 // accumulates each column exactly in int64 per warp, converted to double
-// every 256 rows; A x1 forms each row's chunk sum exactly and converts it
-// once.  KC as in gemv_rows_body; smem_ext as in gemv_tile_body.
+// every 256 rows; A x1 forms each row's chunk sum exactly, reduced across
+// the warp in int64, converted 32 rows at a time (fx_tile_row_store).  KC as
+// in gemv_rows_body; smem_ext as in gemv_tile_body.
 template <bool Y1, bool KC>
 __device__ __forceinline__ void gemv_fx_tile_body(const int4* __restrict__ C, const int* __restrict__ rowexp,
                                                   int64_t n, int64_t rows_per_range, const int4* xd1, int xexp1,
@@ -318,7 +347,38 @@ __device__ __forceinline__ void gemv_fx_tile_body(const int4* __restrict__ C, co
     dim[j] = 0.0;
   }
   int cnt = 0;
-  for (int64_t r = r0 + warp; r < r1; r += kWarps) {
+  int kept = 0;      // rows of this warp whose sums wait in lanes 0 .. kept-1
+  FxAcc kq;          // this lane's waiting row sums, and their row
+  int64_t krow = 0;
+  kq.zero();
+  int64_t r = r0 + warp;
+  if constexpr (!Y1) {
+    // A^H x2 alone: two rows per iteration, 8 loads of 16 bytes in flight per lane
+    for (; r + kWarps < r1; r += 2 * kWarps) {
+      const int4* ca = C + r * n;
+      const int4* cb = ca + kWarps * n;
+      int4 av[E], bv[E];
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        const int64_t u = col0 + lane + 32 * j;
+        av[j] = u < n ? ld_stream_i4(ca + u) : make_int4(0, 0, 0, 0);
+        bv[j] = u < n ? ld_stream_i4(cb + u) : make_int4(0, 0, 0, 0);
+      }
+      const int4 xa = KC ? ldc_i4(xd2 + r) : __ldg(xd2 + r);
+      const int4 xb = KC ? ldc_i4(xd2 + r + kWarps) : __ldg(xd2 + r + kWarps);
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        acc[j].mac(av[j], xa);
+        acc[j].mac(bv[j], xb);
+      }
+      if ((cnt += 2) >= 256) {
+#pragma unroll
+        for (int j = 0; j < E; ++j) acc[j].flush(dre[j], dim[j]);
+        cnt = 0;
+      }
+    }
+  }
+  for (; r < r1; r += kWarps) {
     const int4* c = C + r * n;
     int4 av[E];
 #pragma unroll
@@ -329,24 +389,38 @@ __device__ __forceinline__ void gemv_fx_tile_body(const int4* __restrict__ C, co
     const int4 xr = KC ? ldc_i4(xd2 + r) : __ldg(xd2 + r);
 #pragma unroll
     for (int j = 0; j < E; ++j) acc[j].mac(av[j], xr);
-    if (++cnt == 256) {
+    if (++cnt >= 256) {
 #pragma unroll
       for (int j = 0; j < E; ++j) acc[j].flush(dre[j], dim[j]);
       cnt = 0;
     }
     if constexpr (Y1) {
+      // the row's chunk sum, reduced across the warp in int64 (exact, below
+      // 2^61); lane (k mod 32) keeps the sums of the warp's k-th row, and
+      // every 32 rows all lanes convert and store theirs at once
       FxAcc s;
       s.zero();
 #pragma unroll
       for (int j = 0; j < E; ++j) s.mac(av[j], xl[j]);
-      double sre = 0.0, sim = 0.0;
-      s.flush(sre, sim);
-      double2 t = warp_csum(make_double2(sre, sim));
-      if (lane == 0) {
-        const int e = max(rowexp[r], 1) + max(xexp1, 1) - 2122;
-        P1[chunk * n + r] = make_double2(ldexp(t.x, e), ldexp(t.y, e));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        s.hre = shfl_xor_add_i64(s.hre, o);
+        s.mre = shfl_xor_add_i64(s.mre, o);
+        s.him = shfl_xor_add_i64(s.him, o);
+        s.mim = shfl_xor_add_i64(s.mim, o);
+      }
+      if (lane == kept) {
+        kq = s;
+        krow = r;
+      }
+      if (++kept == 32) {
+        fx_tile_row_store(kq, krow, rowexp, xexp1, P1 + chunk * n);
+        kept = 0;
       }
     }
+  }
+  if constexpr (Y1) {
+    if (lane < kept) fx_tile_row_store(kq, krow, rowexp, xexp1, P1 + chunk * n);
   }
 #pragma unroll
   for (int j = 0; j < E; ++j) acc[j].flush(dre[j], dim[j]);
