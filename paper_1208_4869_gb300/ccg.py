@@ -39,6 +39,8 @@ OPT_PDL = 11
 PIPE_FP64_FMA = 0
 PIPE_FP32_FMA = 1
 PIPE_IMAD_WIDE = 2
+PIPE_MAD_WIDE_PTX = 3
+PIPE_MAD_PAIR_PTX = 4
 
 # ccg_matvec_fn: int (*)(void* ctx, int64_t n, const void* x, void* y, void* stream)
 MATVEC_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,

@@ -75,6 +75,39 @@ __global__ void __launch_bounds__(256) rate_imad_wide(const int* in, long long* 
   if (s == 0x123456789ll) out[0] = s;
 }
 
+// The same product through the two explicit PTX forms of a 32 x 32 + 64
+// multiply-add: FORM 0 mad.wide.s32, FORM 1 mad.lo.cc.u32 + madc.hi.s32.
+template <int FORM>
+__global__ void __launch_bounds__(256) rate_mad_ptx(const int* in, long long* out, int iters) {
+  const int b = in[threadIdx.x & 31];
+  int a[kChains];
+  long long c[kChains];
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) {
+    a[k] = in[(threadIdx.x + k) & 31];
+    c[k] = in[(threadIdx.x + k + 3) & 31];
+  }
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) {
+      long long d;
+      if (FORM == 0) {
+        asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a[k]), "r"(b), "l"(c[k]));
+      } else {
+        asm("{\n\t.reg .u32 cl, ch, dl, dh;\n\tmov.b64 {cl, ch}, %3;\n\t"
+            "mad.lo.cc.u32 dl, %1, %2, cl;\n\tmadc.hi.s32 dh, %1, %2, ch;\n\tmov.b64 %0, {dl, dh};\n\t}"
+            : "=l"(d) : "r"(a[k]), "r"(b), "l"(c[k]));
+      }
+      c[k] = d;
+      asm volatile("" : "+r"(a[k]));
+    }
+  }
+  long long s = 0;
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) s += c[k];
+  if (s == 0x123456789ll) out[0] = s;
+}
+
 }  // namespace
 }  // namespace ccg
 
@@ -92,7 +125,7 @@ using namespace ccg;
 extern "C" {
 
 ccg_status ccg_pipe_rate(ccg_handle* h, int pipe, double* gops) {
-  if (!h || !gops || pipe < 0 || pipe > 2) {
+  if (!h || !gops || pipe < 0 || pipe > 4) {
     set_error("ccg_pipe_rate: bad handle, pipe or output pointer");
     return CCG_ERR_INVALID;
   }
@@ -106,7 +139,7 @@ ccg_status ccg_pipe_rate(ccg_handle* h, int pipe, double* gops) {
   if (pipe == 1) {
     std::vector<float> f(32, 1.0000001f);
     RATE_CUDA(cudaMemcpyAsync(buf, f.data(), 128, cudaMemcpyHostToDevice, h->stream));
-  } else if (pipe == 2) {
+  } else if (pipe >= 2) {
     std::vector<int> v(32);
     for (int k = 0; k < 32; ++k) v[k] = 7 * k + 3;
     RATE_CUDA(cudaMemcpyAsync(buf, v.data(), 128, cudaMemcpyHostToDevice, h->stream));
@@ -115,7 +148,9 @@ ccg_status ccg_pipe_rate(ccg_handle* h, int pipe, double* gops) {
     char* p = static_cast<char*>(buf);
     if (pipe == 0) rate_dfma<<<blocks, threads, 0, h->stream>>>((const double*)p, (double*)(p + 256), iters);
     else if (pipe == 1) rate_ffma<<<blocks, threads, 0, h->stream>>>((const float*)p, (float*)(p + 256), iters);
-    else rate_imad_wide<<<blocks, threads, 0, h->stream>>>((const int*)p, (long long*)(p + 256), iters);
+    else if (pipe == 2) rate_imad_wide<<<blocks, threads, 0, h->stream>>>((const int*)p, (long long*)(p + 256), iters);
+    else if (pipe == 3) rate_mad_ptx<0><<<blocks, threads, 0, h->stream>>>((const int*)p, (long long*)(p + 256), iters);
+    else rate_mad_ptx<1><<<blocks, threads, 0, h->stream>>>((const int*)p, (long long*)(p + 256), iters);
   };
   cudaEvent_t e0, e1;
   RATE_CUDA(cudaEventCreate(&e0));

@@ -26,6 +26,7 @@ def test_pipe_rates_in_proportion(ccg):
     assert 0.625e3 / 2 < fp64 < 2 * 0.625e3
     assert fp32 > 16 * fp64
     assert imad > 4 * fp64
+    assert h.pipe_rate(ccg.PIPE_MAD_WIDE_PTX) > 4 * fp64 and h.pipe_rate(ccg.PIPE_MAD_PAIR_PTX) > 4 * fp64
     before = h.launch_count()
     h.pipe_rate(ccg.PIPE_FP64_FMA)
     assert h.launch_count() == before + 6
@@ -33,7 +34,7 @@ def test_pipe_rates_in_proportion(ccg):
 
 def test_pipe_rate_rejects_bad_arguments(ccg):
     h = ccg.Handle()
-    for pipe in (-1, 3):
+    for pipe in (-1, 5):
         with pytest.raises(ccg.CcgError) as e:
             h.pipe_rate(pipe)
         assert e.value.status == ccg.ERR_INVALID
