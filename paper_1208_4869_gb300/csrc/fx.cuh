@@ -103,35 +103,6 @@ __global__ void __launch_bounds__(THREADS) fx_split_vector(const double2* __rest
   fx_split_block<THREADS, ROWS>(x, n, xd, meta, rowexp);
 }
 
-// Both vectors of the fused sweep in one launch of two blocks: x1 plain
-// (block 0), x2 row-scaled (block 1).
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS) fx_split_pair(const double2* __restrict__ x1, int4* __restrict__ xd1,
-                                                         int* __restrict__ meta1, const double2* __restrict__ x2,
-                                                         int4* __restrict__ xd2, int* __restrict__ meta2, int64_t n,
-                                                         const int* __restrict__ rowexp,
-                                                         const SolveState* __restrict__ st) {
-  pdl_wait();
-  pdl_launch();
-  if (sweep_skipped(st, nullptr)) return;
-  if (blockIdx.x == 0) fx_split_block<THREADS, false>(x1, n, xd1, meta1, rowexp);
-  else fx_split_block<THREADS, true>(x2, n, xd2, meta2, rowexp);
-}
-
-// A sum of two int64 values through 32-bit adds with carry (integer pipe).
-__device__ __forceinline__ long long add_i64(long long a, long long b) {
-  long long d;
-  asm("{\n\t.reg .u32 al, ah, bl, bh, dl, dh;\n\t"
-      "mov.b64 {al, ah}, %1;\n\tmov.b64 {bl, bh}, %2;\n\t"
-      "add.cc.u32 dl, al, bl;\n\taddc.u32 dh, ah, bh;\n\t"
-      "mov.b64 %0, {dl, dh};\n\t}"
-      : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ long long shfl_xor_add_i64(long long v, int o) {
-  return add_i64(v, __shfl_xor_sync(0xffffffffu, v, o));
-}
-
 // Exact complex digit products into int64: re += ar xr - ai xi,
 // im += ar xi + ai xr, high digit products (x 2^52) apart from the middle
 // ones (x 2^26).
@@ -295,49 +266,28 @@ __global__ void __launch_bounds__(kBlock) gemv_fx_rows(const double2* __restrict
   pdl_launch();
 }
 
-// One row's A x1 chunk sum from its exact int64 parts, scaled by
-// 2^(F_r + F_x1 - 78) into P1[row].  GB300's FP64 pipe does the int64 ->
-// double conversions at a warp instruction per conversion whatever the
-// active lanes, so the fused sweep batches them: a warp converts 32 rows
-// at once (one conversion per row each had held that sweep to the FP64
-// pipe, 80% busy at 1.2 TB/s).
-__device__ __forceinline__ void fx_tile_row_store(FxAcc q, int64_t row, const int* __restrict__ rowexp, int xexp1,
-                                                  double2* P1c) {
-  double re = 0.0, im = 0.0;
-  q.flush(re, im);
-  const int e = max(rowexp[row], 1) + max(xexp1, 1) - 2122;
-  P1c[row] = make_double2(ldexp(re, e), ldexp(im, e));
-}
-
-// The column-tiled complex128 sweeps on the integer pipe: A^H x2 alone
-// (Y1 = false) or with A x1 (Y1 = true) from one read of the digits, over the
-// tiles of gemv_tile_body (column chunk of 128 columns, a lane per 4 columns,
-// row range `range` of rows_per_range rows; the same partial-sum outputs).
-// xd1 holds the digits of x1 (exponent xexp1), xd2 those of the row-scaled
-// x2' (exponent xexp2, fm the operator's largest row exponent).  A^H x2
-// accumulates each column exactly in int64 per warp, converted to double
-// every 256 rows; A x1 forms each row's chunk sum exactly, reduced across
-// the warp in int64, converted 32 rows at a time (fx_tile_row_store).  KC as
-// in gemv_rows_body; smem_ext as in gemv_tile_body.
-template <bool Y1, bool KC>
+// A^H x on the integer pipe over the tiles of gemv_tile_body (column chunk
+// of 128 columns, a lane per 4 columns, row range `range` of rows_per_range
+// rows; the same partial-sum output).  xd2 holds the digits of the
+// row-scaled x' (exponent xexp2; rowexp[n + 1] is the operator's largest row
+// exponent).  Each column accumulates exactly in int64 per warp, two rows
+// per iteration (8 loads of 16 bytes in flight per lane), converted to
+// double every 256 rows.  KC as in gemv_rows_body; smem_ext as in
+// gemv_tile_body.  (A fused form that also formed A x1 from the same read
+// reduced each row's chunk sum across the warp and ran at 0.58 ms at
+// n = 8192, slower than this sweep and the row sweep run one after the
+// other, 0.26 + 0.20 ms: the complex128 A p + A^H q uses the two.)
+template <bool KC>
 __device__ __forceinline__ void gemv_fx_tile_body(const int4* __restrict__ C, const int* __restrict__ rowexp,
-                                                  int64_t n, int64_t rows_per_range, const int4* xd1, int xexp1,
-                                                  const int4* xd2, int xexp2, double2* P1, double2* P2,
-                                                  int64_t chunk, int64_t range, double2* smem_ext = nullptr) {
+                                                  int64_t n, int64_t rows_per_range, const int4* xd2, int xexp2,
+                                                  double2* P2, int64_t chunk, int64_t range,
+                                                  double2* smem_ext = nullptr) {
   constexpr int E = 4, CBU = 32 * E;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t col0 = chunk * CBU;
   const int64_t r0 = range * rows_per_range;
   const int64_t r1 = r0 + rows_per_range < n ? r0 + rows_per_range : n;
   const int fm = max(rowexp[n + 1], 1);
-  int4 xl[E];
-  if constexpr (Y1) {
-#pragma unroll
-    for (int j = 0; j < E; ++j) {
-      const int64_t u = col0 + lane + 32 * j;
-      xl[j] = u < n ? (KC ? ldc_i4(xd1 + u) : __ldg(xd1 + u)) : make_int4(0, 0, 0, 0);
-    }
-  }
   FxAccH acc[E];
   double dre[E], dim[E];
 #pragma unroll
@@ -347,35 +297,28 @@ __device__ __forceinline__ void gemv_fx_tile_body(const int4* __restrict__ C, co
     dim[j] = 0.0;
   }
   int cnt = 0;
-  int kept = 0;      // rows of this warp whose sums wait in lanes 0 .. kept-1
-  FxAcc kq;          // this lane's waiting row sums, and their row
-  int64_t krow = 0;
-  kq.zero();
   int64_t r = r0 + warp;
-  if constexpr (!Y1) {
-    // A^H x2 alone: two rows per iteration, 8 loads of 16 bytes in flight per lane
-    for (; r + kWarps < r1; r += 2 * kWarps) {
-      const int4* ca = C + r * n;
-      const int4* cb = ca + kWarps * n;
-      int4 av[E], bv[E];
+  for (; r + kWarps < r1; r += 2 * kWarps) {
+    const int4* ca = C + r * n;
+    const int4* cb = ca + kWarps * n;
+    int4 av[E], bv[E];
 #pragma unroll
-      for (int j = 0; j < E; ++j) {
-        const int64_t u = col0 + lane + 32 * j;
-        av[j] = u < n ? ld_stream_i4(ca + u) : make_int4(0, 0, 0, 0);
-        bv[j] = u < n ? ld_stream_i4(cb + u) : make_int4(0, 0, 0, 0);
-      }
-      const int4 xa = KC ? ldc_i4(xd2 + r) : __ldg(xd2 + r);
-      const int4 xb = KC ? ldc_i4(xd2 + r + kWarps) : __ldg(xd2 + r + kWarps);
+    for (int j = 0; j < E; ++j) {
+      const int64_t u = col0 + lane + 32 * j;
+      av[j] = u < n ? ld_stream_i4(ca + u) : make_int4(0, 0, 0, 0);
+      bv[j] = u < n ? ld_stream_i4(cb + u) : make_int4(0, 0, 0, 0);
+    }
+    const int4 xa = KC ? ldc_i4(xd2 + r) : __ldg(xd2 + r);
+    const int4 xb = KC ? ldc_i4(xd2 + r + kWarps) : __ldg(xd2 + r + kWarps);
 #pragma unroll
-      for (int j = 0; j < E; ++j) {
-        acc[j].mac(av[j], xa);
-        acc[j].mac(bv[j], xb);
-      }
-      if ((cnt += 2) >= 256) {
+    for (int j = 0; j < E; ++j) {
+      acc[j].mac(av[j], xa);
+      acc[j].mac(bv[j], xb);
+    }
+    if ((cnt += 2) >= 256) {
 #pragma unroll
-        for (int j = 0; j < E; ++j) acc[j].flush(dre[j], dim[j]);
-        cnt = 0;
-      }
+      for (int j = 0; j < E; ++j) acc[j].flush(dre[j], dim[j]);
+      cnt = 0;
     }
   }
   for (; r < r1; r += kWarps) {
@@ -394,33 +337,6 @@ __device__ __forceinline__ void gemv_fx_tile_body(const int4* __restrict__ C, co
       for (int j = 0; j < E; ++j) acc[j].flush(dre[j], dim[j]);
       cnt = 0;
     }
-    if constexpr (Y1) {
-      // the row's chunk sum, reduced across the warp in int64 (exact, below
-      // 2^61); lane (k mod 32) keeps the sums of the warp's k-th row, and
-      // every 32 rows all lanes convert and store theirs at once
-      FxAcc s;
-      s.zero();
-#pragma unroll
-      for (int j = 0; j < E; ++j) s.mac(av[j], xl[j]);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        s.hre = shfl_xor_add_i64(s.hre, o);
-        s.mre = shfl_xor_add_i64(s.mre, o);
-        s.him = shfl_xor_add_i64(s.him, o);
-        s.mim = shfl_xor_add_i64(s.mim, o);
-      }
-      if (lane == kept) {
-        kq = s;
-        krow = r;
-      }
-      if (++kept == 32) {
-        fx_tile_row_store(kq, krow, rowexp, xexp1, P1 + chunk * n);
-        kept = 0;
-      }
-    }
-  }
-  if constexpr (Y1) {
-    if (lane < kept) fx_tile_row_store(kq, krow, rowexp, xexp1, P1 + chunk * n);
   }
 #pragma unroll
   for (int j = 0; j < E; ++j) acc[j].flush(dre[j], dim[j]);
@@ -447,29 +363,25 @@ __device__ __forceinline__ void gemv_fx_tile_body(const int4* __restrict__ C, co
   if (KC) __syncthreads();  // a persistent block's next tile reuses sm
 }
 
-// Entry point of the column-tiled integer sweeps.  With a non-finite entry in
-// A (rowexp[n]) or in a vector (meta[1]) the tile is summed from A on the
-// FP64 pipe instead.
-template <bool Y1>
-__global__ void __launch_bounds__(kBlock, 2) gemv_fx_tile(const double2* __restrict__ A, int64_t lda,
-                                                       const int4* __restrict__ C, const int* __restrict__ rowexp,
-                                                       int64_t n, int64_t rows_per_range,
-                                                       const double2* __restrict__ x1, const double2* __restrict__ x2,
-                                                       const int4* __restrict__ xd1, const int* __restrict__ meta1,
-                                                       const int4* __restrict__ xd2, const int* __restrict__ meta2,
-                                                       double2* __restrict__ P1, double2* __restrict__ P2,
-                                                       const SolveState* __restrict__ st, int* skip_rec = nullptr) {
+// Entry point of the integer A^H x sweep.  With a non-finite entry in A
+// (rowexp[n]) or in the vector (meta[1]) the tile is summed from A on the FP64
+// pipe instead.
+static __global__ void __launch_bounds__(kBlock, 2) gemv_fx_tile_h(const double2* __restrict__ A, int64_t lda,
+                                                         const int4* __restrict__ C, const int* __restrict__ rowexp,
+                                                         int64_t n, int64_t rows_per_range,
+                                                         const double2* __restrict__ x, const int4* __restrict__ xd,
+                                                         const int* __restrict__ meta, double2* __restrict__ P2,
+                                                         const SolveState* __restrict__ st, int* skip_rec = nullptr) {
   pdl_wait();
   if (sweep_skipped(st, skip_rec)) {
     pdl_launch();
     return;
   }
-  const bool bad = rowexp[n] != 0 || meta2[1] != 0 || (Y1 && meta1[1] != 0);
-  if (bad) {
-    gemv_tile_body<double, 1, 4, Y1, true>(A, lda, n, rows_per_range, x1, x2, P1, P2, blockIdx.x, blockIdx.y);
+  if (rowexp[n] != 0 || meta[1] != 0) {
+    gemv_tile_body<double, 1, 4, false, true>(A, lda, n, rows_per_range, nullptr, x, nullptr, P2, blockIdx.x,
+                                              blockIdx.y);
   } else {
-    gemv_fx_tile_body<Y1, false>(C, rowexp, n, rows_per_range, xd1, Y1 ? meta1[0] : 0, xd2, meta2[0], P1, P2,
-                                 blockIdx.x, blockIdx.y);
+    gemv_fx_tile_body<false>(C, rowexp, n, rows_per_range, xd, meta[0], P2, blockIdx.x, blockIdx.y);
   }
   pdl_launch();
 }

@@ -254,8 +254,7 @@ template <class R, int U> struct PkCtx {
           fx = !bad;
           if (fx)
             for (int64_t t = lb; t < nt; t += G)
-              gemv_fx_tile_body<false, true>(S.fxC, S.fxrow, S.n, S.rpr_c, nullptr, 0, S.xfx2, e2, nullptr, S.P2,
-                                             t % S.ncb, t / S.ncb, tsm);
+              gemv_fx_tile_body<true>(S.fxC, S.fxrow, S.n, S.rpr_c, S.xfx2, e2, S.P2, t % S.ncb, t / S.ncb, tsm);
         } else {
           fx = true;  // a barrier gave up: the caller's next barrier returns
         }
@@ -270,29 +269,21 @@ template <class R, int U> struct PkCtx {
     m.y = nullptr; m.P = S.P2; m.ld = S.n; m.nparts = S.ns_c;
     return m;
   }
-  // A x1 (ncb partials in P1) and A^H x2 (ns_b partials in P2) from one read of A
-  __device__ void sweep_both(const cx<R>* x1, const cx<R>* x2, MvOut<R>& o1, MvOut<R>& o2) {
-    const int64_t nt = (int64_t)S.ncb * S.ns_b;
-    bool fx = false;
+  // A x1 (ncb partials in P1) and A^H x2 (ns_b partials in P2) from one read
+  // of A; complex128 on the integer pipe: the two sweeps, A x1 into y1 (as
+  // the kernel loop does)
+  __device__ void sweep_both(const cx<R>* x1, const cx<R>* x2, cx<R>* y1, MvOut<R>& o1, MvOut<R>& o2) {
     if constexpr (sizeof(R) == 8) {
       if (S.fxC != nullptr) {
-        int e1 = 0, e2 = 0;
-        bool bad = false;
-        if (fx_split_group(x1, S.xfx, x2, S.xfx2, e1, e2, bad)) {
-          fx = !bad;
-          if (fx)
-            for (int64_t t = lb; t < nt; t += G)
-              gemv_fx_tile_body<true, true>(S.fxC, S.fxrow, S.n, S.rpr_b, S.xfx, e1, S.xfx2, e2, S.P1, S.P2,
-                                            t % S.ncb, t / S.ncb, tsm);
-        } else {
-          fx = true;
-        }
+        o1 = sweep_n(x1, y1);
+        o2 = sweep_c(x2);
+        return;
       }
     }
-    if (!fx)
-      for (int64_t t = lb; t < nt; t += G)
-        gemv_tile_body<R, U, 4, true, true, true>(S.A, S.lda, S.n, S.rpr_b, x1, x2, S.P1, S.P2, t % S.ncb,
-                                                  t / S.ncb, tsm);
+    const int64_t nt = (int64_t)S.ncb * S.ns_b;
+    for (int64_t t = lb; t < nt; t += G)
+      gemv_tile_body<R, U, 4, true, true, true>(S.A, S.lda, S.n, S.rpr_b, x1, x2, S.P1, S.P2, t % S.ncb, t / S.ncb,
+                                                tsm);
     count_sweep();
     o1.y = nullptr; o1.P = S.P1; o1.ld = S.n; o1.nparts = S.ncb;
     o2.y = nullptr; o2.P = S.P2; o2.ld = S.n; o2.nparts = S.ns_b;
@@ -418,7 +409,7 @@ template <class R, int U, int method> __device__ void pk_run_method(PkCtx<R, U>&
       { QPQ<R> a; a.n = n; a.v = v; a.w = wv; a.p = pv; a.q = q; c.phase(a); }
       if (!c.sync()) return;
       MvOut<R> m1, m2;
-      c.sweep_both(pv, q, m1, m2);
+      c.sweep_both(pv, q, pt, m1, m2);
       if (!c.sync()) return;
       { QEps<R> b; b.n = n; b.pt = pt; b.u = u; b.q = q; b.mv1 = m1; b.mv2 = m2; c.phase(b); }
       if (!c.sync()) return;

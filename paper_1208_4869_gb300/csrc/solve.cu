@@ -441,9 +441,8 @@ template <class R> struct Runner {
       // the integer-pipe sweep: the row-scaled vector's digits, then the tiles
       const int* rowexp = fx_rowexp();
       launch(fx_split_vector<1024, true>, dim3(1), dim3(1024), x, n, w.xfx2, w.xmeta2, cst, rowexp);
-      launch(gemv_fx_tile<false>, grid, dim3(kBlock), A, lda, C, rowexp, n, rpr, static_cast<const cx<R>*>(nullptr),
-             x, static_cast<const int4*>(nullptr), static_cast<const int*>(nullptr), static_cast<const int4*>(w.xfx2),
-             static_cast<const int*>(w.xmeta2), static_cast<cx<R>*>(nullptr), P2, cst, rec);
+      launch(gemv_fx_tile_h, grid, dim3(kBlock), A, lda, C, rowexp, n, rpr, x, static_cast<const int4*>(w.xfx2),
+             static_cast<const int*>(w.xmeta2), P2, cst, rec);
     } else {
       launch(gemv_tile_h<R, 1, Dense<R>::E>, grid, dim3(kBlock), A, lda, n, rpr, x, P2, cst, rec);
     }
@@ -452,10 +451,12 @@ template <class R> struct Runner {
     return m;
   }
   // A x1 and A^H x2: dense operators from one sweep (ncb partials in P1,
-  // nsplit in P2); others by two applications into y1, y2.
+  // nsplit in P2); others, and complex128 operators on the integer pipe
+  // (whose two sweeps run faster than one fused one), by two applications
+  // into y1, y2.
   void apply_both(const cx<R>* x1, const cx<R>* x2, cx<R>* y1, cx<R>* y2, MvOut<R>& o1, MvOut<R>& o2,
                   const SolveState* st) {
-    if (op->kind != CCG_OPK_DENSE) {
+    if (op->kind != CCG_OPK_DENSE || fx_digits() != nullptr) {
       o1 = apply_n(x1, y1, st);
       o2 = apply_c(x2, y2, st);
       return;
@@ -474,14 +475,6 @@ template <class R> struct Runner {
         launch(gemv_tile<R, 2, Dense<R>::E, true, true>, grid, dim3(kBlock), A, lda, n, rpr, x1, x2, P1, P2, cst, rec);
       else
         launch(gemv_tile<R, 1, Dense<R>::E, true, true>, grid, dim3(kBlock), A, lda, n, rpr, x1, x2, P1, P2, cst, rec);
-    } else if (const int4* C = fx_digits()) {
-      // the integer-pipe sweep: the digits of x1 and of the row-scaled x2 in
-      // one launch, then the tiles
-      const int* rowexp = fx_rowexp();
-      launch(fx_split_pair<1024>, dim3(2), dim3(1024), x1, w.xfx, w.xmeta, x2, w.xfx2, w.xmeta2, n, rowexp, cst);
-      launch(gemv_fx_tile<true>, grid, dim3(kBlock), A, lda, C, rowexp, n, rpr, x1, x2,
-             static_cast<const int4*>(w.xfx), static_cast<const int*>(w.xmeta), static_cast<const int4*>(w.xfx2),
-             static_cast<const int*>(w.xmeta2), P1, P2, cst, rec);
     } else {
       launch(gemv_tile<R, 1, Dense<R>::E, true, true>, grid, dim3(kBlock), A, lda, n, rpr, x1, x2, P1, P2, cst, rec);
     }

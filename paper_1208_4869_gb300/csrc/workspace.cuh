@@ -37,8 +37,8 @@ constexpr int kFxSplit = 2;
 
 // Launch geometry of the dense sweeps for one operator.
 // Resident blocks per SM of the column-tiled sweep (A^H x alone, or A x1 with
-// A^H x2), from the occupancy calculator; for complex128 that of the
-// integer-pipe sweeps (the default; the FP64-pipe fallback runs the same
+// A^H x2), from the occupancy calculator; for complex128 A^H x that of the
+// integer-pipe sweep (the default; the FP64-pipe fallback runs the same
 // tiles).
 template <class R> static int tile_occupancy(int unit, bool both) {
   static int cache[2][2] = {{0, 0}, {0, 0}};
@@ -49,7 +49,7 @@ template <class R> static int tile_occupancy(int unit, bool both) {
       if (unit == 2) fn = both ? (const void*)gemv_tile<R, 2, 4, true, true> : (const void*)gemv_tile_h<R, 2, 4>;
       else fn = both ? (const void*)gemv_tile<R, 1, 4, true, true> : (const void*)gemv_tile_h<R, 1, 4>;
     } else {
-      fn = both ? (const void*)gemv_fx_tile<true> : (const void*)gemv_fx_tile<false>;
+      fn = both ? (const void*)gemv_tile<R, 1, 4, true, true> : (const void*)gemv_fx_tile_h;
     }
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kBlock, 0) != cudaSuccess) {

@@ -215,9 +215,9 @@ def test_non_finite_takes_the_fp64_pipe(ccg):
 
 
 def test_fixed_point_solves_match_oracle(ccg):
-    """complex128 solves on the fixed-point sweeps (rows, A^H x, and A p with
-    A^H q from one read for QMR and BiCG): whole solves against the oracle (x
-    to 1e-9) with the integer and the FP64 sweeps."""
+    """complex128 solves on the fixed-point sweeps (A x and A^H x; QMR and
+    BiCG take their A p and A^H q from the two): whole solves against the
+    oracle (x to 1e-9) with the integer and the FP64 sweeps."""
     n = 1000
     A, y = W.dense_system(n, 3.0, 21)
     for m in ("bicgstab", "cgnr", "qmr", "bicg", "cgne"):
