@@ -363,25 +363,122 @@ __device__ __forceinline__ void gemv_fx_tile_body(const int4* __restrict__ C, co
   if (KC) __syncthreads();  // a persistent block's next tile reuses sm
 }
 
-// Entry point of the integer A^H x sweep.  With a non-finite entry in A
-// (rowexp[n]) or in the vector (meta[1]) the tile is summed from A on the FP64
-// pipe instead.
-static __global__ void __launch_bounds__(kBlock, 2) gemv_fx_tile_h(const double2* __restrict__ A, int64_t lda,
-                                                         const int4* __restrict__ C, const int* __restrict__ rowexp,
-                                                         int64_t n, int64_t rows_per_range,
-                                                         const double2* __restrict__ x, const int4* __restrict__ xd,
-                                                         const int* __restrict__ meta, double2* __restrict__ P2,
-                                                         const SolveState* __restrict__ st, int* skip_rec = nullptr) {
+// The same sweep with the digit rows staged through shared memory: each
+// warp keeps kFxStages rows of its tile in flight with cp.async (16-byte
+// copies that bypass L1), so the loads no longer wait on registers: the
+// register-held form (gemv_fx_tile_body) stopped at 2 blocks per SM with
+// 8 loads in flight per lane.  A lane copies and later reads only its own 4
+// columns of each row, so no synchronisation within the warp is needed.
+// Rows, flush points and the final sums are those of gemv_fx_tile_body, so
+// the results are bitwise the same.  smem: kFxStages x 128 int4 per warp.
+constexpr int kFxStages = 4;
+constexpr size_t kFxTileSmem = (size_t)kWarps * kFxStages * 128 * sizeof(int4);
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void gemv_fx_tile_staged(const int4* __restrict__ C, const int* __restrict__ rowexp,
+                                                    int64_t n, int64_t rows_per_range, const int4* __restrict__ xd2,
+                                                    int xexp2, double2* P2, int64_t chunk, int64_t range,
+                                                    int4* stage) {
+  constexpr int E = 4, CBU = 32 * E;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t col0 = chunk * CBU;
+  const int64_t r0 = range * rows_per_range;
+  const int64_t r1 = r0 + rows_per_range < n ? r0 + rows_per_range : n;
+  const int fm = max(rowexp[n + 1], 1);
+  int4* ws = stage + (size_t)warp * kFxStages * CBU;
+  // row k of this warp (r0 + warp + k kWarps) into ring slot k mod kFxStages;
+  // columns beyond n are filled with zeros (source address kept in the row)
+  auto issue = [&](int64_t k) {
+    const int64_t r = r0 + warp + k * kWarps;
+    if (r < r1) {
+      const int4* src = C + r * n;
+      int4* dst = ws + (int)(k % kFxStages) * CBU;
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        const int64_t u = col0 + lane + 32 * j;
+        cp_async16(dst + lane + 32 * j, src + (u < n ? u : 0), u < n ? 16 : 0);
+      }
+    }
+    cp_async_commit();
+  };
+  FxAccH acc[E];
+  double dre[E], dim[E];
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    acc[j].zero();
+    dre[j] = 0.0;
+    dim[j] = 0.0;
+  }
+#pragma unroll
+  for (int k = 0; k < kFxStages - 1; ++k) issue(k);
+  int cnt = 0;
+  int64_t k = 0;
+  for (int64_t r = r0 + warp; r < r1; r += kWarps, ++k) {
+    issue(k + kFxStages - 1);
+    cp_async_wait<kFxStages - 1>();
+    const int4* row = ws + (int)(k % kFxStages) * CBU;
+    const int4 xr = __ldg(xd2 + r);
+#pragma unroll
+    for (int j = 0; j < E; ++j) acc[j].mac(row[lane + 32 * j], xr);
+    if (++cnt >= 256) {
+#pragma unroll
+      for (int j = 0; j < E; ++j) acc[j].flush(dre[j], dim[j]);
+      cnt = 0;
+    }
+  }
+  cp_async_wait<0>();
+#pragma unroll
+  for (int j = 0; j < E; ++j) acc[j].flush(dre[j], dim[j]);
+  // the warps' column sums, each through its own warp's ring (16-byte
+  // slots, like the int4 rows)
+  double2* sm = reinterpret_cast<double2*>(stage);
+  constexpr int WS = kFxStages * CBU;
+#pragma unroll
+  for (int j = 0; j < E; ++j) sm[warp * WS + lane + 32 * j] = make_double2(dre[j], dim[j]);
+  __syncthreads();
+  const int e2 = fm + max(xexp2, 1) - 2122;  // units 2^(Fm + Fx' - 78)
+  for (int t = threadIdx.x; t < CBU; t += kBlock) {
+    const int64_t col = col0 + t;
+    if (col < n) {
+      double2 v = sm[t];
+#pragma unroll
+      for (int w = 1; w < kWarps; ++w) v = cadd(v, sm[w * WS + t]);
+      P2[range * n + col] = make_double2(ldexp(v.x, e2), ldexp(v.y, e2));
+    }
+  }
+}
+
+// Entry point of the integer A^H x sweep (kFxTileSmem bytes of dynamic
+// shared memory).  With a non-finite entry in A (rowexp[n]) or in the vector
+// (meta[1]) the tile is summed from A on the FP64 pipe instead.
+static __global__ void __launch_bounds__(kBlock, 3) gemv_fx_tile_h(const double2* __restrict__ A, int64_t lda,
+                                                                const int4* __restrict__ C,
+                                                                const int* __restrict__ rowexp, int64_t n,
+                                                                int64_t rows_per_range,
+                                                                const double2* __restrict__ x,
+                                                                const int4* __restrict__ xd,
+                                                                const int* __restrict__ meta, double2* __restrict__ P2,
+                                                                const SolveState* __restrict__ st,
+                                                                int* skip_rec = nullptr) {
+  extern __shared__ int4 fx_stage[];
   pdl_wait();
   if (sweep_skipped(st, skip_rec)) {
     pdl_launch();
     return;
   }
   if (rowexp[n] != 0 || meta[1] != 0) {
-    gemv_tile_body<double, 1, 4, false, true>(A, lda, n, rows_per_range, nullptr, x, nullptr, P2, blockIdx.x,
-                                              blockIdx.y);
+    gemv_tile_body<double, 1, 4, false, true, true>(A, lda, n, rows_per_range, nullptr, x, nullptr, P2, blockIdx.x,
+                                                    blockIdx.y, reinterpret_cast<double2*>(fx_stage));
   } else {
-    gemv_fx_tile_body<false>(C, rowexp, n, rows_per_range, xd, meta[0], P2, blockIdx.x, blockIdx.y);
+    gemv_fx_tile_staged(C, rowexp, n, rows_per_range, xd, meta[0], P2, blockIdx.x, blockIdx.y, fx_stage);
   }
   pdl_launch();
 }

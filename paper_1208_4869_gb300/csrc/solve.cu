@@ -329,11 +329,15 @@ template <class R> struct Runner {
   // (each kernel waits for its predecessor inside, pdl_wait).
   template <class... KArgs, class... Args>
   void launch(void (*kern)(KArgs...), dim3 grid, dim3 block, Args... args) {
+    launch_smem(kern, grid, block, 0, args...);
+  }
+  template <class... KArgs, class... Args>
+  void launch_smem(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, Args... args) {
     if (h->pdl) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = grid;
       cfg.blockDim = block;
-      cfg.dynamicSmemBytes = 0;
+      cfg.dynamicSmemBytes = smem;
       cfg.stream = s;
       cudaLaunchAttribute attr[1];
       attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -342,7 +346,7 @@ template <class R> struct Runner {
       cfg.numAttrs = 1;
       cudaLaunchKernelEx(&cfg, kern, args...);
     } else {
-      kern<<<grid, block, 0, s>>>(args...);
+      kern<<<grid, block, smem, s>>>(args...);
     }
     ++h->launches;
   }
@@ -441,8 +445,12 @@ template <class R> struct Runner {
       // the integer-pipe sweep: the row-scaled vector's digits, then the tiles
       const int* rowexp = fx_rowexp();
       launch(fx_split_vector<1024, true>, dim3(1), dim3(1024), x, n, w.xfx2, w.xmeta2, cst, rowexp);
-      launch(gemv_fx_tile_h, grid, dim3(kBlock), A, lda, C, rowexp, n, rpr, x, static_cast<const int4*>(w.xfx2),
-             static_cast<const int*>(w.xmeta2), P2, cst, rec);
+      static const bool opted =
+          cudaFuncSetAttribute((const void*)gemv_fx_tile_h, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kFxTileSmem) == cudaSuccess;
+      (void)opted;
+      launch_smem(gemv_fx_tile_h, grid, dim3(kBlock), kFxTileSmem, A, lda, C, rowexp, n, rpr, x,
+                  static_cast<const int4*>(w.xfx2), static_cast<const int*>(w.xmeta2), P2, cst, rec);
     } else {
       launch(gemv_tile_h<R, 1, Dense<R>::E>, grid, dim3(kBlock), A, lda, n, rpr, x, P2, cst, rec);
     }

@@ -51,8 +51,11 @@ template <class R> static int tile_occupancy(int unit, bool both) {
     } else {
       fn = both ? (const void*)gemv_tile<R, 1, 4, true, true> : (const void*)gemv_fx_tile_h;
     }
+    // the integer A^H sweep stages its rows in dynamic shared memory
+    const size_t dyn = (sizeof(R) == 8 && !both) ? kFxTileSmem : 0;
+    if (dyn > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kBlock, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kBlock, dyn) != cudaSuccess) {
       cudaGetLastError();
       occ = 2;
     }
