@@ -230,3 +230,32 @@ def test_fixed_point_solves_match_oracle(ccg):
             st, info, hist = h.solve(m, op, torch.from_numpy(y).cuda(), xd, tol=1e-10, maxit=300)
             assert st == 0 and info["iters"] == ref.iters and info["true_relres"] <= 1e-10
             assert np.linalg.norm(xd.cpu().numpy() - ref.x) <= 1e-9 * np.linalg.norm(ref.x), (m, fx)
+
+
+@pytest.mark.parametrize("n", [33, 1000])
+def test_fixed_point_padded_rows(ccg, n):
+    """An operator whose rows are padded (lda = n + 5): the digits are made
+    from the strided rows, so A x and A^H x are bitwise those of the
+    contiguous matrix, and a CGNR solve (both sweeps) matches the oracle."""
+    A, y = W.dense_system(n, 3.0, n + 7)
+    x = W.random_vector(n, n + 8)
+    store = np.zeros((n, n + 5), dtype=np.complex128)
+    store[:, :n] = A
+    h = ccg.Handle()
+    Ad = torch.from_numpy(A).cuda()
+    Sd = torch.from_numpy(store).cuda()
+    op_c = h.op_dense(Ad)
+    op_p = h.op_dense(Sd[:, :n])
+    xd = torch.from_numpy(x).cuda()
+    for trans in (False, True):
+        yc = torch.empty(n, dtype=torch.complex128, device="cuda")
+        yp = torch.empty_like(yc)
+        h.matvec(op_c, xd, yc, trans=trans)
+        h.matvec(op_p, xd, yp, trans=trans)
+        torch.cuda.synchronize()
+        assert torch.equal(yc, yp), trans
+    ref = O.solve(O.DenseOp(A), "cgnr", y, tol=1e-10, maxit=300)
+    xs = torch.zeros(n, dtype=torch.complex128, device="cuda")
+    st, info, _ = h.solve("cgnr", op_p, torch.from_numpy(y).cuda(), xs, tol=1e-10, maxit=300)
+    assert st == 0 and info["iters"] == ref.iters
+    assert np.linalg.norm(xs.cpu().numpy() - ref.x) <= 1e-9 * np.linalg.norm(ref.x)
