@@ -100,6 +100,8 @@ struct ccg_handle {
   int bicgstab_l = 2;   // degree l of BiCGstab(l)
   void* tc_buf = nullptr;
   size_t tc_bytes = 0;
+  size_t tc_flag_bytes = 0;   // bytes of the stream-K flags zeroed since the buffer was made
+  unsigned tc_epoch = 0;      // launches of the split-bf16 product (the flags' epoch)
   // exact tensor-core block products (integer digit slices; FP64-accurate
   // for complex128, FP32-accurate for complex64): enabled flag, staging for
   // the block's slices and the pipeline's error flag (first 256 bytes)

@@ -14,14 +14,27 @@
 //   T = 2: A0 X0 + A0 X1 + A1 X0                    (~2^-17 relative)
 //   T = 3: A0 X0 + A0 X1 + A1 X0 + A0 X2 + A1 X1 + A2 X0   (~2^-24, fp32 level)
 //
-// Kernel: one CTA per 128 x BN output tile (BN = 256 for T = 2, 128 for
-// T = 3), 4 warps.  Lane 0 of warp 0 feeds a 2-stage ring of shared-memory
-// tiles (T tiles of A, 128 x 64 bf16, and T of X, BN x 64; 128-byte swizzle)
-// with cp.async.bulk.tensor and mbarrier transaction counts; lane 0 of warp 1
-// issues the tcgen05.mma of every product and K=16 step of a stage and
-// releases the stage with tcgen05.commit; after the last stage all four warps
-// read their 32 rows of the fp32 accumulator with tcgen05.ld and store them.  Every mbarrier wait
-// gives up after about two seconds, records an error flag and lets the CTA
+// Kernel: output tiles of 128 x BN (BN = 256 for T = 2, 128 for T = 3),
+// 6 warps.  Lane 0 of warp 0 feeds a 2-stage ring of shared-memory tiles (T
+// tiles of A, 128 x 64 bf16, and T of X, BN x 64; 128-byte swizzle) with
+// cp.async.bulk.tensor and mbarrier transaction counts; lane 0 of warp 1
+// issues the tcgen05.mma of every product and K = 16 step of a stage,
+// releases the stage with tcgen05.commit and alternates between two
+// accumulators in tensor memory; warps 2-5 read a finished accumulator with
+// tcgen05.ld while the next one fills.
+//
+// Schedule (stream-K): a row unit is one K block (64) of one row block; the
+// R = row blocks x K blocks units, in row-block order, are cut into P equal
+// ranges (+-1), P = SMs / column tiles, and range p goes to the ncol CTAs
+// p * ncol + c, one per column tile c, which therefore read the same A rows
+// at the same time.  Every SM gets the same work whatever the number of
+// tiles (at n = 8192, k = 256: 128 tiles, 152 SMs).  A range cuts at most its
+// last row block short; that piece is computed first and its fp32 partial
+// tile published (per-warp flags carrying the launch's epoch), the pieces
+// that end a tile last: the CTA holding a tile's last K block adds the
+// partials of the lower ranges, in order of K, to its own.  Waits go only to
+// lower-numbered CTAs, which start no later, and are bounded like every
+// mbarrier wait: a wait that gives up records an error flag and lets the CTA
 // finish (tensor memory is always freed), so a fault in the pipeline cannot
 // hang the GPU.
 #include <cuda.h>
@@ -29,6 +42,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <string>
 
@@ -39,14 +53,15 @@
 namespace ccg {
 namespace tc {
 
-constexpr int BM = 128, BK = 64, STAGES = 2, THREADS = 128;
+constexpr int BM = 128, BK = 64, STAGES = 2, THREADS = 192;
+constexpr int MIN_UNITS = 16;  // K blocks per range at least (fewer ranges on small products)
 template <int T> struct Cfg {
   static constexpr int BN = T == 2 ? 256 : 128;
   static constexpr int A_TILE = BM * BK * 2;         // bytes of one bf16 A tile
   static constexpr int B_TILE = BN * BK * 2;         // bytes of one bf16 X tile
   static constexpr int STAGE_BYTES = T * (A_TILE + B_TILE);
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-  static constexpr uint32_t TMEM_COLS = BN;
+  static constexpr uint32_t TMEM_COLS = 2 * BN;      // two accumulators
   static constexpr int NPROD = T == 2 ? 3 : 6;       // products of order below T
 };
 // (term of A, term of X) of each product
@@ -58,34 +73,90 @@ struct TcMaps {
   CUtensorMap x[3];
 };
 
+// The stream-K cut: ranges [begin(p), begin(p + 1)) of the R row units.
+struct Split {
+  int nrb, nkb, ncol, P;
+  __host__ __device__ int64_t begin(int p) const { return (int64_t)nrb * nkb * p / P; }
+};
+
+// Segment si of range [u0, u1): its row block and K blocks [kb0, kb1).  The
+// last row block (the only one a range can cut short) comes first.
+struct Seg {
+  int r, kb0, kb1;
+};
+__device__ __forceinline__ Seg segment(const Split& sp, int64_t u0, int64_t u1, int si) {
+  const int rlo = (int)(u0 / sp.nkb), rhi = (int)((u1 - 1) / sp.nkb);
+  const int r = si == 0 ? rhi : rlo + si - 1;
+  const int64_t base = (int64_t)r * sp.nkb;
+  Seg g;
+  g.r = r;
+  g.kb0 = (int)((u0 > base ? u0 : base) - base);
+  g.kb1 = (int)((u1 < base + sp.nkb ? u1 : base + sp.nkb) - base);
+  return g;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Bounded wait for a flag to carry this launch's epoch (false and the error
+// flag set when it runs out or another thread gave up).
+__device__ __forceinline__ bool flag_wait(const unsigned* f, unsigned epoch, volatile int* err, long long limit) {
+  const long long t0 = clock64();
+  while (ld_acquire(f) != epoch) {
+    if (*err) return false;
+    if (clock64() - t0 > limit) {
+      *err = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
 // C (M x N fp32, leading dimension ldc) = sum of the split products.
+// work: one BM x BN fp32 partial tile per CTA (column-major); flags: 4 per
+// CTA (one per epilogue warp), holding the epoch of the launch that last
+// published that warp's rows.
 template <int T>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_bf16_split(const __grid_constant__ TcMaps maps, float* __restrict__ C, int M, int N, int K, int64_t ldc,
-                    int* err, const int* skip, int* skip_rec,
-                    long long wait_limit, int withhold) {
+                    Split sp, float* __restrict__ work, unsigned* flags, unsigned epoch, int* err,
+                    const int* skip, int* skip_rec, long long wait_limit, int withhold) {
   using G = Cfg<T>;
+  constexpr int BN = G::BN;
   if (skip != nullptr && *skip) {  // every column has stopped
-    if (skip_rec != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *skip_rec = 1;
+    if (skip_rec != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *skip_rec = 1;
     return;
   }
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * G::STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* accf = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 1);
+  uint64_t* tfull = empty + STAGES;  // accumulator b holds a finished segment
+  uint64_t* tempty = tfull + 2;      // the epilogue has read accumulator b
+  uint64_t* done = tempty + 2;       // every MMA has completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* verr = err;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * G::BN;
-  const int nkb = (K + BK - 1) / BK;
+  const int cta = blockIdx.x, p = cta / sp.ncol, ct = cta - p * sp.ncol;
+  const int n0 = ct * BN;
+  const int64_t u0 = sp.begin(p), u1 = sp.begin(p + 1);
+  const int nseg = (int)((u1 - 1) / sp.nkb - u0 / sp.nkb) + 1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accf, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -102,68 +173,135 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   int issued = 0;
   if (warp == 0 && lane == 0) {
-    // producer: stage s of block kb waits until the MMAs of block kb - STAGES released it
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % STAGES;
-      if (kb == withhold) break;  // test hook: this stage's copies are never issued
-      if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) & 1) ^ 1, verr, wait_limit)) break;
-      unsigned char* st = smem + s * G::STAGE_BYTES;
-      mbar_expect_tx(&full[s], G::STAGE_BYTES);
+    // producer: the g-th K block of this CTA uses stage g % STAGES, which
+    // the MMAs of K block g - STAGES released
+    int g = 0;
+    bool go = true;
+    for (int si = 0; si < nseg && go; ++si) {
+      const Seg sg = segment(sp, u0, u1, si);
+      const int m0 = sg.r * BM;
+      for (int kb = sg.kb0; kb < sg.kb1; ++kb, ++g) {
+        const int s = g % STAGES;
+        // (g == withhold: test hook, no copies from this K block on)
+        if (g == withhold || (g >= STAGES && !mbar_wait(&empty[s], ((g / STAGES) & 1) ^ 1, verr, wait_limit))) {
+          go = false;
+          break;
+        }
+        unsigned char* st = smem + s * G::STAGE_BYTES;
+        mbar_expect_tx(&full[s], G::STAGE_BYTES);
 #pragma unroll
-      for (int t = 0; t < T; ++t) {
-        tma_load_2d(st + t * G::A_TILE, &maps.a[t], &full[s], kb * BK, m0);
-        tma_load_2d(st + T * G::A_TILE + t * G::B_TILE, &maps.x[t], &full[s], kb * BK, n0);
+        for (int t = 0; t < T; ++t) {
+          tma_load_2d(st + t * G::A_TILE, &maps.a[t], &full[s], kb * BK, m0);
+          tma_load_2d(st + T * G::A_TILE + t * G::B_TILE, &maps.x[t], &full[s], kb * BK, n0);
+        }
+        issued = g + 1;
       }
-      issued = kb + 1;
     }
   } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    constexpr uint32_t idesc = idesc_bf16(BM, G::BN);
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % STAGES;
-      if (!mbar_wait(&full[s], (kb / STAGES) & 1, verr, wait_limit)) break;
+    // MMA issuer: segment si accumulates into buffer si & 1
+    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    int g = 0;
+    bool ok = true;
+    for (int si = 0; si < nseg && ok; ++si) {
+      const Seg sg = segment(sp, u0, u1, si);
+      const int b = si & 1;
+      if (si >= 2 && !mbar_wait(&tempty[b], ((si >> 1) - 1) & 1, verr, wait_limit)) break;
+      const uint32_t acc = tmem + (uint32_t)(b * BN);
+      for (int kb = sg.kb0; kb < sg.kb1; ++kb, ++g) {
+        const int s = g % STAGES;
+        if (!mbar_wait(&full[s], (g / STAGES) & 1, verr, wait_limit)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t base = smem_u32(smem + s * G::STAGE_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint32_t off = kk * 32;  // 16 bf16 along K
+#pragma unroll
+          for (int q = 0; q < G::NPROD; ++q) {
+            const uint64_t a = sdesc_k128(base + kProdA[q] * G::A_TILE + off);
+            const uint64_t bd = sdesc_k128(base + T * G::A_TILE + kProdX[q] * G::B_TILE + off);
+            umma(acc, a, bd, idesc, (kb != sg.kb0 || kk != 0 || q != 0) ? 1u : 0u);
+          }
+        }
+        umma_commit(&empty[s]);
+      }
+      umma_commit(&tfull[b]);  // also after a failure: it tracks the MMAs issued
+    }
+    umma_commit(done);
+  } else if (warp >= 2) {
+    // epilogue: warp w reads tensor-memory lanes (rows) 32 (w % 4) .. + 31
+    const int q = warp & 3, rt = q * 32 + lane;
+    for (int si = 0; si < nseg; ++si) {
+      const Seg sg = segment(sp, u0, u1, si);
+      const int b = si & 1;
+      if (!__all_sync(0xffffffffu, mbar_wait(&tfull[b], (si >> 1) & 1, verr, wait_limit))) break;
       fence_after();
-      const uint32_t base = smem_u32(smem + s * G::STAGE_BYTES);
+      const bool last = sg.kb1 == sp.nkb;  // this CTA finishes the tile
+      // the lower ranges holding K blocks of this tile: pf .. p - 1
+      int pf = p;
+      if (last && sg.kb0 > 0) {
+        const int64_t rs = (int64_t)sg.r * sp.nkb;
+        pf = p - 1;
+        while (sp.begin(pf) > rs) --pf;
+        bool ok = true;
+        for (int pp = pf; pp < p && ok; ++pp) ok = flag_wait(&flags[(pp * sp.ncol + ct) * 4 + q], epoch, verr, wait_limit);
+        if (!__all_sync(0xffffffffu, ok)) break;
+      }
+      if (__shfl_sync(0xffffffffu, *verr, 0) != 0) break;
+      const int row = sg.r * BM + rt;
+#pragma unroll 1
+      for (int h = 0; h < BN / 32; ++h) {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + 32 * h), r);
+        if (h == BN / 32 - 1) {  // the accumulator is free once its last columns are in registers
+          fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tempty[b]);
+        }
+        if (!last) {
+          float* w = work + (size_t)cta * BM * BN + (size_t)(32 * h) * BM + rt;
 #pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk) {
-        const uint32_t off = kk * 32;  // 16 bf16 along K
+          for (int j = 0; j < 32; ++j) w[(size_t)j * BM] = __uint_as_float(r[j]);
+        } else {
+          float v[32];
+          if (pf < p) {
+            const float* w = work + (size_t)(pf * sp.ncol + ct) * BM * BN + (size_t)(32 * h) * BM + rt;
 #pragma unroll
-        for (int q = 0; q < G::NPROD; ++q) {
-          const uint64_t a = sdesc_k128(base + kProdA[q] * G::A_TILE + off);
-          const uint64_t b = sdesc_k128(base + T * G::A_TILE + kProdX[q] * G::B_TILE + off);
-          umma(tmem, a, b, idesc, (kb | kk | q) != 0 ? 1u : 0u);
+            for (int j = 0; j < 32; ++j) v[j] = __ldcg(w + (size_t)j * BM);
+            for (int pp = pf + 1; pp < p; ++pp) {
+              w = work + (size_t)(pp * sp.ncol + ct) * BM * BN + (size_t)(32 * h) * BM + rt;
+#pragma unroll
+              for (int j = 0; j < 32; ++j) v[j] += __ldcg(w + (size_t)j * BM);
+            }
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] += __uint_as_float(r[j]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+          }
+          if (row < M) {
+            float* dst = C + (int64_t)row * ldc + n0 + 32 * h;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (n0 + 32 * h + j < N) dst[j] = v[j];
+          }
         }
       }
-      umma_commit(&empty[s]);
-    }
-    umma_commit(accf);  // always: it also tracks every MMA issued before a failure
-  }
-  __syncwarp();
-
-  // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w + 31
-  mbar_drain(accf, 0, verr, wait_limit);
-  fence_after();
-  __syncwarp();
-  // tcgen05.ld is warp-collective: take lane 0's reading of the flag
-  const bool ready = __shfl_sync(0xffffffffu, *verr, 0) == 0;
-  const int row = m0 + warp * 32 + lane;
-  if (ready) {
-#pragma unroll 1
-    for (int c0 = 0; c0 < G::BN; c0 += 32) {
-      uint32_t r[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-      if (row < M) {
-        float* dst = C + (int64_t)row * ldc + n0 + c0;
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (n0 + c0 + j < N) dst[j] = __uint_as_float(r[j]);
+      if (!last) {  // publish this warp's rows of the partial tile
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) st_release(&flags[cta * 4 + q], epoch);
       }
     }
   }
+  __syncwarp();
+  // teardown: no MMA or copy of this CTA may be in flight when it frees its memory
+  if (threadIdx.x == 32) mbar_drain(done, 0, verr, wait_limit);
   if (warp == 0 && lane == 0) {
-    // drain the copies this CTA issued (all consumed unless the pipeline failed)
-    for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
-      mbar_drain(&full[kb % STAGES], (kb / STAGES) & 1, verr, wait_limit);
+    for (int g = issued > STAGES ? issued - STAGES : 0; g < issued; ++g)
+      mbar_drain(&full[g % STAGES], (g / STAGES) & 1, verr, wait_limit);
   }
   fence_before();
   __syncthreads();
@@ -262,26 +400,47 @@ static int tc_product_t(ccg_handle* h, ccg_operator* op, const float2* X, float2
     op->tc_terms = T;
     op->tc_ready = true;
   }
-  // split X into the handle's bf16 staging (T terms of 2k x 2n)
+  // the handle's staging: error flag (256 B), the ranges' flags (4 per CTA),
+  // the T bf16 terms of Xh^T (2k x 2n each), one partial tile per CTA
+  const int Nr = 2 * k;
+  tc::Split sp;
+  sp.nrb = (int)((n + tc::BM - 1) / tc::BM);
+  sp.nkb = (int)((2 * n + tc::BK - 1) / tc::BK);
+  sp.ncol = (Nr + G::BN - 1) / G::BN;
+  const int64_t units = (int64_t)sp.nrb * sp.nkb;
+  sp.P = (int)std::min<int64_t>(std::max(1, h->num_sms / sp.ncol), std::max<int64_t>(1, units / tc::MIN_UNITS));
+  const int ctas = sp.P * sp.ncol;
+  const size_t flag_bytes = ((size_t)ctas * 4 * sizeof(unsigned) + 255) / 256 * 256;
   const size_t xb = (size_t)2 * k * 2 * n * sizeof(__nv_bfloat16);
-  if (h->tc_bytes < T * xb + 256) {
+  const size_t xoff = 256 + flag_bytes;
+  const size_t woff = (xoff + T * xb + 255) / 256 * 256;
+  const size_t need = woff + (size_t)ctas * tc::BM * G::BN * sizeof(float);
+  if (h->tc_bytes < need) {
     if (h->tc_buf) {
       cudaStreamSynchronize(s);
       cudaFree(h->tc_buf);
       h->tc_buf = nullptr;
       h->tc_bytes = 0;
     }
-    if (cudaMalloc(&h->tc_buf, T * xb + 256) != cudaSuccess) {
+    if (cudaMalloc(&h->tc_buf, need) != cudaSuccess) {
       cudaGetLastError();
       h->tc_buf = nullptr;
       set_error("tensor-core staging allocation failed");
       return CCG_ERR_NOMEM;
     }
-    h->tc_bytes = T * xb + 256;
-    cudaMemsetAsync(h->tc_buf, 0, 256, s);
+    h->tc_bytes = need;
+    h->tc_flag_bytes = 0;
   }
-  int* err = static_cast<int*>(h->tc_buf);
-  __nv_bfloat16* xs = reinterpret_cast<__nv_bfloat16*>(static_cast<char*>(h->tc_buf) + 256);
+  char* buf = static_cast<char*>(h->tc_buf);
+  if (h->tc_flag_bytes < flag_bytes) {  // flags never written yet hold no epoch (0)
+    cudaMemsetAsync(buf, 0, 256 + flag_bytes, s);
+    h->tc_flag_bytes = flag_bytes;
+  }
+  if (++h->tc_epoch == 0) h->tc_epoch = 1;
+  int* err = reinterpret_cast<int*>(buf);
+  unsigned* flags = reinterpret_cast<unsigned*>(buf + 256);
+  __nv_bfloat16* xs = reinterpret_cast<__nv_bfloat16*>(buf + xoff);
+  float* work = reinterpret_cast<float*>(buf + woff);
   dim3 sg((unsigned)((n + 31) / 32), (unsigned)((k + 31) / 32));
   tc::split_block<T><<<sg, kBlock, 0, s>>>(X, n, k, xs);
   tc::TcMaps maps;
@@ -301,12 +460,9 @@ static int tc_product_t(ccg_handle* h, ccg_operator* op, const float2* X, float2
     set_error("tensor-core kernel: shared memory opt-in failed");
     return CCG_ERR_CUDA;
   }
-  const int Nr = 2 * k;
-  dim3 grid((unsigned)((Nr + G::BN - 1) / G::BN), (unsigned)((n + tc::BM - 1) / tc::BM));
-  tc::gemm_bf16_split<T><<<grid, tc::THREADS, G::SMEM_BYTES, s>>>(maps, reinterpret_cast<float*>(Y), (int)n, Nr,
-                                                                    (int)(2 * n), (int64_t)Nr, err, skip,
-                                                                    timing_rec(h), h->wait_limit,
-                                                                    h->test_withhold ? 0 : -1);
+  tc::gemm_bf16_split<T><<<ctas, tc::THREADS, G::SMEM_BYTES, s>>>(
+      maps, reinterpret_cast<float*>(Y), (int)n, Nr, (int)(2 * n), (int64_t)Nr, sp, work, flags, h->tc_epoch, err,
+      skip, timing_rec(h), h->wait_limit, h->test_withhold ? 0 : -1);
   h->launches += 2;
   return cudaGetLastError() == cudaSuccess ? CCG_OK : CCG_ERR_CUDA;
 }

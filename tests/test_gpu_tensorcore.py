@@ -86,6 +86,21 @@ def test_tensor_core_full_size(ccg):
         assert col.max() < tc_bound(8192), (terms, col.max())
 
 
+@pytest.mark.parametrize("n,k", [(2048, 256), (8192, 1), (4099, 200), (640, 24)])
+def test_tensor_core_stream_k(ccg, n, k):
+    """Shapes whose stream-K ranges cut tiles into two to four pieces (partial
+    tiles of lower ranges added by the range holding the tile's last K block)
+    or give one CTA several row blocks: every product within the bound, and
+    two runs bitwise equal (the partial tiles are added in a fixed order)."""
+    A, _ = W.dense_system(n, 1.0, n + k, dtype=np.complex64)
+    X = W.dense_rhs_block(n, k, seed=k + 3, dtype=np.complex64)
+    for terms in (2, 3):
+        a = product(ccg, 1, A, X, terms)
+        b = product(ccg, 1, A, X, terms)
+        assert err(a, A, X) < tc_bound(n), (terms, err(a, A, X))
+        assert np.array_equal(a, b)
+
+
 def test_complex128_block_product(ccg):
     n, k = 300, 17
     A, _ = W.dense_system(n, 1.0, 3)
