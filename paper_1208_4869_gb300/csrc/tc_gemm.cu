@@ -15,15 +15,15 @@
 //   T = 3: A0 X0 + A0 X1 + A1 X0 + A0 X2 + A1 X1 + A2 X0   (~2^-24, fp32 level)
 //
 // Kernel: output tiles of 128 x BN (BN = 256 for T = 2, 128 for T = 3),
-// 6 warps.  Lane 0 of warp 0 feeds a 2-stage ring of shared-memory tiles (T
-// tiles of A, 128 x 64 bf16, and T of X, BN x 64; 128-byte swizzle) with
+// 6 warps.  Lane 0 of warp 0 feeds a 4-stage ring of shared-memory tiles (T
+// tiles of A, 128 x 32 bf16, and T of X, BN x 32; 64-byte swizzle) with
 // cp.async.bulk.tensor and mbarrier transaction counts; lane 0 of warp 1
 // issues the tcgen05.mma of every product and K = 16 step of a stage,
 // releases the stage with tcgen05.commit and alternates between two
 // accumulators in tensor memory; warps 2-5 read a finished accumulator with
 // tcgen05.ld while the next one fills.
 //
-// Schedule (stream-K): a row unit is one K block (64) of one row block; the
+// Schedule (stream-K): a row unit is one K block (32) of one row block; the
 // R = row blocks x K blocks units, in row-block order, are cut into P equal
 // ranges (+-1), P = SMs / column tiles, and range p goes to the ncol CTAs
 // p * ncol + c, one per column tile c, which therefore read the same A rows
@@ -53,8 +53,8 @@
 namespace ccg {
 namespace tc {
 
-constexpr int BM = 128, BK = 64, STAGES = 2, THREADS = 192;
-constexpr int MIN_UNITS = 16;  // K blocks per range at least (fewer ranges on small products)
+constexpr int BM = 128, BK = 32, STAGES = 4, THREADS = 192;
+constexpr int MIN_UNITS = 32;  // K blocks per range at least (fewer ranges on small products)
 template <int T> struct Cfg {
   static constexpr int BN = T == 2 ? 256 : 128;
   static constexpr int A_TILE = BM * BK * 2;         // bytes of one bf16 A tile
@@ -220,8 +220,8 @@ __global__ void __launch_bounds__(THREADS, 1)
           const uint32_t off = kk * 32;  // 16 bf16 along K
 #pragma unroll
           for (int q = 0; q < G::NPROD; ++q) {
-            const uint64_t a = sdesc_k128(base + kProdA[q] * G::A_TILE + off);
-            const uint64_t bd = sdesc_k128(base + T * G::A_TILE + kProdX[q] * G::B_TILE + off);
+            const uint64_t a = sdesc_k64(base + kProdA[q] * G::A_TILE + off);
+            const uint64_t bd = sdesc_k64(base + T * G::A_TILE + kProdX[q] * G::B_TILE + off);
             umma(acc, a, bd, idesc, (kb != sg.kb0 || kk != 0 || q != 0) ? 1u : 0u);
           }
         }
@@ -393,7 +393,7 @@ static int tc_product_t(ccg_handle* h, ccg_operator* op, const float2* X, float2
                                                  static_cast<__nv_bfloat16*>(op->tc_ahi));
     for (int t = 0; t < T; ++t)
       if (!tc::make_map(reinterpret_cast<CUtensorMap*>(op->tc_map[t]), static_cast<char*>(op->tc_ahi) + t * abytes, n,
-                        2 * n, tc::BM)) {
+                        2 * n, tc::BM, tc::BK)) {
         set_error("cuTensorMapEncodeTiled failed for the matrix");
         return CCG_ERR_CUDA;
       }
@@ -447,7 +447,7 @@ static int tc_product_t(ccg_handle* h, ccg_operator* op, const float2* X, float2
   std::memset(&maps, 0, sizeof(maps));
   for (int t = 0; t < T; ++t) {
     std::memcpy(&maps.a[t], op->tc_map[t], sizeof(CUtensorMap));
-    if (!tc::make_map(&maps.x[t], reinterpret_cast<char*>(xs) + t * xb, 2 * k, 2 * n, G::BN)) {
+    if (!tc::make_map(&maps.x[t], reinterpret_cast<char*>(xs) + t * xb, 2 * k, 2 * n, G::BN, tc::BK)) {
       set_error("cuTensorMapEncodeTiled failed for the block");
       return CCG_ERR_CUDA;
     }
