@@ -64,6 +64,9 @@ struct BPhaseBase {
   __device__ __forceinline__ bool active(int c, const BCols& s) const { return !s.done[c]; }
 };
 
+// Rows whose operands one thread loads before it applies them.
+constexpr int kRowsIn = 4;
+
 template <class P>
 __global__ void __launch_bounds__(kBlock) bphase_kernel(P p, BCtl* ctl, BCols cols, Red red) {
   if (ctl->all_done) return;
@@ -75,8 +78,19 @@ __global__ void __launch_bounds__(kBlock) bphase_kernel(P p, BCtl* ctl, BCols co
   for (int q = 0; q < P::NQ; ++q) acc_zero(acc[q]);
   if (rs < rpar && p.active(c, cols)) {
     typename P::Col cs = p.col(c, cols);
-    for (int64_t row = (int64_t)blockIdx.x * rpar + rs; row < p.n; row += (int64_t)gridDim.x * rpar)
-      p.element(row, c, cs, acc);
+    // kRowsIn rows' operands are loaded before any of them is applied (no
+    // phase writes an element another row reads), then applied in row
+    // order, so each thread's sums keep the one-row-at-a-time order
+    const int64_t stride = (int64_t)gridDim.x * rpar;
+    int64_t row = (int64_t)blockIdx.x * rpar + rs;
+    for (; row + (kRowsIn - 1) * stride < p.n; row += kRowsIn * stride) {
+      typename P::In in[kRowsIn];
+#pragma unroll
+      for (int u = 0; u < kRowsIn; ++u) in[u] = p.load((row + u * stride) * k + c, cs);
+#pragma unroll
+      for (int u = 0; u < kRowsIn; ++u) p.apply((row + u * stride) * k + c, cs, in[u], acc);
+    }
+    for (; row < p.n; row += stride) p.apply(row * k + c, cs, p.load(row * k + c, cs), acc);
   }
   if (!P::kReduce) return;
   __shared__ double sred[P::NQ][kBlock];
@@ -202,10 +216,16 @@ template <class R> struct BInit : BPhaseBase {
   cx<R>* rh;
   __device__ __forceinline__ bool active(int c, const BCols& s) const { return !s.done[c] && !(s.skip && s.skip[c]); }
   __device__ __forceinline__ Col col(int, const BCols&) const { return Col(); }
-  __device__ __forceinline__ void element(int64_t row, int c, const Col&, Acc* acc) const {
-    const int64_t e = row * k + c;
-    const cx<R> yi = y[e];
-    const cx<R> ri = ax ? csub(yi, ax[e]) : yi;
+  struct In { cx<R> y, ax; };
+  __device__ __forceinline__ In load(int64_t e, const Col&) const {
+    In in;
+    in.y = y[e];
+    in.ax = ax ? ax[e] : mk<R>(0, 0);
+    return in;
+  }
+  __device__ __forceinline__ void apply(int64_t e, const Col&, const In& in, Acc* acc) const {
+    const cx<R> yi = in.y;
+    const cx<R> ri = ax ? csub(yi, in.ax) : yi;
     r[e] = ri;
     rh[e] = ri;
     b_nrm2(acc, yi);
@@ -253,9 +273,16 @@ template <class R> struct BP : BPhaseBase {  // p = r (first) or r + beta (p - o
     o.omega = narrow<R>(s.omega[c]);
     return o;
   }
-  __device__ __forceinline__ void element(int64_t row, int c, const Col& o, double*) const {
-    const int64_t e = row * k + c;
-    p[e] = o.first ? r[e] : cadd(r[e], cmul(o.beta, csub(p[e], cmul(o.omega, v[e]))));
+  struct In { cx<R> r, p, v; };
+  __device__ __forceinline__ In load(int64_t e, const Col& o) const {
+    In in;
+    in.r = r[e];
+    in.p = o.first ? mk<R>(0, 0) : p[e];
+    in.v = o.first ? mk<R>(0, 0) : v[e];
+    return in;
+  }
+  __device__ __forceinline__ void apply(int64_t e, const Col& o, const In& in, double*) const {
+    p[e] = o.first ? in.r : cadd(in.r, cmul(o.beta, csub(in.p, cmul(o.omega, in.v))));
   }
   __device__ void finish(int, const double*, const BCols&, const BCtl*) const {}
 };
@@ -269,10 +296,9 @@ template <class R> struct BSigma : BPhaseBase {  // alpha = rho / <r^, v>
   const cx<R>* rh;
   const cx<R>* v;
   __device__ __forceinline__ Col col(int, const BCols&) const { return Col(); }
-  __device__ __forceinline__ void element(int64_t row, int c, const Col&, Acc* acc) const {
-    const int64_t e = row * k + c;
-    b_dotc(acc, rh[e], v[e]);
-  }
+  struct In { cx<R> rh, v; };
+  __device__ __forceinline__ In load(int64_t e, const Col&) const { return In{rh[e], v[e]}; }
+  __device__ __forceinline__ void apply(int64_t, const Col&, const In& in, Acc* acc) const { b_dotc(acc, in.rh, in.v); }
   __device__ void finish(int c, const double* t, const BCols& s, const BCtl*) const {
     const double2 sigma = mkc(t[0], t[1]);
     if (b_tiny<R>(sigma)) { col_stop(s, c, ST_BREAKDOWN, CCG_BD_SIGMA); return; }
@@ -290,9 +316,10 @@ template <class R> struct BS : BPhaseBase {  // s = r - alpha v; half-step exit 
   const cx<R>* v;
   cx<R>* sv;
   __device__ __forceinline__ Col col(int c, const BCols& s) const { Col o; o.alpha = narrow<R>(s.alpha[c]); return o; }
-  __device__ __forceinline__ void element(int64_t row, int c, const Col& o, Acc* acc) const {
-    const int64_t e = row * k + c;
-    const cx<R> si = csub(r[e], cmul(o.alpha, v[e]));
+  struct In { cx<R> r, v; };
+  __device__ __forceinline__ In load(int64_t e, const Col&) const { return In{r[e], v[e]}; }
+  __device__ __forceinline__ void apply(int64_t e, const Col& o, const In& in, Acc* acc) const {
+    const cx<R> si = csub(in.r, cmul(o.alpha, in.v));
     sv[e] = si;
     b_nrm2(acc, si);
   }
@@ -312,10 +339,11 @@ template <class R> struct BOmega : BPhaseBase {  // omega = <t, s> / <t, t>
   const cx<R>* sv;
   __device__ __forceinline__ bool active(int c, const BCols& s) const { return !s.done[c] && !s.half[c]; }
   __device__ __forceinline__ Col col(int, const BCols&) const { return Col(); }
-  __device__ __forceinline__ void element(int64_t row, int c, const Col&, Acc* acc) const {
-    const int64_t e = row * k + c;
-    b_dotc(acc, t[e], sv[e]);
-    b_nrm2(acc + 2, t[e]);
+  struct In { cx<R> t, s; };
+  __device__ __forceinline__ In load(int64_t e, const Col&) const { return In{t[e], sv[e]}; }
+  __device__ __forceinline__ void apply(int64_t, const Col&, const In& in, Acc* acc) const {
+    b_dotc(acc, in.t, in.s);
+    b_nrm2(acc + 2, in.t);
   }
   __device__ void finish(int c, const double* q, const BCols& s, const BCtl*) const {
     if (s.half[c]) return;
@@ -345,16 +373,26 @@ template <class R> struct BXR : BPhaseBase {  // x += alpha p + omega s; r = s -
     o.half = s.half[c] != 0;
     return o;
   }
-  __device__ __forceinline__ void element(int64_t row, int c, const Col& o, Acc* acc) const {
-    const int64_t e = row * k + c;
+  struct In { cx<R> x, p, s, t, rh; };
+  __device__ __forceinline__ In load(int64_t e, const Col& o) const {
+    In in;
+    in.x = x[e];
+    in.p = p[e];
+    const cx<R> z = mk<R>(0, 0);
+    in.s = o.half ? z : sv[e];
+    in.t = o.half ? z : t[e];
+    in.rh = o.half ? z : rh[e];
+    return in;
+  }
+  __device__ __forceinline__ void apply(int64_t e, const Col& o, const In& in, Acc* acc) const {
     if (o.half) {
-      x[e] = cadd(x[e], cmul(o.alpha, p[e]));
+      x[e] = cadd(in.x, cmul(o.alpha, in.p));
       return;
     }
-    x[e] = cadd(x[e], cadd(cmul(o.alpha, p[e]), cmul(o.omega, sv[e])));
-    const cx<R> ri = csub(sv[e], cmul(o.omega, t[e]));
+    x[e] = cadd(in.x, cadd(cmul(o.alpha, in.p), cmul(o.omega, in.s)));
+    const cx<R> ri = csub(in.s, cmul(o.omega, in.t));
     r[e] = ri;
-    b_dotc(acc, rh[e], ri);
+    b_dotc(acc, in.rh, ri);
     b_nrm2(acc + 2, ri);
   }
   __device__ void finish(int c, const double* q, const BCols& s, const BCtl* ctl) const {
@@ -388,10 +426,16 @@ struct BRefResid : BPhaseBase {  // r32 = round(y - A x), d32 = 0; outer residua
   float2* d32;
   int outer;
   __device__ __forceinline__ Col col(int, const BCols&) const { return Col(); }
-  __device__ __forceinline__ void element(int64_t row, int c, const Col&, double* acc) const {
-    const int64_t e = row * k + c;
-    const double2 yi = y[e];
-    const double2 ri = ax ? csub(yi, ax[e]) : yi;
+  struct In { double2 y, ax; };
+  __device__ __forceinline__ In load(int64_t e, const Col&) const {
+    In in;
+    in.y = y[e];
+    in.ax = ax ? ax[e] : make_double2(0.0, 0.0);
+    return in;
+  }
+  __device__ __forceinline__ void apply(int64_t e, const Col&, const In& in, double* acc) const {
+    const double2 yi = in.y;
+    const double2 ri = ax ? csub(yi, in.ax) : yi;
     r32[e] = make_float2((float)ri.x, (float)ri.y);
     d32[e] = make_float2(0.f, 0.f);
     acc[0] += yi.x * yi.x + yi.y * yi.y;
@@ -427,10 +471,10 @@ struct BRefUpdate : BPhaseBase {  // x += widen(d32) for columns still refining
   double2* x;
   const float2* d32;
   __device__ __forceinline__ Col col(int, const BCols&) const { return Col(); }
-  __device__ __forceinline__ void element(int64_t row, int c, const Col&, double*) const {
-    const int64_t e = row * k + c;
-    const float2 d = d32[e];
-    x[e] = cadd(x[e], make_double2((double)d.x, (double)d.y));
+  struct In { double2 x; float2 d; };
+  __device__ __forceinline__ In load(int64_t e, const Col&) const { return In{x[e], d32[e]}; }
+  __device__ __forceinline__ void apply(int64_t e, const Col&, const In& in, double*) const {
+    x[e] = cadd(in.x, make_double2((double)in.d.x, (double)in.d.y));
   }
   __device__ void finish(int, const double*, const BCols&, const BCtl*) const {}
 };
@@ -445,10 +489,9 @@ struct BMidResid : BPhaseBase {  // rm = r - A d (complex64, exact product)
   const float2* ad;
   float2* rm;
   __device__ __forceinline__ Col col(int, const BCols&) const { return Col(); }
-  __device__ __forceinline__ void element(int64_t row, int c, const Col&, double*) const {
-    const int64_t e = row * k + c;
-    rm[e] = csub(r[e], ad[e]);
-  }
+  struct In { float2 r, ad; };
+  __device__ __forceinline__ In load(int64_t e, const Col&) const { return In{r[e], ad[e]}; }
+  __device__ __forceinline__ void apply(int64_t e, const Col&, const In& in, double*) const { rm[e] = csub(in.r, in.ad); }
   __device__ void finish(int, const double*, const BCols&, const BCtl*) const {}
 };
 struct BMidAdd : BPhaseBase {  // d += e
@@ -460,10 +503,9 @@ struct BMidAdd : BPhaseBase {  // d += e
   float2* d;
   const float2* e;
   __device__ __forceinline__ Col col(int, const BCols&) const { return Col(); }
-  __device__ __forceinline__ void element(int64_t row, int c, const Col&, double*) const {
-    const int64_t x = row * k + c;
-    d[x] = cadd(d[x], e[x]);
-  }
+  struct In { float2 d, e; };
+  __device__ __forceinline__ In load(int64_t i, const Col&) const { return In{d[i], e[i]}; }
+  __device__ __forceinline__ void apply(int64_t i, const Col&, const In& in, double*) const { d[i] = cadd(in.d, in.e); }
   __device__ void finish(int, const double*, const BCols&, const BCtl*) const {}
 };
 
@@ -536,8 +578,20 @@ template <class R> struct BRun {
   BWs<R> w;
   Red red;
 
+  // A phase runs on at most its resident blocks (one wave: the rows a
+  // thread loads ahead need registers, so heavier phases fit fewer blocks);
+  // the reduction's slots and counters are sized for `grid`, the largest.
   template <class P> void phase(const P& p) {
-    bphase_kernel<P><<<grid, kBlock, 0, s>>>(p, w.ctl, w.cols, red);
+    static const int occ = [] {
+      int o = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, bphase_kernel<P>, kBlock, 0) != cudaSuccess) {
+        cudaGetLastError();
+        o = 1;
+      }
+      return o < 1 ? 1 : o;
+    }();
+    const int g = (int)std::min<int64_t>(grid, (int64_t)h->num_sms * occ);
+    bphase_kernel<P><<<g, kBlock, 0, s>>>(p, w.ctl, w.cols, red);
     ++h->launches;
   }
   // C = A B.  complex64 products go to the split-bf16 tensor-core product
