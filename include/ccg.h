@@ -378,9 +378,12 @@ ccg_status ccg_block_matvec(ccg_handle* h, const ccg_operator* op, int64_t nrhs,
  * with programmatic dependent launch (each starts launching while the one
  * before finishes and waits for it inside); 0 plain stream order.  Results
  * are the same either way.
- * CCG_OPT_TEST_WITHHOLD: test hook; 1 makes one block of the next persistent
- * launches leave without arriving at the first barrier, so that the others'
- * waits expire (use with a small CCG_OPT_WAIT_LIMIT); 0 (default) off.
+ * CCG_OPT_TEST_WITHHOLD: test hook (use with a small CCG_OPT_WAIT_LIMIT);
+ * 1 makes one block of the next persistent launches leave without arriving
+ * at the first barrier, and the tensor-core products' TMA producers issue no
+ * copies, so that the waits on them expire; 2 makes the first K range of the
+ * split-bf16 product keep its partial tile unpublished, so that the CTA
+ * finishing that tile waits in vain; 0 (default) off.
  * ccg_set_option returns CCG_ERR_INVALID (and leaves the handle unchanged)
  * for a NULL handle, an unknown option or a value out of range; options
  * apply to the handle's later calls. */

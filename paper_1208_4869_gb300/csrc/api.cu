@@ -524,7 +524,7 @@ ccg_status ccg_set_option(ccg_handle* h, int option, int value) {
     h->wait_limit = value == 0 ? (4ll << 30) : ((long long)value << 10);
     return CCG_OK;
   }
-  if (option == CCG_OPT_TEST_WITHHOLD && (value == 0 || value == 1)) {
+  if (option == CCG_OPT_TEST_WITHHOLD && value >= 0 && value <= 2) {
     h->test_withhold = value;
     return CCG_OK;
   }

@@ -619,7 +619,7 @@ int pk_solve_jobs(ccg_handle* h, int method, int count, const PkJob<R>* jobs, ch
   PK_CUDA(cudaMemsetAsync(dbar, 0, bar_bytes + 256 + (size_t)count * 4 * sizeof(int), s));
 
   const long long limit = h->wait_limit;
-  const int withhold = h->test_withhold;
+  const int withhold = h->test_withhold == 1;
   void* args[] = {(void*)&dsys, (void*)&count, (void*)&limit, (void*)&dfault, (void*)&withhold};
   timing_begin(h);
   PK_CUDA(cudaLaunchCooperativeKernel(fn, dim3(b0), dim3(kBlock), args, 0, s));

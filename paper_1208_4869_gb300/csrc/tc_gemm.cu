@@ -125,7 +125,7 @@ template <int T>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_bf16_split(const __grid_constant__ TcMaps maps, float* __restrict__ C, int M, int N, int K, int64_t ldc,
                     Split sp, float* __restrict__ work, unsigned* flags, unsigned epoch, int* err,
-                    const int* skip, int* skip_rec, long long wait_limit, int withhold) {
+                    const int* skip, int* skip_rec, long long wait_limit, int withhold, int nopub) {
   using G = Cfg<T>;
   constexpr int BN = G::BN;
   if (skip != nullptr && *skip) {  // every column has stopped
@@ -289,7 +289,8 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
         }
       }
-      if (!last) {  // publish this warp's rows of the partial tile
+      if (!last && !(nopub && p == 0)) {  // publish this warp's rows of the partial tile
+        // (nopub: test hook, range 0 never publishes, so its finisher's wait runs out)
         __threadfence();
         __syncwarp();
         if (lane == 0) st_release(&flags[cta * 4 + q], epoch);
@@ -462,7 +463,7 @@ static int tc_product_t(ccg_handle* h, ccg_operator* op, const float2* X, float2
   }
   tc::gemm_bf16_split<T><<<ctas, tc::THREADS, G::SMEM_BYTES, s>>>(
       maps, reinterpret_cast<float*>(Y), (int)n, Nr, (int)(2 * n), (int64_t)Nr, sp, work, flags, h->tc_epoch, err,
-      skip, timing_rec(h), h->wait_limit, h->test_withhold ? 0 : -1);
+      skip, timing_rec(h), h->wait_limit, h->test_withhold == 1 ? 0 : -1, h->test_withhold == 2);
   h->launches += 2;
   return cudaGetLastError() == cudaSuccess ? CCG_OK : CCG_ERR_CUDA;
 }

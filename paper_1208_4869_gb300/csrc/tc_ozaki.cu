@@ -463,7 +463,7 @@ static int oz_product_t(ccg_handle* h, ccg_operator* op, const cx<R>* X, cx<R>* 
   dim3 grid((unsigned)((Nr + G::BN - 1) / G::BN), (unsigned)((n + BM - 1) / BM));
   ozaki_gemm<S, R><<<grid, THREADS, G::SMEM_BYTES, s>>>(maps, erow, fcol, reinterpret_cast<R*>(Y), (int)n, Nr,
                                                         (int)(2 * n), (int64_t)Nr, err, skip, timing_rec(h),
-                                                        h->wait_limit, h->test_withhold ? 0 : -1);
+                                                        h->wait_limit, h->test_withhold == 1 ? 0 : -1);
   h->launches += 3;
   return cudaGetLastError() == cudaSuccess ? CCG_OK : CCG_ERR_CUDA;
 }

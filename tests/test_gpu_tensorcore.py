@@ -156,3 +156,30 @@ def test_pipeline_wait_runs_out(ccg, prec):
     torch.cuda.synchronize()
     bound = tc_bound(n) if dt == np.complex64 else 1e-13
     assert err(Y.cpu().numpy(), A, X) <= bound
+
+
+def test_stream_k_partial_wait_runs_out(ccg):
+    """The split-bf16 product's stream-K flag wait: with the test hook the
+    first K range keeps its partial tile unpublished, so the CTA that
+    finishes that tile waits for it until the (short) limit runs out; the
+    call returns CCG_ERR_TIMEOUT, and the next product on the same handle is
+    correct.  n = 1000, k = 37: 8 row blocks of 63 K blocks in 15 ranges, so
+    the first range ends inside row block 0."""
+    n, k = 1000, 37
+    A, _ = W.dense_system(n, 1.0, 6, dtype=np.complex64)
+    X = W.dense_rhs_block(n, k, seed=7, dtype=np.complex64)
+    h = ccg.Handle()
+    op = h.op_dense(torch.from_numpy(A).cuda())
+    Y = colmajor(np.zeros(X.shape, np.complex64))
+    h.block_matvec(op, colmajor(X), Y)
+    h.set_option(ccg.OPT_WAIT_LIMIT, 64)           # 64 Ki cycles, ~30 us
+    h.set_option(ccg.OPT_TEST_WITHHOLD, 2)
+    with pytest.raises(ccg.CcgError) as e:
+        h.block_matvec(op, colmajor(X), Y)
+    assert e.value.status == ccg.ERR_TIMEOUT
+    h.set_option(ccg.OPT_TEST_WITHHOLD, 0)
+    h.set_option(ccg.OPT_WAIT_LIMIT, 0)
+    Y = colmajor(np.zeros(X.shape, np.complex64))
+    h.block_matvec(op, colmajor(X), Y)
+    torch.cuda.synchronize()
+    assert err(Y.cpu().numpy(), A, X) <= tc_bound(n)
