@@ -529,6 +529,23 @@ int64_t ccg_launch_count(const ccg_handle* h);
  * 0..4, CCG_ERR_CUDA when a CUDA call fails. */
 ccg_status ccg_pipe_rate(ccg_handle* h, int pipe, double* gops);
 
+/* Host-side check of the work split of the complex64 block product on the
+ * tensor cores (diagnostic; no device work, no GPU needed; the paper has no
+ * counterpart).  For an n x n operator, k right-hand sides, `terms` bf16
+ * terms (2 or 3) and `sms` SMs it runs the cut that the product's launcher
+ * and kernel use -- the R = row blocks x K blocks units cut into equal
+ * ranges, one CTA per range and column tile -- and verifies: every (row
+ * block, column tile, K block) is computed exactly once and lies inside the
+ * operator; every output tile has one finishing CTA; a CTA leaves at most its
+ * first segment unfinished; the CTAs a finisher waits for are lower-numbered
+ * and their unfinished pieces are exactly the tile's earlier K blocks; their
+ * partial-tile and flag indexes stay inside the buffers sized for the launch.
+ * *ctas receives the launch's CTA count, *bad the number of violations (0
+ * when the cut is sound).  CCG_ERR_INVALID for n < 1, k outside 1..256,
+ * terms other than 2 or 3, sms < 1 or a NULL output; CCG_ERR_NOMEM when the
+ * host bookkeeping cannot be allocated. */
+ccg_status ccg_check_block_schedule(int64_t n, int k, int terms, int sms, int* ctas, int64_t* bad);
+
 /* Allocation-free y = A^H x for a dense matrix.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
  * device memory -- for instance a host program whose device memory is all

@@ -136,6 +136,8 @@ def lib():
     L.ccg_launch_count.argtypes = [vp]
     L.ccg_pipe_rate.restype = i32
     L.ccg_pipe_rate.argtypes = [vp, i32, ctypes.POINTER(dbl)]
+    L.ccg_check_block_schedule.restype = i32
+    L.ccg_check_block_schedule.argtypes = [i64, i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i64)]
     for name in ("ccg_create", "ccg_destroy", "ccg_set_stream", "ccg_op_dense", "ccg_op_dipole", "ccg_op_destroy", "ccg_matvec",
                  "ccg_dot", "ccg_solve", "ccg_solve_refined", "ccg_solve_batched", "ccg_solve_batched_refined",
                  "ccg_block_matvec", "ccg_set_option", "ccg_solve_multi", "ccg_solve_multi_refined", "ccg_server_create", "ccg_server_submit", "ccg_server_poll",
@@ -421,6 +423,14 @@ def make_request(kind="dense", n=0, nrhs=1, shift=3.0, seed=0, L=0, kd=0.5, m=1.
     r.kd, r.m_re, r.m_im, r.tol, r.keep_x = float(kd), complex(m).real, complex(m).imag, float(tol), int(keep_x)
     r.mode = int(mode)
     return r
+
+
+def check_block_schedule(n, k, terms, sms):
+    """ccg_check_block_schedule: (CTAs of the launch, violations found) of the
+    tensor-core block product's work split, checked on the host."""
+    ctas, bad = ctypes.c_int(), ctypes.c_int64()
+    _check(lib().ccg_check_block_schedule(n, k, terms, sms, ctypes.byref(ctas), ctypes.byref(bad)))
+    return ctas.value, bad.value
 
 
 def server_estimate(**req):

@@ -45,6 +45,7 @@
 #include <algorithm>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -79,12 +80,29 @@ struct Split {
   __host__ __device__ int64_t begin(int p) const { return (int64_t)nrb * nkb * p / P; }
 };
 
+// The cut for an n x n operator, k right-hand sides and `sms` SMs (one CTA
+// per SM): P ranges of row units, ncol column tiles each.
+template <int T> static Split make_split(int64_t n, int k, int sms) {
+  Split sp;
+  sp.nrb = (int)((n + BM - 1) / BM);
+  sp.nkb = (int)((2 * n + BK - 1) / BK);
+  sp.ncol = (2 * k + Cfg<T>::BN - 1) / Cfg<T>::BN;
+  const int64_t units = (int64_t)sp.nrb * sp.nkb;
+  sp.P = (int)std::min<int64_t>(std::max(1, sms / sp.ncol), std::max<int64_t>(1, units / MIN_UNITS));
+  return sp;
+}
+
+// Segments of range [u0, u1) (one per row block it touches).
+__host__ __device__ __forceinline__ int segments(const Split& sp, int64_t u0, int64_t u1) {
+  return (int)((u1 - 1) / sp.nkb - u0 / sp.nkb) + 1;
+}
+
 // Segment si of range [u0, u1): its row block and K blocks [kb0, kb1).  The
 // last row block (the only one a range can cut short) comes first.
 struct Seg {
   int r, kb0, kb1;
 };
-__device__ __forceinline__ Seg segment(const Split& sp, int64_t u0, int64_t u1, int si) {
+__host__ __device__ __forceinline__ Seg segment(const Split& sp, int64_t u0, int64_t u1, int si) {
   const int rlo = (int)(u0 / sp.nkb), rhi = (int)((u1 - 1) / sp.nkb);
   const int r = si == 0 ? rhi : rlo + si - 1;
   const int64_t base = (int64_t)r * sp.nkb;
@@ -93,6 +111,15 @@ __device__ __forceinline__ Seg segment(const Split& sp, int64_t u0, int64_t u1, 
   g.kb0 = (int)((u0 > base ? u0 : base) - base);
   g.kb1 = (int)((u1 < base + sp.nkb ? u1 : base + sp.nkb) - base);
   return g;
+}
+
+// The lowest range holding K blocks of row block r, for the range p that
+// finishes it: ranges first .. p - 1 hold its earlier K blocks.
+__host__ __device__ __forceinline__ int first_contributor(const Split& sp, int p, int r) {
+  const int64_t rs = (int64_t)r * sp.nkb;
+  int pf = p - 1;
+  while (sp.begin(pf) > rs) --pf;
+  return pf;
 }
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -145,7 +172,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int cta = blockIdx.x, p = cta / sp.ncol, ct = cta - p * sp.ncol;
   const int n0 = ct * BN;
   const int64_t u0 = sp.begin(p), u1 = sp.begin(p + 1);
-  const int nseg = (int)((u1 - 1) / sp.nkb - u0 / sp.nkb) + 1;
+  const int nseg = segments(sp, u0, u1);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -242,9 +269,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       // the lower ranges holding K blocks of this tile: pf .. p - 1
       int pf = p;
       if (last && sg.kb0 > 0) {
-        const int64_t rs = (int64_t)sg.r * sp.nkb;
-        pf = p - 1;
-        while (sp.begin(pf) > rs) --pf;
+        pf = first_contributor(sp, p, sg.r);
         bool ok = true;
         for (int pp = pf; pp < p && ok; ++pp) ok = flag_wait(&flags[(pp * sp.ncol + ct) * 4 + q], epoch, verr, wait_limit);
         if (!__all_sync(0xffffffffu, ok)) break;
@@ -404,12 +429,7 @@ static int tc_product_t(ccg_handle* h, ccg_operator* op, const float2* X, float2
   // the handle's staging: error flag (256 B), the ranges' flags (4 per CTA),
   // the T bf16 terms of Xh^T (2k x 2n each), one partial tile per CTA
   const int Nr = 2 * k;
-  tc::Split sp;
-  sp.nrb = (int)((n + tc::BM - 1) / tc::BM);
-  sp.nkb = (int)((2 * n + tc::BK - 1) / tc::BK);
-  sp.ncol = (Nr + G::BN - 1) / G::BN;
-  const int64_t units = (int64_t)sp.nrb * sp.nkb;
-  sp.P = (int)std::min<int64_t>(std::max(1, h->num_sms / sp.ncol), std::max<int64_t>(1, units / tc::MIN_UNITS));
+  const tc::Split sp = tc::make_split<T>(n, k, h->num_sms);
   const int ctas = sp.P * sp.ncol;
   const size_t flag_bytes = ((size_t)ctas * 4 * sizeof(unsigned) + 255) / 256 * 256;
   const size_t xb = (size_t)2 * k * 2 * n * sizeof(__nv_bfloat16);
@@ -475,6 +495,66 @@ int tc_block_product(ccg_handle* h, const ccg_operator* op_c, const float2* X, f
   return h->tc_terms == 2 ? tc_product_t<2>(h, op, X, Y, k, skip) : tc_product_t<3>(h, op, X, Y, k, skip);
 }
 
+namespace tc {
+// Host run of the cut the product uses (launcher and kernel functions), with
+// every invariant the kernel relies on checked; returns the violations.
+template <int T> static int64_t check_cut(int64_t n, int k, int sms, int* ctas_out) {
+  const Split sp = make_split<T>(n, k, sms);
+  const int ctas = sp.P * sp.ncol;
+  *ctas_out = ctas;
+  int64_t bad = 0;
+  const int64_t units = (int64_t)sp.nrb * sp.nkb;
+  // computed[(tile) * nkb + kb], tile = r * ncol + c; published[tile]: ranges
+  // that left a piece of the tile unfinished; finished[tile]: its finishers
+  std::vector<unsigned char> computed((size_t)units * sp.ncol, 0);
+  std::vector<std::vector<int>> published((size_t)sp.nrb * sp.ncol);
+  std::vector<int> finished((size_t)sp.nrb * sp.ncol, 0);
+  struct Fin { int p, c, r, pf; };
+  std::vector<Fin> fins;
+  if (sp.P < 1 || sp.ncol * Cfg<T>::BN < 2 * k) ++bad;
+  for (int cta = 0; cta < ctas; ++cta) {
+    const int p = cta / sp.ncol, c = cta - p * sp.ncol;
+    const int64_t u0 = sp.begin(p), u1 = sp.begin(p + 1);
+    if (!(u1 > u0)) { ++bad; continue; }
+    const int nseg = segments(sp, u0, u1);
+    for (int si = 0; si < nseg; ++si) {
+      const Seg g = segment(sp, u0, u1, si);
+      if (g.r < 0 || g.r >= sp.nrb || g.kb0 < 0 || g.kb0 >= g.kb1 || g.kb1 > sp.nkb) { ++bad; continue; }
+      const size_t tile = (size_t)g.r * sp.ncol + c;
+      for (int kb = g.kb0; kb < g.kb1; ++kb) {
+        if (computed[tile * sp.nkb + kb]++) ++bad;  // a unit computed twice
+        if ((int64_t)kb * BK >= 2 * n) ++bad;       // a K block past the operator
+      }
+      if (g.kb1 < sp.nkb) {
+        if (si != 0) ++bad;  // only a range's first segment may be unfinished
+        published[tile].push_back(p);
+      } else {
+        ++finished[tile];
+        const int pf = g.kb0 > 0 ? first_contributor(sp, p, g.r) : p;
+        if (pf < 0 || pf > p) ++bad;
+        fins.push_back({p, c, g.r, pf});
+      }
+    }
+  }
+  for (size_t u = 0; u < computed.size(); ++u)
+    if (computed[u] != 1) ++bad;  // a unit missed (or counted above)
+  for (size_t t = 0; t < finished.size(); ++t)
+    if (finished[t] != 1) ++bad;  // a tile with no or several finishers
+  for (const Fin& f : fins) {
+    // the finisher waits for ranges pf .. p - 1, lower CTAs whose unfinished
+    // pieces of this tile are exactly those
+    std::vector<int> want;
+    for (int q = f.pf; q < f.p; ++q) want.push_back(q);
+    std::vector<int> got = published[(size_t)f.r * sp.ncol + f.c];
+    std::sort(got.begin(), got.end());
+    if (got != want) ++bad;
+    for (int q : want)
+      if (q * sp.ncol + f.c >= f.p * sp.ncol + f.c || (q * sp.ncol + f.c) * 4 + 3 >= ctas * 4) ++bad;
+  }
+  return bad;
+}
+}  // namespace tc
+
 // Error flag of the tensor-core pipeline (a bounded wait gave up): read and clear.
 int tc_check_error(ccg_handle* h) {
   if (!h->tc_buf) return CCG_OK;
@@ -496,3 +576,17 @@ void tc_free(ccg_operator* op) {
 }
 
 }  // namespace ccg
+
+extern "C" ccg_status ccg_check_block_schedule(int64_t n, int k, int terms, int sms, int* ctas, int64_t* bad) {
+  if (n < 1 || k < 1 || k > 256 || (terms != 2 && terms != 3) || sms < 1 || !ctas || !bad) {
+    ccg::set_error("ccg_check_block_schedule: need n >= 1, 1 <= k <= 256, terms 2 or 3, sms >= 1, outputs");
+    return CCG_ERR_INVALID;
+  }
+  try {
+    *bad = terms == 2 ? ccg::tc::check_cut<2>(n, k, sms, ctas) : ccg::tc::check_cut<3>(n, k, sms, ctas);
+  } catch (const std::bad_alloc&) {
+    ccg::set_error("ccg_check_block_schedule: host allocation failed");
+    return CCG_ERR_NOMEM;
+  }
+  return CCG_OK;
+}
