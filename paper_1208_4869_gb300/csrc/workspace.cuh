@@ -109,10 +109,8 @@ template <class R> struct Dense {
     lda = op->lda;
     n = op->n;
     unit = unit_override > 0 ? unit_override : op->unit;
-    const int64_t rows_blocks = (n + kWarps - 1) / kWarps;
     grid_rows = (int)std::min<int64_t>((n + kWarps / kRowSplit - 1) / (kWarps / kRowSplit), 1 << 30);
     grid_fx = (int)std::min<int64_t>((n + kWarps / kFxSplit - 1) / (kWarps / kFxSplit), 1 << 30);
-    (void)rows_blocks;
     const int64_t nunits = n / unit;
     ncb = (int)((nunits + 32 * E - 1) / (32 * E));
     dense = op->kind == CCG_OPK_DENSE;
