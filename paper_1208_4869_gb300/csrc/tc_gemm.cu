@@ -382,13 +382,20 @@ __global__ void split_block(const float2* __restrict__ X, int64_t n, int k, __nv
     if (c < k && j < n) {
       const float2 x = tile[tx][r];
       const float vals[4] = {x.x, -x.y, x.y, x.x};  // (2c, 2j), (2c, 2j+1), (2c+1, 2j), (2c+1, 2j+1)
+      // each row's pair (2j, 2j + 1) as one 4-byte store (coalesced across the warp)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int64_t e = (int64_t)(2 * c + (q >> 1)) * (2 * n) + 2 * j + (q & 1);
-        __nv_bfloat16 t[3];
-        split_terms<T>(vals[q], t);
+      for (int h = 0; h < 2; ++h) {
+        const int64_t e = (int64_t)(2 * c + h) * (2 * n) + 2 * j;
+        __nv_bfloat16 t0[3], t1[3];
+        split_terms<T>(vals[2 * h], t0);
+        split_terms<T>(vals[2 * h + 1], t1);
 #pragma unroll
-        for (int i = 0; i < T; ++i) out[i * count + e] = t[i];
+        for (int i = 0; i < T; ++i) {
+          __nv_bfloat162 pr;
+          pr.x = t0[i];
+          pr.y = t1[i];
+          *reinterpret_cast<__nv_bfloat162*>(out + i * count + e) = pr;
+        }
       }
     }
   }
